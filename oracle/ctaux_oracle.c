@@ -1,0 +1,774 @@
+/*
+ * ctaux_oracle.c -- TEST INFRASTRUCTURE ONLY (the oracle).
+ *
+ * A plain, slow, FP64 CPU implementation of the CT-AUX walker that the GPU
+ * library must reproduce.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline leg of bench.py may load this code; the product path never
+ * does.  It shares no code, header, table or helper with the CUDA library.
+ *
+ * What it follows (DCA++ paper, Sec. 2.3 "Continuous-time auxiliary-field
+ * quantum Monte Carlo"):
+ *   - expansion of Z in the interaction picture with the constant K
+ *     (Eq. Z_interaction_rep and the order-k expansion after it);
+ *   - the auxiliary-spin decoupling  1 - beta H_int / K =
+ *     (1/2N_corr) sum_s exp(gamma s (n_up - n_dn)),
+ *     cosh(gamma) = 1 + U beta N_corr / (2K), with N_corr = Nc for the
+ *     single-band Hubbard model (decoupling equations of Sec. 2.3);
+ *   - configuration weight (K / (2 beta N_corr))^k prod_sigma det N_sigma^-1
+ *     (Eq. Zk), sampled by Metropolis with single-spin insert / remove
+ *     moves, each a rank-1 change of N_sigma^-1 (text after Eq. Zk);
+ *   - sign tracking for the negative-sign problem (Sec. 2.3, end);
+ *   - the Green's function measured from M = (e^V - 1) N (the equation for
+ *     <G> in terms of M in Sec. 2.3), here on a tau grid.
+ *
+ * Readings where the paper is silent (each is listed in the design doc):
+ *   N_sigma^-1 = e^{V_sigma} - g0_sigma (e^{V_sigma} - 1),  g0 = -G0
+ *     (G0 in the paper's sign convention, negative on (0, beta)),
+ *     V_p^sigma = sigma * gamma * s_p for an interacting vertex, 0 otherwise;
+ *   equal-time entries use g0(0+); g0(tau - beta) = -g0(tau);
+ *   insert / remove proposed with probability 1/2 each, no spin flips;
+ *   acceptance  u < |R|,  R = K/(k+1) rho_up rho_dn (insert),
+ *                         R = k/K     rho_up rho_dn (remove);
+ *   a warm-up sweep is max(k, 1) proposals, k taken at the start of the
+ *     sweep; at the end of warm-up the sweep length is frozen to
+ *     L = max(1, round(mean of those k over the warm-up sweeps)) (or to
+ *     max(k, 1) when there is no warm-up), so that the measured sweeps
+ *     sample the stationary distribution (a state-dependent sweep length
+ *     would bias the configurations seen at measurement time);
+ *   random numbers: Philox4x32-10 (Salmon et al., SC'11) with
+ *     key = (lo32(seed), hi32(seed) ^ walker_id) and
+ *     counter = (lo32(j), hi32(j), tag, 0).
+ *
+ * The oracle does one proposal at a time with full rank-1 updates of N_sigma.
+ * An insertion first extends N by the new vertex as a non-interacting one
+ * (its row of N^-1 is -g0[p,:](e^V - 1), its column e_p), then changes V_p;
+ * the ratio is the matrix determinant lemma det(A + c e_p^T) / det(A) =
+ * 1 + e_p^T A^-1 c for A = N^-1 = I + (I - g0)(e^V - I), whose column p
+ * changes by c when V_p does, and N follows by Sherman-Morrison.  A removal
+ * uses Jacobi's identity (A^-1)_pp = det A_{\p\p} / det A for the ratio and
+ * the Schur-complement downdate for N.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ERR_ARG (-1)
+#define ORC_ERR_OOM (-3)
+#define ORC_ERR_NUMERIC (-5)
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10, from its definition in Salmon, Moraes, Dror, Shaw,  */
+/* "Parallel random numbers: as easy as 1, 2, 3" (SC'11): ten rounds  */
+/* of the 4x32 S-box with multipliers 0xD2511F53 / 0xCD9E8D57 and a   */
+/* Weyl key schedule with increments 0x9E3779B9 / 0xBB67AE85.          */
+/* ------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Uniform double in [0,1) with 53 random bits from two words. */
+static double u53(uint32_t hi, uint32_t lo)
+{
+    uint64_t w = ((uint64_t)hi << 32) | (uint64_t)lo;
+    return (double)(w >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* floor(w * m / 2^32): an index in [0, m) with no floating point. */
+static uint32_t index_of(uint32_t w, uint32_t m)
+{
+    return (uint32_t)(((uint64_t)w * (uint64_t)m) >> 32);
+}
+
+enum { TAG_PROPOSAL = 0, TAG_ACCEPT = 1, TAG_INIT = 2 };
+
+static void draw(const uint32_t key[2], uint64_t j, uint32_t tag, uint32_t out[4])
+{
+    uint32_t ctr[4] = {(uint32_t)j, (uint32_t)(j >> 32), tag, 0u};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* Parameters and state                                                */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int32_t nc;
+    const int32_t* site_sub;  /* [nc*nc] index of r_i - r_j folded into the cluster */
+    double U, beta, K;
+    int32_t n_tau;            /* table intervals; samples at l*beta/n_tau, l=0..n_tau */
+    const double* G0;         /* [2][nc][n_tau+1] paper sign convention */
+    int32_t warmup_sweeps;
+    int32_t n_tau_meas;       /* measurement grid: tau_a = (a + 1/2) beta / n_tau_meas */
+    uint64_t seed;
+    uint32_t walker_id;
+    int32_t init_config_size;
+    double tie_eps;           /* near-tie threshold on | |R| - u | */
+} orc_params;
+
+typedef struct {
+    int32_t nc, n_tau, n_meas_tau, warmup;
+    double U, beta, K, gamma, tie_eps;
+    int32_t* site_sub;        /* [nc*nc] */
+    int32_t* site_add;        /* [nc*nc]: site_add[y*nc + d] = x with site_sub[x*nc+y] == d */
+    double* g0;               /* [2][nc][n_tau+1], g0 = -G0 */
+    double expV[2][2];        /* e^{sigma gamma s}: [spin 0=up,1=dn][s 0:-1, 1:+1] */
+    uint32_t key[2];
+    uint64_t q;               /* next proposal index */
+    int32_t k, cap;
+    int32_t* vsite; double* vtau; int8_t* vs;
+    double* N[2];             /* k x k row-major, leading dimension cap */
+    double* work;             /* scratch vectors */
+    double sign;
+    int64_t sweeps_done;
+    int64_t warm_k_sum;       /* sum of k at the start of each warm-up sweep */
+    int64_t sweep_len;        /* frozen measured-sweep length, 0 until set */
+    double* Gacc;             /* [2][nc][n_tau_meas] sum of sign * G(paper convention) */
+    double sign_sum;
+    int64_t n_meas;
+    uint8_t* log; int64_t log_n, log_cap;
+    const uint8_t* hints; int64_t hints_n;
+    int64_t n_prop, n_acc, n_ties, n_adopted;
+    double k_sum; int64_t k_samples;
+} orc_walker;
+
+/* ------------------------------------------------------------------ */
+/* g0 interpolation: linear on the uniform tau grid, antiperiodic      */
+/* extension to (-beta, 0), dtau == 0 read as 0+.                      */
+/* ------------------------------------------------------------------ */
+static double g0_row(const double* row, int n_tau, double beta, double dtau)
+{
+    double sgn = 1.0;
+    if (dtau < 0.0) {
+        dtau += beta;
+        sgn = -1.0;
+    }
+    double x = dtau * ((double)n_tau / beta);
+    int l = (int)x;
+    if (l >= n_tau) l = n_tau - 1;
+    if (l < 0) l = 0;
+    double f = x - (double)l;
+    return sgn * (row[l] + f * (row[l + 1] - row[l]));
+}
+
+double orc_g0_interp(const double* row, int32_t n_tau, double beta, double dtau)
+{
+    return g0_row(row, n_tau, beta, dtau);
+}
+
+/* g0_sigma(r_a - r_b, tau_a - tau_b) */
+static double g0ab(const orc_walker* w, int sp, int32_t ra, double ta, int32_t rb, double tb)
+{
+    int d = w->site_sub[ra * w->nc + rb];
+    const double* row = w->g0 + ((size_t)sp * w->nc + d) * (size_t)(w->n_tau + 1);
+    return g0_row(row, w->n_tau, w->beta, ta - tb);
+}
+
+static double ev(const orc_walker* w, int sp, int8_t s) { return w->expV[sp][s > 0 ? 1 : 0]; }
+
+/* ------------------------------------------------------------------ */
+/* Dense FP64 helpers (plain loops)                                    */
+/* ------------------------------------------------------------------ */
+
+/* Build A = e^V - g0 (e^V - 1) for the given vertices, row-major n x n. */
+static void build_A(const orc_walker* w, int sp, int n, const int32_t* site, const double* tau,
+                    const int8_t* s, double* A)
+{
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) {
+            double evj = ev(w, sp, s[j]);
+            double gij = (i == j) ? g0ab(w, sp, site[i], 0.0, site[i], 0.0)
+                                  : g0ab(w, sp, site[i], tau[i], site[j], tau[j]);
+            A[(size_t)i * n + j] = ((i == j) ? evj : 0.0) - gij * (evj - 1.0);
+        }
+    }
+}
+
+/* Gauss-Jordan inverse with partial pivoting. A (n x n, row-major) is
+ * destroyed; inv gets the inverse with leading dimension ldi.  Returns the
+ * sign of det A (0 if singular). */
+static int gj_inverse(int n, double* A, double* inv, int ldi)
+{
+    int sgn = 1;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) inv[(size_t)i * ldi + j] = (i == j) ? 1.0 : 0.0;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        double best = fabs(A[(size_t)c * n + c]);
+        for (int r = c + 1; r < n; ++r) {
+            double v = fabs(A[(size_t)r * n + c]);
+            if (v > best) { best = v; piv = r; }
+        }
+        if (best == 0.0) return 0;
+        if (piv != c) {
+            sgn = -sgn;
+            for (int j = 0; j < n; ++j) {
+                double t = A[(size_t)c * n + j]; A[(size_t)c * n + j] = A[(size_t)piv * n + j]; A[(size_t)piv * n + j] = t;
+                t = inv[(size_t)c * ldi + j]; inv[(size_t)c * ldi + j] = inv[(size_t)piv * ldi + j]; inv[(size_t)piv * ldi + j] = t;
+            }
+        }
+        double d = A[(size_t)c * n + c];
+        if (d < 0.0) sgn = -sgn;
+        double rd = 1.0 / d;
+        for (int j = 0; j < n; ++j) { A[(size_t)c * n + j] *= rd; inv[(size_t)c * ldi + j] *= rd; }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            double f = A[(size_t)r * n + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < n; ++j) {
+                A[(size_t)r * n + j] -= f * A[(size_t)c * n + j];
+                inv[(size_t)r * ldi + j] -= f * inv[(size_t)c * ldi + j];
+            }
+        }
+    }
+    return sgn;
+}
+
+/* ------------------------------------------------------------------ */
+/* Creation                                                            */
+/* ------------------------------------------------------------------ */
+static int ensure_cap(orc_walker* w, int need)
+{
+    if (need <= w->cap) return ORC_OK;
+    int nc = w->cap ? w->cap : 16;
+    while (nc < need) nc *= 2;
+    int32_t* vsite = (int32_t*)realloc(w->vsite, sizeof(int32_t) * nc);
+    if (!vsite) return ORC_ERR_OOM;
+    w->vsite = vsite;
+    double* vtau = (double*)realloc(w->vtau, sizeof(double) * nc);
+    if (!vtau) return ORC_ERR_OOM;
+    w->vtau = vtau;
+    int8_t* vs = (int8_t*)realloc(w->vs, (size_t)nc);
+    if (!vs) return ORC_ERR_OOM;
+    w->vs = vs;
+    for (int sp = 0; sp < 2; ++sp) {
+        double* M = (double*)calloc((size_t)nc * nc, sizeof(double));
+        if (!M) return ORC_ERR_OOM;
+        for (int i = 0; i < w->k; ++i)
+            memcpy(M + (size_t)i * nc, w->N[sp] + (size_t)i * w->cap, sizeof(double) * w->k);
+        free(w->N[sp]);
+        w->N[sp] = M;
+    }
+    double* work = (double*)realloc(w->work, sizeof(double) * 8 * (size_t)nc);
+    if (!work) return ORC_ERR_OOM;
+    w->work = work;
+    w->cap = nc;
+    return ORC_OK;
+}
+
+void orc_destroy(orc_walker* w)
+{
+    if (!w) return;
+    free(w->site_sub); free(w->site_add); free(w->g0);
+    free(w->vsite); free(w->vtau); free(w->vs);
+    free(w->N[0]); free(w->N[1]); free(w->work);
+    free(w->Gacc); free(w->log);
+    free(w);
+}
+
+/* Rebuild both N matrices from the vertex list; sets the sign of
+ * prod_sigma det N_sigma^-1.  Returns ORC_ERR_NUMERIC if singular. */
+static int rebuild_N(orc_walker* w, double* sign_out)
+{
+    int n = w->k;
+    int total_sign = 1;
+    if (n == 0) { if (sign_out) *sign_out = 1.0; return ORC_OK; }
+    double* A = (double*)malloc(sizeof(double) * (size_t)n * n);
+    if (!A) return ORC_ERR_OOM;
+    for (int sp = 0; sp < 2; ++sp) {
+        build_A(w, sp, n, w->vsite, w->vtau, w->vs, A);
+        int sg = gj_inverse(n, A, w->N[sp], w->cap);
+        if (sg == 0) { free(A); return ORC_ERR_NUMERIC; }
+        total_sign *= sg;
+    }
+    free(A);
+    if (sign_out) *sign_out = (double)total_sign;
+    return ORC_OK;
+}
+
+orc_walker* orc_create(const orc_params* p, int* err)
+{
+    *err = ORC_ERR_ARG;
+    if (!p || p->nc < 1 || !p->site_sub || !p->G0 || p->n_tau < 1 || !(p->beta > 0.0) ||
+        !(p->K > 0.0) || p->U < 0.0 || p->n_tau_meas < 1 || p->init_config_size < 0 || p->warmup_sweeps < 0)
+        return NULL;
+    orc_walker* w = (orc_walker*)calloc(1, sizeof(orc_walker));
+    if (!w) { *err = ORC_ERR_OOM; return NULL; }
+    int nc = p->nc;
+    w->nc = nc; w->n_tau = p->n_tau; w->n_meas_tau = p->n_tau_meas; w->warmup = p->warmup_sweeps;
+    w->U = p->U; w->beta = p->beta; w->K = p->K;
+    w->tie_eps = p->tie_eps > 0.0 ? p->tie_eps : 1e-10;
+    /* cosh(gamma) = 1 + U beta N_corr / (2K), N_corr = Nc */
+    w->gamma = acosh(1.0 + p->U * p->beta * (double)nc / (2.0 * p->K));
+    for (int sp = 0; sp < 2; ++sp) {
+        double sigma = sp == 0 ? 1.0 : -1.0;
+        w->expV[sp][0] = exp(-sigma * w->gamma);
+        w->expV[sp][1] = exp(sigma * w->gamma);
+    }
+    w->site_sub = (int32_t*)malloc(sizeof(int32_t) * nc * nc);
+    w->site_add = (int32_t*)malloc(sizeof(int32_t) * nc * nc);
+    size_t tsz = (size_t)2 * nc * (p->n_tau + 1);
+    w->g0 = (double*)malloc(sizeof(double) * tsz);
+    w->Gacc = (double*)calloc((size_t)2 * nc * p->n_tau_meas, sizeof(double));
+    if (!w->site_sub || !w->site_add || !w->g0 || !w->Gacc) { orc_destroy(w); *err = ORC_ERR_OOM; return NULL; }
+    memcpy(w->site_sub, p->site_sub, sizeof(int32_t) * nc * nc);
+    for (int i = 0; i < nc * nc; ++i) {
+        if (w->site_sub[i] < 0 || w->site_sub[i] >= nc) { orc_destroy(w); return NULL; }
+        w->site_add[i] = -1;
+    }
+    for (int x = 0; x < nc; ++x)
+        for (int y = 0; y < nc; ++y) w->site_add[y * nc + w->site_sub[x * nc + y]] = x;
+    for (int i = 0; i < nc * nc; ++i)
+        if (w->site_add[i] < 0) { orc_destroy(w); return NULL; }
+    for (size_t i = 0; i < tsz; ++i) w->g0[i] = -p->G0[i];
+    w->key[0] = (uint32_t)p->seed;
+    w->key[1] = (uint32_t)(p->seed >> 32) ^ p->walker_id;
+    w->sign = 1.0;
+
+    /* Initial configuration: init_config_size random interacting vertices
+     * (App. B, "initial-configuration-size"). */
+    int n0 = p->init_config_size;
+    if (ensure_cap(w, n0 > 0 ? n0 : 1) != ORC_OK) { orc_destroy(w); *err = ORC_ERR_OOM; return NULL; }
+    for (int i = 0; i < n0; ++i) {
+        uint32_t r[4];
+        draw(w->key, (uint64_t)i, TAG_INIT, r);
+        w->vs[i] = (r[0] & 2u) ? 1 : -1;
+        w->vsite[i] = (int32_t)index_of(r[1], (uint32_t)nc);
+        w->vtau[i] = p->beta * u53(r[2], r[3]);
+    }
+    w->k = n0;
+    int rc = rebuild_N(w, &w->sign);
+    if (rc != ORC_OK) { orc_destroy(w); *err = rc; return NULL; }
+    *err = ORC_OK;
+    return w;
+}
+
+/* ------------------------------------------------------------------ */
+/* One proposal                                                        */
+/* ------------------------------------------------------------------ */
+static void log_push(orc_walker* w, uint8_t v)
+{
+    if (!w->log) return;
+    if (w->log_n < w->log_cap) w->log[w->log_n] = v;
+    w->log_n++;
+}
+
+static int decide(orc_walker* w, double absR, double u, uint64_t q, int* tie)
+{
+    int acc = u < absR;
+    *tie = fabs(absR - u) < w->tie_eps;
+    if (*tie) {
+        w->n_ties++;
+        if (w->hints && q < (uint64_t)w->hints_n) {
+            acc = w->hints[q] & 1;
+            w->n_adopted++;
+        }
+    }
+    return acc;
+}
+
+/* Insert vertex (site, tau, s) as row/column k. */
+static int propose_insert(orc_walker* w, int32_t site, double tau, int8_t s, double u, uint64_t q)
+{
+    int n = w->k;
+    int rc = ensure_cap(w, n + 1);
+    if (rc != ORC_OK) return rc;
+    int ld = w->cap;
+    double* X[2];
+    double* col[2];
+    double* wv[2];
+    double rho[2];
+    for (int sp = 0; sp < 2; ++sp) {
+        X[sp] = w->work + (size_t)(4 * sp + 0) * ld;
+        col[sp] = w->work + (size_t)(4 * sp + 1) * ld;
+        wv[sp] = w->work + (size_t)(4 * sp + 2) * ld;
+        double* N = w->N[sp];
+        double* urow = w->work + (size_t)(4 * sp + 3) * ld;
+        /* New (non-interacting) row of the extended N: X = g0[p,:] (e^V - 1) N. */
+        for (int i = 0; i < n; ++i)
+            urow[i] = g0ab(w, sp, site, tau, w->vsite[i], w->vtau[i]) * (ev(w, sp, w->vs[i]) - 1.0);
+        for (int j = 0; j < n; ++j) {
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) acc += urow[i] * N[(size_t)i * ld + j];
+            X[sp][j] = acc;
+        }
+        /* Column change of A when V_p goes 0 -> sigma gamma s:
+         * c = (I - g0_ext)[:,p] * (e^{V'} - 1). */
+        double delta = ev(w, sp, s) - 1.0;
+        for (int i = 0; i < n; ++i)
+            col[sp][i] = -g0ab(w, sp, w->vsite[i], w->vtau[i], site, tau) * delta;
+        col[sp][n] = (1.0 - g0ab(w, sp, site, 0.0, site, 0.0)) * delta;
+        /* wv = N_ext c ; N_ext = [[N, 0], [X, 1]]. */
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < n; ++j) acc += N[(size_t)i * ld + j] * col[sp][j];
+            wv[sp][i] = acc;
+        }
+        {
+            double acc = 0.0;
+            for (int j = 0; j < n; ++j) acc += X[sp][j] * col[sp][j];
+            wv[sp][n] = acc + col[sp][n];
+        }
+        rho[sp] = 1.0 + wv[sp][n]; /* matrix determinant lemma */
+    }
+    double R = w->K / (double)(n + 1) * rho[0] * rho[1];
+    if (!isfinite(R)) return ORC_ERR_NUMERIC;
+    int tie;
+    int acc = decide(w, fabs(R), u, q, &tie);
+    w->n_prop++;
+    log_push(w, (uint8_t)(acc | (tie << 1)));
+    if (!acc) return ORC_OK;
+    w->n_acc++;
+    if (R < 0.0) w->sign = -w->sign;
+    for (int sp = 0; sp < 2; ++sp) {
+        double* N = w->N[sp];
+        /* Write the extended matrix, then N' = N_ext - wv (e_p^T N_ext) / rho. */
+        for (int j = 0; j < n; ++j) { N[(size_t)n * ld + j] = X[sp][j]; N[(size_t)j * ld + n] = 0.0; }
+        N[(size_t)n * ld + n] = 1.0;
+        double* rowp = w->work + (size_t)(4 * sp + 3) * ld;
+        for (int j = 0; j <= n; ++j) rowp[j] = N[(size_t)n * ld + j];
+        double inv = 1.0 / rho[sp];
+        for (int i = 0; i <= n; ++i) {
+            double f = wv[sp][i] * inv;
+            if (f == 0.0) continue;
+            for (int j = 0; j <= n; ++j) N[(size_t)i * ld + j] -= f * rowp[j];
+        }
+    }
+    w->vsite[n] = site; w->vtau[n] = tau; w->vs[n] = s;
+    w->k = n + 1;
+    return ORC_OK;
+}
+
+/* Remove vertex p.  With A = N^-1, the ratio det A_{\p\p} / det A is
+ * (A^-1)_pp = N_pp (Jacobi's identity / Cramer's rule), and the inverse of
+ * the reduced matrix is the Schur-complement downdate
+ * N'_rs = N_rs - N_rp N_ps / N_pp  (r, s != p). */
+static int propose_remove(orc_walker* w, int p, double u, uint64_t q)
+{
+    int n = w->k;
+    int ld = w->cap;
+    double rho[2];
+    for (int sp = 0; sp < 2; ++sp) rho[sp] = w->N[sp][(size_t)p * ld + p];
+    double R = (double)n / w->K * rho[0] * rho[1];
+    if (!isfinite(R)) return ORC_ERR_NUMERIC;
+    int tie;
+    int acc = decide(w, fabs(R), u, q, &tie);
+    w->n_prop++;
+    log_push(w, (uint8_t)(acc | (tie << 1)));
+    if (!acc) return ORC_OK;
+    w->n_acc++;
+    if (R < 0.0) w->sign = -w->sign;
+    for (int sp = 0; sp < 2; ++sp) {
+        double* N = w->N[sp];
+        double* rowp = w->work + (size_t)(4 * sp + 3) * ld;
+        double* colp = w->work + (size_t)(4 * sp + 2) * ld;
+        for (int j = 0; j < n; ++j) { rowp[j] = N[(size_t)p * ld + j]; colp[j] = N[(size_t)j * ld + p]; }
+        double inv = 1.0 / rho[sp];
+        for (int i = 0, ii = 0; i < n; ++i) {
+            if (i == p) continue;
+            double f = colp[i] * inv;
+            for (int j = 0, jj = 0; j < n; ++j) {
+                if (j == p) continue;
+                /* write position (ii, jj) never passes the read position (i, j) */
+                N[(size_t)ii * ld + jj] = N[(size_t)i * ld + j] - f * rowp[j];
+                ++jj;
+            }
+            ++ii;
+        }
+    }
+    for (int i = p; i < n - 1; ++i) {
+        w->vsite[i] = w->vsite[i + 1]; w->vtau[i] = w->vtau[i + 1]; w->vs[i] = w->vs[i + 1];
+    }
+    w->k = n - 1;
+    return ORC_OK;
+}
+
+/* Proposal number q: type (insert / remove with probability 1/2), the
+ * new vertex or the removal index, and u for the Metropolis test. */
+static int propose(orc_walker* w, uint64_t q)
+{
+    uint32_t r[4], a[4];
+    draw(w->key, q, TAG_PROPOSAL, r);
+    draw(w->key, q, TAG_ACCEPT, a);
+    double u = u53(a[0], a[1]);
+    if ((r[0] & 1u) == 0u) {
+        int8_t s = (r[0] & 2u) ? 1 : -1;
+        int32_t site = (int32_t)index_of(r[1], (uint32_t)w->nc);
+        double tau = w->beta * u53(r[2], r[3]);
+        return propose_insert(w, site, tau, s, u, q);
+    }
+    if (w->k == 0) { /* nothing to remove: rejected */
+        w->n_prop++;
+        log_push(w, 0);
+        return ORC_OK;
+    }
+    int p = (int)index_of(r[1], (uint32_t)w->k);
+    return propose_remove(w, p, u, q);
+}
+
+/* ------------------------------------------------------------------ */
+/* Measurement on the tau grid                                         */
+/* G(dr, tau_a) = g0(dr, tau_a) + (1/Nc) sum_{r'} sum_{ij}             */
+/*   g0(r'+dr - r_i, tau_a - tau_i) M_ij g0(r_j - r', tau_j),          */
+/* M = (e^V - 1) N; accumulated as sign * (-G) (paper convention).     */
+/* ------------------------------------------------------------------ */
+static void measure(orc_walker* w)
+{
+    int n = w->k, nc = w->nc, nt = w->n_meas_tau, ld = w->cap;
+    double* b = (double*)malloc(sizeof(double) * ((size_t)n * nc + 1));
+    for (int sp = 0; sp < 2; ++sp) {
+        double* N = w->N[sp];
+        /* b[r'][i] = sum_j M_ij g0(r_j - r', tau_j - 0+) */
+        for (int rp = 0; rp < nc; ++rp) {
+            for (int i = 0; i < n; ++i) {
+                double acc = 0.0;
+                for (int j = 0; j < n; ++j)
+                    acc += N[(size_t)i * ld + j] * g0ab(w, sp, w->vsite[j], w->vtau[j], rp, 0.0);
+                b[(size_t)rp * n + i] = (ev(w, sp, w->vs[i]) - 1.0) * acc;
+            }
+        }
+        for (int d = 0; d < nc; ++d) {
+            const double* row = w->g0 + ((size_t)sp * nc + d) * (size_t)(w->n_tau + 1);
+            for (int a = 0; a < nt; ++a) {
+                double ta = ((double)a + 0.5) * w->beta / (double)nt;
+                double G = g0_row(row, w->n_tau, w->beta, ta);
+                double corr = 0.0;
+                for (int rp = 0; rp < nc; ++rp) {
+                    int x = w->site_add[rp * nc + d];
+                    for (int i = 0; i < n; ++i)
+                        corr += g0ab(w, sp, x, ta, w->vsite[i], w->vtau[i]) * b[(size_t)rp * n + i];
+                }
+                G += corr / (double)nc;
+                w->Gacc[((size_t)sp * nc + d) * nt + a] += w->sign * (-G);
+            }
+        }
+    }
+    free(b);
+    w->sign_sum += w->sign;
+    w->n_meas++;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sweeps                                                              */
+/* ------------------------------------------------------------------ */
+int orc_sweep(orc_walker* w, int32_t n_sweeps)
+{
+    if (!w || n_sweeps < 0) return ORC_ERR_ARG;
+    for (int s = 0; s < n_sweeps; ++s) {
+        int64_t len;
+        if (w->sweeps_done < w->warmup) {
+            len = w->k > 1 ? w->k : 1;
+            w->warm_k_sum += w->k;
+        } else {
+            if (w->sweep_len == 0) {
+                int64_t L = w->warmup > 0 ? (2 * w->warm_k_sum + w->warmup) / (2 * (int64_t)w->warmup) : w->k;
+                w->sweep_len = L > 1 ? L : 1;
+            }
+            len = w->sweep_len;
+        }
+        for (int64_t t = 0; t < len; ++t) {
+            int rc = propose(w, w->q);
+            if (rc != ORC_OK) return rc;
+            w->q++;
+        }
+        if (w->sweeps_done >= w->warmup) {
+            measure(w);
+            w->k_sum += (double)w->k;
+            w->k_samples++;
+        }
+        w->sweeps_done++;
+    }
+    return ORC_OK;
+}
+
+int64_t orc_sweep_length(const orc_walker* w) { return w->sweep_len; }
+
+/* ------------------------------------------------------------------ */
+/* Accessors                                                           */
+/* ------------------------------------------------------------------ */
+int32_t orc_order(const orc_walker* w) { return w->k; }
+double orc_sign(const orc_walker* w) { return w->sign; }
+double orc_gamma(const orc_walker* w) { return w->gamma; }
+
+/* Copies the vertex list and both N matrices (k x k, row-major, ld = k). */
+int orc_get_state(const orc_walker* w, int32_t* site, double* tau, int8_t* s, double* N_up, double* N_dn)
+{
+    int n = w->k;
+    for (int i = 0; i < n; ++i) {
+        if (site) site[i] = w->vsite[i];
+        if (tau) tau[i] = w->vtau[i];
+        if (s) s[i] = w->vs[i];
+    }
+    double* out[2] = {N_up, N_dn};
+    for (int sp = 0; sp < 2; ++sp) {
+        if (!out[sp]) continue;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) out[sp][(size_t)i * n + j] = w->N[sp][(size_t)i * w->cap + j];
+    }
+    return ORC_OK;
+}
+
+/* counters: [proposals, accepts, near_ties, adopted, next_q, sweeps_done, n_meas, k_samples] */
+void orc_counters(const orc_walker* w, int64_t* out)
+{
+    out[0] = w->n_prop; out[1] = w->n_acc; out[2] = w->n_ties; out[3] = w->n_adopted;
+    out[4] = (int64_t)w->q; out[5] = w->sweeps_done; out[6] = w->n_meas; out[7] = w->k_samples;
+}
+
+double orc_k_sum(const orc_walker* w) { return w->k_sum; }
+
+int orc_get_G(const orc_walker* w, double* G_out, double* sign_sum, int64_t* n_meas)
+{
+    size_t m = (size_t)2 * w->nc * w->n_meas_tau;
+    if (G_out) memcpy(G_out, w->Gacc, sizeof(double) * m);
+    if (sign_sum) *sign_sum = w->sign_sum;
+    if (n_meas) *n_meas = w->n_meas;
+    return ORC_OK;
+}
+
+void orc_reset_accumulators(orc_walker* w)
+{
+    memset(w->Gacc, 0, sizeof(double) * (size_t)2 * w->nc * w->n_meas_tau);
+    w->sign_sum = 0.0;
+    w->n_meas = 0;
+    w->k_sum = 0.0;
+    w->k_samples = 0;
+}
+
+/* Decision log: one byte per proposal, bit 0 = accepted, bit 1 = near tie. */
+int orc_enable_log(orc_walker* w, int64_t cap)
+{
+    free(w->log);
+    w->log = (uint8_t*)malloc((size_t)(cap > 0 ? cap : 1));
+    if (!w->log) return ORC_ERR_OOM;
+    w->log_cap = cap;
+    w->log_n = 0;
+    return ORC_OK;
+}
+
+int64_t orc_get_log(const orc_walker* w, uint8_t* out, int64_t cap)
+{
+    int64_t n = w->log_n < w->log_cap ? w->log_n : w->log_cap;
+    if (out) memcpy(out, w->log, (size_t)(n < cap ? n : cap));
+    return w->log_n;
+}
+
+/* At a near tie, adopt hints[q] & 1 instead of the oracle's own decision.
+ * The pointer is borrowed; it must outlive the sweeps that use it. */
+void orc_set_hints(orc_walker* w, const uint8_t* hints, int64_t n)
+{
+    w->hints = hints;
+    w->hints_n = n;
+}
+
+/* Fresh N_sigma = [e^V - g0 (e^V - 1)]^-1 for the walker's current vertex
+ * list; out is k x k (ld = k).  Returns the sign of det N_sigma^-1. */
+int orc_fresh_N(const orc_walker* w, int32_t sp, double* out)
+{
+    int n = w->k;
+    if (n == 0) return 1;
+    double* A = (double*)malloc(sizeof(double) * (size_t)n * n);
+    build_A(w, sp, n, w->vsite, w->vtau, w->vs, A);
+    int sg = gj_inverse(n, A, out, n);
+    free(A);
+    return sg;
+}
+
+/* A_sigma = e^V - g0 (e^V - 1) for an arbitrary vertex list, with this
+ * walker's tables (for brute-force determinant checks). */
+int orc_build_A(const orc_walker* w, int32_t sp, int32_t n, const int32_t* site, const double* tau,
+                const int8_t* s, double* A)
+{
+    if (n < 0) return ORC_ERR_ARG;
+    build_A(w, sp, n, site, tau, s, A);
+    return ORC_OK;
+}
+
+/* Replace the walker's configuration (all vertices interacting) and rebuild
+ * N; used by tests that start from a chosen configuration. */
+int orc_set_config(orc_walker* w, int32_t n, const int32_t* site, const double* tau, const int8_t* s)
+{
+    if (n < 0) return ORC_ERR_ARG;
+    int rc = ensure_cap(w, n > 0 ? n : 1);
+    if (rc != ORC_OK) return rc;
+    for (int i = 0; i < n; ++i) {
+        if (site[i] < 0 || site[i] >= w->nc || (s[i] != 1 && s[i] != -1)) return ORC_ERR_ARG;
+        w->vsite[i] = site[i]; w->vtau[i] = tau[i]; w->vs[i] = s[i];
+    }
+    w->k = n;
+    return rebuild_N(w, &w->sign);
+}
+
+/* Apply one proposal of a given kind to the current state, forcing
+ * acceptance (force = 1) or rejection (force = 0).  Used by the determinant
+ * pins; does not advance the proposal counter or the decision log. */
+int orc_try_insert(orc_walker* w, int32_t site, double tau, int8_t s, int32_t force)
+{
+    /* u = -1 accepts every finite |R|; u = 1e300 rejects every one. */
+    double u = force ? -1.0 : 1.0e300;
+    int64_t saved[3] = {w->n_ties, w->n_prop, w->log_n};
+    int rc = propose_insert(w, site, tau, s, u, UINT64_MAX);
+    w->n_ties = saved[0]; w->n_prop = saved[1]; w->log_n = saved[2];
+    return rc;
+}
+
+int orc_try_remove(orc_walker* w, int32_t p, int32_t force)
+{
+    if (p < 0 || p >= w->k) return ORC_ERR_ARG;
+    double u = force ? -1.0 : 1.0e300;
+    int64_t saved[3] = {w->n_ties, w->n_prop, w->log_n};
+    int rc = propose_remove(w, p, u, UINT64_MAX);
+    w->n_ties = saved[0]; w->n_prop = saved[1]; w->log_n = saved[2];
+    return rc;
+}
+
+/* Determinant ratio rho_sigma (both spins) of a proposed insert or remove
+ * on the current state, without changing it. */
+int orc_ratio(orc_walker* w, int32_t is_remove, int32_t p, int32_t site, double tau, int8_t s, double* rho_out)
+{
+    int n = w->k;
+    int rc = ensure_cap(w, n + 1);
+    if (rc != ORC_OK) return rc;
+    int ld = w->cap;
+    for (int sp = 0; sp < 2; ++sp) {
+        double* N = w->N[sp];
+        double acc = 0.0;
+        if (!is_remove) {
+            double* urow = w->work;
+            double* X = w->work + ld;
+            for (int i = 0; i < n; ++i)
+                urow[i] = g0ab(w, sp, site, tau, w->vsite[i], w->vtau[i]) * (ev(w, sp, w->vs[i]) - 1.0);
+            for (int j = 0; j < n; ++j) {
+                double t = 0.0;
+                for (int i = 0; i < n; ++i) t += urow[i] * N[(size_t)i * ld + j];
+                X[j] = t;
+            }
+            double delta = ev(w, sp, s) - 1.0;
+            for (int j = 0; j < n; ++j) acc += X[j] * (-g0ab(w, sp, w->vsite[j], w->vtau[j], site, tau) * delta);
+            acc += (1.0 - g0ab(w, sp, site, 0.0, site, 0.0)) * delta;
+        } else {
+            if (p < 0 || p >= n) return ORC_ERR_ARG;
+            acc = N[(size_t)p * ld + p] - 1.0;
+        }
+        rho_out[sp] = 1.0 + acc;
+    }
+    return ORC_OK;
+}

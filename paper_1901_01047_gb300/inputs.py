@@ -1,0 +1,140 @@
+"""Seeded synthetic inputs shared by the GPU path, its tests and the oracle.
+
+This module holds no CT-AUX arithmetic: only the geometry of square-lattice
+DCA clusters (sites, the r_i - r_j table, cluster momenta), the dispersion of
+the single-band Hubbard model on the square lattice (t, t' as in the model
+parameters of App. B), and the named workload parameter sets.
+
+Cluster geometry.  A cluster is given by two superlattice vectors a1, a2 in
+units of the square-lattice basis (App. B, "cluster").  Its sites are the
+lattice points modulo the superlattice, so Nc = |det[a1; a2]|.  Cluster momenta
+K satisfy K . a1, K . a2 in 2 pi Z.  The vectors of the 16- and 36-site
+clusters are the square ones [[4,0],[0,4]] and [[6,0],[0,6]]; the 8-site
+cluster is [[2,2],[2,-2]].
+"""
+from dataclasses import dataclass, field
+from typing import List, Tuple
+
+import numpy as np
+
+
+@dataclass
+class Cluster:
+    vecs: Tuple[Tuple[int, int], Tuple[int, int]]
+    sites: np.ndarray        # [nc, 2] integer coordinates, reduced into the cell
+    site_sub: np.ndarray     # [nc, nc] int32: index of (r_i - r_j) reduced into the cell
+    kpts: np.ndarray         # [nc, 2] cluster momenta
+
+    @property
+    def nc(self) -> int:
+        return self.sites.shape[0]
+
+
+def _reduce(pts: np.ndarray, A: np.ndarray) -> np.ndarray:
+    """Reduce integer points modulo the superlattice spanned by the rows of A."""
+    Ainv = np.linalg.inv(A.astype(np.float64))
+    f = pts.astype(np.float64) @ Ainv
+    n = np.floor(f + 1e-9).astype(np.int64)
+    return pts - n @ A
+
+
+def make_cluster(vecs) -> Cluster:
+    A = np.array(vecs, dtype=np.int64)
+    nc = int(round(abs(np.linalg.det(A.astype(np.float64)))))
+    if nc < 1:
+        raise ValueError("degenerate cluster vectors")
+    R = int(np.abs(A).sum()) + 1
+    xs = np.arange(-R, R + 1)
+    grid = np.array([(x, y) for x in xs for y in xs], dtype=np.int64)
+    red = _reduce(grid, A)
+    uniq = sorted(set(map(tuple, red.tolist())), key=lambda p: (p[1], p[0]))
+    if len(uniq) != nc:
+        raise ValueError("cluster reduction found %d sites, expected %d" % (len(uniq), nc))
+    sites = np.array(uniq, dtype=np.int64)
+    index = {p: i for i, p in enumerate(uniq)}
+    diff = sites[:, None, :] - sites[None, :, :]
+    dred = _reduce(diff.reshape(-1, 2), A).reshape(nc, nc, 2)
+    site_sub = np.array([[index[tuple(dred[i, j])] for j in range(nc)] for i in range(nc)],
+                        dtype=np.int32)
+    # Cluster momenta: K = 2 pi A^-1 m for integer m, reduced modulo the
+    # reciprocal lattice 2 pi Z^2.
+    Ainv = np.linalg.inv(A.astype(np.float64))
+    ks = set()
+    for m0 in range(-nc, nc + 1):
+        for m1 in range(-nc, nc + 1):
+            k = Ainv @ np.array([m0, m1], dtype=np.float64)
+            k = k - np.floor(k + 1e-9)
+            ks.add((round(k[0] * nc) % nc, round(k[1] * nc) % nc))
+    ks = sorted(ks)
+    if len(ks) != nc:
+        raise ValueError("found %d cluster momenta, expected %d" % (len(ks), nc))
+    kpts = 2.0 * np.pi * np.array(ks, dtype=np.float64) / nc
+    return Cluster(vecs=tuple(map(tuple, A.tolist())), sites=sites, site_sub=site_sub, kpts=kpts)
+
+
+def square_dispersion(kpts: np.ndarray, t: float, tp: float) -> np.ndarray:
+    """eps_K = -2t (cos Kx + cos Ky) - 4t' cos Kx cos Ky (square lattice, App. B model group)."""
+    cx, cy = np.cos(kpts[:, 0]), np.cos(kpts[:, 1])
+    return -2.0 * t * (cx + cy) - 4.0 * tp * cx * cy
+
+
+def k_dot_r(cluster: Cluster) -> np.ndarray:
+    """[nc_K, nc_r] matrix of K . r for the cluster momenta and sites."""
+    return cluster.kpts @ cluster.sites.T.astype(np.float64)
+
+
+CLUSTER_VECS = {
+    1: ((1, 0), (0, 1)),
+    4: ((2, 0), (0, 2)),
+    8: ((2, 2), (2, -2)),
+    16: ((4, 0), (0, 4)),
+    36: ((6, 0), (0, 6)),
+}
+
+
+def cluster(nc: int) -> Cluster:
+    return make_cluster(CLUSTER_VECS[nc])
+
+
+@dataclass
+class Workload:
+    """Named synthetic workload (the paper's Hubbard runs stand behind these shapes)."""
+    name: str
+    nc: int
+    t: float
+    tp: float
+    U: float
+    beta: float
+    mu: float
+    K: float = 1.0
+    n_tau: int = 4096
+    k_sub: int = 32
+    walkers: int = 1
+    sweeps: int = 10000
+    warmup_sweeps: int = 20
+    n_tau_meas: int = 256
+    seed: int = 0
+    init_config_size: int = 10
+    recompute_every: int = 64
+    precision: str = "fp64"
+    extra: dict = field(default_factory=dict)
+
+
+# Chemical potentials.  The atom is at half filling, mu = U/2.  The 2x2 value
+# gives density 0.9 by exact diagonalisation; the 16- and 36-site values are
+# U/2 + mu0 with mu0 giving the target density of the free isolated cluster.
+# Both were produced by tests/golden/make_golden.py and are stored in
+# tests/golden/hubbard_2x2_ed.json and tests/golden/free_cluster_mu.json.
+WORKLOADS = {
+    "atom_nc1": Workload(name="atom_nc1", nc=1, t=0.0, tp=0.0, U=4.0, beta=2.0, mu=2.0, K=1.0,
+                         n_tau=4096, k_sub=8, sweeps=10000, n_tau_meas=256, seed=0),
+    "hubbard_2x2": Workload(name="hubbard_2x2", nc=4, t=1.0, tp=0.0, U=4.0, beta=10.0,
+                            mu=0.9450480104035819,
+                            K=1.0, n_tau=4096, k_sub=32, sweeps=100000, n_tau_meas=256, seed=0),
+}
+
+
+def seeded_uniform(seed: int, n: int, lo: float, hi: float) -> np.ndarray:
+    """Reproducible uniform draws for workload parameters (numpy PCG64)."""
+    rng = np.random.default_rng(seed)
+    return lo + (hi - lo) * rng.random(n)

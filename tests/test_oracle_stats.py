@@ -1,0 +1,152 @@
+"""Statistical pins for the oracle (closed forms and exact diagonalisation).
+
+- U = 0: gamma = 0, every a_p = 0, N = I and M = 0, so each measurement gives
+  G = G0 exactly, and the order follows a birth-death chain with rates
+  K/(k+1), k/K whose stationary law is Poisson(K).
+- Hubbard atom at mu = U/2: G(tau) = -[e^{-tau U/2} + e^{-(beta-tau) U/2}] /
+  (2 (1 + e^{-beta U/2})), and <k> = K - beta <H_int> with
+  <H_int> = -(U/2) P_single (the expansion of Z in powers of K/beta - H_int).
+- 2x2 Hubbard cluster: G(dr, tau), <k> against ED of the same Hamiltonian.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ctaux, ed
+from tests.helpers import binned, problem
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_u0_measures_g0_exactly_and_poisson_order():
+    nc, beta, mu, n_tau, ntm = 4, 3.0, 0.4, 512, 16
+    c, eps, kr, G0 = problem(nc, 1.0, 0.0, 0.0, beta, mu, n_tau)
+    w = ctaux.OracleWalker(nc, c.site_sub, 0.0, beta, 1.7, G0, warmup_sweeps=10, n_tau_meas=ntm,
+                           seed=11)
+    assert w.gamma == 0.0
+    ks = []
+    for b in range(20):
+        w.sweep(500)
+        st = w.state()
+        for sp in range(2):
+            assert np.array_equal(st["N"][sp], np.eye(w.order))
+        ks.append(w.order)
+    g, ss, nm = w.G()
+    assert ss == nm  # no sign problem
+    taus = (np.arange(ntm) + 0.5) * beta / ntm
+    exact = np.array([[ctaux.g0_interp(-G0[0, d], n_tau, beta, t) for t in taus] for d in range(nc)])
+    assert np.abs(g[0] / ss + exact).max() < 1e-13
+    cn = w.counters()
+    assert abs(cn["k_sum"] / cn["k_samples"] - 1.7) < 0.1
+
+
+def _atom_run(seed, n_bins=24, per_bin=4000):
+    U, beta, n_tau, ntm = 4.0, 2.0, 4096, 16
+    c, eps, kr, G0 = problem(1, 0.0, 0.0, U, beta, U / 2, n_tau)
+    w = ctaux.OracleWalker(1, c.site_sub, U, beta, 1.0, G0, warmup_sweeps=200, n_tau_meas=ntm,
+                           seed=seed)
+    Gb, kb = [], []
+    for b in range(n_bins):
+        w.reset_accumulators()
+        w.sweep(per_bin)
+        g, ss, nm = w.G()
+        cn = w.counters()
+        Gb.append(g[:, 0] / ss)
+        kb.append(cn["k_sum"] / cn["k_samples"])
+    return U, beta, ntm, np.array(Gb), np.array(kb)
+
+
+def test_atom_closed_form_and_order_identity():
+    U, beta, ntm, Gb, kb = _atom_run(seed=0)
+    taus = (np.arange(ntm) + 0.5) * beta / ntm
+    exact = ed.atom_greens(U, beta, taus)
+    for sp in range(2):
+        m, e = binned(Gb[:, sp])
+        z = (m - exact) / e
+        assert np.abs(z).max() < 3.0, z
+    p_single = np.exp(beta * U / 2) / (1 + np.exp(beta * U / 2))
+    k_exact = 1.0 + beta * (U / 2) * p_single
+    m, e = binned(kb)
+    assert abs(m - k_exact) < 3 * e, (m, e, k_exact)
+    assert abs(k_exact - 4.928055) < 1e-5
+    # particle-hole symmetry at half filling: G(tau) = G(beta - tau)
+    m, e = binned(Gb[:, 0])
+    assert np.abs((m - m[::-1]) / (np.sqrt(2) * e)).max() < 4.0
+
+
+def test_2x2_cluster_matches_ed():
+    U, beta, mu, n_tau, ntm = 4.0, 4.0, 1.0, 4096, 8
+    c, eps, kr, G0 = problem(4, 1.0, 0.0, U, beta, mu, n_tau)
+    t = ed.hopping_from_dispersion(eps, kr, c.site_sub)
+    E = ed.HubbardED(t, U, mu)
+    taus = (np.arange(ntm) + 0.5) * beta / ntm
+    Gex = E.greens_translation_avg(beta, taus, c.site_sub)
+    k_exact = 1.0 - beta * E.h_int(beta)
+    w = ctaux.OracleWalker(4, c.site_sub, U, beta, 1.0, G0, warmup_sweeps=200, n_tau_meas=ntm, seed=1)
+    Gb, kb, sb = [], [], []
+    for b in range(16):
+        w.reset_accumulators()
+        w.sweep(1500)
+        g, ss, nm = w.G()
+        cn = w.counters()
+        Gb.append(g[:, :, :] / ss)
+        kb.append(cn["k_sum"] / cn["k_samples"])
+        sb.append(ss / nm)
+    Gb = np.array(Gb)
+    for sp in range(2):
+        m, e = binned(Gb[:, sp])
+        z = (m - Gex) / e
+        assert np.abs(z).max() < 3.0, z
+    m, e = binned(kb)
+    assert abs(m - k_exact) < 3 * e, (m, e, k_exact)
+    assert 0.5 < np.mean(sb) < 1.0  # away from half filling: a (mild) sign problem
+
+
+def test_golden_2x2_mu_gives_target_density():
+    with open(os.path.join(GOLDEN, "hubbard_2x2_ed.json")) as f:
+        gd = json.load(f)
+    c, eps, kr, G0 = problem(4, gd["t"], gd["tp"], gd["U"], gd["beta"], gd["mu"], 8)
+    t = ed.hopping_from_dispersion(eps, kr, c.site_sub)
+    E = ed.HubbardED(t, gd["U"], gd["mu"])
+    assert abs(E.density(gd["beta"]) - 0.9) < 1e-9
+
+
+def test_sweep_length_frozen_after_warmup():
+    c, eps, kr, G0 = problem(4, 1.0, 0.0, 4.0, 4.0, 1.0, 256)
+    w = ctaux.OracleWalker(4, c.site_sub, 4.0, 4.0, 1.0, G0, warmup_sweeps=30, n_tau_meas=4, seed=2)
+    w.sweep(30)
+    q_warm = w.counters()["next_q"]
+    w.sweep(1)
+    L = ctaux.lib().orc_sweep_length(w._h)
+    assert L >= 1
+    q1 = w.counters()["next_q"]
+    w.sweep(7)
+    assert w.counters()["next_q"] - q1 == 7 * L
+    assert q1 - q_warm == L
+
+
+def test_near_tie_hints_are_adopted_only_at_ties():
+    c, eps, kr, G0 = problem(4, 1.0, 0.0, 4.0, 4.0, 1.0, 256)
+    mk = lambda eps_: ctaux.OracleWalker(4, c.site_sub, 4.0, 4.0, 1.0, G0, warmup_sweeps=5,
+                                         n_tau_meas=4, seed=4, tie_eps=eps_)
+    a = mk(1e-10)
+    a.enable_log(1 << 20)
+    a.sweep(300)
+    log = a.log()
+    # Flip every hint: with a tiny tie window nothing may change.
+    b = mk(1e-10)
+    b.enable_log(1 << 20)
+    b.set_hints(log ^ 1)
+    b.sweep(300)
+    assert np.array_equal(b.log(), log)
+    # With a huge tie window every decision is a tie and follows the hints.
+    h = mk(10.0)
+    h.enable_log(1 << 20)
+    hints = np.zeros(1 << 20, np.uint8)
+    h.set_hints(hints)
+    h.sweep(50)
+    assert (h.log() & 1).sum() == 0
+    cn = h.counters()
+    assert cn["adopted"] == cn["near_ties"] > 0
