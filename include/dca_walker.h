@@ -1,0 +1,184 @@
+/*
+ * dca_walker.h -- C ABI of the GB300 CT-AUX walker library (libdcawalker.so).
+ *
+ * The library runs continuous-time auxiliary-field QMC walkers (DCA++ paper,
+ * Sec. 2.3) on one GPU: submatrix (delayed) updates of the per-spin N
+ * matrices (Sec. 2.3, "Submatrix updates"), sign tracking, periodic
+ * recomputation of N, and accumulation of the measured Green's function G(tau)
+ * (Sec. 2.3, the equation for <G> in terms of M).  Every step of a sweep runs
+ * in CUDA kernels built for sm_103a; there is no CPU fallback.
+ *
+ * Problem statement (Sec. 2.3, Eq. generalized_hubbard and the decoupling
+ * equations): a single-band Hubbard cluster of Nc sites with on-site U,
+ * inverse temperature beta, expansion constant K > 0 and the bare cluster
+ * propagator G0(r, tau) of H0 (which carries the +U/2 shift of
+ * Eq. generalized_hubbard).  cosh(gamma) = 1 + U beta Nc / (2K).
+ *
+ * Conventions
+ *   - Every function returns DCA_OK (0) or a negative DCA_ERR_* code; nothing
+ *     throws across the ABI.  dca_walker_last_error() gives a message.
+ *   - Host arrays passed in are caller-owned and copied during the call.
+ *     Output buffers are caller-owned host memory.  Device memory is owned by
+ *     the library (allocated in dca_walker_create, freed in destroy).
+ *   - Work is ordered on the CUDA stream given at create (NULL = the legacy
+ *     default stream).  dca_walker_sweep synchronises that stream while it
+ *     runs (it polls a device flag to know when all walkers are done);
+ *     measure_G, stats, get_state and get_decision_log synchronise it too.
+ *   - Matrices are row-major.  Spin index 0 = up, 1 = down.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key
+ *     (lo32(seed), hi32(seed) ^ walker_index) and counter
+ *     (lo32(j), hi32(j), tag, 0); tag 0 = proposal words, 1 = acceptance
+ *     uniform, 2 = initial configuration.
+ */
+#ifndef DCA_WALKER_H
+#define DCA_WALKER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DCA_API __attribute__((visibility("default")))
+#else
+#define DCA_API
+#endif
+
+#define DCA_OK 0
+#define DCA_ERR_ARG (-1)      /* invalid argument */
+#define DCA_ERR_CUDA (-2)     /* a CUDA call failed */
+#define DCA_ERR_OOM (-3)      /* device or host allocation failed */
+#define DCA_ERR_TIMEOUT (-4)  /* a bounded device wait or poll gave up */
+#define DCA_ERR_NUMERIC (-5)  /* NaN / Inf in a ratio, singular recompute */
+#define DCA_ERR_STATE (-6)    /* call not valid in the current state */
+#define DCA_ERR_CAPACITY (-7) /* a walker's order outgrew its matrix capacity */
+
+/* Arithmetic of the N matrices and their updates. */
+#define DCA_PREC_FP64 0       /* N stored and updated in FP64 */
+
+/* One physical problem (a cluster with its bare propagator). */
+typedef struct {
+  int32_t nc;              /* cluster sites; N_corr = Nc (single band, Sec. 2.3) */
+  const int32_t* site_sub; /* host [nc*nc]: index of r_i - r_j folded into the cluster;
+                              rows must be permutations of 0..nc-1 */
+  double U;                /* on-site interaction, >= 0 */
+  double beta;             /* inverse temperature, > 0 */
+  double K;                /* expansion constant, > 0 (App. B "expansion-parameter-K") */
+  int32_t n_tau;           /* G0 grid intervals, samples at l*beta/n_tau, l = 0..n_tau */
+  const double* G0;        /* host [2][nc][n_tau+1] in the paper's sign convention
+                              (negative on (0, beta)); l = 0 holds G0(r, 0+),
+                              l = n_tau holds G0(r, beta-).  Linear interpolation in
+                              between, antiperiodic continuation to (-beta, 0). */
+} dca_problem;
+
+typedef struct {
+  int32_t n_problems;              /* >= 1 */
+  const dca_problem* problems;     /* host [n_problems] */
+  int32_t n_walkers;               /* >= 1 */
+  const int32_t* walker_problem;   /* host [n_walkers] problem index per walker, or NULL
+                                      for walker w -> problem w % n_problems */
+  int32_t k_sub;                   /* proposals per submatrix update, 1..128
+                                      (App. B "max-submatrix-size") */
+  int32_t recompute_every;         /* recompute N from scratch every this many
+                                      submatrix updates; 0 = never */
+  int32_t warmup_sweeps;           /* App. B "warm-up-sweeps" */
+  int32_t n_tau_meas;              /* measurement grid: tau_a = (a + 1/2) beta / n_tau_meas */
+  int32_t precision;               /* DCA_PREC_* */
+  int32_t init_config_size;        /* App. B "initial-configuration-size" */
+  int32_t capacity;                /* max order per walker (matrix size); 0 = automatic */
+  uint64_t seed;                   /* App. B "seed" */
+  double tie_eps;                  /* near-tie band on | |R| - u |; 0 = 1e-10 */
+  int64_t log_capacity;            /* decision-log bytes per walker; 0 = no log */
+} dca_walker_params;
+
+/* Vertex of a configuration: site index, imaginary time, auxiliary spin. */
+typedef struct {
+  int32_t site;
+  int32_t s;      /* +1 or -1 */
+  double tau;     /* in [0, beta) */
+} dca_vertex;
+
+typedef struct {
+  int64_t proposals;        /* decided proposals (accepted + rejected) */
+  int64_t accepts;
+  int64_t near_ties;        /* decisions with | |R| - u | < tie_eps */
+  int64_t aborts;           /* submatrix updates ended early by the duplicate-spin rule */
+  int64_t windows;          /* submatrix updates done */
+  int64_t sweeps;           /* sweeps done (including warm-up) */
+  int64_t measurements;
+  int64_t recomputes;
+  int64_t sweep_length;     /* frozen proposals per measured sweep (0 before set) */
+  int32_t order;            /* current expansion order k */
+  int32_t status;           /* DCA_OK or the walker's error code */
+  double sign;              /* current configuration sign */
+  double k_sum;             /* sum of k over measurements */
+  double max_drift;         /* largest max|N - N_fresh| / max|N_fresh| seen at recomputes */
+  double n_update_flops;    /* algorithmic flop of the N updates (2 n^2 l + 2 n l^2 per spin) */
+} dca_walker_stats_t;
+
+typedef struct dca_walker dca_walker;
+
+/*
+ * Bare propagator of an isolated cluster for the CT-AUX H0 (effective
+ * chemical potential mu - U/2, Eq. generalized_hubbard):
+ *   G0(r, tau) = -(1/Nc) sum_K cos(K.r) e^{-tau xi_K} / (1 + e^{-beta xi_K}),
+ *   xi_K = eps_K - (mu - U/2),
+ * evaluated on the GPU.  eps_K: host [nc]; k_dot_r: host [nc][nc] (K index,
+ * site index); G0_out: host [2][nc][n_tau+1] (both spins equal).
+ */
+DCA_API int dca_g0_isolated_cluster(int32_t nc, const double* eps_K, const double* k_dot_r, double mu,
+                            double U, double beta, int32_t n_tau, double* G0_out);
+
+/* Validate parameters, upload problems, draw each walker's initial
+ * configuration (init_config_size interacting vertices, counter tag 2) and
+ * build its N matrices from scratch.  cuda_stream: a cudaStream_t or NULL. */
+DCA_API int dca_walker_create(const dca_walker_params* params, void* cuda_stream, dca_walker** out);
+
+/* Run n_sweeps more sweeps on every walker.  A warm-up sweep is max(k, 1)
+ * proposals (k at its start); after warm-up the sweep length is frozen to the
+ * rounded mean of those k (max(k,1) when warmup_sweeps = 0).  Every sweep at
+ * or past warm-up ends with one measurement. */
+DCA_API int dca_walker_sweep(dca_walker* w, int32_t n_sweeps);
+
+/* Copy the accumulated sum over measurements of sign * G(dr, tau_a) (paper
+ * convention) to G_out [n_walkers][2][nc][n_tau_meas] (nc of each walker's
+ * problem; walkers laid out back to back), the sign sums to sign_sum_out
+ * [n_walkers] and the measurement counts to n_meas_out [n_walkers].  Any of
+ * the outputs may be NULL.  Synchronises the stream. */
+DCA_API int dca_walker_measure_G(dca_walker* w, double* G_out, double* sign_sum_out, int64_t* n_meas_out);
+
+/* Zero the G accumulators, sign sums and measurement counters. */
+DCA_API int dca_walker_reset_measurements(dca_walker* w);
+
+/* Per-walker counters, out [n_walkers].  Synchronises the stream. */
+DCA_API int dca_walker_stats(dca_walker* w, dca_walker_stats_t* out);
+
+/* Current configuration of walker wi: verts [capacity], *k = order, and both
+ * N matrices as FP64 k x k row-major into N_up / N_dn (each may be NULL). */
+DCA_API int dca_walker_get_state(dca_walker* w, int32_t wi, dca_vertex* verts, int32_t* k, double* N_up,
+                         double* N_dn);
+
+/* Decision log of walker wi: one byte per proposal number q (bit 0 accepted,
+ * bit 1 near tie), out [cap]; *n = number of proposals logged so far. */
+DCA_API int dca_walker_get_decision_log(dca_walker* w, int32_t wi, uint8_t* out, int64_t cap, int64_t* n);
+
+/* Replay mode: walker wi takes the accept bit of log[q] instead of its own
+ * Metropolis decision for proposal q < n (used to compare arithmetic on an
+ * identical trajectory).  n = 0 switches replay off. */
+DCA_API int dca_walker_set_forced_decisions(dca_walker* w, int32_t wi, const uint8_t* log, int64_t n);
+
+/* Device buffer sizes and capacity of walker wi (for diagnostics). */
+DCA_API int dca_walker_capacity(dca_walker* w, int32_t wi, int32_t* capacity);
+
+DCA_API void dca_walker_destroy(dca_walker* w);
+
+/* Message of the last error on this handle (or of the last failed create
+ * when w is NULL).  The string stays valid until the next call on w. */
+DCA_API const char* dca_walker_last_error(dca_walker* w);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DCA_WALKER_H */

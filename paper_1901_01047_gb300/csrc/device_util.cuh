@@ -1,0 +1,88 @@
+// device_util.cuh -- small device helpers of the walker kernels.
+#pragma once
+#include <cstdint>
+
+#include "state.h"
+
+namespace dca {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
+// 4x32 S-box, round multipliers 0xD2511F53 and 0xCD9E8D57, key bumped by the
+// Weyl constants 0x9E3779B9 and 0xBB67AE85 between rounds.
+struct Philox4 {
+  uint32_t v[4];
+};
+
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                 uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  Philox4 out;
+  out.v[0] = c0;
+  out.v[1] = c1;
+  out.v[2] = c2;
+  out.v[3] = c3;
+  return out;
+}
+
+enum : uint32_t { TAG_PROPOSAL = 0u, TAG_ACCEPT = 1u, TAG_INIT = 2u };
+
+__device__ __forceinline__ Philox4 draw(const WalkerDev& w, uint64_t j, uint32_t tag) {
+  return philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), tag, 0u, w.key0, w.key1);
+}
+
+// 53-bit uniform in [0, 1) from two words (high word first).
+__device__ __forceinline__ double uniform53(uint32_t hi, uint32_t lo) {
+  const uint64_t x = ((uint64_t)hi << 32) | (uint64_t)lo;
+  return (double)(x >> 11) * 0x1.0p-53;
+}
+
+// floor(word * m / 2^32), exact integer arithmetic.
+__device__ __forceinline__ uint32_t scaled_index(uint32_t word, uint32_t m) { return __umulhi(word, m); }
+
+// g0 at a time difference in (-beta, beta) from one table row: linear
+// interpolation on the uniform grid, g0(t - beta) = -g0(t), dt == 0 read as 0+.
+__device__ __forceinline__ double g0_interp(const double* __restrict__ row, int n_tau, double beta,
+                                            double tau_scale, double dt) {
+  double sgn = 1.0;
+  if (dt < 0.0) {
+    dt += beta;
+    sgn = -1.0;
+  }
+  const double x = dt * tau_scale;
+  int l = (int)x;
+  l = l < 0 ? 0 : (l >= n_tau ? n_tau - 1 : l);
+  const double f = x - (double)l;
+  const double a = __ldg(row + l), b = __ldg(row + l + 1);
+  return sgn * (a + f * (b - a));
+}
+
+// g0_sigma(r_a - r_b, tau_a - tau_b)
+__device__ __forceinline__ double g0_pair(const ProblemDev& p, int sp, int ra, double ta, int rb, double tb) {
+  const int d = __ldg(p.site_sub + ra * p.nc + rb);
+  const double* row = p.g0 + ((size_t)sp * p.nc + d) * (size_t)(p.n_tau + 1);
+  return g0_interp(row, p.n_tau, p.beta, p.tau_scale, ta - tb);
+}
+
+// Equal-time, same-vertex value g0(0+) on the diagonal.
+__device__ __forceinline__ double g0_diag(const ProblemDev& p, int sp, int r) {
+  const int d = __ldg(p.site_sub + r * p.nc + r);
+  return __ldg(p.g0 + ((size_t)sp * p.nc + d) * (size_t)(p.n_tau + 1));
+}
+
+__device__ __forceinline__ double expV(const ProblemDev& p, int sp, int s) { return p.expV[sp][s > 0 ? 1 : 0]; }
+
+}  // namespace dca

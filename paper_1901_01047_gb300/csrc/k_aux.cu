@@ -1,0 +1,377 @@
+// k_aux.cu -- initial configuration, from-scratch recomputation of N,
+// measurement of G(tau), and the isolated-cluster G0 builder.
+#include <cstdint>
+
+#include "device_util.cuh"
+#include "kernels.h"
+#include "state.h"
+
+namespace dca {
+
+// ---------------------------------------------------------------------------
+// Initial configuration: n0 random interacting vertices (App. B,
+// "initial-configuration-size"), counter tag 2, vertex i <- counter (i, 0, 2, 0).
+// ---------------------------------------------------------------------------
+__global__ void k_init_vertices(Config cfg, int n0) {
+  WalkerDev& w = cfg.W[blockIdx.x];
+  const ProblemDev& pb = cfg.P[w.problem];
+  for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+    const Philox4 r = draw(w, (uint64_t)i, TAG_INIT);
+    w.vs[0][i] = (r.v[0] & 2u) ? 1 : -1;
+    w.vsite[0][i] = (int)scaled_index(r.v[1], (uint32_t)pb.nc);
+    w.vtau[0][i] = pb.beta * uniform53(r.v[2], r.v[3]);
+  }
+  if (threadIdx.x == 0) {
+    w.n = n0;
+    w.parity = 0;
+  }
+}
+
+// A = e^V - g0 (e^V - 1) for the current vertex list, written to N[dst][sp].
+// mode 0: dst = current parity (initial build); mode 1: dst = other parity
+// (periodic recompute, only walkers with recompute_pending).
+__device__ __forceinline__ bool wants_build(const WalkerDev& w, int mode) {
+  return mode == 0 ? true : (w.active && w.recompute_pending && w.status == ST_OK);
+}
+
+__global__ void __launch_bounds__(256) k_build_A(Config cfg, int mode) {
+  const int wi = blockIdx.z >> 1, sp = blockIdx.z & 1;
+  const WalkerDev& w = cfg.W[wi];
+  if (!wants_build(w, mode)) return;
+  const int n = w.n, ld = w.cap, par = w.parity;
+  const int j = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (i >= n || j >= n) return;
+  const ProblemDev& pb = cfg.P[w.problem];
+  double* A = w.N[mode == 0 ? par : par ^ 1][sp];
+  const int* vsite = w.vsite[par];
+  const double* vtau = w.vtau[par];
+  const int* vs = w.vs[par];
+  const double ej = expV(pb, sp, vs[j]);
+  const double g = (i == j) ? g0_diag(pb, sp, vsite[i]) : g0_pair(pb, sp, vsite[i], vtau[i], vsite[j], vtau[j]);
+  A[(size_t)i * ld + j] = (i == j ? ej : 0.0) - g * (ej - 1.0);
+}
+
+// In-place Gauss-Jordan inverse with partial (row) pivoting, one block per
+// (walker, spin).  Column c of the working matrix is turned into column c of
+// the inverse as the elimination proceeds; the row interchanges are undone
+// at the end as column interchanges in reverse order.  Scratch (outside a
+// window): Lrow[sp] holds a copy of the pivot column and the pivot rows.
+// Writes the sign of det A to sgn_out[2*wi + sp] (0 if singular).
+__global__ void __launch_bounds__(1024) k_gj_inplace(Config cfg, int mode, int* sgn_out) {
+  const int wi = blockIdx.x >> 1, sp = blockIdx.x & 1;
+  WalkerDev& w = cfg.W[wi];
+  if (!wants_build(w, mode)) return;
+  const int n = w.n, ld = w.cap;
+  double* A = w.N[mode == 0 ? w.parity : w.parity ^ 1][sp];
+  // scratch: column copy (n doubles) and pivot rows (n ints, stored as doubles)
+  double* colc = w.Lrow[sp];
+  double* pivs = w.Lrow[sp] + ld;
+  __shared__ double s_val[32];
+  __shared__ int s_idx[32];
+  __shared__ int s_piv, s_bad;
+  __shared__ double s_d;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  int sign = 1;
+  if (tid == 0) s_bad = 0;
+  for (int c = 0; c < n; ++c) {
+    // pivot: argmax_{r >= c} |A[r][c]|
+    double best = -1.0;
+    int bi = c;
+    for (int r = c + tid; r < n; r += nt) {
+      const double v = fabs(A[(size_t)r * ld + c]);
+      if (v > best) {
+        best = v;
+        bi = r;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      s_val[warp] = best;
+      s_idx[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double b = -1.0;
+      int ix = c;
+      for (int k = 0; k < nt / 32; ++k)
+        if (s_val[k] > b || (s_val[k] == b && s_idx[k] < ix)) {
+          b = s_val[k];
+          ix = s_idx[k];
+        }
+      s_piv = ix;
+      if (!(b > 0.0)) s_bad = 1;
+      pivs[c] = (double)ix;
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const int p = s_piv;
+    if (p != c) {
+      for (int j = tid; j < n; j += nt) {
+        const double t = A[(size_t)c * ld + j];
+        A[(size_t)c * ld + j] = A[(size_t)p * ld + j];
+        A[(size_t)p * ld + j] = t;
+      }
+      sign = -sign;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      s_d = A[(size_t)c * ld + c];
+      A[(size_t)c * ld + c] = 1.0;
+    }
+    __syncthreads();
+    const double d = s_d;
+    if (d < 0.0) sign = -sign;
+    const double rd = 1.0 / d;
+    for (int j = tid; j < n; j += nt) A[(size_t)c * ld + j] *= rd;
+    for (int r = tid; r < n; r += nt) colc[r] = (r == c) ? 0.0 : A[(size_t)r * ld + c];
+    __syncthreads();
+    for (int r = tid; r < n; r += nt)
+      if (r != c) A[(size_t)r * ld + c] = 0.0;
+    __syncthreads();
+    // A[r][j] -= colc[r] * A[c][j]
+    for (int idx = tid; idx < n * n; idx += nt) {
+      const int r = idx / n, j = idx - r * n;
+      const double f = colc[r];
+      if (f != 0.0) A[(size_t)r * ld + j] -= f * A[(size_t)c * ld + j];
+    }
+    __syncthreads();
+  }
+  if (s_bad) {
+    if (tid == 0) {
+      w.status = ST_ERR_NUMERIC;
+      sgn_out[blockIdx.x] = 0;
+    }
+    return;
+  }
+  // undo the row interchanges as column interchanges, last first
+  for (int c = n - 1; c >= 0; --c) {
+    const int p = (int)pivs[c];
+    if (p != c)
+      for (int r = tid; r < n; r += nt) {
+        const double t = A[(size_t)r * ld + c];
+        A[(size_t)r * ld + c] = A[(size_t)r * ld + p];
+        A[(size_t)r * ld + p] = t;
+      }
+    __syncthreads();
+  }
+  if (tid == 0) sgn_out[blockIdx.x] = sign;
+}
+
+// Initial build finish: sign of prod_sigma det N_sigma^-1.
+__global__ void k_init_finish(Config cfg, const int* sgn) {
+  const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (wi >= cfg.n_walkers) return;
+  WalkerDev& w = cfg.W[wi];
+  if (w.n == 0) {
+    w.sign = 1.0;
+    return;
+  }
+  const int s = sgn[2 * wi] * sgn[2 * wi + 1];
+  if (s == 0) w.status = ST_ERR_NUMERIC;
+  w.sign = s < 0 ? -1.0 : 1.0;
+}
+
+// Drift of the updated N against the fresh inverse, then adopt the fresh one.
+// grid = walkers, block 256.
+__global__ void __launch_bounds__(256) k_recompute_finish(Config cfg, const int* sgn) {
+  WalkerDev& w = cfg.W[blockIdx.x];
+  if (!(w.active && w.recompute_pending && w.status == ST_OK)) return;
+  const int n = w.n, ld = w.cap, par = w.parity;
+  double dmax = 0.0, nmax = 0.0;
+  for (int sp = 0; sp < 2; ++sp) {
+    const double* Nold = w.N[par][sp];
+    const double* Nnew = w.N[par ^ 1][sp];
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int i = idx / n, j = idx - i * n;
+      const double a = Nold[(size_t)i * ld + j], b = Nnew[(size_t)i * ld + j];
+      dmax = fmax(dmax, fabs(a - b));
+      nmax = fmax(nmax, fabs(b));
+    }
+  }
+  __shared__ double s_d[8], s_n[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    nmax = fmax(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_d[threadIdx.x >> 5] = dmax;
+    s_n[threadIdx.x >> 5] = nmax;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    w.vsite[par ^ 1][i] = w.vsite[par][i];
+    w.vtau[par ^ 1][i] = w.vtau[par][i];
+    w.vs[par ^ 1][i] = w.vs[par][i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double d = 0.0, m = 0.0;
+    for (int k = 0; k < 8; ++k) {
+      d = fmax(d, s_d[k]);
+      m = fmax(m, s_n[k]);
+    }
+    const double rel = m > 0.0 ? d / m : 0.0;
+    if (rel > w.max_drift) w.max_drift = rel;
+    w.parity = par ^ 1;
+    w.n_recomputes++;
+    w.recompute_pending = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Measurement on the tau grid (after a post-warm-up sweep):
+//   G(dr, tau_a) = g0(dr, tau_a) + (1/Nc) sum_{r'} sum_i g0(r'+dr - r_i, tau_a - tau_i) b_i(r'),
+//   b_i(r') = (e^{V_i} - 1) sum_j N_ij g0(r_j - r', tau_j),
+// accumulated as sign * (-G) in the paper's convention.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool wants_measure(const WalkerDev& w) { return w.active && w.measure_pending; }
+
+// gR[sp][r'][j] = g0_sp(r_j - r', tau_j - 0+) ; grid = (blocks, walkers*2)
+__global__ void __launch_bounds__(256) k_meas_gr(Config cfg) {
+  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
+  const WalkerDev& w = cfg.W[wi];
+  if (!wants_measure(w)) return;
+  const ProblemDev& pb = cfg.P[w.problem];
+  const int n = w.n, par = w.parity, nc = pb.nc;
+  const int total = nc * n;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int rp = idx / n, j = idx - rp * n;
+    w.gR[((size_t)sp * nc + rp) * w.cap + j] = g0_pair(pb, sp, w.vsite[par][j], w.vtau[par][j], rp, 0.0);
+  }
+}
+
+// bvec[sp][r'][i] = (e^{V_i} - 1) sum_j N[i][j] gR[sp][r'][j]; one warp per (i, r').
+__global__ void __launch_bounds__(256) k_meas_b(Config cfg) {
+  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
+  const WalkerDev& w = cfg.W[wi];
+  if (!wants_measure(w)) return;
+  const ProblemDev& pb = cfg.P[w.problem];
+  const int n = w.n, par = w.parity, nc = pb.nc, ld = w.cap;
+  const double* N = w.N[par][sp];
+  const int lane = threadIdx.x & 31;
+  const int total = nc * n;
+  for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < total; item += (gridDim.x * blockDim.x) >> 5) {
+    const int rp = item / n, i = item - rp * n;
+    const double* g = w.gR + ((size_t)sp * nc + rp) * ld;
+    double acc = 0.0;
+    for (int j = lane; j < n; j += 32) acc += N[(size_t)i * ld + j] * g[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) w.bvec[((size_t)sp * nc + rp) * ld + i] = (expV(pb, sp, w.vs[par][i]) - 1.0) * acc;
+  }
+}
+
+// Gacc[sp][dr][a] += sign * (-G); grid = (blocks, walkers), thread per (sp, dr, a).
+__global__ void __launch_bounds__(256) k_meas_acc(Config cfg) {
+  WalkerDev& w = cfg.W[blockIdx.y];
+  if (!wants_measure(w)) return;
+  const ProblemDev& pb = cfg.P[w.problem];
+  const int n = w.n, par = w.parity, nc = pb.nc, ld = w.cap, ntm = cfg.n_tau_meas;
+  const int total = 2 * nc * ntm;
+  const double sign = w.sign;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int sp = idx / (nc * ntm);
+    const int rem = idx - sp * nc * ntm;
+    const int d = rem / ntm, a = rem - d * ntm;
+    const double ta = ((double)a + 0.5) * pb.beta / (double)ntm;
+    const double* row = pb.g0 + ((size_t)sp * nc + d) * (size_t)(pb.n_tau + 1);
+    double G = g0_interp(row, pb.n_tau, pb.beta, pb.tau_scale, ta);
+    double corr = 0.0;
+    for (int rp = 0; rp < nc; ++rp) {
+      const int x = pb.site_add[rp * nc + d];
+      const double* b = w.bvec + ((size_t)sp * nc + rp) * ld;
+      for (int i = 0; i < n; ++i) corr += g0_pair(pb, sp, x, ta, w.vsite[par][i], w.vtau[par][i]) * b[i];
+    }
+    G += corr / (double)nc;
+    w.Gacc[((size_t)sp * nc + d) * ntm + a] += sign * (-G);
+  }
+}
+
+__global__ void k_meas_finish(Config cfg) {
+  const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (wi >= cfg.n_walkers) return;
+  WalkerDev& w = cfg.W[wi];
+  if (!wants_measure(w)) return;
+  w.sign_sum += w.sign;
+  w.n_meas++;
+  w.k_sum += (double)w.n;
+  w.measure_pending = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Isolated-cluster G0 (paper convention) on the tau grid:
+//   G0(r, tau_l) = -(1/Nc) sum_K cos(K.r) e^{-tau xi_K} / (1 + e^{-beta xi_K})
+// ---------------------------------------------------------------------------
+__global__ void k_g0_isolated(int nc, const double* eps, const double* kr, double mu_eff, double beta, int n_tau,
+                              double* out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = nc * (n_tau + 1);
+  if (idx >= m) return;
+  const int r = idx / (n_tau + 1), l = idx - r * (n_tau + 1);
+  const double tau = (double)l * beta / (double)n_tau;
+  double acc = 0.0;
+  for (int k = 0; k < nc; ++k) {
+    const double xi = eps[k] - mu_eff;
+    double f;
+    if (xi >= 0.0) f = exp(-tau * xi) / (1.0 + exp(-beta * xi));
+    else f = exp((beta - tau) * xi) / (exp(beta * xi) + 1.0);
+    acc += cos(kr[(size_t)k * nc + r]) * f;
+  }
+  const double v = -acc / (double)nc;
+  out[idx] = v;
+  out[m + idx] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+void launch_init(const Config& cfg, int n0, int max_cap, int* d_sgn, cudaStream_t st) {
+  const int W = cfg.n_walkers;
+  k_init_vertices<<<W, 256, 0, st>>>(cfg, n0);
+  if (n0 > 0) {
+    k_build_A<<<dim3((n0 + 31) / 32, (n0 + 7) / 8, 2 * W), 256, 0, st>>>(cfg, 0);
+    k_gj_inplace<<<2 * W, 1024, 0, st>>>(cfg, 0, d_sgn);
+  }
+  k_init_finish<<<(W + 127) / 128, 128, 0, st>>>(cfg, d_sgn);
+  (void)max_cap;
+}
+
+void launch_recompute(const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st) {
+  const int W = cfg.n_walkers;
+  k_build_A<<<dim3((max_cap + 31) / 32, (max_cap + 7) / 8, 2 * W), 256, 0, st>>>(cfg, 1);
+  k_gj_inplace<<<2 * W, 1024, 0, st>>>(cfg, 1, d_sgn);
+  k_recompute_finish<<<W, 256, 0, st>>>(cfg, d_sgn);
+}
+
+void launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) {
+  const int W = cfg.n_walkers;
+  const int items = max_nc * max_cap;
+  int gb = (items + 255) / 256;
+  gb = gb < 1024 ? gb : 1024;
+  k_meas_gr<<<dim3(gb, 2 * W), 256, 0, st>>>(cfg);
+  int gw = (items * 32 + 255) / 256;
+  gw = gw < 2048 ? gw : 2048;
+  k_meas_b<<<dim3(gw, 2 * W), 256, 0, st>>>(cfg);
+  const int outs = 2 * max_nc * cfg.n_tau_meas;
+  int ga = (outs + 255) / 256;
+  ga = ga < 1024 ? ga : 1024;
+  k_meas_acc<<<dim3(ga, W), 256, 0, st>>>(cfg);
+  k_meas_finish<<<(W + 127) / 128, 128, 0, st>>>(cfg);
+}
+
+void launch_g0_isolated(int nc, const double* d_eps, const double* d_kr, double mu_eff, double beta, int n_tau,
+                        double* d_out, cudaStream_t st) {
+  const int m = nc * (n_tau + 1);
+  k_g0_isolated<<<(m + 255) / 256, 256, 0, st>>>(nc, d_eps, d_kr, mu_eff, beta, n_tau, d_out);
+}
+
+}  // namespace dca

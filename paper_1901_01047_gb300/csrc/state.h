@@ -1,0 +1,120 @@
+// state.h -- device-side data layout of the CT-AUX walker library.
+//
+// One WalkerDev record per walker lives in device memory; it holds the
+// walker's scalars and pointers into the library-owned pools.  Every kernel
+// reads the record to find out how much work this window has (the order n
+// changes every submatrix update), so the host launches a fixed kernel
+// sequence per window without reading anything back.
+//
+// Notation (DCA++ paper Sec. 2.3 and the submatrix-update paragraph there):
+//   vertex p = (site r_p, time tau_p, auxiliary spin s_p);
+//   V_p^sigma = sigma gamma s_p if p interacts, 0 otherwise (sigma = +1 up, -1 down);
+//   g0 = -G0;  N_sigma^-1 = e^{V} - g0 (e^{V} - 1);  G = N g0.
+// A window ("submatrix update") evaluates up to k_s proposals against the
+// N of the window start: insertion candidates are appended as
+// non-interacting rows n, n+1, ... of the extended matrices, accepted
+// flips are collected in the ordered set P with a_p = e^{V'_p - V_p} - 1,
+// and B_P = I + (I - G_PP) diag(a_P) is grown by bordering (its inverse
+// Binv).  At the end N <- N + (G[:,P] - E_P) diag(a_P) Binv N[P,:]
+// restricted to the surviving (interacting) rows and columns.
+#pragma once
+#include <cstdint>
+
+namespace dca {
+
+constexpr int KS_MAX = 128;     // largest submatrix size (App. B default is 128)
+
+enum : int32_t {
+  ST_OK = 0,
+  ST_ERR_NUMERIC = -5,
+  ST_ERR_CAPACITY = -7,
+};
+
+struct ProblemDev {
+  int32_t nc, n_tau;
+  double beta, K, gamma, tau_scale;   // tau_scale = n_tau / beta
+  double expV[2][2];                  // e^{sigma gamma s}: [spin][s > 0]
+  const int32_t* site_sub;            // [nc*nc]
+  const int32_t* site_add;            // [nc*nc]: site_add[y*nc + d] = x with site_sub[x*nc + y] = d
+  const double* g0;                   // [2][nc][n_tau+1], g0 = -G0
+};
+
+struct Proposal {
+  double tau;      // insert: new vertex time
+  double u;        // Metropolis uniform
+  int32_t type;    // 0 insert, 1 remove
+  int32_t s;       // insert: +1 / -1
+  int32_t site;    // insert: site
+  uint32_t word;   // remove: index word, index = floor(word * k / 2^32)
+  int32_t slot;    // insert: candidate slot c, extended row n + c
+  int32_t pad;
+};
+
+struct WalkerDev {
+  // ---- configuration and chain state ----
+  int32_t n;                 // order k = rows of N (all interacting between windows)
+  int32_t cap;               // matrix capacity (rows / leading dimension)
+  int32_t problem;           // index into the problem table
+  int32_t status;            // ST_OK or an error code; a walker in error stops
+  int32_t parity;            // which of the two buffers is current
+  int32_t windows_since_recompute;
+  uint32_t key0, key1;       // Philox key
+  uint64_t q;                // next proposal number
+  int64_t sweeps_done, sweeps_target, sweep_pos, sweep_len_cur, sweep_len, warm_k_sum;
+  double sign;
+
+  // ---- current window ----
+  int32_t active;            // this window does work
+  int32_t win_len;           // proposals generated
+  int32_t n_cand;            // insertion candidates generated
+  int32_t n_acc;             // accepted flips l
+  int32_t n_removed;         // accepted removals (existing rows)
+  int32_t n_eval;            // proposals evaluated (win_len unless aborted)
+  int32_t aborted;
+  int32_t n_surv;            // surviving rows after the window
+  int32_t measure_pending;
+  int32_t recompute_pending;
+
+  // ---- counters ----
+  int64_t n_prop, n_accept, n_ties, n_aborts, n_windows, n_meas, n_recomputes;
+  double sign_sum, k_sum, max_drift, flops;
+
+  // ---- decision log / replay ----
+  int64_t log_cap, forced_n;
+  uint8_t* log;              // [log_cap]
+  const uint8_t* forced;     // [forced_n]
+
+  // ---- pools (device pointers) ----
+  int32_t* vsite[2];         // [parity][cap]
+  double* vtau[2];
+  int32_t* vs[2];
+  double* N[2][2];           // [parity][spin] cap x cap, row-major, ld = cap
+  Proposal* prop;            // [KS_MAX]
+  double* Gc[2];             // [spin][KS_MAX][cap]: G_ext[:, n + c] stored per candidate c
+  double* Xr[2];             // [spin][KS_MAX][cap]: X[c, :] = g0[c,:] (e^V - 1) N
+  double* Binv[2];           // [spin][KS_MAX][KS_MAX]
+  double* aP[2];             // [spin][KS_MAX]
+  int32_t* P;                // [KS_MAX] extended index of accepted flips, in order
+  int32_t* removed;          // [KS_MAX] existing rows removed this window, ascending
+  int32_t* surv;             // [cap] new row -> extended old row
+  double* Lrow[2];           // [spin][cap][KS_MAX]
+  double* Lp[2];             // [spin][cap][KS_MAX]  (L Binv)
+  double* Rr[2];             // [spin][KS_MAX][cap]
+  double* Gacc;              // [2][nc][n_tau_meas]
+  double* gR;                // [2][nc][cap]
+  double* bvec;              // [2][nc][cap]
+};
+
+struct Config {
+  int32_t n_walkers;
+  int32_t ks;                // k_sub
+  int32_t warmup;
+  int32_t recompute_every;
+  int32_t n_tau_meas;
+  double tie_eps;
+  WalkerDev* W;              // [n_walkers]
+  const ProblemDev* P;       // [n_problems]
+  int32_t* active_count;     // [1]
+};
+
+}  // namespace dca

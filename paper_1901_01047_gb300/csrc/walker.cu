@@ -1,0 +1,519 @@
+// walker.cu -- host implementation of the C ABI declared in include/dca_walker.h.
+//
+// The host validates parameters, owns the device memory of all walkers,
+// and launches a fixed kernel sequence per submatrix update; all control
+// (order, sweep position, measurement and recompute schedule) lives in the
+// device-side walker records, so the host reads back only a small status word
+// between chunks of windows.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dca_walker.h"
+#include "kernels.h"
+#include "state.h"
+
+using dca::ProblemDev;
+using dca::WalkerDev;
+
+namespace {
+thread_local std::string g_create_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+}  // namespace
+
+struct dca_walker {
+  cudaStream_t stream = nullptr;
+  int W = 0, ks = 0, warmup = 0, R = 0, ntm = 0, precision = 0;
+  double tie_eps = 1e-10;
+  int max_cap = 0, max_nc = 0;
+  std::vector<int> nc_of;           // per walker
+  std::vector<size_t> gacc_off;     // per walker offset into the host G layout
+  std::vector<WalkerDev> h_W;       // host copies of the walker records
+  std::vector<void*> allocs;        // device allocations
+  std::vector<uint8_t*> forced;     // per walker replay buffers
+  WalkerDev* d_W = nullptr;
+  ProblemDev* d_P = nullptr;
+  int* d_active = nullptr;          // [4]: active, errors, first error, pad
+  int* h_active = nullptr;          // pinned
+  int* d_sgn = nullptr;
+  dca::Config cfg{};
+  std::string err;
+  int64_t windows_launched = 0;
+
+  ~dca_walker() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (void* p : allocs) cudaFree(p);
+    for (uint8_t* p : forced)
+      if (p) cudaFree(p);
+    if (h_active) cudaFreeHost(h_active);
+  }
+
+  void* dalloc(size_t bytes) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 1) != cudaSuccess) return nullptr;
+    allocs.push_back(p);
+    return p;
+  }
+};
+
+static int fail(dca_walker* w, int code, const std::string& msg) {
+  if (w) w->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+static int cuda_check(dca_walker* w, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return DCA_OK;
+  return fail(w, e == cudaErrorMemoryAllocation ? DCA_ERR_OOM : DCA_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr)                                               \
+  do {                                                         \
+    int _rc = cuda_check(h, (expr), #expr);                    \
+    if (_rc != DCA_OK) return _rc;                             \
+  } while (0)
+
+extern "C" DCA_API int dca_g0_isolated_cluster(int32_t nc, const double* eps_K, const double* k_dot_r, double mu, double U,
+                                       double beta, int32_t n_tau, double* G0_out) {
+  if (nc < 1 || n_tau < 1 || !(beta > 0.0) || !eps_K || !k_dot_r || !G0_out)
+    return fail(nullptr, DCA_ERR_ARG, "dca_g0_isolated_cluster: invalid argument");
+  const size_t m = (size_t)nc * (size_t)(n_tau + 1);
+  double *d_eps = nullptr, *d_kr = nullptr, *d_out = nullptr;
+  cudaError_t e = cudaMalloc(&d_eps, sizeof(double) * nc);
+  if (e == cudaSuccess) e = cudaMalloc(&d_kr, sizeof(double) * nc * nc);
+  if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(double) * 2 * m);
+  if (e == cudaSuccess) e = cudaMemcpy(d_eps, eps_K, sizeof(double) * nc, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_kr, k_dot_r, sizeof(double) * nc * nc, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    dca::launch_g0_isolated(nc, d_eps, d_kr, mu - 0.5 * U, beta, n_tau, d_out, nullptr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(G0_out, d_out, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost);
+  cudaFree(d_eps);
+  cudaFree(d_kr);
+  cudaFree(d_out);
+  if (e != cudaSuccess) return fail(nullptr, DCA_ERR_CUDA, std::string("dca_g0_isolated_cluster: ") + cudaGetErrorString(e));
+  return DCA_OK;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cuda_stream, dca_walker** out) {
+  if (!out) return fail(nullptr, DCA_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!prm) return fail(nullptr, DCA_ERR_ARG, "params is NULL");
+  const dca_walker_params& p = *prm;
+  if (p.n_problems < 1 || !p.problems) return fail(nullptr, DCA_ERR_ARG, "need at least one problem");
+  if (p.n_walkers < 1) return fail(nullptr, DCA_ERR_ARG, "n_walkers must be >= 1");
+  if (p.k_sub < 1 || p.k_sub > dca::KS_MAX) return fail(nullptr, DCA_ERR_ARG, "k_sub must be in 1..128");
+  if (p.recompute_every < 0 || p.warmup_sweeps < 0 || p.n_tau_meas < 1 || p.init_config_size < 0 ||
+      p.capacity < 0 || p.log_capacity < 0)
+    return fail(nullptr, DCA_ERR_ARG, "negative or zero size parameter");
+  if (p.precision != DCA_PREC_FP64) return fail(nullptr, DCA_ERR_ARG, "unsupported precision");
+  for (int i = 0; i < p.n_problems; ++i) {
+    const dca_problem& pr = p.problems[i];
+    if (pr.nc < 1 || !pr.site_sub || !pr.G0 || pr.n_tau < 1 || !(pr.beta > 0.0) || !(pr.K > 0.0) || !(pr.U >= 0.0) ||
+        !std::isfinite(pr.U) || !std::isfinite(pr.beta) || !std::isfinite(pr.K))
+      return fail(nullptr, DCA_ERR_ARG, "problem " + std::to_string(i) + ": invalid scalar or NULL array");
+    for (int r = 0; r < pr.nc; ++r) {
+      std::vector<int> seen(pr.nc, 0);
+      for (int c = 0; c < pr.nc; ++c) {
+        const int v = pr.site_sub[r * pr.nc + c];
+        if (v < 0 || v >= pr.nc || seen[v]++) return fail(nullptr, DCA_ERR_ARG, "site_sub row is not a permutation");
+      }
+    }
+    const size_t tsz = (size_t)2 * pr.nc * (pr.n_tau + 1);
+    for (size_t t = 0; t < tsz; ++t)
+      if (!std::isfinite(pr.G0[t])) return fail(nullptr, DCA_ERR_ARG, "G0 has a non-finite entry");
+  }
+  if (p.walker_problem)
+    for (int w = 0; w < p.n_walkers; ++w)
+      if (p.walker_problem[w] < 0 || p.walker_problem[w] >= p.n_problems)
+        return fail(nullptr, DCA_ERR_ARG, "walker_problem out of range");
+
+  dca_walker* h = new (std::nothrow) dca_walker();
+  if (!h) return fail(nullptr, DCA_ERR_OOM, "host allocation");
+  auto bail = [&](int code) {
+    g_create_error = h->err;
+    delete h;
+    return code;
+  };
+  h->stream = (cudaStream_t)cuda_stream;
+  h->W = p.n_walkers;
+  h->ks = p.k_sub;
+  h->warmup = p.warmup_sweeps;
+  h->R = p.recompute_every;
+  h->ntm = p.n_tau_meas;
+  h->precision = p.precision;
+  h->tie_eps = p.tie_eps > 0.0 ? p.tie_eps : 1e-10;
+
+  // ---- problems ----
+  std::vector<ProblemDev> hp(p.n_problems);
+  for (int i = 0; i < p.n_problems; ++i) {
+    const dca_problem& pr = p.problems[i];
+    ProblemDev& d = hp[i];
+    d.nc = pr.nc;
+    d.n_tau = pr.n_tau;
+    d.beta = pr.beta;
+    d.K = pr.K;
+    // cosh(gamma) = 1 + U beta N_corr / (2K), N_corr = Nc (Sec. 2.3)
+    d.gamma = std::acosh(1.0 + pr.U * pr.beta * (double)pr.nc / (2.0 * pr.K));
+    d.tau_scale = (double)pr.n_tau / pr.beta;
+    for (int sp = 0; sp < 2; ++sp) {
+      const double sigma = sp == 0 ? 1.0 : -1.0;
+      d.expV[sp][0] = std::exp(-sigma * d.gamma);
+      d.expV[sp][1] = std::exp(sigma * d.gamma);
+    }
+    std::vector<int32_t> add(pr.nc * pr.nc, -1);
+    for (int x = 0; x < pr.nc; ++x)
+      for (int y = 0; y < pr.nc; ++y) add[y * pr.nc + pr.site_sub[x * pr.nc + y]] = x;
+    for (int v : add)
+      if (v < 0) {
+        h->err = "site_sub does not define a group difference table";
+        return bail(DCA_ERR_ARG);
+      }
+    const size_t tsz = (size_t)2 * pr.nc * (pr.n_tau + 1);
+    std::vector<double> g0(tsz);
+    for (size_t t = 0; t < tsz; ++t) g0[t] = -pr.G0[t];
+    void* ds = h->dalloc(sizeof(int32_t) * pr.nc * pr.nc);
+    void* da = h->dalloc(sizeof(int32_t) * pr.nc * pr.nc);
+    void* dg = h->dalloc(sizeof(double) * tsz);
+    if (!ds || !da || !dg) {
+      h->err = "device allocation of problem tables";
+      return bail(DCA_ERR_OOM);
+    }
+    if (cudaMemcpy(ds, pr.site_sub, sizeof(int32_t) * pr.nc * pr.nc, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(da, add.data(), sizeof(int32_t) * pr.nc * pr.nc, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dg, g0.data(), sizeof(double) * tsz, cudaMemcpyHostToDevice) != cudaSuccess) {
+      h->err = "upload of problem tables failed";
+      return bail(DCA_ERR_CUDA);
+    }
+    d.site_sub = (const int32_t*)ds;
+    d.site_add = (const int32_t*)da;
+    d.g0 = (const double*)dg;
+    h->max_nc = std::max(h->max_nc, pr.nc);
+  }
+  h->d_P = (ProblemDev*)h->dalloc(sizeof(ProblemDev) * p.n_problems);
+  if (!h->d_P || cudaMemcpy(h->d_P, hp.data(), sizeof(ProblemDev) * p.n_problems, cudaMemcpyHostToDevice) != cudaSuccess) {
+    h->err = "upload of problem records failed";
+    return bail(DCA_ERR_CUDA);
+  }
+
+  // ---- walkers ----
+  const int KS = dca::KS_MAX;
+  h->h_W.resize(h->W);
+  h->nc_of.resize(h->W);
+  h->gacc_off.resize(h->W);
+  h->forced.assign(h->W, nullptr);
+  size_t goff = 0;
+  for (int wi = 0; wi < h->W; ++wi) {
+    const int pi = p.walker_problem ? p.walker_problem[wi] : wi % p.n_problems;
+    const dca_problem& pr = p.problems[pi];
+    int cap = p.capacity;
+    if (cap == 0) {
+      const double kmax = pr.K + pr.beta * pr.U * pr.nc * 0.5;
+      cap = (int)std::ceil(1.3 * kmax) + 2 * p.k_sub + p.init_config_size + 64;
+    }
+    cap = (int)align_up((size_t)cap, 32);
+    if (p.init_config_size + p.k_sub > cap) {
+      h->err = "capacity too small for the initial configuration";
+      return bail(DCA_ERR_ARG);
+    }
+    h->max_cap = std::max(h->max_cap, cap);
+    h->nc_of[wi] = pr.nc;
+    h->gacc_off[wi] = goff;
+    goff += (size_t)2 * pr.nc * p.n_tau_meas;
+
+    WalkerDev& w = h->h_W[wi];
+    std::memset(&w, 0, sizeof(w));
+    w.cap = cap;
+    w.problem = pi;
+    w.status = dca::ST_OK;
+    w.key0 = (uint32_t)p.seed;
+    w.key1 = (uint32_t)(p.seed >> 32) ^ (uint32_t)wi;
+    w.sign = 1.0;
+    w.log_cap = p.log_capacity;
+    const size_t C = (size_t)cap;
+    const int nc = pr.nc;
+    // one allocation per walker, carved into 256-byte aligned pieces
+    struct Piece {
+      void** dst;
+      size_t bytes;
+    };
+    std::vector<Piece> pieces;
+    for (int par = 0; par < 2; ++par) {
+      pieces.push_back({(void**)&w.vsite[par], sizeof(int32_t) * C});
+      pieces.push_back({(void**)&w.vtau[par], sizeof(double) * C});
+      pieces.push_back({(void**)&w.vs[par], sizeof(int32_t) * C});
+      for (int sp = 0; sp < 2; ++sp) pieces.push_back({(void**)&w.N[par][sp], sizeof(double) * C * C});
+    }
+    pieces.push_back({(void**)&w.prop, sizeof(dca::Proposal) * KS});
+    for (int sp = 0; sp < 2; ++sp) {
+      pieces.push_back({(void**)&w.Gc[sp], sizeof(double) * KS * C});
+      pieces.push_back({(void**)&w.Xr[sp], sizeof(double) * KS * C});
+      pieces.push_back({(void**)&w.Binv[sp], sizeof(double) * KS * KS});
+      pieces.push_back({(void**)&w.aP[sp], sizeof(double) * KS});
+      pieces.push_back({(void**)&w.Lrow[sp], sizeof(double) * KS * C});
+      pieces.push_back({(void**)&w.Lp[sp], sizeof(double) * KS * C});
+      pieces.push_back({(void**)&w.Rr[sp], sizeof(double) * KS * C});
+    }
+    pieces.push_back({(void**)&w.P, sizeof(int32_t) * KS});
+    pieces.push_back({(void**)&w.removed, sizeof(int32_t) * KS});
+    pieces.push_back({(void**)&w.surv, sizeof(int32_t) * C});
+    pieces.push_back({(void**)&w.Gacc, sizeof(double) * 2 * nc * p.n_tau_meas});
+    pieces.push_back({(void**)&w.gR, sizeof(double) * 2 * nc * C});
+    pieces.push_back({(void**)&w.bvec, sizeof(double) * 2 * nc * C});
+    if (p.log_capacity > 0) pieces.push_back({(void**)&w.log, (size_t)p.log_capacity});
+    size_t total = 0;
+    for (auto& pc : pieces) total += align_up(pc.bytes, 256);
+    char* base = (char*)h->dalloc(total);
+    if (!base) {
+      h->err = "device allocation of walker " + std::to_string(wi) + " (" + std::to_string(total) + " bytes)";
+      return bail(DCA_ERR_OOM);
+    }
+    if (cudaMemset(base, 0, total) != cudaSuccess) {
+      h->err = "cudaMemset failed";
+      return bail(DCA_ERR_CUDA);
+    }
+    size_t off = 0;
+    for (auto& pc : pieces) {
+      *pc.dst = base + off;
+      off += align_up(pc.bytes, 256);
+    }
+  }
+  h->d_W = (WalkerDev*)h->dalloc(sizeof(WalkerDev) * h->W);
+  h->d_active = (int*)h->dalloc(sizeof(int) * 4);
+  h->d_sgn = (int*)h->dalloc(sizeof(int) * 2 * h->W);
+  if (!h->d_W || !h->d_active || !h->d_sgn || cudaMallocHost(&h->h_active, sizeof(int) * 4) != cudaSuccess) {
+    h->err = "device allocation of walker records";
+    return bail(DCA_ERR_OOM);
+  }
+  if (cudaMemcpy(h->d_W, h->h_W.data(), sizeof(WalkerDev) * h->W, cudaMemcpyHostToDevice) != cudaSuccess) {
+    h->err = "upload of walker records";
+    return bail(DCA_ERR_CUDA);
+  }
+  h->cfg.n_walkers = h->W;
+  h->cfg.ks = h->ks;
+  h->cfg.warmup = h->warmup;
+  h->cfg.recompute_every = h->R;
+  h->cfg.n_tau_meas = h->ntm;
+  h->cfg.tie_eps = h->tie_eps;
+  h->cfg.W = h->d_W;
+  h->cfg.P = h->d_P;
+  h->cfg.active_count = h->d_active;
+
+  dca::launch_init(h->cfg, p.init_config_size, h->max_cap, h->d_sgn, h->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_W.data(), h->d_W, sizeof(WalkerDev) * h->W, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    h->err = std::string("initial build: ") + cudaGetErrorString(e);
+    return bail(DCA_ERR_CUDA);
+  }
+  for (int wi = 0; wi < h->W; ++wi)
+    if (h->h_W[wi].status != dca::ST_OK) {
+      h->err = "initial configuration of walker " + std::to_string(wi) + " is singular";
+      return bail(DCA_ERR_NUMERIC);
+    }
+  *out = h;
+  return DCA_OK;
+}
+
+static int status_code(int st) {
+  switch (st) {
+    case dca::ST_OK: return DCA_OK;
+    case dca::ST_ERR_NUMERIC: return DCA_ERR_NUMERIC;
+    case dca::ST_ERR_CAPACITY: return DCA_ERR_CAPACITY;
+    default: return DCA_ERR_STATE;
+  }
+}
+
+static int pull_records(dca_walker* h) {
+  CK(cudaMemcpyAsync(h->h_W.data(), h->d_W, sizeof(WalkerDev) * h->W, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return DCA_OK;
+}
+
+static int push_records(dca_walker* h) {
+  CK(cudaMemcpyAsync(h->d_W, h->h_W.data(), sizeof(WalkerDev) * h->W, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_sweep(dca_walker* h, int32_t n_sweeps) {
+  if (!h) return DCA_ERR_ARG;
+  if (n_sweeps < 0) return fail(h, DCA_ERR_ARG, "n_sweeps < 0");
+  if (n_sweeps == 0) return DCA_OK;
+  dca::launch_add_target(h->cfg, n_sweeps, h->stream);
+  CK(cudaGetLastError());
+  int chunk = 8;
+  for (;;) {
+    for (int i = 0; i < chunk; ++i) {
+      dca::launch_window(h->cfg, h->max_cap, h->stream);
+      dca::launch_measure(h->cfg, h->max_cap, h->max_nc, h->stream);
+      if (h->R > 0) dca::launch_recompute(h->cfg, h->max_cap, h->d_sgn, h->stream);
+    }
+    h->windows_launched += chunk;
+    CK(cudaGetLastError());
+    dca::launch_count_active(h->cfg, h->stream);
+    CK(cudaMemcpyAsync(h->h_active, h->d_active, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->h_active[0] == 0) break;
+    if (chunk < 512) chunk *= 2;
+  }
+  int rc = pull_records(h);
+  if (rc != DCA_OK) return rc;
+  for (int wi = 0; wi < h->W; ++wi)
+    if (h->h_W[wi].status != dca::ST_OK)
+      return fail(h, status_code(h->h_W[wi].status),
+                  "walker " + std::to_string(wi) + " stopped with status " + std::to_string(h->h_W[wi].status));
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_measure_G(dca_walker* h, double* G_out, double* sign_sum_out, int64_t* n_meas_out) {
+  if (!h) return DCA_ERR_ARG;
+  int rc = pull_records(h);
+  if (rc != DCA_OK) return rc;
+  for (int wi = 0; wi < h->W; ++wi) {
+    const WalkerDev& w = h->h_W[wi];
+    if (G_out)
+      CK(cudaMemcpyAsync(G_out + h->gacc_off[wi], w.Gacc, sizeof(double) * 2 * h->nc_of[wi] * h->ntm,
+                         cudaMemcpyDeviceToHost, h->stream));
+    if (sign_sum_out) sign_sum_out[wi] = w.sign_sum;
+    if (n_meas_out) n_meas_out[wi] = w.n_meas;
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_reset_measurements(dca_walker* h) {
+  if (!h) return DCA_ERR_ARG;
+  int rc = pull_records(h);
+  if (rc != DCA_OK) return rc;
+  for (int wi = 0; wi < h->W; ++wi) {
+    WalkerDev& w = h->h_W[wi];
+    CK(cudaMemsetAsync(w.Gacc, 0, sizeof(double) * 2 * h->nc_of[wi] * h->ntm, h->stream));
+    w.sign_sum = 0.0;
+    w.n_meas = 0;
+    w.k_sum = 0.0;
+  }
+  return push_records(h);
+}
+
+extern "C" DCA_API int dca_walker_stats(dca_walker* h, dca_walker_stats_t* out) {
+  if (!h || !out) return DCA_ERR_ARG;
+  int rc = pull_records(h);
+  if (rc != DCA_OK) return rc;
+  for (int wi = 0; wi < h->W; ++wi) {
+    const WalkerDev& w = h->h_W[wi];
+    dca_walker_stats_t& s = out[wi];
+    s.proposals = w.n_prop;
+    s.accepts = w.n_accept;
+    s.near_ties = w.n_ties;
+    s.aborts = w.n_aborts;
+    s.windows = w.n_windows;
+    s.sweeps = w.sweeps_done;
+    s.measurements = w.n_meas;
+    s.recomputes = w.n_recomputes;
+    s.sweep_length = w.sweep_len;
+    s.order = w.n;
+    s.status = status_code(w.status);
+    s.sign = w.sign;
+    s.k_sum = w.k_sum;
+    s.max_drift = w.max_drift;
+    s.n_update_flops = w.flops;
+  }
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_get_state(dca_walker* h, int32_t wi, dca_vertex* verts, int32_t* k, double* N_up,
+                                    double* N_dn) {
+  if (!h || wi < 0 || wi >= h->W) return DCA_ERR_ARG;
+  int rc = pull_records(h);
+  if (rc != DCA_OK) return rc;
+  const WalkerDev& w = h->h_W[wi];
+  const int n = w.n, par = w.parity;
+  if (k) *k = n;
+  if (verts && n > 0) {
+    std::vector<int32_t> site(n), s(n);
+    std::vector<double> tau(n);
+    CK(cudaMemcpyAsync(site.data(), w.vsite[par], sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(s.data(), w.vs[par], sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(tau.data(), w.vtau[par], sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < n; ++i) {
+      verts[i].site = site[i];
+      verts[i].s = s[i];
+      verts[i].tau = tau[i];
+    }
+  }
+  double* outs[2] = {N_up, N_dn};
+  for (int sp = 0; sp < 2; ++sp) {
+    if (!outs[sp] || n == 0) continue;
+    CK(cudaMemcpy2DAsync(outs[sp], sizeof(double) * n, w.N[par][sp], sizeof(double) * w.cap, sizeof(double) * n, n,
+                         cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_get_decision_log(dca_walker* h, int32_t wi, uint8_t* out, int64_t cap, int64_t* n) {
+  if (!h || wi < 0 || wi >= h->W) return DCA_ERR_ARG;
+  int rc = pull_records(h);
+  if (rc != DCA_OK) return rc;
+  const WalkerDev& w = h->h_W[wi];
+  const int64_t logged = (int64_t)w.q < w.log_cap ? (int64_t)w.q : w.log_cap;
+  if (n) *n = (int64_t)w.q;
+  if (out && cap > 0 && logged > 0) {
+    CK(cudaMemcpyAsync(out, w.log, (size_t)(logged < cap ? logged : cap), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_set_forced_decisions(dca_walker* h, int32_t wi, const uint8_t* log, int64_t n) {
+  if (!h || wi < 0 || wi >= h->W || n < 0 || (n > 0 && !log)) return DCA_ERR_ARG;
+  int rc = pull_records(h);
+  if (rc != DCA_OK) return rc;
+  if (h->forced[wi]) {
+    cudaFree(h->forced[wi]);
+    h->forced[wi] = nullptr;
+  }
+  WalkerDev& w = h->h_W[wi];
+  w.forced = nullptr;
+  w.forced_n = 0;
+  if (n > 0) {
+    uint8_t* d = nullptr;
+    CK(cudaMalloc(&d, (size_t)n));
+    h->forced[wi] = d;
+    CK(cudaMemcpy(d, log, (size_t)n, cudaMemcpyHostToDevice));
+    w.forced = d;
+    w.forced_n = n;
+  }
+  return push_records(h);
+}
+
+extern "C" DCA_API int dca_walker_capacity(dca_walker* h, int32_t wi, int32_t* capacity) {
+  if (!h || wi < 0 || wi >= h->W || !capacity) return DCA_ERR_ARG;
+  *capacity = h->h_W[wi].cap;
+  return DCA_OK;
+}
+
+extern "C" DCA_API void dca_walker_destroy(dca_walker* h) { delete h; }
+
+extern "C" DCA_API const char* dca_walker_last_error(dca_walker* h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}

@@ -1,0 +1,263 @@
+"""Thin ctypes binding of the C ABI in ``include/dca_walker.h``.
+
+Argument marshalling only: every step of a sweep runs in the CUDA kernels of
+``libdcawalker.so``.  If the library has not been built, ``load()`` raises;
+there is no fallback path.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdcawalker.so")
+
+DCA_OK = 0
+ERRORS = {-1: "ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "NUMERIC", -6: "STATE", -7: "CAPACITY"}
+PRECISIONS = {"fp64": 0}
+
+EXPORTS = [
+    "dca_g0_isolated_cluster", "dca_walker_create", "dca_walker_sweep", "dca_walker_measure_G",
+    "dca_walker_reset_measurements", "dca_walker_stats", "dca_walker_get_state",
+    "dca_walker_get_decision_log", "dca_walker_set_forced_decisions", "dca_walker_capacity",
+    "dca_walker_destroy", "dca_walker_last_error",
+]
+
+
+class Problem(C.Structure):
+    _fields_ = [
+        ("nc", C.c_int32),
+        ("site_sub", C.POINTER(C.c_int32)),
+        ("U", C.c_double),
+        ("beta", C.c_double),
+        ("K", C.c_double),
+        ("n_tau", C.c_int32),
+        ("G0", C.POINTER(C.c_double)),
+    ]
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("n_problems", C.c_int32),
+        ("problems", C.POINTER(Problem)),
+        ("n_walkers", C.c_int32),
+        ("walker_problem", C.POINTER(C.c_int32)),
+        ("k_sub", C.c_int32),
+        ("recompute_every", C.c_int32),
+        ("warmup_sweeps", C.c_int32),
+        ("n_tau_meas", C.c_int32),
+        ("precision", C.c_int32),
+        ("init_config_size", C.c_int32),
+        ("capacity", C.c_int32),
+        ("seed", C.c_uint64),
+        ("tie_eps", C.c_double),
+        ("log_capacity", C.c_int64),
+    ]
+
+
+class Vertex(C.Structure):
+    _fields_ = [("site", C.c_int32), ("s", C.c_int32), ("tau", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("proposals", C.c_int64),
+        ("accepts", C.c_int64),
+        ("near_ties", C.c_int64),
+        ("aborts", C.c_int64),
+        ("windows", C.c_int64),
+        ("sweeps", C.c_int64),
+        ("measurements", C.c_int64),
+        ("recomputes", C.c_int64),
+        ("sweep_length", C.c_int64),
+        ("order", C.c_int32),
+        ("status", C.c_int32),
+        ("sign", C.c_double),
+        ("k_sum", C.c_double),
+        ("max_drift", C.c_double),
+        ("n_update_flops", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libdcawalker.so; raise if it is missing (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libdcawalker.so is not built (%s); run __graft_entry__.build()" % path)
+    L = C.CDLL(path)
+    P = C.c_void_p
+    L.dca_g0_isolated_cluster.argtypes = [C.c_int32, P, P, C.c_double, C.c_double, C.c_double, C.c_int32, P]
+    L.dca_walker_create.argtypes = [C.POINTER(Params), P, C.POINTER(P)]
+    L.dca_walker_sweep.argtypes = [P, C.c_int32]
+    L.dca_walker_measure_G.argtypes = [P, P, P, P]
+    L.dca_walker_reset_measurements.argtypes = [P]
+    L.dca_walker_stats.argtypes = [P, P]
+    L.dca_walker_get_state.argtypes = [P, C.c_int32, P, C.POINTER(C.c_int32), P, P]
+    L.dca_walker_get_decision_log.argtypes = [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]
+    L.dca_walker_set_forced_decisions.argtypes = [P, C.c_int32, P, C.c_int64]
+    L.dca_walker_capacity.argtypes = [P, C.c_int32, C.POINTER(C.c_int32)]
+    L.dca_walker_destroy.argtypes = [P]
+    L.dca_walker_destroy.restype = None
+    L.dca_walker_last_error.argtypes = [P]
+    L.dca_walker_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+class WalkerError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+def _ptr(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def g0_isolated_cluster(eps_K, k_dot_r, mu, U, beta, n_tau):
+    """G0[2][nc][n_tau+1] (paper convention) of an isolated cluster, built on the GPU."""
+    L = load()
+    eps = np.ascontiguousarray(eps_K, np.float64)
+    kr = np.ascontiguousarray(k_dot_r, np.float64)
+    nc = eps.size
+    out = np.zeros((2, nc, n_tau + 1), np.float64)
+    rc = L.dca_g0_isolated_cluster(nc, _ptr(eps), _ptr(kr), float(mu), float(U), float(beta), int(n_tau),
+                                   _ptr(out))
+    if rc != DCA_OK:
+        raise WalkerError(rc, L.dca_walker_last_error(None).decode())
+    return out
+
+
+class Walkers:
+    """A batch of CT-AUX walkers living on the GPU.
+
+    problems: list of dicts with keys nc, site_sub [nc,nc], U, beta, K, G0 [2,nc,n_tau+1].
+    """
+
+    def __init__(self, problems, n_walkers=1, walker_problem=None, k_sub=32, recompute_every=64,
+                 warmup_sweeps=20, n_tau_meas=64, precision="fp64", init_config_size=10, capacity=0,
+                 seed=0, tie_eps=1e-10, log_capacity=0, stream=None):
+        L = load()
+        self._keep = []
+        probs = (Problem * len(problems))()
+        self.nc = []
+        for i, pr in enumerate(problems):
+            ss = np.ascontiguousarray(pr["site_sub"], np.int32).reshape(-1)
+            g0 = np.ascontiguousarray(pr["G0"], np.float64)
+            self._keep += [ss, g0]
+            probs[i].nc = int(pr["nc"])
+            probs[i].site_sub = ss.ctypes.data_as(C.POINTER(C.c_int32))
+            probs[i].U = float(pr["U"])
+            probs[i].beta = float(pr["beta"])
+            probs[i].K = float(pr.get("K", 1.0))
+            probs[i].n_tau = int(g0.shape[-1] - 1)
+            probs[i].G0 = g0.ctypes.data_as(C.POINTER(C.c_double))
+        p = Params()
+        p.n_problems = len(problems)
+        p.problems = probs
+        p.n_walkers = int(n_walkers)
+        if walker_problem is not None:
+            wp = np.ascontiguousarray(walker_problem, np.int32)
+            self._keep.append(wp)
+            p.walker_problem = wp.ctypes.data_as(C.POINTER(C.c_int32))
+            self.walker_problem = wp
+        else:
+            self.walker_problem = np.arange(n_walkers, dtype=np.int32) % len(problems)
+        self.nc = [int(problems[i]["nc"]) for i in self.walker_problem]
+        p.k_sub = int(k_sub)
+        p.recompute_every = int(recompute_every)
+        p.warmup_sweeps = int(warmup_sweeps)
+        p.n_tau_meas = int(n_tau_meas)
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p.init_config_size = int(init_config_size)
+        p.capacity = int(capacity)
+        p.seed = int(seed)
+        p.tie_eps = float(tie_eps)
+        p.log_capacity = int(log_capacity)
+        self.n_walkers = int(n_walkers)
+        self.n_tau_meas = int(n_tau_meas)
+        h = C.c_void_p()
+        st = C.c_void_p(int(stream)) if stream else None
+        rc = L.dca_walker_create(C.byref(p), st, C.byref(h))
+        if rc != DCA_OK:
+            raise WalkerError(rc, L.dca_walker_last_error(None).decode())
+        self._h = h
+        self._L = L
+
+    def _check(self, rc):
+        if rc != DCA_OK:
+            raise WalkerError(rc, self._L.dca_walker_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.dca_walker_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n):
+        self._check(self._L.dca_walker_sweep(self._h, int(n)))
+
+    def measure_G(self):
+        """(G_sum list per walker [2, nc, n_tau_meas], sign sums, measurement counts)."""
+        total = sum(2 * nc * self.n_tau_meas for nc in self.nc)
+        g = np.zeros(total, np.float64)
+        ss = np.zeros(self.n_walkers, np.float64)
+        nm = np.zeros(self.n_walkers, np.int64)
+        self._check(self._L.dca_walker_measure_G(self._h, _ptr(g), _ptr(ss), _ptr(nm)))
+        out, off = [], 0
+        for nc in self.nc:
+            m = 2 * nc * self.n_tau_meas
+            out.append(g[off:off + m].reshape(2, nc, self.n_tau_meas))
+            off += m
+        return out, ss, nm
+
+    def reset_measurements(self):
+        self._check(self._L.dca_walker_reset_measurements(self._h))
+
+    def stats(self):
+        arr = (Stats * self.n_walkers)()
+        self._check(self._L.dca_walker_stats(self._h, arr))
+        return [s.as_dict() for s in arr]
+
+    def capacity(self, wi=0):
+        c = C.c_int32(0)
+        self._check(self._L.dca_walker_capacity(self._h, int(wi), C.byref(c)))
+        return c.value
+
+    def state(self, wi=0):
+        cap = self.capacity(wi)
+        verts = (Vertex * cap)()
+        k = C.c_int32(0)
+        self._check(self._L.dca_walker_get_state(self._h, int(wi), verts, C.byref(k), None, None))
+        n = k.value
+        Nu = np.zeros((n, n), np.float64)
+        Nd = np.zeros((n, n), np.float64)
+        self._check(self._L.dca_walker_get_state(self._h, int(wi), None, C.byref(k), _ptr(Nu), _ptr(Nd)))
+        site = np.array([verts[i].site for i in range(n)], np.int32)
+        s = np.array([verts[i].s for i in range(n)], np.int8)
+        tau = np.array([verts[i].tau for i in range(n)], np.float64)
+        return dict(site=site, tau=tau, s=s, N=(Nu, Nd))
+
+    def decision_log(self, wi=0):
+        n = C.c_int64(0)
+        self._check(self._L.dca_walker_get_decision_log(self._h, int(wi), None, 0, C.byref(n)))
+        out = np.zeros(max(n.value, 1), np.uint8)
+        self._check(self._L.dca_walker_get_decision_log(self._h, int(wi), _ptr(out), out.size, C.byref(n)))
+        return out[:n.value]
+
+    def set_forced_decisions(self, wi, log):
+        log = np.ascontiguousarray(log, np.uint8)
+        self._check(self._L.dca_walker_set_forced_decisions(self._h, int(wi), _ptr(log), int(log.size)))

@@ -1,0 +1,122 @@
+"""GPU walker (FP64) against the oracle on identical seeded inputs.
+
+The submatrix algorithm reaches exactly the chain of single-spin updates, so
+for the same Philox stream both sides must take the same decisions (the
+oracle adopts the GPU's decision only where | |R| - u | < 1e-10), end with the
+same vertex list, and agree on N and on the accumulated sign * G to 1e-10 in
+the norm form max|X_gpu - X_oracle| / max|X_oracle|.
+"""
+import numpy as np
+import pytest
+
+from oracle import ctaux
+from tests.helpers import problem
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def _walkers(**kw):
+    import torch
+    from paper_1901_01047_gb300 import walker
+    kw.setdefault("stream", torch.cuda.current_stream().cuda_stream)
+    return walker.Walkers(**kw)
+
+
+def run_pair(nc, t, tp, U, beta, mu, n_tau, k_sub, sweeps, seed=0, warmup=10, init=10, ntm=16, R=0,
+             walkers=1, K=1.0, chunks=1):
+    c, eps, kr, G0 = problem(nc, t, tp, U, beta, mu, n_tau)
+    prob = dict(nc=nc, site_sub=c.site_sub, U=U, beta=beta, K=K, G0=G0)
+    gw = _walkers(problems=[prob], n_walkers=walkers, k_sub=k_sub, recompute_every=R, warmup_sweeps=warmup,
+                  n_tau_meas=ntm, init_config_size=init, seed=seed, log_capacity=1 << 22)
+    for _ in range(chunks):
+        gw.sweep(sweeps // chunks)
+    Gg, ssg, nmg = gw.measure_G()
+    st = gw.stats()
+    results = []
+    for wi in range(walkers):
+        log = gw.decision_log(wi)
+        ow = ctaux.OracleWalker(nc, c.site_sub, U, beta, K, G0, warmup_sweeps=warmup, n_tau_meas=ntm, seed=seed,
+                                walker_id=wi, init_config_size=init)
+        ow.enable_log(1 << 22)
+        ow.set_hints(log)
+        ow.sweep(sweeps)
+        results.append((gw.state(wi), ow.state(), log, ow.log(), Gg[wi], ssg[wi], nmg[wi], ow.G(), st[wi],
+                        ow.counters()))
+    gw.close()
+    return results
+
+
+def check(results):
+    for gs, os_, glog, olog, Gg, ssg, nmg, (Go, sso, nmo), st, oc in results:
+        assert glog.size == olog.size
+        assert np.array_equal(glog & 1, olog & 1)
+        assert st["proposals"] == oc["proposals"]
+        assert np.array_equal(gs["site"], os_["site"])
+        assert np.array_equal(gs["s"], os_["s"])
+        assert np.array_equal(gs["tau"], os_["tau"])
+        for sp in range(2):
+            ref = os_["N"][sp]
+            if ref.size:
+                assert np.abs(gs["N"][sp] - ref).max() <= TOL * np.abs(ref).max()
+        assert nmg == nmo and ssg == sso
+        assert np.abs(Gg - Go).max() <= TOL * max(np.abs(Go).max(), 1e-300)
+        assert st["status"] == 0
+
+
+def test_atom_parity():
+    # Hubbard atom Nc=1, U=4, beta=2, half filling, K=1, k_s=8, 4096-point G0
+    res = run_pair(1, 0.0, 0.0, 4.0, 2.0, 2.0, 4096, k_sub=8, sweeps=3000, seed=0, warmup=20, ntm=64)
+    check(res)
+
+
+def test_2x2_parity_dense_run():
+    # 2x2 cluster, t=1, U=4, beta=10, density 0.9 (mu from ED), k_s=32
+    res = run_pair(4, 1.0, 0.0, 4.0, 10.0, 0.9450480104035819, 4096, k_sub=32, sweeps=400, seed=0, warmup=20,
+                   ntm=32, R=16)
+    check(res)
+    st = res[0][8]
+    assert st["recomputes"] > 0 and st["max_drift"] < 1e-10
+    assert st["aborts"] > 0  # the duplicate-spin rule fired
+
+
+@pytest.mark.parametrize("k_sub", [1, 3, 16, 128])
+def test_window_sizes_reach_the_same_chain(k_sub):
+    res = run_pair(4, 1.0, 0.0, 4.0, 5.0, 1.2, 1024, k_sub=k_sub, sweeps=120, seed=3, warmup=5, ntm=8)
+    check(res)
+
+
+def test_empty_initial_configuration_and_chunked_calls():
+    res = run_pair(4, 1.0, -0.15, 3.0, 4.0, 0.8, 512, k_sub=16, sweeps=200, seed=5, warmup=0, init=0, ntm=8,
+                   chunks=4)
+    check(res)
+
+
+def test_u0_keeps_N_identity_and_measures_G0():
+    res = run_pair(4, 1.0, 0.0, 0.0, 3.0, 0.4, 512, k_sub=8, sweeps=300, seed=11, warmup=10, ntm=16, K=1.7)
+    check(res)
+    gs = res[0][0]
+    for sp in range(2):
+        assert np.array_equal(gs["N"][sp], np.eye(gs["site"].size))
+
+
+def test_batched_walkers_match_their_own_oracles():
+    res = run_pair(4, 1.0, 0.0, 4.0, 6.0, 1.0, 1024, k_sub=16, sweeps=80, seed=9, warmup=5, ntm=8, walkers=5,
+                   R=8)
+    check(res)
+    logs = [r[2] for r in res]
+    assert not np.array_equal(logs[0][:50], logs[1][:50])  # independent streams
+
+
+def test_g0_builder_matches_oracle_builder():
+    from paper_1901_01047_gb300 import inputs, walker
+    from oracle import g0 as og0
+    for nc, tp, U, beta, mu in [(1, 0.0, 4.0, 2.0, 2.0), (4, 0.0, 4.0, 10.0, 0.945), (16, -0.15, 6.0, 20.0, 2.85),
+                                (36, 0.0, 7.0, 30.0, 3.49)]:
+        c = inputs.cluster(nc)
+        eps = inputs.square_dispersion(c.kpts, 1.0, tp)
+        kr = inputs.k_dot_r(c)
+        ref = og0.g0_table(eps, kr, mu, U, beta, 2048)
+        got = walker.g0_isolated_cluster(eps, kr, mu, U, beta, 2048)
+        assert np.abs(got - ref).max() < 1e-13
