@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 CT-AUX walker (one JSON line on rank 0).
+
+A step is one sweep of every walker of the workload: proposals, candidate
+extension, Metropolis decisions with the Gamma (B^-1) growth, the N update with
+compaction, the measurement of G(tau) that ends the sweep and the periodic
+recompute of N.  The metric is walker vertex updates per second (decided
+proposals per second, all walkers, all ranks) and the N-update TFLOP/s.
+
+  python bench.py [--workload NAME] [--steps K] [--warmup W] [--gpus N]
+  python bench.py --impl reference ...   # the oracle on the host cores
+
+Multi-GPU: replicas only (independent Markov chains per rank, no collective
+on the data path; the ranks only meet at the timing barriers).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1901_01047_gb300 import inputs  # noqa: E402
+
+DEFAULT_WORKLOAD = "hubbard_2x2"
+METRIC = "walker vertex updates/sec"
+UNIT = "updates/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# Nominal GB300 FP64 rate (the recipe's figure); the FP64 path is bound by it.
+FP64_TFLOPS = 1.25
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def config_of(wl, world):
+    return {"workload": wl.name, "nc": wl.nc, "t": wl.t, "tp": wl.tp, "U": wl.U, "beta": wl.beta, "mu": wl.mu,
+            "K": wl.K, "walkers_per_gpu": wl.walkers, "k_sub": wl.k_sub, "n_tau": wl.n_tau,
+            "n_tau_meas": wl.n_tau_meas, "recompute_every": wl.recompute_every, "precision": wl.precision,
+            "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)"}
+
+
+def workload_problem(wl, use_gpu_builder):
+    c = inputs.cluster(wl.nc)
+    eps = inputs.square_dispersion(c.kpts, wl.t, wl.tp)
+    kr = inputs.k_dot_r(c)
+    if use_gpu_builder:
+        from paper_1901_01047_gb300 import walker
+        G0 = walker.g0_isolated_cluster(eps, kr, wl.mu, wl.U, wl.beta, wl.n_tau)
+    else:
+        from oracle import g0 as og0
+        G0 = og0.g0_table(eps, kr, wl.mu, wl.U, wl.beta, wl.n_tau)
+    return dict(nc=wl.nc, site_sub=c.site_sub, U=wl.U, beta=wl.beta, K=wl.K, G0=G0)
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample of the workload
+# --------------------------------------------------------------------------
+def _oracle_sample(args):
+    wl_name, walker_id, seed, seconds = args
+    sys.path.insert(0, ROOT)
+    from oracle import ctaux
+    wl = inputs.WORKLOADS[wl_name]
+    pr = workload_problem(wl, use_gpu_builder=False)
+    w = ctaux.OracleWalker(wl.nc, pr["site_sub"], wl.U, wl.beta, wl.K, pr["G0"], warmup_sweeps=wl.warmup_sweeps,
+                           n_tau_meas=wl.n_tau_meas, seed=seed, walker_id=walker_id,
+                           init_config_size=wl.init_config_size)
+    w.sweep(wl.warmup_sweeps)
+    p0 = w.counters()["proposals"]
+    t0 = time.perf_counter()
+    sweeps = 0
+    while time.perf_counter() - t0 < seconds:
+        w.sweep(1)
+        sweeps += 1
+    dt = time.perf_counter() - t0
+    return w.counters()["proposals"] - p0, dt, sweeps
+
+
+def cpu_baseline(wl_name, seconds=12.0):
+    wl = inputs.WORKLOADS[wl_name]
+    cores = max(1, min(wl.walkers, os.cpu_count() or 1))
+    if cores == 1:
+        props, dt, sweeps = _oracle_sample((wl_name, 0, wl.seed, seconds))
+        rate = props / dt
+        sample = "%d measured sweeps of 1 walker after %d warm-up sweeps (%.1f s)" % (sweeps, wl.warmup_sweeps, dt)
+    else:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_sample, [(wl_name, i, wl.seed, seconds) for i in range(cores)])
+        rate = sum(r[0] / r[1] for r in res)
+        sample = "%d walkers, one per core, %d sweeps in total (%.1f s each)" % (
+            cores, sum(r[2] for r in res), seconds)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    wl = inputs.WORKLOADS[args.workload]
+    per_step = max(0.2, min(10.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline(args.workload, seconds=per_step)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args.workload, seconds=per_step))
+    dt = time.perf_counter() - t0
+    v = sum(x["value"] for x in vals) / len(vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / max(1, args.steps),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config_of(wl, args.gpus),
+           "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_1901_01047_gb300 import walker
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    wl = inputs.WORKLOADS[args.workload]
+    stream = torch.cuda.current_stream()
+    prob = workload_problem(wl, use_gpu_builder=True)
+    seed = wl.seed + 1000003 * rank
+    gw = walker.Walkers([prob], n_walkers=wl.walkers, k_sub=wl.k_sub, recompute_every=wl.recompute_every,
+                        warmup_sweeps=wl.warmup_sweeps, n_tau_meas=wl.n_tau_meas, precision=wl.precision,
+                        init_config_size=wl.init_config_size, seed=seed, stream=stream.cuda_stream)
+    gw.sweep(wl.warmup_sweeps)            # the chain's own warm-up (no measurements)
+    for _ in range(args.warmup):          # bench warm-up steps (measured sweeps, untimed)
+        gw.sweep(1)
+
+    # Calibration (untimed): which kernel group dominates a step.
+    gw.set_timing(walker.GROUPS)
+    gw.timing(reset=True)
+    for _ in range(3):
+        gw.sweep(1)
+    times, _ = gw.timing(reset=True)
+    dominant = max(times, key=lambda g: times[g][0])
+
+    # L2 flush buffer (larger than the 129 MB L2), written between steps.
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    gw.set_timing([dominant])
+    st0 = gw.stats()
+    gw.timing(reset=True)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    phys = vis.split(",")[local_rank] if vis and len(vis.split(",")) > local_rank else str(local_rank)
+    clocks = ClockSampler(phys)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        gw.sweep(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st1 = gw.stats()
+    gtimes, launches = gw.timing(reset=True)
+    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    props = sum(b["proposals"] - a["proposals"] for a, b in zip(st0, st1))
+    flops = sum(b["n_update_flops"] - a["n_update_flops"] for a, b in zip(st0, st1))
+    ubytes = sum(b["n_update_bytes"] - a["n_update_bytes"] for a, b in zip(st0, st1))
+    eflops = sum(b["extend_flops"] - a["extend_flops"] for a, b in zip(st0, st1))
+    ebytes = sum(b["extend_bytes"] - a["extend_bytes"] for a, b in zip(st0, st1))
+    t_step = torch.tensor([dev_ms / 1000.0, float(props), flops], dtype=torch.float64, device="cuda")
+    if dist:
+        tmax = t_step.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t_step[1:], op=dist.ReduceOp.SUM)
+        t_step[0] = tmax[0]
+    seconds, props_all, flops_all = t_step.tolist()
+    value = props_all / seconds
+
+    # End to end through the public API with host buffers: a new bare propagator
+    # uploaded from pinned memory, one sweep, and G read back, every step.
+    G0_host = torch.from_numpy(np.ascontiguousarray(prob["G0"])).pin_memory()
+    g_bytes = sum(2 * nc * wl.n_tau_meas * 8 for nc in gw.nc) + 16 * wl.walkers
+    st2 = gw.stats()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for k in range(args.steps):
+        gw.update_G0(0, G0_host.numpy())
+        gw.sweep(1)
+        gw.measure_G()
+    torch.cuda.synchronize()
+    te = time.perf_counter() - te0
+    st3 = gw.stats()
+    e_props = sum(b["proposals"] - a["proposals"] for a, b in zip(st2, st3))
+    e_t = torch.tensor([te, float(e_props)], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(e_t[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(e_t[1:], op=dist.ReduceOp.SUM)
+    e_value = e_t[1].item() / e_t[0].item()
+
+    if rank == 0:
+        peaks, kind = _peaks()
+        g_ms, g_launch = gtimes[dominant]
+        windows = max(1, g_launch // max(1, {"propose": 1, "extend": 3, "metropolis": 1, "update": 4,
+                                             "measure": 4, "recompute": 3}[dominant]))
+        roof = roofline(dominant, g_ms, windows, flops, ubytes, eflops, ebytes, peaks, kind, wl)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * seconds / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl.precision == "fp64" else wl.precision,
+            "data": "synthetic",
+            "config": config_of(wl, world),
+            "final_order": st1[0]["order"],
+            "n_update_tflops": flops_all / seconds / 1e12,
+            "wall_s": wall,
+            "clocks": clk,
+            "gpu_launches": launches,
+            "kernel_ms": {g: round(v[0], 4) for g, v in times.items()},
+            "roofline": roof,
+            "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": int(G0_host.numel() * 8),
+                    "d2h_bytes_per_step": int(g_bytes)},
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.workload)
+        print(json.dumps(out))
+    gw.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def roofline(group, g_ms, windows, flops, ubytes, eflops, ebytes, peaks, kind, wl):
+    """Roofline of the dominant kernel group from its CUDA-event time."""
+    if group == "update":
+        work_b, work_f = ubytes, flops
+    elif group == "extend":
+        work_b, work_f = ebytes, eflops
+    else:
+        work_b, work_f = None, None
+    sec = g_ms / 1000.0
+    if work_b is None or sec <= 0:
+        return {"kernel": group, "bound": "alu", "achieved": None, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "note": "latency-bound serial kernel; see DESIGN.md",
+                "launch_ms": g_ms / max(1, windows)}
+    gbs = work_b / sec / 1e9
+    tfs = work_f / sec / 1e12
+    ai = work_f / max(work_b, 1.0)
+    hbm = peaks["hbm_gbs"]
+    if wl.precision == "fp64" and ai > FP64_TFLOPS * 1e12 / (hbm * 1e9):
+        return {"kernel": group, "bound": "alu", "achieved": tfs, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": tfs / FP64_TFLOPS, "traffic": None, "peak_kind": "nominal FP64",
+                "hbm_gbs_achieved": gbs, "launch_ms": g_ms / max(1, windows)}
+    return {"kernel": group, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+            "traffic": None, "peak_kind": kind, "launch_ms": g_ms / max(1, windows)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

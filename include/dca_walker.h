@@ -113,9 +113,12 @@ typedef struct {
   int32_t order;            /* current expansion order k */
   int32_t status;           /* DCA_OK or the walker's error code */
   double sign;              /* current configuration sign */
-  double k_sum;             /* sum of k over measurements */
+  double k_sum;             /* sum of sign * k over measurements (<k> = k_sum / sign_sum) */
   double max_drift;         /* largest max|N - N_fresh| / max|N_fresh| seen at recomputes */
   double n_update_flops;    /* algorithmic flop of the N updates (2 n^2 l + 2 n l^2 per spin) */
+  double n_update_bytes;    /* algorithmic bytes of the N updates (read + write n^2, n x l factors) */
+  double extend_flops;      /* flop of the candidate extension (4 n^2 c per spin) */
+  double extend_bytes;      /* bytes of the candidate extension (two reads of N per spin) */
 } dca_walker_stats_t;
 
 typedef struct dca_walker dca_walker;
@@ -168,6 +171,25 @@ DCA_API int dca_walker_get_decision_log(dca_walker* w, int32_t wi, uint8_t* out,
  * Metropolis decision for proposal q < n (used to compare arithmetic on an
  * identical trajectory).  n = 0 switches replay off. */
 DCA_API int dca_walker_set_forced_decisions(dca_walker* w, int32_t wi, const uint8_t* log, int64_t n);
+
+/* Replace the bare propagator of problem `problem` (host [2][nc][n_tau+1],
+ * same layout and convention as dca_problem.G0), e.g. for the next iteration
+ * of an outer DCA loop.  Stream-ordered: sweeps launched afterwards use it. */
+DCA_API int dca_walker_update_G0(dca_walker* w, int32_t problem, const double* G0);
+
+/* Kernel groups for timing: bit g of the mask times group g with CUDA events
+ * recorded on the walker's stream around every launch of that group.
+ *   0 proposals, 1 candidate extension (G columns / X rows), 2 Metropolis
+ *   with the Gamma (B^-1) growth, 3 N update with compaction, 4 measurement,
+ *   5 from-scratch recompute. */
+#define DCA_N_GROUPS 6
+DCA_API int dca_walker_set_timing(dca_walker* w, uint32_t group_mask);
+
+/* Accumulated milliseconds and kernel launches per group (arrays of
+ * DCA_N_GROUPS, either may be NULL) and the total number of kernels the
+ * library launched; reset != 0 zeroes the counters.  Synchronises the stream. */
+DCA_API int dca_walker_get_timing(dca_walker* w, double* group_ms, int64_t* group_launches,
+                                  int64_t* total_launches, int32_t reset);
 
 /* Device buffer sizes and capacity of walker wi (for diagnostics). */
 DCA_API int dca_walker_capacity(dca_walker* w, int32_t wi, int32_t* capacity);

@@ -147,7 +147,7 @@ typedef struct {
     uint8_t* log; int64_t log_n, log_cap;
     const uint8_t* hints; int64_t hints_n;
     int64_t n_prop, n_acc, n_ties, n_adopted;
-    double k_sum; int64_t k_samples;
+    double k_sum; int64_t k_samples;   /* k_sum: sum over measurements of sign * k */
 } orc_walker;
 
 /* ------------------------------------------------------------------ */
@@ -591,7 +591,7 @@ int orc_sweep(orc_walker* w, int32_t n_sweeps)
         }
         if (w->sweeps_done >= w->warmup) {
             measure(w);
-            w->k_sum += (double)w->k;
+            w->k_sum += w->sign * (double)w->k;
             w->k_samples++;
         }
         w->sweeps_done++;

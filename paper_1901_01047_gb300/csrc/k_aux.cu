@@ -303,7 +303,7 @@ __global__ void k_meas_finish(Config cfg) {
   if (!wants_measure(w)) return;
   w.sign_sum += w.sign;
   w.n_meas++;
-  w.k_sum += (double)w.n;
+  w.k_sum += w.sign * (double)w.n;
   w.measure_pending = 0;
 }
 
@@ -345,14 +345,24 @@ void launch_init(const Config& cfg, int n0, int max_cap, int* d_sgn, cudaStream_
   (void)max_cap;
 }
 
-void launch_recompute(const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st) {
+int launch_recompute(const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st) {
   const int W = cfg.n_walkers;
   k_build_A<<<dim3((max_cap + 31) / 32, (max_cap + 7) / 8, 2 * W), 256, 0, st>>>(cfg, 1);
   k_gj_inplace<<<2 * W, 1024, 0, st>>>(cfg, 1, d_sgn);
   k_recompute_finish<<<W, 256, 0, st>>>(cfg, d_sgn);
+  return 3;
 }
 
-void launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) {
+__global__ void k_negate(const double* src, double* dst, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = -src[i];
+}
+
+void launch_negate(const double* src, double* dst, size_t n, cudaStream_t st) {
+  k_negate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
+}
+
+int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) {
   const int W = cfg.n_walkers;
   const int items = max_nc * max_cap;
   int gb = (items + 255) / 256;
@@ -366,6 +376,7 @@ void launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st)
   ga = ga < 1024 ? ga : 1024;
   k_meas_acc<<<dim3(ga, W), 256, 0, st>>>(cfg);
   k_meas_finish<<<(W + 127) / 128, 128, 0, st>>>(cfg);
+  return 4;
 }
 
 void launch_g0_isolated(int nc, const double* d_eps, const double* d_kr, double mu_eff, double beta, int n_tau,

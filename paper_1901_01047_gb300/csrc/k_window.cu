@@ -526,7 +526,19 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
         w.windows_since_recompute = 0;
       }
       const double ns = (double)n_s, ll = (double)l;
-      if (l > 0) w.flops += 2.0 * (2.0 * ns * ns * ll + 2.0 * ns * ll * ll);
+      // N update per spin: 2 n_s^2 l + 2 n_s l^2 flop; reads and writes n_s^2
+      // entries plus the n_s x l factors (8-byte words).
+      if (l > 0) {
+        w.flops += 2.0 * (2.0 * ns * ns * ll + 2.0 * ns * ll * ll);
+        w.upd_bytes += 2.0 * 8.0 * (2.0 * ns * ns + 2.0 * ns * ll);
+      }
+      // candidate extension per spin: G columns (n x n x c) and X rows
+      // (c x n x n), each reading N once.
+      const double nn = (double)n, cc = (double)w.n_cand;
+      if (w.n_cand > 0) {
+        w.ext_flops += 2.0 * (4.0 * nn * nn * cc);
+        w.ext_bytes += 2.0 * 8.0 * (2.0 * nn * nn);
+      }
     } else {
       w.active = 0;
       w.n_acc = 0;
@@ -684,21 +696,34 @@ __global__ void k_add_target(Config cfg, int64_t n_sweeps) {
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
-void launch_window(const Config& cfg, int max_cap, cudaStream_t st) {
+int launch_window_group(int group, const Config& cfg, int max_cap, cudaStream_t st) {
   const int W = cfg.n_walkers;
   const int rt = (max_cap + TT - 1) / TT;
   const int ct = (cfg.ks + TT - 1) / TT;
-  k_begin<<<W, 128, 0, st>>>(cfg);
-  k_cand_g<<<dim3(rt, ct, 2 * W), 256, 0, st>>>(cfg);
-  k_cand_x<<<dim3(rt, ct, 2 * W), 256, 0, st>>>(cfg);
-  k_cand_cc<<<dim3(cfg.ks, 2 * W), 128, 0, st>>>(cfg);
-  k_metropolis<<<W, 256, 0, st>>>(cfg);
-  const int rows = (max_cap * cfg.ks + 255) / 256;
-  const int gb = rows < 512 ? rows : 512;
-  k_upd_lrow<<<dim3(gb, 2 * W), 256, 0, st>>>(cfg);
-  k_upd_lp_rr<<<dim3(gb, 2 * W), 256, 0, st>>>(cfg);
-  k_upd_apply<<<dim3(rt, rt, 2 * W), 256, 0, st>>>(cfg);
-  k_window_end<<<W, 256, 0, st>>>(cfg);
+  switch (group) {
+    case GROUP_PROPOSE:
+      k_begin<<<W, 128, 0, st>>>(cfg);
+      return 1;
+    case GROUP_EXTEND:
+      k_cand_g<<<dim3(rt, ct, 2 * W), 256, 0, st>>>(cfg);
+      k_cand_x<<<dim3(rt, ct, 2 * W), 256, 0, st>>>(cfg);
+      k_cand_cc<<<dim3(cfg.ks, 2 * W), 128, 0, st>>>(cfg);
+      return 3;
+    case GROUP_METROPOLIS:
+      k_metropolis<<<W, 256, 0, st>>>(cfg);
+      return 1;
+    case GROUP_UPDATE: {
+      const int rows = (max_cap * cfg.ks + 255) / 256;
+      const int gb = rows < 512 ? rows : 512;
+      k_upd_lrow<<<dim3(gb, 2 * W), 256, 0, st>>>(cfg);
+      k_upd_lp_rr<<<dim3(gb, 2 * W), 256, 0, st>>>(cfg);
+      k_upd_apply<<<dim3(rt, rt, 2 * W), 256, 0, st>>>(cfg);
+      k_window_end<<<W, 256, 0, st>>>(cfg);
+      return 4;
+    }
+    default:
+      return 0;
+  }
 }
 
 void launch_count_active(const Config& cfg, cudaStream_t st) { k_count_active<<<1, 256, 0, st>>>(cfg); }

@@ -8,12 +8,25 @@
 
 namespace dca {
 
-void launch_window(const Config& cfg, int max_cap, cudaStream_t st);
+// Kernel groups of one window (and the per-window extras), timed separately.
+enum Group : int {
+  GROUP_PROPOSE = 0,     // k_begin
+  GROUP_EXTEND = 1,      // k_cand_g, k_cand_x, k_cand_cc
+  GROUP_METROPOLIS = 2,  // k_metropolis
+  GROUP_UPDATE = 3,      // k_upd_lrow, k_upd_lp_rr, k_upd_apply, k_window_end
+  GROUP_MEASURE = 4,     // k_meas_*
+  GROUP_RECOMPUTE = 5,   // k_build_A, k_gj_inplace, k_recompute_finish
+  N_GROUPS = 6,
+};
+
+// Each launcher returns the number of kernels it launched.
+int launch_window_group(int group, const Config& cfg, int max_cap, cudaStream_t st);
 void launch_count_active(const Config& cfg, cudaStream_t st);
 void launch_add_target(const Config& cfg, int64_t n_sweeps, cudaStream_t st);
 void launch_init(const Config& cfg, int n0, int max_cap, int* d_sgn, cudaStream_t st);
-void launch_recompute(const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st);
-void launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
+int launch_recompute(const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st);
+int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
+void launch_negate(const double* src, double* dst, size_t n, cudaStream_t st);
 void launch_g0_isolated(int nc, const double* d_eps, const double* d_kr, double mu_eff, double beta, int n_tau,
                         double* d_out, cudaStream_t st);
 

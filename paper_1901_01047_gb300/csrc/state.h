@@ -77,7 +77,9 @@ struct WalkerDev {
 
   // ---- counters ----
   int64_t n_prop, n_accept, n_ties, n_aborts, n_windows, n_meas, n_recomputes;
-  double sign_sum, k_sum, max_drift, flops;
+  double sign_sum, k_sum, max_drift;
+  // algorithmic work (both spins): N update flop / bytes, candidate extension flop / bytes
+  double flops, upd_bytes, ext_flops, ext_bytes;
 
   // ---- decision log / replay ----
   int64_t log_cap, forced_n;

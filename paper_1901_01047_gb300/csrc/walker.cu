@@ -50,9 +50,21 @@ struct dca_walker {
   dca::Config cfg{};
   std::string err;
   int64_t windows_launched = 0;
+  // problem tables (device) for dca_walker_update_G0
+  std::vector<ProblemDev> h_P;
+  std::vector<double*> g0_stage;    // per problem staging buffer [2][nc][n_tau+1]
+  // timing of kernel groups with CUDA events on the walker's stream
+  uint32_t timing_mask = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_pending;  // (group, index of the start event)
+  size_t ev_used = 0;
+  double group_ms[dca::N_GROUPS] = {0};
+  int64_t group_launches[dca::N_GROUPS] = {0};
+  int64_t total_launches = 0;
 
   ~dca_walker() {
     if (stream) cudaStreamSynchronize(stream);
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
     for (uint8_t* p : forced)
       if (p) cudaFree(p);
@@ -205,6 +217,15 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     d.g0 = (const double*)dg;
     h->max_nc = std::max(h->max_nc, pr.nc);
   }
+  h->h_P = hp;
+  for (int i = 0; i < p.n_problems; ++i) {
+    double* st = (double*)h->dalloc(sizeof(double) * 2 * hp[i].nc * (hp[i].n_tau + 1));
+    if (!st) {
+      h->err = "device allocation of G0 staging buffer";
+      return bail(DCA_ERR_OOM);
+    }
+    h->g0_stage.push_back(st);
+  }
   h->d_P = (ProblemDev*)h->dalloc(sizeof(ProblemDev) * p.n_problems);
   if (!h->d_P || cudaMemcpy(h->d_P, hp.data(), sizeof(ProblemDev) * p.n_problems, cudaMemcpyHostToDevice) != cudaSuccess) {
     h->err = "upload of problem records failed";
@@ -352,24 +373,77 @@ static int push_records(dca_walker* h) {
   return DCA_OK;
 }
 
+static cudaEvent_t next_event(dca_walker* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+// Launch one kernel group, bracketed by events when its timing bit is set.
+static void run_group(dca_walker* h, int group) {
+  const bool timed = (h->timing_mask >> group) & 1u;
+  cudaEvent_t e0 = nullptr;
+  size_t i0 = 0;
+  if (timed) {
+    i0 = h->ev_used;
+    e0 = next_event(h);
+    if (e0) cudaEventRecord(e0, h->stream);
+  }
+  int k = 0;
+  switch (group) {
+    case dca::GROUP_MEASURE: k = dca::launch_measure(h->cfg, h->max_cap, h->max_nc, h->stream); break;
+    case dca::GROUP_RECOMPUTE: k = dca::launch_recompute(h->cfg, h->max_cap, h->d_sgn, h->stream); break;
+    default: k = dca::launch_window_group(group, h->cfg, h->max_cap, h->stream); break;
+  }
+  h->total_launches += k;
+  h->group_launches[group] += k;
+  if (timed && e0) {
+    cudaEvent_t e1 = next_event(h);
+    if (e1) {
+      cudaEventRecord(e1, h->stream);
+      h->ev_pending.push_back({group, (int)i0});
+    }
+  }
+}
+
+// After a stream synchronisation: fold the recorded intervals into the totals.
+static void collect_events(dca_walker* h) {
+  for (auto& pr : h->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[pr.second], h->ev_pool[pr.second + 1]) == cudaSuccess)
+      h->group_ms[pr.first] += ms;
+  }
+  h->ev_pending.clear();
+  h->ev_used = 0;
+}
+
 extern "C" DCA_API int dca_walker_sweep(dca_walker* h, int32_t n_sweeps) {
   if (!h) return DCA_ERR_ARG;
   if (n_sweeps < 0) return fail(h, DCA_ERR_ARG, "n_sweeps < 0");
   if (n_sweeps == 0) return DCA_OK;
   dca::launch_add_target(h->cfg, n_sweeps, h->stream);
+  h->total_launches += 1;
   CK(cudaGetLastError());
   int chunk = 8;
   for (;;) {
     for (int i = 0; i < chunk; ++i) {
-      dca::launch_window(h->cfg, h->max_cap, h->stream);
-      dca::launch_measure(h->cfg, h->max_cap, h->max_nc, h->stream);
-      if (h->R > 0) dca::launch_recompute(h->cfg, h->max_cap, h->d_sgn, h->stream);
+      run_group(h, dca::GROUP_PROPOSE);
+      run_group(h, dca::GROUP_EXTEND);
+      run_group(h, dca::GROUP_METROPOLIS);
+      run_group(h, dca::GROUP_UPDATE);
+      run_group(h, dca::GROUP_MEASURE);
+      if (h->R > 0) run_group(h, dca::GROUP_RECOMPUTE);
     }
     h->windows_launched += chunk;
     CK(cudaGetLastError());
     dca::launch_count_active(h->cfg, h->stream);
+    h->total_launches += 1;
     CK(cudaMemcpyAsync(h->h_active, h->d_active, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    collect_events(h);
     if (h->h_active[0] == 0) break;
     if (chunk < 512) chunk *= 2;
   }
@@ -379,6 +453,45 @@ extern "C" DCA_API int dca_walker_sweep(dca_walker* h, int32_t n_sweeps) {
     if (h->h_W[wi].status != dca::ST_OK)
       return fail(h, status_code(h->h_W[wi].status),
                   "walker " + std::to_string(wi) + " stopped with status " + std::to_string(h->h_W[wi].status));
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_set_timing(dca_walker* h, uint32_t group_mask) {
+  if (!h) return DCA_ERR_ARG;
+  h->timing_mask = group_mask & ((1u << dca::N_GROUPS) - 1u);
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_get_timing(dca_walker* h, double* group_ms, int64_t* group_launches,
+                                             int64_t* total_launches, int32_t reset) {
+  if (!h) return DCA_ERR_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  collect_events(h);
+  for (int g = 0; g < dca::N_GROUPS; ++g) {
+    if (group_ms) group_ms[g] = h->group_ms[g];
+    if (group_launches) group_launches[g] = h->group_launches[g];
+  }
+  if (total_launches) *total_launches = h->total_launches;
+  if (reset) {
+    for (int g = 0; g < dca::N_GROUPS; ++g) {
+      h->group_ms[g] = 0.0;
+      h->group_launches[g] = 0;
+    }
+    h->total_launches = 0;
+  }
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_update_G0(dca_walker* h, int32_t problem, const double* G0) {
+  if (!h || problem < 0 || problem >= (int)h->h_P.size() || !G0) return DCA_ERR_ARG;
+  const ProblemDev& pd = h->h_P[problem];
+  const size_t tsz = (size_t)2 * pd.nc * (pd.n_tau + 1);
+  for (size_t t = 0; t < tsz; ++t)
+    if (!std::isfinite(G0[t])) return fail(h, DCA_ERR_ARG, "G0 has a non-finite entry");
+  CK(cudaMemcpyAsync(h->g0_stage[problem], G0, sizeof(double) * tsz, cudaMemcpyHostToDevice, h->stream));
+  dca::launch_negate(h->g0_stage[problem], const_cast<double*>(pd.g0), tsz, h->stream);
+  h->total_launches += 1;
+  CK(cudaGetLastError());
   return DCA_OK;
 }
 
@@ -434,6 +547,9 @@ extern "C" DCA_API int dca_walker_stats(dca_walker* h, dca_walker_stats_t* out) 
     s.k_sum = w.k_sum;
     s.max_drift = w.max_drift;
     s.n_update_flops = w.flops;
+    s.n_update_bytes = w.upd_bytes;
+    s.extend_flops = w.ext_flops;
+    s.extend_bytes = w.ext_bytes;
   }
   return DCA_OK;
 }

@@ -20,8 +20,10 @@ EXPORTS = [
     "dca_g0_isolated_cluster", "dca_walker_create", "dca_walker_sweep", "dca_walker_measure_G",
     "dca_walker_reset_measurements", "dca_walker_stats", "dca_walker_get_state",
     "dca_walker_get_decision_log", "dca_walker_set_forced_decisions", "dca_walker_capacity",
-    "dca_walker_destroy", "dca_walker_last_error",
+    "dca_walker_destroy", "dca_walker_last_error", "dca_walker_update_G0", "dca_walker_set_timing",
+    "dca_walker_get_timing",
 ]
+GROUPS = ["propose", "extend", "metropolis", "update", "measure", "recompute"]
 
 
 class Problem(C.Structure):
@@ -76,6 +78,9 @@ class Stats(C.Structure):
         ("k_sum", C.c_double),
         ("max_drift", C.c_double),
         ("n_update_flops", C.c_double),
+        ("n_update_bytes", C.c_double),
+        ("extend_flops", C.c_double),
+        ("extend_bytes", C.c_double),
     ]
 
     def as_dict(self):
@@ -104,6 +109,9 @@ def load(path=LIB_PATH):
     L.dca_walker_get_decision_log.argtypes = [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]
     L.dca_walker_set_forced_decisions.argtypes = [P, C.c_int32, P, C.c_int64]
     L.dca_walker_capacity.argtypes = [P, C.c_int32, C.POINTER(C.c_int32)]
+    L.dca_walker_update_G0.argtypes = [P, C.c_int32, P]
+    L.dca_walker_set_timing.argtypes = [P, C.c_uint32]
+    L.dca_walker_get_timing.argtypes = [P, P, P, C.POINTER(C.c_int64), C.c_int32]
     L.dca_walker_destroy.argtypes = [P]
     L.dca_walker_destroy.restype = None
     L.dca_walker_last_error.argtypes = [P]
@@ -257,6 +265,26 @@ class Walkers:
         out = np.zeros(max(n.value, 1), np.uint8)
         self._check(self._L.dca_walker_get_decision_log(self._h, int(wi), _ptr(out), out.size, C.byref(n)))
         return out[:n.value]
+
+    def update_G0(self, problem, G0):
+        """Upload a new bare propagator (host array, paper convention) for a problem."""
+        G0 = np.ascontiguousarray(G0, np.float64)
+        self._check(self._L.dca_walker_update_G0(self._h, int(problem), _ptr(G0)))
+
+    def set_timing(self, groups):
+        """Time the named kernel groups with CUDA events on the walker's stream."""
+        mask = 0
+        for g in groups:
+            mask |= 1 << GROUPS.index(g)
+        self._check(self._L.dca_walker_set_timing(self._h, mask))
+
+    def timing(self, reset=False):
+        """{group: (ms, launches)} and the total number of library kernel launches."""
+        ms = np.zeros(len(GROUPS), np.float64)
+        ln = np.zeros(len(GROUPS), np.int64)
+        tot = C.c_int64(0)
+        self._check(self._L.dca_walker_get_timing(self._h, _ptr(ms), _ptr(ln), C.byref(tot), 1 if reset else 0))
+        return {g: (float(ms[i]), int(ln[i])) for i, g in enumerate(GROUPS)}, int(tot.value)
 
     def set_forced_decisions(self, wi, log):
         log = np.ascontiguousarray(log, np.uint8)

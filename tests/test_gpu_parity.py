@@ -29,7 +29,7 @@ def run_pair(nc, t, tp, U, beta, mu, n_tau, k_sub, sweeps, seed=0, warmup=10, in
     c, eps, kr, G0 = problem(nc, t, tp, U, beta, mu, n_tau)
     prob = dict(nc=nc, site_sub=c.site_sub, U=U, beta=beta, K=K, G0=G0)
     gw = _walkers(problems=[prob], n_walkers=walkers, k_sub=k_sub, recompute_every=R, warmup_sweeps=warmup,
-                  n_tau_meas=ntm, init_config_size=init, seed=seed, log_capacity=1 << 22)
+                  n_tau_meas=ntm, init_config_size=init, seed=seed, log_capacity=1 << 23)
     for _ in range(chunks):
         gw.sweep(sweeps // chunks)
     Gg, ssg, nmg = gw.measure_G()
@@ -39,7 +39,7 @@ def run_pair(nc, t, tp, U, beta, mu, n_tau, k_sub, sweeps, seed=0, warmup=10, in
         log = gw.decision_log(wi)
         ow = ctaux.OracleWalker(nc, c.site_sub, U, beta, K, G0, warmup_sweeps=warmup, n_tau_meas=ntm, seed=seed,
                                 walker_id=wi, init_config_size=init)
-        ow.enable_log(1 << 22)
+        ow.enable_log(1 << 23)
         ow.set_hints(log)
         ow.sweep(sweeps)
         results.append((gw.state(wi), ow.state(), log, ow.log(), Gg[wi], ssg[wi], nmg[wi], ow.G(), st[wi],
@@ -79,6 +79,16 @@ def test_2x2_parity_dense_run():
     st = res[0][8]
     assert st["recomputes"] > 0 and st["max_drift"] < 1e-10
     assert st["aborts"] > 0  # the duplicate-spin rule fired
+
+
+def test_2x2_full_run_parity():
+    # 2x2 cluster workload at full length: one walker, 1e5 sweeps after 20 warm-up
+    # sweeps, k_s = 32, N recomputed every 64 submatrix updates.
+    res = run_pair(4, 1.0, 0.0, 4.0, 10.0, 0.9450480104035819, 4096, k_sub=32, sweeps=100020, seed=0,
+                   warmup=20, ntm=64, R=64)
+    check(res)
+    st = res[0][8]
+    assert st["proposals"] > 3_000_000 and st["max_drift"] < 1e-9
 
 
 @pytest.mark.parametrize("k_sub", [1, 3, 16, 128])

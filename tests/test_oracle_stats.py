@@ -54,7 +54,7 @@ def _atom_run(seed, n_bins=24, per_bin=4000):
         g, ss, nm = w.G()
         cn = w.counters()
         Gb.append(g[:, 0] / ss)
-        kb.append(cn["k_sum"] / cn["k_samples"])
+        kb.append(cn["k_sum"] / ss)
     return U, beta, ntm, np.array(Gb), np.array(kb)
 
 
@@ -92,7 +92,7 @@ def test_2x2_cluster_matches_ed():
         g, ss, nm = w.G()
         cn = w.counters()
         Gb.append(g[:, :, :] / ss)
-        kb.append(cn["k_sum"] / cn["k_samples"])
+        kb.append(cn["k_sum"] / ss)  # signed average
         sb.append(ss / nm)
     Gb = np.array(Gb)
     for sp in range(2):
