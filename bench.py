@@ -319,7 +319,7 @@ def roofline(group, g_ms, windows, flops, ubytes, eflops, ebytes, peaks, kind, w
     sec = g_ms / 1000.0
     if work_b is None or sec <= 0:
         return {"kernel": group, "bound": "alu", "achieved": None, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "note": "latency-bound serial kernel; see DESIGN.md",
+                "frac": None, "traffic": None, "note": "latency-bound kernel group without an algorithmic byte or flop count",
                 "launch_ms": g_ms / max(1, windows)}
     gbs = work_b / sec / 1e9
     tfs = work_f / sec / 1e12

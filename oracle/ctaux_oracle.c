@@ -21,7 +21,7 @@
  *   - the Green's function measured from M = (e^V - 1) N (the equation for
  *     <G> in terms of M in Sec. 2.3), here on a tau grid.
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings taken where the paper is silent:
  *   N_sigma^-1 = e^{V_sigma} - g0_sigma (e^{V_sigma} - 1),  g0 = -G0
  *     (G0 in the paper's sign convention, negative on (0, beta)),
  *     V_p^sigma = sigma * gamma * s_p for an interacting vertex, 0 otherwise;
