@@ -172,6 +172,17 @@ DCA_API int dca_walker_get_decision_log(dca_walker* w, int32_t wi, uint8_t* out,
  * identical trajectory).  n = 0 switches replay off. */
 DCA_API int dca_walker_set_forced_decisions(dca_walker* w, int32_t wi, const uint8_t* log, int64_t n);
 
+/* N_sigma = [e^{V_sigma} - g0_sigma (e^{V_sigma} - 1)]^-1 from scratch for a
+ * given configuration (all n vertices interacting): the periodic recompute of
+ * a walker (Eq. Zk) as a standalone operation.  problem: as in
+ * dca_walker_create; verts: host [n] (site in 0..nc-1, s = +-1, 0 <= tau < beta);
+ * N_up, N_dn: host n x n row-major outputs (either may be NULL); det_sign:
+ * sign of det N_up^-1 det N_dn^-1 (may be NULL).  Runs on the current device
+ * and default stream, allocating device memory for the call and freeing it;
+ * returns DCA_ERR_NUMERIC if a matrix is singular. */
+DCA_API int dca_fresh_N(const dca_problem* problem, int32_t n, const dca_vertex* verts, double* N_up,
+                        double* N_dn, int32_t* det_sign);
+
 /* Replace the bare propagator of problem `problem` (host [2][nc][n_tau+1],
  * same layout and convention as dca_problem.G0), e.g. for the next iteration
  * of an outer DCA loop.  Stream-ordered: sweeps launched afterwards use it. */

@@ -353,6 +353,15 @@ int launch_recompute(const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st
   return 3;
 }
 
+// From-scratch N for the vertex list held in the current buffer of every walker
+// of cfg (used by the standalone fresh-N operations): build A, invert in place.
+void launch_fresh_inverse(const Config& cfg, int max_n, int* d_sgn, cudaStream_t st) {
+  const int W = cfg.n_walkers;
+  if (max_n <= 0) return;
+  k_build_A<<<dim3((max_n + 31) / 32, (max_n + 7) / 8, 2 * W), 256, 0, st>>>(cfg, 0);
+  k_gj_inplace<<<2 * W, 1024, 0, st>>>(cfg, 0, d_sgn);
+}
+
 __global__ void k_negate(const double* src, double* dst, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = -src[i];

@@ -24,6 +24,7 @@ int launch_window_group(int group, const Config& cfg, int max_cap, cudaStream_t 
 void launch_count_active(const Config& cfg, cudaStream_t st);
 void launch_add_target(const Config& cfg, int64_t n_sweeps, cudaStream_t st);
 void launch_init(const Config& cfg, int n0, int max_cap, int* d_sgn, cudaStream_t st);
+void launch_fresh_inverse(const Config& cfg, int max_n, int* d_sgn, cudaStream_t st);
 int launch_recompute(const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st);
 int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
 void launch_negate(const double* src, double* dst, size_t n, cudaStream_t st);

@@ -16,6 +16,7 @@
 
 #include "../../include/dca_walker.h"
 #include "kernels.h"
+#include "problem_host.h"
 #include "state.h"
 
 using dca::ProblemDev;
@@ -135,20 +136,9 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     return fail(nullptr, DCA_ERR_ARG, "negative or zero size parameter");
   if (p.precision != DCA_PREC_FP64) return fail(nullptr, DCA_ERR_ARG, "unsupported precision");
   for (int i = 0; i < p.n_problems; ++i) {
-    const dca_problem& pr = p.problems[i];
-    if (pr.nc < 1 || !pr.site_sub || !pr.G0 || pr.n_tau < 1 || !(pr.beta > 0.0) || !(pr.K > 0.0) || !(pr.U >= 0.0) ||
-        !std::isfinite(pr.U) || !std::isfinite(pr.beta) || !std::isfinite(pr.K))
-      return fail(nullptr, DCA_ERR_ARG, "problem " + std::to_string(i) + ": invalid scalar or NULL array");
-    for (int r = 0; r < pr.nc; ++r) {
-      std::vector<int> seen(pr.nc, 0);
-      for (int c = 0; c < pr.nc; ++c) {
-        const int v = pr.site_sub[r * pr.nc + c];
-        if (v < 0 || v >= pr.nc || seen[v]++) return fail(nullptr, DCA_ERR_ARG, "site_sub row is not a permutation");
-      }
-    }
-    const size_t tsz = (size_t)2 * pr.nc * (pr.n_tau + 1);
-    for (size_t t = 0; t < tsz; ++t)
-      if (!std::isfinite(pr.G0[t])) return fail(nullptr, DCA_ERR_ARG, "G0 has a non-finite entry");
+    std::string why;
+    if (dca::check_problem(p.problems[i], why) != DCA_OK)
+      return fail(nullptr, DCA_ERR_ARG, "problem " + std::to_string(i) + ": " + why);
   }
   if (p.walker_problem)
     for (int w = 0; w < p.n_walkers; ++w)
@@ -176,29 +166,10 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   for (int i = 0; i < p.n_problems; ++i) {
     const dca_problem& pr = p.problems[i];
     ProblemDev& d = hp[i];
-    d.nc = pr.nc;
-    d.n_tau = pr.n_tau;
-    d.beta = pr.beta;
-    d.K = pr.K;
-    // cosh(gamma) = 1 + U beta N_corr / (2K), N_corr = Nc (Sec. 2.3)
-    d.gamma = std::acosh(1.0 + pr.U * pr.beta * (double)pr.nc / (2.0 * pr.K));
-    d.tau_scale = (double)pr.n_tau / pr.beta;
-    for (int sp = 0; sp < 2; ++sp) {
-      const double sigma = sp == 0 ? 1.0 : -1.0;
-      d.expV[sp][0] = std::exp(-sigma * d.gamma);
-      d.expV[sp][1] = std::exp(sigma * d.gamma);
-    }
-    std::vector<int32_t> add(pr.nc * pr.nc, -1);
-    for (int x = 0; x < pr.nc; ++x)
-      for (int y = 0; y < pr.nc; ++y) add[y * pr.nc + pr.site_sub[x * pr.nc + y]] = x;
-    for (int v : add)
-      if (v < 0) {
-        h->err = "site_sub does not define a group difference table";
-        return bail(DCA_ERR_ARG);
-      }
-    const size_t tsz = (size_t)2 * pr.nc * (pr.n_tau + 1);
-    std::vector<double> g0(tsz);
-    for (size_t t = 0; t < tsz; ++t) g0[t] = -pr.G0[t];
+    std::vector<int32_t> add;
+    std::vector<double> g0;
+    dca::prepare_problem(pr, d, add, g0);
+    const size_t tsz = g0.size();
     void* ds = h->dalloc(sizeof(int32_t) * pr.nc * pr.nc);
     void* da = h->dalloc(sizeof(int32_t) * pr.nc * pr.nc);
     void* dg = h->dalloc(sizeof(double) * tsz);
@@ -632,4 +603,113 @@ extern "C" DCA_API void dca_walker_destroy(dca_walker* h) { delete h; }
 extern "C" DCA_API const char* dca_walker_last_error(dca_walker* h) {
   if (!h) return g_create_error.c_str();
   return h->err.c_str();
+}
+
+// ---------------------------------------------------------------------------
+// Standalone from-scratch N (the periodic recompute as its own operation).
+// ---------------------------------------------------------------------------
+int dca_check_vertices(const dca_problem& pr, int32_t n, const dca_vertex* verts, std::string& err) {
+  if (n < 0 || (n > 0 && !verts)) {
+    err = "invalid vertex list";
+    return DCA_ERR_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    const dca_vertex& v = verts[i];
+    if (v.site < 0 || v.site >= pr.nc || (v.s != 1 && v.s != -1) || !(v.tau >= 0.0) || !(v.tau < pr.beta)) {
+      err = "vertex " + std::to_string(i) + " out of range";
+      return DCA_ERR_ARG;
+    }
+  }
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_fresh_N(const dca_problem* problem, int32_t n, const dca_vertex* verts, double* N_up,
+                                   double* N_dn, int32_t* det_sign) {
+  if (!problem) return fail(nullptr, DCA_ERR_ARG, "dca_fresh_N: problem is NULL");
+  std::string why;
+  if (dca::check_problem(*problem, why) != DCA_OK || dca_check_vertices(*problem, n, verts, why) != DCA_OK)
+    return fail(nullptr, DCA_ERR_ARG, "dca_fresh_N: " + why);
+  if (n == 0) {
+    if (det_sign) *det_sign = 1;
+    return DCA_OK;
+  }
+  const dca_problem& pr = *problem;
+  ProblemDev d;
+  std::vector<int32_t> add;
+  std::vector<double> g0;
+  dca::prepare_problem(pr, d, add, g0);
+  const size_t nn = (size_t)n * n, nc2 = (size_t)pr.nc * pr.nc;
+  struct Piece {
+    void** dst;
+    size_t bytes;
+  };
+  int32_t *d_ss, *d_sa, *d_site, *d_s, *d_sgn;
+  double *d_g0, *d_tau, *d_N[2], *d_scr[2];
+  ProblemDev* d_P;
+  WalkerDev* d_W;
+  std::vector<Piece> pieces = {{(void**)&d_ss, sizeof(int32_t) * nc2},   {(void**)&d_sa, sizeof(int32_t) * nc2},
+                               {(void**)&d_g0, sizeof(double) * g0.size()}, {(void**)&d_P, sizeof(ProblemDev)},
+                               {(void**)&d_W, sizeof(WalkerDev)},          {(void**)&d_site, sizeof(int32_t) * n},
+                               {(void**)&d_tau, sizeof(double) * n},       {(void**)&d_s, sizeof(int32_t) * n},
+                               {(void**)&d_N[0], sizeof(double) * nn},     {(void**)&d_N[1], sizeof(double) * nn},
+                               {(void**)&d_scr[0], sizeof(double) * 2 * n}, {(void**)&d_scr[1], sizeof(double) * 2 * n},
+                               {(void**)&d_sgn, sizeof(int32_t) * 2}};
+  size_t total = 0;
+  for (auto& pc : pieces) total += align_up(pc.bytes, 256);
+  char* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, total);
+  if (e != cudaSuccess) return fail(nullptr, DCA_ERR_OOM, std::string("dca_fresh_N: ") + cudaGetErrorString(e));
+  size_t off = 0;
+  for (auto& pc : pieces) {
+    *pc.dst = base + off;
+    off += align_up(pc.bytes, 256);
+  }
+  d.site_sub = d_ss;
+  d.site_add = d_sa;
+  d.g0 = d_g0;
+  WalkerDev w;
+  std::memset(&w, 0, sizeof(w));
+  w.n = n;
+  w.cap = n;
+  w.status = dca::ST_OK;
+  w.sign = 1.0;
+  w.vsite[0] = d_site;
+  w.vtau[0] = d_tau;
+  w.vs[0] = d_s;
+  w.N[0][0] = d_N[0];
+  w.N[0][1] = d_N[1];
+  w.Lrow[0] = d_scr[0];
+  w.Lrow[1] = d_scr[1];
+  std::vector<int32_t> site(n), s(n);
+  std::vector<double> tau(n);
+  for (int i = 0; i < n; ++i) {
+    site[i] = verts[i].site;
+    s[i] = verts[i].s;
+    tau[i] = verts[i].tau;
+  }
+  dca::Config cfg{};
+  cfg.n_walkers = 1;
+  cfg.W = d_W;
+  cfg.P = d_P;
+  int32_t sgn[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(d_ss, pr.site_sub, sizeof(int32_t) * nc2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_sa, add.data(), sizeof(int32_t) * nc2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_g0, g0.data(), sizeof(double) * g0.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_P, &d, sizeof(ProblemDev), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_W, &w, sizeof(WalkerDev), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_site, site.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_tau, tau.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_s, s.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    dca::launch_fresh_inverse(cfg, n, d_sgn, nullptr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(sgn, d_sgn, sizeof(sgn), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && N_up) e = cudaMemcpy(N_up, d_N[0], sizeof(double) * nn, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && N_dn) e = cudaMemcpy(N_dn, d_N[1], sizeof(double) * nn, cudaMemcpyDeviceToHost);
+  cudaFree(base);
+  if (e != cudaSuccess) return fail(nullptr, DCA_ERR_CUDA, std::string("dca_fresh_N: ") + cudaGetErrorString(e));
+  if (sgn[0] == 0 || sgn[1] == 0) return fail(nullptr, DCA_ERR_NUMERIC, "dca_fresh_N: singular matrix");
+  if (det_sign) *det_sign = sgn[0] * sgn[1];
+  return DCA_OK;
 }

@@ -21,7 +21,7 @@ EXPORTS = [
     "dca_walker_reset_measurements", "dca_walker_stats", "dca_walker_get_state",
     "dca_walker_get_decision_log", "dca_walker_set_forced_decisions", "dca_walker_capacity",
     "dca_walker_destroy", "dca_walker_last_error", "dca_walker_update_G0", "dca_walker_set_timing",
-    "dca_walker_get_timing",
+    "dca_walker_get_timing", "dca_fresh_N",
 ]
 GROUPS = ["propose", "extend", "metropolis", "update", "measure", "recompute"]
 
@@ -112,6 +112,7 @@ def load(path=LIB_PATH):
     L.dca_walker_update_G0.argtypes = [P, C.c_int32, P]
     L.dca_walker_set_timing.argtypes = [P, C.c_uint32]
     L.dca_walker_get_timing.argtypes = [P, P, P, C.POINTER(C.c_int64), C.c_int32]
+    L.dca_fresh_N.argtypes = [C.POINTER(Problem), C.c_int32, P, P, P, C.POINTER(C.c_int32)]
     L.dca_walker_destroy.argtypes = [P]
     L.dca_walker_destroy.restype = None
     L.dca_walker_last_error.argtypes = [P]
@@ -142,6 +143,47 @@ def g0_isolated_cluster(eps_K, k_dot_r, mu, U, beta, n_tau):
     if rc != DCA_OK:
         raise WalkerError(rc, L.dca_walker_last_error(None).decode())
     return out
+
+
+def _problem_struct(pr, keep):
+    ss = np.ascontiguousarray(pr["site_sub"], np.int32).reshape(-1)
+    g0 = np.ascontiguousarray(pr["G0"], np.float64)
+    keep += [ss, g0]
+    p = Problem()
+    p.nc = int(pr["nc"])
+    p.site_sub = ss.ctypes.data_as(C.POINTER(C.c_int32))
+    p.U = float(pr["U"])
+    p.beta = float(pr["beta"])
+    p.K = float(pr.get("K", 1.0))
+    p.n_tau = int(g0.shape[-1] - 1)
+    p.G0 = g0.ctypes.data_as(C.POINTER(C.c_double))
+    return p
+
+
+def _vertices(site, tau, s):
+    n = len(site)
+    verts = (Vertex * max(n, 1))()
+    for i in range(n):
+        verts[i].site = int(site[i])
+        verts[i].s = int(s[i])
+        verts[i].tau = float(tau[i])
+    return verts
+
+
+def fresh_N(problem, site, tau, s, fn="dca_fresh_N"):
+    """(N_up, N_dn, det_sign) from scratch for an all-interacting vertex list."""
+    L = load()
+    keep = []
+    pr = _problem_struct(problem, keep)
+    n = len(site)
+    verts = _vertices(site, tau, s)
+    Nu = np.zeros((n, n), np.float64)
+    Nd = np.zeros((n, n), np.float64)
+    sg = C.c_int32(0)
+    rc = getattr(L, fn)(C.byref(pr), n, verts, _ptr(Nu), _ptr(Nd), C.byref(sg))
+    if rc != DCA_OK:
+        raise WalkerError(rc, L.dca_walker_last_error(None).decode())
+    return Nu, Nd, int(sg.value)
 
 
 class Walkers:
