@@ -183,6 +183,28 @@ DCA_API int dca_walker_set_forced_decisions(dca_walker* w, int32_t wi, const uin
 DCA_API int dca_fresh_N(const dca_problem* problem, int32_t n, const dca_vertex* verts, double* N_up,
                         double* N_dn, int32_t* det_sign);
 
+/* Same operation and outputs as dca_fresh_N, for callers that cannot allocate
+ * device memory (code running during CUDA stream capture, where cudaMalloc is
+ * not allowed; processes whose device memory belongs to another allocator;
+ * services with a fixed device footprint).  The paper has no counterpart: it
+ * is a deployment variant of the recompute.  It calls no cudaMalloc, cudaFree
+ * or other allocating routine; all device memory is one fixed file-scope
+ * __device__ array (about 3.2 MB, held by every GPU that loads the library
+ * until exit).  Limits: n <= DCA_NOALLOC_MAX_ORDER, nc <= DCA_NOALLOC_MAX_SITES,
+ * 2 * nc * (n_tau + 1) <= DCA_NOALLOC_MAX_TABLE; larger sizes return
+ * DCA_ERR_ARG with a message in dca_walker_last_error(NULL).  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every
+ * call reuses the same array and leaves its contents behind; calls are
+ * serialised on the host, but GPU work that overlaps a call and touches the
+ * array races with it.  Uses the current device and the legacy default stream
+ * with synchronous copies. */
+#define DCA_NOALLOC_MAX_ORDER 256
+#define DCA_NOALLOC_MAX_SITES 64
+#define DCA_NOALLOC_MAX_TABLE 262144
+DCA_API int dca_fresh_N_noalloc(const dca_problem* problem, int32_t n, const dca_vertex* verts,
+                                double* N_up, double* N_dn, int32_t* det_sign);
+
 /* Replace the bare propagator of problem `problem` (host [2][nc][n_tau+1],
  * same layout and convention as dca_problem.G0), e.g. for the next iteration
  * of an outer DCA loop.  Stream-ordered: sweeps launched afterwards use it. */

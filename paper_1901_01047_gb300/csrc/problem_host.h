@@ -17,4 +17,7 @@ int check_problem(const dca_problem& pr, std::string& err);
 // table site_add[y*nc + d] = x with site_sub[x*nc + y] = d, and g0 = -G0.
 void prepare_problem(const dca_problem& pr, ProblemDev& d, std::vector<int32_t>& add, std::vector<double>& g0);
 
+// Message returned by dca_walker_last_error(NULL) on this thread.
+void set_handleless_error(const std::string& msg);
+
 }  // namespace dca

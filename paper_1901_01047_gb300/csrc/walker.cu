@@ -713,3 +713,7 @@ extern "C" DCA_API int dca_fresh_N(const dca_problem* problem, int32_t n, const 
   if (det_sign) *det_sign = sgn[0] * sgn[1];
   return DCA_OK;
 }
+
+namespace dca {
+void set_handleless_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace dca

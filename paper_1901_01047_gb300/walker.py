@@ -21,7 +21,7 @@ EXPORTS = [
     "dca_walker_reset_measurements", "dca_walker_stats", "dca_walker_get_state",
     "dca_walker_get_decision_log", "dca_walker_set_forced_decisions", "dca_walker_capacity",
     "dca_walker_destroy", "dca_walker_last_error", "dca_walker_update_G0", "dca_walker_set_timing",
-    "dca_walker_get_timing", "dca_fresh_N",
+    "dca_walker_get_timing", "dca_fresh_N", "dca_fresh_N_noalloc",
 ]
 GROUPS = ["propose", "extend", "metropolis", "update", "measure", "recompute"]
 
@@ -113,6 +113,7 @@ def load(path=LIB_PATH):
     L.dca_walker_set_timing.argtypes = [P, C.c_uint32]
     L.dca_walker_get_timing.argtypes = [P, P, P, C.POINTER(C.c_int64), C.c_int32]
     L.dca_fresh_N.argtypes = [C.POINTER(Problem), C.c_int32, P, P, P, C.POINTER(C.c_int32)]
+    L.dca_fresh_N_noalloc.argtypes = [C.POINTER(Problem), C.c_int32, P, P, P, C.POINTER(C.c_int32)]
     L.dca_walker_destroy.argtypes = [P]
     L.dca_walker_destroy.restype = None
     L.dca_walker_last_error.argtypes = [P]
