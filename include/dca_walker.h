@@ -142,7 +142,12 @@ DCA_API int dca_walker_create(const dca_walker_params* params, void* cuda_stream
 /* Run n_sweeps more sweeps on every walker.  A warm-up sweep is max(k, 1)
  * proposals (k at its start); after warm-up the sweep length is frozen to the
  * rounded mean of those k (max(k,1) when warmup_sweeps = 0).  Every sweep at
- * or past warm-up ends with one measurement. */
+ * or past warm-up ends with one measurement.  The submatrix updates run as a
+ * device-side loop (a CUDA graph with a conditional WHILE node, captured on
+ * the first call) until every walker is done, so the host launches one graph
+ * and reads back one status record per call; with kernel timing on
+ * (dca_walker_set_timing) the host drives the same kernels instead.
+ * Returns DCA_ERR_TIMEOUT if the loop hits its iteration bound. */
 DCA_API int dca_walker_sweep(dca_walker* w, int32_t n_sweeps);
 
 /* Copy the accumulated sum over measurements of sign * G(dr, tau_a) (paper

@@ -733,3 +733,44 @@ void launch_add_target(const Config& cfg, int64_t n_sweeps, cudaStream_t st) {
 }
 
 }  // namespace dca
+
+namespace dca {
+
+// Loop control of the device-side window loop (body of a conditional WHILE
+// graph node): continue while any walker still has sweeps to do, and stop
+// with a timeout flag after max_iters windows (every window advances each
+// active walker by at least one proposal, so the host's bound is never
+// reached unless something is wrong).
+__global__ void k_loop_control(Config cfg, cudaGraphConditionalHandle handle, LoopState* ls) {
+  __shared__ int s_cnt;
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < cfg.n_walkers; i += blockDim.x) {
+    const WalkerDev& w = cfg.W[i];
+    if (w.status == ST_OK && w.sweeps_done < w.sweeps_target) atomicAdd(&s_cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ls->iters++;
+    unsigned int cont = s_cnt > 0 ? 1u : 0u;
+    if (cont && ls->iters >= ls->max_iters) {
+      ls->timed_out = 1;
+      cont = 0u;
+    }
+    cudaGraphSetConditional(handle, cont);
+  }
+}
+
+__global__ void k_loop_reset(LoopState* ls, int64_t max_iters) {
+  ls->iters = 0;
+  ls->max_iters = max_iters;
+  ls->timed_out = 0;
+}
+
+void launch_loop_control(const Config& cfg, cudaGraphConditionalHandle handle, LoopState* ls, cudaStream_t st) {
+  k_loop_control<<<1, 256, 0, st>>>(cfg, handle, ls);
+}
+
+void launch_loop_reset(LoopState* ls, int64_t max_iters, cudaStream_t st) { k_loop_reset<<<1, 1, 0, st>>>(ls, max_iters); }
+
+}  // namespace dca

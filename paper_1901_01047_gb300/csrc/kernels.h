@@ -22,6 +22,8 @@ enum Group : int {
 // Each launcher returns the number of kernels it launched.
 int launch_window_group(int group, const Config& cfg, int max_cap, cudaStream_t st);
 void launch_count_active(const Config& cfg, cudaStream_t st);
+void launch_loop_control(const Config& cfg, cudaGraphConditionalHandle handle, LoopState* ls, cudaStream_t st);
+void launch_loop_reset(LoopState* ls, int64_t max_iters, cudaStream_t st);
 void launch_add_target(const Config& cfg, int64_t n_sweeps, cudaStream_t st);
 void launch_init(const Config& cfg, int n0, int max_cap, int* d_sgn, cudaStream_t st);
 void launch_fresh_inverse(const Config& cfg, int max_n, int* d_sgn, cudaStream_t st);

@@ -107,6 +107,14 @@ struct WalkerDev {
   double* bvec;              // [2][nc][cap]
 };
 
+// Iteration state of the device-side window loop.
+struct LoopState {
+  int64_t iters;
+  int64_t max_iters;
+  int32_t timed_out;
+  int32_t pad;
+};
+
 struct Config {
   int32_t n_walkers;
   int32_t ks;                // k_sub

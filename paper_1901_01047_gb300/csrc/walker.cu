@@ -62,9 +62,18 @@ struct dca_walker {
   double group_ms[dca::N_GROUPS] = {0};
   int64_t group_launches[dca::N_GROUPS] = {0};
   int64_t total_launches = 0;
+  // device-side window loop: a graph with a conditional WHILE node
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t loop_graph = nullptr;
+  cudaGraphExec_t loop_exec = nullptr;
+  dca::LoopState* d_loop = nullptr;
+  int kernels_per_window = 0;
 
   ~dca_walker() {
     if (stream) cudaStreamSynchronize(stream);
+    if (loop_exec) cudaGraphExecDestroy(loop_exec);
+    if (loop_graph) cudaGraphDestroy(loop_graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
     for (uint8_t* p : forced)
@@ -391,14 +400,82 @@ static void collect_events(dca_walker* h) {
   h->ev_used = 0;
 }
 
+// Build the device-side window loop once: an outer graph holding one
+// conditional WHILE node whose body (captured from the same launchers the
+// host loop uses) is one window plus the loop-control kernel.
+static int build_loop_graph(dca_walker* h) {
+  if (h->loop_exec) return DCA_OK;
+  if (!h->d_loop) {
+    h->d_loop = (dca::LoopState*)h->dalloc(sizeof(dca::LoopState));
+    if (!h->d_loop) return fail(h, DCA_ERR_OOM, "loop state allocation");
+  }
+  if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  CK(cudaGraphCreate(&h->loop_graph, 0));
+  cudaGraphConditionalHandle handle;
+  CK(cudaGraphConditionalHandleCreate(&handle, h->loop_graph, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = handle;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, h->loop_graph, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  int k = 0;
+  for (int g = dca::GROUP_PROPOSE; g <= dca::GROUP_UPDATE; ++g) k += dca::launch_window_group(g, h->cfg, h->max_cap, h->cap_stream);
+  k += dca::launch_measure(h->cfg, h->max_cap, h->max_nc, h->cap_stream);
+  if (h->R > 0) k += dca::launch_recompute(h->cfg, h->max_cap, h->d_sgn, h->cap_stream);
+  dca::launch_loop_control(h->cfg, handle, h->d_loop, h->cap_stream);
+  k += 1;
+  cudaGraph_t captured = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &captured);
+  if (e != cudaSuccess) return cuda_check(h, e, "capture of the window loop");
+  CK(cudaGraphInstantiate(&h->loop_exec, h->loop_graph, 0));
+  h->kernels_per_window = k;
+  return DCA_OK;
+}
+
+static int sweep_graph(dca_walker* h, int32_t n_sweeps) {
+  int rc = build_loop_graph(h);
+  if (rc != DCA_OK) return rc;
+  // Every window advances each active walker by >= 1 proposal and a sweep is
+  // at most `capacity` proposals, so this bound is never reached normally.
+  const int64_t max_iters = (int64_t)n_sweeps * (int64_t)(h->max_cap + 1) + 64;
+  dca::launch_add_target(h->cfg, n_sweeps, h->stream);
+  dca::launch_loop_reset(h->d_loop, max_iters, h->stream);
+  CK(cudaGetLastError());
+  CK(cudaGraphLaunch(h->loop_exec, h->stream));
+  dca::LoopState ls;
+  CK(cudaMemcpyAsync(&ls, h->d_loop, sizeof(ls), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->windows_launched += ls.iters;
+  h->total_launches += 2 + ls.iters * h->kernels_per_window;
+  if (ls.timed_out) return fail(h, DCA_ERR_TIMEOUT, "window loop reached its iteration bound");
+  return DCA_OK;
+}
+
 extern "C" DCA_API int dca_walker_sweep(dca_walker* h, int32_t n_sweeps) {
   if (!h) return DCA_ERR_ARG;
   if (n_sweeps < 0) return fail(h, DCA_ERR_ARG, "n_sweeps < 0");
   if (n_sweeps == 0) return DCA_OK;
+  if (h->timing_mask == 0) {
+    int rc = sweep_graph(h, n_sweeps);
+    if (rc != DCA_OK) return rc;
+    rc = pull_records(h);
+    if (rc != DCA_OK) return rc;
+    for (int wi = 0; wi < h->W; ++wi)
+      if (h->h_W[wi].status != dca::ST_OK)
+        return fail(h, status_code(h->h_W[wi].status),
+                    "walker " + std::to_string(wi) + " stopped with status " + std::to_string(h->h_W[wi].status));
+    return DCA_OK;
+  }
+  // Timed kernel groups: host-driven loop with CUDA events around each group
+  // (event nodes are not allowed inside conditional graph bodies).
   dca::launch_add_target(h->cfg, n_sweeps, h->stream);
   h->total_launches += 1;
   CK(cudaGetLastError());
-  int chunk = 8;
+  int chunk = 2;
   for (;;) {
     for (int i = 0; i < chunk; ++i) {
       run_group(h, dca::GROUP_PROPOSE);
@@ -416,7 +493,7 @@ extern "C" DCA_API int dca_walker_sweep(dca_walker* h, int32_t n_sweeps) {
     CK(cudaStreamSynchronize(h->stream));
     collect_events(h);
     if (h->h_active[0] == 0) break;
-    if (chunk < 512) chunk *= 2;
+    if (chunk < 64) chunk *= 2;
   }
   int rc = pull_records(h);
   if (rc != DCA_OK) return rc;

@@ -25,11 +25,14 @@ def _walkers(**kw):
 
 
 def run_pair(nc, t, tp, U, beta, mu, n_tau, k_sub, sweeps, seed=0, warmup=10, init=10, ntm=16, R=0,
-             walkers=1, K=1.0, chunks=1):
+             walkers=1, K=1.0, chunks=1, timed=False):
     c, eps, kr, G0 = problem(nc, t, tp, U, beta, mu, n_tau)
     prob = dict(nc=nc, site_sub=c.site_sub, U=U, beta=beta, K=K, G0=G0)
     gw = _walkers(problems=[prob], n_walkers=walkers, k_sub=k_sub, recompute_every=R, warmup_sweeps=warmup,
                   n_tau_meas=ntm, init_config_size=init, seed=seed, log_capacity=1 << 23)
+    if timed:  # host-driven window loop with CUDA events instead of the graph loop
+        from paper_1901_01047_gb300 import walker
+        gw.set_timing(walker.GROUPS)
     for _ in range(chunks):
         gw.sweep(sweeps // chunks)
     Gg, ssg, nmg = gw.measure_G()
@@ -94,6 +97,12 @@ def test_2x2_full_run_parity():
 @pytest.mark.parametrize("k_sub", [1, 3, 16, 128])
 def test_window_sizes_reach_the_same_chain(k_sub):
     res = run_pair(4, 1.0, 0.0, 4.0, 5.0, 1.2, 1024, k_sub=k_sub, sweeps=120, seed=3, warmup=5, ntm=8)
+    check(res)
+
+
+def test_host_driven_timed_loop_reaches_the_same_chain():
+    res = run_pair(4, 1.0, 0.0, 4.0, 6.0, 1.1, 1024, k_sub=16, sweeps=150, seed=8, warmup=5, ntm=8, R=8,
+                   walkers=3, chunks=3, timed=True)
     check(res)
 
 
