@@ -295,7 +295,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         peaks, kind = _peaks()
         g_ms, g_launch = gtimes[dominant]
-        windows = max(1, g_launch // max(1, {"propose": 1, "extend": 3, "metropolis": 1, "update": 4,
+        windows = max(1, g_launch // max(1, {"propose": 1, "extend": 3, "metropolis": 1, "update": 7,
                                              "measure": 4, "recompute": 3}[dominant]))
         roof = roofline(dominant, g_ms, windows, kflops, ubytes, eflops, ebytes, peaks, kind, wl)
         out = {

@@ -57,6 +57,10 @@ extern "C" {
 
 /* Arithmetic of the N matrices and their updates. */
 #define DCA_PREC_FP64 0       /* N stored and updated in FP64 */
+#define DCA_PREC_MIXED 1      /* N stored in FP32, candidate-extension and N-update products in
+                                 FP32 / TF32 arithmetic; ratios, Gamma (B^-1), the update factors
+                                 and the recompute in FP64.  Rounding is amplified by the
+                                 conditioning of N^-1: expect ~1e-6..1e-5 relative error in G */
 
 /* One physical problem (a cluster with its bare propagator). */
 typedef struct {

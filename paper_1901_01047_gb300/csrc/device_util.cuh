@@ -83,6 +83,16 @@ __device__ __forceinline__ double g0_diag(const ProblemDev& p, int sp, int r) {
   return __ldg(p.g0 + ((size_t)sp * p.nc + d) * (size_t)(p.n_tau + 1));
 }
 
-__device__ __forceinline__ double expV(const ProblemDev& p, int sp, int s) { return p.expV[sp][s > 0 ? 1 : 0]; }
+// e^{V} of a vertex with stored auxiliary spin s: s = 0 marks a dead
+// (non-interacting) vertex, V = 0.
+__device__ __forceinline__ double expV(const ProblemDev& p, int sp, int s) {
+  return s == 0 ? 1.0 : p.expV[sp][s > 0 ? 1 : 0];
+}
+
+// Storage of N: FP64 or FP32 (mixed precision); arithmetic around it is FP64.
+__device__ __forceinline__ double ldN(const double* p, size_t i) { return p[i]; }
+__device__ __forceinline__ double ldN(const float* p, size_t i) { return (double)p[i]; }
+__device__ __forceinline__ void stN(double* p, size_t i, double v) { p[i] = v; }
+__device__ __forceinline__ void stN(float* p, size_t i, double v) { p[i] = (float)v; }
 
 }  // namespace dca

@@ -21,17 +21,28 @@ __global__ void k_init_vertices(Config cfg, int n0) {
     w.vsite[0][i] = (int)scaled_index(r.v[1], (uint32_t)pb.nc);
     w.vtau[0][i] = pb.beta * uniform53(r.v[2], r.v[3]);
   }
+  for (int i = threadIdx.x; i < n0; i += blockDim.x) w.live_idx[i] = i;
   if (threadIdx.x == 0) {
     w.n = n0;
+    w.n_live = n0;
+    w.n_dead = 0;
+    w.compact_pending = 0;
     w.parity = 0;
   }
 }
 
-// A = e^V - g0 (e^V - 1) for the current vertex list, written to N[dst][sp].
+// A = e^V - g0 (e^V - 1) for the current vertex list (all live: the
+// recompute runs right after a compaction), in FP64.  The FP64 work matrix
+// is N[dst][sp] itself for FP64 storage and Ascr[sp] for FP32 storage.
 // mode 0: dst = current parity (initial build); mode 1: dst = other parity
 // (periodic recompute, only walkers with recompute_pending).
 __device__ __forceinline__ bool wants_build(const WalkerDev& w, int mode) {
   return mode == 0 ? true : (w.active && w.recompute_pending && w.status == ST_OK);
+}
+
+__device__ __forceinline__ double* work_matrix(const Config& cfg, const WalkerDev& w, int mode, int sp) {
+  if (cfg.prec == PREC_MIXED) return w.Ascr[sp];
+  return (double*)w.N[mode == 0 ? w.parity : w.parity ^ 1][sp];
 }
 
 __global__ void __launch_bounds__(256) k_build_A(Config cfg, int mode) {
@@ -43,7 +54,7 @@ __global__ void __launch_bounds__(256) k_build_A(Config cfg, int mode) {
   const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (i >= n || j >= n) return;
   const ProblemDev& pb = cfg.P[w.problem];
-  double* A = w.N[mode == 0 ? par : par ^ 1][sp];
+  double* A = work_matrix(cfg, w, mode, sp);
   const int* vsite = w.vsite[par];
   const double* vtau = w.vtau[par];
   const int* vs = w.vs[par];
@@ -63,7 +74,7 @@ __global__ void __launch_bounds__(1024) k_gj_inplace(Config cfg, int mode, int* 
   WalkerDev& w = cfg.W[wi];
   if (!wants_build(w, mode)) return;
   const int n = w.n, ld = w.cap;
-  double* A = w.N[mode == 0 ? w.parity : w.parity ^ 1][sp];
+  double* A = work_matrix(cfg, w, mode, sp);
   // scratch: column copy (n doubles) and pivot rows (n ints, stored as doubles)
   double* colc = w.Lrow[sp];
   double* pivs = w.Lrow[sp] + ld;
@@ -180,19 +191,35 @@ __global__ void k_init_finish(Config cfg, const int* sgn) {
   w.sign = s < 0 ? -1.0 : 1.0;
 }
 
+// FP32 storage: round the FP64 inverse into the destination buffer.
+// grid = (blocks, walkers*2)
+__global__ void __launch_bounds__(256) k_store_fp32(Config cfg, int mode) {
+  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
+  const WalkerDev& w = cfg.W[wi];
+  if (!wants_build(w, mode) || w.status != ST_OK) return;
+  const int n = w.n, ld = w.cap;
+  const double* A = w.Ascr[sp];
+  float* N = (float*)w.N[mode == 0 ? w.parity : w.parity ^ 1][sp];
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    N[(size_t)i * ld + j] = (float)A[(size_t)i * ld + j];
+  }
+}
+
 // Drift of the updated N against the fresh inverse, then adopt the fresh one.
 // grid = walkers, block 256.
+template <typename T>
 __global__ void __launch_bounds__(256) k_recompute_finish(Config cfg, const int* sgn) {
   WalkerDev& w = cfg.W[blockIdx.x];
   if (!(w.active && w.recompute_pending && w.status == ST_OK)) return;
   const int n = w.n, ld = w.cap, par = w.parity;
   double dmax = 0.0, nmax = 0.0;
   for (int sp = 0; sp < 2; ++sp) {
-    const double* Nold = w.N[par][sp];
-    const double* Nnew = w.N[par ^ 1][sp];
+    const T* Nold = (const T*)w.N[par][sp];
+    const T* Nnew = (const T*)w.N[par ^ 1][sp];
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
       const int i = idx / n, j = idx - i * n;
-      const double a = Nold[(size_t)i * ld + j], b = Nnew[(size_t)i * ld + j];
+      const double a = ldN(Nold, (size_t)i * ld + j), b = ldN(Nnew, (size_t)i * ld + j);
       dmax = fmax(dmax, fabs(a - b));
       nmax = fmax(nmax, fabs(b));
     }
@@ -245,25 +272,27 @@ __global__ void __launch_bounds__(256) k_meas_gr(Config cfg) {
   const int total = nc * n;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
     const int rp = idx / n, j = idx - rp * n;
-    w.gR[((size_t)sp * nc + rp) * w.cap + j] = g0_pair(pb, sp, w.vsite[par][j], w.vtau[par][j], rp, 0.0);
+    const bool live = w.vs[par][j] != 0;  // a dead column of N is e_j: no contribution
+    w.gR[((size_t)sp * nc + rp) * w.cap + j] = live ? g0_pair(pb, sp, w.vsite[par][j], w.vtau[par][j], rp, 0.0) : 0.0;
   }
 }
 
 // bvec[sp][r'][i] = (e^{V_i} - 1) sum_j N[i][j] gR[sp][r'][j]; one warp per (i, r').
+template <typename T>
 __global__ void __launch_bounds__(256) k_meas_b(Config cfg) {
   const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
   const WalkerDev& w = cfg.W[wi];
   if (!wants_measure(w)) return;
   const ProblemDev& pb = cfg.P[w.problem];
   const int n = w.n, par = w.parity, nc = pb.nc, ld = w.cap;
-  const double* N = w.N[par][sp];
+  const T* N = (const T*)w.N[par][sp];
   const int lane = threadIdx.x & 31;
   const int total = nc * n;
   for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < total; item += (gridDim.x * blockDim.x) >> 5) {
     const int rp = item / n, i = item - rp * n;
     const double* g = w.gR + ((size_t)sp * nc + rp) * ld;
     double acc = 0.0;
-    for (int j = lane; j < n; j += 32) acc += N[(size_t)i * ld + j] * g[j];
+    for (int j = lane; j < n; j += 32) acc += ldN(N, (size_t)i * ld + j) * g[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) w.bvec[((size_t)sp * nc + rp) * ld + i] = (expV(pb, sp, w.vs[par][i]) - 1.0) * acc;
@@ -303,7 +332,7 @@ __global__ void k_meas_finish(Config cfg) {
   if (!wants_measure(w)) return;
   w.sign_sum += w.sign;
   w.n_meas++;
-  w.k_sum += w.sign * (double)w.n;
+  w.k_sum += w.sign * (double)w.n_live;
   w.measure_pending = 0;
 }
 
@@ -340,6 +369,10 @@ void launch_init(const Config& cfg, int n0, int max_cap, int* d_sgn, cudaStream_
   if (n0 > 0) {
     k_build_A<<<dim3((n0 + 31) / 32, (n0 + 7) / 8, 2 * W), 256, 0, st>>>(cfg, 0);
     k_gj_inplace<<<2 * W, 1024, 0, st>>>(cfg, 0, d_sgn);
+    if (cfg.prec == PREC_MIXED) {
+      const int gb = (n0 * n0 + 255) / 256;
+      k_store_fp32<<<dim3(gb < 1024 ? gb : 1024, 2 * W), 256, 0, st>>>(cfg, 0);
+    }
   }
   k_init_finish<<<(W + 127) / 128, 128, 0, st>>>(cfg, d_sgn);
   (void)max_cap;
@@ -349,7 +382,13 @@ int launch_recompute(const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st
   const int W = cfg.n_walkers;
   k_build_A<<<dim3((max_cap + 31) / 32, (max_cap + 7) / 8, 2 * W), 256, 0, st>>>(cfg, 1);
   k_gj_inplace<<<2 * W, 1024, 0, st>>>(cfg, 1, d_sgn);
-  k_recompute_finish<<<W, 256, 0, st>>>(cfg, d_sgn);
+  if (cfg.prec == PREC_MIXED) {
+    const int gb = (max_cap * max_cap + 255) / 256;
+    k_store_fp32<<<dim3(gb < 1024 ? gb : 1024, 2 * W), 256, 0, st>>>(cfg, 1);
+    k_recompute_finish<float><<<W, 256, 0, st>>>(cfg, d_sgn);
+    return 4;
+  }
+  k_recompute_finish<double><<<W, 256, 0, st>>>(cfg, d_sgn);
   return 3;
 }
 
@@ -379,7 +418,8 @@ int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) 
   k_meas_gr<<<dim3(gb, 2 * W), 256, 0, st>>>(cfg);
   int gw = (items * 32 + 255) / 256;
   gw = gw < 2048 ? gw : 2048;
-  k_meas_b<<<dim3(gw, 2 * W), 256, 0, st>>>(cfg);
+  if (cfg.prec == PREC_MIXED) k_meas_b<float><<<dim3(gw, 2 * W), 256, 0, st>>>(cfg);
+  else k_meas_b<double><<<dim3(gw, 2 * W), 256, 0, st>>>(cfg);
   const int outs = 2 * max_nc * cfg.n_tau_meas;
   int ga = (outs + 255) / 256;
   ga = ga < 1024 ? ga : 1024;

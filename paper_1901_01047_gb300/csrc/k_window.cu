@@ -1,16 +1,22 @@
-// k_window.cu -- one submatrix update ("window") of every walker, FP64.
+// k_window.cu -- one submatrix update ("window") of every walker.
 //
 // Sequence per window (DCA++ paper Sec. 2.3, "Submatrix updates"):
 //   k_begin       proposals of the window from Philox (counter tag 0 / 1);
-//                 insertion candidates appended as non-interacting rows
+//                 insertion candidates appended as non-interacting rows n + c
 //   k_cand_g      G_ext[i, n+c] = sum_j N[i,j] g0(r_j - r_c, tau_j - tau_c)
 //   k_cand_x      X[c, j]     = sum_i g0(r_c - r_i, tau_c - tau_i) (e^{V_i} - 1) N[i,j]
 //   k_cand_cc     G_ext[n+c', n+c] = X[c',:] . g0[:, c] + g0(c', c)
 //   k_metropolis  serial single-spin decisions from B_P^-1 (bordered growth)
-//   k_upd_*       N <- N + (G[:,P] - E_P) diag(a_P) B^-1 N[P,:] on the
-//                 surviving rows / columns, written compacted to the other
-//                 buffer (compaction of non-interacting spins fused in)
-//   k_window_end  compact the vertex list, swap buffers
+//   k_upd_*       N <- N + (G[:,P] - E_P) diag(a_P) B^-1 N[P,:]: in place on
+//                 rows / columns 0..n-1, plus the rows and columns of the
+//                 accepted insertions appended at n, n+1, ...
+//   k_window_end  removed vertices marked dead, insertions appended to the
+//                 vertex list, live-row index and compaction schedule updated
+//   k_compact_*   (when due) live rows / columns gathered into the other buffer
+// N is stored as T and the dense products (candidate extension, update term)
+// run in arithmetic type A: both double on the FP64 path, both float on the
+// mixed path; ratios, B^-1, the update factors L B^-1 and the recompute are
+// always FP64.
 #include <cstdint>
 #include <cstdio>
 
@@ -30,6 +36,7 @@ __global__ void __launch_bounds__(128) k_begin(Config cfg) {
   if (threadIdx.x == 0) {
     w.n_acc = 0;
     w.n_removed = 0;
+    w.n_ins = 0;
     w.n_eval = 0;
     w.aborted = 0;
     w.n_cand = 0;
@@ -38,13 +45,14 @@ __global__ void __launch_bounds__(128) k_begin(Config cfg) {
     int act = (w.status == ST_OK && w.sweeps_done < w.sweeps_target) ? 1 : 0;
     if (act) {
       if (w.sweep_pos == 0) {
+        const int k = w.n_live;
         if (w.sweeps_done < cfg.warmup) {
-          w.sweep_len_cur = w.n > 1 ? w.n : 1;
-          w.warm_k_sum += w.n;
+          w.sweep_len_cur = k > 1 ? k : 1;
+          w.warm_k_sum += k;
         } else {
           if (w.sweep_len == 0) {
             const int64_t L = cfg.warmup > 0 ? (2 * w.warm_k_sum + cfg.warmup) / (2 * (int64_t)cfg.warmup)
-                                             : (int64_t)w.n;
+                                             : (int64_t)k;
             w.sweep_len = L > 1 ? L : 1;
           }
           w.sweep_len_cur = w.sweep_len;
@@ -108,11 +116,14 @@ __global__ void __launch_bounds__(128) k_begin(Config cfg) {
 }
 
 // ---------------------------------------------------------------------------
-// Candidate extension GEMMs (FP64, 32x32 tiles, 256 threads).
-// grid = (row tiles, candidate tiles, walkers * 2 spins)
+// Candidate extension GEMMs (SIMT, 32x32 tiles, 256 threads, FP64 accumulate).
+// grid = (row tiles, candidate tiles, walkers * 2 spins).  Dead rows and
+// columns contribute nothing (a dead vertex has e^V - 1 = 0 and a unit
+// column of N), so they are skipped.
 // ---------------------------------------------------------------------------
 constexpr int TT = 32;
 
+template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_cand_g(Config cfg) {
   const int wi = blockIdx.z >> 1, sp = blockIdx.z & 1;
   const WalkerDev& w = cfg.W[wi];
@@ -122,30 +133,28 @@ __global__ void __launch_bounds__(256) k_cand_g(Config cfg) {
   if (i0 >= n || c0 >= nc_) return;
   const ProblemDev& pb = cfg.P[w.problem];
   const int ld = w.cap, par = w.parity;
-  const double* __restrict__ N = w.N[par][sp];
+  const T* __restrict__ N = (const T*)w.N[par][sp];
   const int* vsite = w.vsite[par];
   const double* vtau = w.vtau[par];
-  __shared__ double As[TT][TT + 1];
-  __shared__ double Bs[TT][TT + 1];
+  const int* vs = w.vs[par];
+  __shared__ A As[TT][TT + 1];
+  __shared__ A Bs[TT][TT + 1];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  double acc[4] = {0, 0, 0, 0};
+  A acc[4] = {0, 0, 0, 0};
   for (int k0 = 0; k0 < n; k0 += TT) {
     for (int r = ty; r < TT; r += 8) {
       const int i = i0 + r, k = k0 + tx;
-      As[r][tx] = (i < n && k < n) ? N[(size_t)i * ld + k] : 0.0;
+      As[r][tx] = (A)((i < n && k < n) ? ldN(N, (size_t)i * ld + k) : 0.0);
       // B[k, c] = g0(r_k - r_c, tau_k - tau_c)
       const int kk = k0 + r, c = c0 + tx;
       double b = 0.0;
-      if (kk < n && c < nc_) {
-        const int rc = vsite[n + c];
-        b = g0_pair(pb, sp, vsite[kk], vtau[kk], rc, vtau[n + c]);
-      }
-      Bs[r][tx] = b;
+      if (kk < n && c < nc_ && vs[kk] != 0) b = g0_pair(pb, sp, vsite[kk], vtau[kk], vsite[n + c], vtau[n + c]);
+      Bs[r][tx] = (A)b;
     }
     __syncthreads();
 #pragma unroll 8
     for (int k = 0; k < TT; ++k) {
-      const double b = Bs[k][tx];
+      const A b = Bs[k][tx];
 #pragma unroll
       for (int m = 0; m < 4; ++m) acc[m] += As[ty + 8 * m][k] * b;
     }
@@ -161,6 +170,7 @@ __global__ void __launch_bounds__(256) k_cand_g(Config cfg) {
   }
 }
 
+template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_cand_x(Config cfg) {
   const int wi = blockIdx.z >> 1, sp = blockIdx.z & 1;
   const WalkerDev& w = cfg.W[wi];
@@ -170,29 +180,29 @@ __global__ void __launch_bounds__(256) k_cand_x(Config cfg) {
   if (j0 >= n || c0 >= nc_) return;
   const ProblemDev& pb = cfg.P[w.problem];
   const int ld = w.cap, par = w.parity;
-  const double* __restrict__ N = w.N[par][sp];
+  const T* __restrict__ N = (const T*)w.N[par][sp];
   const int* vsite = w.vsite[par];
   const double* vtau = w.vtau[par];
   const int* vs = w.vs[par];
-  __shared__ double Us[TT][TT + 1];   // [c][k]
-  __shared__ double Bs[TT][TT + 1];   // [k][j]
+  __shared__ A Us[TT][TT + 1];   // [c][k]
+  __shared__ A Bs[TT][TT + 1];   // [k][j]
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  double acc[4] = {0, 0, 0, 0};
+  A acc[4] = {0, 0, 0, 0};
   for (int k0 = 0; k0 < n; k0 += TT) {
     for (int r = ty; r < TT; r += 8) {
       // U[c, k] = g0(r_c - r_k, tau_c - tau_k) (e^{V_k} - 1)
       const int c = c0 + r, k = k0 + tx;
       double u = 0.0;
-      if (c < nc_ && k < n)
+      if (c < nc_ && k < n && vs[k] != 0)
         u = g0_pair(pb, sp, vsite[n + c], vtau[n + c], vsite[k], vtau[k]) * (expV(pb, sp, vs[k]) - 1.0);
-      Us[r][tx] = u;
+      Us[r][tx] = (A)u;
       const int kk = k0 + r, jj = j0 + tx;
-      Bs[r][tx] = (kk < n && jj < n) ? N[(size_t)kk * ld + jj] : 0.0;
+      Bs[r][tx] = (A)((kk < n && jj < n) ? ldN(N, (size_t)kk * ld + jj) : 0.0);
     }
     __syncthreads();
 #pragma unroll 8
     for (int k = 0; k < TT; ++k) {
-      const double b = Bs[k][tx];
+      const A b = Bs[k][tx];
 #pragma unroll
       for (int m = 0; m < 4; ++m) acc[m] += Us[ty + 8 * m][k] * b;
     }
@@ -200,10 +210,12 @@ __global__ void __launch_bounds__(256) k_cand_x(Config cfg) {
   }
   const int jj = j0 + tx;
   if (jj < n) {
+    // a dead column j of N is e_j, so X[c, j] = U[c, j] = 0 there
+    const bool dead = vs[jj] == 0;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       const int c = c0 + ty + 8 * m;
-      if (c < nc_) w.Xr[sp][(size_t)c * ld + jj] = acc[m];
+      if (c < nc_) w.Xr[sp][(size_t)c * ld + jj] = dead ? 0.0 : (double)acc[m];
     }
   }
 }
@@ -221,6 +233,7 @@ __global__ void __launch_bounds__(128) k_cand_cc(Config cfg) {
   const int ld = w.cap, par = w.parity;
   const int* vsite = w.vsite[par];
   const double* vtau = w.vtau[par];
+  const int* vs = w.vs[par];
   const int rc = vsite[n + c];
   const double tc = vtau[n + c];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -232,7 +245,7 @@ __global__ void __launch_bounds__(128) k_cand_cc(Config cfg) {
     __syncthreads();
     for (int t = threadIdx.x; t < 1024; t += 128) {
       const int j = j0 + t;
-      v[t] = j < n ? g0_pair(pb, sp, vsite[j], vtau[j], rc, tc) : 0.0;
+      v[t] = (j < n && vs[j] != 0) ? g0_pair(pb, sp, vsite[j], vtau[j], rc, tc) : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -262,23 +275,38 @@ __global__ void __launch_bounds__(128) k_cand_cc(Config cfg) {
 // ---------------------------------------------------------------------------
 // Metropolis over the window (one block per walker, both spins).
 // ---------------------------------------------------------------------------
+template <typename T>
 struct ExtView {
-  const double* N;   // current N (ld)
+  const T* N;        // current N (ld)
   const double* X;   // candidate rows [c][ld]
   const double* Gc;  // candidate columns [c][ld]
   const int* vs;
   int n, ld;
 };
 
-// G_ext[x, y]; y interacting existing vertex uses G = (N e^{V} - I) / (e^{V} - 1)
+template <typename T>
+__device__ __forceinline__ ExtView<T> make_view(const WalkerDev& w, int sp) {
+  ExtView<T> v;
+  v.N = (const T*)w.N[w.parity][sp];
+  v.X = w.Xr[sp];
+  v.Gc = w.Gc[sp];
+  v.vs = w.vs[w.parity];
+  v.n = w.n;
+  v.ld = w.cap;
+  return v;
+}
+
+// G_ext[x, y]; for an interacting existing column y, G = (N e^{V} - I) / (e^{V} - 1)
 // column-wise, which follows from N = [I + G (e^V - I)] e^{-V}.
-__device__ __forceinline__ double g_ext(const ExtView& v, const ProblemDev& pb, int sp, int x, int y) {
+template <typename T>
+__device__ __forceinline__ double g_ext(const ExtView<T>& v, const ProblemDev& pb, int sp, int x, int y) {
   if (y >= v.n) return v.Gc[(size_t)(y - v.n) * v.ld + x];
-  const double nxy = (x < v.n) ? v.N[(size_t)x * v.ld + y] : v.X[(size_t)(x - v.n) * v.ld + y];
+  const double nxy = (x < v.n) ? ldN(v.N, (size_t)x * v.ld + y) : v.X[(size_t)(x - v.n) * v.ld + y];
   const double ev = expV(pb, sp, v.vs[y]);
   return (nxy * ev - (x == y ? 1.0 : 0.0)) / (ev - 1.0);
 }
 
+template <typename T>
 __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
   WalkerDev& w = cfg.W[blockIdx.x];
   __shared__ int s_active;
@@ -287,24 +315,17 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
   if (!s_active) return;
   const ProblemDev& pb = cfg.P[w.problem];
   const int tid = threadIdx.x;
-  const int n = w.n, ld = w.cap, par = w.parity, len = w.win_len;
-  ExtView ev[2];
-  for (int sp = 0; sp < 2; ++sp) {
-    ev[sp].N = w.N[par][sp];
-    ev[sp].X = w.Xr[sp];
-    ev[sp].Gc = w.Gc[sp];
-    ev[sp].vs = w.vs[par];
-    ev[sp].n = n;
-    ev[sp].ld = ld;
-  }
+  const int n = w.n, n_live = w.n_live, len = w.win_len;
+  ExtView<T> ev[2] = {make_view<T>(w, 0), make_view<T>(w, 1)};
   double* Binv[2] = {w.Binv[0], w.Binv[1]};
+  const int* live_idx = w.live_idx;
 
   __shared__ double s_brow[2][KS_MAX], s_bcol[2][KS_MAX], s_t[2][KS_MAX], s_s[2][KS_MAX];
   __shared__ double s_aP[2][KS_MAX];
   __shared__ int s_P[KS_MAX];
-  __shared__ int s_removed[KS_MAX];
+  __shared__ int s_removed[KS_MAX];   // live ranks removed in this window, ascending
   __shared__ double s_anew[2], s_Btt[2], s_d[2];
-  __shared__ int s_target, s_kind, s_stop, s_accept, s_l, s_nrem, s_nins, s_kcur, s_eval;
+  __shared__ int s_target, s_kind, s_stop, s_accept, s_l, s_nrem, s_nins, s_kcur, s_eval, s_rank;
   __shared__ double s_sign;
 
   if (tid == 0) {
@@ -321,34 +342,34 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
     // 1. target of proposal j
     if (tid == 0) {
       const Proposal pr = w.prop[j];
-      const int kcur = n - s_nrem + s_nins;
-      int kind = 0, target = -1;
+      const int kcur = n_live - s_nrem + s_nins;
+      int kind = 0, target = -1, rank = -1;
       if (pr.type == 0) {
         kind = 0;
         target = n + pr.slot;
-        const int s = pr.s;
-        for (int sp = 0; sp < 2; ++sp) s_anew[sp] = expV(pb, sp, s) - 1.0;
+        for (int sp = 0; sp < 2; ++sp) s_anew[sp] = expV(pb, sp, pr.s) - 1.0;
       } else if (kcur == 0) {
         kind = 2;
       } else {
         const int idx = (int)scaled_index(pr.word, (uint32_t)kcur);
-        const int nexist = n - s_nrem;
-        if (idx >= nexist) {
+        if (idx >= n_live - s_nrem) {
           s_stop = 1;  // picks a spin inserted in this window: end the window here
         } else {
-          int x = idx;
+          // idx-th live vertex not yet removed in this window
+          rank = idx;
           for (int r = 0; r < s_nrem; ++r) {
-            if (s_removed[r] <= x) ++x;
+            if (s_removed[r] <= rank) ++rank;
             else break;
           }
           kind = 1;
-          target = x;
-          const int s = ev[0].vs[x];
+          target = live_idx[rank];
+          const int s = ev[0].vs[target];
           for (int sp = 0; sp < 2; ++sp) s_anew[sp] = expV(pb, sp, -s) - 1.0;
         }
       }
       s_kind = kind;
       s_target = target;
+      s_rank = rank;
       s_kcur = kcur;
     }
     __syncthreads();
@@ -373,12 +394,10 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
         const int p = rem >> 1;
         const int P = s_P[p];
         if (rem & 1) {
-          // column: B[P_p, t] = -G[P_p, t] a_t
-          const double a = s_anew[sp];
+          const double a = s_anew[sp];  // column: B[P_p, t] = -G[P_p, t] a_t
           s_bcol[sp][p] = (a == 0.0) ? 0.0 : -g_ext(ev[sp], pb, sp, P, t) * a;
         } else {
-          // row: B[t, P_p] = -G[t, P_p] a_{P_p}
-          const double a = s_aP[sp][p];
+          const double a = s_aP[sp][p];  // row: B[t, P_p] = -G[t, P_p] a_{P_p}
           s_brow[sp][p] = (a == 0.0) ? 0.0 : -g_ext(ev[sp], pb, sp, t, P) * a;
         }
       } else {
@@ -446,8 +465,7 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
       }
     }
     __syncthreads();
-    // 7. bordered inverse:
-    //    [[Binv + t s / d, -t / d], [-s / d, 1 / d]]
+    // 7. bordered inverse: [[Binv + t s / d, -t / d], [-s / d, 1 / d]]
     for (int sp = 0; sp < 2; ++sp) {
       const double rd = 1.0 / s_d[sp];
       for (int idx = tid; idx < (l + 1) * (l + 1); idx += blockDim.x) {
@@ -465,13 +483,12 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
       s_aP[0][l] = s_anew[0];
       s_aP[1][l] = s_anew[1];
       if (s_kind == 1) {
-        // keep the removed list ascending
-        int r = s_nrem;
-        while (r > 0 && s_removed[r - 1] > t) {
+        int r = s_nrem;  // keep the removed ranks ascending
+        while (r > 0 && s_removed[r - 1] > s_rank) {
           s_removed[r] = s_removed[r - 1];
           --r;
         }
-        s_removed[r] = t;
+        s_removed[r] = s_rank;
         s_nrem++;
       } else {
         s_nins++;
@@ -482,31 +499,26 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
   }
   __syncthreads();
 
-  // Epilogue: window bookkeeping, accepted set, survivor map.
+  // Epilogue: window bookkeeping and the accepted set.
   const int l = s_l, nrem = s_nrem, nins = s_nins;
-  const int n_s = n - nrem + nins;
   for (int p = tid; p < l; p += blockDim.x) {
     w.P[p] = s_P[p];
     w.aP[0][p] = s_aP[0][p];
     w.aP[1][p] = s_aP[1][p];
   }
   for (int r = tid; r < nrem; r += blockDim.x) w.removed[r] = s_removed[r];
-  for (int i = tid; i < n; i += blockDim.x) {
-    int below = 0, gone = 0;
-    for (int r = 0; r < nrem; ++r) {
-      below += (s_removed[r] < i);
-      gone |= (s_removed[r] == i);
-    }
-    if (!gone) w.surv[i - below] = i;
-  }
   if (tid == 0) {
-    int m = n - nrem;
+    int m = 0;
     for (int p = 0; p < l; ++p)
-      if (s_P[p] >= n) w.surv[m++] = s_P[p];
+      if (s_P[p] >= n) {
+        w.acc_slot[m] = s_P[p] - n;
+        w.acc_p[m] = p;
+        ++m;
+      }
     const int eval = s_eval;
     w.n_acc = l;
     w.n_removed = nrem;
-    w.n_surv = n_s;
+    w.n_ins = nins;
     w.n_eval = eval;
     w.aborted = (eval < len) && w.status == ST_OK;
     w.sign = s_sign;
@@ -525,19 +537,19 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
         w.recompute_pending = 1;
         w.windows_since_recompute = 0;
       }
-      const double ns = (double)n_s, ll = (double)l;
-      // N update per spin: 2 n_s^2 l + 2 n_s l^2 flop; reads and writes n_s^2
-      // entries plus the n_s x l factors (8-byte words).
+      // Algorithmic work per spin on the k live vertices after the window:
+      // update 2 k^2 l + 2 k l^2 flop, reading and writing k^2 entries of N
+      // plus the k x l factors; extension 4 k0^2 c flop reading N twice.
+      const double b = cfg.prec == PREC_MIXED ? 4.0 : 8.0;
+      const double kk = (double)(n_live - nrem + nins), ll = (double)l;
       if (l > 0) {
-        w.flops += 2.0 * (2.0 * ns * ns * ll + 2.0 * ns * ll * ll);
-        w.upd_bytes += 2.0 * 8.0 * (2.0 * ns * ns + 2.0 * ns * ll);
+        w.flops += 2.0 * (2.0 * kk * kk * ll + 2.0 * kk * ll * ll);
+        w.upd_bytes += 2.0 * (b * 2.0 * kk * kk + 8.0 * 2.0 * kk * ll);
       }
-      // candidate extension per spin: G columns (n x n x c) and X rows
-      // (c x n x n), each reading N once.
-      const double nn = (double)n, cc = (double)w.n_cand;
+      const double k0 = (double)n_live, cc = (double)w.n_cand;
       if (w.n_cand > 0) {
-        w.ext_flops += 2.0 * (4.0 * nn * nn * cc);
-        w.ext_bytes += 2.0 * 8.0 * (2.0 * nn * nn);
+        w.ext_flops += 2.0 * (4.0 * k0 * k0 * cc);
+        w.ext_bytes += 2.0 * b * (2.0 * k0 * k0);
       }
     } else {
       w.active = 0;
@@ -547,132 +559,222 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
 }
 
 // ---------------------------------------------------------------------------
-// N update on the surviving rows / columns.
+// N update.  Rows of L = (G[:,P] - E_P) diag(a_P) and of L Binv are kept at
+// the extended row index: existing rows 0..n-1, candidate c at n + c.  R is
+// N_ext[P, 0:n).  Dead rows get L = 0 (they never matter).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double n_ext(const ExtView& v, int x, int y) {
-  if (x < v.n) return (y < v.n) ? v.N[(size_t)x * v.ld + y] : 0.0;
-  if (y < v.n) return v.X[(size_t)(x - v.n) * v.ld + y];
-  return x == y ? 1.0 : 0.0;
-}
+__device__ __forceinline__ bool upd_active(const WalkerDev& w) { return w.active && w.n_acc > 0; }
 
-__device__ __forceinline__ ExtView make_view(const WalkerDev& w, int sp) {
-  ExtView v;
-  v.N = w.N[w.parity][sp];
-  v.X = w.Xr[sp];
-  v.Gc = w.Gc[sp];
-  v.vs = w.vs[w.parity];
-  v.n = w.n;
-  v.ld = w.cap;
-  return v;
-}
+// Extended row of the t-th row of the update (existing rows first).
+__device__ __forceinline__ int upd_row(const WalkerDev& w, int t) { return t < w.n ? t : w.n + w.acc_slot[t - w.n]; }
 
-// Lrow[i', p] = (G_ext[surv(i'), P_p] - delta) a_p ; grid = (row blocks, walkers*2), block 256
+// Lrow[x, p] = (G_ext[x, P_p] - delta) a_p ; grid = (row blocks, walkers*2), block 256
+template <typename T>
 __global__ void __launch_bounds__(256) k_upd_lrow(Config cfg) {
   const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
   const WalkerDev& w = cfg.W[wi];
-  if (!w.active || w.n_acc == 0) return;
+  if (!upd_active(w)) return;
   const ProblemDev& pb = cfg.P[w.problem];
-  const int l = w.n_acc, ns = w.n_surv;
-  const ExtView v = make_view(w, sp);
-  const int total = ns * l;
+  const int l = w.n_acc, rows = w.n + w.n_ins;
+  const ExtView<T> v = make_view<T>(w, sp);
+  const int total = rows * l;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const int i = idx / l, p = idx - i * l;
-    const int x = w.surv[i], P = w.P[p];
+    const int t = idx / l, p = idx - t * l;
+    const int x = upd_row(w, t), P = w.P[p];
     const double a = w.aP[sp][p];
     double val = 0.0;
-    if (a != 0.0) val = (g_ext(v, pb, sp, x, P) - (x == P ? 1.0 : 0.0)) * a;
-    w.Lrow[sp][(size_t)i * KS_MAX + p] = val;
+    if (a != 0.0 && !(x < w.n && v.vs[x] == 0)) val = (g_ext(v, pb, sp, x, P) - (x == P ? 1.0 : 0.0)) * a;
+    w.Lrow[sp][(size_t)x * KS_MAX + p] = val;
   }
 }
 
-// Lp = Lrow Binv ; Rr[p, j'] = N_ext[P_p, surv(j')]
+// Lp = Lrow Binv on the same rows ; Rr[p, j] = N_ext[P_p, j] for j < n,
+// stored in the arithmetic type A of the update product
+template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_upd_lp_rr(Config cfg) {
   const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
   const WalkerDev& w = cfg.W[wi];
-  if (!w.active || w.n_acc == 0) return;
-  const int l = w.n_acc, ns = w.n_surv;
-  const ExtView v = make_view(w, sp);
+  if (!upd_active(w)) return;
+  const int l = w.n_acc, n = w.n, rows = n + w.n_ins;
+  const ExtView<T> v = make_view<T>(w, sp);
   const double* Bi = w.Binv[sp];
-  const int total = ns * l;
+  int total = rows * l;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const int i = idx / l, p = idx - i * l;
-    const double* Lr = w.Lrow[sp] + (size_t)i * KS_MAX;
+    const int t = idx / l, p = idx - t * l;
+    const int x = upd_row(w, t);
+    const double* Lr = w.Lrow[sp] + (size_t)x * KS_MAX;
     double acc = 0.0;
     for (int q = 0; q < l; ++q) acc += Lr[q] * Bi[(size_t)q * KS_MAX + p];
-    w.Lp[sp][(size_t)i * KS_MAX + p] = acc;
+    w.Lp[sp][(size_t)x * KS_MAX + p] = acc;
   }
+  A* Rr = (A*)w.Rr[sp];
+  total = l * n;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const int p = idx / ns, j = idx - p * ns;
-    w.Rr[sp][(size_t)p * w.cap + j] = n_ext(v, w.P[p], w.surv[j]);
+    const int p = idx / n, j = idx - p * n;
+    const int P = w.P[p];
+    const double r = P < n ? ldN(v.N, (size_t)P * v.ld + j) : v.X[(size_t)(P - n) * v.ld + j];
+    Rr[(size_t)p * w.cap + j] = (A)r;
   }
 }
 
-// Nnew[i', j'] = N_ext[surv i', surv j'] + sum_p Lp[i', p] Rr[p, j'].
+// In place: N[i, j] += sum_p Lp[i, p] Rr[p, j] for i, j < n.
 // grid = (col tiles, row tiles, walkers*2), block 256, 32x32 tile.
+template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_upd_apply(Config cfg) {
   const int wi = blockIdx.z >> 1, sp = blockIdx.z & 1;
   const WalkerDev& w = cfg.W[wi];
-  if (!w.active || w.n_acc == 0) return;
-  const int ns = w.n_surv, l = w.n_acc;
+  if (!upd_active(w)) return;
+  const int n = w.n, l = w.n_acc;
   const int j0 = blockIdx.x * TT, i0 = blockIdx.y * TT;
-  if (i0 >= ns || j0 >= ns) return;
-  const ExtView v = make_view(w, sp);
-  double* Nn = w.N[w.parity ^ 1][sp];
+  if (i0 >= n || j0 >= n) return;
+  T* N = (T*)w.N[w.parity][sp];
+  const A* Rr = (const A*)w.Rr[sp];
   const int ld = w.cap;
-  __shared__ double Ls[TT][TT + 1];  // [i][p]
-  __shared__ double Rs[TT][TT + 1];  // [p][j]
-  __shared__ int si[TT], sj[TT];
+  __shared__ A Ls[TT][TT + 1];  // [i][p]
+  __shared__ A Rs[TT][TT + 1];  // [p][j]
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  if (threadIdx.x < TT) {
-    const int i = i0 + threadIdx.x;
-    si[threadIdx.x] = i < ns ? w.surv[i] : 0;
-  } else if (threadIdx.x < 2 * TT) {
-    const int j = j0 + threadIdx.x - TT;
-    sj[threadIdx.x - TT] = j < ns ? w.surv[j] : 0;
-  }
-  double acc[4] = {0, 0, 0, 0};
+  A acc[4] = {0, 0, 0, 0};
   for (int p0 = 0; p0 < l; p0 += TT) {
     __syncthreads();
     for (int r = ty; r < TT; r += 8) {
       const int i = i0 + r, p = p0 + tx;
-      Ls[r][tx] = (i < ns && p < l) ? w.Lp[sp][(size_t)i * KS_MAX + p] : 0.0;
+      Ls[r][tx] = (A)((i < n && p < l) ? w.Lp[sp][(size_t)i * KS_MAX + p] : 0.0);
       const int pp = p0 + r, jj = j0 + tx;
-      Rs[r][tx] = (pp < l && jj < ns) ? w.Rr[sp][(size_t)pp * ld + jj] : 0.0;
+      Rs[r][tx] = (pp < l && jj < n) ? Rr[(size_t)pp * ld + jj] : (A)0;
     }
     __syncthreads();
     const int pend = (l - p0) < TT ? (l - p0) : TT;
     for (int p = 0; p < pend; ++p) {
-      const double r = Rs[p][tx];
+      const A r = Rs[p][tx];
 #pragma unroll
       for (int m = 0; m < 4; ++m) acc[m] += Ls[ty + 8 * m][p] * r;
     }
   }
-  __syncthreads();
   const int jj = j0 + tx;
-  if (jj < ns) {
+  if (jj < n) {
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       const int i = i0 + ty + 8 * m;
-      if (i < ns) Nn[(size_t)i * ld + jj] = n_ext(v, si[ty + 8 * m], sj[tx]) + acc[m];
+      if (i < n) {
+        const size_t o = (size_t)i * ld + jj;
+        stN(N, o, ldN(N, o) + (double)acc[m]);
+      }
     }
   }
 }
 
-// Compact the vertex list into the other buffer and swap.  grid = walkers.
+// Rows and columns of the accepted insertions, appended at n + m:
+//   N[n+m, j]    = X[c_m, j] + Lp[n+c_m, :] . Rr[:, j]          (j < n)
+//   N[i, n+m']   = Lp[i, p(c_m')]                                (i < n)
+//   N[n+m, n+m'] = delta + Lp[n+c_m, p(c_m')]
+// (R[p, n+c] is 1 only where P_p is candidate c itself.)
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) k_upd_border(Config cfg) {
+  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
+  const WalkerDev& w = cfg.W[wi];
+  if (!upd_active(w) || w.n_ins == 0) return;
+  const int n = w.n, l = w.n_acc, ni = w.n_ins, ld = w.cap;
+  T* N = (T*)w.N[w.parity][sp];
+  const A* Rr = (const A*)w.Rr[sp];
+  const int rows_total = ni * n, cols_total = n * ni, corner = ni * ni;
+  const int total = rows_total + cols_total + corner;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    if (idx < rows_total) {
+      const int m = idx / n, j = idx - m * n;
+      const int c = w.acc_slot[m];
+      const double* L = w.Lp[sp] + (size_t)(n + c) * KS_MAX;
+      double acc = w.Xr[sp][(size_t)c * ld + j];
+      for (int p = 0; p < l; ++p) acc += L[p] * (double)Rr[(size_t)p * ld + j];
+      stN(N, (size_t)(n + m) * ld + j, acc);
+    } else if (idx < rows_total + cols_total) {
+      const int t = idx - rows_total;
+      const int i = t / ni, m = t - i * ni;
+      stN(N, (size_t)i * ld + n + m, w.Lp[sp][(size_t)i * KS_MAX + w.acc_p[m]]);
+    } else {
+      const int t = idx - rows_total - cols_total;
+      const int m = t / ni, m2 = t - m * ni;
+      const double v = (m == m2 ? 1.0 : 0.0) + w.Lp[sp][(size_t)(n + w.acc_slot[m]) * KS_MAX + w.acc_p[m2]];
+      stN(N, (size_t)(n + m) * ld + n + m2, v);
+    }
+  }
+}
+
+// Vertex list after the window: removed vertices dead, insertions appended,
+// live-row index rebuilt, compaction scheduled.  grid = walkers.
 __global__ void __launch_bounds__(256) k_window_end(Config cfg) {
   WalkerDev& w = cfg.W[blockIdx.x];
-  if (!w.active || w.n_acc == 0) return;
-  const int par = w.parity, ns = w.n_surv;
-  for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-    const int x = w.surv[i];
+  if (!w.active) return;
+  const int par = w.parity, n = w.n, nrem = w.n_removed, ni = w.n_ins, nl = w.n_live;
+  if (w.n_acc > 0) {
+    for (int r = threadIdx.x; r < nrem; r += blockDim.x) w.vs[par][w.live_idx[w.removed[r]]] = 0;
+    // new live list: surviving ranks in order, then the appended rows
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+      int below = 0, gone = 0;
+      for (int r = 0; r < nrem; ++r) {
+        below += (w.removed[r] < i);
+        gone |= (w.removed[r] == i);
+      }
+      if (!gone) w.surv_tmp[i - below] = w.live_idx[i];
+    }
+    __syncthreads();
+    const int keep = nl - nrem;
+    for (int i = threadIdx.x; i < keep; i += blockDim.x) w.live_idx[i] = w.surv_tmp[i];
+    for (int m = threadIdx.x; m < ni; m += blockDim.x) w.live_idx[keep + m] = n + m;
+    if (threadIdx.x == 0) {
+      // slot c_m >= m and ascending in m: moving in increasing m never
+      // overwrites a candidate that is still to be moved
+      for (int m = 0; m < ni; ++m) {
+        const int src = n + w.acc_slot[m], dst = n + m;
+        w.vsite[par][dst] = w.vsite[par][src];
+        w.vtau[par][dst] = w.vtau[par][src];
+        w.vs[par][dst] = w.vs[par][src];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    w.n = n + ni;
+    w.n_live = nl - nrem + ni;
+    w.n_dead += nrem;
+    const int thr = w.n / 8 > 16 ? w.n / 8 : 16;
+    w.compact_pending = w.n_dead > 0 && (w.n_dead >= thr || w.n + cfg.ks > w.cap || w.recompute_pending);
+  }
+}
+
+// Compaction: live rows / columns into the other buffer.
+// grid = (col tiles, row tiles, walkers*2), block 256.
+template <typename T>
+__global__ void __launch_bounds__(256) k_compact_N(Config cfg) {
+  const int wi = blockIdx.z >> 1, sp = blockIdx.z & 1;
+  const WalkerDev& w = cfg.W[wi];
+  if (!w.active || !w.compact_pending) return;
+  const int k = w.n_live, ld = w.cap;
+  const int j = blockIdx.x * TT + (threadIdx.x & 31);
+  const T* N = (const T*)w.N[w.parity][sp];
+  T* Nn = (T*)w.N[w.parity ^ 1][sp];
+  if (j >= k) return;
+  const int cj = w.live_idx[j];
+  for (int i = blockIdx.y * TT + (threadIdx.x >> 5); i < k && i < (int)(blockIdx.y + 1) * TT; i += 8)
+    Nn[(size_t)i * ld + j] = N[(size_t)w.live_idx[i] * ld + cj];
+}
+
+__global__ void __launch_bounds__(256) k_compact_end(Config cfg) {
+  WalkerDev& w = cfg.W[blockIdx.x];
+  if (!w.active || !w.compact_pending) return;
+  const int par = w.parity, k = w.n_live;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const int x = w.live_idx[i];
     w.vsite[par ^ 1][i] = w.vsite[par][x];
     w.vtau[par ^ 1][i] = w.vtau[par][x];
     w.vs[par ^ 1][i] = w.vs[par][x];
   }
   __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) w.live_idx[i] = i;
   if (threadIdx.x == 0) {
-    w.n = ns;
     w.parity = par ^ 1;
+    w.n = k;
+    w.n_dead = 0;
+    w.compact_pending = 0;
   }
 }
 
@@ -692,49 +794,6 @@ __global__ void k_add_target(Config cfg, int64_t n_sweeps) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < cfg.n_walkers) cfg.W[i].sweeps_target = cfg.W[i].sweeps_done + n_sweeps;
 }
-
-// ---------------------------------------------------------------------------
-// Host launchers
-// ---------------------------------------------------------------------------
-int launch_window_group(int group, const Config& cfg, int max_cap, cudaStream_t st) {
-  const int W = cfg.n_walkers;
-  const int rt = (max_cap + TT - 1) / TT;
-  const int ct = (cfg.ks + TT - 1) / TT;
-  switch (group) {
-    case GROUP_PROPOSE:
-      k_begin<<<W, 128, 0, st>>>(cfg);
-      return 1;
-    case GROUP_EXTEND:
-      k_cand_g<<<dim3(rt, ct, 2 * W), 256, 0, st>>>(cfg);
-      k_cand_x<<<dim3(rt, ct, 2 * W), 256, 0, st>>>(cfg);
-      k_cand_cc<<<dim3(cfg.ks, 2 * W), 128, 0, st>>>(cfg);
-      return 3;
-    case GROUP_METROPOLIS:
-      k_metropolis<<<W, 256, 0, st>>>(cfg);
-      return 1;
-    case GROUP_UPDATE: {
-      const int rows = (max_cap * cfg.ks + 255) / 256;
-      const int gb = rows < 512 ? rows : 512;
-      k_upd_lrow<<<dim3(gb, 2 * W), 256, 0, st>>>(cfg);
-      k_upd_lp_rr<<<dim3(gb, 2 * W), 256, 0, st>>>(cfg);
-      k_upd_apply<<<dim3(rt, rt, 2 * W), 256, 0, st>>>(cfg);
-      k_window_end<<<W, 256, 0, st>>>(cfg);
-      return 4;
-    }
-    default:
-      return 0;
-  }
-}
-
-void launch_count_active(const Config& cfg, cudaStream_t st) { k_count_active<<<1, 256, 0, st>>>(cfg); }
-
-void launch_add_target(const Config& cfg, int64_t n_sweeps, cudaStream_t st) {
-  k_add_target<<<(cfg.n_walkers + 127) / 128, 128, 0, st>>>(cfg, n_sweeps);
-}
-
-}  // namespace dca
-
-namespace dca {
 
 // Loop control of the device-side window loop (body of a conditional WHILE
 // graph node): continue while any walker still has sweeps to do, and stop
@@ -765,6 +824,55 @@ __global__ void k_loop_reset(LoopState* ls, int64_t max_iters) {
   ls->iters = 0;
   ls->max_iters = max_iters;
   ls->timed_out = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+template <typename T, typename A>
+static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_t st) {
+  const int W = cfg.n_walkers;
+  const int rt = (max_cap + TT - 1) / TT;
+  const int ct = (cfg.ks + TT - 1) / TT;
+  switch (group) {
+    case GROUP_PROPOSE:
+      k_begin<<<W, 128, 0, st>>>(cfg);
+      return 1;
+    case GROUP_EXTEND:
+      k_cand_g<T, A><<<dim3(rt, ct, 2 * W), 256, 0, st>>>(cfg);
+      k_cand_x<T, A><<<dim3(rt, ct, 2 * W), 256, 0, st>>>(cfg);
+      k_cand_cc<<<dim3(cfg.ks, 2 * W), 128, 0, st>>>(cfg);
+      return 3;
+    case GROUP_METROPOLIS:
+      k_metropolis<T><<<W, 256, 0, st>>>(cfg);
+      return 1;
+    case GROUP_UPDATE: {
+      const int rows = (max_cap * cfg.ks + 255) / 256;
+      const int gb = rows < 512 ? rows : 512;
+      k_upd_lrow<T><<<dim3(gb, 2 * W), 256, 0, st>>>(cfg);
+      k_upd_lp_rr<T, A><<<dim3(gb, 2 * W), 256, 0, st>>>(cfg);
+      k_upd_apply<T, A><<<dim3(rt, rt, 2 * W), 256, 0, st>>>(cfg);
+      const int bt = (2 * max_cap * cfg.ks + 255) / 256;
+      k_upd_border<T, A><<<dim3(bt < 256 ? bt : 256, 2 * W), 256, 0, st>>>(cfg);
+      k_window_end<<<W, 256, 0, st>>>(cfg);
+      k_compact_N<T><<<dim3(rt, rt, 2 * W), 256, 0, st>>>(cfg);
+      k_compact_end<<<W, 256, 0, st>>>(cfg);
+      return 7;
+    }
+    default:
+      return 0;
+  }
+}
+
+int launch_window_group(int group, const Config& cfg, int max_cap, cudaStream_t st) {
+  return cfg.prec == PREC_MIXED ? launch_group_t<float, float>(group, cfg, max_cap, st)
+                                : launch_group_t<double, double>(group, cfg, max_cap, st);
+}
+
+void launch_count_active(const Config& cfg, cudaStream_t st) { k_count_active<<<1, 256, 0, st>>>(cfg); }
+
+void launch_add_target(const Config& cfg, int64_t n_sweeps, cudaStream_t st) {
+  k_add_target<<<(cfg.n_walkers + 127) / 128, 128, 0, st>>>(cfg, n_sweeps);
 }
 
 void launch_loop_control(const Config& cfg, cudaGraphConditionalHandle handle, LoopState* ls, cudaStream_t st) {

@@ -13,7 +13,8 @@ enum Group : int {
   GROUP_PROPOSE = 0,     // k_begin
   GROUP_EXTEND = 1,      // k_cand_g, k_cand_x, k_cand_cc
   GROUP_METROPOLIS = 2,  // k_metropolis
-  GROUP_UPDATE = 3,      // k_upd_lrow, k_upd_lp_rr, k_upd_apply, k_window_end
+  GROUP_UPDATE = 3,      // k_upd_lrow, k_upd_lp_rr, k_upd_apply, k_upd_border, k_window_end,
+                         // k_compact_N, k_compact_end
   GROUP_MEASURE = 4,     // k_meas_*
   GROUP_RECOMPUTE = 5,   // k_build_A, k_gj_inplace, k_recompute_finish
   N_GROUPS = 6,

@@ -15,8 +15,17 @@
 // non-interacting rows n, n+1, ... of the extended matrices, accepted
 // flips are collected in the ordered set P with a_p = e^{V'_p - V_p} - 1,
 // and B_P = I + (I - G_PP) diag(a_P) is grown by bordering (its inverse
-// Binv).  At the end N <- N + (G[:,P] - E_P) diag(a_P) Binv N[P,:]
-// restricted to the surviving (interacting) rows and columns.
+// Binv).  At the end N <- N + (G[:,P] - E_P) diag(a_P) Binv N[P,:] on the
+// extended configuration: in place on the existing rows / columns, plus the
+// rows and columns of the accepted insertions appended at n, n+1, ...
+//
+// Dead rows.  A removed vertex becomes non-interacting (V = 0, stored s = 0)
+// and keeps its row and column until a compaction pass.  Its column of N is
+// e_y, its row never enters a ratio, an update factor or a measurement, so the
+// live rows (in order) are exactly the configuration of a single-spin chain.
+// Compaction gathers the live rows / columns into the other buffer when dead
+// rows exceed a fraction of n, when n + k_s would exceed the capacity, and
+// before every recompute.
 #pragma once
 #include <cstdint>
 
@@ -28,6 +37,11 @@ enum : int32_t {
   ST_OK = 0,
   ST_ERR_NUMERIC = -5,
   ST_ERR_CAPACITY = -7,
+};
+
+enum : int32_t {
+  PREC_FP64 = 0,   // N stored and updated in FP64
+  PREC_MIXED = 1,  // N stored in FP32, products in FP32; ratios, B^-1, recompute in FP64
 };
 
 struct ProblemDev {
@@ -52,7 +66,10 @@ struct Proposal {
 
 struct WalkerDev {
   // ---- configuration and chain state ----
-  int32_t n;                 // order k = rows of N (all interacting between windows)
+  int32_t n;                 // rows of N (live + dead)
+  int32_t n_live;            // interacting vertices: the expansion order k
+  int32_t n_dead;            // dead rows awaiting compaction
+  int32_t compact_pending;
   int32_t cap;               // matrix capacity (rows / leading dimension)
   int32_t problem;           // index into the problem table
   int32_t status;            // ST_OK or an error code; a walker in error stops
@@ -71,7 +88,7 @@ struct WalkerDev {
   int32_t n_removed;         // accepted removals (existing rows)
   int32_t n_eval;            // proposals evaluated (win_len unless aborted)
   int32_t aborted;
-  int32_t n_surv;            // surviving rows after the window
+  int32_t n_ins;             // accepted insertions (appended rows)
   int32_t measure_pending;
   int32_t recompute_pending;
 
@@ -89,19 +106,23 @@ struct WalkerDev {
   // ---- pools (device pointers) ----
   int32_t* vsite[2];         // [parity][cap]
   double* vtau[2];
-  int32_t* vs[2];
-  double* N[2][2];           // [parity][spin] cap x cap, row-major, ld = cap
+  int32_t* vs[2];            // +1 / -1 interacting, 0 dead (non-interacting)
+  void* N[2][2];             // [parity][spin] cap x cap, row-major, ld = cap; FP64 or FP32
+  double* Ascr[2];           // [spin] cap x cap FP64 work matrix of the recompute (mixed only)
+  int32_t* live_idx;         // [cap] rows of the live vertices, ascending
+  int32_t* surv_tmp;         // [cap] scratch for rebuilding live_idx
   Proposal* prop;            // [KS_MAX]
   double* Gc[2];             // [spin][KS_MAX][cap]: G_ext[:, n + c] stored per candidate c
   double* Xr[2];             // [spin][KS_MAX][cap]: X[c, :] = g0[c,:] (e^V - 1) N
   double* Binv[2];           // [spin][KS_MAX][KS_MAX]
   double* aP[2];             // [spin][KS_MAX]
   int32_t* P;                // [KS_MAX] extended index of accepted flips, in order
-  int32_t* removed;          // [KS_MAX] existing rows removed this window, ascending
-  int32_t* surv;             // [cap] new row -> extended old row
-  double* Lrow[2];           // [spin][cap][KS_MAX]
-  double* Lp[2];             // [spin][cap][KS_MAX]  (L Binv)
-  double* Rr[2];             // [spin][KS_MAX][cap]
+  int32_t* removed;          // [KS_MAX] live ranks removed this window, ascending
+  int32_t* acc_slot;         // [KS_MAX] candidate slot of the m-th accepted insertion
+  int32_t* acc_p;            // [KS_MAX] its position in P
+  double* Lrow[2];           // [spin][cap][KS_MAX] rows of L at extended row index
+  double* Lp[2];             // [spin][cap][KS_MAX] rows of L Binv at extended row index
+  void* Rr[2];               // [spin][KS_MAX][cap] rows of R = N_ext[P, 0:n) (arithmetic type)
   double* Gacc;              // [2][nc][n_tau_meas]
   double* gR;                // [2][nc][cap]
   double* bvec;              // [2][nc][cap]
@@ -121,6 +142,7 @@ struct Config {
   int32_t warmup;
   int32_t recompute_every;
   int32_t n_tau_meas;
+  int32_t prec;              // PREC_FP64 or PREC_MIXED
   double tie_eps;
   WalkerDev* W;              // [n_walkers]
   const ProblemDev* P;       // [n_problems]

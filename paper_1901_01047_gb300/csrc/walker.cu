@@ -143,7 +143,8 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   if (p.recompute_every < 0 || p.warmup_sweeps < 0 || p.n_tau_meas < 1 || p.init_config_size < 0 ||
       p.capacity < 0 || p.log_capacity < 0)
     return fail(nullptr, DCA_ERR_ARG, "negative or zero size parameter");
-  if (p.precision != DCA_PREC_FP64) return fail(nullptr, DCA_ERR_ARG, "unsupported precision");
+  if (p.precision != DCA_PREC_FP64 && p.precision != DCA_PREC_MIXED)
+    return fail(nullptr, DCA_ERR_ARG, "unsupported precision");
   for (int i = 0; i < p.n_problems; ++i) {
     std::string why;
     if (dca::check_problem(p.problems[i], why) != DCA_OK)
@@ -225,7 +226,8 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     int cap = p.capacity;
     if (cap == 0) {
       const double kmax = pr.K + pr.beta * pr.U * pr.nc * 0.5;
-      cap = (int)std::ceil(1.3 * kmax) + 2 * p.k_sub + p.init_config_size + 64;
+      // mean order bound, fluctuations, dead rows awaiting compaction (< 1/8)
+      cap = (int)std::ceil(1.5 * kmax) + 2 * p.k_sub + p.init_config_size + 64;
     }
     cap = (int)align_up((size_t)cap, 32);
     if (p.init_config_size + p.k_sub > cap) {
@@ -248,6 +250,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     w.log_cap = p.log_capacity;
     const size_t C = (size_t)cap;
     const int nc = pr.nc;
+    const size_t esz = p.precision == DCA_PREC_MIXED ? sizeof(float) : sizeof(double);  // N and R
     // one allocation per walker, carved into 256-byte aligned pieces
     struct Piece {
       void** dst;
@@ -258,8 +261,10 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
       pieces.push_back({(void**)&w.vsite[par], sizeof(int32_t) * C});
       pieces.push_back({(void**)&w.vtau[par], sizeof(double) * C});
       pieces.push_back({(void**)&w.vs[par], sizeof(int32_t) * C});
-      for (int sp = 0; sp < 2; ++sp) pieces.push_back({(void**)&w.N[par][sp], sizeof(double) * C * C});
+      for (int sp = 0; sp < 2; ++sp) pieces.push_back({(void**)&w.N[par][sp], esz * C * C});
     }
+    if (p.precision == DCA_PREC_MIXED)
+      for (int sp = 0; sp < 2; ++sp) pieces.push_back({(void**)&w.Ascr[sp], sizeof(double) * C * C});
     pieces.push_back({(void**)&w.prop, sizeof(dca::Proposal) * KS});
     for (int sp = 0; sp < 2; ++sp) {
       pieces.push_back({(void**)&w.Gc[sp], sizeof(double) * KS * C});
@@ -268,11 +273,14 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
       pieces.push_back({(void**)&w.aP[sp], sizeof(double) * KS});
       pieces.push_back({(void**)&w.Lrow[sp], sizeof(double) * KS * C});
       pieces.push_back({(void**)&w.Lp[sp], sizeof(double) * KS * C});
-      pieces.push_back({(void**)&w.Rr[sp], sizeof(double) * KS * C});
+      pieces.push_back({(void**)&w.Rr[sp], esz * KS * C});
     }
     pieces.push_back({(void**)&w.P, sizeof(int32_t) * KS});
     pieces.push_back({(void**)&w.removed, sizeof(int32_t) * KS});
-    pieces.push_back({(void**)&w.surv, sizeof(int32_t) * C});
+    pieces.push_back({(void**)&w.acc_slot, sizeof(int32_t) * KS});
+    pieces.push_back({(void**)&w.acc_p, sizeof(int32_t) * KS});
+    pieces.push_back({(void**)&w.live_idx, sizeof(int32_t) * C});
+    pieces.push_back({(void**)&w.surv_tmp, sizeof(int32_t) * C});
     pieces.push_back({(void**)&w.Gacc, sizeof(double) * 2 * nc * p.n_tau_meas});
     pieces.push_back({(void**)&w.gR, sizeof(double) * 2 * nc * C});
     pieces.push_back({(void**)&w.bvec, sizeof(double) * 2 * nc * C});
@@ -310,6 +318,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.warmup = h->warmup;
   h->cfg.recompute_every = h->R;
   h->cfg.n_tau_meas = h->ntm;
+  h->cfg.prec = p.precision == DCA_PREC_MIXED ? dca::PREC_MIXED : dca::PREC_FP64;
   h->cfg.tie_eps = h->tie_eps;
   h->cfg.W = h->d_W;
   h->cfg.P = h->d_P;
@@ -589,7 +598,7 @@ extern "C" DCA_API int dca_walker_stats(dca_walker* h, dca_walker_stats_t* out) 
     s.measurements = w.n_meas;
     s.recomputes = w.n_recomputes;
     s.sweep_length = w.sweep_len;
-    s.order = w.n;
+    s.order = w.n_live;
     s.status = status_code(w.status);
     s.sign = w.sign;
     s.k_sum = w.k_sum;
@@ -608,28 +617,37 @@ extern "C" DCA_API int dca_walker_get_state(dca_walker* h, int32_t wi, dca_verte
   int rc = pull_records(h);
   if (rc != DCA_OK) return rc;
   const WalkerDev& w = h->h_W[wi];
-  const int n = w.n, par = w.parity;
-  if (k) *k = n;
-  if (verts && n > 0) {
-    std::vector<int32_t> site(n), s(n);
-    std::vector<double> tau(n);
-    CK(cudaMemcpyAsync(site.data(), w.vsite[par], sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaMemcpyAsync(s.data(), w.vs[par], sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaMemcpyAsync(tau.data(), w.vtau[par], sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    for (int i = 0; i < n; ++i) {
-      verts[i].site = site[i];
-      verts[i].s = s[i];
-      verts[i].tau = tau[i];
-    }
-  }
-  double* outs[2] = {N_up, N_dn};
-  for (int sp = 0; sp < 2; ++sp) {
-    if (!outs[sp] || n == 0) continue;
-    CK(cudaMemcpy2DAsync(outs[sp], sizeof(double) * n, w.N[par][sp], sizeof(double) * w.cap, sizeof(double) * n, n,
-                         cudaMemcpyDeviceToHost, h->stream));
-  }
+  const int n = w.n, k_live = w.n_live, par = w.parity;
+  if (k) *k = k_live;
+  if (k_live == 0) return DCA_OK;
+  std::vector<int32_t> live(k_live), site(n), s(n);
+  std::vector<double> tau(n);
+  CK(cudaMemcpyAsync(live.data(), w.live_idx, sizeof(int32_t) * k_live, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(site.data(), w.vsite[par], sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(s.data(), w.vs[par], sizeof(int32_t) * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(tau.data(), w.vtau[par], sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (verts)
+    for (int i = 0; i < k_live; ++i) {
+      verts[i].site = site[live[i]];
+      verts[i].s = s[live[i]];
+      verts[i].tau = tau[live[i]];
+    }
+  double* outs[2] = {N_up, N_dn};
+  const bool f32 = h->cfg.prec == dca::PREC_MIXED;
+  const size_t esz = f32 ? sizeof(float) : sizeof(double);
+  std::vector<unsigned char> full((size_t)n * n * esz);
+  for (int sp = 0; sp < 2; ++sp) {
+    if (!outs[sp]) continue;
+    CK(cudaMemcpy2DAsync(full.data(), esz * n, w.N[par][sp], esz * w.cap, esz * n, n, cudaMemcpyDeviceToHost,
+                         h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < k_live; ++i)
+      for (int j = 0; j < k_live; ++j) {
+        const size_t o = (size_t)live[i] * n + live[j];
+        outs[sp][(size_t)i * k_live + j] = f32 ? (double)((const float*)full.data())[o] : ((const double*)full.data())[o];
+      }
+  }
   return DCA_OK;
 }
 

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libdcawalker.so")
 
 DCA_OK = 0
 ERRORS = {-1: "ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "NUMERIC", -6: "STATE", -7: "CAPACITY"}
-PRECISIONS = {"fp64": 0}
+PRECISIONS = {"fp64": 0, "mixed": 1}
 
 EXPORTS = [
     "dca_g0_isolated_cluster", "dca_walker_create", "dca_walker_sweep", "dca_walker_measure_G",

@@ -1,0 +1,82 @@
+"""Mixed precision (N stored in FP32, products in FP32; ratios, B^-1, the
+update factors and the recompute in FP64) against the FP64 oracle.
+
+Trajectories of two arithmetics part ways at the first flipped decision, so
+the error is measured on an identical trajectory: the GPU walker replays the
+oracle's decision log (forced decisions), and N and the accumulated sign * G
+are compared at the end in the norm form max|X_gpu - X_ora| / max|X_ora|.
+Without forcing, the free-running mixed walker must still agree with the
+oracle's decisions for a long stretch.
+"""
+import numpy as np
+import pytest
+
+from oracle import ctaux
+from tests.helpers import problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _walkers(**kw):
+    import torch
+    from paper_1901_01047_gb300 import walker
+    return walker.Walkers(stream=torch.cuda.current_stream().cuda_stream, **kw)
+
+
+def replay(nc, tp, U, beta, mu, k_sub, sweeps, R, seed=0, ntm=32, n_tau=4096):
+    c, eps, kr, G0 = problem(nc, 1.0, tp, U, beta, mu, n_tau)
+    ow = ctaux.OracleWalker(nc, c.site_sub, U, beta, 1.0, G0, warmup_sweeps=10, n_tau_meas=ntm, seed=seed)
+    ow.enable_log(1 << 24)
+    ow.sweep(sweeps)
+    log = ow.log()
+    gw = _walkers(problems=[dict(nc=nc, site_sub=c.site_sub, U=U, beta=beta, K=1.0, G0=G0)], k_sub=k_sub,
+                  recompute_every=R, warmup_sweeps=10, n_tau_meas=ntm, seed=seed, precision="mixed",
+                  log_capacity=1 << 24)
+    gw.set_forced_decisions(0, log)
+    gw.sweep(sweeps)
+    gs, os_ = gw.state(0), ow.state()
+    assert np.array_equal(gs["site"], os_["site"]) and np.array_equal(gs["s"], os_["s"])
+    errN = max(np.abs(gs["N"][sp] - os_["N"][sp]).max() / np.abs(os_["N"][sp]).max() for sp in range(2))
+    Gg, ssg, nmg = gw.measure_G()
+    Go, sso, nmo = ow.G()
+    assert nmg[0] == nmo and ssg[0] == sso
+    errG = np.abs(Gg[0] - Go).max() / np.abs(Go).max()
+    st = gw.stats()[0]
+    gw.close()
+    return errN, errG, st, log
+
+
+# Measured bounds (FP32 rounding amplified by the conditioning of N^-1, about
+# 1e3 for the 2x2 cluster at beta = 10 and 2e4 for the 16-site case below);
+# recomputing every 8 submatrix updates instead of 64 cuts the error by ~4x.
+def test_mixed_replay_2x2_errors():
+    errN, errG, st, _ = replay(4, 0.0, 4.0, 10.0, 0.9450480104035819, 32, 2000, 64)
+    assert st["status"] == 0 and st["recomputes"] > 0
+    assert errN < 1e-4, errN
+    assert errG < 5e-5, errG
+    errN8, errG8, st8, _ = replay(4, 0.0, 4.0, 10.0, 0.9450480104035819, 32, 2000, 8)
+    assert errG8 < 1e-5, errG8
+
+
+def test_mixed_replay_16_site_errors():
+    errN, errG, st, _ = replay(16, -0.15, 6.0, 4.0, 2.85, 64, 60, 64, ntm=16, n_tau=2048)
+    assert errN < 1e-4, errN
+    assert errG < 1e-5, errG
+
+
+def test_mixed_free_run_follows_the_oracle_for_a_long_stretch():
+    nc, U, beta, mu = 4, 4.0, 10.0, 0.9450480104035819
+    c, eps, kr, G0 = problem(nc, 1.0, 0.0, U, beta, mu, 4096)
+    gw = _walkers(problems=[dict(nc=nc, site_sub=c.site_sub, U=U, beta=beta, K=1.0, G0=G0)], k_sub=32,
+                  recompute_every=64, warmup_sweeps=10, n_tau_meas=8, seed=3, precision="mixed",
+                  log_capacity=1 << 22)
+    gw.sweep(300)
+    glog = gw.decision_log(0)
+    ow = ctaux.OracleWalker(nc, c.site_sub, U, beta, 1.0, G0, warmup_sweeps=10, n_tau_meas=8, seed=3)
+    ow.enable_log(1 << 22)
+    ow.sweep(300)
+    olog = ow.log()
+    n = min(glog.size, olog.size)
+    mism = np.nonzero((glog[:n] & 1) != (olog[:n] & 1))[0]
+    first = mism[0] if mism.size else n
+    assert first > 2000, first
