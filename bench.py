@@ -296,7 +296,7 @@ def run_ours(args, rank, world, local_rank):
         peaks, kind = _peaks()
         g_ms, g_launch = gtimes[dominant]
         windows = max(1, g_launch // max(1, {"propose": 1, "extend": 3, "metropolis": 1, "update": 7,
-                                             "measure": 4, "recompute": 3}[dominant]))
+                                             "measure": 5, "recompute": 3}[dominant]))
         roof = roofline(dominant, g_ms, windows, kflops, ubytes, eflops, ebytes, peaks, kind, wl)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

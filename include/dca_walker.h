@@ -64,7 +64,7 @@ extern "C" {
 
 /* One physical problem (a cluster with its bare propagator). */
 typedef struct {
-  int32_t nc;              /* cluster sites; N_corr = Nc (single band, Sec. 2.3) */
+  int32_t nc;              /* cluster sites, 1..64; N_corr = Nc (single band, Sec. 2.3) */
   const int32_t* site_sub; /* host [nc*nc]: index of r_i - r_j folded into the cluster;
                               rows must be permutations of 0..nc-1 */
   double U;                /* on-site interaction, >= 0 */

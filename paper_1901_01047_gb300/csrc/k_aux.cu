@@ -45,136 +45,30 @@ __device__ __forceinline__ double* work_matrix(const Config& cfg, const WalkerDe
   return (double*)w.N[mode == 0 ? w.parity : w.parity ^ 1][sp];
 }
 
+// grid = (blocks, walkers*2), grid-stride over the n x n entries
 __global__ void __launch_bounds__(256) k_build_A(Config cfg, int mode) {
-  const int wi = blockIdx.z >> 1, sp = blockIdx.z & 1;
+  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
   const WalkerDev& w = cfg.W[wi];
   if (!wants_build(w, mode)) return;
   const int n = w.n, ld = w.cap, par = w.parity;
-  const int j = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
-  if (i >= n || j >= n) return;
   const ProblemDev& pb = cfg.P[w.problem];
   double* A = work_matrix(cfg, w, mode, sp);
   const int* vsite = w.vsite[par];
   const double* vtau = w.vtau[par];
   const int* vs = w.vs[par];
-  const double ej = expV(pb, sp, vs[j]);
-  const double g = (i == j) ? g0_diag(pb, sp, vsite[i]) : g0_pair(pb, sp, vsite[i], vtau[i], vsite[j], vtau[j]);
-  A[(size_t)i * ld + j] = (i == j ? ej : 0.0) - g * (ej - 1.0);
+  const long long total = (long long)n * n;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
+    const double ej = expV(pb, sp, vs[j]);
+    const double g = (i == j) ? g0_diag(pb, sp, vsite[i]) : g0_pair(pb, sp, vsite[i], vtau[i], vsite[j], vtau[j]);
+    A[(size_t)i * ld + j] = (i == j ? ej : 0.0) - g * (ej - 1.0);
+  }
 }
 
-// In-place Gauss-Jordan inverse with partial (row) pivoting, one block per
-// (walker, spin).  Column c of the working matrix is turned into column c of
-// the inverse as the elimination proceeds; the row interchanges are undone
-// at the end as column interchanges in reverse order.  Scratch (outside a
-// window): Lrow[sp] holds a copy of the pivot column and the pivot rows.
-// Writes the sign of det A to sgn_out[2*wi + sp] (0 if singular).
-__global__ void __launch_bounds__(1024) k_gj_inplace(Config cfg, int mode, int* sgn_out) {
-  const int wi = blockIdx.x >> 1, sp = blockIdx.x & 1;
-  WalkerDev& w = cfg.W[wi];
-  if (!wants_build(w, mode)) return;
-  const int n = w.n, ld = w.cap;
-  double* A = work_matrix(cfg, w, mode, sp);
-  // scratch: column copy (n doubles) and pivot rows (n ints, stored as doubles)
-  double* colc = w.Lrow[sp];
-  double* pivs = w.Lrow[sp] + ld;
-  __shared__ double s_val[32];
-  __shared__ int s_idx[32];
-  __shared__ int s_piv, s_bad;
-  __shared__ double s_d;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  int sign = 1;
-  if (tid == 0) s_bad = 0;
-  for (int c = 0; c < n; ++c) {
-    // pivot: argmax_{r >= c} |A[r][c]|
-    double best = -1.0;
-    int bi = c;
-    for (int r = c + tid; r < n; r += nt) {
-      const double v = fabs(A[(size_t)r * ld + c]);
-      if (v > best) {
-        best = v;
-        bi = r;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) {
-        best = ov;
-        bi = oi;
-      }
-    }
-    if (lane == 0) {
-      s_val[warp] = best;
-      s_idx[warp] = bi;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double b = -1.0;
-      int ix = c;
-      for (int k = 0; k < nt / 32; ++k)
-        if (s_val[k] > b || (s_val[k] == b && s_idx[k] < ix)) {
-          b = s_val[k];
-          ix = s_idx[k];
-        }
-      s_piv = ix;
-      if (!(b > 0.0)) s_bad = 1;
-      pivs[c] = (double)ix;
-    }
-    __syncthreads();
-    if (s_bad) break;
-    const int p = s_piv;
-    if (p != c) {
-      for (int j = tid; j < n; j += nt) {
-        const double t = A[(size_t)c * ld + j];
-        A[(size_t)c * ld + j] = A[(size_t)p * ld + j];
-        A[(size_t)p * ld + j] = t;
-      }
-      sign = -sign;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      s_d = A[(size_t)c * ld + c];
-      A[(size_t)c * ld + c] = 1.0;
-    }
-    __syncthreads();
-    const double d = s_d;
-    if (d < 0.0) sign = -sign;
-    const double rd = 1.0 / d;
-    for (int j = tid; j < n; j += nt) A[(size_t)c * ld + j] *= rd;
-    for (int r = tid; r < n; r += nt) colc[r] = (r == c) ? 0.0 : A[(size_t)r * ld + c];
-    __syncthreads();
-    for (int r = tid; r < n; r += nt)
-      if (r != c) A[(size_t)r * ld + c] = 0.0;
-    __syncthreads();
-    // A[r][j] -= colc[r] * A[c][j]
-    for (int idx = tid; idx < n * n; idx += nt) {
-      const int r = idx / n, j = idx - r * n;
-      const double f = colc[r];
-      if (f != 0.0) A[(size_t)r * ld + j] -= f * A[(size_t)c * ld + j];
-    }
-    __syncthreads();
-  }
-  if (s_bad) {
-    if (tid == 0) {
-      w.status = ST_ERR_NUMERIC;
-      sgn_out[blockIdx.x] = 0;
-    }
-    return;
-  }
-  // undo the row interchanges as column interchanges, last first
-  for (int c = n - 1; c >= 0; --c) {
-    const int p = (int)pivs[c];
-    if (p != c)
-      for (int r = tid; r < n; r += nt) {
-        const double t = A[(size_t)r * ld + c];
-        A[(size_t)r * ld + c] = A[(size_t)r * ld + p];
-        A[(size_t)r * ld + p] = t;
-      }
-    __syncthreads();
-  }
-  if (tid == 0) sgn_out[blockIdx.x] = sign;
+static int build_blocks(int max_n) {
+  const long long b = ((long long)max_n * max_n + 255) / 256;
+  return (int)(b < 512 ? (b > 0 ? b : 1) : 512);
 }
 
 // Initial build finish: sign of prod_sigma det N_sigma^-1.
@@ -299,12 +193,83 @@ __global__ void __launch_bounds__(256) k_meas_b(Config cfg) {
   }
 }
 
-// Gacc[sp][dr][a] += sign * (-G); grid = (blocks, walkers), thread per (sp, dr, a).
+// Correction term as a product: rows (x, tau_a), inner index the vertex i,
+// columns the reference site r':
+//   C[(x, a), r'] = sum_i g0(x - r_i, tau_a - tau_i) b_i(r'),
+// scattered to Gtmp[sp][x - r'][a] (FP64 atomics).  The g0 factor is
+// interpolated on the fly.  A is the arithmetic type of the products.
+// grid = (nc * ceil(n_tau_meas / 64), walkers * 2), block 256.
+constexpr int MT = 64;   // tau points per block
+constexpr int MK = 32;   // vertices per step
+constexpr int MR = 64;   // reference sites per block (nc <= 64)
+
+template <typename A>
+__global__ void __launch_bounds__(256) k_meas_gemm(Config cfg) {
+  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
+  const WalkerDev& w = cfg.W[wi];
+  if (!wants_measure(w)) return;
+  const ProblemDev& pb = cfg.P[w.problem];
+  const int nc = pb.nc, ntm = cfg.n_tau_meas, n = w.n, par = w.parity, ld = w.cap;
+  const int tblocks = (ntm + MT - 1) / MT;
+  const int x = blockIdx.x / tblocks, a0 = (blockIdx.x - x * tblocks) * MT;
+  if (x >= nc) return;
+  __shared__ A As[MT][MK + 1];
+  __shared__ A Bs[MK][MR + 1];
+  const int tid = threadIdx.x;
+  const int ta = tid & (MT - 1), tr = tid >> 6;  // 4 groups of reference sites
+  A acc[MR / 4];
+#pragma unroll
+  for (int m = 0; m < MR / 4; ++m) acc[m] = (A)0;
+  const int* vsite = w.vsite[par];
+  const double* vtau = w.vtau[par];
+  const int* vs = w.vs[par];
+  const double* row_base = pb.g0 + (size_t)sp * nc * (pb.n_tau + 1);
+  for (int i0 = 0; i0 < n; i0 += MK) {
+    __syncthreads();
+    for (int e = tid; e < MT * MK; e += 256) {
+      const int al = e / MK, il = e - al * MK;
+      const int a = a0 + al, i = i0 + il;
+      double v = 0.0;
+      if (a < ntm && i < n && vs[i] != 0) {
+        const double ta_ = ((double)a + 0.5) * pb.beta / (double)ntm;
+        const int d = __ldg(pb.site_sub + x * nc + vsite[i]);
+        v = g0_interp(row_base + (size_t)d * (pb.n_tau + 1), pb.n_tau, pb.beta, pb.tau_scale, ta_ - vtau[i]);
+      }
+      As[al][il] = (A)v;
+    }
+    for (int e = tid; e < MK * MR; e += 256) {
+      const int il = e / MR, rp = e - il * MR;
+      const int i = i0 + il;
+      Bs[il][rp] = (A)((i < n && rp < nc) ? w.bvec[((size_t)sp * nc + rp) * ld + i] : 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < MK; ++k) {
+      const A g = As[ta][k];
+#pragma unroll
+      for (int m = 0; m < MR / 4; ++m) acc[m] += g * Bs[k][tr + 4 * m];
+    }
+  }
+  const int a = a0 + ta;
+  if (a < ntm) {
+#pragma unroll
+    for (int m = 0; m < MR / 4; ++m) {
+      const int rp = tr + 4 * m;
+      if (rp < nc) {
+        const int d = __ldg(pb.site_sub + x * nc + rp);
+        atomicAdd(&w.Gtmp[((size_t)sp * nc + d) * ntm + a], (double)acc[m]);
+      }
+    }
+  }
+}
+
+// Gacc[sp][dr][a] += sign * (-G), G = g0(dr, tau_a) + Gtmp / Nc; Gtmp cleared.
+// grid = (blocks, walkers), thread per (sp, dr, a).
 __global__ void __launch_bounds__(256) k_meas_acc(Config cfg) {
   WalkerDev& w = cfg.W[blockIdx.y];
   if (!wants_measure(w)) return;
   const ProblemDev& pb = cfg.P[w.problem];
-  const int n = w.n, par = w.parity, nc = pb.nc, ld = w.cap, ntm = cfg.n_tau_meas;
+  const int nc = pb.nc, ntm = cfg.n_tau_meas;
   const int total = 2 * nc * ntm;
   const double sign = w.sign;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
@@ -313,15 +278,9 @@ __global__ void __launch_bounds__(256) k_meas_acc(Config cfg) {
     const int d = rem / ntm, a = rem - d * ntm;
     const double ta = ((double)a + 0.5) * pb.beta / (double)ntm;
     const double* row = pb.g0 + ((size_t)sp * nc + d) * (size_t)(pb.n_tau + 1);
-    double G = g0_interp(row, pb.n_tau, pb.beta, pb.tau_scale, ta);
-    double corr = 0.0;
-    for (int rp = 0; rp < nc; ++rp) {
-      const int x = pb.site_add[rp * nc + d];
-      const double* b = w.bvec + ((size_t)sp * nc + rp) * ld;
-      for (int i = 0; i < n; ++i) corr += g0_pair(pb, sp, x, ta, w.vsite[par][i], w.vtau[par][i]) * b[i];
-    }
-    G += corr / (double)nc;
-    w.Gacc[((size_t)sp * nc + d) * ntm + a] += sign * (-G);
+    const double G = g0_interp(row, pb.n_tau, pb.beta, pb.tau_scale, ta) + w.Gtmp[idx] / (double)nc;
+    w.Gtmp[idx] = 0.0;
+    w.Gacc[idx] += sign * (-G);
   }
 }
 
@@ -367,8 +326,8 @@ void launch_init(const Config& cfg, int n0, int max_cap, int* d_sgn, cudaStream_
   const int W = cfg.n_walkers;
   k_init_vertices<<<W, 256, 0, st>>>(cfg, n0);
   if (n0 > 0) {
-    k_build_A<<<dim3((n0 + 31) / 32, (n0 + 7) / 8, 2 * W), 256, 0, st>>>(cfg, 0);
-    k_gj_inplace<<<2 * W, 1024, 0, st>>>(cfg, 0, d_sgn);
+    k_build_A<<<dim3(build_blocks(n0), 2 * W), 256, 0, st>>>(cfg, 0);
+    launch_gj(cfg, 0, n0, d_sgn, st);
     if (cfg.prec == PREC_MIXED) {
       const int gb = (n0 * n0 + 255) / 256;
       k_store_fp32<<<dim3(gb < 1024 ? gb : 1024, 2 * W), 256, 0, st>>>(cfg, 0);
@@ -380,8 +339,8 @@ void launch_init(const Config& cfg, int n0, int max_cap, int* d_sgn, cudaStream_
 
 int launch_recompute(const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st) {
   const int W = cfg.n_walkers;
-  k_build_A<<<dim3((max_cap + 31) / 32, (max_cap + 7) / 8, 2 * W), 256, 0, st>>>(cfg, 1);
-  k_gj_inplace<<<2 * W, 1024, 0, st>>>(cfg, 1, d_sgn);
+  k_build_A<<<dim3(build_blocks(max_cap), 2 * W), 256, 0, st>>>(cfg, 1);
+  launch_gj(cfg, 1, max_cap, d_sgn, st);
   if (cfg.prec == PREC_MIXED) {
     const int gb = (max_cap * max_cap + 255) / 256;
     k_store_fp32<<<dim3(gb < 1024 ? gb : 1024, 2 * W), 256, 0, st>>>(cfg, 1);
@@ -397,8 +356,8 @@ int launch_recompute(const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st
 void launch_fresh_inverse(const Config& cfg, int max_n, int* d_sgn, cudaStream_t st) {
   const int W = cfg.n_walkers;
   if (max_n <= 0) return;
-  k_build_A<<<dim3((max_n + 31) / 32, (max_n + 7) / 8, 2 * W), 256, 0, st>>>(cfg, 0);
-  k_gj_inplace<<<2 * W, 1024, 0, st>>>(cfg, 0, d_sgn);
+  k_build_A<<<dim3(build_blocks(max_n), 2 * W), 256, 0, st>>>(cfg, 0);
+  launch_gj(cfg, 0, max_n, d_sgn, st);
 }
 
 __global__ void k_negate(const double* src, double* dst, size_t n) {
@@ -420,12 +379,15 @@ int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) 
   gw = gw < 2048 ? gw : 2048;
   if (cfg.prec == PREC_MIXED) k_meas_b<float><<<dim3(gw, 2 * W), 256, 0, st>>>(cfg);
   else k_meas_b<double><<<dim3(gw, 2 * W), 256, 0, st>>>(cfg);
+  const int mblocks = max_nc * ((cfg.n_tau_meas + MT - 1) / MT);
+  if (cfg.prec == PREC_MIXED) k_meas_gemm<float><<<dim3(mblocks, 2 * W), 256, 0, st>>>(cfg);
+  else k_meas_gemm<double><<<dim3(mblocks, 2 * W), 256, 0, st>>>(cfg);
   const int outs = 2 * max_nc * cfg.n_tau_meas;
   int ga = (outs + 255) / 256;
   ga = ga < 1024 ? ga : 1024;
   k_meas_acc<<<dim3(ga, W), 256, 0, st>>>(cfg);
   k_meas_finish<<<(W + 127) / 128, 128, 0, st>>>(cfg);
-  return 4;
+  return 5;
 }
 
 void launch_g0_isolated(int nc, const double* d_eps, const double* d_kr, double mu_eff, double beta, int n_tau,

@@ -16,7 +16,7 @@ enum Group : int {
   GROUP_UPDATE = 3,      // k_upd_lrow, k_upd_lp_rr, k_upd_apply, k_upd_border, k_window_end,
                          // k_compact_N, k_compact_end
   GROUP_MEASURE = 4,     // k_meas_*
-  GROUP_RECOMPUTE = 5,   // k_build_A, k_gj_inplace, k_recompute_finish
+  GROUP_RECOMPUTE = 5,   // k_build_A, k_gj_cluster, (k_store_fp32), k_recompute_finish
   N_GROUPS = 6,
 };
 
@@ -28,6 +28,8 @@ void launch_loop_reset(LoopState* ls, int64_t max_iters, cudaStream_t st);
 void launch_add_target(const Config& cfg, int64_t n_sweeps, cudaStream_t st);
 void launch_init(const Config& cfg, int n0, int max_cap, int* d_sgn, cudaStream_t st);
 void launch_fresh_inverse(const Config& cfg, int max_n, int* d_sgn, cudaStream_t st);
+// Gauss-Jordan inverse of the FP64 work matrices, one 8-block cluster each.
+void launch_gj(const Config& cfg, int mode, int max_n, int* d_sgn, cudaStream_t st);
 int launch_recompute(const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st);
 int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
 void launch_negate(const double* src, double* dst, size_t n, cudaStream_t st);

@@ -124,6 +124,7 @@ struct WalkerDev {
   double* Lp[2];             // [spin][cap][KS_MAX] rows of L Binv at extended row index
   void* Rr[2];               // [spin][KS_MAX][cap] rows of R = N_ext[P, 0:n) (arithmetic type)
   double* Gacc;              // [2][nc][n_tau_meas]
+  double* Gtmp;              // [2][nc][n_tau_meas] correction term of one measurement
   double* gR;                // [2][nc][cap]
   double* bvec;              // [2][nc][cap]
 };

@@ -149,6 +149,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     std::string why;
     if (dca::check_problem(p.problems[i], why) != DCA_OK)
       return fail(nullptr, DCA_ERR_ARG, "problem " + std::to_string(i) + ": " + why);
+    if (p.problems[i].nc > 64) return fail(nullptr, DCA_ERR_ARG, "problem " + std::to_string(i) + ": nc > 64");
   }
   if (p.walker_problem)
     for (int w = 0; w < p.n_walkers; ++w)
@@ -282,6 +283,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     pieces.push_back({(void**)&w.live_idx, sizeof(int32_t) * C});
     pieces.push_back({(void**)&w.surv_tmp, sizeof(int32_t) * C});
     pieces.push_back({(void**)&w.Gacc, sizeof(double) * 2 * nc * p.n_tau_meas});
+    pieces.push_back({(void**)&w.Gtmp, sizeof(double) * 2 * nc * p.n_tau_meas});
     pieces.push_back({(void**)&w.gR, sizeof(double) * 2 * nc * C});
     pieces.push_back({(void**)&w.bvec, sizeof(double) * 2 * nc * C});
     if (p.log_capacity > 0) pieces.push_back({(void**)&w.log, (size_t)p.log_capacity});

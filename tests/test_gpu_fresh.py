@@ -56,3 +56,31 @@ def test_fresh_N_rejects_bad_vertices():
     for site, tau, s in [([4], [0.5], [1]), ([0], [3.0], [1]), ([0], [-0.1], [1]), ([0], [0.5], [0])]:
         with pytest.raises(walker.WalkerError, match="ARG"):
             walker.fresh_N(prob, site, tau, s)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n", [300, 700])
+def test_fresh_N_large_random_configuration(n):
+    # many rows per block of the 8-block cluster inverse.  Random vertices give
+    # ill-conditioned A (entries of N over ~10 decades), so the check is the
+    # residual A N - I against the oracle's own, plus a kappa-scaled agreement.
+    from paper_1901_01047_gb300 import walker
+    nc, U, beta = 16, 1.0, 5.0
+    c, eps, kr, G0 = problem(nc, 1.0, -0.15, U, beta, 0.3, 1024)
+    rng = np.random.default_rng(n)
+    site = rng.integers(0, nc, n).astype(np.int32)
+    tau = rng.uniform(0, beta, n)
+    s = rng.choice([-1, 1], n).astype(np.int8)
+    prob = dict(nc=nc, site_sub=c.site_sub, U=U, beta=beta, K=1.0, G0=G0)
+    Nu, Nd, sg = walker.fresh_N(prob, site, tau, s)
+    ow = ctaux.OracleWalker(nc, c.site_sub, U, beta, 1.0, G0, init_config_size=0)
+    ow.set_config(site, tau, s)
+    assert sg == int(ow.sign)
+    for sp, Ng in enumerate((Nu, Nd)):
+        ref, _ = ow.fresh_N(sp)
+        A = ow.build_A(sp, site, tau, s)
+        res_g = np.abs(A @ Ng - np.eye(n)).max()
+        res_o = np.abs(A @ ref - np.eye(n)).max()
+        assert res_g <= 10 * res_o + 1e-12, (res_g, res_o)
+        kappa = np.linalg.cond(A)
+        assert np.abs(Ng - ref).max() <= 1e-15 * kappa * np.abs(ref).max()
