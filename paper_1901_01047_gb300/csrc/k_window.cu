@@ -3,8 +3,9 @@
 // Sequence per window (DCA++ paper Sec. 2.3, "Submatrix updates"):
 //   k_begin       proposals of the window from Philox (counter tag 0 / 1);
 //                 insertion candidates appended as non-interacting rows n + c
-//   k_cand_g      G_ext[i, n+c] = sum_j N[i,j] g0(r_j - r_c, tau_j - tau_c)
-//   k_cand_x      X[c, j]     = sum_i g0(r_c - r_i, tau_c - tau_i) (e^{V_i} - 1) N[i,j]
+//   k_cand_ext    one pass over N for both candidate products:
+//                 G_ext[i, n+c] = sum_j N[i,j] g0(r_j - r_c, tau_j - tau_c)
+//                 X[c, j]     = sum_i g0(r_c - r_i, tau_c - tau_i) (e^{V_i} - 1) N[i,j]
 //   k_cand_cc     G_ext[n+c', n+c] = X[c',:] . g0[:, c] + g0(c', c)
 //   k_metropolis  serial single-spin decisions from B_P^-1 (bordered growth)
 //   k_upd_*       N <- N + (G[:,P] - E_P) diag(a_P) B^-1 N[P,:]: in place on
@@ -116,108 +117,102 @@ __global__ void __launch_bounds__(128) k_begin(Config cfg) {
 }
 
 // ---------------------------------------------------------------------------
-// Candidate extension GEMMs (SIMT, 32x32 tiles, 256 threads, FP64 accumulate).
-// grid = (row tiles, candidate tiles, walkers * 2 spins).  Dead rows and
-// columns contribute nothing (a dead vertex has e^V - 1 = 0 and a unit
-// column of N), so they are skipped.
+// Candidate extension, both products in one pass over N (SIMT).  A 64 x 64
+// tile N[I, J] contributes
+//   G_ext[I, n+c] += N[I, J] V[J, c],  V[j, c] = g0(r_j - r_c, tau_j - tau_c)
+//   X[c, J]       += U[c, I] N[I, J],  U[c, i] = g0(r_c - r_i, tau_c - tau_i) (e^{V_i} - 1)
+// and the partial sums are reduced into the FP64 buffers Gc / Xr with
+// atomics (zeroed by k_cand_zero).  Dead rows have e^V - 1 = 0 and dead
+// columns of N are unit columns, so both are skipped.
+// grid = (tiles^2, walkers * 2), block 256, dynamic shared memory.
 // ---------------------------------------------------------------------------
-constexpr int TT = 32;
+constexpr int TT = 32;   // tile of the update kernel
+constexpr int METRO_SMEM_KS = 96;  // largest k_s whose B^-1 (both spins) lives in shared memory
+constexpr int ET = 64;   // tile of the extension kernel
+constexpr int EC = 32;   // candidates per pass
 
-template <typename T, typename A>
-__global__ void __launch_bounds__(256) k_cand_g(Config cfg) {
-  const int wi = blockIdx.z >> 1, sp = blockIdx.z & 1;
+__global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
+  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
   const WalkerDev& w = cfg.W[wi];
-  if (!w.active) return;
-  const int n = w.n, nc_ = w.n_cand;
-  const int i0 = blockIdx.x * TT, c0 = blockIdx.y * TT;
-  if (i0 >= n || c0 >= nc_) return;
-  const ProblemDev& pb = cfg.P[w.problem];
-  const int ld = w.cap, par = w.parity;
-  const T* __restrict__ N = (const T*)w.N[par][sp];
-  const int* vsite = w.vsite[par];
-  const double* vtau = w.vtau[par];
-  const int* vs = w.vs[par];
-  __shared__ A As[TT][TT + 1];
-  __shared__ A Bs[TT][TT + 1];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  A acc[4] = {0, 0, 0, 0};
-  for (int k0 = 0; k0 < n; k0 += TT) {
-    for (int r = ty; r < TT; r += 8) {
-      const int i = i0 + r, k = k0 + tx;
-      As[r][tx] = (A)((i < n && k < n) ? ldN(N, (size_t)i * ld + k) : 0.0);
-      // B[k, c] = g0(r_k - r_c, tau_k - tau_c)
-      const int kk = k0 + r, c = c0 + tx;
-      double b = 0.0;
-      if (kk < n && c < nc_ && vs[kk] != 0) b = g0_pair(pb, sp, vsite[kk], vtau[kk], vsite[n + c], vtau[n + c]);
-      Bs[r][tx] = (A)b;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < TT; ++k) {
-      const A b = Bs[k][tx];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) acc[m] += As[ty + 8 * m][k] * b;
-    }
-    __syncthreads();
-  }
-  const int c = c0 + tx;
-  if (c < nc_) {
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int i = i0 + ty + 8 * m;
-      if (i < n) w.Gc[sp][(size_t)c * ld + i] = acc[m];
-    }
+  if (!w.active || w.n_cand == 0) return;
+  const int nc_ = w.n_cand, n = w.n, ld = w.cap;
+  const int total = nc_ * n;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int c = idx / n, i = idx - c * n;
+    w.Gc[sp][(size_t)c * ld + i] = 0.0;
+    w.Xr[sp][(size_t)c * ld + i] = 0.0;
   }
 }
 
 template <typename T, typename A>
-__global__ void __launch_bounds__(256) k_cand_x(Config cfg) {
-  const int wi = blockIdx.z >> 1, sp = blockIdx.z & 1;
+__global__ void __launch_bounds__(256) k_cand_ext(Config cfg, int tiles) {
+  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
   const WalkerDev& w = cfg.W[wi];
-  if (!w.active) return;
+  if (!w.active || w.n_cand == 0) return;
   const int n = w.n, nc_ = w.n_cand;
-  const int j0 = blockIdx.x * TT, c0 = blockIdx.y * TT;
-  if (j0 >= n || c0 >= nc_) return;
+  const int ti = blockIdx.x / tiles, tj = blockIdx.x - ti * tiles;
+  const int i0 = ti * ET, j0 = tj * ET;
+  if (i0 >= n || j0 >= n) return;
   const ProblemDev& pb = cfg.P[w.problem];
   const int ld = w.cap, par = w.parity;
   const T* __restrict__ N = (const T*)w.N[par][sp];
   const int* vsite = w.vsite[par];
   const double* vtau = w.vtau[par];
   const int* vs = w.vs[par];
-  __shared__ A Us[TT][TT + 1];   // [c][k]
-  __shared__ A Bs[TT][TT + 1];   // [k][j]
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  A acc[4] = {0, 0, 0, 0};
-  for (int k0 = 0; k0 < n; k0 += TT) {
-    for (int r = ty; r < TT; r += 8) {
-      // U[c, k] = g0(r_c - r_k, tau_c - tau_k) (e^{V_k} - 1)
-      const int c = c0 + r, k = k0 + tx;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  A(*Ns)[ET + 1] = reinterpret_cast<A(*)[ET + 1]>(smem_raw);                  // [i][j]
+  A(*Vs)[EC + 1] = reinterpret_cast<A(*)[EC + 1]>(Ns + ET);                   // [j][c]
+  A(*Us)[ET + 1] = reinterpret_cast<A(*)[ET + 1]>(Vs + ET);                   // [c][i]
+  const int tid = threadIdx.x;
+  for (int e = tid; e < ET * ET; e += 256) {
+    const int r = e / ET, cc = e - r * ET;
+    const int i = i0 + r, j = j0 + cc;
+    Ns[r][cc] = (A)((i < n && j < n) ? ldN(N, (size_t)i * ld + j) : 0.0);
+  }
+  const int lo = tid & (ET - 1), hi = tid >> 6;  // 64 lanes x 4 groups
+  for (int cb = 0; cb < nc_; cb += EC) {
+    __syncthreads();
+    for (int e = tid; e < ET * EC; e += 256) {
+      const int r = e / EC, c = e - r * EC;
+      const int j = j0 + r, cg = cb + c;
+      double v = 0.0;
+      if (j < n && cg < nc_ && vs[j] != 0) v = g0_pair(pb, sp, vsite[j], vtau[j], vsite[n + cg], vtau[n + cg]);
+      Vs[r][c] = (A)v;
+      const int i = i0 + r;
       double u = 0.0;
-      if (c < nc_ && k < n && vs[k] != 0)
-        u = g0_pair(pb, sp, vsite[n + c], vtau[n + c], vsite[k], vtau[k]) * (expV(pb, sp, vs[k]) - 1.0);
-      Us[r][tx] = (A)u;
-      const int kk = k0 + r, jj = j0 + tx;
-      Bs[r][tx] = (A)((kk < n && jj < n) ? ldN(N, (size_t)kk * ld + jj) : 0.0);
+      if (i < n && cg < nc_ && vs[i] != 0)
+        u = g0_pair(pb, sp, vsite[n + cg], vtau[n + cg], vsite[i], vtau[i]) * (expV(pb, sp, vs[i]) - 1.0);
+      Us[c][r] = (A)u;
     }
     __syncthreads();
+    A g[EC / 4], x[EC / 4];
+#pragma unroll
+    for (int m = 0; m < EC / 4; ++m) g[m] = x[m] = (A)0;
+    // G partial: row i = lo, candidates hi + 4m ; X partial: column j = lo
 #pragma unroll 8
-    for (int k = 0; k < TT; ++k) {
-      const A b = Bs[k][tx];
+    for (int k = 0; k < ET; ++k) {
+      const A nik = Ns[lo][k];
+      const A nkj = Ns[k][lo];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) acc[m] += Us[ty + 8 * m][k] * b;
+      for (int m = 0; m < EC / 4; ++m) {
+        g[m] += nik * Vs[k][hi + 4 * m];
+        x[m] += Us[hi + 4 * m][k] * nkj;
+      }
     }
-    __syncthreads();
-  }
-  const int jj = j0 + tx;
-  if (jj < n) {
-    // a dead column j of N is e_j, so X[c, j] = U[c, j] = 0 there
-    const bool dead = vs[jj] == 0;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int c = c0 + ty + 8 * m;
-      if (c < nc_) w.Xr[sp][(size_t)c * ld + jj] = dead ? 0.0 : (double)acc[m];
+    for (int m = 0; m < EC / 4; ++m) {
+      const int cg = cb + hi + 4 * m;
+      if (cg < nc_) {
+        if (i0 + lo < n) atomicAdd(&w.Gc[sp][(size_t)cg * ld + i0 + lo], (double)g[m]);
+        if (j0 + lo < n) atomicAdd(&w.Xr[sp][(size_t)cg * ld + j0 + lo], (double)x[m]);
+      }
     }
   }
+}
+
+template <typename A>
+constexpr int ext_smem_bytes() {
+  return (int)sizeof(A) * (ET * (ET + 1) + ET * (EC + 1) + EC * (ET + 1));
 }
 
 // G_ext[n+c', n+c] = X[c',:] . g0[:, c] + g0(r_c' - r_c, tau_c' - tau_c).
@@ -317,7 +312,12 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
   const int tid = threadIdx.x;
   const int n = w.n, n_live = w.n_live, len = w.win_len;
   ExtView<T> ev[2] = {make_view<T>(w, 0), make_view<T>(w, 1)};
-  double* Binv[2] = {w.Binv[0], w.Binv[1]};
+  // B^-1 of both spins: in shared memory when k_s <= METRO_SMEM_KS (copied to
+  // the global buffers at the end for the update kernels), else in global memory.
+  extern __shared__ double s_binv[];
+  const bool in_smem = cfg.ks <= METRO_SMEM_KS;
+  const int bst = in_smem ? cfg.ks : KS_MAX;
+  double* Binv[2] = {in_smem ? s_binv : w.Binv[0], in_smem ? s_binv + cfg.ks * cfg.ks : w.Binv[1]};
   const int* live_idx = w.live_idx;
 
   __shared__ double s_brow[2][KS_MAX], s_bcol[2][KS_MAX], s_t[2][KS_MAX], s_s[2][KS_MAX];
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
     if (tid < 2 * KS_MAX) {
       const int sp = tid / KS_MAX, i = tid - sp * KS_MAX;
       if (i < l) {
-        const double* B = Binv[sp] + (size_t)i * KS_MAX;
+        const double* B = Binv[sp] + (size_t)i * bst;
         double acc = 0.0;
         for (int p = 0; p < l; ++p) acc += B[p] * s_bcol[sp][p];
         s_t[sp][i] = acc;
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
       const int sp = tid / KS_MAX, jj = tid - sp * KS_MAX;
       if (jj < l) {
         double acc = 0.0;
-        for (int i = 0; i < l; ++i) acc += s_brow[sp][i] * Binv[sp][(size_t)i * KS_MAX + jj];
+        for (int i = 0; i < l; ++i) acc += s_brow[sp][i] * Binv[sp][(size_t)i * bst + jj];
         s_s[sp][jj] = acc;
       }
     }
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
       const double rd = 1.0 / s_d[sp];
       for (int idx = tid; idx < (l + 1) * (l + 1); idx += blockDim.x) {
         const int i = idx / (l + 1), jj = idx - i * (l + 1);
-        double* B = Binv[sp] + (size_t)i * KS_MAX + jj;
+        double* B = Binv[sp] + (size_t)i * bst + jj;
         if (i < l && jj < l) *B += s_t[sp][i] * s_s[sp][jj] * rd;
         else if (i < l) *B = -s_t[sp][i] * rd;
         else if (jj < l) *B = -s_s[sp][jj] * rd;
@@ -501,6 +501,12 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
 
   // Epilogue: window bookkeeping and the accepted set.
   const int l = s_l, nrem = s_nrem, nins = s_nins;
+  if (in_smem)
+    for (int sp = 0; sp < 2; ++sp)
+      for (int idx = tid; idx < l * l; idx += blockDim.x) {
+        const int i = idx / l, jj = idx - i * l;
+        w.Binv[sp][(size_t)i * KS_MAX + jj] = Binv[sp][(size_t)i * bst + jj];
+      }
   for (int p = tid; p < l; p += blockDim.x) {
     w.P[p] = s_P[p];
     w.aP[0][p] = s_aP[0][p];
@@ -833,19 +839,23 @@ template <typename T, typename A>
 static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_t st) {
   const int W = cfg.n_walkers;
   const int rt = (max_cap + TT - 1) / TT;
-  const int ct = (cfg.ks + TT - 1) / TT;
   switch (group) {
     case GROUP_PROPOSE:
       k_begin<<<W, 128, 0, st>>>(cfg);
       return 1;
-    case GROUP_EXTEND:
-      k_cand_g<T, A><<<dim3(rt, ct, 2 * W), 256, 0, st>>>(cfg);
-      k_cand_x<T, A><<<dim3(rt, ct, 2 * W), 256, 0, st>>>(cfg);
+    case GROUP_EXTEND: {
+      const int et = (max_cap + ET - 1) / ET;
+      const int zb = (cfg.ks * max_cap + 255) / 256;
+      k_cand_zero<<<dim3(zb < 256 ? zb : 256, 2 * W), 256, 0, st>>>(cfg);
+      k_cand_ext<T, A><<<dim3(et * et, 2 * W), 256, ext_smem_bytes<A>(), st>>>(cfg, et);
       k_cand_cc<<<dim3(cfg.ks, 2 * W), 128, 0, st>>>(cfg);
       return 3;
-    case GROUP_METROPOLIS:
-      k_metropolis<T><<<W, 256, 0, st>>>(cfg);
+    }
+    case GROUP_METROPOLIS: {
+      const int sm = cfg.ks <= METRO_SMEM_KS ? (int)sizeof(double) * 2 * cfg.ks * cfg.ks : 0;
+      k_metropolis<T><<<W, 256, sm, st>>>(cfg);
       return 1;
+    }
     case GROUP_UPDATE: {
       const int rows = (max_cap * cfg.ks + 255) / 256;
       const int gb = rows < 512 ? rows : 512;
@@ -862,6 +872,18 @@ static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_
     default:
       return 0;
   }
+}
+
+cudaError_t setup_window_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(k_cand_ext<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       ext_smem_bytes<double>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cand_ext<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             ext_smem_bytes<float>());
+  const int msm = (int)sizeof(double) * 2 * METRO_SMEM_KS * METRO_SMEM_KS;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_metropolis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, msm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_metropolis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, msm);
+  return e;
 }
 
 int launch_window_group(int group, const Config& cfg, int max_cap, cudaStream_t st) {

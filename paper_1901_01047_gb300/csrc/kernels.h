@@ -20,6 +20,10 @@ enum Group : int {
   N_GROUPS = 6,
 };
 
+// Kernel attributes (dynamic shared memory limits); call once per process
+// and device before any launch or stream capture.
+cudaError_t setup_window_kernels();
+
 // Each launcher returns the number of kernels it launched.
 int launch_window_group(int group, const Config& cfg, int max_cap, cudaStream_t st);
 void launch_count_active(const Config& cfg, cudaStream_t st);

@@ -326,6 +326,10 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.P = h->d_P;
   h->cfg.active_count = h->d_active;
 
+  if (dca::setup_window_kernels() != cudaSuccess) {
+    h->err = "kernel attribute setup failed";
+    return bail(DCA_ERR_CUDA);
+  }
   dca::launch_init(h->cfg, p.init_config_size, h->max_cap, h->d_sgn, h->stream);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_W.data(), h->d_W, sizeof(WalkerDev) * h->W, cudaMemcpyDeviceToHost, h->stream);
