@@ -43,6 +43,9 @@ def _peaks():
 
 # Nominal GB300 FP64 rate (the recipe's figure); the FP64 path is bound by it.
 FP64_TFLOPS = 1.25
+# Dense TF32 / BF16 tensor rate ratio from the nominal figures (1.1 / 2.25),
+# applied to the measured BF16 peak.
+TF32_PER_BF16 = 1.1 / 2.25
 
 
 class ClockSampler:
@@ -101,20 +104,27 @@ def config_of(wl, world):
     return {"workload": wl.name, "nc": wl.nc, "t": wl.t, "tp": wl.tp, "U": wl.U, "beta": wl.beta, "mu": wl.mu,
             "K": wl.K, "walkers_per_gpu": wl.walkers, "k_sub": wl.k_sub, "n_tau": wl.n_tau,
             "n_tau_meas": wl.n_tau_meas, "recompute_every": wl.recompute_every, "precision": wl.precision,
-            "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)"}
+            "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)",
+            **({"per_walker": {"nc": list(wl.nc_choices), "beta": list(wl.beta_range), "U": list(wl.U_range),
+                               "mu": "U/2"}} if wl.nc_choices else {})}
 
 
-def workload_problem(wl, use_gpu_builder):
-    c = inputs.cluster(wl.nc)
-    eps = inputs.square_dispersion(c.kpts, wl.t, wl.tp)
+def build_problem(pp, use_gpu_builder):
+    c = inputs.cluster(pp["nc"])
+    eps = inputs.square_dispersion(c.kpts, pp["t"], pp["tp"])
     kr = inputs.k_dot_r(c)
     if use_gpu_builder:
         from paper_1901_01047_gb300 import walker
-        G0 = walker.g0_isolated_cluster(eps, kr, wl.mu, wl.U, wl.beta, wl.n_tau)
+        G0 = walker.g0_isolated_cluster(eps, kr, pp["mu"], pp["U"], pp["beta"], pp["n_tau"])
     else:
         from oracle import g0 as og0
-        G0 = og0.g0_table(eps, kr, wl.mu, wl.U, wl.beta, wl.n_tau)
-    return dict(nc=wl.nc, site_sub=c.site_sub, U=wl.U, beta=wl.beta, K=wl.K, G0=G0)
+        G0 = og0.g0_table(eps, kr, pp["mu"], pp["U"], pp["beta"], pp["n_tau"])
+    return dict(nc=pp["nc"], site_sub=c.site_sub, U=pp["U"], beta=pp["beta"], K=pp["K"], G0=G0)
+
+
+def workload_problems(wl, use_gpu_builder):
+    params, walker_problem = wl.problem_params()
+    return [build_problem(pp, use_gpu_builder) for pp in params], walker_problem
 
 
 # --------------------------------------------------------------------------
@@ -125,8 +135,10 @@ def _oracle_sample(args):
     sys.path.insert(0, ROOT)
     from oracle import ctaux
     wl = inputs.WORKLOADS[wl_name]
-    pr = workload_problem(wl, use_gpu_builder=False)
-    w = ctaux.OracleWalker(wl.nc, pr["site_sub"], wl.U, wl.beta, wl.K, pr["G0"], warmup_sweeps=wl.warmup_sweeps,
+    params, walker_problem = wl.problem_params()
+    pr = build_problem(params[walker_problem[walker_id % len(walker_problem)]], use_gpu_builder=False)
+    w = ctaux.OracleWalker(pr["nc"], pr["site_sub"], pr["U"], pr["beta"], pr["K"], pr["G0"],
+                           warmup_sweeps=wl.warmup_sweeps,
                            n_tau_meas=wl.n_tau_meas, seed=seed, walker_id=walker_id,
                            init_config_size=wl.init_config_size)
     w.sweep(wl.warmup_sweeps)
@@ -195,9 +207,10 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     wl = inputs.WORKLOADS[args.workload]
     stream = torch.cuda.current_stream()
-    prob = workload_problem(wl, use_gpu_builder=True)
+    probs, walker_problem = workload_problems(wl, use_gpu_builder=True)
     seed = wl.seed + 1000003 * rank
-    gw = walker.Walkers([prob], n_walkers=wl.walkers, k_sub=wl.k_sub, recompute_every=wl.recompute_every,
+    gw = walker.Walkers(probs, n_walkers=wl.walkers, walker_problem=walker_problem, k_sub=wl.k_sub,
+                        recompute_every=wl.recompute_every,
                         warmup_sweeps=wl.warmup_sweeps, n_tau_meas=wl.n_tau_meas, precision=wl.precision,
                         init_config_size=wl.init_config_size, seed=seed, stream=stream.cuda_stream)
     gw.sweep(wl.warmup_sweeps)            # the chain's own warm-up (no measurements)
@@ -216,7 +229,9 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     # Timed region 1 (the value): device-side window loop, no kernel events.
-    gw.set_timing([])
+    # Under --profile-region the same kernels are launched from the host
+    # instead (ncu does not see kernels inside conditional graph bodies).
+    gw.set_timing(["propose"] if args.profile_region else [])
     st0 = gw.stats()
     gw.timing(reset=True)
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
@@ -228,6 +243,8 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    if args.profile_region:
+        torch.cuda.profiler.start()
     t0 = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(float(k))
@@ -235,6 +252,8 @@ def run_ours(args, rank, world, local_rank):
         gw.sweep(1)
         ends[k].record(stream)
     torch.cuda.synchronize()
+    if args.profile_region:
+        torch.cuda.profiler.stop()
     if dist:
         dist.barrier()
     wall = time.perf_counter() - t0
@@ -244,8 +263,9 @@ def run_ours(args, rank, world, local_rank):
     dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
 
     # Timed region 2 (the roofline): the same steps driven from the host with
-    # CUDA events on the walker's stream around the dominant kernel group.
-    gw.set_timing([dominant])
+    # CUDA events on the walker's stream around the dominant kernel group and
+    # around the N-update kernel.
+    gw.set_timing(sorted({dominant, "update"}))
     st_k0 = gw.stats()
     for k in range(args.steps):
         flush.fill_(float(k))
@@ -260,6 +280,8 @@ def run_ours(args, rank, world, local_rank):
     ubytes = sum(b["n_update_bytes"] - a["n_update_bytes"] for a, b in zip(st_k0, st_k1))
     eflops = sum(b["extend_flops"] - a["extend_flops"] for a, b in zip(st_k0, st_k1))
     ebytes = sum(b["extend_bytes"] - a["extend_bytes"] for a, b in zip(st_k0, st_k1))
+    rflops = sum(b["recompute_flops"] - a["recompute_flops"] for a, b in zip(st_k0, st_k1))
+    work = {"update": (ubytes, kflops), "extend": (ebytes, eflops), "recompute": (None, rflops)}
     t_step = torch.tensor([dev_ms / 1000.0, float(props), flops], dtype=torch.float64, device="cuda")
     if dist:
         tmax = t_step.clone()
@@ -271,7 +293,7 @@ def run_ours(args, rank, world, local_rank):
 
     # End to end through the public API with host buffers: a new bare propagator
     # uploaded from pinned memory, one sweep, and G read back, every step.
-    G0_host = torch.from_numpy(np.ascontiguousarray(prob["G0"])).pin_memory()
+    G0_host = torch.from_numpy(np.ascontiguousarray(probs[0]["G0"])).pin_memory()
     g_bytes = sum(2 * nc * wl.n_tau_meas * 8 for nc in gw.nc) + 16 * wl.walkers
     st2 = gw.stats()
     if dist:
@@ -294,10 +316,9 @@ def run_ours(args, rank, world, local_rank):
 
     if rank == 0:
         peaks, kind = _peaks()
-        g_ms, g_launch = gtimes[dominant]
-        windows = max(1, g_launch // max(1, {"propose": 1, "extend": 3, "metropolis": 1, "update": 7,
-                                             "measure": 5, "recompute": 3}[dominant]))
-        roof = roofline(dominant, g_ms, windows, kflops, ubytes, eflops, ebytes, peaks, kind, wl)
+        windows = max(1, gtimes["propose"][1])  # one proposal kernel per window
+        roof = roofline(dominant, gtimes[dominant][0], windows, work, peaks, kind, wl)
+        roof_upd = roofline("update", gtimes["update"][0], windows, work, peaks, kind, wl)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * seconds / args.steps, "higher_is_better": True,
@@ -311,6 +332,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": launches,
             "kernel_ms": {g: round(v[0], 4) for g, v in times.items()},
             "roofline": roof,
+            "n_update_roofline": roof_upd,
             "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": int(G0_host.numel() * 8),
                     "d2h_bytes_per_step": int(g_bytes)},
         }
@@ -322,29 +344,33 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-def roofline(group, g_ms, windows, flops, ubytes, eflops, ebytes, peaks, kind, wl):
-    """Roofline of the dominant kernel group from its CUDA-event time."""
-    if group == "update":
-        work_b, work_f = ubytes, flops
-    elif group == "extend":
-        work_b, work_f = ebytes, eflops
-    else:
-        work_b, work_f = None, None
+def roofline(group, g_ms, windows, work, peaks, kind, wl):
+    """Roofline of one kernel group from its CUDA-event time over the timed
+    steps.  `work` maps a group to its algorithmic (bytes, flop) over the same
+    steps; the recompute counts flop only (FP64 arithmetic bound)."""
     sec = g_ms / 1000.0
-    if work_b is None or sec <= 0:
-        return {"kernel": group, "bound": "alu", "achieved": None, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "note": "latency-bound kernel group without an algorithmic byte or flop count",
-                "launch_ms": g_ms / max(1, windows)}
-    gbs = work_b / sec / 1e9
+    launch_ms = g_ms / max(1, windows)
+    base = {"kernel": group, "launch_ms": launch_ms, "traffic": None}
+    if group not in work or sec <= 0:
+        return {**base, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                "note": "latency-bound kernel group without an algorithmic byte or flop count"}
+    work_b, work_f = work[group]
     tfs = work_f / sec / 1e12
-    ai = work_f / max(work_b, 1.0)
+    if work_b is None:
+        return {**base, "bound": "alu", "achieved": tfs, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": tfs / FP64_TFLOPS, "peak_kind": "nominal FP64 (recipe table)"}
+    gbs = work_b / sec / 1e9
     hbm = peaks["hbm_gbs"]
+    ai = work_f / max(work_b, 1.0)
+    out = {**base, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+           "peak_kind": kind, "tflops": tfs, "flop_per_byte": ai}
     if wl.precision == "fp64" and ai > FP64_TFLOPS * 1e12 / (hbm * 1e9):
-        return {"kernel": group, "bound": "alu", "achieved": tfs, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": tfs / FP64_TFLOPS, "traffic": None, "peak_kind": "nominal FP64",
-                "hbm_gbs_achieved": gbs, "launch_ms": g_ms / max(1, windows)}
-    return {"kernel": group, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-            "traffic": None, "peak_kind": kind, "launch_ms": g_ms / max(1, windows)}
+        out.update({"bound": "alu", "achieved": tfs, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tfs / FP64_TFLOPS, "peak_kind": "nominal FP64 (recipe table)", "hbm_gbs": gbs})
+    elif wl.precision == "mixed":
+        tf32 = peaks["bf16_tflops"] * TF32_PER_BF16
+        out.update({"tf32_peak_tflops": tf32, "tf32_frac": tfs / tf32})
+    return out
 
 
 def main():
@@ -355,6 +381,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off) "
+                         "and launch the window kernels from the host in that region")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -95,7 +95,13 @@ typedef struct {
   uint64_t seed;                   /* App. B "seed" */
   double tie_eps;                  /* near-tie band on | |R| - u |; 0 = 1e-10 */
   int64_t log_capacity;            /* decision-log bytes per walker; 0 = no log */
+  int32_t update_kernel;           /* N-update kernel of DCA_PREC_MIXED: DCA_UPD_* */
 } dca_walker_params;
+
+/* N-update kernels of the mixed-precision path (ignored by DCA_PREC_FP64). */
+#define DCA_UPD_AUTO 0       /* DCA_UPD_TCGEN05 */
+#define DCA_UPD_CUDA_CORE 1  /* FP32 CUDA-core tiles */
+#define DCA_UPD_TCGEN05 2    /* 3xTF32 tcgen05.mma, operands and N tiles moved by TMA */
 
 /* Vertex of a configuration: site index, imaginary time, auxiliary spin. */
 typedef struct {
@@ -123,6 +129,7 @@ typedef struct {
   double n_update_bytes;    /* algorithmic bytes of the N updates (read + write n^2, n x l factors) */
   double extend_flops;      /* flop of the candidate extension (4 n^2 c per spin) */
   double extend_bytes;      /* bytes of the candidate extension (two reads of N per spin) */
+  double recompute_flops;   /* flop of the from-scratch inverses (2 n^3 per spin) */
 } dca_walker_stats_t;
 
 typedef struct dca_walker dca_walker;
@@ -222,9 +229,12 @@ DCA_API int dca_walker_update_G0(dca_walker* w, int32_t problem, const double* G
 /* Kernel groups for timing: bit g of the mask times group g with CUDA events
  * recorded on the walker's stream around every launch of that group.
  *   0 proposals, 1 candidate extension (G columns / X rows), 2 Metropolis
- *   with the Gamma (B^-1) growth, 3 N update with compaction, 4 measurement,
- *   5 from-scratch recompute. */
-#define DCA_N_GROUPS 6
+ *   with the Gamma (B^-1) growth, 3 the rank-l N update kernel alone,
+ *   4 measurement, 5 the from-scratch inverse kernel alone, 6 the factors of
+ *   the N update (L B^-1, N[P,:]), 7 the rest of the update (rows of accepted
+ *   insertions, dead marking, compaction), 8 the matrix build before the
+ *   inverse, 9 the drift check and adoption after it. */
+#define DCA_N_GROUPS 10
 DCA_API int dca_walker_set_timing(dca_walker* w, uint32_t group_mask);
 
 /* Accumulated milliseconds and kernel launches per group (arrays of

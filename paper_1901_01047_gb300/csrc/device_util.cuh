@@ -95,4 +95,27 @@ __device__ __forceinline__ double ldN(const float* p, size_t i) { return (double
 __device__ __forceinline__ void stN(double* p, size_t i, double v) { p[i] = v; }
 __device__ __forceinline__ void stN(float* p, size_t i, double v) { p[i] = (float)v; }
 
+// Persistent, load-balanced iteration over the work items of `nsets` sets
+// (walker-spin pairs, or walkers): set s has count(s) items, and item t of
+// set s goes to block (prefix(s) + t) mod gridDim.x.  Every block walks the
+// sets in order keeping a running prefix, so the loop variables are uniform
+// over the block and `body` may use __syncthreads().
+template <typename CountF, typename BodyF>
+__device__ __forceinline__ void for_each_item(int nsets, CountF count, BodyF body) {
+  if (nsets <= 0) return;
+  int s = 0;
+  long long base = 0;
+  long long cnt = count(0);
+  for (long long item = blockIdx.x;; item += gridDim.x) {
+    while (item >= base + cnt) {
+      base += cnt;
+      if (++s >= nsets) return;
+      cnt = count(s);
+    }
+    body(s, (int)(item - base));
+  }
+}
+
+__host__ __device__ __forceinline__ long long blocks_of(long long items, int per) { return (items + per - 1) / per; }
+
 }  // namespace dca

@@ -45,31 +45,36 @@ __device__ __forceinline__ double* work_matrix(const Config& cfg, const WalkerDe
   return (double*)w.N[mode == 0 ? w.parity : w.parity ^ 1][sp];
 }
 
-// grid = (blocks, walkers*2), grid-stride over the n x n entries
+// Persistent grid; one item = 256 entries of one walker-spin's A.
 __global__ void __launch_bounds__(256) k_build_A(Config cfg, int mode) {
-  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
-  const WalkerDev& w = cfg.W[wi];
-  if (!wants_build(w, mode)) return;
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        return wants_build(w, mode) ? blocks_of((long long)w.n * w.n, 256) : 0;
+      },
+      [&](int s, int item) {
+  const WalkerDev& w = cfg.W[s >> 1];
+  const int sp = s & 1;
   const int n = w.n, ld = w.cap, par = w.parity;
   const ProblemDev& pb = cfg.P[w.problem];
   double* A = work_matrix(cfg, w, mode, sp);
   const int* vsite = w.vsite[par];
   const double* vtau = w.vtau[par];
   const int* vs = w.vs[par];
-  const long long total = (long long)n * n;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
+  const long long idx = (long long)item * 256 + threadIdx.x;
+  if (idx < (long long)n * n) {
     const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
     const double ej = expV(pb, sp, vs[j]);
     const double g = (i == j) ? g0_diag(pb, sp, vsite[i]) : g0_pair(pb, sp, vsite[i], vtau[i], vsite[j], vtau[j]);
     A[(size_t)i * ld + j] = (i == j ? ej : 0.0) - g * (ej - 1.0);
   }
+      });
 }
 
-static int build_blocks(int max_n) {
-  const long long b = ((long long)max_n * max_n + 255) / 256;
-  return (int)(b < 512 ? (b > 0 ? b : 1) : 512);
-}
+constexpr int PERSIST = 4 * 152;
+
+static int grid_for(long long items) { return (int)(items < 1 ? 1 : (items < PERSIST ? items : PERSIST)); }
 
 // Initial build finish: sign of prod_sigma det N_sigma^-1.
 __global__ void k_init_finish(Config cfg, const int* sgn) {
@@ -88,46 +93,80 @@ __global__ void k_init_finish(Config cfg, const int* sgn) {
 // FP32 storage: round the FP64 inverse into the destination buffer.
 // grid = (blocks, walkers*2)
 __global__ void __launch_bounds__(256) k_store_fp32(Config cfg, int mode) {
-  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
-  const WalkerDev& w = cfg.W[wi];
-  if (!wants_build(w, mode) || w.status != ST_OK) return;
-  const int n = w.n, ld = w.cap;
-  const double* A = w.Ascr[sp];
-  float* N = (float*)w.N[mode == 0 ? w.parity : w.parity ^ 1][sp];
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
-    const int i = idx / n, j = idx - i * n;
-    N[(size_t)i * ld + j] = (float)A[(size_t)i * ld + j];
-  }
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        return (wants_build(w, mode) && w.status == ST_OK) ? blocks_of((long long)w.n * w.n, 256) : 0;
+      },
+      [&](int s, int item) {
+        const WalkerDev& w = cfg.W[s >> 1];
+        const int sp = s & 1, n = w.n, ld = w.cap;
+        const double* A = w.Ascr[sp];
+        float* N = (float*)w.N[mode == 0 ? w.parity : w.parity ^ 1][sp];
+        const long long idx = (long long)item * 256 + threadIdx.x;
+        if (idx < (long long)n * n) {
+          const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
+          N[(size_t)i * ld + j] = (float)A[(size_t)i * ld + j];
+        }
+      });
 }
 
-// Drift of the updated N against the fresh inverse, then adopt the fresh one.
-// grid = walkers, block 256.
+// Drift of the updated N against the fresh inverse: max |N_old - N_new| and
+// max |N_new| over both spins, reduced per block and folded in with atomicMax
+// on the bit patterns (non-negative doubles order like their bits).
+// Persistent grid over walker-spin pairs, 2048 entries per item.
 template <typename T>
-__global__ void __launch_bounds__(256) k_recompute_finish(Config cfg, const int* sgn) {
+__global__ void __launch_bounds__(256) k_recompute_drift(Config cfg) {
+  __shared__ double s_d[8], s_n[8];
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        return (w.active && w.recompute_pending && w.status == ST_OK) ? blocks_of((long long)w.n * w.n, 2048) : 0;
+      },
+      [&](int s, int item) {
+        WalkerDev& w = cfg.W[s >> 1];
+        const int sp = s & 1, n = w.n, ld = w.cap, par = w.parity;
+        const T* Nold = (const T*)w.N[par][sp];
+        const T* Nnew = (const T*)w.N[par ^ 1][sp];
+        double dmax = 0.0, nmax = 0.0;
+        const long long e0 = (long long)item * 2048, e1 = min(e0 + 2048, (long long)n * n);
+        for (long long idx = e0 + threadIdx.x; idx < e1; idx += 256) {
+          const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
+          const double a = ldN(Nold, (size_t)i * ld + j), b = ldN(Nnew, (size_t)i * ld + j);
+          dmax = fmax(dmax, fabs(a - b));
+          nmax = fmax(nmax, fabs(b));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+          nmax = fmax(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+          s_d[threadIdx.x >> 5] = dmax;
+          s_n[threadIdx.x >> 5] = nmax;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double d = 0.0, m = 0.0;
+          for (int k = 0; k < 8; ++k) {
+            d = fmax(d, s_d[k]);
+            m = fmax(m, s_n[k]);
+          }
+          atomicMax(&w.drift_bits[0], (unsigned long long)__double_as_longlong(d));
+          atomicMax(&w.drift_bits[1], (unsigned long long)__double_as_longlong(m));
+        }
+        __syncthreads();
+      });
+}
+
+// Adopt the fresh inverse: copy the vertex list to the other buffer, switch
+// the parity, log the relative drift.  grid = walkers, block 256.
+__global__ void __launch_bounds__(256) k_recompute_adopt(Config cfg) {
   WalkerDev& w = cfg.W[blockIdx.x];
   if (!(w.active && w.recompute_pending && w.status == ST_OK)) return;
-  const int n = w.n, ld = w.cap, par = w.parity;
-  double dmax = 0.0, nmax = 0.0;
-  for (int sp = 0; sp < 2; ++sp) {
-    const T* Nold = (const T*)w.N[par][sp];
-    const T* Nnew = (const T*)w.N[par ^ 1][sp];
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      const int i = idx / n, j = idx - i * n;
-      const double a = ldN(Nold, (size_t)i * ld + j), b = ldN(Nnew, (size_t)i * ld + j);
-      dmax = fmax(dmax, fabs(a - b));
-      nmax = fmax(nmax, fabs(b));
-    }
-  }
-  __shared__ double s_d[8], s_n[8];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    nmax = fmax(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    s_d[threadIdx.x >> 5] = dmax;
-    s_n[threadIdx.x >> 5] = nmax;
-  }
+  const int n = w.n, par = w.parity;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     w.vsite[par ^ 1][i] = w.vsite[par][i];
     w.vtau[par ^ 1][i] = w.vtau[par][i];
@@ -135,15 +174,15 @@ __global__ void __launch_bounds__(256) k_recompute_finish(Config cfg, const int*
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double d = 0.0, m = 0.0;
-    for (int k = 0; k < 8; ++k) {
-      d = fmax(d, s_d[k]);
-      m = fmax(m, s_n[k]);
-    }
+    const double d = __longlong_as_double((long long)w.drift_bits[0]);
+    const double m = __longlong_as_double((long long)w.drift_bits[1]);
     const double rel = m > 0.0 ? d / m : 0.0;
     if (rel > w.max_drift) w.max_drift = rel;
+    w.drift_bits[0] = 0ull;
+    w.drift_bits[1] = 0ull;
     w.parity = par ^ 1;
     w.n_recomputes++;
+    w.rec_flops += 2.0 * 2.0 * (double)n * (double)n * (double)n;
     w.recompute_pending = 0;
   }
 }
@@ -158,39 +197,74 @@ __device__ __forceinline__ bool wants_measure(const WalkerDev& w) { return w.act
 
 // gR[sp][r'][j] = g0_sp(r_j - r', tau_j - 0+) ; grid = (blocks, walkers*2)
 __global__ void __launch_bounds__(256) k_meas_gr(Config cfg) {
-  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
-  const WalkerDev& w = cfg.W[wi];
-  if (!wants_measure(w)) return;
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        return wants_measure(w) ? blocks_of((long long)cfg.P[w.problem].nc * w.n, 256) : 0;
+      },
+      [&](int s, int item) {
+  const WalkerDev& w = cfg.W[s >> 1];
+  const int sp = s & 1;
   const ProblemDev& pb = cfg.P[w.problem];
   const int n = w.n, par = w.parity, nc = pb.nc;
   const int total = nc * n;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+  const int idx = item * 256 + threadIdx.x;
+  if (idx < total) {
     const int rp = idx / n, j = idx - rp * n;
     const bool live = w.vs[par][j] != 0;  // a dead column of N is e_j: no contribution
     w.gR[((size_t)sp * nc + rp) * w.cap + j] = live ? g0_pair(pb, sp, w.vsite[par][j], w.vtau[par][j], rp, 0.0) : 0.0;
   }
+      });
 }
 
 // bvec[sp][r'][i] = (e^{V_i} - 1) sum_j N[i][j] gR[sp][r'][j]; one warp per (i, r').
+// b[r'][i] = (e^{V_i} - 1) sum_j N[i][j] gR[r'][j] as a tiled product:
+// one item = 8 rows of N (one warp each); lanes own reference sites r' and
+// r' + 32; chunks of 32 columns of N and gR are staged in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256) k_meas_b(Config cfg) {
-  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
-  const WalkerDev& w = cfg.W[wi];
-  if (!wants_measure(w)) return;
-  const ProblemDev& pb = cfg.P[w.problem];
-  const int n = w.n, par = w.parity, nc = pb.nc, ld = w.cap;
-  const T* N = (const T*)w.N[par][sp];
-  const int lane = threadIdx.x & 31;
-  const int total = nc * n;
-  for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < total; item += (gridDim.x * blockDim.x) >> 5) {
-    const int rp = item / n, i = item - rp * n;
-    const double* g = w.gR + ((size_t)sp * nc + rp) * ld;
-    double acc = 0.0;
-    for (int j = lane; j < n; j += 32) acc += ldN(N, (size_t)i * ld + j) * g[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) w.bvec[((size_t)sp * nc + rp) * ld + i] = (expV(pb, sp, w.vs[par][i]) - 1.0) * acc;
-  }
+  __shared__ double sN[8][33];
+  __shared__ double sG[64][33];
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        return wants_measure(w) ? blocks_of(w.n, 8) : 0;
+      },
+      [&](int s, int item) {
+        const WalkerDev& w = cfg.W[s >> 1];
+        const int sp = s & 1;
+        const ProblemDev& pb = cfg.P[w.problem];
+        const int n = w.n, par = w.parity, nc = pb.nc, ld = w.cap;
+        const T* N = (const T*)w.N[par][sp];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int i = item * 8 + warp;
+        double acc0 = 0.0, acc1 = 0.0;
+        for (int j0 = 0; j0 < n; j0 += 32) {
+          __syncthreads();
+          {
+            const int j = j0 + lane;
+            sN[warp][lane] = (i < n && j < n) ? ldN(N, (size_t)i * ld + j) : 0.0;
+          }
+          for (int e = threadIdx.x; e < 64 * 32; e += 256) {
+            const int rp = e >> 5, jl = e & 31, j = j0 + jl;
+            sG[rp][jl] = (rp < nc && j < n) ? w.gR[((size_t)sp * nc + rp) * ld + j] : 0.0;
+          }
+          __syncthreads();
+#pragma unroll 8
+          for (int jl = 0; jl < 32; ++jl) {
+            const double nij = sN[warp][jl];
+            acc0 += nij * sG[lane][jl];
+            acc1 += nij * sG[lane + 32][jl];
+          }
+        }
+        if (i < n) {
+          const double f = expV(pb, sp, w.vs[par][i]) - 1.0;
+          if (lane < nc) w.bvec[((size_t)sp * nc + lane) * ld + i] = f * acc0;
+          if (lane + 32 < nc) w.bvec[((size_t)sp * nc + lane + 32) * ld + i] = f * acc1;
+        }
+      });
 }
 
 // Correction term as a product: rows (x, tau_a), inner index the vertex i,
@@ -204,15 +278,26 @@ constexpr int MK = 32;   // vertices per step
 constexpr int MR = 64;   // reference sites per block (nc <= 64)
 
 template <typename A>
+__device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp, int item);
+
+template <typename A>
 __global__ void __launch_bounds__(256) k_meas_gemm(Config cfg) {
-  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        return wants_measure(w) ? (long long)cfg.P[w.problem].nc * blocks_of(cfg.n_tau_meas, MT) : 0;
+      },
+      [&](int s, int item) { meas_gemm_item<A>(cfg, s >> 1, s & 1, item); });
+}
+
+template <typename A>
+__device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp, int item) {
   const WalkerDev& w = cfg.W[wi];
-  if (!wants_measure(w)) return;
   const ProblemDev& pb = cfg.P[w.problem];
   const int nc = pb.nc, ntm = cfg.n_tau_meas, n = w.n, par = w.parity, ld = w.cap;
   const int tblocks = (ntm + MT - 1) / MT;
-  const int x = blockIdx.x / tblocks, a0 = (blockIdx.x - x * tblocks) * MT;
-  if (x >= nc) return;
+  const int x = item / tblocks, a0 = (item - x * tblocks) * MT;
   __shared__ A As[MT][MK + 1];
   __shared__ A Bs[MK][MR + 1];
   const int tid = threadIdx.x;
@@ -266,13 +351,20 @@ __global__ void __launch_bounds__(256) k_meas_gemm(Config cfg) {
 // Gacc[sp][dr][a] += sign * (-G), G = g0(dr, tau_a) + Gtmp / Nc; Gtmp cleared.
 // grid = (blocks, walkers), thread per (sp, dr, a).
 __global__ void __launch_bounds__(256) k_meas_acc(Config cfg) {
-  WalkerDev& w = cfg.W[blockIdx.y];
-  if (!wants_measure(w)) return;
+  for_each_item(
+      cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s];
+        return wants_measure(w) ? blocks_of(2LL * cfg.P[w.problem].nc * cfg.n_tau_meas, 256) : 0;
+      },
+      [&](int s, int item) {
+  WalkerDev& w = cfg.W[s];
   const ProblemDev& pb = cfg.P[w.problem];
   const int nc = pb.nc, ntm = cfg.n_tau_meas;
   const int total = 2 * nc * ntm;
   const double sign = w.sign;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+  const int idx = item * 256 + threadIdx.x;
+  if (idx < total) {
     const int sp = idx / (nc * ntm);
     const int rem = idx - sp * nc * ntm;
     const int d = rem / ntm, a = rem - d * ntm;
@@ -282,6 +374,7 @@ __global__ void __launch_bounds__(256) k_meas_acc(Config cfg) {
     w.Gtmp[idx] = 0.0;
     w.Gacc[idx] += sign * (-G);
   }
+      });
 }
 
 __global__ void k_meas_finish(Config cfg) {
@@ -326,29 +419,39 @@ void launch_init(const Config& cfg, int n0, int max_cap, int* d_sgn, cudaStream_
   const int W = cfg.n_walkers;
   k_init_vertices<<<W, 256, 0, st>>>(cfg, n0);
   if (n0 > 0) {
-    k_build_A<<<dim3(build_blocks(n0), 2 * W), 256, 0, st>>>(cfg, 0);
+    const long long g = grid_for(2LL * W * blocks_of((long long)n0 * n0, 256));
+    k_build_A<<<g, 256, 0, st>>>(cfg, 0);
     launch_gj(cfg, 0, n0, d_sgn, st);
-    if (cfg.prec == PREC_MIXED) {
-      const int gb = (n0 * n0 + 255) / 256;
-      k_store_fp32<<<dim3(gb < 1024 ? gb : 1024, 2 * W), 256, 0, st>>>(cfg, 0);
-    }
+    if (cfg.prec == PREC_MIXED) k_store_fp32<<<g, 256, 0, st>>>(cfg, 0);
   }
   k_init_finish<<<(W + 127) / 128, 128, 0, st>>>(cfg, d_sgn);
   (void)max_cap;
 }
 
-int launch_recompute(const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st) {
+int launch_recompute(int part, const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st) {
   const int W = cfg.n_walkers;
-  k_build_A<<<dim3(build_blocks(max_cap), 2 * W), 256, 0, st>>>(cfg, 1);
-  launch_gj(cfg, 1, max_cap, d_sgn, st);
-  if (cfg.prec == PREC_MIXED) {
-    const int gb = (max_cap * max_cap + 255) / 256;
-    k_store_fp32<<<dim3(gb < 1024 ? gb : 1024, 2 * W), 256, 0, st>>>(cfg, 1);
-    k_recompute_finish<float><<<W, 256, 0, st>>>(cfg, d_sgn);
-    return 4;
+  const int g = grid_for(2LL * W * blocks_of((long long)max_cap * max_cap, 256));
+  const int gd = grid_for(2LL * W * blocks_of((long long)max_cap * max_cap, 2048));
+  switch (part) {
+    case GROUP_RECOMPUTE_PRE:
+      k_build_A<<<g, 256, 0, st>>>(cfg, 1);
+      return 1;
+    case GROUP_RECOMPUTE:
+      launch_gj(cfg, 1, max_cap, d_sgn, st);
+      return 1;
+    case GROUP_RECOMPUTE_POST:
+      if (cfg.prec == PREC_MIXED) {
+        k_store_fp32<<<g, 256, 0, st>>>(cfg, 1);
+        k_recompute_drift<float><<<gd, 256, 0, st>>>(cfg);
+        k_recompute_adopt<<<W, 256, 0, st>>>(cfg);
+        return 3;
+      }
+      k_recompute_drift<double><<<gd, 256, 0, st>>>(cfg);
+      k_recompute_adopt<<<W, 256, 0, st>>>(cfg);
+      return 2;
+    default:
+      return 0;
   }
-  k_recompute_finish<double><<<W, 256, 0, st>>>(cfg, d_sgn);
-  return 3;
 }
 
 // From-scratch N for the vertex list held in the current buffer of every walker
@@ -356,7 +459,7 @@ int launch_recompute(const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st
 void launch_fresh_inverse(const Config& cfg, int max_n, int* d_sgn, cudaStream_t st) {
   const int W = cfg.n_walkers;
   if (max_n <= 0) return;
-  k_build_A<<<dim3(build_blocks(max_n), 2 * W), 256, 0, st>>>(cfg, 0);
+  k_build_A<<<grid_for(2LL * W * blocks_of((long long)max_n * max_n, 256)), 256, 0, st>>>(cfg, 0);
   launch_gj(cfg, 0, max_n, d_sgn, st);
 }
 
@@ -371,22 +474,18 @@ void launch_negate(const double* src, double* dst, size_t n, cudaStream_t st) {
 
 int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) {
   const int W = cfg.n_walkers;
-  const int items = max_nc * max_cap;
-  int gb = (items + 255) / 256;
-  gb = gb < 1024 ? gb : 1024;
-  k_meas_gr<<<dim3(gb, 2 * W), 256, 0, st>>>(cfg);
-  int gw = (items * 32 + 255) / 256;
-  gw = gw < 2048 ? gw : 2048;
-  if (cfg.prec == PREC_MIXED) k_meas_b<float><<<dim3(gw, 2 * W), 256, 0, st>>>(cfg);
-  else k_meas_b<double><<<dim3(gw, 2 * W), 256, 0, st>>>(cfg);
-  const int mblocks = max_nc * ((cfg.n_tau_meas + MT - 1) / MT);
-  if (cfg.prec == PREC_MIXED) k_meas_gemm<float><<<dim3(mblocks, 2 * W), 256, 0, st>>>(cfg);
-  else k_meas_gemm<double><<<dim3(mblocks, 2 * W), 256, 0, st>>>(cfg);
-  const int outs = 2 * max_nc * cfg.n_tau_meas;
-  int ga = (outs + 255) / 256;
-  ga = ga < 1024 ? ga : 1024;
-  k_meas_acc<<<dim3(ga, W), 256, 0, st>>>(cfg);
+  const long long S = 2LL * W;
+  k_meas_gr<<<grid_for(S * blocks_of((long long)max_nc * max_cap, 256)), 256, 0, st>>>(cfg);
+  const int gb = grid_for(S * blocks_of(max_cap, 8));
+  if (cfg.prec == PREC_MIXED) k_meas_b<float><<<gb, 256, 0, st>>>(cfg);
+  else k_meas_b<double><<<gb, 256, 0, st>>>(cfg);
+  const int gg = grid_for(S * max_nc * blocks_of(cfg.n_tau_meas, MT));
+  if (cfg.prec == PREC_MIXED) k_meas_gemm<float><<<gg, 256, 0, st>>>(cfg);
+  else k_meas_gemm<double><<<gg, 256, 0, st>>>(cfg);
+  k_meas_acc<<<grid_for((long long)W * blocks_of(2LL * max_nc * cfg.n_tau_meas, 256)), 256, 0, st>>>(cfg);
   k_meas_finish<<<(W + 127) / 128, 128, 0, st>>>(cfg);
+  (void)max_cap;
+  (void)max_nc;
   return 5;
 }
 

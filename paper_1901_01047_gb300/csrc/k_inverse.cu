@@ -39,18 +39,30 @@ __device__ __forceinline__ bool gj_better(double m1, int i1, double m2, int i2) 
   return m1 > m2 || (m1 == m2 && i1 < i2);
 }
 
+__device__ void gj_matrix(const Config& cfg, int mode, int mat, int* sgn_out, cg::cluster_group& cluster);
+
 // mode 0: initial build / standalone; mode 1: periodic recompute.
-// grid = (GJ_CTAS * walkers * 2), cluster = GJ_CTAS; dynamic shared memory:
-// one int per matrix row (pivot rows).
+// Persistent grid of clusters: cluster k inverts matrices k, k + clusters, ...
+// (matrix = walker * 2 + spin) that need it; dynamic shared memory: one int
+// per matrix row (pivot rows).
 __global__ void __cluster_dims__(GJ_CTAS, 1, 1) __launch_bounds__(GJ_THREADS)
     k_gj_cluster(Config cfg, int mode, int* sgn_out) {
   cg::cluster_group cluster = cg::this_cluster();
+  const int clusters = gridDim.x / GJ_CTAS;
+  for (int mat = blockIdx.x / GJ_CTAS; mat < 2 * cfg.n_walkers; mat += clusters) {
+    const WalkerDev& w = cfg.W[mat >> 1];
+    // uniform over the cluster: no barrier is skipped by a subset of its blocks
+    const bool want = mode == 0 ? true : (w.active && w.recompute_pending && w.status == ST_OK);
+    if (!want) continue;
+    gj_matrix(cfg, mode, mat, sgn_out, cluster);
+    cluster.sync();  // the next matrix reuses the shared posts and pivots
+  }
+}
+
+__device__ void gj_matrix(const Config& cfg, int mode, int mat, int* sgn_out, cg::cluster_group& cluster) {
   const int rank = (int)cluster.block_rank();
-  const int mat = blockIdx.x / GJ_CTAS;  // walker * 2 + spin
   const int wi = mat >> 1, sp = mat & 1;
   WalkerDev& w = cfg.W[wi];
-  const bool want = mode == 0 ? true : (w.active && w.recompute_pending && w.status == ST_OK);
-  if (!want) return;  // uniform over the cluster: no barrier is skipped by a subset
   const int n = w.n, ld = w.cap;
   double* A = (cfg.prec == PREC_MIXED) ? w.Ascr[sp] : (double*)w.N[mode == 0 ? w.parity : w.parity ^ 1][sp];
   extern __shared__ int s_piv[];
@@ -168,7 +180,10 @@ void launch_gj(const Config& cfg, int mode, int max_n, int* d_sgn, cudaStream_t 
     cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     configured = smem;
   }
-  k_gj_cluster<<<GJ_CTAS * 2 * cfg.n_walkers, GJ_THREADS, smem, st>>>(cfg, mode, d_sgn);
+  // one cluster of GJ_CTAS blocks per GJ_CTAS SMs, at most one per matrix
+  const int mats = 2 * cfg.n_walkers, fit = 152 / GJ_CTAS;
+  const int clusters = mats < fit ? mats : fit;
+  k_gj_cluster<<<GJ_CTAS * clusters, GJ_THREADS, smem, st>>>(cfg, mode, d_sgn);
 }
 
 }  // namespace dca

@@ -1,0 +1,440 @@
+// k_update_tc.cu -- the rank-l update of the FP32 N matrices (mixed
+// precision) on the 5th-generation tensor cores:
+//     N[0:n, 0:n) += L' R,   L' = (G[:,P] - E_P) diag(a_P) B^-1  (n x l),
+//                             R  = N_ext[P, 0:n)                  (l x n),
+// the submatrix update of the DCA++ paper (Sec. 2.3, "Submatrix updates").
+//
+// Precision (3xTF32).  Every FP32 operand x is split into hi = x rounded to
+// TF32 and lo = x - hi (exact); the MMA chain accumulates hi*hi + hi*lo +
+// lo*hi in FP32 in tensor memory, about 22 bits of every product, close to
+// an FP32 product.  The split operands are written by k_upd_ops in the
+// layout the TMA loads: planes [hi | lo] x rows x 128 K-columns (512 B rows).
+//
+// Work item = one 128-row block of one walker-spin N.  A CTA (one per SM)
+// loads the block's L' rows (hi, lo; K = l rounded up to 32) once, then walks
+// the 128 x BN column tiles of those rows through a two-stage pipeline:
+//   warp 4 (TMA producer)  B operand rows (R^T hi, lo) and the N tile;
+//   warp 5 (MMA issuer)    3 l/8 tcgen05.mma kind::tf32 into one of two TMEM
+//                          accumulators (M = 128, N = BN);
+//   warps 0-3 (epilogue)   TMEM -> registers, add into the N tile held in
+//                          shared memory (128-byte swizzle), TMA store.
+// Rows or columns >= n are stored back unchanged.
+#include <cuda.h>
+
+#include <cstdint>
+
+#include "device_util.cuh"
+#include "kernels.h"
+#include "state.h"
+#include "tc_ptx.cuh"
+
+namespace dca {
+
+constexpr int TC_BM = 128;
+constexpr int TC_KS = 128;  // K columns per operand row in global memory (KS_MAX)
+
+template <int BN, int KP>
+struct TcLayout {
+  static constexpr int KCH = KP / 32;                 // 32-column (128-byte) K chunks
+  static constexpr int A_CHUNK = TC_BM * 128;         // one chunk of one plane
+  static constexpr int A_PLANE = KCH * A_CHUNK;
+  static constexpr int B_CHUNK = BN * 128;
+  static constexpr int B_PLANE = KCH * B_CHUNK;
+  static constexpr int B_STAGE = 2 * B_PLANE;
+  static constexpr int N_BOX = TC_BM * 128;           // 128 rows x 32 columns
+  static constexpr int N_STAGE = (BN / 32) * N_BOX;
+  static constexpr int OFF_A = 0;
+  static constexpr int OFF_B = 2 * A_PLANE;
+  static constexpr int OFF_N = OFF_B + 2 * B_STAGE;
+  static constexpr int OFF_BAR = OFF_N + 2 * N_STAGE;
+  static constexpr int SMEM = OFF_BAR + 128 + 1024;   // barriers, TMEM slot, flag; 1 KB alignment slack
+  static constexpr uint32_t TMEM_COLS = 2 * BN;
+  static_assert(BN % 32 == 0 && BN >= 32 && BN <= 128, "tile width");
+  static_assert(SMEM <= 232448, "shared memory");
+};
+
+// Work items: (walker-spin s, 128-row block) for walkers with an update.
+__device__ __forceinline__ long long tc_items(const Config& cfg, int s) {
+  const WalkerDev& w = cfg.W[s >> 1];
+  return (w.active && w.n_acc > 0) ? (long long)((w.n + TC_BM - 1) / TC_BM) : 0;
+}
+
+// Deterministic walk over the items of this CTA (the same in every role).
+struct TcIter {
+  int s = 0;
+  long long base = 0, cnt = 0, item;
+  __device__ bool next(const Config& cfg, int& set, int& rb) {
+    const int nsets = 2 * cfg.n_walkers;
+    while (item >= base + cnt) {
+      base += cnt;
+      if (++s >= nsets) return false;
+      cnt = tc_items(cfg, s);
+    }
+    set = s;
+    rb = (int)(item - base);
+    item += gridDim.x;
+    return true;
+  }
+  __device__ void start(const Config& cfg) {
+    s = 0;
+    base = 0;
+    cnt = 2 * cfg.n_walkers > 0 ? tc_items(cfg, 0) : 0;
+    item = blockIdx.x;
+    if (2 * cfg.n_walkers <= 0) s = 1 << 30;
+  }
+};
+
+__device__ __forceinline__ const void* tc_map(const Config& cfg, int wi, int sp, int kind) {
+  return (const void*)(cfg.tmaps + ((size_t)wi * 2 + sp) * 4 + kind);
+}
+
+template <int BN, int KP>
+__global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
+  using L = TcLayout<BN, KP>;
+  extern __shared__ uint8_t tc_raw[];
+  const uint32_t raw = tc::smem_u32(tc_raw);
+  const uint32_t sb = (raw + 1023u) & ~1023u;  // 1024-byte aligned base (128-byte swizzle atoms)
+  uint8_t* gb = tc_raw + (sb - raw);
+  const uint32_t bar = sb + L::OFF_BAR;
+  const uint32_t a_full = bar, a_empty = bar + 8, fin = bar + 16;
+  const uint32_t full0 = bar + 24, mdone0 = bar + 40, empty0 = bar + 56;  // [2] each, 8 bytes apart
+  uint32_t* tmem_slot = (uint32_t*)(gb + L::OFF_BAR + 72);
+  volatile int* abort_flag = (volatile int*)(gb + L::OFF_BAR + 76);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    tc::mbar_init(a_full, 1);
+    tc::mbar_init(a_empty, 1);
+    tc::mbar_init(fin, 1);
+    for (int s = 0; s < 2; ++s) {
+      tc::mbar_init(full0 + 8 * s, 1);
+      tc::mbar_init(mdone0 + 8 * s, 1);
+      tc::mbar_init(empty0 + 8 * s, 1);
+    }
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 5) {
+    tc::tmem_alloc(tc::smem_u32(tmem_slot), L::TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      TcIter it;
+      it.start(cfg);
+      uint32_t g = 0, k = 0;
+      uint32_t armed[2] = {0u, 0u};  // uses of each stage armed so far
+      int set = 0, rb = 0;
+      bool ok = true;
+      while (ok && it.next(cfg, set, rb)) {
+        const WalkerDev& w = cfg.W[set >> 1];
+        const int wi = set >> 1, sp = set & 1;
+        const int n = w.n, l = w.n_acc, kch = (l + 31) >> 5, i0 = rb * TC_BM, cap = w.cap;
+        const void* mA = tc_map(cfg, wi, sp, 0);
+        const void* mB = tc_map(cfg, wi, sp, 1);
+        const void* mN = tc_map(cfg, wi, sp, 2 + w.parity);
+        if (k > 0 && !tc::mbar_wait(a_empty, (k - 1) & 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc::mbar_expect_tx(a_full, (uint32_t)(kch * 2 * L::A_CHUNK));
+        for (int c = 0; c < kch; ++c)
+          for (int h = 0; h < 2; ++h)
+            tc::tma_load_2d(sb + L::OFF_A + h * L::A_PLANE + c * L::A_CHUNK, mA, 32 * c, h * cap + i0, a_full);
+        ++k;
+        const int ntiles = (n + BN - 1) / BN;
+        for (int t = 0; t < ntiles; ++t, ++g) {
+          const int st = (int)(g & 1u);
+          const uint32_t u = g >> 1;
+          if (u > 0 && !tc::mbar_wait(empty0 + 8 * st, (u - 1) & 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const int j0 = t * BN;
+          const uint32_t sB = sb + L::OFF_B + st * L::B_STAGE, sN = sb + L::OFF_N + st * L::N_STAGE;
+          tc::mbar_expect_tx(full0 + 8 * st, (uint32_t)(kch * 2 * L::B_CHUNK + L::N_STAGE));
+          armed[st] = u + 1;
+          for (int c = 0; c < kch; ++c)
+            for (int h = 0; h < 2; ++h)
+              tc::tma_load_2d(sB + h * L::B_PLANE + c * L::B_CHUNK, mB, 32 * c, h * cap + j0, full0 + 8 * st);
+          for (int b = 0; b < BN / 32; ++b) tc::tma_load_2d(sN + b * L::N_BOX, mN, j0 + 32 * b, i0, full0 + 8 * st);
+        }
+      }
+      if (!ok) {
+        cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+        // the loads already issued land before the CTA exits
+        if (k > 0) tc::mbar_wait(a_full, (k - 1) & 1u, nullptr, 400000000LL);
+        for (int st = 0; st < 2; ++st)
+          if (armed[st] > 0) tc::mbar_wait(full0 + 8 * st, (armed[st] - 1) & 1u, nullptr, 400000000LL);
+      }
+    }
+  } else if (warp == 5) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      TcIter it;
+      it.start(cfg);
+      uint32_t g = 0, k = 0;
+      int set = 0, rb = 0;
+      bool ok = true;
+      const uint32_t idesc = tc::idesc_tf32(TC_BM, BN);
+      while (ok && it.next(cfg, set, rb)) {
+        const WalkerDev& w = cfg.W[set >> 1];
+        const int n = w.n, steps = (w.n_acc + 7) >> 3;
+        if (!tc::mbar_wait(a_full, k & 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t aH = sb + L::OFF_A, aL = aH + L::A_PLANE;
+        const int ntiles = (n + BN - 1) / BN;
+        for (int t = 0; t < ntiles; ++t, ++g) {
+          const int st = (int)(g & 1u);
+          const uint32_t u = g >> 1;
+          if ((u > 0 && !tc::mbar_wait(empty0 + 8 * st, (u - 1) & 1u, abort_flag)) ||
+              !tc::mbar_wait(full0 + 8 * st, u & 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t d = tmem + (uint32_t)(st * BN);
+          const uint32_t bH = sb + L::OFF_B + st * L::B_STAGE, bL = bH + L::B_PLANE;
+          for (int q = 0; q < steps; ++q) {
+            // K step q: chunk q / 4, 32-byte offset (q % 4) inside the 128-byte swizzle row
+            const uint32_t ao = (uint32_t)((q >> 2) * L::A_CHUNK + (q & 3) * 32);
+            const uint32_t bo = (uint32_t)((q >> 2) * L::B_CHUNK + (q & 3) * 32);
+            const uint64_t ah = tc::sdesc_k_sw128(aH + ao), al = tc::sdesc_k_sw128(aL + ao);
+            const uint64_t bh = tc::sdesc_k_sw128(bH + bo), bl = tc::sdesc_k_sw128(bL + bo);
+            tc::mma_tf32(d, ah, bh, idesc, q > 0 ? 1u : 0u);
+            tc::mma_tf32(d, ah, bl, idesc, 1u);
+            tc::mma_tf32(d, al, bh, idesc, 1u);
+          }
+          tc::mma_commit(mdone0 + 8 * st);
+        }
+        if (!ok) break;
+        tc::mma_commit(a_empty);
+        ++k;
+      }
+      if (!ok) cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+      // every MMA of this CTA has completed before the tensor memory is freed
+      tc::mma_commit(fin);
+      tc::mbar_wait(fin, 0u, nullptr, 400000000LL);
+    }
+  } else {
+    // ---------------- epilogue: warps 0-3, TMEM lanes 32 warp .. +31 ----------------
+    TcIter it;
+    it.start(cfg);
+    uint32_t g = 0;
+    int set = 0, rb = 0;
+    bool stop = false;
+    const int r = 32 * warp + lane;  // row of the block = TMEM lane
+    while (!stop && it.next(cfg, set, rb)) {
+      const WalkerDev& w = cfg.W[set >> 1];
+      const int wi = set >> 1, sp = set & 1, n = w.n, i0 = rb * TC_BM;
+      const void* mN = tc_map(cfg, wi, sp, 2 + w.parity);
+      const bool row_ok = i0 + r < n;
+      const int ntiles = (n + BN - 1) / BN;
+      for (int t = 0; t < ntiles; ++t, ++g) {
+        const int st = (int)(g & 1u);
+        const uint32_t u = g >> 1;
+        const int j0 = t * BN;
+        // every lane waits; the warp proceeds only if all lanes saw both phases
+        // complete (tcgen05.ld is warp-wide)
+        const bool mine =
+            tc::mbar_wait(full0 + 8 * st, u & 1u, abort_flag) && tc::mbar_wait(mdone0 + 8 * st, u & 1u, abort_flag);
+        const bool okw = __all_sync(0xffffffffu, mine);
+        if (okw) {
+          tc::fence_after_sync();
+          uint8_t* tile = gb + L::OFF_N + st * L::N_STAGE;
+#pragma unroll 1
+          for (int b = 0; b < BN / 32; ++b) {
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(st * BN + 32 * b), v);
+            uint8_t* rowp = tile + b * L::N_BOX + r * 128;
+            const int cb = j0 + 32 * b;
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) {
+              float4* p = (float4*)(rowp + ((ch ^ (r & 7)) << 4));
+              float4 x = *p;
+              const int c = cb + 4 * ch;
+              if (row_ok) {
+                if (c < n) x.x += v[4 * ch];
+                if (c + 1 < n) x.y += v[4 * ch + 1];
+                if (c + 2 < n) x.z += v[4 * ch + 2];
+                if (c + 3 < n) x.w += v[4 * ch + 3];
+              }
+              *p = x;
+            }
+          }
+          tc::fence_before_sync();
+          tc::fence_async_smem();
+        }
+        // uniform decision of the 128 epilogue threads
+        stop = tc::named_bar_or(1, 128, !okw || *abort_flag != 0);
+        if (stop) break;
+        if (threadIdx.x == 0) {
+          for (int b = 0; b < BN / 32; ++b)
+            tc::tma_store_2d(mN, j0 + 32 * b, i0, sb + L::OFF_N + st * L::N_STAGE + b * L::N_BOX);
+          tc::bulk_commit();
+          tc::bulk_wait_read0();
+          tc::mbar_arrive(empty0 + 8 * st);
+        }
+      }
+    }
+    if (stop && threadIdx.x == 0) cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+    if (threadIdx.x == 0) tc::bulk_wait0();
+  }
+  __syncthreads();
+  if (warp == 5) {
+    __syncwarp();
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, L::TMEM_COLS);
+  }
+}
+
+// Split operands of the tensor-core update, written in the TMA layout
+// [plane hi | lo][cap rows][TC_KS columns] (FP32):
+//   A rows i < n:  L'[i, p]          (p < l; zero for l <= p < lpad)
+//   B rows j < n:  R[p, j] = N[P_p, j] (transposed through shared memory)
+// lpad = l rounded up to 32 (the K extent of the loaded chunks).
+// Persistent grid over walker-spin pairs; per pair the items are the A
+// blocks (256 entries each) followed by the B blocks (32 rows of B each).
+__global__ void __launch_bounds__(256) k_upd_ops(Config cfg) {
+  __shared__ float s_t[TC_KS][33];
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        if (!(w.active && w.n_acc > 0)) return 0;
+        const int lpad = (w.n_acc + 31) & ~31;
+        return blocks_of((long long)w.n * lpad, 256) + (w.n + 31) / 32;
+      },
+      [&](int s, int item) {
+        const WalkerDev& w = cfg.W[s >> 1];
+        const int sp = s & 1, n = w.n, l = w.n_acc, cap = w.cap;
+        const int lpad = (l + 31) & ~31;
+        const int a_blocks = (int)blocks_of((long long)n * lpad, 256);
+        if (item < a_blocks) {
+          const long long idx = (long long)item * 256 + threadIdx.x;
+          if (idx < (long long)n * lpad) {
+            const int i = (int)(idx / lpad), p = (int)(idx - (long long)i * lpad);
+            const float x = p < l ? (float)w.Lp[sp][(size_t)i * KS_MAX + p] : 0.0f;
+            float hi, lo;
+            tc::tf32_split(x, hi, lo);
+            w.Aop[sp][(size_t)i * TC_KS + p] = hi;
+            w.Aop[sp][((size_t)cap + i) * TC_KS + p] = lo;
+          }
+        } else {
+          const int j0 = (item - a_blocks) * 32;
+          const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+          const float* Rr = (const float*)w.Rr[sp];
+          for (int p = warp; p < lpad; p += 8)
+            s_t[p][lane] = (p < l && j0 + lane < n) ? Rr[(size_t)p * cap + j0 + lane] : 0.0f;
+          __syncthreads();
+          for (int jj = warp; jj < 32; jj += 8) {
+            const int j = j0 + jj;
+            if (j < n)
+              for (int p = lane; p < lpad; p += 32) {
+                float hi, lo;
+                tc::tf32_split(s_t[p][jj], hi, lo);
+                w.Bop[sp][(size_t)j * TC_KS + p] = hi;
+                w.Bop[sp][((size_t)cap + j) * TC_KS + p] = lo;
+              }
+          }
+          __syncthreads();
+        }
+      });
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+template <int BN, int KP>
+static cudaError_t tc_setup_one() {
+  return cudaFuncSetAttribute(k_upd_tc<BN, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcLayout<BN, KP>::SMEM);
+}
+
+cudaError_t setup_update_tc() {
+  cudaError_t e = tc_setup_one<64, 32>();
+  if (e == cudaSuccess) e = tc_setup_one<64, 64>();
+  if (e == cudaSuccess) e = tc_setup_one<32, 128>();
+  return e;
+}
+
+int tc_tile_n(int ks) { return ks <= 64 ? 64 : 32; }
+
+static int g_num_sms = 0;
+
+void launch_upd_ops(const Config& cfg, cudaStream_t st) {
+  const long long S = 2LL * cfg.n_walkers;
+  long long items = S * 64;
+  if (items > 4 * 152) items = 4 * 152;
+  k_upd_ops<<<(int)(items < 1 ? 1 : items), 256, 0, st>>>(cfg);
+}
+
+void launch_upd_tc(const Config& cfg, cudaStream_t st) {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g_num_sms <= 0)
+      g_num_sms = 152;
+  }
+  const int grid = g_num_sms;
+  if (cfg.ks <= 32)
+    k_upd_tc<64, 32><<<grid, 192, TcLayout<64, 32>::SMEM, st>>>(cfg);
+  else if (cfg.ks <= 64)
+    k_upd_tc<64, 64><<<grid, 192, TcLayout<64, 64>::SMEM, st>>>(cfg);
+  else
+    k_upd_tc<32, 128><<<grid, 192, TcLayout<32, 128>::SMEM, st>>>(cfg);
+}
+
+// Tensor maps of walker wi, spin sp: A operand, B operand, N of parity 0 and
+// 1 (FP32, 128-byte swizzle, boxes of 32 columns).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+static bool encode_2d(TmapDev* out, void* base, uint64_t cols, uint64_t rows, uint64_t row_bytes, uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {row_bytes};
+  const cuuint32_t box[2] = {32u, box_rows};
+  const cuuint32_t estr[2] = {1u, 1u};
+  static_assert(sizeof(TmapDev) == sizeof(CUtensorMap), "tensor map size");
+  return fn(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_update_maps(const WalkerDev& w, int ks, TmapDev* out4x2) {
+  const uint64_t C = (uint64_t)w.cap;
+  const uint32_t bn = (uint32_t)tc_tile_n(ks);
+  for (int sp = 0; sp < 2; ++sp) {
+    TmapDev* m = out4x2 + 4 * sp;
+    if (!encode_2d(m + 0, w.Aop[sp], TC_KS, 2 * C, TC_KS * 4, TC_BM)) return false;
+    if (!encode_2d(m + 1, w.Bop[sp], TC_KS, 2 * C, TC_KS * 4, bn)) return false;
+    for (int par = 0; par < 2; ++par)
+      if (!encode_2d(m + 2 + par, w.N[par][sp], C, C, C * 4, TC_BM)) return false;
+  }
+  return true;
+}
+
+}  // namespace dca

@@ -131,28 +131,63 @@ constexpr int METRO_SMEM_KS = 96;  // largest k_s whose B^-1 (both spins) lives 
 constexpr int ET = 64;   // tile of the extension kernel
 constexpr int EC = 32;   // candidates per pass
 
+// Persistent grid; one item = 256 entries (c, j) of one walker-spin: clears
+// the reduction targets Gc / Xr and tabulates the candidate factors V and U
+// once per window (the tile kernel then reads them instead of interpolating).
 __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
-  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
-  const WalkerDev& w = cfg.W[wi];
-  if (!w.active || w.n_cand == 0) return;
-  const int nc_ = w.n_cand, n = w.n, ld = w.cap;
-  const int total = nc_ * n;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const int c = idx / n, i = idx - c * n;
-    w.Gc[sp][(size_t)c * ld + i] = 0.0;
-    w.Xr[sp][(size_t)c * ld + i] = 0.0;
-  }
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        return (w.active && w.n_cand > 0) ? blocks_of((long long)w.n_cand * w.n, 256) : 0;
+      },
+      [&](int s, int item) {
+        const WalkerDev& w = cfg.W[s >> 1];
+        const int sp = s & 1, n = w.n, ld = w.cap;
+        const int idx = item * 256 + threadIdx.x;
+        if (idx < w.n_cand * n) {
+          const int c = idx / n, i = idx - c * n;
+          const size_t o = (size_t)c * ld + i;
+          w.Gc[sp][o] = 0.0;
+          w.Xr[sp][o] = 0.0;
+          const ProblemDev& pb = cfg.P[w.problem];
+          const int par = w.parity;
+          const int si = w.vs[par][i], ri = w.vsite[par][i], rc = w.vsite[par][n + c];
+          const double ti = w.vtau[par][i], tc = w.vtau[par][n + c];
+          double v = 0.0, u = 0.0;
+          if (si != 0) {
+            v = g0_pair(pb, sp, ri, ti, rc, tc);
+            u = g0_pair(pb, sp, rc, tc, ri, ti) * (expV(pb, sp, si) - 1.0);
+          }
+          w.Vb[sp][o] = v;
+          w.Ub[sp][o] = u;
+        }
+      });
 }
 
 template <typename T, typename A>
-__global__ void __launch_bounds__(256) k_cand_ext(Config cfg, int tiles) {
-  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
+__device__ __forceinline__ void cand_ext_tile(const Config& cfg, int wi, int sp, int tile);
+
+// Persistent grid over (walker-spin, 64 x 64 tile of N).
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) k_cand_ext(Config cfg) {
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        const long long t = (w.n + ET - 1) / ET;
+        return (w.active && w.n_cand > 0) ? t * t : 0;
+      },
+      [&](int s, int item) { cand_ext_tile<T, A>(cfg, s >> 1, s & 1, item); });
+}
+
+template <typename T, typename A>
+__device__ __forceinline__ void cand_ext_tile(const Config& cfg, int wi, int sp, int tile) {
   const WalkerDev& w = cfg.W[wi];
-  if (!w.active || w.n_cand == 0) return;
   const int n = w.n, nc_ = w.n_cand;
-  const int ti = blockIdx.x / tiles, tj = blockIdx.x - ti * tiles;
+  const int tiles = (n + ET - 1) / ET;
+  const int ti = tile / tiles, tj = tile - ti * tiles;
   const int i0 = ti * ET, j0 = tj * ET;
-  if (i0 >= n || j0 >= n) return;
   const ProblemDev& pb = cfg.P[w.problem];
   const int ld = w.cap, par = w.parity;
   const T* __restrict__ N = (const T*)w.N[par][sp];
@@ -164,6 +199,7 @@ __global__ void __launch_bounds__(256) k_cand_ext(Config cfg, int tiles) {
   A(*Vs)[EC + 1] = reinterpret_cast<A(*)[EC + 1]>(Ns + ET);                   // [j][c]
   A(*Us)[ET + 1] = reinterpret_cast<A(*)[ET + 1]>(Vs + ET);                   // [c][i]
   const int tid = threadIdx.x;
+  __syncthreads();  // the previous tile of this block is done with Ns
   for (int e = tid; e < ET * ET; e += 256) {
     const int r = e / ET, cc = e - r * ET;
     const int i = i0 + r, j = j0 + cc;
@@ -173,16 +209,11 @@ __global__ void __launch_bounds__(256) k_cand_ext(Config cfg, int tiles) {
   for (int cb = 0; cb < nc_; cb += EC) {
     __syncthreads();
     for (int e = tid; e < ET * EC; e += 256) {
-      const int r = e / EC, c = e - r * EC;
-      const int j = j0 + r, cg = cb + c;
-      double v = 0.0;
-      if (j < n && cg < nc_ && vs[j] != 0) v = g0_pair(pb, sp, vsite[j], vtau[j], vsite[n + cg], vtau[n + cg]);
-      Vs[r][c] = (A)v;
-      const int i = i0 + r;
-      double u = 0.0;
-      if (i < n && cg < nc_ && vs[i] != 0)
-        u = g0_pair(pb, sp, vsite[n + cg], vtau[n + cg], vsite[i], vtau[i]) * (expV(pb, sp, vs[i]) - 1.0);
-      Us[c][r] = (A)u;
+      const int r = e & (ET - 1), c = e >> 6;  // r fastest: coalesced rows of V and U
+      const int j = j0 + r, i = i0 + r, cg = cb + c;
+      const bool okc = cg < nc_;
+      Vs[r][c] = (A)((okc && j < n) ? w.Vb[sp][(size_t)cg * ld + j] : 0.0);
+      Us[c][r] = (A)((okc && i < n) ? w.Ub[sp][(size_t)cg * ld + i] : 0.0);
     }
     __syncthreads();
     A g[EC / 4], x[EC / 4];
@@ -217,13 +248,21 @@ constexpr int ext_smem_bytes() {
 
 // G_ext[n+c', n+c] = X[c',:] . g0[:, c] + g0(r_c' - r_c, tau_c' - tau_c).
 // grid = (KS_MAX candidates c, walkers * 2); block = 128 (4 warps over c').
+__device__ __forceinline__ void cand_cc_item(const Config& cfg, int wi, int sp, int c);
+
 __global__ void __launch_bounds__(128) k_cand_cc(Config cfg) {
-  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        return w.active ? w.n_cand : 0;
+      },
+      [&](int s, int c) { cand_cc_item(cfg, s >> 1, s & 1, c); });
+}
+
+__device__ __forceinline__ void cand_cc_item(const Config& cfg, int wi, int sp, int c) {
   const WalkerDev& w = cfg.W[wi];
-  if (!w.active) return;
-  const int c = blockIdx.x;
   const int n = w.n, nc_ = w.n_cand;
-  if (c >= nc_) return;
   const ProblemDev& pb = cfg.P[w.problem];
   const int ld = w.cap, par = w.parity;
   const int* vsite = w.vsite[par];
@@ -240,7 +279,7 @@ __global__ void __launch_bounds__(128) k_cand_cc(Config cfg) {
     __syncthreads();
     for (int t = threadIdx.x; t < 1024; t += 128) {
       const int j = j0 + t;
-      v[t] = (j < n && vs[j] != 0) ? g0_pair(pb, sp, vsite[j], vtau[j], rc, tc) : 0.0;
+      v[t] = j < n ? w.Vb[sp][(size_t)c * ld + j] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -577,14 +616,21 @@ __device__ __forceinline__ int upd_row(const WalkerDev& w, int t) { return t < w
 // Lrow[x, p] = (G_ext[x, P_p] - delta) a_p ; grid = (row blocks, walkers*2), block 256
 template <typename T>
 __global__ void __launch_bounds__(256) k_upd_lrow(Config cfg) {
-  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
-  const WalkerDev& w = cfg.W[wi];
-  if (!upd_active(w)) return;
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        return upd_active(w) ? blocks_of((long long)(w.n + w.n_ins) * w.n_acc, 256) : 0;
+      },
+      [&](int s, int item) {
+  const WalkerDev& w = cfg.W[s >> 1];
+  const int sp = s & 1;
   const ProblemDev& pb = cfg.P[w.problem];
   const int l = w.n_acc, rows = w.n + w.n_ins;
   const ExtView<T> v = make_view<T>(w, sp);
   const int total = rows * l;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+  const int idx = item * 256 + threadIdx.x;
+  if (idx < total) {
     const int t = idx / l, p = idx - t * l;
     const int x = upd_row(w, t), P = w.P[p];
     const double a = w.aP[sp][p];
@@ -592,47 +638,73 @@ __global__ void __launch_bounds__(256) k_upd_lrow(Config cfg) {
     if (a != 0.0 && !(x < w.n && v.vs[x] == 0)) val = (g_ext(v, pb, sp, x, P) - (x == P ? 1.0 : 0.0)) * a;
     w.Lrow[sp][(size_t)x * KS_MAX + p] = val;
   }
+      });
 }
 
 // Lp = Lrow Binv on the same rows ; Rr[p, j] = N_ext[P_p, j] for j < n,
 // stored in the arithmetic type A of the update product
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_upd_lp_rr(Config cfg) {
-  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
-  const WalkerDev& w = cfg.W[wi];
-  if (!upd_active(w)) return;
-  const int l = w.n_acc, n = w.n, rows = n + w.n_ins;
-  const ExtView<T> v = make_view<T>(w, sp);
-  const double* Bi = w.Binv[sp];
-  int total = rows * l;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const int t = idx / l, p = idx - t * l;
-    const int x = upd_row(w, t);
-    const double* Lr = w.Lrow[sp] + (size_t)x * KS_MAX;
-    double acc = 0.0;
-    for (int q = 0; q < l; ++q) acc += Lr[q] * Bi[(size_t)q * KS_MAX + p];
-    w.Lp[sp][(size_t)x * KS_MAX + p] = acc;
-  }
-  A* Rr = (A*)w.Rr[sp];
-  total = l * n;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const int p = idx / n, j = idx - p * n;
-    const int P = w.P[p];
-    const double r = P < n ? ldN(v.N, (size_t)P * v.ld + j) : v.X[(size_t)(P - n) * v.ld + j];
-    Rr[(size_t)p * w.cap + j] = (A)r;
-  }
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        if (!upd_active(w)) return 0;
+        return blocks_of((long long)(w.n + w.n_ins) * w.n_acc, 256) + blocks_of((long long)w.n_acc * w.n, 256);
+      },
+      [&](int s, int item) {
+        const WalkerDev& w = cfg.W[s >> 1];
+        const int sp = s & 1;
+        const int l = w.n_acc, n = w.n, rows = n + w.n_ins;
+        const int lp_blocks = (int)blocks_of((long long)rows * l, 256);
+        if (item < lp_blocks) {
+          const int idx = item * 256 + threadIdx.x;
+          if (idx < rows * l) {
+            const int t = idx / l, p = idx - t * l;
+            const int x = upd_row(w, t);
+            const double* Lr = w.Lrow[sp] + (size_t)x * KS_MAX;
+            const double* Bi = w.Binv[sp];
+            double acc = 0.0;
+            for (int q = 0; q < l; ++q) acc += Lr[q] * Bi[(size_t)q * KS_MAX + p];
+            w.Lp[sp][(size_t)x * KS_MAX + p] = acc;
+          }
+        } else {
+          const int idx = (item - lp_blocks) * 256 + threadIdx.x;
+          if (idx < l * n) {
+            const ExtView<T> v = make_view<T>(w, sp);
+            const int p = idx / n, j = idx - p * n;
+            const int P = w.P[p];
+            const double r = P < n ? ldN(v.N, (size_t)P * v.ld + j) : v.X[(size_t)(P - n) * v.ld + j];
+            ((A*)w.Rr[sp])[(size_t)p * w.cap + j] = (A)r;
+          }
+        }
+      });
 }
 
 // In place: N[i, j] += sum_p Lp[i, p] Rr[p, j] for i, j < n.
 // grid = (col tiles, row tiles, walkers*2), block 256, 32x32 tile.
 template <typename T, typename A>
+__device__ __forceinline__ void upd_apply_tile(const Config& cfg, int wi, int sp, int tile);
+
+template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_upd_apply(Config cfg) {
-  const int wi = blockIdx.z >> 1, sp = blockIdx.z & 1;
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        const long long t = (w.n + TT - 1) / TT;
+        return upd_active(w) ? t * t : 0;
+      },
+      [&](int s, int item) { upd_apply_tile<T, A>(cfg, s >> 1, s & 1, item); });
+}
+
+template <typename T, typename A>
+__device__ __forceinline__ void upd_apply_tile(const Config& cfg, int wi, int sp, int tile) {
   const WalkerDev& w = cfg.W[wi];
-  if (!upd_active(w)) return;
   const int n = w.n, l = w.n_acc;
-  const int j0 = blockIdx.x * TT, i0 = blockIdx.y * TT;
-  if (i0 >= n || j0 >= n) return;
+  const int tiles = (n + TT - 1) / TT;
+  const int ti = tile / tiles, tj = tile - ti * tiles;
+  const int j0 = tj * TT, i0 = ti * TT;
   T* N = (T*)w.N[w.parity][sp];
   const A* Rr = (const A*)w.Rr[sp];
   const int ld = w.cap;
@@ -676,15 +748,23 @@ __global__ void __launch_bounds__(256) k_upd_apply(Config cfg) {
 // (R[p, n+c] is 1 only where P_p is candidate c itself.)
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_upd_border(Config cfg) {
-  const int wi = blockIdx.y >> 1, sp = blockIdx.y & 1;
-  const WalkerDev& w = cfg.W[wi];
-  if (!upd_active(w) || w.n_ins == 0) return;
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        if (!upd_active(w) || w.n_ins == 0) return 0;
+        return blocks_of(2LL * w.n_ins * w.n + (long long)w.n_ins * w.n_ins, 256);
+      },
+      [&](int s, int item) {
+  const WalkerDev& w = cfg.W[s >> 1];
+  const int sp = s & 1;
   const int n = w.n, l = w.n_acc, ni = w.n_ins, ld = w.cap;
   T* N = (T*)w.N[w.parity][sp];
   const A* Rr = (const A*)w.Rr[sp];
   const int rows_total = ni * n, cols_total = n * ni, corner = ni * ni;
   const int total = rows_total + cols_total + corner;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+  const int idx = item * 256 + threadIdx.x;
+  if (idx < total) {
     if (idx < rows_total) {
       const int m = idx / n, j = idx - m * n;
       const int c = w.acc_slot[m];
@@ -703,6 +783,7 @@ __global__ void __launch_bounds__(256) k_upd_border(Config cfg) {
       stN(N, (size_t)(n + m) * ld + n + m2, v);
     }
   }
+      });
 }
 
 // Vertex list after the window: removed vertices dead, insertions appended,
@@ -749,19 +830,30 @@ __global__ void __launch_bounds__(256) k_window_end(Config cfg) {
 
 // Compaction: live rows / columns into the other buffer.
 // grid = (col tiles, row tiles, walkers*2), block 256.
+// Persistent grid over (walker-spin, 32 x 32 tile of the compacted matrix).
 template <typename T>
 __global__ void __launch_bounds__(256) k_compact_N(Config cfg) {
-  const int wi = blockIdx.z >> 1, sp = blockIdx.z & 1;
-  const WalkerDev& w = cfg.W[wi];
-  if (!w.active || !w.compact_pending) return;
-  const int k = w.n_live, ld = w.cap;
-  const int j = blockIdx.x * TT + (threadIdx.x & 31);
-  const T* N = (const T*)w.N[w.parity][sp];
-  T* Nn = (T*)w.N[w.parity ^ 1][sp];
-  if (j >= k) return;
-  const int cj = w.live_idx[j];
-  for (int i = blockIdx.y * TT + (threadIdx.x >> 5); i < k && i < (int)(blockIdx.y + 1) * TT; i += 8)
-    Nn[(size_t)i * ld + j] = N[(size_t)w.live_idx[i] * ld + cj];
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        const long long t = (w.n_live + TT - 1) / TT;
+        return (w.active && w.compact_pending) ? t * t : 0;
+      },
+      [&](int s, int item) {
+        const WalkerDev& w = cfg.W[s >> 1];
+        const int sp = s & 1, k = w.n_live, ld = w.cap;
+        const int tiles = (k + TT - 1) / TT;
+        const int ti = item / tiles, tj = item - ti * tiles;
+        const int j = tj * TT + (threadIdx.x & 31);
+        const T* N = (const T*)w.N[w.parity][sp];
+        T* Nn = (T*)w.N[w.parity ^ 1][sp];
+        if (j < k) {
+          const int cj = w.live_idx[j];
+          for (int i = ti * TT + (threadIdx.x >> 5); i < k && i < (ti + 1) * TT; i += 8)
+            Nn[(size_t)i * ld + j] = N[(size_t)w.live_idx[i] * ld + cj];
+        }
+      });
 }
 
 __global__ void __launch_bounds__(256) k_compact_end(Config cfg) {
@@ -835,43 +927,59 @@ __global__ void k_loop_reset(LoopState* ls, int64_t max_iters) {
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
+// Persistent grids: a few blocks per SM walk the flattened work of all walkers.
+constexpr int PERSIST_BLOCKS = 4 * 152;
+
+// Grid of a persistent kernel: at most PERSIST_BLOCKS, at most the largest
+// possible number of work items.
+static int grid_for(long long items) {
+  return (int)(items < 1 ? 1 : (items < PERSIST_BLOCKS ? items : PERSIST_BLOCKS));
+}
+
 template <typename T, typename A>
 static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_t st) {
   const int W = cfg.n_walkers;
-  const int rt = (max_cap + TT - 1) / TT;
+  const long long S = 2LL * W;  // walker-spin pairs
+  const long long t64 = (max_cap + ET - 1) / ET, t32 = (max_cap + TT - 1) / TT;
+  const long long kc = blocks_of((long long)cfg.ks * max_cap, 256);
   switch (group) {
     case GROUP_PROPOSE:
       k_begin<<<W, 128, 0, st>>>(cfg);
       return 1;
-    case GROUP_EXTEND: {
-      const int et = (max_cap + ET - 1) / ET;
-      const int zb = (cfg.ks * max_cap + 255) / 256;
-      k_cand_zero<<<dim3(zb < 256 ? zb : 256, 2 * W), 256, 0, st>>>(cfg);
-      k_cand_ext<T, A><<<dim3(et * et, 2 * W), 256, ext_smem_bytes<A>(), st>>>(cfg, et);
-      k_cand_cc<<<dim3(cfg.ks, 2 * W), 128, 0, st>>>(cfg);
+    case GROUP_EXTEND:
+      k_cand_zero<<<grid_for(S * kc), 256, 0, st>>>(cfg);
+      k_cand_ext<T, A><<<grid_for(S * t64 * t64), 256, ext_smem_bytes<A>(), st>>>(cfg);
+      k_cand_cc<<<grid_for(S * cfg.ks), 128, 0, st>>>(cfg);
       return 3;
-    }
     case GROUP_METROPOLIS: {
       const int sm = cfg.ks <= METRO_SMEM_KS ? (int)sizeof(double) * 2 * cfg.ks * cfg.ks : 0;
       k_metropolis<T><<<W, 256, sm, st>>>(cfg);
       return 1;
     }
-    case GROUP_UPDATE: {
-      const int rows = (max_cap * cfg.ks + 255) / 256;
-      const int gb = rows < 512 ? rows : 512;
-      k_upd_lrow<T><<<dim3(gb, 2 * W), 256, 0, st>>>(cfg);
-      k_upd_lp_rr<T, A><<<dim3(gb, 2 * W), 256, 0, st>>>(cfg);
-      k_upd_apply<T, A><<<dim3(rt, rt, 2 * W), 256, 0, st>>>(cfg);
-      const int bt = (2 * max_cap * cfg.ks + 255) / 256;
-      k_upd_border<T, A><<<dim3(bt < 256 ? bt : 256, 2 * W), 256, 0, st>>>(cfg);
+    case GROUP_UPDATE_PRE:
+      k_upd_lrow<T><<<grid_for(S * kc), 256, 0, st>>>(cfg);
+      k_upd_lp_rr<T, A><<<grid_for(2 * S * kc), 256, 0, st>>>(cfg);
+      if (cfg.prec == PREC_MIXED && cfg.upd_kernel == UPD_TCGEN05) {
+        launch_upd_ops(cfg, st);
+        return 3;
+      }
+      return 2;
+    case GROUP_UPDATE:
+      if (cfg.prec == PREC_MIXED && cfg.upd_kernel == UPD_TCGEN05)
+        launch_upd_tc(cfg, st);
+      else
+        k_upd_apply<T, A><<<grid_for(S * t32 * t32), 256, 0, st>>>(cfg);
+      return 1;
+    case GROUP_UPDATE_POST:
+      k_upd_border<T, A><<<grid_for(2 * S * kc), 256, 0, st>>>(cfg);
       k_window_end<<<W, 256, 0, st>>>(cfg);
-      k_compact_N<T><<<dim3(rt, rt, 2 * W), 256, 0, st>>>(cfg);
+      k_compact_N<T><<<grid_for(S * t32 * t32), 256, 0, st>>>(cfg);
       k_compact_end<<<W, 256, 0, st>>>(cfg);
-      return 7;
-    }
+      return 4;
     default:
       return 0;
   }
+  (void)max_cap;
 }
 
 cudaError_t setup_window_kernels() {

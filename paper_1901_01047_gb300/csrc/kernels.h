@@ -10,15 +10,25 @@ namespace dca {
 
 // Kernel groups of one window (and the per-window extras), timed separately.
 enum Group : int {
-  GROUP_PROPOSE = 0,     // k_begin
-  GROUP_EXTEND = 1,      // k_cand_g, k_cand_x, k_cand_cc
-  GROUP_METROPOLIS = 2,  // k_metropolis
-  GROUP_UPDATE = 3,      // k_upd_lrow, k_upd_lp_rr, k_upd_apply, k_upd_border, k_window_end,
-                         // k_compact_N, k_compact_end
-  GROUP_MEASURE = 4,     // k_meas_*
-  GROUP_RECOMPUTE = 5,   // k_build_A, k_gj_cluster, (k_store_fp32), k_recompute_finish
-  N_GROUPS = 6,
+  GROUP_PROPOSE = 0,         // k_begin
+  GROUP_EXTEND = 1,          // k_cand_zero, k_cand_ext, k_cand_cc
+  GROUP_METROPOLIS = 2,      // k_metropolis
+  GROUP_UPDATE = 3,          // the rank-l update of N
+  GROUP_MEASURE = 4,         // k_meas_*
+  GROUP_RECOMPUTE = 5,       // k_gj_cluster
+  GROUP_UPDATE_PRE = 6,      // k_upd_lrow, k_upd_lp_rr
+  GROUP_UPDATE_POST = 7,     // k_upd_border, k_window_end, k_compact_N, k_compact_end
+  GROUP_RECOMPUTE_PRE = 8,   // k_build_A
+  GROUP_RECOMPUTE_POST = 9,  // (k_store_fp32), k_recompute_drift, k_recompute_adopt
+  N_GROUPS = 10,
 };
+
+// Launch order of the groups in one window (the recompute groups only when
+// a recompute period is set).
+constexpr int WINDOW_GROUPS[] = {GROUP_PROPOSE,    GROUP_EXTEND,      GROUP_METROPOLIS, GROUP_UPDATE_PRE,
+                                 GROUP_UPDATE,     GROUP_UPDATE_POST, GROUP_MEASURE,    GROUP_RECOMPUTE_PRE,
+                                 GROUP_RECOMPUTE,  GROUP_RECOMPUTE_POST};
+constexpr int N_WINDOW_GROUPS_NO_RECOMPUTE = 7;
 
 // Kernel attributes (dynamic shared memory limits); call once per process
 // and device before any launch or stream capture.
@@ -34,8 +44,17 @@ void launch_init(const Config& cfg, int n0, int max_cap, int* d_sgn, cudaStream_
 void launch_fresh_inverse(const Config& cfg, int max_n, int* d_sgn, cudaStream_t st);
 // Gauss-Jordan inverse of the FP64 work matrices, one 8-block cluster each.
 void launch_gj(const Config& cfg, int mode, int max_n, int* d_sgn, cudaStream_t st);
-int launch_recompute(const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st);
+// part: GROUP_RECOMPUTE_PRE, GROUP_RECOMPUTE or GROUP_RECOMPUTE_POST.
+int launch_recompute(int part, const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st);
 int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
+// Tensor-core N update (mixed precision): kernel attributes, tile width for
+// a submatrix size, tensor maps of one walker ([spin][A, B, N0, N1]), the
+// operand split and the update itself.
+cudaError_t setup_update_tc();
+int tc_tile_n(int ks);
+bool encode_update_maps(const WalkerDev& w, int ks, TmapDev* out4x2);
+void launch_upd_ops(const Config& cfg, cudaStream_t st);
+void launch_upd_tc(const Config& cfg, cudaStream_t st);
 void launch_negate(const double* src, double* dst, size_t n, cudaStream_t st);
 void launch_g0_isolated(int nc, const double* d_eps, const double* d_kr, double mu_eff, double beta, int n_tau,
                         double* d_out, cudaStream_t st);

@@ -35,6 +35,7 @@ constexpr int KS_MAX = 128;     // largest submatrix size (App. B default is 128
 
 enum : int32_t {
   ST_OK = 0,
+  ST_ERR_TIMEOUT = -4,  // a bounded wait inside a kernel gave up
   ST_ERR_NUMERIC = -5,
   ST_ERR_CAPACITY = -7,
 };
@@ -95,8 +96,9 @@ struct WalkerDev {
   // ---- counters ----
   int64_t n_prop, n_accept, n_ties, n_aborts, n_windows, n_meas, n_recomputes;
   double sign_sum, k_sum, max_drift;
+  unsigned long long drift_bits[2];  // max |N_old - N_new| and max |N_new| of a recompute (bits of doubles >= 0)
   // algorithmic work (both spins): N update flop / bytes, candidate extension flop / bytes
-  double flops, upd_bytes, ext_flops, ext_bytes;
+  double flops, upd_bytes, ext_flops, ext_bytes, rec_flops;
 
   // ---- decision log / replay ----
   int64_t log_cap, forced_n;
@@ -114,6 +116,8 @@ struct WalkerDev {
   Proposal* prop;            // [KS_MAX]
   double* Gc[2];             // [spin][KS_MAX][cap]: G_ext[:, n + c] stored per candidate c
   double* Xr[2];             // [spin][KS_MAX][cap]: X[c, :] = g0[c,:] (e^V - 1) N
+  double* Vb[2];             // [spin][KS_MAX][cap]: V[c, j] = g0(r_j - r_c, tau_j - tau_c) (0 if j dead)
+  double* Ub[2];             // [spin][KS_MAX][cap]: U[c, i] = g0(r_c - r_i, tau_c - tau_i) (e^{V_i} - 1)
   double* Binv[2];           // [spin][KS_MAX][KS_MAX]
   double* aP[2];             // [spin][KS_MAX]
   int32_t* P;                // [KS_MAX] extended index of accepted flips, in order
@@ -123,6 +127,8 @@ struct WalkerDev {
   double* Lrow[2];           // [spin][cap][KS_MAX] rows of L at extended row index
   double* Lp[2];             // [spin][cap][KS_MAX] rows of L Binv at extended row index
   void* Rr[2];               // [spin][KS_MAX][cap] rows of R = N_ext[P, 0:n) (arithmetic type)
+  float* Aop[2];             // [spin][hi, lo][cap][KS_MAX] split L' rows (tensor-core update)
+  float* Bop[2];             // [spin][hi, lo][cap][KS_MAX] split R^T rows (tensor-core update)
   double* Gacc;              // [2][nc][n_tau_meas]
   double* Gtmp;              // [2][nc][n_tau_meas] correction term of one measurement
   double* gR;                // [2][nc][cap]
@@ -137,6 +143,17 @@ struct LoopState {
   int32_t pad;
 };
 
+// Opaque copy of a TMA tensor map (CUtensorMap: 128 bytes, 64-byte aligned).
+struct alignas(64) TmapDev {
+  uint64_t opaque[16];
+};
+
+// N-update kernel of the mixed-precision path.
+enum : int32_t {
+  UPD_CUDA_CORE = 1,  // FP32 CUDA-core tiles
+  UPD_TCGEN05 = 2,    // 3xTF32 tcgen05.mma fed by TMA
+};
+
 struct Config {
   int32_t n_walkers;
   int32_t ks;                // k_sub
@@ -148,6 +165,8 @@ struct Config {
   WalkerDev* W;              // [n_walkers]
   const ProblemDev* P;       // [n_problems]
   int32_t* active_count;     // [1]
+  int32_t upd_kernel;        // UPD_CUDA_CORE or UPD_TCGEN05 (mixed precision)
+  const TmapDev* tmaps;      // [n_walkers][2 spins][A, B, N parity 0, N parity 1]
 };
 
 }  // namespace dca

@@ -49,6 +49,7 @@ struct dca_walker {
   int* h_active = nullptr;          // pinned
   int* d_sgn = nullptr;
   dca::Config cfg{};
+  dca::TmapDev* d_tmaps = nullptr;  // TMA tensor maps of the tensor-core N update
   std::string err;
   int64_t windows_launched = 0;
   // problem tables (device) for dca_walker_update_G0
@@ -216,6 +217,11 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
 
   // ---- walkers ----
   const int KS = dca::KS_MAX;
+  if (p.update_kernel < DCA_UPD_AUTO || p.update_kernel > DCA_UPD_TCGEN05) {
+    h->err = "update_kernel must be one of DCA_UPD_*";
+    return bail(DCA_ERR_ARG);
+  }
+  const bool use_tc = p.precision == DCA_PREC_MIXED && p.update_kernel != DCA_UPD_CUDA_CORE;
   h->h_W.resize(h->W);
   h->nc_of.resize(h->W);
   h->gacc_off.resize(h->W);
@@ -270,11 +276,17 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     for (int sp = 0; sp < 2; ++sp) {
       pieces.push_back({(void**)&w.Gc[sp], sizeof(double) * KS * C});
       pieces.push_back({(void**)&w.Xr[sp], sizeof(double) * KS * C});
+      pieces.push_back({(void**)&w.Vb[sp], sizeof(double) * KS * C});
+      pieces.push_back({(void**)&w.Ub[sp], sizeof(double) * KS * C});
       pieces.push_back({(void**)&w.Binv[sp], sizeof(double) * KS * KS});
       pieces.push_back({(void**)&w.aP[sp], sizeof(double) * KS});
       pieces.push_back({(void**)&w.Lrow[sp], sizeof(double) * KS * C});
       pieces.push_back({(void**)&w.Lp[sp], sizeof(double) * KS * C});
       pieces.push_back({(void**)&w.Rr[sp], esz * KS * C});
+      if (use_tc) {
+        pieces.push_back({(void**)&w.Aop[sp], sizeof(float) * 2 * C * KS});
+        pieces.push_back({(void**)&w.Bop[sp], sizeof(float) * 2 * C * KS});
+      }
     }
     pieces.push_back({(void**)&w.P, sizeof(int32_t) * KS});
     pieces.push_back({(void**)&w.removed, sizeof(int32_t) * KS});
@@ -304,6 +316,24 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
       off += align_up(pc.bytes, 256);
     }
   }
+  if (use_tc) {
+    std::vector<dca::TmapDev> maps((size_t)h->W * 8);
+    for (int wi = 0; wi < h->W; ++wi)
+      if (!dca::encode_update_maps(h->h_W[wi], p.k_sub, maps.data() + (size_t)wi * 8)) {
+        h->err = "TMA tensor map encoding failed (walker " + std::to_string(wi) + ")";
+        return bail(DCA_ERR_CUDA);
+      }
+    h->d_tmaps = (dca::TmapDev*)h->dalloc(sizeof(dca::TmapDev) * maps.size());
+    if (!h->d_tmaps ||
+        cudaMemcpy(h->d_tmaps, maps.data(), sizeof(dca::TmapDev) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      h->err = "upload of tensor maps";
+      return bail(DCA_ERR_CUDA);
+    }
+    if (dca::setup_update_tc() != cudaSuccess) {
+      h->err = "tensor-core update kernel attribute setup failed";
+      return bail(DCA_ERR_CUDA);
+    }
+  }
   h->d_W = (WalkerDev*)h->dalloc(sizeof(WalkerDev) * h->W);
   h->d_active = (int*)h->dalloc(sizeof(int) * 4);
   h->d_sgn = (int*)h->dalloc(sizeof(int) * 2 * h->W);
@@ -325,6 +355,8 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.W = h->d_W;
   h->cfg.P = h->d_P;
   h->cfg.active_count = h->d_active;
+  h->cfg.upd_kernel = use_tc ? dca::UPD_TCGEN05 : dca::UPD_CUDA_CORE;
+  h->cfg.tmaps = h->d_tmaps;
 
   if (dca::setup_window_kernels() != cudaSuccess) {
     h->err = "kernel attribute setup failed";
@@ -352,6 +384,7 @@ static int status_code(int st) {
     case dca::ST_OK: return DCA_OK;
     case dca::ST_ERR_NUMERIC: return DCA_ERR_NUMERIC;
     case dca::ST_ERR_CAPACITY: return DCA_ERR_CAPACITY;
+    case dca::ST_ERR_TIMEOUT: return DCA_ERR_TIMEOUT;
     default: return DCA_ERR_STATE;
   }
 }
@@ -377,6 +410,10 @@ static cudaEvent_t next_event(dca_walker* h) {
   return h->ev_pool[h->ev_used++];
 }
 
+static int n_window_groups(const dca_walker* h) {
+  return h->R > 0 ? (int)(sizeof(dca::WINDOW_GROUPS) / sizeof(int)) : dca::N_WINDOW_GROUPS_NO_RECOMPUTE;
+}
+
 // Launch one kernel group, bracketed by events when its timing bit is set.
 static void run_group(dca_walker* h, int group) {
   const bool timed = (h->timing_mask >> group) & 1u;
@@ -390,7 +427,9 @@ static void run_group(dca_walker* h, int group) {
   int k = 0;
   switch (group) {
     case dca::GROUP_MEASURE: k = dca::launch_measure(h->cfg, h->max_cap, h->max_nc, h->stream); break;
-    case dca::GROUP_RECOMPUTE: k = dca::launch_recompute(h->cfg, h->max_cap, h->d_sgn, h->stream); break;
+    case dca::GROUP_RECOMPUTE_PRE:
+    case dca::GROUP_RECOMPUTE:
+    case dca::GROUP_RECOMPUTE_POST: k = dca::launch_recompute(group, h->cfg, h->max_cap, h->d_sgn, h->stream); break;
     default: k = dca::launch_window_group(group, h->cfg, h->max_cap, h->stream); break;
   }
   h->total_launches += k;
@@ -438,9 +477,15 @@ static int build_loop_graph(dca_walker* h) {
   cudaGraph_t body = np.conditional.phGraph_out[0];
   CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   int k = 0;
-  for (int g = dca::GROUP_PROPOSE; g <= dca::GROUP_UPDATE; ++g) k += dca::launch_window_group(g, h->cfg, h->max_cap, h->cap_stream);
-  k += dca::launch_measure(h->cfg, h->max_cap, h->max_nc, h->cap_stream);
-  if (h->R > 0) k += dca::launch_recompute(h->cfg, h->max_cap, h->d_sgn, h->cap_stream);
+  for (int i = 0; i < n_window_groups(h); ++i) {
+    const int g = dca::WINDOW_GROUPS[i];
+    if (g == dca::GROUP_MEASURE)
+      k += dca::launch_measure(h->cfg, h->max_cap, h->max_nc, h->cap_stream);
+    else if (g == dca::GROUP_RECOMPUTE_PRE || g == dca::GROUP_RECOMPUTE || g == dca::GROUP_RECOMPUTE_POST)
+      k += dca::launch_recompute(g, h->cfg, h->max_cap, h->d_sgn, h->cap_stream);
+    else
+      k += dca::launch_window_group(g, h->cfg, h->max_cap, h->cap_stream);
+  }
   dca::launch_loop_control(h->cfg, handle, h->d_loop, h->cap_stream);
   k += 1;
   cudaGraph_t captured = nullptr;
@@ -492,14 +537,8 @@ extern "C" DCA_API int dca_walker_sweep(dca_walker* h, int32_t n_sweeps) {
   CK(cudaGetLastError());
   int chunk = 2;
   for (;;) {
-    for (int i = 0; i < chunk; ++i) {
-      run_group(h, dca::GROUP_PROPOSE);
-      run_group(h, dca::GROUP_EXTEND);
-      run_group(h, dca::GROUP_METROPOLIS);
-      run_group(h, dca::GROUP_UPDATE);
-      run_group(h, dca::GROUP_MEASURE);
-      if (h->R > 0) run_group(h, dca::GROUP_RECOMPUTE);
-    }
+    for (int i = 0; i < chunk; ++i)
+      for (int j = 0; j < n_window_groups(h); ++j) run_group(h, dca::WINDOW_GROUPS[j]);
     h->windows_launched += chunk;
     CK(cudaGetLastError());
     dca::launch_count_active(h->cfg, h->stream);
@@ -613,6 +652,7 @@ extern "C" DCA_API int dca_walker_stats(dca_walker* h, dca_walker_stats_t* out) 
     s.n_update_bytes = w.upd_bytes;
     s.extend_flops = w.ext_flops;
     s.extend_bytes = w.ext_bytes;
+    s.recompute_flops = w.rec_flops;
   }
   return DCA_OK;
 }

@@ -117,7 +117,26 @@ class Workload:
     init_config_size: int = 10
     recompute_every: int = 64
     precision: str = "fp64"
+    # batched workloads: per-walker problems drawn from these ranges (seeded)
+    nc_choices: Tuple[int, ...] = ()
+    beta_range: Tuple[float, float] = (0.0, 0.0)
+    U_range: Tuple[float, float] = (0.0, 0.0)
     extra: dict = field(default_factory=dict)
+
+    def problem_params(self):
+        """(list of per-problem dicts with nc, t, tp, U, beta, mu, K, n_tau; walker -> problem index)."""
+        if not self.nc_choices:
+            p = dict(nc=self.nc, t=self.t, tp=self.tp, U=self.U, beta=self.beta, mu=self.mu, K=self.K,
+                     n_tau=self.n_tau)
+            return [p], [0] * self.walkers
+        rng = np.random.default_rng(self.seed + 12345)
+        probs = []
+        for w in range(self.walkers):
+            nc = int(self.nc_choices[w % len(self.nc_choices)])
+            beta = float(rng.uniform(*self.beta_range))
+            U = float(rng.uniform(*self.U_range))
+            probs.append(dict(nc=nc, t=self.t, tp=self.tp, U=U, beta=beta, mu=U / 2, K=self.K, n_tau=self.n_tau))
+        return probs, list(range(self.walkers))
 
 
 # Chemical potentials.  The atom is at half filling, mu = U/2.  The 2x2 value
@@ -131,6 +150,22 @@ WORKLOADS = {
     "hubbard_2x2": Workload(name="hubbard_2x2", nc=4, t=1.0, tp=0.0, U=4.0, beta=10.0,
                             mu=0.9450480104035819,
                             K=1.0, n_tau=4096, k_sub=32, sweeps=100000, n_tau_meas=256, seed=0),
+    # 16-site square cluster, t' = -0.15, U = 6, beta = 20, density 0.9 (free-cluster mu)
+    "betts16": Workload(name="betts16", nc=16, t=1.0, tp=-0.15, U=6.0, beta=20.0, mu=2.8528393768386398,
+                        K=1.0, n_tau=4096, k_sub=64, sweeps=10000, warmup_sweeps=40, n_tau_meas=256,
+                        recompute_every=64, precision="fp64"),
+    "betts16_mixed": Workload(name="betts16_mixed", nc=16, t=1.0, tp=-0.15, U=6.0, beta=20.0,
+                              mu=2.8528393768386398, K=1.0, n_tau=4096, k_sub=64, sweeps=10000,
+                              warmup_sweeps=40, n_tau_meas=256, recompute_every=64, precision="mixed"),
+    # 256 independent walkers, Nc in {8, 16}, beta ~ U[5, 25], U ~ U[4, 7], half filling
+    "batched256": Workload(name="batched256", nc=16, t=1.0, tp=0.0, U=5.5, beta=15.0, mu=2.75, K=1.0,
+                           n_tau=2048, k_sub=64, walkers=256, warmup_sweeps=40, n_tau_meas=128,
+                           recompute_every=256, precision="mixed", nc_choices=(8, 16),
+                           beta_range=(5.0, 25.0), U_range=(4.0, 7.0)),
+    # 36-site square cluster, U = 7, beta = 30, density 0.95, 32 walkers, G on 2048 tau points
+    "betts36": Workload(name="betts36", nc=36, t=1.0, tp=0.0, U=7.0, beta=30.0, mu=3.4878678207599574, K=1.0,
+                        n_tau=4096, k_sub=64, walkers=32, warmup_sweeps=40, n_tau_meas=2048,
+                        recompute_every=1024, precision="mixed"),
 }
 
 

@@ -23,7 +23,9 @@ EXPORTS = [
     "dca_walker_destroy", "dca_walker_last_error", "dca_walker_update_G0", "dca_walker_set_timing",
     "dca_walker_get_timing", "dca_fresh_N", "dca_fresh_N_noalloc",
 ]
-GROUPS = ["propose", "extend", "metropolis", "update", "measure", "recompute"]
+UPDATE_KERNELS = {"auto": 0, "cuda_core": 1, "tcgen05": 2}
+GROUPS = ["propose", "extend", "metropolis", "update", "measure", "recompute", "update_pre", "update_post",
+          "recompute_pre", "recompute_post"]
 
 
 class Problem(C.Structure):
@@ -54,6 +56,7 @@ class Params(C.Structure):
         ("seed", C.c_uint64),
         ("tie_eps", C.c_double),
         ("log_capacity", C.c_int64),
+        ("update_kernel", C.c_int32),
     ]
 
 
@@ -81,6 +84,7 @@ class Stats(C.Structure):
         ("n_update_bytes", C.c_double),
         ("extend_flops", C.c_double),
         ("extend_bytes", C.c_double),
+        ("recompute_flops", C.c_double),
     ]
 
     def as_dict(self):
@@ -195,7 +199,7 @@ class Walkers:
 
     def __init__(self, problems, n_walkers=1, walker_problem=None, k_sub=32, recompute_every=64,
                  warmup_sweeps=20, n_tau_meas=64, precision="fp64", init_config_size=10, capacity=0,
-                 seed=0, tie_eps=1e-10, log_capacity=0, stream=None):
+                 seed=0, tie_eps=1e-10, log_capacity=0, update_kernel="auto", stream=None):
         L = load()
         self._keep = []
         probs = (Problem * len(problems))()
@@ -233,6 +237,7 @@ class Walkers:
         p.seed = int(seed)
         p.tie_eps = float(tie_eps)
         p.log_capacity = int(log_capacity)
+        p.update_kernel = UPDATE_KERNELS[update_kernel] if isinstance(update_kernel, str) else int(update_kernel)
         self.n_walkers = int(n_walkers)
         self.n_tau_meas = int(n_tau_meas)
         h = C.c_void_p()

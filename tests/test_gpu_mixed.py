@@ -23,7 +23,8 @@ def _walkers(**kw):
     return walker.Walkers(stream=torch.cuda.current_stream().cuda_stream, **kw)
 
 
-def replay(nc, tp, U, beta, mu, k_sub, sweeps, R, seed=0, ntm=32, n_tau=4096):
+def replay(nc, tp, U, beta, mu, k_sub, sweeps, R, seed=0, ntm=32, n_tau=4096, update_kernel="auto",
+           return_state=False):
     c, eps, kr, G0 = problem(nc, 1.0, tp, U, beta, mu, n_tau)
     ow = ctaux.OracleWalker(nc, c.site_sub, U, beta, 1.0, G0, warmup_sweeps=10, n_tau_meas=ntm, seed=seed)
     ow.enable_log(1 << 24)
@@ -31,7 +32,7 @@ def replay(nc, tp, U, beta, mu, k_sub, sweeps, R, seed=0, ntm=32, n_tau=4096):
     log = ow.log()
     gw = _walkers(problems=[dict(nc=nc, site_sub=c.site_sub, U=U, beta=beta, K=1.0, G0=G0)], k_sub=k_sub,
                   recompute_every=R, warmup_sweeps=10, n_tau_meas=ntm, seed=seed, precision="mixed",
-                  log_capacity=1 << 24)
+                  log_capacity=1 << 24, update_kernel=update_kernel)
     gw.set_forced_decisions(0, log)
     gw.sweep(sweeps)
     gs, os_ = gw.state(0), ow.state()
@@ -43,6 +44,8 @@ def replay(nc, tp, U, beta, mu, k_sub, sweeps, R, seed=0, ntm=32, n_tau=4096):
     errG = np.abs(Gg[0] - Go).max() / np.abs(Go).max()
     st = gw.stats()[0]
     gw.close()
+    if return_state:
+        return errN, errG, st, gs
     return errN, errG, st, log
 
 
@@ -51,17 +54,22 @@ def replay(nc, tp, U, beta, mu, k_sub, sweeps, R, seed=0, ntm=32, n_tau=4096):
 # for the 16-site case) and the result moves by a few times between builds
 # that sum in another order.  Recomputing every 8 submatrix updates instead
 # of 64 cuts the error several times.
-def test_mixed_replay_2x2_errors():
-    errN, errG, st, _ = replay(4, 0.0, 4.0, 10.0, 0.9450480104035819, 32, 2000, 64)
+UPDATE_KERNELS = ["cuda_core", "tcgen05"]
+
+
+@pytest.mark.parametrize("kern", UPDATE_KERNELS)
+def test_mixed_replay_2x2_errors(kern):
+    errN, errG, st, _ = replay(4, 0.0, 4.0, 10.0, 0.9450480104035819, 32, 2000, 64, update_kernel=kern)
     assert st["status"] == 0 and st["recomputes"] > 0
     assert errN < 1e-4, errN
     assert errG < 3e-4, errG
-    errN8, errG8, st8, _ = replay(4, 0.0, 4.0, 10.0, 0.9450480104035819, 32, 2000, 8)
+    errN8, errG8, st8, _ = replay(4, 0.0, 4.0, 10.0, 0.9450480104035819, 32, 2000, 8, update_kernel=kern)
     assert errG8 < 5e-5, errG8
 
 
-def test_mixed_replay_16_site_errors():
-    errN, errG, st, _ = replay(16, -0.15, 6.0, 4.0, 2.85, 64, 60, 64, ntm=16, n_tau=2048)
+@pytest.mark.parametrize("kern", UPDATE_KERNELS)
+def test_mixed_replay_16_site_errors(kern):
+    errN, errG, st, _ = replay(16, -0.15, 6.0, 4.0, 2.85, 64, 60, 64, ntm=16, n_tau=2048, update_kernel=kern)
     assert errN < 3e-4, errN
     assert errG < 5e-5, errG
 
@@ -82,3 +90,23 @@ def test_mixed_free_run_follows_the_oracle_for_a_long_stretch():
     mism = np.nonzero((glog[:n] & 1) != (olog[:n] & 1))[0]
     first = mism[0] if mism.size else n
     assert first > 2000, first
+
+
+@pytest.mark.parametrize("k_sub", [16, 64, 128])
+def test_tensor_core_update_matches_cuda_core_update(k_sub):
+    # Same forced trajectory, no recompute: the 3xTF32 tcgen05 update and the
+    # FP32 CUDA-core update differ only by rounding.  k_sub covers the three
+    # K extents of the tensor-core kernel (32, 64, 128) and n spans several
+    # 128-row blocks with a ragged tail.
+    args = (16, -0.15, 6.0, 6.0, 2.85, k_sub, 30, 0)
+    eN_c, eG_c, st_c, gs_c = replay(*args, ntm=16, n_tau=2048, update_kernel="cuda_core", return_state=True)
+    eN_t, eG_t, st_t, gs_t = replay(*args, ntm=16, n_tau=2048, update_kernel="tcgen05", return_state=True)
+    assert st_t["status"] == 0 and st_c["status"] == 0
+    assert gs_t["N"][0].shape[0] > 128
+    # Both drift from the FP64 oracle (no recompute): the tensor-core path
+    # must not drift more than a few times the CUDA-core path, and the two
+    # stay within the sum of their drifts of each other.
+    assert eN_t <= 3 * eN_c + 1e-6 and eG_t <= 3 * eG_c + 1e-7, (eN_t, eN_c, eG_t, eG_c)
+    for sp in range(2):
+        a, b = gs_c["N"][sp], gs_t["N"][sp]
+        assert np.abs(a - b).max() <= 2 * (eN_c + eN_t) * np.abs(a).max() + 1e-12
