@@ -103,7 +103,8 @@ class ClockSampler:
 def config_of(wl, world):
     return {"workload": wl.name, "nc": wl.nc, "t": wl.t, "tp": wl.tp, "U": wl.U, "beta": wl.beta, "mu": wl.mu,
             "K": wl.K, "walkers_per_gpu": wl.walkers, "k_sub": wl.k_sub, "n_tau": wl.n_tau,
-            "n_tau_meas": wl.n_tau_meas, "recompute_every": wl.recompute_every, "precision": wl.precision,
+            "n_tau_meas": wl.n_tau_meas, "recompute_every": wl.recompute_every, "recompute_sweeps": wl.recompute_sweeps,
+            "precision": wl.precision,
             "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)",
             **({"per_walker": {"nc": list(wl.nc_choices), "beta": list(wl.beta_range), "U": list(wl.U_range),
                                "mu": "U/2"}} if wl.nc_choices else {})}
@@ -210,7 +211,7 @@ def run_ours(args, rank, world, local_rank):
     probs, walker_problem = workload_problems(wl, use_gpu_builder=True)
     seed = wl.seed + 1000003 * rank
     gw = walker.Walkers(probs, n_walkers=wl.walkers, walker_problem=walker_problem, k_sub=wl.k_sub,
-                        recompute_every=wl.recompute_every,
+                        recompute_every=wl.recompute_every, recompute_sweeps=wl.recompute_sweeps,
                         warmup_sweeps=wl.warmup_sweeps, n_tau_meas=wl.n_tau_meas, precision=wl.precision,
                         init_config_size=wl.init_config_size, seed=seed, stream=stream.cuda_stream)
     gw.sweep(wl.warmup_sweeps)            # the chain's own warm-up (no measurements)

@@ -96,6 +96,10 @@ typedef struct {
   double tie_eps;                  /* near-tie band on | |R| - u |; 0 = 1e-10 */
   int64_t log_capacity;            /* decision-log bytes per walker; 0 = no log */
   int32_t update_kernel;           /* N-update kernel of DCA_PREC_MIXED: DCA_UPD_* */
+  int32_t recompute_sweeps;        /* batched schedule: every walker recomputes N after the
+                                      first window of every this-many-th sweep (all walkers in
+                                      the same window, so the inverses share the GPU); 0 = off.
+                                      Independent of recompute_every. */
 } dca_walker_params;
 
 /* N-update kernels of the mixed-precision path (ignored by DCA_PREC_FP64). */

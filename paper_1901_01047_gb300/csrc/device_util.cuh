@@ -83,6 +83,43 @@ __device__ __forceinline__ double g0_diag(const ProblemDev& p, int sp, int r) {
   return __ldg(p.g0 + ((size_t)sp * p.nc + d) * (size_t)(p.n_tau + 1));
 }
 
+// Mixed-precision interpolation.  An imaginary time is carried on the g0 grid
+// as x = tau n_tau / beta split into an integer part and an FP32 fraction
+// (formed once per vertex in FP64).  The grid index of a difference x_a - x_b
+// is then exact and only the interpolation weight (error ~2^-24 of a grid
+// step) and the arithmetic are FP32: no FP64 operation per table lookup.
+struct GridTime {
+  int i;
+  float f;
+};
+
+__device__ __forceinline__ GridTime grid_time(double tau, double tau_scale) {
+  const double x = tau * tau_scale;
+  const double fl = floor(x);
+  return GridTime{(int)fl, (float)(x - fl)};
+}
+
+// g0(t_a - t_b) from one table row with the conventions of g0_interp.
+__device__ __forceinline__ float g0_interp_grid(const double* __restrict__ row, int n_tau, GridTime a, GridTime b) {
+  int l = a.i - b.i;
+  float f = a.f - b.f;
+  if (f < 0.0f) {
+    f += 1.0f;
+    --l;
+  }
+  float sgn = 1.0f;
+  if (l < 0) {
+    l += n_tau;
+    sgn = -1.0f;
+  }
+  if (l >= n_tau) {
+    f += (float)(l - (n_tau - 1));
+    l = n_tau - 1;
+  }
+  const float lo = (float)__ldg(row + l), hi = (float)__ldg(row + l + 1);
+  return sgn * (lo + f * (hi - lo));
+}
+
 // e^{V} of a vertex with stored auxiliary spin s: s = 0 marks a dead
 // (non-interacting) vertex, V = 0.
 __device__ __forceinline__ double expV(const ProblemDev& p, int sp, int s) {

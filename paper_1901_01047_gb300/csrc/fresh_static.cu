@@ -54,7 +54,7 @@ constexpr size_t kOffN1 = kOffN0 + up256(sizeof(double) * kMaxOrder * kMaxOrder)
 constexpr size_t kOffScr0 = kOffN1 + up256(sizeof(double) * kMaxOrder * kMaxOrder);
 constexpr size_t kOffScr1 = kOffScr0 + up256(sizeof(double) * 2 * kMaxOrder);
 constexpr size_t kOffSign = kOffScr1 + up256(sizeof(double) * 2 * kMaxOrder);
-constexpr size_t kScratchBytes = kOffSign + up256(sizeof(int32_t) * 2);
+constexpr size_t kScratchBytes = kOffSign + up256(sizeof(int32_t) * 4);  // two signs, work queue
 
 static __device__ __align__(256) unsigned char g_fresh_scratch[kScratchBytes];
 
@@ -139,6 +139,7 @@ extern "C" DCA_API int dca_fresh_N_noalloc(const dca_problem* problem, int32_t n
   cfg.n_walkers = 1;
   cfg.W = (dca::WalkerDev*)(base + kOffWalker);
   cfg.P = (const dca::ProblemDev*)(base + kOffProblem);
+  cfg.gj_next = d_sgn + 2;  // work queue of the inverse
 
   const size_t nc2 = (size_t)pr.nc * pr.nc, nn = (size_t)n * n;
   // The determinant signs must read 0 unless this call's inverse finished.

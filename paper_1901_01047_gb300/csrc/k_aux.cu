@@ -47,6 +47,7 @@ __device__ __forceinline__ double* work_matrix(const Config& cfg, const WalkerDe
 
 // Persistent grid; one item = 256 entries of one walker-spin's A.
 __global__ void __launch_bounds__(256) k_build_A(Config cfg, int mode) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *cfg.gj_next = 0;  // work queue of the inverse that follows
   for_each_item(
       2 * cfg.n_walkers,
       [&](int s) -> long long {
@@ -222,10 +223,10 @@ __global__ void __launch_bounds__(256) k_meas_gr(Config cfg) {
 // b[r'][i] = (e^{V_i} - 1) sum_j N[i][j] gR[r'][j] as a tiled product:
 // one item = 8 rows of N (one warp each); lanes own reference sites r' and
 // r' + 32; chunks of 32 columns of N and gR are staged in shared memory.
-template <typename T>
+template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_meas_b(Config cfg) {
-  __shared__ double sN[8][33];
-  __shared__ double sG[64][33];
+  __shared__ A sN[8][33];
+  __shared__ A sG[64][33];
   for_each_item(
       2 * cfg.n_walkers,
       [&](int s) -> long long {
@@ -240,29 +241,35 @@ __global__ void __launch_bounds__(256) k_meas_b(Config cfg) {
         const T* N = (const T*)w.N[par][sp];
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int i = item * 8 + warp;
-        double acc0 = 0.0, acc1 = 0.0;
+        A acc0 = (A)0, acc1 = (A)0;
+        const bool two = nc > 32;  // uniform: the second reference-site half exists
         for (int j0 = 0; j0 < n; j0 += 32) {
           __syncthreads();
           {
             const int j = j0 + lane;
-            sN[warp][lane] = (i < n && j < n) ? ldN(N, (size_t)i * ld + j) : 0.0;
+            sN[warp][lane] = (A)((i < n && j < n) ? ldN(N, (size_t)i * ld + j) : 0.0);
           }
-          for (int e = threadIdx.x; e < 64 * 32; e += 256) {
+          for (int e = threadIdx.x; e < (two ? 64 : 32) * 32; e += 256) {
             const int rp = e >> 5, jl = e & 31, j = j0 + jl;
-            sG[rp][jl] = (rp < nc && j < n) ? w.gR[((size_t)sp * nc + rp) * ld + j] : 0.0;
+            sG[rp][jl] = (A)((rp < nc && j < n) ? w.gR[((size_t)sp * nc + rp) * ld + j] : 0.0);
           }
           __syncthreads();
+          if (two) {
 #pragma unroll 8
-          for (int jl = 0; jl < 32; ++jl) {
-            const double nij = sN[warp][jl];
-            acc0 += nij * sG[lane][jl];
-            acc1 += nij * sG[lane + 32][jl];
+            for (int jl = 0; jl < 32; ++jl) {
+              const A nij = sN[warp][jl];
+              acc0 += nij * sG[lane][jl];
+              acc1 += nij * sG[lane + 32][jl];
+            }
+          } else {
+#pragma unroll 8
+            for (int jl = 0; jl < 32; ++jl) acc0 += sN[warp][jl] * sG[lane][jl];
           }
         }
         if (i < n) {
           const double f = expV(pb, sp, w.vs[par][i]) - 1.0;
-          if (lane < nc) w.bvec[((size_t)sp * nc + lane) * ld + i] = f * acc0;
-          if (lane + 32 < nc) w.bvec[((size_t)sp * nc + lane + 32) * ld + i] = f * acc1;
+          if (lane < nc) w.bvec[((size_t)sp * nc + lane) * ld + i] = f * (double)acc0;
+          if (lane + 32 < nc) w.bvec[((size_t)sp * nc + lane + 32) * ld + i] = f * (double)acc1;
         }
       });
 }
@@ -271,13 +278,14 @@ __global__ void __launch_bounds__(256) k_meas_b(Config cfg) {
 // columns the reference site r':
 //   C[(x, a), r'] = sum_i g0(x - r_i, tau_a - tau_i) b_i(r'),
 // scattered to Gtmp[sp][x - r'][a] (FP64 atomics).  The g0 factor is
-// interpolated on the fly.  A is the arithmetic type of the products.
-// grid = (nc * ceil(n_tau_meas / 64), walkers * 2), block 256.
-constexpr int MT = 64;   // tau points per block
+// interpolated on the fly (FP64 path: FP64; mixed path: FP32 on the split
+// grid time, with the tau_a and tau_i grid times formed once per tile).  A is
+// the arithmetic type of the products, MR >= nc the reference-site tile.
+// Item = (site x, block of MT tau points) of one walker-spin, block 256.
+constexpr int MT = 64;   // tau points per item
 constexpr int MK = 32;   // vertices per step
-constexpr int MR = 64;   // reference sites per block (nc <= 64)
 
-template <typename A>
+template <typename A, int MR>
 __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp, int item);
 
 template <typename A>
@@ -288,18 +296,26 @@ __global__ void __launch_bounds__(256) k_meas_gemm(Config cfg) {
         const WalkerDev& w = cfg.W[s >> 1];
         return wants_measure(w) ? (long long)cfg.P[w.problem].nc * blocks_of(cfg.n_tau_meas, MT) : 0;
       },
-      [&](int s, int item) { meas_gemm_item<A>(cfg, s >> 1, s & 1, item); });
+      [&](int s, int item) {
+        const int nc = cfg.P[cfg.W[s >> 1].problem].nc;  // uniform over the block
+        if (nc <= 16) meas_gemm_item<A, 16>(cfg, s >> 1, s & 1, item);
+        else if (nc <= 32) meas_gemm_item<A, 32>(cfg, s >> 1, s & 1, item);
+        else meas_gemm_item<A, 64>(cfg, s >> 1, s & 1, item);
+      });
 }
 
-template <typename A>
+template <typename A, int MR>
 __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp, int item) {
   const WalkerDev& w = cfg.W[wi];
   const ProblemDev& pb = cfg.P[w.problem];
   const int nc = pb.nc, ntm = cfg.n_tau_meas, n = w.n, par = w.parity, ld = w.cap;
   const int tblocks = (ntm + MT - 1) / MT;
   const int x = item / tblocks, a0 = (item - x * tblocks) * MT;
+  constexpr bool kGrid = sizeof(A) == 4;
   __shared__ A As[MT][MK + 1];
   __shared__ A Bs[MK][MR + 1];
+  __shared__ GridTime s_ga[MT], s_gi[MK];
+  __shared__ int s_row[MK];  // table row of g0(x - r_i, .), -1 for a dead vertex
   const int tid = threadIdx.x;
   const int ta = tid & (MT - 1), tr = tid >> 6;  // 4 groups of reference sites
   A acc[MR / 4];
@@ -308,19 +324,33 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
   const int* vsite = w.vsite[par];
   const double* vtau = w.vtau[par];
   const int* vs = w.vs[par];
-  const double* row_base = pb.g0 + (size_t)sp * nc * (pb.n_tau + 1);
+  const int np1 = pb.n_tau + 1;
+  const double* row_base = pb.g0 + (size_t)sp * nc * np1;
+  __syncthreads();  // the previous item of this block is done with the shared tiles
+  if (kGrid && tid < MT) s_ga[tid] = grid_time(((double)(a0 + tid) + 0.5) * pb.beta / (double)ntm, pb.tau_scale);
   for (int i0 = 0; i0 < n; i0 += MK) {
+    __syncthreads();
+    if (tid < MK) {
+      const int i = i0 + tid;
+      const bool live = i < n && vs[i] != 0;
+      s_row[tid] = live ? __ldg(pb.site_sub + x * nc + vsite[i]) : -1;
+      if (kGrid && live) s_gi[tid] = grid_time(vtau[i], pb.tau_scale);
+    }
     __syncthreads();
     for (int e = tid; e < MT * MK; e += 256) {
       const int al = e / MK, il = e - al * MK;
-      const int a = a0 + al, i = i0 + il;
-      double v = 0.0;
-      if (a < ntm && i < n && vs[i] != 0) {
-        const double ta_ = ((double)a + 0.5) * pb.beta / (double)ntm;
-        const int d = __ldg(pb.site_sub + x * nc + vsite[i]);
-        v = g0_interp(row_base + (size_t)d * (pb.n_tau + 1), pb.n_tau, pb.beta, pb.tau_scale, ta_ - vtau[i]);
+      const int a = a0 + al, d = s_row[il];
+      A v = (A)0;
+      if (a < ntm && d >= 0) {
+        const double* row = row_base + (size_t)d * np1;
+        if (kGrid) {
+          v = (A)g0_interp_grid(row, pb.n_tau, s_ga[al], s_gi[il]);
+        } else {
+          const double ta_ = ((double)a + 0.5) * pb.beta / (double)ntm;
+          v = (A)g0_interp(row, pb.n_tau, pb.beta, pb.tau_scale, ta_ - vtau[i0 + il]);
+        }
       }
-      As[al][il] = (A)v;
+      As[al][il] = v;
     }
     for (int e = tid; e < MK * MR; e += 256) {
       const int il = e / MR, rp = e - il * MR;
@@ -477,8 +507,8 @@ int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) 
   const long long S = 2LL * W;
   k_meas_gr<<<grid_for(S * blocks_of((long long)max_nc * max_cap, 256)), 256, 0, st>>>(cfg);
   const int gb = grid_for(S * blocks_of(max_cap, 8));
-  if (cfg.prec == PREC_MIXED) k_meas_b<float><<<gb, 256, 0, st>>>(cfg);
-  else k_meas_b<double><<<gb, 256, 0, st>>>(cfg);
+  if (cfg.prec == PREC_MIXED) k_meas_b<float, float><<<gb, 256, 0, st>>>(cfg);
+  else k_meas_b<double, double><<<gb, 256, 0, st>>>(cfg);
   const int gg = grid_for(S * max_nc * blocks_of(cfg.n_tau_meas, MT));
   if (cfg.prec == PREC_MIXED) k_meas_gemm<float><<<gg, 256, 0, st>>>(cfg);
   else k_meas_gemm<double><<<gg, 256, 0, st>>>(cfg);

@@ -41,19 +41,37 @@ __device__ __forceinline__ bool gj_better(double m1, int i1, double m2, int i2) 
 
 __device__ void gj_matrix(const Config& cfg, int mode, int mat, int* sgn_out, cg::cluster_group& cluster);
 
+__device__ __forceinline__ bool gj_wants(const Config& cfg, int mode, int mat) {
+  const WalkerDev& w = cfg.W[mat >> 1];
+  return mode == 0 ? true : (w.active && w.recompute_pending && w.status == ST_OK);
+}
+
 // mode 0: initial build / standalone; mode 1: periodic recompute.
-// Persistent grid of clusters: cluster k inverts matrices k, k + clusters, ...
-// (matrix = walker * 2 + spin) that need it; dynamic shared memory: one int
-// per matrix row (pivot rows).
+// Persistent grid of clusters fed by a work queue: the rank-0 block of a
+// cluster takes the next matrix (walker * 2 + spin) from cfg.gj_next (reset to
+// 0 by k_build_A before every launch), so clusters that drew small matrices
+// take more of them.  Dynamic shared memory: one int per row (pivot rows).
 __global__ void __cluster_dims__(GJ_CTAS, 1, 1) __launch_bounds__(GJ_THREADS)
     k_gj_cluster(Config cfg, int mode, int* sgn_out) {
   cg::cluster_group cluster = cg::this_cluster();
-  const int clusters = gridDim.x / GJ_CTAS;
-  for (int mat = blockIdx.x / GJ_CTAS; mat < 2 * cfg.n_walkers; mat += clusters) {
-    const WalkerDev& w = cfg.W[mat >> 1];
-    // uniform over the cluster: no barrier is skipped by a subset of its blocks
-    const bool want = mode == 0 ? true : (w.active && w.recompute_pending && w.status == ST_OK);
-    if (!want) continue;
+  __shared__ int s_next;
+  // Nothing to do in most windows: every block sees the same records, so the
+  // decision is uniform over the cluster.
+  __shared__ int s_any;
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  for (int m = threadIdx.x; m < 2 * cfg.n_walkers && !s_any; m += blockDim.x)
+    if (gj_wants(cfg, mode, m)) s_any = 1;
+  __syncthreads();
+  if (!s_any) return;
+  const int rank = (int)cluster.block_rank();
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) s_next = atomicAdd(cfg.gj_next, 1);
+    cluster.sync();
+    const int mat = *cluster.map_shared_rank(&s_next, 0);
+    cluster.sync();  // every block has read s_next before it changes
+    if (mat >= 2 * cfg.n_walkers) break;
+    if (!gj_wants(cfg, mode, mat)) continue;
     gj_matrix(cfg, mode, mat, sgn_out, cluster);
     cluster.sync();  // the next matrix reuses the shared posts and pivots
   }

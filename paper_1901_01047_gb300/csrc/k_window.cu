@@ -14,10 +14,11 @@
 //   k_window_end  removed vertices marked dead, insertions appended to the
 //                 vertex list, live-row index and compaction schedule updated
 //   k_compact_*   (when due) live rows / columns gathered into the other buffer
-// N is stored as T and the dense products (candidate extension, update term)
-// run in arithmetic type A: both double on the FP64 path, both float on the
-// mixed path; ratios, B^-1, the update factors L B^-1 and the recompute are
-// always FP64.
+// N is stored as T and the dense products (candidate extension, the G block
+// of the candidates, L B^-1, the update term) run in arithmetic type A: both
+// double on the FP64 path, both float on the mixed path, where the g0
+// lookups of the candidate factors also interpolate in FP32 on the split grid
+// time.  Ratios, B^-1 and the recompute are always FP64.
 #include <cstdint>
 #include <cstdio>
 
@@ -34,6 +35,18 @@ __global__ void __launch_bounds__(128) k_begin(Config cfg) {
   WalkerDev& w = cfg.W[blockIdx.x];
   __shared__ int s_active, s_len, s_n, s_cap, s_par;
   __shared__ int s_type[KS_MAX];
+  // Lockstep sweeps: a walker works only while its sweep count equals the
+  // smallest count among the walkers that still have sweeps to do, so every
+  // walker starts sweep m in the same window (each chain is unchanged; only
+  // the interleaving of the walkers is fixed).
+  __shared__ unsigned long long s_min;
+  if (threadIdx.x == 0) s_min = ~0ull;
+  __syncthreads();
+  for (int i = threadIdx.x; i < cfg.n_walkers; i += blockDim.x) {
+    const WalkerDev& o = cfg.W[i];
+    if (o.status == ST_OK && o.sweeps_done < o.sweeps_target) atomicMin(&s_min, (unsigned long long)o.sweeps_done);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     w.n_acc = 0;
     w.n_removed = 0;
@@ -43,8 +56,10 @@ __global__ void __launch_bounds__(128) k_begin(Config cfg) {
     w.n_cand = 0;
     w.measure_pending = 0;
     w.recompute_pending = 0;
-    int act = (w.status == ST_OK && w.sweeps_done < w.sweeps_target) ? 1 : 0;
+    int act = (w.status == ST_OK && w.sweeps_done < w.sweeps_target &&
+               (unsigned long long)w.sweeps_done == s_min) ? 1 : 0;
     if (act) {
+      w.first_window = w.sweep_pos == 0 ? 1 : 0;
       if (w.sweep_pos == 0) {
         const int k = w.n_live;
         if (w.sweeps_done < cfg.warmup) {
@@ -131,33 +146,57 @@ constexpr int METRO_SMEM_KS = 96;  // largest k_s whose B^-1 (both spins) lives 
 constexpr int ET = 64;   // tile of the extension kernel
 constexpr int EC = 32;   // candidates per pass
 
-// Persistent grid; one item = 256 entries (c, j) of one walker-spin: clears
-// the reduction targets Gc / Xr and tabulates the candidate factors V and U
-// once per window (the tile kernel then reads them instead of interpolating).
+// Persistent grid; one item = 256 vertices i of one walker-spin, all
+// candidates c: clears the reduction targets Gc / Xr and tabulates the
+// candidate factors V and U once per window (the tile kernel then reads them
+// instead of interpolating).  The mixed path interpolates on the split grid
+// time (FP32 arithmetic), the FP64 path in FP64.
 __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
+  __shared__ GridTime s_gc[KS_MAX];
+  __shared__ double s_tc[KS_MAX];
+  __shared__ int s_rc[KS_MAX];
   for_each_item(
       2 * cfg.n_walkers,
       [&](int s) -> long long {
         const WalkerDev& w = cfg.W[s >> 1];
-        return (w.active && w.n_cand > 0) ? blocks_of((long long)w.n_cand * w.n, 256) : 0;
+        return (w.active && w.n_cand > 0) ? blocks_of(w.n, 256) : 0;
       },
       [&](int s, int item) {
         const WalkerDev& w = cfg.W[s >> 1];
-        const int sp = s & 1, n = w.n, ld = w.cap;
-        const int idx = item * 256 + threadIdx.x;
-        if (idx < w.n_cand * n) {
-          const int c = idx / n, i = idx - c * n;
+        const int sp = s & 1, n = w.n, ld = w.cap, nc_ = w.n_cand, par = w.parity;
+        const ProblemDev& pb = cfg.P[w.problem];
+        const bool mixed = cfg.prec == PREC_MIXED;
+        __syncthreads();  // the previous item of this block is done with the candidate table
+        for (int c = threadIdx.x; c < nc_; c += 256) {
+          s_rc[c] = w.vsite[par][n + c];
+          s_tc[c] = w.vtau[par][n + c];
+          if (mixed) s_gc[c] = grid_time(s_tc[c], pb.tau_scale);
+        }
+        __syncthreads();
+        const int i = item * 256 + threadIdx.x;
+        if (i >= n) return;
+        const int si = w.vs[par][i], ri = w.vsite[par][i];
+        const double ti = w.vtau[par][i];
+        const double em1 = si != 0 ? expV(pb, sp, si) - 1.0 : 0.0;
+        const GridTime gi = grid_time(ti, pb.tau_scale);
+        const int np1 = pb.n_tau + 1;
+        const double* g0s = pb.g0 + (size_t)sp * pb.nc * np1;
+        for (int c = 0; c < nc_; ++c) {
           const size_t o = (size_t)c * ld + i;
           w.Gc[sp][o] = 0.0;
           w.Xr[sp][o] = 0.0;
-          const ProblemDev& pb = cfg.P[w.problem];
-          const int par = w.parity;
-          const int si = w.vs[par][i], ri = w.vsite[par][i], rc = w.vsite[par][n + c];
-          const double ti = w.vtau[par][i], tc = w.vtau[par][n + c];
           double v = 0.0, u = 0.0;
           if (si != 0) {
-            v = g0_pair(pb, sp, ri, ti, rc, tc);
-            u = g0_pair(pb, sp, rc, tc, ri, ti) * (expV(pb, sp, si) - 1.0);
+            const int rc = s_rc[c];
+            if (mixed) {
+              const double* rv = g0s + (size_t)__ldg(pb.site_sub + ri * pb.nc + rc) * np1;
+              const double* ru = g0s + (size_t)__ldg(pb.site_sub + rc * pb.nc + ri) * np1;
+              v = (double)g0_interp_grid(rv, pb.n_tau, gi, s_gc[c]);
+              u = (double)(g0_interp_grid(ru, pb.n_tau, s_gc[c], gi) * (float)em1);
+            } else {
+              v = g0_pair(pb, sp, ri, ti, rc, s_tc[c]);
+              u = g0_pair(pb, sp, rc, s_tc[c], ri, ti) * em1;
+            }
           }
           w.Vb[sp][o] = v;
           w.Ub[sp][o] = u;
@@ -248,8 +287,11 @@ constexpr int ext_smem_bytes() {
 
 // G_ext[n+c', n+c] = X[c',:] . g0[:, c] + g0(r_c' - r_c, tau_c' - tau_c).
 // grid = (KS_MAX candidates c, walkers * 2); block = 128 (4 warps over c').
+// The products run in the arithmetic type A.
+template <typename A>
 __device__ __forceinline__ void cand_cc_item(const Config& cfg, int wi, int sp, int c);
 
+template <typename A>
 __global__ void __launch_bounds__(128) k_cand_cc(Config cfg) {
   for_each_item(
       2 * cfg.n_walkers,
@@ -257,9 +299,10 @@ __global__ void __launch_bounds__(128) k_cand_cc(Config cfg) {
         const WalkerDev& w = cfg.W[s >> 1];
         return w.active ? w.n_cand : 0;
       },
-      [&](int s, int c) { cand_cc_item(cfg, s >> 1, s & 1, c); });
+      [&](int s, int c) { cand_cc_item<A>(cfg, s >> 1, s & 1, c); });
 }
 
+template <typename A>
 __device__ __forceinline__ void cand_cc_item(const Config& cfg, int wi, int sp, int c) {
   const WalkerDev& w = cfg.W[wi];
   const int n = w.n, nc_ = w.n_cand;
@@ -271,15 +314,15 @@ __device__ __forceinline__ void cand_cc_item(const Config& cfg, int wi, int sp, 
   const int rc = vsite[n + c];
   const double tc = vtau[n + c];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __shared__ double v[1024];
-  double acc[KS_MAX / 4];
+  __shared__ A v[1024];
+  A acc[KS_MAX / 4];
 #pragma unroll
-  for (int m = 0; m < KS_MAX / 4; ++m) acc[m] = 0.0;
+  for (int m = 0; m < KS_MAX / 4; ++m) acc[m] = (A)0;
   for (int j0 = 0; j0 < n; j0 += 1024) {
     __syncthreads();
     for (int t = threadIdx.x; t < 1024; t += 128) {
       const int j = j0 + t;
-      v[t] = j < n ? w.Vb[sp][(size_t)c * ld + j] : 0.0;
+      v[t] = (A)(j < n ? w.Vb[sp][(size_t)c * ld + j] : 0.0);
     }
     __syncthreads();
 #pragma unroll
@@ -287,8 +330,8 @@ __device__ __forceinline__ void cand_cc_item(const Config& cfg, int wi, int sp, 
       const int cp = warp + 4 * m;
       if (cp < nc_) {
         const double* X = w.Xr[sp] + (size_t)cp * ld;
-        double s = 0.0;
-        for (int t = lane; t < 1024 && j0 + t < n; t += 32) s += X[j0 + t] * v[t];
+        A s = (A)0;
+        for (int t = lane; t < 1024 && j0 + t < n; t += 32) s += (A)X[j0 + t] * v[t];
         acc[m] += s;
       }
     }
@@ -296,7 +339,7 @@ __device__ __forceinline__ void cand_cc_item(const Config& cfg, int wi, int sp, 
 #pragma unroll
   for (int m = 0; m < KS_MAX / 4; ++m) {
     const int cp = warp + 4 * m;
-    double s = acc[m];
+    double s = (double)acc[m];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0 && cp < nc_) {
@@ -572,6 +615,7 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
       w.sweep_pos += eval;
       w.n_windows++;
       if (w.aborted) w.n_aborts++;
+      const int64_t sweep_no = w.sweeps_done;  // the sweep this window belongs to
       if (w.sweep_pos >= w.sweep_len_cur) {
         w.measure_pending = (w.sweeps_done >= cfg.warmup) ? 1 : 0;
         w.sweeps_done++;
@@ -579,6 +623,12 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
       }
       w.windows_since_recompute++;
       if (cfg.recompute_every > 0 && w.windows_since_recompute >= cfg.recompute_every) {
+        w.recompute_pending = 1;
+        w.windows_since_recompute = 0;
+      }
+      // Batched schedule: every walker recomputes after the first window of
+      // every recompute_sweeps-th sweep (the same window for all walkers).
+      if (cfg.recompute_sweeps > 0 && w.first_window && sweep_no > 0 && sweep_no % cfg.recompute_sweeps == 0) {
         w.recompute_pending = 1;
         w.windows_since_recompute = 0;
       }
@@ -664,7 +714,7 @@ __global__ void __launch_bounds__(256) k_upd_lp_rr(Config cfg) {
             const int x = upd_row(w, t);
             const double* Lr = w.Lrow[sp] + (size_t)x * KS_MAX;
             const double* Bi = w.Binv[sp];
-            double acc = 0.0;
+            double acc = 0.0;  // FP64 on both paths: B^-1 carries the conditioning of the window
             for (int q = 0; q < l; ++q) acc += Lr[q] * Bi[(size_t)q * KS_MAX + p];
             w.Lp[sp][(size_t)x * KS_MAX + p] = acc;
           }
@@ -949,7 +999,7 @@ static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_
     case GROUP_EXTEND:
       k_cand_zero<<<grid_for(S * kc), 256, 0, st>>>(cfg);
       k_cand_ext<T, A><<<grid_for(S * t64 * t64), 256, ext_smem_bytes<A>(), st>>>(cfg);
-      k_cand_cc<<<grid_for(S * cfg.ks), 128, 0, st>>>(cfg);
+      k_cand_cc<A><<<grid_for(S * cfg.ks), 128, 0, st>>>(cfg);
       return 3;
     case GROUP_METROPOLIS: {
       const int sm = cfg.ks <= METRO_SMEM_KS ? (int)sizeof(double) * 2 * cfg.ks * cfg.ks : 0;

@@ -92,6 +92,7 @@ struct WalkerDev {
   int32_t n_ins;             // accepted insertions (appended rows)
   int32_t measure_pending;
   int32_t recompute_pending;
+  int32_t first_window;      // this window starts a sweep
 
   // ---- counters ----
   int64_t n_prop, n_accept, n_ties, n_aborts, n_windows, n_meas, n_recomputes;
@@ -159,6 +160,7 @@ struct Config {
   int32_t ks;                // k_sub
   int32_t warmup;
   int32_t recompute_every;
+  int32_t recompute_sweeps;  // batched schedule: recompute every walker every this many sweeps
   int32_t n_tau_meas;
   int32_t prec;              // PREC_FP64 or PREC_MIXED
   double tie_eps;
@@ -167,6 +169,7 @@ struct Config {
   int32_t* active_count;     // [1]
   int32_t upd_kernel;        // UPD_CUDA_CORE or UPD_TCGEN05 (mixed precision)
   const TmapDev* tmaps;      // [n_walkers][2 spins][A, B, N parity 0, N parity 1]
+  int32_t* gj_next;          // [1] next matrix of the Gauss-Jordan work queue (reset by k_build_A)
 };
 
 }  // namespace dca

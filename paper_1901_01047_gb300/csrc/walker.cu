@@ -141,7 +141,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   if (p.n_problems < 1 || !p.problems) return fail(nullptr, DCA_ERR_ARG, "need at least one problem");
   if (p.n_walkers < 1) return fail(nullptr, DCA_ERR_ARG, "n_walkers must be >= 1");
   if (p.k_sub < 1 || p.k_sub > dca::KS_MAX) return fail(nullptr, DCA_ERR_ARG, "k_sub must be in 1..128");
-  if (p.recompute_every < 0 || p.warmup_sweeps < 0 || p.n_tau_meas < 1 || p.init_config_size < 0 ||
+  if (p.recompute_sweeps < 0 || p.recompute_every < 0 || p.warmup_sweeps < 0 || p.n_tau_meas < 1 || p.init_config_size < 0 ||
       p.capacity < 0 || p.log_capacity < 0)
     return fail(nullptr, DCA_ERR_ARG, "negative or zero size parameter");
   if (p.precision != DCA_PREC_FP64 && p.precision != DCA_PREC_MIXED)
@@ -355,6 +355,8 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.W = h->d_W;
   h->cfg.P = h->d_P;
   h->cfg.active_count = h->d_active;
+  h->cfg.gj_next = h->d_active + 3;
+  h->cfg.recompute_sweeps = p.recompute_sweeps;
   h->cfg.upd_kernel = use_tc ? dca::UPD_TCGEN05 : dca::UPD_CUDA_CORE;
   h->cfg.tmaps = h->d_tmaps;
 
@@ -794,7 +796,7 @@ extern "C" DCA_API int dca_fresh_N(const dca_problem* problem, int32_t n, const 
                                {(void**)&d_tau, sizeof(double) * n},       {(void**)&d_s, sizeof(int32_t) * n},
                                {(void**)&d_N[0], sizeof(double) * nn},     {(void**)&d_N[1], sizeof(double) * nn},
                                {(void**)&d_scr[0], sizeof(double) * 2 * n}, {(void**)&d_scr[1], sizeof(double) * 2 * n},
-                               {(void**)&d_sgn, sizeof(int32_t) * 2}};
+                               {(void**)&d_sgn, sizeof(int32_t) * 4}};
   size_t total = 0;
   for (auto& pc : pieces) total += align_up(pc.bytes, 256);
   char* base = nullptr;
@@ -832,6 +834,7 @@ extern "C" DCA_API int dca_fresh_N(const dca_problem* problem, int32_t n, const 
   cfg.n_walkers = 1;
   cfg.W = d_W;
   cfg.P = d_P;
+  cfg.gj_next = d_sgn + 2;  // work queue of the inverse
   int32_t sgn[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpy(d_ss, pr.site_sub, sizeof(int32_t) * nc2, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_sa, add.data(), sizeof(int32_t) * nc2, cudaMemcpyHostToDevice);
