@@ -100,7 +100,17 @@ typedef struct {
                                       first window of every this-many-th sweep (all walkers in
                                       the same window, so the inverses share the GPU); 0 = off.
                                       Independent of recompute_every. */
+  int32_t recompute_method;        /* DCA_RECOMPUTE_* */
 } dca_walker_params;
+
+/* Recompute of N (the inverse of e^V - g0 (e^V - 1), Eq. Zk, formed from
+ * scratch in FP64 for the current configuration):
+ *   AUTO: DCA_PREC_FP64 inverts it by Gauss-Jordan with partial pivoting;
+ *         DCA_PREC_MIXED applies one Newton step N <- N + N (I - A N) with the
+ *         residual in FP64 (squares the relative error of the FP32 N).
+ *   GJ:   Gauss-Jordan on both paths. */
+#define DCA_RECOMPUTE_AUTO 0
+#define DCA_RECOMPUTE_GJ 1
 
 /* N-update kernels of the mixed-precision path (ignored by DCA_PREC_FP64). */
 #define DCA_UPD_AUTO 0       /* DCA_UPD_TCGEN05 */

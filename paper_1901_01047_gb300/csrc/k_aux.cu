@@ -467,9 +467,18 @@ int launch_recompute(int part, const Config& cfg, int max_cap, int* d_sgn, cudaS
       k_build_A<<<g, 256, 0, st>>>(cfg, 1);
       return 1;
     case GROUP_RECOMPUTE:
+      if (cfg.prec == PREC_MIXED && !cfg.recompute_gj) {
+        launch_refine_gemms(cfg, max_cap, st);
+        return 2;
+      }
       launch_gj(cfg, 1, max_cap, d_sgn, st);
       return 1;
     case GROUP_RECOMPUTE_POST:
+      if (cfg.prec == PREC_MIXED && !cfg.recompute_gj) {
+        launch_refine_adopt(cfg, max_cap, st);
+        k_recompute_adopt<<<W, 256, 0, st>>>(cfg);
+        return 2;
+      }
       if (cfg.prec == PREC_MIXED) {
         k_store_fp32<<<g, 256, 0, st>>>(cfg, 1);
         k_recompute_drift<float><<<gd, 256, 0, st>>>(cfg);

@@ -1,0 +1,215 @@
+// k_refine.cu -- periodic recompute of the FP32 N matrices (mixed
+// precision) as a Newton-Schulz step against the from-scratch inverse
+// N^-1 = A = e^V - g0 (e^V - 1) of the current configuration (Eq. Zk), which
+// k_build_A forms in FP64:
+//     R  = I - A N0      FP64 products and accumulation
+//     N1 = N0 + N0 R     FP32 (R is of the size of the drift)
+// One step squares the relative error of N0: an FP32 N0 that drifted by 1e-5
+// comes back to the FP32 rounding level.  Both products are tiled GEMMs on a
+// persistent grid over (walker-spin, 64 x 64 output tile), so one walker's
+// recompute spreads over every SM; the FP64 product is the whole cost (GB300
+// FP64 runs at ~2 FMA per clock per SM).
+//
+// Buffers (the recompute follows a compaction, all n rows live):
+//   A   Ascr[sp] (FP64)          -> R  into N[parity ^ 1][sp] (FP32)
+//   N0  N[parity][sp]            -> N1 into Ascr[sp] viewed as FP32
+// k_refine_adopt then measures the drift max|N1 - N0| / max|N1| and copies
+// N1 into N[parity ^ 1][sp] for the parity switch.
+#include <cstdint>
+
+#include "device_util.cuh"
+#include "kernels.h"
+#include "state.h"
+
+namespace dca {
+
+constexpr int RT = 64;   // output tile
+constexpr int RK = 16;   // K step of the FP64 product
+constexpr int RK32 = 32; // K step of the FP32 product
+
+__device__ __forceinline__ bool refine_wants(const WalkerDev& w) {
+  return w.active && w.recompute_pending && w.status == ST_OK;
+}
+
+__device__ __forceinline__ long long refine_tiles(const WalkerDev& w) {
+  const long long t = (w.n + RT - 1) / RT;
+  return refine_wants(w) ? t * t : 0;
+}
+
+// R = I - A N0, FP64.  Thread (tx, ty) of 16 x 16 owns rows ty + 16 a and
+// columns tx + 16 b (a, b < 4) of the tile.
+__global__ void __launch_bounds__(256) k_refine_resid(Config cfg) {
+  __shared__ double As[RK][RT + 1];  // [k][i]
+  __shared__ double Bs[RK][RT];      // [k][j]
+  for_each_item(
+      2 * cfg.n_walkers, [&](int s) -> long long { return refine_tiles(cfg.W[s >> 1]); },
+      [&](int s, int item) {
+        const WalkerDev& w = cfg.W[s >> 1];
+        const int sp = s & 1, n = w.n, ld = w.cap;
+        const int tiles = (n + RT - 1) / RT;
+        const int i0 = (item / tiles) * RT, j0 = (item - (item / tiles) * tiles) * RT;
+        const double* A = w.Ascr[sp];
+        const float* N0 = (const float*)w.N[w.parity][sp];
+        float* R = (float*)w.N[w.parity ^ 1][sp];
+        const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+        double acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+        for (int k0 = 0; k0 < n; k0 += RK) {
+          __syncthreads();
+          for (int e = threadIdx.x; e < RT * RK; e += 256) {
+            const int i = e / RK, k = e - i * RK;  // k fastest: rows of A
+            As[k][i] = (i0 + i < n && k0 + k < n) ? A[(size_t)(i0 + i) * ld + k0 + k] : 0.0;
+            const int kk = e / RT, j = e - kk * RT;  // j fastest: rows of N0
+            Bs[kk][j] = (k0 + kk < n && j0 + j < n) ? (double)N0[(size_t)(k0 + kk) * ld + j0 + j] : 0.0;
+          }
+          __syncthreads();
+#pragma unroll
+          for (int k = 0; k < RK; ++k) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[k][ty + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[k][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int i = i0 + ty + 16 * a;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int j = j0 + tx + 16 * b;
+            if (i < n && j < n) R[(size_t)i * ld + j] = (float)((i == j ? 1.0 : 0.0) - acc[a][b]);
+          }
+        }
+      });
+}
+
+// N1 = N0 + N0 R, FP32, into Ascr[sp] viewed as FP32 (ld = cap).
+__global__ void __launch_bounds__(256) k_refine_correct(Config cfg) {
+  __shared__ float As[RK32][RT + 1];  // [k][i] of N0
+  __shared__ float Bs[RK32][RT];      // [k][j] of R
+  for_each_item(
+      2 * cfg.n_walkers, [&](int s) -> long long { return refine_tiles(cfg.W[s >> 1]); },
+      [&](int s, int item) {
+        const WalkerDev& w = cfg.W[s >> 1];
+        const int sp = s & 1, n = w.n, ld = w.cap;
+        const int tiles = (n + RT - 1) / RT;
+        const int i0 = (item / tiles) * RT, j0 = (item - (item / tiles) * tiles) * RT;
+        const float* N0 = (const float*)w.N[w.parity][sp];
+        const float* R = (const float*)w.N[w.parity ^ 1][sp];
+        float* N1 = (float*)w.Ascr[sp];
+        const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+        for (int k0 = 0; k0 < n; k0 += RK32) {
+          __syncthreads();
+          for (int e = threadIdx.x; e < RT * RK32; e += 256) {
+            const int i = e / RK32, k = e - i * RK32;
+            As[k][i] = (i0 + i < n && k0 + k < n) ? N0[(size_t)(i0 + i) * ld + k0 + k] : 0.0f;
+            const int kk = e / RT, j = e - kk * RT;
+            Bs[kk][j] = (k0 + kk < n && j0 + j < n) ? R[(size_t)(k0 + kk) * ld + j0 + j] : 0.0f;
+          }
+          __syncthreads();
+#pragma unroll 8
+          for (int k = 0; k < RK32; ++k) {
+            float av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[k][ty + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[k][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int i = i0 + ty + 16 * a;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int j = j0 + tx + 16 * b;
+            if (i < n && j < n) N1[(size_t)i * ld + j] = N0[(size_t)i * ld + j] + acc[a][b];
+          }
+        }
+      });
+}
+
+// Drift max|N1 - N0| and max|N1| (atomicMax on the bits of non-negative
+// doubles, folded into the walker by k_recompute_adopt) and the copy of N1
+// into N[parity ^ 1].  Persistent grid, 2048 entries per item.
+__global__ void __launch_bounds__(256) k_refine_adopt(Config cfg) {
+  __shared__ double s_d[8], s_n[8];
+  for_each_item(
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        return refine_wants(w) ? blocks_of((long long)w.n * w.n, 2048) : 0;
+      },
+      [&](int s, int item) {
+        WalkerDev& w = cfg.W[s >> 1];
+        const int sp = s & 1, n = w.n, ld = w.cap;
+        const float* N0 = (const float*)w.N[w.parity][sp];
+        const float* N1 = (const float*)w.Ascr[sp];
+        float* dst = (float*)w.N[w.parity ^ 1][sp];
+        double dmax = 0.0, nmax = 0.0;
+        const long long e0 = (long long)item * 2048, e1 = min(e0 + 2048, (long long)n * n);
+        for (long long idx = e0 + threadIdx.x; idx < e1; idx += 256) {
+          const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
+          const size_t o = (size_t)i * ld + j;
+          const float b = N1[o];
+          dmax = fmax(dmax, fabs((double)b - (double)N0[o]));
+          nmax = fmax(nmax, fabs((double)b));
+          dst[o] = b;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+          nmax = fmax(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+          s_d[threadIdx.x >> 5] = dmax;
+          s_n[threadIdx.x >> 5] = nmax;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double d = 0.0, m = 0.0;
+          for (int k = 0; k < 8; ++k) {
+            d = fmax(d, s_d[k]);
+            m = fmax(m, s_n[k]);
+          }
+          atomicMax(&w.drift_bits[0], (unsigned long long)__double_as_longlong(d));
+          atomicMax(&w.drift_bits[1], (unsigned long long)__double_as_longlong(m));
+        }
+        __syncthreads();
+      });
+}
+
+static int refine_grid(long long items) {
+  constexpr int kPersist = 4 * 152;
+  return (int)(items < 1 ? 1 : (items < kPersist ? items : kPersist));
+}
+
+void launch_refine_gemms(const Config& cfg, int max_cap, cudaStream_t st) {
+  const long long t = (max_cap + RT - 1) / RT;
+  const int g = refine_grid(2LL * cfg.n_walkers * t * t);
+  k_refine_resid<<<g, 256, 0, st>>>(cfg);
+  k_refine_correct<<<g, 256, 0, st>>>(cfg);
+}
+
+void launch_refine_adopt(const Config& cfg, int max_cap, cudaStream_t st) {
+  k_refine_adopt<<<refine_grid(2LL * cfg.n_walkers * blocks_of((long long)max_cap * max_cap, 2048)), 256, 0, st>>>(
+      cfg);
+}
+
+}  // namespace dca

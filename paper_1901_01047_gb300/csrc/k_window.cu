@@ -285,68 +285,62 @@ constexpr int ext_smem_bytes() {
   return (int)sizeof(A) * (ET * (ET + 1) + ET * (EC + 1) + EC * (ET + 1));
 }
 
-// G_ext[n+c', n+c] = X[c',:] . g0[:, c] + g0(r_c' - r_c, tau_c' - tau_c).
-// grid = (KS_MAX candidates c, walkers * 2); block = 128 (4 warps over c').
-// The products run in the arithmetic type A.
+// G_ext[n+c', n+c] = X[c',:] . V[c,:] + g0(r_c' - r_c, tau_c' - tau_c)
+// (V[c, j] = g0(r_j - r_c, tau_j - tau_c), zero on dead j).  Item = 32 x 32
+// tile of candidate pairs of one walker-spin; the X and V rows are staged
+// through shared memory 32 columns at a time, so each row is read once per
+// tile.  The products run in the arithmetic type A.  Block 256 = 32 c x 8 c'.
 template <typename A>
-__device__ __forceinline__ void cand_cc_item(const Config& cfg, int wi, int sp, int c);
-
-template <typename A>
-__global__ void __launch_bounds__(128) k_cand_cc(Config cfg) {
+__global__ void __launch_bounds__(256) k_cand_cc(Config cfg) {
+  __shared__ A Xs[32][33];
+  __shared__ A Vs[32][33];
   for_each_item(
       2 * cfg.n_walkers,
       [&](int s) -> long long {
         const WalkerDev& w = cfg.W[s >> 1];
-        return w.active ? w.n_cand : 0;
+        const long long t = (w.n_cand + 31) / 32;
+        return (w.active && w.n_cand > 0) ? t * t : 0;
       },
-      [&](int s, int c) { cand_cc_item<A>(cfg, s >> 1, s & 1, c); });
-}
-
-template <typename A>
-__device__ __forceinline__ void cand_cc_item(const Config& cfg, int wi, int sp, int c) {
-  const WalkerDev& w = cfg.W[wi];
-  const int n = w.n, nc_ = w.n_cand;
-  const ProblemDev& pb = cfg.P[w.problem];
-  const int ld = w.cap, par = w.parity;
-  const int* vsite = w.vsite[par];
-  const double* vtau = w.vtau[par];
-  const int* vs = w.vs[par];
-  const int rc = vsite[n + c];
-  const double tc = vtau[n + c];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __shared__ A v[1024];
-  A acc[KS_MAX / 4];
+      [&](int s, int item) {
+        const WalkerDev& w = cfg.W[s >> 1];
+        const int sp = s & 1, n = w.n, nc_ = w.n_cand, ld = w.cap, par = w.parity;
+        const int tiles = (nc_ + 31) / 32;
+        const int cpb = (item / tiles) * 32, cb = (item - (item / tiles) * tiles) * 32;
+        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+        const double* X = w.Xr[sp];
+        const double* V = w.Vb[sp];
+        A acc[4] = {(A)0, (A)0, (A)0, (A)0};
+        for (int j0 = 0; j0 < n; j0 += 32) {
+          __syncthreads();
+          const int j = j0 + tx;
+          for (int r = ty; r < 32; r += 8) {
+            Xs[r][tx] = (A)((cpb + r < nc_ && j < n) ? X[(size_t)(cpb + r) * ld + j] : 0.0);
+            Vs[r][tx] = (A)((cb + r < nc_ && j < n) ? V[(size_t)(cb + r) * ld + j] : 0.0);
+          }
+          __syncthreads();
+#pragma unroll 8
+          for (int jj = 0; jj < 32; ++jj) {
+            const A v = Vs[tx][jj];
 #pragma unroll
-  for (int m = 0; m < KS_MAX / 4; ++m) acc[m] = (A)0;
-  for (int j0 = 0; j0 < n; j0 += 1024) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < 1024; t += 128) {
-      const int j = j0 + t;
-      v[t] = (A)(j < n ? w.Vb[sp][(size_t)c * ld + j] : 0.0);
-    }
-    __syncthreads();
+            for (int m = 0; m < 4; ++m) acc[m] += Xs[ty + 8 * m][jj] * v;
+          }
+        }
+        const int c = cb + tx;
+        if (c < nc_) {
+          const ProblemDev& pb = cfg.P[w.problem];
+          const int rc = w.vsite[par][n + c];
+          const double tc = w.vtau[par][n + c];
 #pragma unroll
-    for (int m = 0; m < KS_MAX / 4; ++m) {
-      const int cp = warp + 4 * m;
-      if (cp < nc_) {
-        const double* X = w.Xr[sp] + (size_t)cp * ld;
-        A s = (A)0;
-        for (int t = lane; t < 1024 && j0 + t < n; t += 32) s += (A)X[j0 + t] * v[t];
-        acc[m] += s;
-      }
-    }
-  }
-#pragma unroll
-  for (int m = 0; m < KS_MAX / 4; ++m) {
-    const int cp = warp + 4 * m;
-    double s = (double)acc[m];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0 && cp < nc_) {
-      const double g = (cp == c) ? g0_diag(pb, sp, rc) : g0_pair(pb, sp, vsite[n + cp], vtau[n + cp], rc, tc);
-      w.Gc[sp][(size_t)c * ld + n + cp] = s + g;
-    }
-  }
+          for (int m = 0; m < 4; ++m) {
+            const int cp = cpb + ty + 8 * m;
+            if (cp < nc_) {
+              const double g = (cp == c) ? g0_diag(pb, sp, rc)
+                                         : g0_pair(pb, sp, w.vsite[par][n + cp], w.vtau[par][n + cp], rc, tc);
+              w.Gc[sp][(size_t)c * ld + n + cp] = (double)acc[m] + g;
+            }
+          }
+        }
+      });
 }
 
 // ---------------------------------------------------------------------------
@@ -819,6 +813,7 @@ __global__ void __launch_bounds__(256) k_upd_border(Config cfg) {
       const int m = idx / n, j = idx - m * n;
       const int c = w.acc_slot[m];
       const double* L = w.Lp[sp] + (size_t)(n + c) * KS_MAX;
+      // FP64 on both paths: the new row X + L'R is formed with cancellation
       double acc = w.Xr[sp][(size_t)c * ld + j];
       for (int p = 0; p < l; ++p) acc += L[p] * (double)Rr[(size_t)p * ld + j];
       stN(N, (size_t)(n + m) * ld + j, acc);
@@ -999,7 +994,7 @@ static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_
     case GROUP_EXTEND:
       k_cand_zero<<<grid_for(S * kc), 256, 0, st>>>(cfg);
       k_cand_ext<T, A><<<grid_for(S * t64 * t64), 256, ext_smem_bytes<A>(), st>>>(cfg);
-      k_cand_cc<A><<<grid_for(S * cfg.ks), 128, 0, st>>>(cfg);
+      k_cand_cc<A><<<grid_for(S * 16), 256, 0, st>>>(cfg);
       return 3;
     case GROUP_METROPOLIS: {
       const int sm = cfg.ks <= METRO_SMEM_KS ? (int)sizeof(double) * 2 * cfg.ks * cfg.ks : 0;

@@ -44,6 +44,11 @@ void launch_init(const Config& cfg, int n0, int max_cap, int* d_sgn, cudaStream_
 void launch_fresh_inverse(const Config& cfg, int max_n, int* d_sgn, cudaStream_t st);
 // Gauss-Jordan inverse of the FP64 work matrices, one 8-block cluster each.
 void launch_gj(const Config& cfg, int mode, int max_n, int* d_sgn, cudaStream_t st);
+// Mixed-precision recompute by one Newton step against the FP64 A = N^-1:
+// the two products (R = I - A N0 in FP64, N1 = N0 + N0 R in FP32), then the
+// drift measurement and the copy of N1 into the other buffer.
+void launch_refine_gemms(const Config& cfg, int max_cap, cudaStream_t st);
+void launch_refine_adopt(const Config& cfg, int max_cap, cudaStream_t st);
 // part: GROUP_RECOMPUTE_PRE, GROUP_RECOMPUTE or GROUP_RECOMPUTE_POST.
 int launch_recompute(int part, const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st);
 int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);

@@ -161,6 +161,7 @@ struct Config {
   int32_t warmup;
   int32_t recompute_every;
   int32_t recompute_sweeps;  // batched schedule: recompute every walker every this many sweeps
+  int32_t recompute_gj;      // mixed path: Gauss-Jordan inverse instead of the Newton step
   int32_t n_tau_meas;
   int32_t prec;              // PREC_FP64 or PREC_MIXED
   double tie_eps;

@@ -217,6 +217,10 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
 
   // ---- walkers ----
   const int KS = dca::KS_MAX;
+  if (p.recompute_method < DCA_RECOMPUTE_AUTO || p.recompute_method > DCA_RECOMPUTE_GJ) {
+    h->err = "recompute_method must be one of DCA_RECOMPUTE_*";
+    return bail(DCA_ERR_ARG);
+  }
   if (p.update_kernel < DCA_UPD_AUTO || p.update_kernel > DCA_UPD_TCGEN05) {
     h->err = "update_kernel must be one of DCA_UPD_*";
     return bail(DCA_ERR_ARG);
@@ -357,6 +361,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.active_count = h->d_active;
   h->cfg.gj_next = h->d_active + 3;
   h->cfg.recompute_sweeps = p.recompute_sweeps;
+  h->cfg.recompute_gj = p.recompute_method == DCA_RECOMPUTE_GJ ? 1 : 0;
   h->cfg.upd_kernel = use_tc ? dca::UPD_TCGEN05 : dca::UPD_CUDA_CORE;
   h->cfg.tmaps = h->d_tmaps;
 
@@ -413,7 +418,8 @@ static cudaEvent_t next_event(dca_walker* h) {
 }
 
 static int n_window_groups(const dca_walker* h) {
-  return h->R > 0 ? (int)(sizeof(dca::WINDOW_GROUPS) / sizeof(int)) : dca::N_WINDOW_GROUPS_NO_RECOMPUTE;
+  return (h->R > 0 || h->cfg.recompute_sweeps > 0) ? (int)(sizeof(dca::WINDOW_GROUPS) / sizeof(int))
+                                                   : dca::N_WINDOW_GROUPS_NO_RECOMPUTE;
 }
 
 // Launch one kernel group, bracketed by events when its timing bit is set.

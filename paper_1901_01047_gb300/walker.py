@@ -58,6 +58,7 @@ class Params(C.Structure):
         ("log_capacity", C.c_int64),
         ("update_kernel", C.c_int32),
         ("recompute_sweeps", C.c_int32),
+        ("recompute_method", C.c_int32),
     ]
 
 
@@ -201,7 +202,7 @@ class Walkers:
     def __init__(self, problems, n_walkers=1, walker_problem=None, k_sub=32, recompute_every=64,
                  warmup_sweeps=20, n_tau_meas=64, precision="fp64", init_config_size=10, capacity=0,
                  seed=0, tie_eps=1e-10, log_capacity=0, update_kernel="auto", recompute_sweeps=0,
-                 stream=None):
+                 recompute_method="auto", stream=None):
         L = load()
         self._keep = []
         probs = (Problem * len(problems))()
@@ -240,6 +241,7 @@ class Walkers:
         p.tie_eps = float(tie_eps)
         p.log_capacity = int(log_capacity)
         p.recompute_sweeps = int(recompute_sweeps)
+        p.recompute_method = {"auto": 0, "gj": 1}[recompute_method]
         p.update_kernel = UPDATE_KERNELS[update_kernel] if isinstance(update_kernel, str) else int(update_kernel)
         self.n_walkers = int(n_walkers)
         self.n_tau_meas = int(n_tau_meas)

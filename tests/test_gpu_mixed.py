@@ -24,7 +24,7 @@ def _walkers(**kw):
 
 
 def replay(nc, tp, U, beta, mu, k_sub, sweeps, R, seed=0, ntm=32, n_tau=4096, update_kernel="auto",
-           return_state=False):
+           return_state=False, recompute_method="auto"):
     c, eps, kr, G0 = problem(nc, 1.0, tp, U, beta, mu, n_tau)
     ow = ctaux.OracleWalker(nc, c.site_sub, U, beta, 1.0, G0, warmup_sweeps=10, n_tau_meas=ntm, seed=seed)
     ow.enable_log(1 << 24)
@@ -32,7 +32,7 @@ def replay(nc, tp, U, beta, mu, k_sub, sweeps, R, seed=0, ntm=32, n_tau=4096, up
     log = ow.log()
     gw = _walkers(problems=[dict(nc=nc, site_sub=c.site_sub, U=U, beta=beta, K=1.0, G0=G0)], k_sub=k_sub,
                   recompute_every=R, warmup_sweeps=10, n_tau_meas=ntm, seed=seed, precision="mixed",
-                  log_capacity=1 << 24, update_kernel=update_kernel)
+                  log_capacity=1 << 24, update_kernel=update_kernel, recompute_method=recompute_method)
     gw.set_forced_decisions(0, log)
     gw.sweep(sweeps)
     gs, os_ = gw.state(0), ow.state()
@@ -111,3 +111,35 @@ def test_tensor_core_update_matches_cuda_core_update(k_sub):
     for sp in range(2):
         a, b = gs_c["N"][sp], gs_t["N"][sp]
         assert np.abs(a - b).max() <= 2 * (eN_c + eN_t) * np.abs(a).max() + 1e-12
+
+
+def test_mixed_batched_sweep_synchronised_recompute():
+    # Uneven batch (two cluster sizes, several temperatures) with the batched
+    # recompute schedule: every walker recomputes after the first window of
+    # every second sweep, and the FP32 drift it removes stays small.
+    import torch
+    from paper_1901_01047_gb300 import walker
+    probs = []
+    for nc, beta in [(4, 4.0), (8, 3.0), (4, 8.0), (8, 5.0)]:
+        c, eps, kr, G0 = problem(nc, 1.0, 0.0, 5.0, beta, 2.5, 2048)
+        probs.append(dict(nc=nc, site_sub=c.site_sub, U=5.0, beta=beta, K=1.0, G0=G0))
+    gw = walker.Walkers(probs, n_walkers=16, k_sub=32, recompute_every=0, recompute_sweeps=2, warmup_sweeps=4,
+                        n_tau_meas=16, precision="mixed", seed=11, stream=torch.cuda.current_stream().cuda_stream)
+    gw.sweep(21)
+    for st in gw.stats():
+        assert st["status"] == 0
+        assert st["recomputes"] == 10, st["recomputes"]
+        assert st["max_drift"] < 1e-3, st["max_drift"]
+    gw.close()
+
+
+@pytest.mark.parametrize("method", ["auto", "gj"])
+def test_mixed_recompute_methods_restore_accuracy(method):
+    # The Newton step (FP64 residual, FP32 correction) and the Gauss-Jordan
+    # inverse both bring N back to the FP32 level: recomputing every 8
+    # submatrix updates keeps the error of N and G small on the 16-site case.
+    errN, errG, st, _ = replay(16, -0.15, 6.0, 4.0, 2.85, 64, 60, 8, ntm=16, n_tau=2048, recompute_method=method)
+    assert st["status"] == 0 and st["recomputes"] >= 10
+    assert errN < 1e-4, errN
+    assert errG < 2e-5, errG
+    assert st["max_drift"] < 1e-3

@@ -25,11 +25,12 @@ def _walkers(**kw):
 
 
 def run_pair(nc, t, tp, U, beta, mu, n_tau, k_sub, sweeps, seed=0, warmup=10, init=10, ntm=16, R=0,
-             walkers=1, K=1.0, chunks=1, timed=False):
+             walkers=1, K=1.0, chunks=1, timed=False, R_sweeps=0):
     c, eps, kr, G0 = problem(nc, t, tp, U, beta, mu, n_tau)
     prob = dict(nc=nc, site_sub=c.site_sub, U=U, beta=beta, K=K, G0=G0)
     gw = _walkers(problems=[prob], n_walkers=walkers, k_sub=k_sub, recompute_every=R, warmup_sweeps=warmup,
-                  n_tau_meas=ntm, init_config_size=init, seed=seed, log_capacity=1 << 23)
+                  n_tau_meas=ntm, init_config_size=init, seed=seed, log_capacity=1 << 23,
+                  recompute_sweeps=R_sweeps)
     if timed:  # host-driven window loop with CUDA events instead of the graph loop
         from paper_1901_01047_gb300 import walker
         gw.set_timing(walker.GROUPS)
@@ -139,3 +140,16 @@ def test_g0_builder_matches_oracle_builder():
         ref = og0.g0_table(eps, kr, mu, U, beta, 2048)
         got = walker.g0_isolated_cluster(eps, kr, mu, U, beta, 2048)
         assert np.abs(got - ref).max() < 1e-13
+
+
+def test_batched_sweep_synchronised_recompute_keeps_parity():
+    # Eight walkers recompute together after the first window of every third
+    # sweep; in FP64 a recompute changes N only by rounding, so every chain
+    # still matches the oracle (which never recomputes) decision for decision.
+    res = run_pair(4, 1.0, 0.0, 4.0, 6.0, 0.9450480104035819, 2048, k_sub=16, sweeps=60, seed=5, warmup=6,
+                   walkers=8, R_sweeps=3)
+    check(res)
+    for r in res:
+        st = r[8]
+        assert st["recomputes"] == (60 - 1) // 3, st["recomputes"]
+        assert st["max_drift"] < 1e-9
