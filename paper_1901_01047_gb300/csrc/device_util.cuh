@@ -99,8 +99,9 @@ __device__ __forceinline__ GridTime grid_time(double tau, double tau_scale) {
   return GridTime{(int)fl, (float)(x - fl)};
 }
 
-// g0(t_a - t_b) from one table row with the conventions of g0_interp.
-__device__ __forceinline__ float g0_interp_grid(const double* __restrict__ row, int n_tau, GridTime a, GridTime b) {
+// g0(t_a - t_b) from one row of the FP32 copy of the table, with the
+// conventions of g0_interp.
+__device__ __forceinline__ float g0_interp_grid(const float* __restrict__ row, int n_tau, GridTime a, GridTime b) {
   int l = a.i - b.i;
   float f = a.f - b.f;
   if (f < 0.0f) {
@@ -116,14 +117,26 @@ __device__ __forceinline__ float g0_interp_grid(const double* __restrict__ row, 
     f += (float)(l - (n_tau - 1));
     l = n_tau - 1;
   }
-  const float lo = (float)__ldg(row + l), hi = (float)__ldg(row + l + 1);
+  const float lo = __ldg(row + l), hi = __ldg(row + l + 1);
   return sgn * (lo + f * (hi - lo));
+}
+
+// Row of the FP32 g0 table for displacement class d of spin sp.
+__device__ __forceinline__ const float* g0f_row(const ProblemDev& p, int sp, int d) {
+  return p.g0f + ((size_t)sp * p.nc + d) * (size_t)(p.n_tau + 1);
 }
 
 // e^{V} of a vertex with stored auxiliary spin s: s = 0 marks a dead
 // (non-interacting) vertex, V = 0.
 __device__ __forceinline__ double expV(const ProblemDev& p, int sp, int s) {
   return s == 0 ? 1.0 : p.expV[sp][s > 0 ? 1 : 0];
+}
+
+// Load of a stored value directly in the arithmetic type A (no FP64 round
+// trip for FP32 storage: on GB300 every FP64 conversion costs an FP64 issue).
+template <typename A, typename T>
+__device__ __forceinline__ A ldA(const T* p, size_t i) {
+  return (A)p[i];
 }
 
 // Storage of N: FP64 or FP32 (mixed precision); arithmetic around it is FP64.
@@ -134,22 +147,76 @@ __device__ __forceinline__ void stN(float* p, size_t i, double v) { p[i] = (floa
 
 // Persistent, load-balanced iteration over the work items of `nsets` sets
 // (walker-spin pairs, or walkers): set s has count(s) items, and item t of
-// set s goes to block (prefix(s) + t) mod gridDim.x.  Every block walks the
-// sets in order keeping a running prefix, so the loop variables are uniform
-// over the block and `body` may use __syncthreads().
+// set s is global item prefix(s) + t, taken by block (global item) mod
+// gridDim.x.  The block evaluates the counts of up to FE_CHUNK sets in
+// parallel and scans them in shared memory (a serial walk over the walker
+// records costs one dependent global load per set and dominated idle
+// launches); items find their set by binary search.  All loop variables are
+// uniform over the block, so `body` may use __syncthreads().  blockDim.x must
+// be a multiple of 32; a set holds fewer than 2^31 items and a chunk's total
+// fits in an int.
+constexpr int FE_CHUNK = 1024;
+
 template <typename CountF, typename BodyF>
 __device__ __forceinline__ void for_each_item(int nsets, CountF count, BodyF body) {
-  if (nsets <= 0) return;
-  int s = 0;
-  long long base = 0;
-  long long cnt = count(0);
-  for (long long item = blockIdx.x;; item += gridDim.x) {
-    while (item >= base + cnt) {
-      base += cnt;
-      if (++s >= nsets) return;
-      cnt = count(s);
+  __shared__ int fe_pre[FE_CHUNK + 1];  // exclusive prefix of the chunk's counts
+  __shared__ int fe_warp[32];
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+  const long long G = gridDim.x;
+  long long base = 0;  // items of the earlier chunks (uniform over the block)
+  for (int s0 = 0; s0 < nsets; s0 += FE_CHUNK) {
+    const int m = min(FE_CHUNK, nsets - s0);
+    __syncthreads();  // earlier readers of fe_pre are done
+    // 1. each thread counts a contiguous segment of the chunk's sets
+    const int per = (m + nthr - 1) / nthr;
+    const int k0 = min(m, tid * per), k1 = min(m, k0 + per);
+    int own = 0;
+    for (int k = k0; k < k1; ++k) {
+      const int c = (int)count(s0 + k);
+      fe_pre[k] = c;
+      own += c;
     }
-    body(s, (int)(item - base));
+    // 2. block-wide scan of the segment totals (warp shuffles, then over warps)
+    int incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) fe_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      int v = lane < nw ? fe_warp[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+      }
+      if (lane < nw) fe_warp[lane] = v;
+    }
+    __syncthreads();
+    // 3. counts -> exclusive prefix, each thread on its own segment
+    int run = incl - own + (warp > 0 ? fe_warp[warp - 1] : 0);
+    for (int k = k0; k < k1; ++k) {
+      const int c = fe_pre[k];
+      fe_pre[k] = run;
+      run += c;
+    }
+    const int total = fe_warp[nw - 1];
+    if (tid == 0) fe_pre[m] = total;
+    __syncthreads();
+    // 4. this block's items: global g in [base, base + total) with g = blockIdx (mod G)
+    for (long long g = base + ((((long long)blockIdx.x - base) % G) + G) % G; g < base + total; g += G) {
+      const int local = (int)(g - base);
+      int lo = 0, hi = m;  // fe_pre[lo] <= local < fe_pre[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (fe_pre[mid] <= local) lo = mid;
+        else hi = mid;
+      }
+      body(s0 + lo, local - fe_pre[lo]);
+    }
+    base += total;
   }
 }
 

@@ -214,7 +214,17 @@ __global__ void __launch_bounds__(256) k_meas_gr(Config cfg) {
   if (idx < total) {
     const int rp = idx / n, j = idx - rp * n;
     const bool live = w.vs[par][j] != 0;  // a dead column of N is e_j: no contribution
-    w.gR[((size_t)sp * nc + rp) * w.cap + j] = live ? g0_pair(pb, sp, w.vsite[par][j], w.vtau[par][j], rp, 0.0) : 0.0;
+    const size_t o = ((size_t)sp * nc + rp) * w.cap + j;
+    if (cfg.prec == PREC_MIXED) {
+      float g = 0.0f;
+      if (live) {
+        const int d = __ldg(pb.site_sub + w.vsite[par][j] * nc + rp);
+        g = g0_interp_grid(g0f_row(pb, sp, d), pb.n_tau, grid_time(w.vtau[par][j], pb.tau_scale), GridTime{0, 0.0f});
+      }
+      reinterpret_cast<float*>(w.gR)[o] = g;
+    } else {
+      w.gR[o] = live ? g0_pair(pb, sp, w.vsite[par][j], w.vtau[par][j], rp, 0.0) : 0.0;
+    }
   }
       });
 }
@@ -247,11 +257,11 @@ __global__ void __launch_bounds__(256) k_meas_b(Config cfg) {
           __syncthreads();
           {
             const int j = j0 + lane;
-            sN[warp][lane] = (A)((i < n && j < n) ? ldN(N, (size_t)i * ld + j) : 0.0);
+            sN[warp][lane] = (i < n && j < n) ? ldA<A>(N, (size_t)i * ld + j) : (A)0;
           }
           for (int e = threadIdx.x; e < (two ? 64 : 32) * 32; e += 256) {
             const int rp = e >> 5, jl = e & 31, j = j0 + jl;
-            sG[rp][jl] = (A)((rp < nc && j < n) ? w.gR[((size_t)sp * nc + rp) * ld + j] : 0.0);
+            sG[rp][jl] = (rp < nc && j < n) ? reinterpret_cast<const A*>(w.gR)[((size_t)sp * nc + rp) * ld + j] : (A)0;
           }
           __syncthreads();
           if (two) {
@@ -267,9 +277,10 @@ __global__ void __launch_bounds__(256) k_meas_b(Config cfg) {
           }
         }
         if (i < n) {
-          const double f = expV(pb, sp, w.vs[par][i]) - 1.0;
-          if (lane < nc) w.bvec[((size_t)sp * nc + lane) * ld + i] = f * (double)acc0;
-          if (lane + 32 < nc) w.bvec[((size_t)sp * nc + lane + 32) * ld + i] = f * (double)acc1;
+          const A f = (A)(expV(pb, sp, w.vs[par][i]) - 1.0);
+          A* bv = reinterpret_cast<A*>(w.bvec);
+          if (lane < nc) bv[((size_t)sp * nc + lane) * ld + i] = f * acc0;
+          if (lane + 32 < nc) bv[((size_t)sp * nc + lane + 32) * ld + i] = f * acc1;
         }
       });
 }
@@ -344,7 +355,7 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
       if (a < ntm && d >= 0) {
         const double* row = row_base + (size_t)d * np1;
         if (kGrid) {
-          v = (A)g0_interp_grid(row, pb.n_tau, s_ga[al], s_gi[il]);
+          v = (A)g0_interp_grid(g0f_row(pb, sp, d), pb.n_tau, s_ga[al], s_gi[il]);
         } else {
           const double ta_ = ((double)a + 0.5) * pb.beta / (double)ntm;
           v = (A)g0_interp(row, pb.n_tau, pb.beta, pb.tau_scale, ta_ - vtau[i0 + il]);
@@ -355,7 +366,7 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
     for (int e = tid; e < MK * MR; e += 256) {
       const int il = e / MR, rp = e - il * MR;
       const int i = i0 + il;
-      Bs[il][rp] = (A)((i < n && rp < nc) ? w.bvec[((size_t)sp * nc + rp) * ld + i] : 0.0);
+      Bs[il][rp] = (i < n && rp < nc) ? reinterpret_cast<const A*>(w.bvec)[((size_t)sp * nc + rp) * ld + i] : (A)0;
     }
     __syncthreads();
 #pragma unroll 4
@@ -502,13 +513,17 @@ void launch_fresh_inverse(const Config& cfg, int max_n, int* d_sgn, cudaStream_t
   launch_gj(cfg, 0, max_n, d_sgn, st);
 }
 
-__global__ void k_negate(const double* src, double* dst, size_t n) {
+// g0 = -G0 in FP64 and its FP32 copy.
+__global__ void k_negate(const double* src, double* dst, float* dstf, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = -src[i];
+  if (i < n) {
+    dst[i] = -src[i];
+    dstf[i] = (float)(-src[i]);
+  }
 }
 
-void launch_negate(const double* src, double* dst, size_t n, cudaStream_t st) {
-  k_negate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
+void launch_negate(const double* src, double* dst, float* dstf, size_t n, cudaStream_t st) {
+  k_negate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, dstf, n);
 }
 
 int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) {

@@ -179,27 +179,29 @@ __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
         const double ti = w.vtau[par][i];
         const double em1 = si != 0 ? expV(pb, sp, si) - 1.0 : 0.0;
         const GridTime gi = grid_time(ti, pb.tau_scale);
-        const int np1 = pb.n_tau + 1;
-        const double* g0s = pb.g0 + (size_t)sp * pb.nc * np1;
+        const float em1f = (float)em1;
         for (int c = 0; c < nc_; ++c) {
           const size_t o = (size_t)c * ld + i;
           w.Gc[sp][o] = 0.0;
           w.Xr[sp][o] = 0.0;
-          double v = 0.0, u = 0.0;
-          if (si != 0) {
-            const int rc = s_rc[c];
-            if (mixed) {
-              const double* rv = g0s + (size_t)__ldg(pb.site_sub + ri * pb.nc + rc) * np1;
-              const double* ru = g0s + (size_t)__ldg(pb.site_sub + rc * pb.nc + ri) * np1;
-              v = (double)g0_interp_grid(rv, pb.n_tau, gi, s_gc[c]);
-              u = (double)(g0_interp_grid(ru, pb.n_tau, s_gc[c], gi) * (float)em1);
-            } else {
+          const int rc = s_rc[c];
+          if (mixed) {
+            float v = 0.0f, u = 0.0f;
+            if (si != 0) {
+              v = g0_interp_grid(g0f_row(pb, sp, __ldg(pb.site_sub + ri * pb.nc + rc)), pb.n_tau, gi, s_gc[c]);
+              u = g0_interp_grid(g0f_row(pb, sp, __ldg(pb.site_sub + rc * pb.nc + ri)), pb.n_tau, s_gc[c], gi) * em1f;
+            }
+            reinterpret_cast<float*>(w.Vb[sp])[o] = v;
+            reinterpret_cast<float*>(w.Ub[sp])[o] = u;
+          } else {
+            double v = 0.0, u = 0.0;
+            if (si != 0) {
               v = g0_pair(pb, sp, ri, ti, rc, s_tc[c]);
               u = g0_pair(pb, sp, rc, s_tc[c], ri, ti) * em1;
             }
+            w.Vb[sp][o] = v;
+            w.Ub[sp][o] = u;
           }
-          w.Vb[sp][o] = v;
-          w.Ub[sp][o] = u;
         }
       });
 }
@@ -227,54 +229,66 @@ __device__ __forceinline__ void cand_ext_tile(const Config& cfg, int wi, int sp,
   const int tiles = (n + ET - 1) / ET;
   const int ti = tile / tiles, tj = tile - ti * tiles;
   const int i0 = ti * ET, j0 = tj * ET;
-  const ProblemDev& pb = cfg.P[w.problem];
   const int ld = w.cap, par = w.parity;
   const T* __restrict__ N = (const T*)w.N[par][sp];
-  const int* vsite = w.vsite[par];
-  const double* vtau = w.vtau[par];
-  const int* vs = w.vs[par];
+  // Shared tiles: N[i][j] and its transpose (so that both products read two
+  // adjacent outputs' operands with one vector load), V[j][c], U^T[i][c].
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  A(*Ns)[ET + 1] = reinterpret_cast<A(*)[ET + 1]>(smem_raw);                  // [i][j]
-  A(*Vs)[EC + 1] = reinterpret_cast<A(*)[EC + 1]>(Ns + ET);                   // [j][c]
-  A(*Us)[ET + 1] = reinterpret_cast<A(*)[ET + 1]>(Vs + ET);                   // [c][i]
+  A(*Ns)[ET] = reinterpret_cast<A(*)[ET]>(smem_raw);          // [i][j]
+  A(*Vs)[EC] = reinterpret_cast<A(*)[EC]>(Ns + ET);           // [j][c]
+  A(*Ut)[EC] = Vs + ET;                                       // [i][c]
+  A(*Nt)[ET + 1] = reinterpret_cast<A(*)[ET + 1]>(Ut + ET);   // [j][i], padded: conflict-free transpose
   const int tid = threadIdx.x;
-  __syncthreads();  // the previous tile of this block is done with Ns
+  __syncthreads();  // the previous tile of this block is done with the shared tiles
   for (int e = tid; e < ET * ET; e += 256) {
     const int r = e / ET, cc = e - r * ET;
     const int i = i0 + r, j = j0 + cc;
-    Ns[r][cc] = (A)((i < n && j < n) ? ldN(N, (size_t)i * ld + j) : 0.0);
+    const A v = (i < n && j < n) ? ldA<A>(N, (size_t)i * ld + j) : (A)0;
+    Ns[r][cc] = v;
+    Nt[cc][r] = v;
   }
-  const int lo = tid & (ET - 1), hi = tid >> 6;  // 64 lanes x 4 groups
+  // thread: outputs 2 rows (or columns) x 4 candidates
+  const int tp = tid & 31, tc = tid >> 5;  // pair index, candidate quad (uniform per warp)
   for (int cb = 0; cb < nc_; cb += EC) {
     __syncthreads();
     for (int e = tid; e < ET * EC; e += 256) {
       const int r = e & (ET - 1), c = e >> 6;  // r fastest: coalesced rows of V and U
       const int j = j0 + r, i = i0 + r, cg = cb + c;
       const bool okc = cg < nc_;
-      Vs[r][c] = (A)((okc && j < n) ? w.Vb[sp][(size_t)cg * ld + j] : 0.0);
-      Us[c][r] = (A)((okc && i < n) ? w.Ub[sp][(size_t)cg * ld + i] : 0.0);
+      Vs[r][c] = (okc && j < n) ? reinterpret_cast<const A*>(w.Vb[sp])[(size_t)cg * ld + j] : (A)0;
+      Ut[r][c] = (okc && i < n) ? reinterpret_cast<const A*>(w.Ub[sp])[(size_t)cg * ld + i] : (A)0;
     }
     __syncthreads();
-    A g[EC / 4], x[EC / 4];
+    A g[2][4], x[2][4];
 #pragma unroll
-    for (int m = 0; m < EC / 4; ++m) g[m] = x[m] = (A)0;
-    // G partial: row i = lo, candidates hi + 4m ; X partial: column j = lo
-#pragma unroll 8
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) g[a][b] = x[a][b] = (A)0;
+    // G partial: rows 2 tp, 2 tp + 1 of the tile, candidates 4 tc .. 4 tc + 3 (sum over j);
+    // X partial: columns 2 tp, 2 tp + 1, same candidates (sum over i).
+#pragma unroll 4
     for (int k = 0; k < ET; ++k) {
-      const A nik = Ns[lo][k];
-      const A nkj = Ns[k][lo];
+      const A n0 = Nt[k][2 * tp], n1 = Nt[k][2 * tp + 1];      // N[2tp][k], N[2tp+1][k]
+      const A m0 = Ns[k][2 * tp], m1 = Ns[k][2 * tp + 1];      // N[k][2tp], N[k][2tp+1]
 #pragma unroll
-      for (int m = 0; m < EC / 4; ++m) {
-        g[m] += nik * Vs[k][hi + 4 * m];
-        x[m] += Us[hi + 4 * m][k] * nkj;
+      for (int b = 0; b < 4; ++b) {
+        const A v = Vs[k][4 * tc + b], u = Ut[k][4 * tc + b];
+        g[0][b] += n0 * v;
+        g[1][b] += n1 * v;
+        x[0][b] += u * m0;
+        x[1][b] += u * m1;
       }
     }
 #pragma unroll
-    for (int m = 0; m < EC / 4; ++m) {
-      const int cg = cb + hi + 4 * m;
+    for (int b = 0; b < 4; ++b) {
+      const int cg = cb + 4 * tc + b;
       if (cg < nc_) {
-        if (i0 + lo < n) atomicAdd(&w.Gc[sp][(size_t)cg * ld + i0 + lo], (double)g[m]);
-        if (j0 + lo < n) atomicAdd(&w.Xr[sp][(size_t)cg * ld + j0 + lo], (double)x[m]);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const int r = 2 * tp + a;
+          if (i0 + r < n) atomicAdd(&w.Gc[sp][(size_t)cg * ld + i0 + r], (double)g[a][b]);
+          if (j0 + r < n) atomicAdd(&w.Xr[sp][(size_t)cg * ld + j0 + r], (double)x[a][b]);
+        }
       }
     }
   }
@@ -282,7 +296,7 @@ __device__ __forceinline__ void cand_ext_tile(const Config& cfg, int wi, int sp,
 
 template <typename A>
 constexpr int ext_smem_bytes() {
-  return (int)sizeof(A) * (ET * (ET + 1) + ET * (EC + 1) + EC * (ET + 1));
+  return (int)sizeof(A) * (ET * ET + ET * (ET + 1) + 2 * ET * EC);
 }
 
 // G_ext[n+c', n+c] = X[c',:] . V[c,:] + g0(r_c' - r_c, tau_c' - tau_c)
@@ -308,14 +322,14 @@ __global__ void __launch_bounds__(256) k_cand_cc(Config cfg) {
         const int cpb = (item / tiles) * 32, cb = (item - (item / tiles) * tiles) * 32;
         const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
         const double* X = w.Xr[sp];
-        const double* V = w.Vb[sp];
+        const A* V = reinterpret_cast<const A*>(w.Vb[sp]);
         A acc[4] = {(A)0, (A)0, (A)0, (A)0};
         for (int j0 = 0; j0 < n; j0 += 32) {
           __syncthreads();
           const int j = j0 + tx;
           for (int r = ty; r < 32; r += 8) {
             Xs[r][tx] = (A)((cpb + r < nc_ && j < n) ? X[(size_t)(cpb + r) * ld + j] : 0.0);
-            Vs[r][tx] = (A)((cb + r < nc_ && j < n) ? V[(size_t)(cb + r) * ld + j] : 0.0);
+            Vs[r][tx] = (cb + r < nc_ && j < n) ? V[(size_t)(cb + r) * ld + j] : (A)0;
           }
           __syncthreads();
 #pragma unroll 8

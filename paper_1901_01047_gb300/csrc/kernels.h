@@ -60,7 +60,7 @@ int tc_tile_n(int ks);
 bool encode_update_maps(const WalkerDev& w, int ks, TmapDev* out4x2);
 void launch_upd_ops(const Config& cfg, cudaStream_t st);
 void launch_upd_tc(const Config& cfg, cudaStream_t st);
-void launch_negate(const double* src, double* dst, size_t n, cudaStream_t st);
+void launch_negate(const double* src, double* dst, float* dstf, size_t n, cudaStream_t st);
 void launch_g0_isolated(int nc, const double* d_eps, const double* d_kr, double mu_eff, double beta, int n_tau,
                         double* d_out, cudaStream_t st);
 

@@ -52,6 +52,7 @@ struct ProblemDev {
   const int32_t* site_sub;            // [nc*nc]
   const int32_t* site_add;            // [nc*nc]: site_add[y*nc + d] = x with site_sub[x*nc + y] = d
   const double* g0;                   // [2][nc][n_tau+1], g0 = -G0
+  const float* g0f;                   // FP32 copy of g0 (mixed-precision interpolation)
 };
 
 struct Proposal {
@@ -117,6 +118,8 @@ struct WalkerDev {
   Proposal* prop;            // [KS_MAX]
   double* Gc[2];             // [spin][KS_MAX][cap]: G_ext[:, n + c] stored per candidate c
   double* Xr[2];             // [spin][KS_MAX][cap]: X[c, :] = g0[c,:] (e^V - 1) N
+  // V, U, gR and bvec hold the arithmetic type of the products: FP64 on the
+  // FP64 path, FP32 (first half of the buffer, same indexing) on the mixed path.
   double* Vb[2];             // [spin][KS_MAX][cap]: V[c, j] = g0(r_j - r_c, tau_j - tau_c) (0 if j dead)
   double* Ub[2];             // [spin][KS_MAX][cap]: U[c, i] = g0(r_c - r_i, tau_c - tau_i) (e^{V_i} - 1)
   double* Binv[2];           // [spin][KS_MAX][KS_MAX]

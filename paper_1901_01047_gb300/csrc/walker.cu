@@ -185,19 +185,23 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     void* ds = h->dalloc(sizeof(int32_t) * pr.nc * pr.nc);
     void* da = h->dalloc(sizeof(int32_t) * pr.nc * pr.nc);
     void* dg = h->dalloc(sizeof(double) * tsz);
-    if (!ds || !da || !dg) {
+    void* dgf = h->dalloc(sizeof(float) * tsz);
+    std::vector<float> g0f(g0.begin(), g0.end());
+    if (!ds || !da || !dg || !dgf) {
       h->err = "device allocation of problem tables";
       return bail(DCA_ERR_OOM);
     }
     if (cudaMemcpy(ds, pr.site_sub, sizeof(int32_t) * pr.nc * pr.nc, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(da, add.data(), sizeof(int32_t) * pr.nc * pr.nc, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(dg, g0.data(), sizeof(double) * tsz, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(dg, g0.data(), sizeof(double) * tsz, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dgf, g0f.data(), sizeof(float) * tsz, cudaMemcpyHostToDevice) != cudaSuccess) {
       h->err = "upload of problem tables failed";
       return bail(DCA_ERR_CUDA);
     }
     d.site_sub = (const int32_t*)ds;
     d.site_add = (const int32_t*)da;
     d.g0 = (const double*)dg;
+    d.g0f = (const float*)dgf;
     h->max_nc = std::max(h->max_nc, pr.nc);
   }
   h->h_P = hp;
@@ -599,7 +603,7 @@ extern "C" DCA_API int dca_walker_update_G0(dca_walker* h, int32_t problem, cons
   for (size_t t = 0; t < tsz; ++t)
     if (!std::isfinite(G0[t])) return fail(h, DCA_ERR_ARG, "G0 has a non-finite entry");
   CK(cudaMemcpyAsync(h->g0_stage[problem], G0, sizeof(double) * tsz, cudaMemcpyHostToDevice, h->stream));
-  dca::launch_negate(h->g0_stage[problem], const_cast<double*>(pd.g0), tsz, h->stream);
+  dca::launch_negate(h->g0_stage[problem], const_cast<double*>(pd.g0), const_cast<float*>(pd.g0f), tsz, h->stream);
   h->total_launches += 1;
   CK(cudaGetLastError());
   return DCA_OK;
