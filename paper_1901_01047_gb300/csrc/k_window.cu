@@ -1007,6 +1007,11 @@ static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_
       return 1;
     case GROUP_EXTEND:
       k_cand_zero<<<grid_for(S * kc), 256, 0, st>>>(cfg);
+      if (cfg.prec == PREC_MIXED) {
+        launch_ext_mixed(cfg, max_cap, st);
+        k_cand_cc<A><<<grid_for(S * 16), 256, 0, st>>>(cfg);
+        return 4;
+      }
       k_cand_ext<T, A><<<grid_for(S * t64 * t64), 256, ext_smem_bytes<A>(), st>>>(cfg);
       k_cand_cc<A><<<grid_for(S * 16), 256, 0, st>>>(cfg);
       return 3;

@@ -11,7 +11,7 @@ namespace dca {
 // Kernel groups of one window (and the per-window extras), timed separately.
 enum Group : int {
   GROUP_PROPOSE = 0,         // k_begin
-  GROUP_EXTEND = 1,          // k_cand_zero, k_cand_ext, k_cand_cc
+  GROUP_EXTEND = 1,          // k_cand_zero, k_cand_ext (mixed: k_ext_g, k_ext_x), k_cand_cc
   GROUP_METROPOLIS = 2,      // k_metropolis
   GROUP_UPDATE = 3,          // the rank-l update of N
   GROUP_MEASURE = 4,         // k_meas_*
@@ -52,6 +52,8 @@ void launch_refine_adopt(const Config& cfg, int max_cap, cudaStream_t st);
 // part: GROUP_RECOMPUTE_PRE, GROUP_RECOMPUTE or GROUP_RECOMPUTE_POST.
 int launch_recompute(int part, const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st);
 int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
+// Candidate extension of the mixed path: the two streaming passes over N.
+void launch_ext_mixed(const Config& cfg, int max_cap, cudaStream_t st);
 // Tensor-core N update (mixed precision): kernel attributes, tile width for
 // a submatrix size, tensor maps of one walker ([spin][A, B, N0, N1]), the
 // operand split and the update itself.
