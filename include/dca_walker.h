@@ -240,6 +240,13 @@ DCA_API int dca_fresh_N_noalloc(const dca_problem* problem, int32_t n, const dca
  * of an outer DCA loop.  Stream-ordered: sweeps launched afterwards use it. */
 DCA_API int dca_walker_update_G0(dca_walker* w, int32_t problem, const double* G0);
 
+/* Change the submatrix size (1..128) and the N-update kernel (DCA_UPD_*,
+ * mixed precision only) between sweeps.  The submatrix method reaches the
+ * same Markov chain as single-spin updates for every k_sub (Sec. 2.3,
+ * "Submatrix updates"), so both are pure performance parameters; used by the
+ * autotuner.  Synchronises the stream. */
+DCA_API int dca_walker_set_tuning(dca_walker* w, int32_t k_sub, int32_t update_kernel);
+
 /* Kernel groups for timing: bit g of the mask times group g with CUDA events
  * recorded on the walker's stream around every launch of that group.
  *   0 proposals, 1 candidate extension (G columns / X rows), 2 Metropolis

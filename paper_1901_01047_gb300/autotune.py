@@ -1,0 +1,57 @@
+"""Autotuner of the submatrix size k_s and the N-update kernel.
+
+The submatrix method reaches exactly the Markov chain of single-spin updates
+for every k_s (DCA++ paper, Sec. 2.3, "Submatrix updates"), and the two
+mixed-precision update kernels differ only by rounding, so both are pure
+performance parameters.  The tuner times every candidate on the caller's own
+walkers, after their warm-up (the orders then have their working size),
+with CUDA events on the walker's stream around whole sweeps, and leaves the
+walkers on the fastest candidate.  The chains simply continue: each trial
+sweep is an ordinary sweep of the run.
+"""
+import itertools
+
+KS_CANDIDATES = (16, 32, 64, 128)
+KERNEL_CANDIDATES = ("tcgen05", "cuda_core")
+
+
+def _time_sweeps(gw, sweeps, stream, tries=3):
+    """Updates/s over `sweeps` sweeps.  The periodic recompute is the same for
+    every candidate, so a trial it falls into is repeated (up to `tries`)."""
+    import torch
+    for _ in range(tries):
+        s = gw.stats()
+        p0 = sum(x["proposals"] for x in s)
+        r0 = sum(x["recomputes"] for x in s)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gw.sweep(sweeps)
+        e1.record(stream)
+        e1.synchronize()
+        s = gw.stats()
+        ms = e0.elapsed_time(e1)
+        if sum(x["recomputes"] for x in s) == r0:
+            break
+    return (sum(x["proposals"] for x in s) - p0) / (ms / 1000.0), ms
+
+
+def tune(gw, precision, ks_candidates=KS_CANDIDATES, kernels=KERNEL_CANDIDATES, sweeps=2, settle=1):
+    """Time each (k_s, kernel) candidate on the walkers `gw` and select the
+    fastest.  Returns {"k_sub": .., "update_kernel": .., "table": [...]}.
+    `settle` untimed sweeps follow every switch (the first sweep after a
+    switch also rebuilds the captured window loop)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    if precision != "mixed":
+        kernels = ("cuda_core",)
+    table = []
+    for ks, kern in itertools.product(ks_candidates, kernels):
+        gw.set_tuning(ks, kern)
+        if settle:
+            gw.sweep(settle)
+        rate, ms = _time_sweeps(gw, sweeps, stream)
+        table.append({"k_sub": ks, "update_kernel": kern, "updates_per_s": rate, "ms": ms})
+    best = max(table, key=lambda r: r["updates_per_s"])
+    gw.set_tuning(best["k_sub"], best["update_kernel"])
+    return {"k_sub": best["k_sub"], "update_kernel": best["update_kernel"], "table": table}

@@ -68,7 +68,14 @@ __global__ void __launch_bounds__(256) k_build_A(Config cfg, int mode) {
     const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
     const double ej = expV(pb, sp, vs[j]);
     const double g = (i == j) ? g0_diag(pb, sp, vsite[i]) : g0_pair(pb, sp, vsite[i], vtau[i], vsite[j], vtau[j]);
-    A[(size_t)i * ld + j] = (i == j ? ej : 0.0) - g * (ej - 1.0);
+    const double a = (i == j ? ej : 0.0) - g * (ej - 1.0);
+    if (mode == 1 && cfg.prec == PREC_MIXED && !cfg.recompute_gj) {
+      // Newton recompute: A as an unevaluated FP32 pair hi + lo (~48 bits)
+      const float hi = (float)a;
+      reinterpret_cast<float2*>(A)[(size_t)i * ld + j] = make_float2(hi, (float)(a - (double)hi));
+    } else {
+      A[(size_t)i * ld + j] = a;
+    }
   }
       });
 }

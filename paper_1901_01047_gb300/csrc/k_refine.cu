@@ -1,17 +1,18 @@
 // k_refine.cu -- periodic recompute of the FP32 N matrices (mixed
 // precision) as a Newton-Schulz step against the from-scratch inverse
 // N^-1 = A = e^V - g0 (e^V - 1) of the current configuration (Eq. Zk), which
-// k_build_A forms in FP64:
-//     R  = I - A N0      FP64 products and accumulation
+// k_build_A forms in FP64 and stores as FP32 pairs (hi, lo):
+//     R  = I - A N0      FP64-grade (double-float products and sums)
 //     N1 = N0 + N0 R     FP32 (R is of the size of the drift)
 // One step squares the relative error of N0: an FP32 N0 that drifted by 1e-5
 // comes back to the FP32 rounding level.  Both products are tiled GEMMs on a
 // persistent grid over (walker-spin, 64 x 64 output tile), so one walker's
-// recompute spreads over every SM; the FP64 product is the whole cost (GB300
-// FP64 runs at ~2 FMA per clock per SM).
+// recompute spreads over every SM.  The residual is the whole cost; it runs
+// on the FP32 pipes in double-float arithmetic because GB300's FP64 units
+// issue ~2 FMA per clock per SM against 128 FP32 operations.
 //
 // Buffers (the recompute follows a compaction, all n rows live):
-//   A   Ascr[sp] (FP64)          -> R  into N[parity ^ 1][sp] (FP32)
+//   A   Ascr[sp] (FP32 pairs)    -> R  into N[parity ^ 1][sp] (FP32)
 //   N0  N[parity][sp]            -> N1 into Ascr[sp] viewed as FP32
 // k_refine_adopt then measures the drift max|N1 - N0| / max|N1| and copies
 // N1 into N[parity ^ 1][sp] for the parity switch.
@@ -36,11 +37,19 @@ __device__ __forceinline__ long long refine_tiles(const WalkerDev& w) {
   return refine_wants(w) ? t * t : 0;
 }
 
-// R = I - A N0, FP64.  Thread (tx, ty) of 16 x 16 owns rows ty + 16 a and
-// columns tx + 16 b (a, b < 4) of the tile.
+// R = I - A N0 with FP64-grade accuracy in double-float arithmetic on the
+// FP32 pipes (GB300 issues 64 FP32 operations per FP64 FMA).  A arrives as
+// FP32 pairs (hi, lo) from k_build_A, N0 is FP32 (exact).  Per term:
+// the product hi*b is split exactly by an FMA (p + e), lo*b joins the error
+// term, and p is added to the running sum by an error-free two-sum whose
+// rounding error also goes to the low word: the accumulated value carries
+// ~2^-44 relative error of sum |A||N0|, against the ~1e-5 drift the step
+// removes.  Thread (tx, ty) of 16 x 16 owns rows ty + 16 a and columns
+// tx + 16 b (a, b < 4) of the tile.
 __global__ void __launch_bounds__(256) k_refine_resid(Config cfg) {
-  __shared__ double As[RK][RT + 1];  // [k][i]
-  __shared__ double Bs[RK][RT];      // [k][j]
+  __shared__ float Ah[RK][RT + 1];  // [k][i]
+  __shared__ float Al[RK][RT + 1];
+  __shared__ float Bs[RK][RT];      // [k][j]
   for_each_item(
       2 * cfg.n_walkers, [&](int s) -> long long { return refine_tiles(cfg.W[s >> 1]); },
       [&](int s, int item) {
@@ -48,35 +57,51 @@ __global__ void __launch_bounds__(256) k_refine_resid(Config cfg) {
         const int sp = s & 1, n = w.n, ld = w.cap;
         const int tiles = (n + RT - 1) / RT;
         const int i0 = (item / tiles) * RT, j0 = (item - (item / tiles) * tiles) * RT;
-        const double* A = w.Ascr[sp];
+        const float2* A = reinterpret_cast<const float2*>(w.Ascr[sp]);
         const float* N0 = (const float*)w.N[w.parity][sp];
         float* R = (float*)w.N[w.parity ^ 1][sp];
         const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-        double acc[4][4];
+        float hi[4][4], lo[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+          for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = 0.0f;
         for (int k0 = 0; k0 < n; k0 += RK) {
           __syncthreads();
           for (int e = threadIdx.x; e < RT * RK; e += 256) {
             const int i = e / RK, k = e - i * RK;  // k fastest: rows of A
-            As[k][i] = (i0 + i < n && k0 + k < n) ? A[(size_t)(i0 + i) * ld + k0 + k] : 0.0;
+            const float2 v = (i0 + i < n && k0 + k < n) ? A[(size_t)(i0 + i) * ld + k0 + k] : make_float2(0.f, 0.f);
+            Ah[k][i] = v.x;
+            Al[k][i] = v.y;
             const int kk = e / RT, j = e - kk * RT;  // j fastest: rows of N0
-            Bs[kk][j] = (k0 + kk < n && j0 + j < n) ? (double)N0[(size_t)(k0 + kk) * ld + j0 + j] : 0.0;
+            Bs[kk][j] = (k0 + kk < n && j0 + j < n) ? N0[(size_t)(k0 + kk) * ld + j0 + j] : 0.0f;
           }
           __syncthreads();
-#pragma unroll
+#pragma unroll 4
           for (int k = 0; k < RK; ++k) {
-            double av[4], bv[4];
+            float ah[4], al[4], bv[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = As[k][ty + 16 * a];
+            for (int a = 0; a < 4; ++a) {
+              ah[a] = Ah[k][ty + 16 * a];
+              al[a] = Al[k][ty + 16 * a];
+            }
 #pragma unroll
             for (int b = 0; b < 4; ++b) bv[b] = Bs[k][tx + 16 * b];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-              for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+              for (int b = 0; b < 4; ++b) {
+                // the _rn forms are never contracted into FMAs, which the
+                // error-free transformations below rely on
+                const float p = __fmul_rn(ah[a], bv[b]);
+                float e = fmaf(ah[a], bv[b], -p);  // exact: ah * b = p + e
+                e = fmaf(al[a], bv[b], e);
+                const float s1 = __fadd_rn(hi[a][b], p);  // two-sum of hi and p
+                const float bb = __fsub_rn(s1, hi[a][b]);
+                const float err = __fadd_rn(__fsub_rn(hi[a][b], __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+                hi[a][b] = s1;
+                lo[a][b] += err + e;
+              }
           }
         }
 #pragma unroll
@@ -85,7 +110,11 @@ __global__ void __launch_bounds__(256) k_refine_resid(Config cfg) {
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             const int j = j0 + tx + 16 * b;
-            if (i < n && j < n) R[(size_t)i * ld + j] = (float)((i == j ? 1.0 : 0.0) - acc[a][b]);
+            if (i < n && j < n) {
+              // (delta - hi) - lo, the difference of nearly equal numbers taken exactly first
+              const float d = __fsub_rn(i == j ? 1.0f : 0.0f, hi[a][b]);
+              R[(size_t)i * ld + j] = __fsub_rn(d, lo[a][b]);
+            }
           }
         }
       });
@@ -120,7 +149,7 @@ __global__ void __launch_bounds__(256) k_refine_correct(Config cfg) {
             Bs[kk][j] = (k0 + kk < n && j0 + j < n) ? R[(size_t)(k0 + kk) * ld + j0 + j] : 0.0f;
           }
           __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
           for (int k = 0; k < RK32; ++k) {
             float av[4], bv[4];
 #pragma unroll

@@ -133,6 +133,8 @@ extern "C" DCA_API int dca_g0_isolated_cluster(int32_t nc, const double* eps_K, 
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+static int upload_update_maps(dca_walker* h, int ks);
+
 extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cuda_stream, dca_walker** out) {
   if (!out) return fail(nullptr, DCA_ERR_ARG, "out is NULL");
   *out = nullptr;
@@ -229,7 +231,10 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     h->err = "update_kernel must be one of DCA_UPD_*";
     return bail(DCA_ERR_ARG);
   }
+  // The tensor-core operands exist on every mixed-precision walker, so the
+  // update kernel can be switched by dca_walker_set_tuning.
   const bool use_tc = p.precision == DCA_PREC_MIXED && p.update_kernel != DCA_UPD_CUDA_CORE;
+  const bool alloc_tc = p.precision == DCA_PREC_MIXED;
   h->h_W.resize(h->W);
   h->nc_of.resize(h->W);
   h->gacc_off.resize(h->W);
@@ -291,7 +296,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
       pieces.push_back({(void**)&w.Lrow[sp], sizeof(double) * KS * C});
       pieces.push_back({(void**)&w.Lp[sp], sizeof(double) * KS * C});
       pieces.push_back({(void**)&w.Rr[sp], esz * KS * C});
-      if (use_tc) {
+      if (alloc_tc) {
         pieces.push_back({(void**)&w.Aop[sp], sizeof(float) * 2 * C * KS});
         pieces.push_back({(void**)&w.Bop[sp], sizeof(float) * 2 * C * KS});
       }
@@ -324,17 +329,10 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
       off += align_up(pc.bytes, 256);
     }
   }
-  if (use_tc) {
-    std::vector<dca::TmapDev> maps((size_t)h->W * 8);
-    for (int wi = 0; wi < h->W; ++wi)
-      if (!dca::encode_update_maps(h->h_W[wi], p.k_sub, maps.data() + (size_t)wi * 8)) {
-        h->err = "TMA tensor map encoding failed (walker " + std::to_string(wi) + ")";
-        return bail(DCA_ERR_CUDA);
-      }
-    h->d_tmaps = (dca::TmapDev*)h->dalloc(sizeof(dca::TmapDev) * maps.size());
-    if (!h->d_tmaps ||
-        cudaMemcpy(h->d_tmaps, maps.data(), sizeof(dca::TmapDev) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-      h->err = "upload of tensor maps";
+  if (alloc_tc) {
+    h->d_tmaps = (dca::TmapDev*)h->dalloc(sizeof(dca::TmapDev) * (size_t)h->W * 8);
+    if (!h->d_tmaps || upload_update_maps(h, p.k_sub) != DCA_OK) {
+      h->err = "TMA tensor maps of the tensor-core update";
       return bail(DCA_ERR_CUDA);
     }
     if (dca::setup_update_tc() != cudaSuccess) {
@@ -387,6 +385,17 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
       return bail(DCA_ERR_NUMERIC);
     }
   *out = h;
+  return DCA_OK;
+}
+
+// Encode and upload the TMA tensor maps of every walker (the B-operand box
+// depends on the submatrix size).
+static int upload_update_maps(dca_walker* h, int ks) {
+  std::vector<dca::TmapDev> maps((size_t)h->W * 8);
+  for (int wi = 0; wi < h->W; ++wi)
+    if (!dca::encode_update_maps(h->h_W[wi], ks, maps.data() + (size_t)wi * 8)) return DCA_ERR_CUDA;
+  if (cudaMemcpy(h->d_tmaps, maps.data(), sizeof(dca::TmapDev) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return DCA_ERR_CUDA;
   return DCA_OK;
 }
 
@@ -567,6 +576,33 @@ extern "C" DCA_API int dca_walker_sweep(dca_walker* h, int32_t n_sweeps) {
     if (h->h_W[wi].status != dca::ST_OK)
       return fail(h, status_code(h->h_W[wi].status),
                   "walker " + std::to_string(wi) + " stopped with status " + std::to_string(h->h_W[wi].status));
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_set_tuning(dca_walker* h, int32_t k_sub, int32_t update_kernel) {
+  if (!h) return DCA_ERR_ARG;
+  if (k_sub < 1 || k_sub > dca::KS_MAX) return fail(h, DCA_ERR_ARG, "k_sub must be in 1..128");
+  if (update_kernel < DCA_UPD_AUTO || update_kernel > DCA_UPD_TCGEN05)
+    return fail(h, DCA_ERR_ARG, "update_kernel must be one of DCA_UPD_*");
+  CK(cudaStreamSynchronize(h->stream));
+  const bool mixed = h->cfg.prec == dca::PREC_MIXED;
+  const bool tc = mixed && update_kernel != DCA_UPD_CUDA_CORE;
+  if (tc && dca::tc_tile_n(k_sub) != dca::tc_tile_n(h->ks)) {
+    const int rc = upload_update_maps(h, k_sub);
+    if (rc != DCA_OK) return fail(h, rc, "TMA tensor maps of the tensor-core update");
+  }
+  h->ks = k_sub;
+  h->cfg.ks = k_sub;
+  h->cfg.upd_kernel = tc ? dca::UPD_TCGEN05 : dca::UPD_CUDA_CORE;
+  // the captured window loop holds the old launch configuration
+  if (h->loop_exec) {
+    cudaGraphExecDestroy(h->loop_exec);
+    h->loop_exec = nullptr;
+  }
+  if (h->loop_graph) {
+    cudaGraphDestroy(h->loop_graph);
+    h->loop_graph = nullptr;
+  }
   return DCA_OK;
 }
 

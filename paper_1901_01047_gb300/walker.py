@@ -21,7 +21,7 @@ EXPORTS = [
     "dca_walker_reset_measurements", "dca_walker_stats", "dca_walker_get_state",
     "dca_walker_get_decision_log", "dca_walker_set_forced_decisions", "dca_walker_capacity",
     "dca_walker_destroy", "dca_walker_last_error", "dca_walker_update_G0", "dca_walker_set_timing",
-    "dca_walker_get_timing", "dca_fresh_N", "dca_fresh_N_noalloc",
+    "dca_walker_get_timing", "dca_walker_set_tuning", "dca_fresh_N", "dca_fresh_N_noalloc",
 ]
 UPDATE_KERNELS = {"auto": 0, "cuda_core": 1, "tcgen05": 2}
 GROUPS = ["propose", "extend", "metropolis", "update", "measure", "recompute", "update_pre", "update_post",
@@ -117,6 +117,7 @@ def load(path=LIB_PATH):
     L.dca_walker_capacity.argtypes = [P, C.c_int32, C.POINTER(C.c_int32)]
     L.dca_walker_update_G0.argtypes = [P, C.c_int32, P]
     L.dca_walker_set_timing.argtypes = [P, C.c_uint32]
+    L.dca_walker_set_tuning.argtypes = [P, C.c_int32, C.c_int32]
     L.dca_walker_get_timing.argtypes = [P, P, P, C.POINTER(C.c_int64), C.c_int32]
     L.dca_fresh_N.argtypes = [C.POINTER(Problem), C.c_int32, P, P, P, C.POINTER(C.c_int32)]
     L.dca_fresh_N_noalloc.argtypes = [C.POINTER(Problem), C.c_int32, P, P, P, C.POINTER(C.c_int32)]
@@ -231,6 +232,7 @@ class Walkers:
             self.walker_problem = np.arange(n_walkers, dtype=np.int32) % len(problems)
         self.nc = [int(problems[i]["nc"]) for i in self.walker_problem]
         p.k_sub = int(k_sub)
+        self.k_sub = int(k_sub)
         p.recompute_every = int(recompute_every)
         p.warmup_sweeps = int(warmup_sweeps)
         p.n_tau_meas = int(n_tau_meas)
@@ -323,6 +325,12 @@ class Walkers:
         """Upload a new bare propagator (host array, paper convention) for a problem."""
         G0 = np.ascontiguousarray(G0, np.float64)
         self._check(self._L.dca_walker_update_G0(self._h, int(problem), _ptr(G0)))
+
+    def set_tuning(self, k_sub, update_kernel="auto"):
+        """Change the submatrix size and the N-update kernel between sweeps (same Markov chain)."""
+        uk = UPDATE_KERNELS[update_kernel] if isinstance(update_kernel, str) else int(update_kernel)
+        self._check(self._L.dca_walker_set_tuning(self._h, int(k_sub), uk))
+        self.k_sub = int(k_sub)
 
     def set_timing(self, groups):
         """Time the named kernel groups with CUDA events on the walker's stream."""

@@ -143,3 +143,23 @@ def test_mixed_recompute_methods_restore_accuracy(method):
     assert errN < 1e-4, errN
     assert errG < 2e-5, errG
     assert st["max_drift"] < 1e-3
+
+
+def test_autotuner_selects_a_candidate_and_leaves_walkers_on_it():
+    import torch
+    from paper_1901_01047_gb300 import autotune, walker
+    probs = []
+    for nc, beta in [(4, 6.0), (8, 4.0)]:
+        c, eps, kr, G0 = problem(nc, 1.0, 0.0, 5.0, beta, 2.5, 1024)
+        probs.append(dict(nc=nc, site_sub=c.site_sub, U=5.0, beta=beta, K=1.0, G0=G0))
+    gw = walker.Walkers(probs, n_walkers=8, k_sub=32, recompute_every=0, recompute_sweeps=4, warmup_sweeps=2,
+                        n_tau_meas=8, precision="mixed", seed=3, stream=torch.cuda.current_stream().cuda_stream)
+    gw.sweep(6)
+    res = autotune.tune(gw, "mixed", sweeps=1, settle=1)
+    assert len(res["table"]) == 8
+    assert res["k_sub"] in autotune.KS_CANDIDATES and res["update_kernel"] in autotune.KERNEL_CANDIDATES
+    assert all(r["updates_per_s"] > 0 for r in res["table"])
+    assert gw.k_sub == res["k_sub"]
+    gw.sweep(2)
+    assert all(s["status"] == 0 for s in gw.stats())
+    gw.close()

@@ -153,3 +153,30 @@ def test_batched_sweep_synchronised_recompute_keeps_parity():
         st = r[8]
         assert st["recomputes"] == (60 - 1) // 3, st["recomputes"]
         assert st["max_drift"] < 1e-9
+
+
+def test_retuning_k_sub_between_sweeps_keeps_the_chain():
+    # k_s only groups proposals into windows: changing it between sweeps (as
+    # the autotuner does) leaves every decision and N unchanged.
+    nc, U, beta, mu = 4, 4.0, 6.0, 0.9450480104035819
+    c, eps, kr, G0 = problem(nc, 1.0, 0.0, U, beta, mu, 2048)
+    prob = dict(nc=nc, site_sub=c.site_sub, U=U, beta=beta, K=1.0, G0=G0)
+    gw = _walkers(problems=[prob], n_walkers=3, k_sub=16, recompute_every=8, warmup_sweeps=5, n_tau_meas=8,
+                  seed=9, log_capacity=1 << 22)
+    for ks in (16, 64, 3, 128, 32):
+        gw.set_tuning(ks)
+        gw.sweep(8)
+    for wi in range(3):
+        log = gw.decision_log(wi)
+        ow = ctaux.OracleWalker(nc, c.site_sub, U, beta, 1.0, G0, warmup_sweeps=5, n_tau_meas=8, seed=9,
+                                walker_id=wi)
+        ow.enable_log(1 << 22)
+        ow.set_hints(log)
+        ow.sweep(40)
+        assert np.array_equal(log & 1, ow.log() & 1)
+        gs, os_ = gw.state(wi), ow.state()
+        assert np.array_equal(gs["site"], os_["site"])
+        for sp in range(2):
+            ref = os_["N"][sp]
+            assert np.abs(gs["N"][sp] - ref).max() <= TOL * np.abs(ref).max()
+    gw.close()
