@@ -49,6 +49,11 @@ FP64_TFLOPS = 1.25
 # applied to the measured BF16 peak.
 TF32_PER_BF16 = 1.1 / 2.25
 
+# DRAM bytes (read + write) per launch of a kernel from an ncu capture of the
+# named workload (profiles/top_kernels_batched256_mixed.md); quoted as
+# `traffic` for that kernel on that workload only.
+NCU_TRAFFIC = {("batched256", "update"): 1.388e9}
+
 
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
@@ -326,6 +331,7 @@ def run_ours(args, rank, world, local_rank):
         windows = max(1, gtimes["propose"][1])  # one proposal kernel per window
         roof = roofline(dominant, gtimes[dominant][0], windows, work, peaks, kind, wl)
         roof_upd = roofline("update", gtimes["update"][0], windows, work, peaks, kind, wl)
+        roof_upd["traffic"] = NCU_TRAFFIC.get((wl.name, "update"))
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * seconds / args.steps, "higher_is_better": True,

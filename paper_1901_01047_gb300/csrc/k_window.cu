@@ -387,8 +387,10 @@ template <typename T>
 __device__ __forceinline__ double g_ext(const ExtView<T>& v, const ProblemDev& pb, int sp, int x, int y) {
   if (y >= v.n) return v.Gc[(size_t)(y - v.n) * v.ld + x];
   const double nxy = (x < v.n) ? ldN(v.N, (size_t)x * v.ld + y) : v.X[(size_t)(x - v.n) * v.ld + y];
-  const double ev = expV(pb, sp, v.vs[y]);
-  return (nxy * ev - (x == y ? 1.0 : 0.0)) / (ev - 1.0);
+  const int sy = v.vs[y];
+  const double ev = expV(pb, sp, sy);
+  // (N e^V - 1) / (e^V - 1) with the reciprocal tabulated per spin (no FP64 division)
+  return (nxy * ev - (x == y ? 1.0 : 0.0)) * pb.rexpVm1[sp][sy > 0 ? 1 : 0];
 }
 
 template <typename T>

@@ -51,6 +51,7 @@ void prepare_problem(const dca_problem& pr, ProblemDev& d, std::vector<int32_t>&
     const double sigma = sp == 0 ? 1.0 : -1.0;
     d.expV[sp][0] = std::exp(-sigma * d.gamma);
     d.expV[sp][1] = std::exp(sigma * d.gamma);
+    for (int k = 0; k < 2; ++k) d.rexpVm1[sp][k] = 1.0 / (d.expV[sp][k] - 1.0);
   }
   add.assign(pr.nc * pr.nc, -1);
   for (int x = 0; x < pr.nc; ++x)

@@ -49,6 +49,7 @@ struct ProblemDev {
   int32_t nc, n_tau;
   double beta, K, gamma, tau_scale;   // tau_scale = n_tau / beta
   double expV[2][2];                  // e^{sigma gamma s}: [spin][s > 0]
+  double rexpVm1[2][2];               // 1 / (e^{sigma gamma s} - 1) (inf when gamma = 0; never used then)
   const int32_t* site_sub;            // [nc*nc]
   const int32_t* site_add;            // [nc*nc]: site_add[y*nc + d] = x with site_sub[x*nc + y] = d
   const double* g0;                   // [2][nc][n_tau+1], g0 = -G0
