@@ -132,6 +132,34 @@ __device__ __forceinline__ double expV(const ProblemDev& p, int sp, int s) {
   return s == 0 ? 1.0 : p.expV[sp][s > 0 ? 1 : 0];
 }
 
+// Double-float arithmetic on the FP32 pipes (an unevaluated pair hi + lo,
+// ~2^-44 relative): GB300 issues 64 FP32 operations per FP64 FMA.  The _rn
+// forms are never contracted into FMAs, which the error-free transformations
+// rely on (Dekker / Knuth: exact product by FMA, two-sum).
+__device__ __forceinline__ float2 df_split(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
+// (shi, slo) += (ahi + alo)(bhi + blo), dropping alo * blo.
+__device__ __forceinline__ void df_fma(float& shi, float& slo, float ahi, float alo, float bhi, float blo) {
+  const float p = __fmul_rn(ahi, bhi);
+  float e = fmaf(ahi, bhi, -p);
+  e = fmaf(ahi, blo, e);
+  e = fmaf(alo, bhi, e);
+  const float s1 = __fadd_rn(shi, p);
+  const float bb = __fsub_rn(s1, shi);
+  const float err = __fadd_rn(__fsub_rn(shi, __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+  shi = s1;
+  slo = __fadd_rn(slo, __fadd_rn(err, e));
+}
+
+// Normalised pair (|lo| <= ulp(hi) / 2) of hi + lo.
+__device__ __forceinline__ float2 df_norm(float hi, float lo) {
+  const float s = __fadd_rn(hi, lo);
+  return make_float2(s, __fsub_rn(lo, __fsub_rn(s, hi)));
+}
+
 // Load of a stored value directly in the arithmetic type A (no FP64 round
 // trip for FP32 storage: on GB300 every FP64 conversion costs an FP64 issue).
 template <typename A, typename T>

@@ -323,7 +323,8 @@ __global__ void __launch_bounds__(256) k_upd_ops(Config cfg) {
           const long long idx = (long long)item * 256 + threadIdx.x;
           if (idx < (long long)n * lpad) {
             const int i = (int)(idx / lpad), p = (int)(idx - (long long)i * lpad);
-            const float x = p < l ? (float)w.Lp[sp][(size_t)i * KS_MAX + p] : 0.0f;
+            // L' is stored as FP32 pairs on the mixed path (hi carries the FP32 value)
+            const float x = p < l ? reinterpret_cast<const float2*>(w.Lp[sp])[(size_t)i * KS_MAX + p].x : 0.0f;
             float hi, lo;
             tc::tf32_split(x, hi, lo);
             w.Aop[sp][(size_t)i * TC_KS + p] = hi;

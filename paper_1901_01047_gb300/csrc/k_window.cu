@@ -593,11 +593,17 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
 
   // Epilogue: window bookkeeping and the accepted set.
   const int l = s_l, nrem = s_nrem, nins = s_nins;
-  if (in_smem)
+  // B^-1 for the update kernels: FP64 on the FP64 path, FP32 pairs (hi, lo)
+  // in the same buffer on the mixed path (element by element, so the
+  // in-place conversion of the global working copy is safe).
+  constexpr bool kPairs = sizeof(T) == 4;
+  if (in_smem || kPairs)
     for (int sp = 0; sp < 2; ++sp)
       for (int idx = tid; idx < l * l; idx += blockDim.x) {
         const int i = idx / l, jj = idx - i * l;
-        w.Binv[sp][(size_t)i * KS_MAX + jj] = Binv[sp][(size_t)i * bst + jj];
+        const double b = Binv[sp][(size_t)i * bst + jj];
+        if (kPairs) reinterpret_cast<float2*>(w.Binv[sp])[(size_t)i * KS_MAX + jj] = df_split(b);
+        else w.Binv[sp][(size_t)i * KS_MAX + jj] = b;
       }
   for (int p = tid; p < l; p += blockDim.x) {
     w.P[p] = s_P[p];
@@ -670,6 +676,21 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool upd_active(const WalkerDev& w) { return w.active && w.n_acc > 0; }
 
+// L' = L B^-1 is stored as FP64 (FP64 path) or as FP32 pairs (mixed path).
+template <typename A>
+__device__ __forceinline__ A lp_value(const double* Lp, size_t i) {
+  if (sizeof(A) == 4) return (A)reinterpret_cast<const float2*>(Lp)[i].x;
+  return (A)Lp[i];
+}
+template <typename A>
+__device__ __forceinline__ double lp_pair_value(const double* Lp, size_t i) {
+  if (sizeof(A) == 4) {
+    const float2 v = reinterpret_cast<const float2*>(Lp)[i];
+    return (double)v.x + (double)v.y;
+  }
+  return Lp[i];
+}
+
 // Extended row of the t-th row of the update (existing rows first).
 __device__ __forceinline__ int upd_row(const WalkerDev& w, int t) { return t < w.n ? t : w.n + w.acc_slot[t - w.n]; }
 
@@ -696,7 +717,8 @@ __global__ void __launch_bounds__(256) k_upd_lrow(Config cfg) {
     const double a = w.aP[sp][p];
     double val = 0.0;
     if (a != 0.0 && !(x < w.n && v.vs[x] == 0)) val = (g_ext(v, pb, sp, x, P) - (x == P ? 1.0 : 0.0)) * a;
-    w.Lrow[sp][(size_t)x * KS_MAX + p] = val;
+    if (sizeof(T) == 4) reinterpret_cast<float2*>(w.Lrow[sp])[(size_t)x * KS_MAX + p] = df_split(val);
+    else w.Lrow[sp][(size_t)x * KS_MAX + p] = val;
   }
       });
 }
@@ -722,11 +744,24 @@ __global__ void __launch_bounds__(256) k_upd_lp_rr(Config cfg) {
           if (idx < rows * l) {
             const int t = idx / l, p = idx - t * l;
             const int x = upd_row(w, t);
-            const double* Lr = w.Lrow[sp] + (size_t)x * KS_MAX;
-            const double* Bi = w.Binv[sp];
-            double acc = 0.0;  // FP64 on both paths: B^-1 carries the conditioning of the window
-            for (int q = 0; q < l; ++q) acc += Lr[q] * Bi[(size_t)q * KS_MAX + p];
-            w.Lp[sp][(size_t)x * KS_MAX + p] = acc;
+            // FP64-grade on both paths (B^-1 carries the conditioning of the
+            // window): FP64, or double-float on FP32 pairs on the mixed path
+            if (sizeof(T) == 4) {
+              const float2* Lr = reinterpret_cast<const float2*>(w.Lrow[sp]) + (size_t)x * KS_MAX;
+              const float2* Bi = reinterpret_cast<const float2*>(w.Binv[sp]);
+              float hi = 0.f, lo = 0.f;
+              for (int q = 0; q < l; ++q) {
+                const float2 a = Lr[q], b = Bi[(size_t)q * KS_MAX + p];
+                df_fma(hi, lo, a.x, a.y, b.x, b.y);
+              }
+              reinterpret_cast<float2*>(w.Lp[sp])[(size_t)x * KS_MAX + p] = df_norm(hi, lo);
+            } else {
+              const double* Lr = w.Lrow[sp] + (size_t)x * KS_MAX;
+              const double* Bi = w.Binv[sp];
+              double acc = 0.0;
+              for (int q = 0; q < l; ++q) acc += Lr[q] * Bi[(size_t)q * KS_MAX + p];
+              w.Lp[sp][(size_t)x * KS_MAX + p] = acc;
+            }
           }
         } else {
           const int idx = (item - lp_blocks) * 256 + threadIdx.x;
@@ -776,7 +811,7 @@ __device__ __forceinline__ void upd_apply_tile(const Config& cfg, int wi, int sp
     __syncthreads();
     for (int r = ty; r < TT; r += 8) {
       const int i = i0 + r, p = p0 + tx;
-      Ls[r][tx] = (A)((i < n && p < l) ? w.Lp[sp][(size_t)i * KS_MAX + p] : 0.0);
+      Ls[r][tx] = (i < n && p < l) ? lp_value<A>(w.Lp[sp], (size_t)i * KS_MAX + p) : (A)0;
       const int pp = p0 + r, jj = j0 + tx;
       Rs[r][tx] = (pp < l && jj < n) ? Rr[(size_t)pp * ld + jj] : (A)0;
     }
@@ -828,19 +863,31 @@ __global__ void __launch_bounds__(256) k_upd_border(Config cfg) {
     if (idx < rows_total) {
       const int m = idx / n, j = idx - m * n;
       const int c = w.acc_slot[m];
-      const double* L = w.Lp[sp] + (size_t)(n + c) * KS_MAX;
-      // FP64 on both paths: the new row X + L'R is formed with cancellation
-      double acc = w.Xr[sp][(size_t)c * ld + j];
-      for (int p = 0; p < l; ++p) acc += L[p] * (double)Rr[(size_t)p * ld + j];
-      stN(N, (size_t)(n + m) * ld + j, acc);
+      // FP64-grade on both paths: the new row X + L'R is formed with
+      // cancellation (double-float on the mixed path)
+      if (sizeof(A) == 4) {
+        const float2* L = reinterpret_cast<const float2*>(w.Lp[sp]) + (size_t)(n + c) * KS_MAX;
+        const float2 x0 = df_split(w.Xr[sp][(size_t)c * ld + j]);
+        float hi = x0.x, lo = x0.y;
+        for (int p = 0; p < l; ++p) {
+          const float2 a = L[p];
+          df_fma(hi, lo, a.x, a.y, (float)Rr[(size_t)p * ld + j], 0.f);
+        }
+        stN(N, (size_t)(n + m) * ld + j, (double)__fadd_rn(hi, lo));
+      } else {
+        const double* L = w.Lp[sp] + (size_t)(n + c) * KS_MAX;
+        double acc = w.Xr[sp][(size_t)c * ld + j];
+        for (int p = 0; p < l; ++p) acc += L[p] * (double)Rr[(size_t)p * ld + j];
+        stN(N, (size_t)(n + m) * ld + j, acc);
+      }
     } else if (idx < rows_total + cols_total) {
       const int t = idx - rows_total;
       const int i = t / ni, m = t - i * ni;
-      stN(N, (size_t)i * ld + n + m, w.Lp[sp][(size_t)i * KS_MAX + w.acc_p[m]]);
+      stN(N, (size_t)i * ld + n + m, (double)lp_value<A>(w.Lp[sp], (size_t)i * KS_MAX + w.acc_p[m]));
     } else {
       const int t = idx - rows_total - cols_total;
       const int m = t / ni, m2 = t - m * ni;
-      const double v = (m == m2 ? 1.0 : 0.0) + w.Lp[sp][(size_t)(n + w.acc_slot[m]) * KS_MAX + w.acc_p[m2]];
+      const double v = (m == m2 ? 1.0 : 0.0) + lp_pair_value<A>(w.Lp[sp], (size_t)(n + w.acc_slot[m]) * KS_MAX + w.acc_p[m2]);
       stN(N, (size_t)(n + m) * ld + n + m2, v);
     }
   }
