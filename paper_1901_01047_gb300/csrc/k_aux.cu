@@ -306,20 +306,20 @@ constexpr int MK = 32;   // vertices per step
 template <typename A, int MR>
 __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp, int item);
 
-template <typename A>
+// One kernel per reference-site tile MR, each taking the walkers whose
+// cluster falls in its class (MR / 2 < nc <= MR; nc <= 16 for MR = 16): the
+// register allocation of each follows its own tile.
+template <typename A, int MR>
 __global__ void __launch_bounds__(256) k_meas_gemm(Config cfg) {
   for_each_item(
       2 * cfg.n_walkers,
       [&](int s) -> long long {
         const WalkerDev& w = cfg.W[s >> 1];
-        return wants_measure(w) ? (long long)cfg.P[w.problem].nc * blocks_of(cfg.n_tau_meas, MT) : 0;
+        const int nc = cfg.P[w.problem].nc;
+        const bool mine = MR == 16 ? nc <= 16 : (nc > MR / 2 && nc <= MR);
+        return (wants_measure(w) && mine) ? (long long)nc * blocks_of(cfg.n_tau_meas, MT) : 0;
       },
-      [&](int s, int item) {
-        const int nc = cfg.P[cfg.W[s >> 1].problem].nc;  // uniform over the block
-        if (nc <= 16) meas_gemm_item<A, 16>(cfg, s >> 1, s & 1, item);
-        else if (nc <= 32) meas_gemm_item<A, 32>(cfg, s >> 1, s & 1, item);
-        else meas_gemm_item<A, 64>(cfg, s >> 1, s & 1, item);
-      });
+      [&](int s, int item) { meas_gemm_item<A, MR>(cfg, s >> 1, s & 1, item); });
 }
 
 template <typename A, int MR>
@@ -541,13 +541,19 @@ int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) 
   if (cfg.prec == PREC_MIXED) k_meas_b<float, float><<<gb, 256, 0, st>>>(cfg);
   else k_meas_b<double, double><<<gb, 256, 0, st>>>(cfg);
   const int gg = grid_for(S * max_nc * blocks_of(cfg.n_tau_meas, MT));
-  if (cfg.prec == PREC_MIXED) k_meas_gemm<float><<<gg, 256, 0, st>>>(cfg);
-  else k_meas_gemm<double><<<gg, 256, 0, st>>>(cfg);
+  if (cfg.prec == PREC_MIXED) {
+    k_meas_gemm<float, 16><<<gg, 256, 0, st>>>(cfg);
+    if (max_nc > 16) k_meas_gemm<float, 32><<<gg, 256, 0, st>>>(cfg);
+    if (max_nc > 32) k_meas_gemm<float, 64><<<gg, 256, 0, st>>>(cfg);
+  } else {
+    k_meas_gemm<double, 16><<<gg, 256, 0, st>>>(cfg);
+    if (max_nc > 16) k_meas_gemm<double, 32><<<gg, 256, 0, st>>>(cfg);
+    if (max_nc > 32) k_meas_gemm<double, 64><<<gg, 256, 0, st>>>(cfg);
+  }
   k_meas_acc<<<grid_for((long long)W * blocks_of(2LL * max_nc * cfg.n_tau_meas, 256)), 256, 0, st>>>(cfg);
   k_meas_finish<<<(W + 127) / 128, 128, 0, st>>>(cfg);
   (void)max_cap;
-  (void)max_nc;
-  return 5;
+  return 5 + (max_nc > 16) + (max_nc > 32);
 }
 
 void launch_g0_isolated(int nc, const double* d_eps, const double* d_kr, double mu_eff, double beta, int n_tau,

@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
       2 * cfg.n_walkers,
       [&](int s) -> long long {
         const WalkerDev& w = cfg.W[s >> 1];
-        return (w.active && w.n_cand > 0) ? blocks_of(w.n, 256) : 0;
+        return (w.active && w.n_cand > 0) ? blocks_of(w.n + w.n_cand, 256) : 0;
       },
       [&](int s, int item) {
         const WalkerDev& w = cfg.W[s >> 1];
@@ -174,7 +174,11 @@ __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
         }
         __syncthreads();
         const int i = item * 256 + threadIdx.x;
-        if (i >= n) return;
+        if (i >= n + nc_) return;
+        if (i >= n) {  // targets of the candidate block (k_cand_cc adds into them)
+          for (int c = 0; c < nc_; ++c) w.Gc[sp][(size_t)c * ld + i] = 0.0;
+          return;
+        }
         const int si = w.vs[par][i], ri = w.vsite[par][i];
         const double ti = w.vtau[par][i];
         const double em1 = si != 0 ? expV(pb, sp, si) - 1.0 : 0.0;
@@ -301,9 +305,13 @@ constexpr int ext_smem_bytes() {
 
 // G_ext[n+c', n+c] = X[c',:] . V[c,:] + g0(r_c' - r_c, tau_c' - tau_c)
 // (V[c, j] = g0(r_j - r_c, tau_j - tau_c), zero on dead j).  Item = 32 x 32
-// tile of candidate pairs of one walker-spin; the X and V rows are staged
-// through shared memory 32 columns at a time, so each row is read once per
-// tile.  The products run in the arithmetic type A.  Block 256 = 32 c x 8 c'.
+// tile of candidate pairs and one segment of CC_SEG columns of one
+// walker-spin; the X and V rows are staged through shared memory 32 columns
+// at a time, the segment sums are added into the targets (zeroed by
+// k_cand_zero) with FP64 atomics and segment 0 adds the g0 term.  The products
+// run in the arithmetic type A.  Block 256 = 32 c x 8 c'.
+constexpr int CC_SEG = 256;
+
 template <typename A>
 __global__ void __launch_bounds__(256) k_cand_cc(Config cfg) {
   __shared__ A Xs[32][33];
@@ -313,23 +321,25 @@ __global__ void __launch_bounds__(256) k_cand_cc(Config cfg) {
       [&](int s) -> long long {
         const WalkerDev& w = cfg.W[s >> 1];
         const long long t = (w.n_cand + 31) / 32;
-        return (w.active && w.n_cand > 0) ? t * t : 0;
+        return (w.active && w.n_cand > 0) ? t * t * ((w.n + CC_SEG - 1) / CC_SEG + (w.n == 0)) : 0;
       },
       [&](int s, int item) {
         const WalkerDev& w = cfg.W[s >> 1];
         const int sp = s & 1, n = w.n, nc_ = w.n_cand, ld = w.cap, par = w.parity;
-        const int tiles = (nc_ + 31) / 32;
-        const int cpb = (item / tiles) * 32, cb = (item - (item / tiles) * tiles) * 32;
+        const int tiles = (nc_ + 31) / 32, segs = (n + CC_SEG - 1) / CC_SEG + (n == 0);
+        const int seg = item % segs, tile = item / segs;
+        const int cpb = (tile / tiles) * 32, cb = (tile - (tile / tiles) * tiles) * 32;
+        const int jlo = seg * CC_SEG, jhi = min(n, jlo + CC_SEG);
         const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
         const double* X = w.Xr[sp];
         const A* V = reinterpret_cast<const A*>(w.Vb[sp]);
         A acc[4] = {(A)0, (A)0, (A)0, (A)0};
-        for (int j0 = 0; j0 < n; j0 += 32) {
+        for (int j0 = jlo; j0 < jhi; j0 += 32) {
           __syncthreads();
           const int j = j0 + tx;
           for (int r = ty; r < 32; r += 8) {
-            Xs[r][tx] = (A)((cpb + r < nc_ && j < n) ? X[(size_t)(cpb + r) * ld + j] : 0.0);
-            Vs[r][tx] = (cb + r < nc_ && j < n) ? V[(size_t)(cb + r) * ld + j] : (A)0;
+            Xs[r][tx] = (A)((cpb + r < nc_ && j < jhi) ? X[(size_t)(cpb + r) * ld + j] : 0.0);
+            Vs[r][tx] = (cb + r < nc_ && j < jhi) ? V[(size_t)(cb + r) * ld + j] : (A)0;
           }
           __syncthreads();
 #pragma unroll 8
@@ -348,9 +358,11 @@ __global__ void __launch_bounds__(256) k_cand_cc(Config cfg) {
           for (int m = 0; m < 4; ++m) {
             const int cp = cpb + ty + 8 * m;
             if (cp < nc_) {
-              const double g = (cp == c) ? g0_diag(pb, sp, rc)
-                                         : g0_pair(pb, sp, w.vsite[par][n + cp], w.vtau[par][n + cp], rc, tc);
-              w.Gc[sp][(size_t)c * ld + n + cp] = (double)acc[m] + g;
+              double v = (double)acc[m];
+              if (seg == 0)
+                v += (cp == c) ? g0_diag(pb, sp, rc)
+                               : g0_pair(pb, sp, w.vsite[par][n + cp], w.vtau[par][n + cp], rc, tc);
+              atomicAdd(&w.Gc[sp][(size_t)c * ld + n + cp], v);
             }
           }
         }
