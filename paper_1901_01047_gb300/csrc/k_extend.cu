@@ -25,12 +25,12 @@ __device__ __forceinline__ long long ext_items(const WalkerDev& w) {
 }
 
 // G_ext[i, n + c] = sum_j N[i, j] V[c, j] for a 128-row block and 32
-// candidates.  Per K step of 32 columns: Ns[i][k] (rows of N as loaded) and
-// Vs[k][c] (V transposed); thread (tc, tr) of (8, 32) owns rows tr + 32 r
-// (r < 4) and candidates 4 tc .. 4 tc + 3.
+// candidates.  Per K step of 32 columns: Nt[k][i] (N transposed) and
+// Vs[k][c] (V transposed); thread (tc, tr) of (8, 32) owns rows 4 tr .. 4 tr + 3
+// and candidates 4 tc .. 4 tc + 3: two 16-byte shared loads per 16 FMAs.
 __global__ void __launch_bounds__(256) k_ext_g(Config cfg) {
-  __shared__ float Ns[XB][XK + 1];
-  __shared__ __align__(16) float Vs[XK][XC + 4];  // padded: 4-way (not 32-way) conflicts on the transposing fill
+  __shared__ __align__(16) float Nt[XK][XB + 4];  // padded: 4-way conflicts on the transposing fill
+  __shared__ __align__(16) float Vs[XK][XC + 4];
   for_each_item(
       2 * cfg.n_walkers, [&](int s) -> long long { return ext_items(cfg.W[s >> 1]); },
       [&](int s, int item) {
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256) k_ext_g(Config cfg) {
           __syncthreads();
           for (int e = tid; e < XB * XK; e += 256) {
             const int r = e / XK, k = e - r * XK;  // k fastest: rows of N
-            Ns[r][k] = (i0 + r < n && k0 + k < n) ? N[(size_t)(i0 + r) * ld + k0 + k] : 0.f;
+            Nt[k][r] = (i0 + r < n && k0 + k < n) ? N[(size_t)(i0 + r) * ld + k0 + k] : 0.f;
           }
           for (int e = tid; e < XC * XK; e += 256) {
             const int c = e / XK, k = e - c * XK;  // k fastest: rows of V
@@ -58,19 +58,20 @@ __global__ void __launch_bounds__(256) k_ext_g(Config cfg) {
 #pragma unroll 8
           for (int k = 0; k < XK; ++k) {
             const float4 v = *reinterpret_cast<const float4*>(&Vs[k][4 * tc]);
+            const float4 a4 = *reinterpret_cast<const float4*>(&Nt[k][4 * tr]);
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-              const float a = Ns[tr + 32 * r][k];
-              acc[r][0] += a * v.x;
-              acc[r][1] += a * v.y;
-              acc[r][2] += a * v.z;
-              acc[r][3] += a * v.w;
+              acc[r][0] += av[r] * v.x;
+              acc[r][1] += av[r] * v.y;
+              acc[r][2] += av[r] * v.z;
+              acc[r][3] += av[r] * v.w;
             }
           }
         }
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          const int i = i0 + tr + 32 * r;
+          const int i = i0 + 4 * tr + r;
           if (i < n)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -84,10 +85,10 @@ __global__ void __launch_bounds__(256) k_ext_g(Config cfg) {
 // X[c, j] = sum_i U[c, i] N[i, j] for a 128-column block and 32 candidates.
 // Per K step of 32 rows: Ns[k][j] (row segments of N, coalesced) and Us[k][c]
 // (U transposed); thread (tc, tj) of (8, 32) owns columns 4 tj .. 4 tj + 3
-// and candidates tc + 8 q (q < 4).
+// and candidates 4 tc .. 4 tc + 3: two 16-byte shared loads per 16 FMAs.
 __global__ void __launch_bounds__(256) k_ext_x(Config cfg) {
   __shared__ __align__(16) float Ns[XK][XB];
-  __shared__ float Us[XK][XC + 1];
+  __shared__ __align__(16) float Us[XK][XC + 4];
   for_each_item(
       2 * cfg.n_walkers, [&](int s) -> long long { return ext_items(cfg.W[s >> 1]); },
       [&](int s, int item) {
@@ -127,19 +128,20 @@ __global__ void __launch_bounds__(256) k_ext_x(Config cfg) {
 #pragma unroll 8
           for (int k = 0; k < XK; ++k) {
             const float4 a = *reinterpret_cast<const float4*>(&Ns[k][4 * tj]);
+            const float4 u4 = *reinterpret_cast<const float4*>(&Us[k][4 * tc]);
+            const float uv[4] = {u4.x, u4.y, u4.z, u4.w};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              const float u = Us[k][tc + 8 * q];
-              acc[q][0] += u * a.x;
-              acc[q][1] += u * a.y;
-              acc[q][2] += u * a.z;
-              acc[q][3] += u * a.w;
+              acc[q][0] += uv[q] * a.x;
+              acc[q][1] += uv[q] * a.y;
+              acc[q][2] += uv[q] * a.z;
+              acc[q][3] += uv[q] * a.w;
             }
           }
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int c = cb + tc + 8 * q;
+          const int c = cb + 4 * tc + q;
           if (c < nc_)
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
