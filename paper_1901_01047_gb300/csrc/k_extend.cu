@@ -152,13 +152,15 @@ __global__ void __launch_bounds__(256) k_ext_x(Config cfg) {
       });
 }
 
-void launch_ext_mixed(const Config& cfg, int max_cap, cudaStream_t st) {
+int launch_ext_mixed(const Config& cfg, int max_cap, cudaStream_t st) {
   const long long S = 2LL * cfg.n_walkers;
   long long items = S * ((max_cap + XB - 1) / XB) * ((cfg.ks + XC - 1) / XC);
   constexpr long long kPersist = 8 * 152;
   items = items < 1 ? 1 : (items < kPersist ? items : kPersist);
-  k_ext_g<<<(int)items, 256, 0, st>>>(cfg);
+  if (cfg.ext_tc) launch_ext_g_tc(cfg, st);
+  else k_ext_g<<<(int)items, 256, 0, st>>>(cfg);
   k_ext_x<<<(int)items, 256, 0, st>>>(cfg);
+  return 2;
 }
 
 }  // namespace dca

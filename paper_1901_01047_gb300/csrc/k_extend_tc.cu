@@ -1,0 +1,294 @@
+// k_extend_tc.cu -- candidate column block of the extension on the 5th
+// generation tensor cores (mixed precision), Sec. 2.3 "Submatrix updates":
+//     G_ext[i, n + c] = sum_j N[i, j] V[c, j],   V[c, j] = g0(r_j - r_c, tau_j - tau_c).
+// 3xTF32 as in the N update: every operand x is used as hi = x with the low
+// 13 mantissa bits cleared and lo = x - hi; hi*hi + hi*lo + lo*hi accumulate
+// in FP32 in tensor memory.  V arrives pre-split from k_cand_zero ([hi | lo]
+// planes x KS_MAX rows x cap columns, in the update-operand buffer that is
+// free during the extension); N tiles are split in shared memory.
+//
+// Work item = one 128-row block of one walker-spin N.  The CTA streams the
+// block's columns 32 at a time through a three-stage ring:
+//   warp 4 (TMA producer)   N box (128 rows x 32 columns) and the V boxes;
+//   warps 0-3 (converters)  split the N box in place into hi and a lo plane,
+//                           zero the columns >= n; at the end of the item they
+//                           read the accumulator and store G_ext;
+//   warp 5 (MMA issuer)     4 K steps x 3 tcgen05.mma kind::tf32 (M = 128,
+//                           N = CN candidates) into one TMEM accumulator.
+// Every wait is bounded; a timeout sets the walker's status to
+// ST_ERR_TIMEOUT, lets the copies in flight land, frees the tensor memory and
+// returns.
+#include <cstdint>
+
+#include "device_util.cuh"
+#include "kernels.h"
+#include "state.h"
+#include "tc_ptx.cuh"
+
+namespace dca {
+
+constexpr int XT_BM = 128;    // rows per item
+constexpr int XT_STAGES = 3;
+
+template <int CN>
+struct XtLayout {
+  static constexpr int N_BOX = XT_BM * 128;     // 128 rows x 32 FP32 columns
+  static constexpr int V_BOX = CN * 128;        // CN rows x 32 columns
+  static constexpr int STAGE = 2 * N_BOX + 2 * V_BOX;  // N (hi), N lo, V hi, V lo
+  static constexpr int OFF_BAR = XT_STAGES * STAGE;
+  static constexpr int SMEM = OFF_BAR + 256 + 1024;
+  static constexpr uint32_t TMEM_COLS = CN < 32 ? 32 : CN;
+  static_assert(SMEM <= 232448, "shared memory");
+};
+
+__device__ __forceinline__ long long xt_items(const Config& cfg, int s) {
+  const WalkerDev& w = cfg.W[s >> 1];
+  return (w.active && w.n_cand > 0 && w.n > 0) ? (long long)((w.n + XT_BM - 1) / XT_BM) : 0;
+}
+
+struct XtIter {
+  int s = 0;
+  long long base = 0, cnt = 0, item = 0;
+  __device__ void start(const Config& cfg) {
+    s = 0;
+    base = 0;
+    cnt = cfg.n_walkers > 0 ? xt_items(cfg, 0) : 0;
+    item = blockIdx.x;
+  }
+  __device__ bool next(const Config& cfg, int& set, int& rb) {
+    const int nsets = 2 * cfg.n_walkers;
+    while (item >= base + cnt) {
+      base += cnt;
+      if (++s >= nsets) return false;
+      cnt = xt_items(cfg, s);
+    }
+    set = s;
+    rb = (int)(item - base);
+    item += gridDim.x;
+    return true;
+  }
+};
+
+__device__ __forceinline__ const void* xt_map(const Config& cfg, int wi, int sp, int kind) {
+  return (const void*)(cfg.tmaps + ((size_t)wi * 2 + sp) * TMAPS_PER_SPIN + kind);
+}
+
+template <int CN>
+__global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
+  using L = XtLayout<CN>;
+  extern __shared__ uint8_t xt_raw[];
+  const uint32_t raw = tc::smem_u32(xt_raw);
+  const uint32_t sb = (raw + 1023u) & ~1023u;
+  uint8_t* gb = xt_raw + (sb - raw);
+  const uint32_t bar = sb + L::OFF_BAR;
+  // barriers: full[3], conv[3], empty[3], dg_full, dg_empty, fin
+  auto full = [&](int st) { return bar + 8 * st; };
+  auto conv = [&](int st) { return bar + 24 + 8 * st; };
+  auto empty = [&](int st) { return bar + 48 + 8 * st; };
+  const uint32_t dg_full = bar + 72, dg_empty = bar + 80, fin = bar + 88;
+  uint32_t* tmem_slot = (uint32_t*)(gb + L::OFF_BAR + 96);
+  volatile int* abort_flag = (volatile int*)(gb + L::OFF_BAR + 100);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < XT_STAGES; ++st) {
+      tc::mbar_init(full(st), 1);
+      tc::mbar_init(conv(st), 4);
+      tc::mbar_init(empty(st), 1);
+    }
+    tc::mbar_init(dg_full, 1);
+    tc::mbar_init(dg_empty, 4);
+    tc::mbar_init(fin, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 5) {
+    tc::tmem_alloc(tc::smem_u32(tmem_slot), L::TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      XtIter it;
+      it.start(cfg);
+      uint32_t g = 0;
+      uint32_t armed[XT_STAGES] = {0u, 0u, 0u};
+      int set = 0, rb = 0;
+      bool ok = true;
+      while (ok && it.next(cfg, set, rb)) {
+        const WalkerDev& w = cfg.W[set >> 1];
+        const int wi = set >> 1, sp = set & 1, n = w.n, i0 = rb * XT_BM;
+        const void* mN = xt_map(cfg, wi, sp, 2 + w.parity);
+        const void* mV = xt_map(cfg, wi, sp, 4);
+        for (int j0 = 0; j0 < n; j0 += 32, ++g) {
+          const int st = (int)(g % XT_STAGES);
+          const uint32_t u = g / XT_STAGES;
+          if (u > 0 && !tc::mbar_wait(empty(st), (u - 1) & 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t s0 = sb + st * L::STAGE;
+          tc::mbar_expect_tx(full(st), (uint32_t)(L::N_BOX + 2 * L::V_BOX));
+          armed[st] = u + 1;
+          tc::tma_load_2d(s0, mN, j0, i0, full(st));
+          tc::tma_load_2d(s0 + 2 * L::N_BOX, mV, j0, 0, full(st));
+          tc::tma_load_2d(s0 + 2 * L::N_BOX + L::V_BOX, mV, j0, KS_MAX, full(st));
+        }
+      }
+      if (!ok) {
+        cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+        for (int st = 0; st < XT_STAGES; ++st)
+          if (armed[st] > 0) tc::mbar_wait(full(st), (armed[st] - 1) & 1u, nullptr, 400000000LL);
+      }
+    }
+  } else if (warp == 5) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      XtIter it;
+      it.start(cfg);
+      uint32_t g = 0, k = 0;
+      int set = 0, rb = 0;
+      bool ok = true;
+      const uint32_t idesc = tc::idesc_tf32(XT_BM, CN);
+      while (ok && it.next(cfg, set, rb)) {
+        const int n = cfg.W[set >> 1].n;
+        if (k > 0 && !tc::mbar_wait(dg_empty, (k - 1) & 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        bool first = true;
+        for (int j0 = 0; j0 < n; j0 += 32, ++g) {
+          const int st = (int)(g % XT_STAGES);
+          const uint32_t u = g / XT_STAGES;
+          if (!tc::mbar_wait(conv(st), u & 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t s0 = sb + st * L::STAGE;
+          const uint32_t nH = s0, nL = s0 + L::N_BOX, vH = s0 + 2 * L::N_BOX, vL = vH + L::V_BOX;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {  // K step of 8 columns: 32 bytes inside the 128-byte swizzle row
+            const uint64_t ah = tc::sdesc_k_sw128(nH + 32 * q), al = tc::sdesc_k_sw128(nL + 32 * q);
+            const uint64_t bh = tc::sdesc_k_sw128(vH + 32 * q), bl = tc::sdesc_k_sw128(vL + 32 * q);
+            tc::mma_tf32(tmem, ah, bh, idesc, first ? 0u : 1u);
+            tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+            tc::mma_tf32(tmem, al, bh, idesc, 1u);
+            first = false;
+          }
+          tc::mma_commit(empty(st));
+        }
+        if (!ok) break;
+        tc::mma_commit(dg_full);
+        ++k;
+      }
+      if (!ok) cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+      tc::mma_commit(fin);
+      tc::mbar_wait(fin, 0u, nullptr, 400000000LL);
+    }
+  } else {
+    // ---------------- converters / epilogue: warps 0-3 ----------------
+    XtIter it;
+    it.start(cfg);
+    uint32_t g = 0, k = 0;
+    int set = 0, rb = 0;
+    bool stop = false;
+    const int r = 32 * warp + lane;  // row of the block = TMEM lane
+    const uint32_t mask = 0xFFFFE000u;
+    while (!stop && it.next(cfg, set, rb)) {
+      WalkerDev& w = cfg.W[set >> 1];
+      const int sp = set & 1, n = w.n, nc_ = w.n_cand, ld = w.cap, i0 = rb * XT_BM;
+      for (int j0 = 0; j0 < n; j0 += 32, ++g) {
+        const int st = (int)(g % XT_STAGES);
+        const uint32_t u = g / XT_STAGES;
+        const bool mine = tc::mbar_wait(full(st), u & 1u, abort_flag);
+        if (!__all_sync(0xffffffffu, mine)) {
+          stop = true;
+          break;
+        }
+        // split this thread's row of the N box: hi in place, lo in the lo plane.
+        // Logical 16-byte chunk lc of row r sits at physical chunk lc ^ (r & 7)
+        // (128-byte swizzle): walking logical chunks spreads the lanes of a warp
+        // over all banks (walking physical chunks put all 32 lanes on 4 banks).
+        uint8_t* nrow = gb + st * L::STAGE + r * 128;
+#pragma unroll
+        for (int lc = 0; lc < 8; ++lc) {
+          const int pc = lc ^ (r & 7);
+          float4* ph = (float4*)(nrow + pc * 16);
+          float4* pl = (float4*)(nrow + L::N_BOX + pc * 16);
+          float4 x = *ph;
+          const int jc = j0 + 4 * lc;
+          float xv[4] = {x.x, x.y, x.z, x.w}, hv[4], lv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float v = jc + q < n ? xv[q] : 0.f;
+            hv[q] = __uint_as_float(__float_as_uint(v) & mask);
+            lv[q] = v - hv[q];
+          }
+          *ph = make_float4(hv[0], hv[1], hv[2], hv[3]);
+          *pl = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        }
+        tc::fence_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(conv(st));
+      }
+      if (stop) break;
+      // accumulator of the item: row i0 + r, candidates 0 .. CN - 1
+      const bool mine = tc::mbar_wait(dg_full, k & 1u, abort_flag);
+      if (!__all_sync(0xffffffffu, mine)) {
+        stop = true;
+        break;
+      }
+      tc::fence_after_sync();
+      const int i = i0 + r;
+#pragma unroll 1
+      for (int cb = 0; cb < CN; cb += 32) {
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cb, v);
+        if (i < n)
+#pragma unroll
+          for (int c = 0; c < 32; ++c)
+            if (cb + c < nc_) w.Gc[sp][(size_t)(cb + c) * ld + i] = (double)v[c];
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(dg_empty);
+      ++k;
+    }
+    if (stop && lane == 0) cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+    if (stop) *abort_flag = 1;
+  }
+  __syncthreads();
+  if (warp == 5) {
+    __syncwarp();
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, L::TMEM_COLS);
+  }
+}
+
+cudaError_t setup_ext_tc() {
+  cudaError_t e = cudaFuncSetAttribute(k_ext_g_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       XtLayout<64>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ext_g_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, XtLayout<128>::SMEM);
+  return e;
+}
+
+void launch_ext_g_tc(const Config& cfg, cudaStream_t st) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+  }
+  if (cfg.ks <= 64) k_ext_g_tc<64><<<sms, 192, XtLayout<64>::SMEM, st>>>(cfg);
+  else k_ext_g_tc<128><<<sms, 192, XtLayout<128>::SMEM, st>>>(cfg);
+}
+
+}  // namespace dca

@@ -85,7 +85,7 @@ struct TcIter {
 };
 
 __device__ __forceinline__ const void* tc_map(const Config& cfg, int wi, int sp, int kind) {
-  return (const void*)(cfg.tmaps + ((size_t)wi * 2 + sp) * 4 + kind);
+  return (const void*)(cfg.tmaps + ((size_t)wi * 2 + sp) * TMAPS_PER_SPIN + kind);
 }
 
 template <int BN, int KP>
@@ -425,15 +425,20 @@ static bool encode_2d(TmapDev* out, void* base, uint64_t cols, uint64_t rows, ui
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool encode_update_maps(const WalkerDev& w, int ks, TmapDev* out4x2) {
+int ext_tile_c(int ks) { return ks <= 64 ? 64 : 128; }
+
+bool encode_update_maps(const WalkerDev& w, int ks, TmapDev* out) {
   const uint64_t C = (uint64_t)w.cap;
   const uint32_t bn = (uint32_t)tc_tile_n(ks);
   for (int sp = 0; sp < 2; ++sp) {
-    TmapDev* m = out4x2 + 4 * sp;
+    TmapDev* m = out + TMAPS_PER_SPIN * sp;
     if (!encode_2d(m + 0, w.Aop[sp], TC_KS, 2 * C, TC_KS * 4, TC_BM)) return false;
     if (!encode_2d(m + 1, w.Bop[sp], TC_KS, 2 * C, TC_KS * 4, bn)) return false;
     for (int par = 0; par < 2; ++par)
       if (!encode_2d(m + 2 + par, w.N[par][sp], C, C, C * 4, TC_BM)) return false;
+    // candidate table V of the tensor-core extension: [hi | lo] x KS_MAX rows x C columns,
+    // in the update-operand buffer (free during the extension)
+    if (!encode_2d(m + 4, w.Aop[sp], C, 2 * (uint64_t)KS_MAX, C * 4, (uint32_t)ext_tile_c(ks))) return false;
   }
   return true;
 }

@@ -159,7 +159,9 @@ __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
       2 * cfg.n_walkers,
       [&](int s) -> long long {
         const WalkerDev& w = cfg.W[s >> 1];
-        return (w.active && w.n_cand > 0) ? blocks_of(w.n + w.n_cand, 256) : 0;
+        // columns up to n + n_cand (candidate-block targets) and up to the
+        // 32-column padding of the tensor-core extension's last K chunk
+        return (w.active && w.n_cand > 0) ? blocks_of(max(w.n + w.n_cand, (w.n + 31) & ~31), 256) : 0;
       },
       [&](int s, int item) {
         const WalkerDev& w = cfg.W[s >> 1];
@@ -174,9 +176,16 @@ __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
         }
         __syncthreads();
         const int i = item * 256 + threadIdx.x;
-        if (i >= n + nc_) return;
-        if (i >= n) {  // targets of the candidate block (k_cand_cc adds into them)
-          for (int c = 0; c < nc_; ++c) w.Gc[sp][(size_t)c * ld + i] = 0.0;
+        // split V for the tensor-core extension: [hi | lo] planes x KS_MAX rows x ld columns
+        float* Vop = cfg.ext_tc ? reinterpret_cast<float*>(w.Aop[sp]) : nullptr;
+        if (i >= n) {
+          if (i < n + nc_)  // targets of the candidate block (k_cand_cc adds into them)
+            for (int c = 0; c < nc_; ++c) w.Gc[sp][(size_t)c * ld + i] = 0.0;
+          if (Vop && i < ((n + 31) & ~31))  // K padding of the last chunk: finite zeros
+            for (int c = 0; c < nc_; ++c) {
+              Vop[(size_t)c * ld + i] = 0.f;
+              Vop[(size_t)(KS_MAX + c) * ld + i] = 0.f;
+            }
           return;
         }
         const int si = w.vs[par][i], ri = w.vsite[par][i];
@@ -197,6 +206,11 @@ __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
             }
             reinterpret_cast<float*>(w.Vb[sp])[o] = v;
             reinterpret_cast<float*>(w.Ub[sp])[o] = u;
+            if (Vop) {
+              const float hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+              Vop[(size_t)c * ld + i] = hi;
+              Vop[(size_t)(KS_MAX + c) * ld + i] = v - hi;
+            }
           } else {
             double v = 0.0, u = 0.0;
             if (si != 0) {
@@ -1069,9 +1083,9 @@ static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_
     case GROUP_EXTEND:
       k_cand_zero<<<grid_for(S * kc), 256, 0, st>>>(cfg);
       if (cfg.prec == PREC_MIXED) {
-        launch_ext_mixed(cfg, max_cap, st);
+        int k = launch_ext_mixed(cfg, max_cap, st);
         k_cand_cc<A><<<grid_for(S * 16), 256, 0, st>>>(cfg);
-        return 4;
+        return 2 + k;
       }
       k_cand_ext<T, A><<<grid_for(S * t64 * t64), 256, ext_smem_bytes<A>(), st>>>(cfg);
       k_cand_cc<A><<<grid_for(S * 16), 256, 0, st>>>(cfg);

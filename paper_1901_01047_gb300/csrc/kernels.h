@@ -53,13 +53,16 @@ void launch_refine_adopt(const Config& cfg, int max_cap, cudaStream_t st);
 int launch_recompute(int part, const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st);
 int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
 // Candidate extension of the mixed path: the two streaming passes over N.
-void launch_ext_mixed(const Config& cfg, int max_cap, cudaStream_t st);
+int launch_ext_mixed(const Config& cfg, int max_cap, cudaStream_t st);
 // Tensor-core N update (mixed precision): kernel attributes, tile width for
 // a submatrix size, tensor maps of one walker ([spin][A, B, N0, N1]), the
 // operand split and the update itself.
 cudaError_t setup_update_tc();
 int tc_tile_n(int ks);
-bool encode_update_maps(const WalkerDev& w, int ks, TmapDev* out4x2);
+int ext_tile_c(int ks);  // candidate tile (N extent) of the tensor-core extension
+bool encode_update_maps(const WalkerDev& w, int ks, TmapDev* out);
+cudaError_t setup_ext_tc();
+void launch_ext_g_tc(const Config& cfg, cudaStream_t st);
 void launch_upd_ops(const Config& cfg, cudaStream_t st);
 void launch_upd_tc(const Config& cfg, cudaStream_t st);
 void launch_negate(const double* src, double* dst, float* dstf, size_t n, cudaStream_t st);

@@ -148,6 +148,10 @@ struct LoopState {
   int32_t pad;
 };
 
+// TMA tensor maps per walker and spin: update operands A and B, N of parity 0
+// and 1, the candidate table V of the tensor-core extension.
+constexpr int TMAPS_PER_SPIN = 5;
+
 // Opaque copy of a TMA tensor map (CUtensorMap: 128 bytes, 64-byte aligned).
 struct alignas(64) TmapDev {
   uint64_t opaque[16];
@@ -173,7 +177,8 @@ struct Config {
   const ProblemDev* P;       // [n_problems]
   int32_t* active_count;     // [1]
   int32_t upd_kernel;        // UPD_CUDA_CORE or UPD_TCGEN05 (mixed precision)
-  const TmapDev* tmaps;      // [n_walkers][2 spins][A, B, N parity 0, N parity 1]
+  const TmapDev* tmaps;      // [n_walkers][2 spins][TMAPS_PER_SPIN]
+  int32_t ext_tc;            // mixed path: candidate product G_ext on tcgen05
   int32_t* gj_next;          // [1] next matrix of the Gauss-Jordan work queue (reset by k_build_A)
 };
 

@@ -330,12 +330,12 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     }
   }
   if (alloc_tc) {
-    h->d_tmaps = (dca::TmapDev*)h->dalloc(sizeof(dca::TmapDev) * (size_t)h->W * 8);
+    h->d_tmaps = (dca::TmapDev*)h->dalloc(sizeof(dca::TmapDev) * (size_t)h->W * 2 * dca::TMAPS_PER_SPIN);
     if (!h->d_tmaps || upload_update_maps(h, p.k_sub) != DCA_OK) {
       h->err = "TMA tensor maps of the tensor-core update";
       return bail(DCA_ERR_CUDA);
     }
-    if (dca::setup_update_tc() != cudaSuccess) {
+    if (dca::setup_update_tc() != cudaSuccess || dca::setup_ext_tc() != cudaSuccess) {
       h->err = "tensor-core update kernel attribute setup failed";
       return bail(DCA_ERR_CUDA);
     }
@@ -365,6 +365,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.recompute_sweeps = p.recompute_sweeps;
   h->cfg.recompute_gj = p.recompute_method == DCA_RECOMPUTE_GJ ? 1 : 0;
   h->cfg.upd_kernel = use_tc ? dca::UPD_TCGEN05 : dca::UPD_CUDA_CORE;
+  h->cfg.ext_tc = use_tc ? 1 : 0;  // the tcgen05 path covers the G_ext product of the extension too
   h->cfg.tmaps = h->d_tmaps;
 
   if (dca::setup_window_kernels() != cudaSuccess) {
@@ -391,9 +392,10 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
 // Encode and upload the TMA tensor maps of every walker (the B-operand box
 // depends on the submatrix size).
 static int upload_update_maps(dca_walker* h, int ks) {
-  std::vector<dca::TmapDev> maps((size_t)h->W * 8);
+  std::vector<dca::TmapDev> maps((size_t)h->W * 2 * dca::TMAPS_PER_SPIN);
   for (int wi = 0; wi < h->W; ++wi)
-    if (!dca::encode_update_maps(h->h_W[wi], ks, maps.data() + (size_t)wi * 8)) return DCA_ERR_CUDA;
+    if (!dca::encode_update_maps(h->h_W[wi], ks, maps.data() + (size_t)wi * 2 * dca::TMAPS_PER_SPIN))
+      return DCA_ERR_CUDA;
   if (cudaMemcpy(h->d_tmaps, maps.data(), sizeof(dca::TmapDev) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return DCA_ERR_CUDA;
   return DCA_OK;
@@ -587,13 +589,14 @@ extern "C" DCA_API int dca_walker_set_tuning(dca_walker* h, int32_t k_sub, int32
   CK(cudaStreamSynchronize(h->stream));
   const bool mixed = h->cfg.prec == dca::PREC_MIXED;
   const bool tc = mixed && update_kernel != DCA_UPD_CUDA_CORE;
-  if (tc && dca::tc_tile_n(k_sub) != dca::tc_tile_n(h->ks)) {
+  if (mixed && (dca::tc_tile_n(k_sub) != dca::tc_tile_n(h->ks) || dca::ext_tile_c(k_sub) != dca::ext_tile_c(h->ks))) {
     const int rc = upload_update_maps(h, k_sub);
     if (rc != DCA_OK) return fail(h, rc, "TMA tensor maps of the tensor-core update");
   }
   h->ks = k_sub;
   h->cfg.ks = k_sub;
   h->cfg.upd_kernel = tc ? dca::UPD_TCGEN05 : dca::UPD_CUDA_CORE;
+  h->cfg.ext_tc = tc ? 1 : 0;
   // the captured window loop holds the old launch configuration
   if (h->loop_exec) {
     cudaGraphExecDestroy(h->loop_exec);
