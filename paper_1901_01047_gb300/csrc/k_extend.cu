@@ -157,9 +157,13 @@ int launch_ext_mixed(const Config& cfg, int max_cap, cudaStream_t st) {
   long long items = S * ((max_cap + XB - 1) / XB) * ((cfg.ks + XC - 1) / XC);
   constexpr long long kPersist = 8 * 152;
   items = items < 1 ? 1 : (items < kPersist ? items : kPersist);
-  if (cfg.ext_tc) launch_ext_g_tc(cfg, st);
-  else k_ext_g<<<(int)items, 256, 0, st>>>(cfg);
-  k_ext_x<<<(int)items, 256, 0, st>>>(cfg);
+  if (cfg.ext_tc) {
+    launch_ext_g_tc(cfg, st);
+    launch_ext_x_tc(cfg, st);
+  } else {
+    k_ext_g<<<(int)items, 256, 0, st>>>(cfg);
+    k_ext_x<<<(int)items, 256, 0, st>>>(cfg);
+  }
   return 2;
 }
 

@@ -1,6 +1,7 @@
-// k_extend_tc.cu -- candidate column block of the extension on the 5th
+// k_extend_tc.cu -- candidate products of the extension on the 5th
 // generation tensor cores (mixed precision), Sec. 2.3 "Submatrix updates":
-//     G_ext[i, n + c] = sum_j N[i, j] V[c, j],   V[c, j] = g0(r_j - r_c, tau_j - tau_c).
+//     G_ext[i, n + c] = sum_j N[i, j] V[c, j],   V[c, j] = g0(r_j - r_c, tau_j - tau_c)   (k_ext_g_tc)
+//     X[c, j]         = sum_i U[c, i] N[i, j],   U[c, i] = g0(r_c - r_i, tau_c - tau_i) (e^{V_i} - 1)   (k_ext_x_tc)
 // 3xTF32 as in the N update: every operand x is used as hi = x with the low
 // 13 mantissa bits cleared and lo = x - hi; hi*hi + hi*lo + lo*hi accumulate
 // in FP32 in tensor memory.  V arrives pre-split from k_cand_zero ([hi | lo]
@@ -272,11 +273,267 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// X[c, j] = sum_i U[c, i] N[i, j] (the candidates' rows of N), same 3xTF32
+// scheme.  Work item = one 128-column block of one walker-spin N; the CTA
+// streams the rows 32 at a time.  Operands per stage: U (A, K-major: 128
+// candidate rows x 32 rows of N, [hi | lo] from k_cand_zero) and N^T (B,
+// K-major: 128 columns of N x 32 rows), which the converter warps write
+// transposed, split and swizzled from the four 32 x 32 boxes the TMA loads.
+// Accumulator: 128 lanes (candidates) x 128 columns.
+constexpr int XX2_BJ = 128;  // columns per item
+constexpr int XX2_STAGES = 2;
+
+struct Xx2Layout {
+  static constexpr int N_BOX = 32 * 128;               // 32 rows x 32 columns (TMA)
+  static constexpr int N_TILE = 4 * N_BOX;             // 32 rows x 128 columns
+  static constexpr int T_TILE = 128 * 128;             // N^T: 128 columns x 32 rows, one plane
+  static constexpr int U_TILE = 128 * 128;             // 128 candidates x 32 rows
+  static constexpr int STAGE = N_TILE + 2 * T_TILE + 2 * U_TILE;
+  static constexpr int OFF_BAR = XX2_STAGES * STAGE;
+  static constexpr int SMEM = OFF_BAR + 256 + 1024;
+  static constexpr uint32_t TMEM_COLS = XX2_BJ;
+  static_assert(SMEM <= 232448, "shared memory");
+};
+
+__device__ __forceinline__ long long xx2_items(const Config& cfg, int s) {
+  const WalkerDev& w = cfg.W[s >> 1];
+  return (w.active && w.n_cand > 0 && w.n > 0) ? (long long)((w.n + XX2_BJ - 1) / XX2_BJ) : 0;
+}
+
+struct Xx2Iter {
+  int s = 0;
+  long long base = 0, cnt = 0, item = 0;
+  __device__ void start(const Config& cfg) {
+    s = 0;
+    base = 0;
+    cnt = cfg.n_walkers > 0 ? xx2_items(cfg, 0) : 0;
+    item = blockIdx.x;
+  }
+  __device__ bool next(const Config& cfg, int& set, int& jb) {
+    const int nsets = 2 * cfg.n_walkers;
+    while (item >= base + cnt) {
+      base += cnt;
+      if (++s >= nsets) return false;
+      cnt = xx2_items(cfg, s);
+    }
+    set = s;
+    jb = (int)(item - base);
+    item += gridDim.x;
+    return true;
+  }
+};
+
+__global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
+  using L = Xx2Layout;
+  extern __shared__ uint8_t xx_raw[];
+  const uint32_t raw = tc::smem_u32(xx_raw);
+  const uint32_t sb = (raw + 1023u) & ~1023u;
+  uint8_t* gb = xx_raw + (sb - raw);
+  const uint32_t bar = sb + L::OFF_BAR;
+  auto full = [&](int st) { return bar + 8 * st; };
+  auto conv = [&](int st) { return bar + 24 + 8 * st; };
+  auto empty = [&](int st) { return bar + 48 + 8 * st; };
+  const uint32_t dx_full = bar + 72, dx_empty = bar + 80, fin = bar + 88;
+  uint32_t* tmem_slot = (uint32_t*)(gb + L::OFF_BAR + 96);
+  volatile int* abort_flag = (volatile int*)(gb + L::OFF_BAR + 100);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < XX2_STAGES; ++st) {
+      tc::mbar_init(full(st), 1);
+      tc::mbar_init(conv(st), 4);
+      tc::mbar_init(empty(st), 1);
+    }
+    tc::mbar_init(dx_full, 1);
+    tc::mbar_init(dx_empty, 4);
+    tc::mbar_init(fin, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 5) {
+    tc::tmem_alloc(tc::smem_u32(tmem_slot), L::TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      Xx2Iter it;
+      it.start(cfg);
+      uint32_t g = 0;
+      uint32_t armed[XX2_STAGES] = {0u, 0u};
+      int set = 0, jb = 0;
+      bool ok = true;
+      while (ok && it.next(cfg, set, jb)) {
+        const WalkerDev& w = cfg.W[set >> 1];
+        const int wi = set >> 1, sp = set & 1, n = w.n, j0 = jb * XX2_BJ;
+        const void* mN = xt_map(cfg, wi, sp, 6 + w.parity);
+        const void* mU = xt_map(cfg, wi, sp, 5);
+        for (int i0 = 0; i0 < n; i0 += 32, ++g) {
+          const int st = (int)(g % XX2_STAGES);
+          const uint32_t u = g / XX2_STAGES;
+          if (u > 0 && !tc::mbar_wait(empty(st), (u - 1) & 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t s0 = sb + st * L::STAGE;
+          tc::mbar_expect_tx(full(st), (uint32_t)(L::N_TILE + 2 * L::U_TILE));
+          armed[st] = u + 1;
+          for (int b = 0; b < 4; ++b) tc::tma_load_2d(s0 + b * L::N_BOX, mN, j0 + 32 * b, i0, full(st));
+          tc::tma_load_2d(s0 + L::N_TILE + 2 * L::T_TILE, mU, i0, 0, full(st));
+          tc::tma_load_2d(s0 + L::N_TILE + 2 * L::T_TILE + L::U_TILE, mU, i0, KS_MAX, full(st));
+        }
+      }
+      if (!ok) {
+        cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+        for (int st = 0; st < XX2_STAGES; ++st)
+          if (armed[st] > 0) tc::mbar_wait(full(st), (armed[st] - 1) & 1u, nullptr, 400000000LL);
+      }
+    }
+  } else if (warp == 5) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      Xx2Iter it;
+      it.start(cfg);
+      uint32_t g = 0, k = 0;
+      int set = 0, jb = 0;
+      bool ok = true;
+      const uint32_t idesc = tc::idesc_tf32(128, XX2_BJ);
+      while (ok && it.next(cfg, set, jb)) {
+        const int n = cfg.W[set >> 1].n;
+        if (k > 0 && !tc::mbar_wait(dx_empty, (k - 1) & 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        bool first = true;
+        for (int i0 = 0; i0 < n; i0 += 32, ++g) {
+          const int st = (int)(g % XX2_STAGES);
+          const uint32_t u = g / XX2_STAGES;
+          if (!tc::mbar_wait(conv(st), u & 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t s0 = sb + st * L::STAGE;
+          const uint32_t tH = s0 + L::N_TILE, tL = tH + L::T_TILE, uH = tL + L::T_TILE, uL = uH + L::U_TILE;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            // K step of 8 rows of N: 32 bytes inside the 128-byte swizzle rows of U and N^T
+            const uint64_t ah = tc::sdesc_k_sw128(uH + 32 * q), al = tc::sdesc_k_sw128(uL + 32 * q);
+            const uint64_t bh = tc::sdesc_k_sw128(tH + 32 * q), bl = tc::sdesc_k_sw128(tL + 32 * q);
+            tc::mma_tf32(tmem, ah, bh, idesc, first ? 0u : 1u);
+            tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+            tc::mma_tf32(tmem, al, bh, idesc, 1u);
+            first = false;
+          }
+          tc::mma_commit(empty(st));
+        }
+        if (!ok) break;
+        tc::mma_commit(dx_full);
+        ++k;
+      }
+      if (!ok) cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+      tc::mma_commit(fin);
+      tc::mbar_wait(fin, 0u, nullptr, 400000000LL);
+    }
+  } else {
+    // ---------------- converters / epilogue: warps 0-3 ----------------
+    Xx2Iter it;
+    it.start(cfg);
+    uint32_t g = 0, k = 0;
+    int set = 0, jb = 0;
+    bool stop = false;
+    const int bx = warp, r = lane;  // converter: box bx, row r of the box
+    const uint32_t mask = 0xFFFFE000u;
+    while (!stop && it.next(cfg, set, jb)) {
+      WalkerDev& w = cfg.W[set >> 1];
+      const int sp = set & 1, n = w.n, nc_ = w.n_cand, ld = w.cap, j0 = jb * XX2_BJ;
+      for (int i0 = 0; i0 < n; i0 += 32, ++g) {
+        const int st = (int)(g % XX2_STAGES);
+        const uint32_t u = g / XX2_STAGES;
+        const bool mine = tc::mbar_wait(full(st), u & 1u, abort_flag);
+        if (!__all_sync(0xffffffffu, mine)) {
+          stop = true;
+          break;
+        }
+        // row i = i0 + r of box bx (columns j = 32 bx + 4 lc + q of the item):
+        // split, and write N^T[j][i] into the K-major planes (row j, 128-byte
+        // swizzle: 16-byte chunk (r >> 2) ^ (j & 7), word r & 3).  The 32 lanes
+        // of a warp write the 32 words of one 128-byte row: no bank conflicts.
+        // Rows >= n are zeroed (K padding); the logical chunk lc of the box row
+        // sits at physical chunk lc ^ (r & 7).
+        const bool row_ok = i0 + r < n;
+        const uint8_t* nrow = gb + st * L::STAGE + bx * L::N_BOX + r * 128;
+        uint8_t* tH = gb + st * L::STAGE + L::N_TILE;
+        uint8_t* tL = tH + L::T_TILE;
+#pragma unroll
+        for (int lc = 0; lc < 8; ++lc) {
+          const float4 x = *(const float4*)(nrow + ((lc ^ (r & 7)) << 4));
+          const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float v = row_ok ? xv[q] : 0.f;
+            const float hv = __uint_as_float(__float_as_uint(v) & mask);
+            const int j = 32 * bx + 4 * lc + q;
+            const int off = j * 128 + ((((r >> 2) ^ (j & 7)) << 4) | ((r & 3) << 2));
+            *(float*)(tH + off) = hv;
+            *(float*)(tL + off) = v - hv;
+          }
+        }
+        tc::fence_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(conv(st));
+      }
+      if (stop) break;
+      const bool mine = tc::mbar_wait(dx_full, k & 1u, abort_flag);
+      if (!__all_sync(0xffffffffu, mine)) {
+        stop = true;
+        break;
+      }
+      tc::fence_after_sync();
+      // accumulator lane = candidate 32 warp + lane, columns j0 .. j0 + 127
+      if (32 * warp < nc_) {
+        const int c = 32 * warp + lane;
+        double* xrow = w.Xr[sp] + (size_t)c * ld;
+#pragma unroll 1
+        for (int cb = 0; cb < XX2_BJ; cb += 32) {
+          float v[32];
+          tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cb, v);
+          if (c < nc_)
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+              if (j0 + cb + q < n) xrow[j0 + cb + q] = (double)v[q];
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(dx_empty);
+      ++k;
+    }
+    if (stop && lane == 0) cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+    if (stop) *abort_flag = 1;
+  }
+  __syncthreads();
+  if (warp == 5) {
+    __syncwarp();
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, L::TMEM_COLS);
+  }
+}
+
 cudaError_t setup_ext_tc() {
   cudaError_t e = cudaFuncSetAttribute(k_ext_g_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        XtLayout<64>::SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_ext_g_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, XtLayout<128>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ext_x_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, Xx2Layout::SMEM);
   return e;
 }
 
@@ -289,6 +546,16 @@ void launch_ext_g_tc(const Config& cfg, cudaStream_t st) {
   }
   if (cfg.ks <= 64) k_ext_g_tc<64><<<sms, 192, XtLayout<64>::SMEM, st>>>(cfg);
   else k_ext_g_tc<128><<<sms, 192, XtLayout<128>::SMEM, st>>>(cfg);
+}
+
+void launch_ext_x_tc(const Config& cfg, cudaStream_t st) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+  }
+  k_ext_x_tc<<<sms, 192, Xx2Layout::SMEM, st>>>(cfg);
 }
 
 }  // namespace dca

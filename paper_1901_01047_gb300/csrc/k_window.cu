@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
         const int i = item * 256 + threadIdx.x;
         // split V for the tensor-core extension: [hi | lo] planes x KS_MAX rows x ld columns
         float* Vop = cfg.ext_tc ? reinterpret_cast<float*>(w.Aop[sp]) : nullptr;
+        float* Uop = cfg.ext_tc ? reinterpret_cast<float*>(w.Bop[sp]) : nullptr;
         if (i >= n) {
           if (i < n + nc_)  // targets of the candidate block (k_cand_cc adds into them)
             for (int c = 0; c < nc_; ++c) w.Gc[sp][(size_t)c * ld + i] = 0.0;
@@ -185,6 +186,8 @@ __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
             for (int c = 0; c < nc_; ++c) {
               Vop[(size_t)c * ld + i] = 0.f;
               Vop[(size_t)(KS_MAX + c) * ld + i] = 0.f;
+              Uop[(size_t)c * ld + i] = 0.f;
+              Uop[(size_t)(KS_MAX + c) * ld + i] = 0.f;
             }
           return;
         }
@@ -207,9 +210,12 @@ __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
             reinterpret_cast<float*>(w.Vb[sp])[o] = v;
             reinterpret_cast<float*>(w.Ub[sp])[o] = u;
             if (Vop) {
-              const float hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-              Vop[(size_t)c * ld + i] = hi;
-              Vop[(size_t)(KS_MAX + c) * ld + i] = v - hi;
+              const float hv = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+              Vop[(size_t)c * ld + i] = hv;
+              Vop[(size_t)(KS_MAX + c) * ld + i] = v - hv;
+              const float hu = __uint_as_float(__float_as_uint(u) & 0xFFFFE000u);
+              Uop[(size_t)c * ld + i] = hu;
+              Uop[(size_t)(KS_MAX + c) * ld + i] = u - hu;
             }
           } else {
             double v = 0.0, u = 0.0;

