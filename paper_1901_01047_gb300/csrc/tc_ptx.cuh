@@ -132,29 +132,12 @@ __device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
   return d;
 }
 
-// Descriptor of an MN-major operand tile with 128-byte swizzling: atoms of
-// 32 FP32 along MN (128 bytes) x 8 rows along K (1024 bytes); the leading byte
-// offset is the distance between atoms adjacent along MN, the stride byte
-// offset the distance between 8-row groups along K.
-__device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1u << 46;
-  d |= (uint64_t)2u << 61;
-  return d;
-}
-
 // Instruction descriptor of kind::tf32 with FP32 accumulation, both operands
 // K-major, no negation or sparsity: D format bits 4-5 (1 = F32), A and B
 // formats bits 7-9 / 10-12 (2 = TF32), N >> 3 at bits 17-22, M >> 4 at 24-28.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-
-// Same with B MN-major (bit 16, "transpose B").
-__host__ __device__ constexpr uint32_t idesc_tf32_bmn(int M, int N) { return idesc_tf32(M, N) | (1u << 16); }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
