@@ -45,7 +45,7 @@ struct dca_walker {
   std::vector<uint8_t*> forced;     // per walker replay buffers
   WalkerDev* d_W = nullptr;
   ProblemDev* d_P = nullptr;
-  int* d_active = nullptr;          // [4]: active, errors, first error, pad
+  int* d_active = nullptr;          // [8]: active count, -, -, work queues of the inverse (3, 4)
   int* h_active = nullptr;          // pinned
   int* d_sgn = nullptr;
   dca::Config cfg{};
@@ -65,6 +65,8 @@ struct dca_walker {
   int64_t total_launches = 0;
   // device-side window loop: a graph with a conditional WHILE node
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_stream2 = nullptr;      // second branch of the captured window (half of the batch)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;
   dca::LoopState* d_loop = nullptr;
@@ -74,6 +76,9 @@ struct dca_walker {
     if (stream) cudaStreamSynchronize(stream);
     if (loop_exec) cudaGraphExecDestroy(loop_exec);
     if (loop_graph) cudaGraphDestroy(loop_graph);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (cap_stream2) cudaStreamDestroy(cap_stream2);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
@@ -341,7 +346,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     }
   }
   h->d_W = (WalkerDev*)h->dalloc(sizeof(WalkerDev) * h->W);
-  h->d_active = (int*)h->dalloc(sizeof(int) * 4);
+  h->d_active = (int*)h->dalloc(sizeof(int) * 8);
   h->d_sgn = (int*)h->dalloc(sizeof(int) * 2 * h->W);
   if (!h->d_W || !h->d_active || !h->d_sgn || cudaMallocHost(&h->h_active, sizeof(int) * 4) != cudaSuccess) {
     h->err = "device allocation of walker records";
@@ -477,6 +482,25 @@ static void collect_events(dca_walker* h) {
   h->ev_used = 0;
 }
 
+// Batches of at least this many walkers are split into two concurrent
+// halves inside the captured window.
+constexpr int kSplitWalkers = 32;
+
+// One window's kernel sequence for the walkers of cfg on stream st.
+static int launch_window_sequence(dca_walker* h, const dca::Config& cfg, cudaStream_t st) {
+  int k = 0;
+  for (int i = 0; i < n_window_groups(h); ++i) {
+    const int g = dca::WINDOW_GROUPS[i];
+    if (g == dca::GROUP_MEASURE)
+      k += dca::launch_measure(cfg, h->max_cap, h->max_nc, st);
+    else if (g == dca::GROUP_RECOMPUTE_PRE || g == dca::GROUP_RECOMPUTE || g == dca::GROUP_RECOMPUTE_POST)
+      k += dca::launch_recompute(g, cfg, h->max_cap, h->d_sgn, st);
+    else
+      k += dca::launch_window_group(g, cfg, h->max_cap, st);
+  }
+  return k;
+}
+
 // Build the device-side window loop once: an outer graph holding one
 // conditional WHILE node whose body (captured from the same launchers the
 // host loop uses) is one window plus the loop-control kernel.
@@ -500,14 +524,28 @@ static int build_loop_graph(dca_walker* h) {
   cudaGraph_t body = np.conditional.phGraph_out[0];
   CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   int k = 0;
-  for (int i = 0; i < n_window_groups(h); ++i) {
-    const int g = dca::WINDOW_GROUPS[i];
-    if (g == dca::GROUP_MEASURE)
-      k += dca::launch_measure(h->cfg, h->max_cap, h->max_nc, h->cap_stream);
-    else if (g == dca::GROUP_RECOMPUTE_PRE || g == dca::GROUP_RECOMPUTE || g == dca::GROUP_RECOMPUTE_POST)
-      k += dca::launch_recompute(g, h->cfg, h->max_cap, h->d_sgn, h->cap_stream);
-    else
-      k += dca::launch_window_group(g, h->cfg, h->max_cap, h->cap_stream);
+  if (h->W >= kSplitWalkers) {
+    // Two independent halves of the batch in two branches of the body: the
+    // latency-bound kernels of one half (Metropolis, the factor kernels)
+    // overlap the bandwidth- and tensor-bound kernels of the other.
+    if (!h->cap_stream2) CK(cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking));
+    if (!h->ev_fork) CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    if (!h->ev_join) CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    const int wa = h->W / 2;
+    dca::Config ca = h->cfg, cb = h->cfg;
+    ca.n_walkers = wa;
+    cb.n_walkers = h->W - wa;
+    cb.W = h->cfg.W + wa;
+    if (cb.tmaps) cb.tmaps = h->cfg.tmaps + (size_t)wa * 2 * dca::TMAPS_PER_SPIN;
+    cb.gj_next = h->d_active + 4;
+    CK(cudaEventRecord(h->ev_fork, h->cap_stream));
+    CK(cudaStreamWaitEvent(h->cap_stream2, h->ev_fork, 0));
+    k += launch_window_sequence(h, ca, h->cap_stream);
+    k += launch_window_sequence(h, cb, h->cap_stream2);
+    CK(cudaEventRecord(h->ev_join, h->cap_stream2));
+    CK(cudaStreamWaitEvent(h->cap_stream, h->ev_join, 0));
+  } else {
+    k += launch_window_sequence(h, h->cfg, h->cap_stream);
   }
   dca::launch_loop_control(h->cfg, handle, h->d_loop, h->cap_stream);
   k += 1;
