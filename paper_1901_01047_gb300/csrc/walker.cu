@@ -45,7 +45,7 @@ struct dca_walker {
   std::vector<uint8_t*> forced;     // per walker replay buffers
   WalkerDev* d_W = nullptr;
   ProblemDev* d_P = nullptr;
-  int* d_active = nullptr;          // [8]: active count, -, -, work queues of the inverse (3, 4)
+  int* d_active = nullptr;          // [8]: active count, -, -, work queues of the inverse (3 .. 6)
   int* h_active = nullptr;          // pinned
   int* d_sgn = nullptr;
   dca::Config cfg{};
@@ -65,8 +65,8 @@ struct dca_walker {
   int64_t total_launches = 0;
   // device-side window loop: a graph with a conditional WHILE node
   cudaStream_t cap_stream = nullptr;
-  cudaStream_t cap_stream2 = nullptr;      // second branch of the captured window (half of the batch)
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t cap_br[4] = {nullptr, nullptr, nullptr, nullptr};  // branches of the captured window
+  cudaEvent_t ev_fork = nullptr, ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;
   dca::LoopState* d_loop = nullptr;
@@ -77,8 +77,10 @@ struct dca_walker {
     if (loop_exec) cudaGraphExecDestroy(loop_exec);
     if (loop_graph) cudaGraphDestroy(loop_graph);
     if (ev_fork) cudaEventDestroy(ev_fork);
-    if (ev_join) cudaEventDestroy(ev_join);
-    if (cap_stream2) cudaStreamDestroy(cap_stream2);
+    for (int b = 0; b < 4; ++b) {
+      if (ev_join[b]) cudaEventDestroy(ev_join[b]);
+      if (cap_br[b]) cudaStreamDestroy(cap_br[b]);
+    }
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
@@ -482,9 +484,8 @@ static void collect_events(dca_walker* h) {
   h->ev_used = 0;
 }
 
-// Batches of at least this many walkers are split into two concurrent
-// halves inside the captured window.
-constexpr int kSplitWalkers = 32;
+// Concurrent branches of the captured window for a batch of W walkers.
+static int window_branches(int W) { return W >= 128 ? 4 : (W >= 32 ? 2 : 1); }
 
 // One window's kernel sequence for the walkers of cfg on stream st.
 static int launch_window_sequence(dca_walker* h, const dca::Config& cfg, cudaStream_t st) {
@@ -524,26 +525,27 @@ static int build_loop_graph(dca_walker* h) {
   cudaGraph_t body = np.conditional.phGraph_out[0];
   CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   int k = 0;
-  if (h->W >= kSplitWalkers) {
-    // Two independent halves of the batch in two branches of the body: the
-    // latency-bound kernels of one half (Metropolis, the factor kernels)
-    // overlap the bandwidth- and tensor-bound kernels of the other.
-    if (!h->cap_stream2) CK(cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking));
+  const int nb = window_branches(h->W);
+  if (nb > 1) {
+    // Independent parts of the batch in concurrent branches of the body: the
+    // latency-bound kernels of one part (Metropolis, the factor kernels)
+    // overlap the bandwidth- and tensor-bound kernels of the others.
     if (!h->ev_fork) CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-    if (!h->ev_join) CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-    const int wa = h->W / 2;
-    dca::Config ca = h->cfg, cb = h->cfg;
-    ca.n_walkers = wa;
-    cb.n_walkers = h->W - wa;
-    cb.W = h->cfg.W + wa;
-    if (cb.tmaps) cb.tmaps = h->cfg.tmaps + (size_t)wa * 2 * dca::TMAPS_PER_SPIN;
-    cb.gj_next = h->d_active + 4;
     CK(cudaEventRecord(h->ev_fork, h->cap_stream));
-    CK(cudaStreamWaitEvent(h->cap_stream2, h->ev_fork, 0));
-    k += launch_window_sequence(h, ca, h->cap_stream);
-    k += launch_window_sequence(h, cb, h->cap_stream2);
-    CK(cudaEventRecord(h->ev_join, h->cap_stream2));
-    CK(cudaStreamWaitEvent(h->cap_stream, h->ev_join, 0));
+    for (int b = 0; b < nb; ++b) {
+      if (!h->cap_br[b]) CK(cudaStreamCreateWithFlags(&h->cap_br[b], cudaStreamNonBlocking));
+      if (!h->ev_join[b]) CK(cudaEventCreateWithFlags(&h->ev_join[b], cudaEventDisableTiming));
+      const int w0 = (int)((long long)h->W * b / nb), w1 = (int)((long long)h->W * (b + 1) / nb);
+      dca::Config cp = h->cfg;
+      cp.n_walkers = w1 - w0;
+      cp.W = h->cfg.W + w0;
+      if (cp.tmaps) cp.tmaps = h->cfg.tmaps + (size_t)w0 * 2 * dca::TMAPS_PER_SPIN;
+      cp.gj_next = h->d_active + 3 + b;  // own work queue of the inverse
+      CK(cudaStreamWaitEvent(h->cap_br[b], h->ev_fork, 0));
+      k += launch_window_sequence(h, cp, h->cap_br[b]);
+      CK(cudaEventRecord(h->ev_join[b], h->cap_br[b]));
+      CK(cudaStreamWaitEvent(h->cap_stream, h->ev_join[b], 0));
+    }
   } else {
     k += launch_window_sequence(h, h->cfg, h->cap_stream);
   }
