@@ -589,15 +589,21 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
       }
     }
     __syncthreads();
-    // 7. bordered inverse: [[Binv + t s / d, -t / d], [-s / d, 1 / d]]
+    // 7. bordered inverse: [[Binv + t s / d, -t / d], [-s / d, 1 / d]],
+    //    with s / d formed once per column (one FMA per element)
+    if (tid < 2 * KS_MAX) {
+      const int sp = tid / KS_MAX, jj = tid - sp * KS_MAX;
+      if (jj < l) s_s[sp][jj] *= 1.0 / s_d[sp];
+    }
+    __syncthreads();
     for (int sp = 0; sp < 2; ++sp) {
       const double rd = 1.0 / s_d[sp];
       for (int idx = tid; idx < (l + 1) * (l + 1); idx += blockDim.x) {
         const int i = idx / (l + 1), jj = idx - i * (l + 1);
         double* B = Binv[sp] + (size_t)i * bst + jj;
-        if (i < l && jj < l) *B += s_t[sp][i] * s_s[sp][jj] * rd;
+        if (i < l && jj < l) *B = fma(s_t[sp][i], s_s[sp][jj], *B);
         else if (i < l) *B = -s_t[sp][i] * rd;
-        else if (jj < l) *B = -s_s[sp][jj] * rd;
+        else if (jj < l) *B = -s_s[sp][jj];
         else *B = rd;
       }
     }

@@ -167,3 +167,13 @@ def test_autotuner_selects_a_candidate_and_leaves_walkers_on_it():
     gw.sweep(2)
     assert all(s["status"] == 0 for s in gw.stats())
     gw.close()
+
+
+def test_mixed_replay_error_at_the_batched_recompute_interval():
+    # The batched bench recomputes every 8 sweeps, about 320 windows for its
+    # largest walkers; the 16-site case recomputing every 320 windows states
+    # the error reached there.
+    errN, errG, st, _ = replay(16, -0.15, 6.0, 4.0, 2.85, 16, 200, 320, ntm=16, n_tau=2048)
+    assert st["status"] == 0 and st["recomputes"] >= 1
+    assert errN < 2e-4, errN  # measured 2.5e-5
+    assert errG < 3e-5, errG  # measured 4.3e-6
