@@ -763,36 +763,51 @@ __global__ void __launch_bounds__(256) k_upd_lrow(Config cfg) {
 
 // Lp = Lrow Binv on the same rows ; Rr[p, j] = N_ext[P_p, j] for j < n,
 // stored in the arithmetic type A of the update product
+// Per thread: one output (FP64 path) or four consecutive outputs of a row
+// (mixed path: four independent double-float chains sharing the loads of L).
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_upd_lp_rr(Config cfg) {
+  constexpr int PT = sizeof(T) == 4 ? 4 : 1;
   for_each_item(
       2 * cfg.n_walkers,
       [&](int s) -> long long {
         const WalkerDev& w = cfg.W[s >> 1];
         if (!upd_active(w)) return 0;
-        return blocks_of((long long)(w.n + w.n_ins) * w.n_acc, 256) + blocks_of((long long)w.n_acc * w.n, 256);
+        const int lq = (w.n_acc + PT - 1) / PT;
+        return blocks_of((long long)(w.n + w.n_ins) * lq, 256) + blocks_of((long long)w.n_acc * w.n, 256);
       },
       [&](int s, int item) {
         const WalkerDev& w = cfg.W[s >> 1];
         const int sp = s & 1;
         const int l = w.n_acc, n = w.n, rows = n + w.n_ins;
-        const int lp_blocks = (int)blocks_of((long long)rows * l, 256);
+        const int lq = (l + PT - 1) / PT;
+        const int lp_blocks = (int)blocks_of((long long)rows * lq, 256);
         if (item < lp_blocks) {
           const int idx = item * 256 + threadIdx.x;
-          if (idx < rows * l) {
-            const int t = idx / l, p = idx - t * l;
+          if (idx < rows * lq) {
+            const int t = idx / lq, p = (idx - t * lq) * PT;
             const int x = upd_row(w, t);
             // FP64-grade on both paths (B^-1 carries the conditioning of the
             // window): FP64, or double-float on FP32 pairs on the mixed path
             if (sizeof(T) == 4) {
               const float2* Lr = reinterpret_cast<const float2*>(w.Lrow[sp]) + (size_t)x * KS_MAX;
               const float2* Bi = reinterpret_cast<const float2*>(w.Binv[sp]);
-              float hi = 0.f, lo = 0.f;
+              float hi[PT], lo[PT];
+#pragma unroll
+              for (int u = 0; u < PT; ++u) hi[u] = lo[u] = 0.f;
               for (int q = 0; q < l; ++q) {
-                const float2 a = Lr[q], b = Bi[(size_t)q * KS_MAX + p];
-                df_fma(hi, lo, a.x, a.y, b.x, b.y);
+                const float2 a = Lr[q];
+                const float2* brow = Bi + (size_t)q * KS_MAX + p;
+#pragma unroll
+                for (int u = 0; u < PT; ++u) {
+                  const float2 b = brow[u];  // columns >= l of B^-1 are never read back
+                  df_fma(hi[u], lo[u], a.x, a.y, b.x, b.y);
+                }
               }
-              reinterpret_cast<float2*>(w.Lp[sp])[(size_t)x * KS_MAX + p] = df_norm(hi, lo);
+              float2* out = reinterpret_cast<float2*>(w.Lp[sp]) + (size_t)x * KS_MAX + p;
+#pragma unroll
+              for (int u = 0; u < PT; ++u)
+                if (p + u < l) out[u] = df_norm(hi[u], lo[u]);
             } else {
               const double* Lr = w.Lrow[sp] + (size_t)x * KS_MAX;
               const double* Bi = w.Binv[sp];
@@ -807,8 +822,8 @@ __global__ void __launch_bounds__(256) k_upd_lp_rr(Config cfg) {
             const ExtView<T> v = make_view<T>(w, sp);
             const int p = idx / n, j = idx - p * n;
             const int P = w.P[p];
-            const double r = P < n ? ldN(v.N, (size_t)P * v.ld + j) : v.X[(size_t)(P - n) * v.ld + j];
-            ((A*)w.Rr[sp])[(size_t)p * w.cap + j] = (A)r;
+            ((A*)w.Rr[sp])[(size_t)p * w.cap + j] =
+                P < n ? ldA<A>(v.N, (size_t)P * v.ld + j) : (A)v.X[(size_t)(P - n) * v.ld + j];
           }
         }
       });
