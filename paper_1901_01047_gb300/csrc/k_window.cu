@@ -425,8 +425,68 @@ __device__ __forceinline__ double g_ext(const ExtView<T>& v, const ProblemDev& p
   return (nxy * ev - (x == y ? 1.0 : 0.0)) * pb.rexpVm1[sp][sy > 0 ? 1 : 0];
 }
 
+// G_ext[x, y] with the spin factors of column y given: e^{V_y} and
+// 1 / (e^{V_y} - 1) (unused for a candidate column y >= n).
+template <typename T>
+__device__ __forceinline__ double g_ext_at(const ExtView<T>& v, int x, int y, double ev, double rv) {
+  if (y >= v.n) return v.Gc[(size_t)(y - v.n) * v.ld + x];
+  const double nxy = (x < v.n) ? ldN(v.N, (size_t)x * v.ld + y) : v.X[(size_t)(x - v.n) * v.ld + y];
+  return (nxy * ev - (x == y ? 1.0 : 0.0)) * rv;
+}
+
+// Arithmetic of the bordered growth of B^-1 (App. B): FP64 on the FP64 path;
+// on the mixed path double-float pairs (hi, lo) of FP32, about 44 significant
+// bits at the FP32 issue rate (FP64 issues at a small fraction of it on this
+// GPU).  The pairs are also the format in which the update kernels read B^-1.
+template <typename T>
+struct MetroScalar {
+  using type = double;
+};
+template <>
+struct MetroScalar<float> {
+  using type = float2;
+};
+
+__device__ __forceinline__ void m_set(double& r, double x) { r = x; }
+__device__ __forceinline__ void m_set(float2& r, double x) { r = df_split(x); }
+__device__ __forceinline__ double m_val(double a) { return a; }
+__device__ __forceinline__ double m_val(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ void m_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ void m_zero(float2& a) { a = make_float2(0.f, 0.f); }
+// acc += a b
+__device__ __forceinline__ void m_fma(double& acc, double a, double b) { acc = fma(a, b, acc); }
+__device__ __forceinline__ void m_fma(float2& acc, float2 a, float2 b) { df_fma(acc.x, acc.y, a.x, a.y, b.x, b.y); }
+// acc += b
+__device__ __forceinline__ void m_acc(double& acc, double b) { acc += b; }
+__device__ __forceinline__ void m_acc(float2& acc, float2 b) { df_fma(acc.x, acc.y, b.x, b.y, 1.f, 0.f); }
+// normalised value of an accumulator
+__device__ __forceinline__ double m_fin(double a) { return a; }
+__device__ __forceinline__ float2 m_fin(float2 a) { return df_norm(a.x, a.y); }
+__device__ __forceinline__ double m_neg(double a) { return -a; }
+__device__ __forceinline__ float2 m_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ double m_mul(double a, double b) { return a * b; }
+__device__ __forceinline__ float2 m_mul(float2 a, float2 b) {
+  float hi = 0.f, lo = 0.f;
+  df_fma(hi, lo, a.x, a.y, b.x, b.y);
+  return df_norm(hi, lo);
+}
+__device__ __forceinline__ double m_shfl_xor(double a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+__device__ __forceinline__ float2 m_shfl_xor(float2 a, int o) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
+}
+
+constexpr int METRO_LIVE = 2048;  // live vertices whose rows and spins are staged in shared memory
+
+// One block per walker, both spins.  Per proposal: (1) its target and a_t,
+// (2) the border of B against the accepted set P, (3) t = B^-1 b_col, (4) the
+// Schur complements d_sigma = B_tt - b_row t, (5) the decision on
+// R = (K / (k + 1) or k / K) d_up d_down, and on acceptance (6) s = b_row B^-1 / d
+// and (7) the bordered inverse [[B^-1 + t s, -t / d], [-s, 1 / d]].  Thread 0
+// plans proposal j + 1 (step 1) together with decision j, so a rejection
+// costs three block barriers and an acceptance four.
 template <typename T>
 __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
+  using M = typename MetroScalar<T>::type;
   WalkerDev& w = cfg.W[blockIdx.x];
   __shared__ int s_active;
   if (threadIdx.x == 0) s_active = w.active;
@@ -435,23 +495,42 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
   const ProblemDev& pb = cfg.P[w.problem];
   const int tid = threadIdx.x;
   const int n = w.n, n_live = w.n_live, len = w.win_len;
-  ExtView<T> ev[2] = {make_view<T>(w, 0), make_view<T>(w, 1)};
-  // B^-1 of both spins: in shared memory when k_s <= METRO_SMEM_KS (copied to
-  // the global buffers at the end for the update kernels), else in global memory.
+  const ExtView<T> ev[2] = {make_view<T>(w, 0), make_view<T>(w, 1)};
+  // B^-1 of both spins: in shared memory when k_s <= METRO_SMEM_KS, with row
+  // stride k_s | 1 (odd: the row-wise products of step 3 are free of bank
+  // conflicts), copied to the global buffers at the end; else in the global
+  // buffers (row stride KS_MAX).
   extern __shared__ double s_binv[];
   const bool in_smem = cfg.ks <= METRO_SMEM_KS;
-  const int bst = in_smem ? cfg.ks : KS_MAX;
-  double* Binv[2] = {in_smem ? s_binv : w.Binv[0], in_smem ? s_binv + cfg.ks * cfg.ks : w.Binv[1]};
-  const int* live_idx = w.live_idx;
+  const int bst = in_smem ? (cfg.ks | 1) : KS_MAX;
+  M* const Binv[2] = {in_smem ? reinterpret_cast<M*>(s_binv) : reinterpret_cast<M*>(w.Binv[0]),
+                      in_smem ? reinterpret_cast<M*>(s_binv) + (size_t)cfg.ks * bst : reinterpret_cast<M*>(w.Binv[1])};
 
-  __shared__ double s_brow[2][KS_MAX], s_bcol[2][KS_MAX], s_t[2][KS_MAX], s_s[2][KS_MAX];
+  __shared__ Proposal s_prop[KS_MAX];
+  __shared__ int s_live[METRO_LIVE];  // 2 row + (s > 0) of the live vertex of each rank
+  __shared__ M s_brow[2][KS_MAX], s_bcol[2][KS_MAX], s_t[2][KS_MAX], s_s[2][KS_MAX];
+  __shared__ M s_rd[2];
   __shared__ double s_aP[2][KS_MAX];
   __shared__ int s_P[KS_MAX];
+  __shared__ int s_Pup[KS_MAX];       // spin of a live P_p > 0
   __shared__ int s_removed[KS_MAX];   // live ranks removed in this window, ascending
-  __shared__ double s_anew[2], s_Btt[2], s_d[2];
-  __shared__ int s_target, s_kind, s_stop, s_accept, s_l, s_nrem, s_nins, s_kcur, s_eval, s_rank;
+  __shared__ double s_ev[2][2], s_rv[2][2];  // e^{V} and 1 / (e^{V} - 1): [spin][s > 0]
+  __shared__ double s_anew[2], s_Btt[2];
+  __shared__ int s_target, s_tup, s_kind, s_stop, s_accept, s_l, s_nrem, s_nins, s_kcur, s_eval, s_rank;
   __shared__ double s_sign;
 
+  const bool live_smem = n_live <= METRO_LIVE;
+  for (int j = tid; j < len; j += blockDim.x) s_prop[j] = w.prop[j];
+  if (live_smem)
+    for (int r = tid; r < n_live; r += blockDim.x) {
+      const int x = w.live_idx[r];
+      s_live[r] = 2 * x + (ev[0].vs[x] > 0 ? 1 : 0);
+    }
+  if (tid < 4) {
+    const int sp = tid >> 1, up = tid & 1;
+    s_ev[sp][up] = pb.expV[sp][up];
+    s_rv[sp][up] = pb.rexpVm1[sp][up];
+  }
   if (tid == 0) {
     s_l = 0;
     s_nrem = 0;
@@ -460,56 +539,72 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
     s_sign = w.sign;
     s_eval = 0;
   }
+  // thread 0's view of the chain state
+  const uint64_t q0 = w.q;
+  const int64_t forced_n = w.forced_n, log_cap = w.log_cap;
+  const double K = pb.K;
+  int64_t c_prop = 0, c_acc = 0, c_ties = 0;
+  __syncthreads();
+
+  // Step 1 (thread 0): target of proposal j, its spin and the new a_t.
+  auto plan = [&](int j) {
+    const Proposal& pr = s_prop[j];
+    const int kcur = n_live - s_nrem + s_nins;
+    int kind = 0, target = -1, rank = -1, up = 0;
+    if (pr.type == 0) {
+      target = n + pr.slot;
+      for (int sp = 0; sp < 2; ++sp) s_anew[sp] = s_ev[sp][pr.s > 0 ? 1 : 0] - 1.0;
+    } else if (kcur == 0) {
+      kind = 2;
+    } else {
+      const int idx = (int)scaled_index(pr.word, (uint32_t)kcur);
+      if (idx >= n_live - s_nrem) {
+        s_stop = 1;  // picks a spin inserted in this window: end the window here
+      } else {
+        // idx-th live vertex not yet removed in this window
+        rank = idx;
+        for (int r = 0; r < s_nrem; ++r) {
+          if (s_removed[r] <= rank) ++rank;
+          else break;
+        }
+        kind = 1;
+        if (live_smem) {
+          const int v = s_live[rank];
+          target = v >> 1;
+          up = v & 1;
+        } else {
+          target = w.live_idx[rank];
+          up = ev[0].vs[target] > 0 ? 1 : 0;
+        }
+        for (int sp = 0; sp < 2; ++sp) s_anew[sp] = s_ev[sp][up ? 0 : 1] - 1.0;  // e^{V(-s)} - 1
+      }
+    }
+    s_kind = kind;
+    s_target = target;
+    s_rank = rank;
+    s_kcur = kcur;
+    s_tup = up;
+  };
+  if (tid == 0 && len > 0) plan(0);
   __syncthreads();
 
   for (int j = 0; j < len; ++j) {
-    // 1. target of proposal j
-    if (tid == 0) {
-      const Proposal pr = w.prop[j];
-      const int kcur = n_live - s_nrem + s_nins;
-      int kind = 0, target = -1, rank = -1;
-      if (pr.type == 0) {
-        kind = 0;
-        target = n + pr.slot;
-        for (int sp = 0; sp < 2; ++sp) s_anew[sp] = expV(pb, sp, pr.s) - 1.0;
-      } else if (kcur == 0) {
-        kind = 2;
-      } else {
-        const int idx = (int)scaled_index(pr.word, (uint32_t)kcur);
-        if (idx >= n_live - s_nrem) {
-          s_stop = 1;  // picks a spin inserted in this window: end the window here
-        } else {
-          // idx-th live vertex not yet removed in this window
-          rank = idx;
-          for (int r = 0; r < s_nrem; ++r) {
-            if (s_removed[r] <= rank) ++rank;
-            else break;
-          }
-          kind = 1;
-          target = live_idx[rank];
-          const int s = ev[0].vs[target];
-          for (int sp = 0; sp < 2; ++sp) s_anew[sp] = expV(pb, sp, -s) - 1.0;
-        }
-      }
-      s_kind = kind;
-      s_target = target;
-      s_rank = rank;
-      s_kcur = kcur;
-    }
-    __syncthreads();
     if (s_stop) break;
     const int l = s_l;
     if (s_kind == 2) {
+      // a removal from the empty configuration: ratio zero, rejected
+      __syncthreads();  // every thread has read s_kind and s_l
       if (tid == 0) {
-        const uint64_t q = w.q + (uint64_t)j;
-        if ((int64_t)q < w.log_cap) w.log[q] = 0;
-        w.n_prop++;
+        const uint64_t q = q0 + (uint64_t)j;
+        if ((int64_t)q < log_cap) w.log[q] = 0;
+        ++c_prop;
         s_eval = j + 1;
+        if (j + 1 < len) plan(j + 1);
       }
       __syncthreads();
       continue;
     }
-    const int t = s_target;
+    const int t = s_target, tup = s_tup;
     // 2. border of B: row / column against P, and the new diagonal entry
     for (int idx = tid; idx < 4 * l + 2; idx += blockDim.x) {
       if (idx < 4 * l) {
@@ -519,129 +614,138 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
         const int P = s_P[p];
         if (rem & 1) {
           const double a = s_anew[sp];  // column: B[P_p, t] = -G[P_p, t] a_t
-          s_bcol[sp][p] = (a == 0.0) ? 0.0 : -g_ext(ev[sp], pb, sp, P, t) * a;
+          m_set(s_bcol[sp][p], a == 0.0 ? 0.0 : -g_ext_at(ev[sp], P, t, s_ev[sp][tup], s_rv[sp][tup]) * a);
         } else {
           const double a = s_aP[sp][p];  // row: B[t, P_p] = -G[t, P_p] a_{P_p}
-          s_brow[sp][p] = (a == 0.0) ? 0.0 : -g_ext(ev[sp], pb, sp, t, P) * a;
+          const int up = s_Pup[p];
+          m_set(s_brow[sp][p], a == 0.0 ? 0.0 : -g_ext_at(ev[sp], t, P, s_ev[sp][up], s_rv[sp][up]) * a);
         }
       } else {
         const int sp = idx - 4 * l;
         const double a = s_anew[sp];
-        s_Btt[sp] = (a == 0.0) ? 1.0 : 1.0 + (1.0 - g_ext(ev[sp], pb, sp, t, t)) * a;
+        s_Btt[sp] = (a == 0.0) ? 1.0 : 1.0 + (1.0 - g_ext_at(ev[sp], t, t, s_ev[sp][tup], s_rv[sp][tup])) * a;
       }
     }
     __syncthreads();
-    // 3. t = Binv b_col
+    // 3. t = B^-1 b_col
     if (tid < 2 * KS_MAX) {
       const int sp = tid / KS_MAX, i = tid - sp * KS_MAX;
       if (i < l) {
-        const double* B = Binv[sp] + (size_t)i * bst;
-        double acc = 0.0;
-        for (int p = 0; p < l; ++p) acc += B[p] * s_bcol[sp][p];
-        s_t[sp][i] = acc;
+        const M* B = Binv[sp] + (size_t)i * bst;
+        M acc;
+        m_zero(acc);
+        for (int p = 0; p < l; ++p) m_fma(acc, B[p], s_bcol[sp][p]);
+        s_t[sp][i] = m_fin(acc);
       }
     }
     __syncthreads();
-    // 4. Schur complement d = B_tt - b_row . t  (warp 0: up, warp 1: down)
-    if (tid < 64) {
-      const int sp = tid >> 5, lane = tid & 31;
-      double acc = 0.0;
-      for (int i = lane; i < l; i += 32) acc += s_brow[sp][i] * s_t[sp][i];
+    // 4. Schur complements d = B_tt - b_row . t, and 5. the decision (warp 0);
+    //    thread 0 then records an acceptance and plans proposal j + 1
+    if (tid < 32) {
+      M a0, a1;
+      m_zero(a0);
+      m_zero(a1);
+      for (int i = tid; i < l; i += 32) {
+        m_fma(a0, s_brow[0][i], s_t[0][i]);
+        m_fma(a1, s_brow[1][i], s_t[1][i]);
+      }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) s_d[sp] = s_Btt[sp] - acc;
-    }
-    __syncthreads();
-    // 5. decision
-    if (tid == 0) {
-      const Proposal pr = w.prop[j];
-      const uint64_t q = w.q + (uint64_t)j;
-      const int kcur = s_kcur;
-      const double R = (s_kind == 0 ? pb.K / (double)(kcur + 1) : (double)kcur / pb.K) * s_d[0] * s_d[1];
-      int acc = 0, tie = 0;
-      if (!isfinite(R)) {
-        w.status = ST_ERR_NUMERIC;
-        s_stop = 1;
-      } else {
-        const double absR = fabs(R);
-        acc = pr.u < absR;
-        tie = fabs(absR - pr.u) < cfg.tie_eps;
-        if ((int64_t)q < w.forced_n) acc = w.forced[q] & 1;
-        if (acc && R < 0.0) s_sign = -s_sign;
-        if ((int64_t)q < w.log_cap) w.log[q] = (uint8_t)(acc | (tie << 1));
-        w.n_prop++;
-        w.n_ties += tie;
-        w.n_accept += acc;
-        s_eval = j + 1;
+      for (int o = 16; o > 0; o >>= 1) {
+        m_acc(a0, m_shfl_xor(a0, o));
+        m_acc(a1, m_shfl_xor(a1, o));
       }
-      s_accept = acc;
+      if (tid == 0) {
+        const double d0 = s_Btt[0] - m_val(a0), d1 = s_Btt[1] - m_val(a1);
+        const Proposal& pr = s_prop[j];
+        const uint64_t q = q0 + (uint64_t)j;
+        const int kcur = s_kcur;
+        const double R = (s_kind == 0 ? K / (double)(kcur + 1) : (double)kcur / K) * d0 * d1;
+        int acc = 0, tie = 0;
+        if (!isfinite(R)) {
+          w.status = ST_ERR_NUMERIC;
+          s_stop = 1;
+        } else {
+          const double absR = fabs(R);
+          acc = pr.u < absR;
+          tie = fabs(absR - pr.u) < cfg.tie_eps;
+          if ((int64_t)q < forced_n) acc = w.forced[q] & 1;
+          if (acc && R < 0.0) s_sign = -s_sign;
+          if ((int64_t)q < log_cap) w.log[q] = (uint8_t)(acc | (tie << 1));
+          ++c_prop;
+          c_ties += tie;
+          c_acc += acc;
+          s_eval = j + 1;
+          if (acc) {
+            m_set(s_rd[0], 1.0 / d0);
+            m_set(s_rd[1], 1.0 / d1);
+            s_P[l] = t;
+            s_Pup[l] = tup;
+            s_aP[0][l] = s_anew[0];
+            s_aP[1][l] = s_anew[1];
+            if (s_kind == 1) {
+              int r = s_nrem;  // keep the removed ranks ascending
+              while (r > 0 && s_removed[r - 1] > s_rank) {
+                s_removed[r] = s_removed[r - 1];
+                --r;
+              }
+              s_removed[r] = s_rank;
+              s_nrem++;
+            } else {
+              s_nins++;
+            }
+            s_l = l + 1;
+          }
+          if (j + 1 < len) plan(j + 1);
+        }
+        s_accept = acc;
+      }
     }
     __syncthreads();
-    if (s_stop) break;
     if (!s_accept) continue;
-    // 6. s = b_row Binv
+    // 6. s = b_row B^-1 / d
     if (tid < 2 * KS_MAX) {
       const int sp = tid / KS_MAX, jj = tid - sp * KS_MAX;
       if (jj < l) {
-        double acc = 0.0;
-        for (int i = 0; i < l; ++i) acc += s_brow[sp][i] * Binv[sp][(size_t)i * bst + jj];
-        s_s[sp][jj] = acc;
+        M acc;
+        m_zero(acc);
+        for (int i = 0; i < l; ++i) m_fma(acc, s_brow[sp][i], Binv[sp][(size_t)i * bst + jj]);
+        s_s[sp][jj] = m_mul(m_fin(acc), s_rd[sp]);
       }
     }
     __syncthreads();
-    // 7. bordered inverse: [[Binv + t s / d, -t / d], [-s / d, 1 / d]],
-    //    with s / d formed once per column (one FMA per element)
-    if (tid < 2 * KS_MAX) {
-      const int sp = tid / KS_MAX, jj = tid - sp * KS_MAX;
-      if (jj < l) s_s[sp][jj] *= 1.0 / s_d[sp];
-    }
-    __syncthreads();
-    for (int sp = 0; sp < 2; ++sp) {
-      const double rd = 1.0 / s_d[sp];
-      for (int idx = tid; idx < (l + 1) * (l + 1); idx += blockDim.x) {
-        const int i = idx / (l + 1), jj = idx - i * (l + 1);
-        double* B = Binv[sp] + (size_t)i * bst + jj;
-        if (i < l && jj < l) *B = fma(s_t[sp][i], s_s[sp][jj], *B);
-        else if (i < l) *B = -s_t[sp][i] * rd;
-        else if (jj < l) *B = -s_s[sp][jj];
-        else *B = rd;
-      }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      s_P[l] = t;
-      s_aP[0][l] = s_anew[0];
-      s_aP[1][l] = s_anew[1];
-      if (s_kind == 1) {
-        int r = s_nrem;  // keep the removed ranks ascending
-        while (r > 0 && s_removed[r - 1] > s_rank) {
-          s_removed[r] = s_removed[r - 1];
-          --r;
+    // 7. bordered inverse: [[B^-1 + t s, -t / d], [-s, 1 / d]] (s already / d)
+    {
+      const int e = (l + 1) * (l + 1);
+      for (int idx = tid; idx < 2 * e; idx += blockDim.x) {
+        const int sp = idx >= e ? 1 : 0, r = idx - sp * e;
+        const int i = r / (l + 1), jj = r - i * (l + 1);
+        M* B = Binv[sp] + (size_t)i * bst + jj;
+        if (i < l && jj < l) {
+          M b = *B;
+          m_fma(b, s_t[sp][i], s_s[sp][jj]);
+          *B = m_fin(b);
+        } else if (i < l) {
+          *B = m_neg(m_mul(s_t[sp][i], s_rd[sp]));
+        } else if (jj < l) {
+          *B = m_neg(s_s[sp][jj]);
+        } else {
+          *B = s_rd[sp];
         }
-        s_removed[r] = s_rank;
-        s_nrem++;
-      } else {
-        s_nins++;
       }
-      s_l = l + 1;
     }
-    __syncthreads();
+    // no barrier: the next reads of B^-1 and of s_t / s_s / s_rd follow the
+    // barrier after step 2, and steps 1-2 write nothing step 7 reads
   }
   __syncthreads();
 
   // Epilogue: window bookkeeping and the accepted set.
   const int l = s_l, nrem = s_nrem, nins = s_nins;
-  // B^-1 for the update kernels: FP64 on the FP64 path, FP32 pairs (hi, lo)
-  // in the same buffer on the mixed path (element by element, so the
-  // in-place conversion of the global working copy is safe).
-  constexpr bool kPairs = sizeof(T) == 4;
-  if (in_smem || kPairs)
+  // B^-1 for the update kernels (FP64, or the FP32 pairs on the mixed path)
+  if (in_smem)
     for (int sp = 0; sp < 2; ++sp)
       for (int idx = tid; idx < l * l; idx += blockDim.x) {
         const int i = idx / l, jj = idx - i * l;
-        const double b = Binv[sp][(size_t)i * bst + jj];
-        if (kPairs) reinterpret_cast<float2*>(w.Binv[sp])[(size_t)i * KS_MAX + jj] = df_split(b);
-        else w.Binv[sp][(size_t)i * KS_MAX + jj] = b;
+        reinterpret_cast<M*>(w.Binv[sp])[(size_t)i * KS_MAX + jj] = Binv[sp][(size_t)i * bst + jj];
       }
   for (int p = tid; p < l; p += blockDim.x) {
     w.P[p] = s_P[p];
@@ -650,6 +754,9 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
   }
   for (int r = tid; r < nrem; r += blockDim.x) w.removed[r] = s_removed[r];
   if (tid == 0) {
+    w.n_prop += c_prop;
+    w.n_ties += c_ties;
+    w.n_accept += c_acc;
     int m = 0;
     for (int p = 0; p < l; ++p)
       if (s_P[p] >= n) {
@@ -1118,7 +1225,7 @@ static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_
       k_cand_cc<A><<<grid_for(S * 16), 256, 0, st>>>(cfg);
       return 3;
     case GROUP_METROPOLIS: {
-      const int sm = cfg.ks <= METRO_SMEM_KS ? (int)sizeof(double) * 2 * cfg.ks * cfg.ks : 0;
+      const int sm = cfg.ks <= METRO_SMEM_KS ? (int)sizeof(double) * 2 * cfg.ks * (cfg.ks | 1) : 0;
       k_metropolis<T><<<W, 256, sm, st>>>(cfg);
       return 1;
     }
@@ -1154,7 +1261,7 @@ cudaError_t setup_window_kernels() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_cand_ext<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              ext_smem_bytes<float>());
-  const int msm = (int)sizeof(double) * 2 * METRO_SMEM_KS * METRO_SMEM_KS;
+  const int msm = (int)sizeof(double) * 2 * METRO_SMEM_KS * (METRO_SMEM_KS | 1);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_metropolis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, msm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_metropolis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, msm);
   return e;
