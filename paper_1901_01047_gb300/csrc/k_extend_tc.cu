@@ -24,6 +24,7 @@
 #include "device_util.cuh"
 #include "kernels.h"
 #include "state.h"
+#include "item_plan.cuh"
 #include "tc_ptx.cuh"
 
 namespace dca {
@@ -39,7 +40,7 @@ struct XtLayout {
   static constexpr int OFF_BAR = XT_STAGES * STAGE;
   static constexpr int SMEM = OFF_BAR + 256 + 1024;
   static constexpr uint32_t TMEM_COLS = CN < 32 ? 32 : CN;
-  static_assert(SMEM <= 232448, "shared memory");
+  static_assert(SMEM + sizeof(ItemPlan) <= 232448, "shared memory (dynamic + the static item plan)");
 };
 
 __device__ __forceinline__ long long xt_items(const Config& cfg, int s) {
@@ -48,25 +49,10 @@ __device__ __forceinline__ long long xt_items(const Config& cfg, int s) {
 }
 
 struct XtIter {
-  int s = 0;
-  long long base = 0, cnt = 0, item = 0;
-  __device__ void start(const Config& cfg) {
-    s = 0;
-    base = 0;
-    cnt = cfg.n_walkers > 0 ? xt_items(cfg, 0) : 0;
-    item = blockIdx.x;
-  }
+  PlanWalk<ItemPlan> pw;
+  __device__ void start(const Config&, const ItemPlan& plan) { pw.start(plan); }
   __device__ bool next(const Config& cfg, int& set, int& rb) {
-    const int nsets = 2 * cfg.n_walkers;
-    while (item >= base + cnt) {
-      base += cnt;
-      if (++s >= nsets) return false;
-      cnt = xt_items(cfg, s);
-    }
-    set = s;
-    rb = (int)(item - base);
-    item += gridDim.x;
-    return true;
+    return pw.next(2 * cfg.n_walkers, [&](int s) { return xt_items(cfg, s); }, set, rb);
   }
 };
 
@@ -111,12 +97,14 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  __shared__ ItemPlan plan;
+  plan_items(plan, 2 * cfg.n_walkers, [&](int s) { return xt_items(cfg, s); });
 
   if (warp == 4) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       XtIter it;
-      it.start(cfg);
+      it.start(cfg, plan);
       uint32_t g = 0;
       uint32_t armed[XT_STAGES] = {0u, 0u, 0u};
       int set = 0, rb = 0;
@@ -151,7 +139,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       XtIter it;
-      it.start(cfg);
+      it.start(cfg, plan);
       uint32_t g = 0, k = 0;
       int set = 0, rb = 0;
       bool ok = true;
@@ -196,7 +184,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
   } else {
     // ---------------- converters / epilogue: warps 0-3 ----------------
     XtIter it;
-    it.start(cfg);
+    it.start(cfg, plan);
     uint32_t g = 0, k = 0;
     int set = 0, rb = 0;
     bool stop = false;
@@ -293,7 +281,7 @@ struct Xx2Layout {
   static constexpr int OFF_BAR = XX2_STAGES * STAGE;
   static constexpr int SMEM = OFF_BAR + 256 + 1024;
   static constexpr uint32_t TMEM_COLS = XX2_BJ;
-  static_assert(SMEM <= 232448, "shared memory");
+  static_assert(SMEM + sizeof(ItemPlan) <= 232448, "shared memory (dynamic + the static item plan)");
 };
 
 __device__ __forceinline__ long long xx2_items(const Config& cfg, int s) {
@@ -302,25 +290,10 @@ __device__ __forceinline__ long long xx2_items(const Config& cfg, int s) {
 }
 
 struct Xx2Iter {
-  int s = 0;
-  long long base = 0, cnt = 0, item = 0;
-  __device__ void start(const Config& cfg) {
-    s = 0;
-    base = 0;
-    cnt = cfg.n_walkers > 0 ? xx2_items(cfg, 0) : 0;
-    item = blockIdx.x;
-  }
+  PlanWalk<ItemPlan> pw;
+  __device__ void start(const Config&, const ItemPlan& plan) { pw.start(plan); }
   __device__ bool next(const Config& cfg, int& set, int& jb) {
-    const int nsets = 2 * cfg.n_walkers;
-    while (item >= base + cnt) {
-      base += cnt;
-      if (++s >= nsets) return false;
-      cnt = xx2_items(cfg, s);
-    }
-    set = s;
-    jb = (int)(item - base);
-    item += gridDim.x;
-    return true;
+    return pw.next(2 * cfg.n_walkers, [&](int s) { return xx2_items(cfg, s); }, set, jb);
   }
 };
 
@@ -359,12 +332,14 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  __shared__ ItemPlan plan;
+  plan_items(plan, 2 * cfg.n_walkers, [&](int s) { return xx2_items(cfg, s); });
 
   if (warp == 4) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       Xx2Iter it;
-      it.start(cfg);
+      it.start(cfg, plan);
       uint32_t g = 0;
       uint32_t armed[XX2_STAGES] = {0u, 0u};
       int set = 0, jb = 0;
@@ -399,7 +374,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       Xx2Iter it;
-      it.start(cfg);
+      it.start(cfg, plan);
       uint32_t g = 0, k = 0;
       int set = 0, jb = 0;
       bool ok = true;
@@ -445,7 +420,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
   } else {
     // ---------------- converters / epilogue: warps 0-3 ----------------
     Xx2Iter it;
-    it.start(cfg);
+    it.start(cfg, plan);
     uint32_t g = 0, k = 0;
     int set = 0, jb = 0;
     bool stop = false;

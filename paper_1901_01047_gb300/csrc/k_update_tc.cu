@@ -22,10 +22,12 @@
 #include <cuda.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "device_util.cuh"
 #include "kernels.h"
 #include "state.h"
+#include "item_plan.cuh"
 #include "tc_ptx.cuh"
 
 namespace dca {
@@ -50,7 +52,8 @@ struct TcLayout {
   static constexpr int SMEM = OFF_BAR + 128 + 1024;   // barriers, TMEM slot, flag; 1 KB alignment slack
   static constexpr uint32_t TMEM_COLS = 2 * BN;
   static_assert(BN % 32 == 0 && BN >= 32 && BN <= 128, "tile width");
-  static_assert(SMEM <= 232448, "shared memory");
+  using Plan = typename std::conditional<SMEM + sizeof(ItemPlan) <= 232448, ItemPlan, ItemPlanSmall>::type;
+  static_assert(SMEM + sizeof(Plan) <= 232448, "shared memory (dynamic + the static item plan)");
 };
 
 // Work items: (walker-spin s, 128-row block) for walkers with an update.
@@ -59,28 +62,13 @@ __device__ __forceinline__ long long tc_items(const Config& cfg, int s) {
   return (w.active && w.n_acc > 0) ? (long long)((w.n + TC_BM - 1) / TC_BM) : 0;
 }
 
-// Deterministic walk over the items of this CTA (the same in every role).
+// Walk over the items of this CTA (the same in every role), from its plan.
+template <typename Plan>
 struct TcIter {
-  int s = 0;
-  long long base = 0, cnt = 0, item;
+  PlanWalk<Plan> pw;
+  __device__ void start(const Config&, const Plan& plan) { pw.start(plan); }
   __device__ bool next(const Config& cfg, int& set, int& rb) {
-    const int nsets = 2 * cfg.n_walkers;
-    while (item >= base + cnt) {
-      base += cnt;
-      if (++s >= nsets) return false;
-      cnt = tc_items(cfg, s);
-    }
-    set = s;
-    rb = (int)(item - base);
-    item += gridDim.x;
-    return true;
-  }
-  __device__ void start(const Config& cfg) {
-    s = 0;
-    base = 0;
-    cnt = 2 * cfg.n_walkers > 0 ? tc_items(cfg, 0) : 0;
-    item = blockIdx.x;
-    if (2 * cfg.n_walkers <= 0) s = 1 << 30;
+    return pw.next(2 * cfg.n_walkers, [&](int s) { return tc_items(cfg, s); }, set, rb);
   }
 };
 
@@ -122,12 +110,14 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  __shared__ typename L::Plan plan;
+  plan_items(plan, 2 * cfg.n_walkers, [&](int s) { return tc_items(cfg, s); });
 
   if (warp == 4) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      TcIter it;
-      it.start(cfg);
+      TcIter<typename L::Plan> it;
+      it.start(cfg, plan);
       uint32_t g = 0, k = 0;
       uint32_t armed[2] = {0u, 0u};  // uses of each stage armed so far
       int set = 0, rb = 0;
@@ -177,8 +167,8 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
   } else if (warp == 5) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      TcIter it;
-      it.start(cfg);
+      TcIter<typename L::Plan> it;
+      it.start(cfg, plan);
       uint32_t g = 0, k = 0;
       int set = 0, rb = 0;
       bool ok = true;
@@ -227,8 +217,8 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
     }
   } else {
     // ---------------- epilogue: warps 0-3, TMEM lanes 32 warp .. +31 ----------------
-    TcIter it;
-    it.start(cfg);
+    TcIter<typename L::Plan> it;
+    it.start(cfg, plan);
     uint32_t g = 0;
     int set = 0, rb = 0;
     bool stop = false;
