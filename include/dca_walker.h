@@ -101,7 +101,22 @@ typedef struct {
                                       the same window, so the inverses share the GPU); 0 = off.
                                       Independent of recompute_every. */
   int32_t recompute_method;        /* DCA_RECOMPUTE_* */
+  int32_t schedule;                /* DCA_SCHEDULE_*: how dca_walker_sweep shares the windows */
 } dca_walker_params;
+
+/* Scheduling of the walkers by dca_walker_sweep(n).  The chains do not depend
+ * on it: each walker's windows, recomputes and measurements follow from its
+ * own proposal counter and sweep count only.
+ *   LOCKSTEP: every walker runs exactly n more sweeps, and all walkers start
+ *             each sweep in the same window (a walker with a shorter sweep
+ *             waits for the others).
+ *   POOLED:   the walkers together run n * n_walkers more sweeps, every walker
+ *             taking part in every window until that total is reached (the
+ *             measurement budget is shared, as independent walkers of uneven
+ *             expansion order do; a walker may stop part-way through a sweep
+ *             and resumes it on the next call). */
+#define DCA_SCHEDULE_LOCKSTEP 0
+#define DCA_SCHEDULE_POOLED 1
 
 /* Recompute of N (the inverse of e^V - g0 (e^V - 1), Eq. Zk, formed from
  * scratch in FP64 for the current configuration):
@@ -164,12 +179,14 @@ DCA_API int dca_g0_isolated_cluster(int32_t nc, const double* eps_K, const doubl
  * build its N matrices from scratch.  cuda_stream: a cudaStream_t or NULL. */
 DCA_API int dca_walker_create(const dca_walker_params* params, void* cuda_stream, dca_walker** out);
 
-/* Run n_sweeps more sweeps on every walker.  A warm-up sweep is max(k, 1)
+/* Run n_sweeps more sweeps on every walker (DCA_SCHEDULE_LOCKSTEP), or
+ * n_sweeps * n_walkers more sweeps over all walkers together
+ * (DCA_SCHEDULE_POOLED).  A warm-up sweep is max(k, 1)
  * proposals (k at its start); after warm-up the sweep length is frozen to the
  * rounded mean of those k (max(k,1) when warmup_sweeps = 0).  Every sweep at
  * or past warm-up ends with one measurement.  The submatrix updates run as a
  * device-side loop (a CUDA graph with a conditional WHILE node, captured on
- * the first call) until every walker is done, so the host launches one graph
+ * the first call) until the sweeps are done, so the host launches one graph
  * and reads back one status record per call; with kernel timing on
  * (dca_walker_set_timing) the host drives the same kernels instead.
  * Returns DCA_ERR_TIMEOUT if the loop hits its iteration bound. */

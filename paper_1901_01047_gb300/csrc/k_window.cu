@@ -42,10 +42,11 @@ __global__ void __launch_bounds__(128) k_begin(Config cfg) {
   __shared__ unsigned long long s_min;
   if (threadIdx.x == 0) s_min = ~0ull;
   __syncthreads();
-  for (int i = threadIdx.x; i < cfg.n_walkers; i += blockDim.x) {
-    const WalkerDev& o = cfg.W[i];
-    if (o.status == ST_OK && o.sweeps_done < o.sweeps_target) atomicMin(&s_min, (unsigned long long)o.sweeps_done);
-  }
+  if (!cfg.pooled)
+    for (int i = threadIdx.x; i < cfg.n_walkers; i += blockDim.x) {
+      const WalkerDev& o = cfg.W[i];
+      if (o.status == ST_OK && o.sweeps_done < o.sweeps_target) atomicMin(&s_min, (unsigned long long)o.sweeps_done);
+    }
   __syncthreads();
   if (threadIdx.x == 0) {
     w.n_acc = 0;
@@ -56,8 +57,9 @@ __global__ void __launch_bounds__(128) k_begin(Config cfg) {
     w.n_cand = 0;
     w.measure_pending = 0;
     w.recompute_pending = 0;
-    int act = (w.status == ST_OK && w.sweeps_done < w.sweeps_target &&
-               (unsigned long long)w.sweeps_done == s_min) ? 1 : 0;
+    int act = cfg.pooled ? ((w.status == ST_OK && cfg.pool->go) ? 1 : 0)
+                         : ((w.status == ST_OK && w.sweeps_done < w.sweeps_target &&
+                             (unsigned long long)w.sweeps_done == s_min) ? 1 : 0);
     if (act) {
       w.first_window = w.sweep_pos == 0 ? 1 : 0;
       if (w.sweep_pos == 0) {
@@ -1144,7 +1146,51 @@ __global__ void __launch_bounds__(256) k_compact_end(Config cfg) {
   }
 }
 
+// Pooled schedule (one block over all walkers): the summed sweep count and
+// whether the target is still ahead; returns the go flag to every thread.
+__device__ int pool_refresh(const Config& cfg) {
+  __shared__ unsigned long long s_sum;
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    s_sum = 0ull;
+    s_ok = 0;
+  }
+  __syncthreads();
+  unsigned long long sum = 0ull;
+  int ok = 0;
+  for (int i = threadIdx.x; i < cfg.n_walkers; i += blockDim.x) {
+    const WalkerDev& w = cfg.W[i];
+    sum += (unsigned long long)w.sweeps_done;
+    ok |= w.status == ST_OK ? 1 : 0;
+  }
+  atomicAdd(&s_sum, sum);
+  if (ok) atomicOr(&s_ok, 1);
+  __syncthreads();
+  const int go = (s_ok && (int64_t)s_sum < cfg.pool->target) ? 1 : 0;
+  if (threadIdx.x == 0) {
+    cfg.pool->sum = (int64_t)s_sum;
+    cfg.pool->go = go;
+  }
+  return go;
+}
+
+__global__ void k_pool_target(Config cfg, int64_t n_sweeps) {
+  if (threadIdx.x == 0) cfg.pool->target = INT64_MAX;
+  __syncthreads();
+  pool_refresh(cfg);  // the current sum
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cfg.pool->target = cfg.pool->sum + n_sweeps * (int64_t)cfg.n_walkers;
+    cfg.pool->go = (cfg.pool->go && n_sweeps > 0) ? 1 : 0;
+  }
+}
+
 __global__ void k_count_active(Config cfg) {
+  if (cfg.pooled) {
+    const int go = pool_refresh(cfg);
+    if (threadIdx.x == 0) *cfg.active_count = go;
+    return;
+  }
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
@@ -1162,7 +1208,8 @@ __global__ void k_add_target(Config cfg, int64_t n_sweeps) {
 }
 
 // Loop control of the device-side window loop (body of a conditional WHILE
-// graph node): continue while any walker still has sweeps to do, and stop
+// graph node): continue while any walker still has sweeps to do (lockstep)
+// or the pooled sweep target is still ahead (pooled), and stop
 // with a timeout flag after max_iters windows (every window advances each
 // active walker by at least one proposal, so the host's bound is never
 // reached unless something is wrong).
@@ -1170,9 +1217,14 @@ __global__ void k_loop_control(Config cfg, cudaGraphConditionalHandle handle, Lo
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < cfg.n_walkers; i += blockDim.x) {
-    const WalkerDev& w = cfg.W[i];
-    if (w.status == ST_OK && w.sweeps_done < w.sweeps_target) atomicAdd(&s_cnt, 1);
+  if (cfg.pooled) {
+    const int go = pool_refresh(cfg);
+    if (threadIdx.x == 0) s_cnt = go;
+  } else {
+    for (int i = threadIdx.x; i < cfg.n_walkers; i += blockDim.x) {
+      const WalkerDev& w = cfg.W[i];
+      if (w.status == ST_OK && w.sweeps_done < w.sweeps_target) atomicAdd(&s_cnt, 1);
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1275,7 +1327,8 @@ int launch_window_group(int group, const Config& cfg, int max_cap, cudaStream_t 
 void launch_count_active(const Config& cfg, cudaStream_t st) { k_count_active<<<1, 256, 0, st>>>(cfg); }
 
 void launch_add_target(const Config& cfg, int64_t n_sweeps, cudaStream_t st) {
-  k_add_target<<<(cfg.n_walkers + 127) / 128, 128, 0, st>>>(cfg, n_sweeps);
+  if (cfg.pooled) k_pool_target<<<1, 256, 0, st>>>(cfg, n_sweeps);
+  else k_add_target<<<(cfg.n_walkers + 127) / 128, 128, 0, st>>>(cfg, n_sweeps);
 }
 
 void launch_loop_control(const Config& cfg, cudaGraphConditionalHandle handle, LoopState* ls, cudaStream_t st) {

@@ -148,6 +148,16 @@ struct LoopState {
   int32_t pad;
 };
 
+// Pooled schedule: the walkers together run until their summed sweep count
+// reaches `target`; `go` (recomputed before every window) says whether it has
+// not yet.
+struct PoolState {
+  int64_t target;
+  int64_t sum;
+  int32_t go;
+  int32_t pad;
+};
+
 // TMA tensor maps per walker and spin: update operands A and B, N of parity 0
 // and 1 (128-row boxes), the candidate tables V and U of the tensor-core
 // extension, N of parity 0 and 1 in 32-row boxes (MN-major operand).
@@ -181,6 +191,8 @@ struct Config {
   const TmapDev* tmaps;      // [n_walkers][2 spins][TMAPS_PER_SPIN]
   int32_t ext_tc;            // mixed path: candidate products G_ext and X on tcgen05
   int32_t* gj_next;          // [1] next matrix of the Gauss-Jordan work queue (reset by k_build_A)
+  int32_t pooled;            // pooled schedule (else lockstep sweeps)
+  PoolState* pool;           // [1] target and go flag of the pooled schedule (all walkers)
 };
 
 }  // namespace dca

@@ -70,6 +70,7 @@ struct dca_walker {
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;
   dca::LoopState* d_loop = nullptr;
+  dca::PoolState* d_pool = nullptr;  // pooled schedule: sweep target and go flag
   int kernels_per_window = 0;
 
   ~dca_walker() {
@@ -238,6 +239,10 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     h->err = "update_kernel must be one of DCA_UPD_*";
     return bail(DCA_ERR_ARG);
   }
+  if (p.schedule < DCA_SCHEDULE_LOCKSTEP || p.schedule > DCA_SCHEDULE_POOLED) {
+    h->err = "schedule must be one of DCA_SCHEDULE_*";
+    return bail(DCA_ERR_ARG);
+  }
   // The tensor-core operands exist on every mixed-precision walker, so the
   // update kernel can be switched by dca_walker_set_tuning.
   const bool use_tc = p.precision == DCA_PREC_MIXED && p.update_kernel != DCA_UPD_CUDA_CORE;
@@ -350,7 +355,9 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->d_W = (WalkerDev*)h->dalloc(sizeof(WalkerDev) * h->W);
   h->d_active = (int*)h->dalloc(sizeof(int) * 8);
   h->d_sgn = (int*)h->dalloc(sizeof(int) * 2 * h->W);
-  if (!h->d_W || !h->d_active || !h->d_sgn || cudaMallocHost(&h->h_active, sizeof(int) * 4) != cudaSuccess) {
+  h->d_pool = (dca::PoolState*)h->dalloc(sizeof(dca::PoolState));
+  if (!h->d_W || !h->d_active || !h->d_sgn || !h->d_pool ||
+      cudaMallocHost(&h->h_active, sizeof(int) * 4) != cudaSuccess) {
     h->err = "device allocation of walker records";
     return bail(DCA_ERR_OOM);
   }
@@ -374,6 +381,8 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.upd_kernel = use_tc ? dca::UPD_TCGEN05 : dca::UPD_CUDA_CORE;
   h->cfg.ext_tc = use_tc ? 1 : 0;  // the tcgen05 path covers the G_ext product of the extension too
   h->cfg.tmaps = h->d_tmaps;
+  h->cfg.pooled = p.schedule == DCA_SCHEDULE_POOLED ? 1 : 0;
+  h->cfg.pool = h->d_pool;
 
   if (dca::setup_window_kernels() != cudaSuccess) {
     h->err = "kernel attribute setup failed";

@@ -118,6 +118,7 @@ class Workload:
     recompute_every: int = 64
     recompute_sweeps: int = 0
     autotune: bool = False  # bench: choose k_s and the update kernel by the autotuner
+    schedule: str = "lockstep"  # "pooled": the walkers share the sweep budget (all active every window)
     precision: str = "fp64"
     # batched workloads: per-walker problems drawn from these ranges (seeded)
     nc_choices: Tuple[int, ...] = ()
@@ -163,7 +164,7 @@ WORKLOADS = {
     "batched256": Workload(name="batched256", nc=16, t=1.0, tp=0.0, U=5.5, beta=15.0, mu=2.75, K=1.0,
                            n_tau=2048, k_sub=64, walkers=256, warmup_sweeps=40, n_tau_meas=128,
                            recompute_every=0, recompute_sweeps=8, precision="mixed", nc_choices=(8, 16),
-                           autotune=True,
+                           autotune=True, schedule="pooled",
                            beta_range=(5.0, 25.0), U_range=(4.0, 7.0)),
     # 36-site square cluster, U = 7, beta = 30, density 0.95, 32 walkers, G on 2048 tau points
     "betts36": Workload(name="betts36", nc=36, t=1.0, tp=0.0, U=7.0, beta=30.0, mu=3.4878678207599574, K=1.0,

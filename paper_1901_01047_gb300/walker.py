@@ -24,6 +24,9 @@ EXPORTS = [
     "dca_walker_get_timing", "dca_walker_set_tuning", "dca_fresh_N", "dca_fresh_N_noalloc",
 ]
 UPDATE_KERNELS = {"auto": 0, "cuda_core": 1, "tcgen05": 2}
+# lockstep: every walker runs n more sweeps per sweep(n); pooled: the walkers
+# together run n * n_walkers more sweeps, all of them in every window
+SCHEDULES = {"lockstep": 0, "pooled": 1}
 GROUPS = ["propose", "extend", "metropolis", "update", "measure", "recompute", "update_pre", "update_post",
           "recompute_pre", "recompute_post"]
 
@@ -59,6 +62,7 @@ class Params(C.Structure):
         ("update_kernel", C.c_int32),
         ("recompute_sweeps", C.c_int32),
         ("recompute_method", C.c_int32),
+        ("schedule", C.c_int32),
     ]
 
 
@@ -203,7 +207,7 @@ class Walkers:
     def __init__(self, problems, n_walkers=1, walker_problem=None, k_sub=32, recompute_every=64,
                  warmup_sweeps=20, n_tau_meas=64, precision="fp64", init_config_size=10, capacity=0,
                  seed=0, tie_eps=1e-10, log_capacity=0, update_kernel="auto", recompute_sweeps=0,
-                 recompute_method="auto", stream=None):
+                 recompute_method="auto", schedule="lockstep", stream=None):
         L = load()
         self._keep = []
         probs = (Problem * len(problems))()
@@ -244,6 +248,7 @@ class Walkers:
         p.log_capacity = int(log_capacity)
         p.recompute_sweeps = int(recompute_sweeps)
         p.recompute_method = {"auto": 0, "gj": 1}[recompute_method]
+        p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
         p.update_kernel = UPDATE_KERNELS[update_kernel] if isinstance(update_kernel, str) else int(update_kernel)
         self.n_walkers = int(n_walkers)
         self.n_tau_meas = int(n_tau_meas)

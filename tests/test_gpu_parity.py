@@ -180,3 +180,43 @@ def test_retuning_k_sub_between_sweeps_keeps_the_chain():
             ref = os_["N"][sp]
             assert np.abs(gs["N"][sp] - ref).max() <= TOL * np.abs(ref).max()
     gw.close()
+
+
+def test_pooled_schedule_keeps_every_chain():
+    # Pooled schedule: the walkers (beta = 3 and 8) share a budget of 6 sweeps
+    # each and all take part in every window, so they complete different
+    # numbers of sweeps.  Each chain is still its own Markov chain: its
+    # decisions and its accumulated sign * G equal those of its oracle run for
+    # the sweeps it completed.
+    nc, U, mu, n_tau, ntm, warm, seed = 4, 4.0, 0.9450480104035819, 2048, 8, 3, 4
+    c = None
+    probs, setups = [], []
+    for beta in (3.0, 8.0):
+        c, eps, kr, G0 = problem(nc, 1.0, 0.0, U, beta, mu, n_tau)
+        probs.append(dict(nc=nc, site_sub=c.site_sub, U=U, beta=beta, K=1.0, G0=G0))
+        setups.append((beta, G0))
+    W = 4
+    wp = np.arange(W, dtype=np.int32) % 2
+    gw = _walkers(problems=probs, n_walkers=W, walker_problem=wp, k_sub=16, recompute_every=8,
+                  warmup_sweeps=warm, n_tau_meas=ntm, seed=seed, log_capacity=1 << 22, schedule="pooled")
+    gw.sweep(6)
+    Gg, ssg, nmg = gw.measure_G()
+    st = gw.stats()
+    sweeps = [s["sweeps"] for s in st]
+    assert sum(sweeps) >= 6 * W
+    for wi in range(W):
+        beta, G0 = setups[wp[wi]]
+        log = gw.decision_log(wi)
+        ow = ctaux.OracleWalker(nc, c.site_sub, U, beta, 1.0, G0, warmup_sweeps=warm, n_tau_meas=ntm, seed=seed,
+                                walker_id=wi)
+        ow.enable_log(1 << 22)
+        ow.set_hints(log)
+        ow.sweep(sweeps[wi])
+        olog = ow.log()
+        assert log.size >= olog.size
+        assert np.array_equal(log[:olog.size] & 1, olog & 1)
+        Go, sso, nmo = ow.G()
+        assert nmg[wi] == nmo and ssg[wi] == sso
+        assert np.abs(Gg[wi] - Go).max() <= TOL * max(np.abs(Go).max(), 1e-300)
+        assert st[wi]["status"] == 0
+    gw.close()
