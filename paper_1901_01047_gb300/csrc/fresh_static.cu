@@ -105,7 +105,7 @@ extern "C" DCA_API int dca_fresh_N_noalloc(const dca_problem* problem, int32_t n
   }
   unsigned char* base = g_addr[dev];
 
-  dca::ProblemDev d;
+  dca::ProblemDev d{};
   std::vector<int32_t> add;
   std::vector<double> g0;
   dca::prepare_problem(pr, d, add, g0);

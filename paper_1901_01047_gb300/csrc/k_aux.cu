@@ -238,17 +238,21 @@ __global__ void __launch_bounds__(256) k_meas_gr(Config cfg) {
 
 // bvec[sp][r'][i] = (e^{V_i} - 1) sum_j N[i][j] gR[sp][r'][j]; one warp per (i, r').
 // b[r'][i] = (e^{V_i} - 1) sum_j N[i][j] gR[r'][j] as a tiled product:
-// one item = 8 rows of N (one warp each); lanes own reference sites r' and
-// r' + 32; chunks of 32 columns of N and gR are staged in shared memory.
+// a warp owns R rows of N (R = 4 for nc <= 8, 2 for nc <= 16, else 1), each
+// row on 32 / R lanes that own the reference sites r' (and r' + 32 for
+// nc > 32); one item = the 8 R rows of the block's warps; chunks of 32 columns
+// of N and gR are staged in shared memory.
+__device__ __forceinline__ int meas_b_rows(int nc) { return nc <= 8 ? 4 : (nc <= 16 ? 2 : 1); }
+
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_meas_b(Config cfg) {
-  __shared__ A sN[8][33];
+  __shared__ A sN[32][33];
   __shared__ A sG[64][33];
   for_each_item(
       2 * cfg.n_walkers,
       [&](int s) -> long long {
         const WalkerDev& w = cfg.W[s >> 1];
-        return wants_measure(w) ? blocks_of(w.n, 8) : 0;
+        return wants_measure(w) ? blocks_of(w.n, 8 * meas_b_rows(cfg.P[w.problem].nc)) : 0;
       },
       [&](int s, int item) {
         const WalkerDev& w = cfg.W[s >> 1];
@@ -257,18 +261,22 @@ __global__ void __launch_bounds__(256) k_meas_b(Config cfg) {
         const int n = w.n, par = w.parity, nc = pb.nc, ld = w.cap;
         const T* N = (const T*)w.N[par][sp];
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const int i = item * 8 + warp;
+        const int R = meas_b_rows(nc), lw = 32 / R;
+        const int sub = lane / lw, rp = lane - sub * lw;  // row of the warp, reference site
+        const int i0 = item * 8 * R + warp * R;           // first row of the warp
+        const int i = i0 + sub;
         A acc0 = (A)0, acc1 = (A)0;
-        const bool two = nc > 32;  // uniform: the second reference-site half exists
+        const bool two = nc > 32;  // uniform: the second reference-site half exists (R = 1)
         for (int j0 = 0; j0 < n; j0 += 32) {
           __syncthreads();
           {
             const int j = j0 + lane;
-            sN[warp][lane] = (i < n && j < n) ? ldA<A>(N, (size_t)i * ld + j) : (A)0;
+            for (int r = 0; r < R; ++r)
+              sN[warp * R + r][lane] = (i0 + r < n && j < n) ? ldA<A>(N, (size_t)(i0 + r) * ld + j) : (A)0;
           }
-          for (int e = threadIdx.x; e < (two ? 64 : 32) * 32; e += 256) {
-            const int rp = e >> 5, jl = e & 31, j = j0 + jl;
-            sG[rp][jl] = (rp < nc && j < n) ? reinterpret_cast<const A*>(w.gR)[((size_t)sp * nc + rp) * ld + j] : (A)0;
+          for (int e = threadIdx.x; e < (two ? 64 : lw) * 32; e += 256) {
+            const int q = e >> 5, jl = e & 31, j = j0 + jl;
+            sG[q][jl] = (q < nc && j < n) ? reinterpret_cast<const A*>(w.gR)[((size_t)sp * nc + q) * ld + j] : (A)0;
           }
           __syncthreads();
           if (two) {
@@ -279,15 +287,16 @@ __global__ void __launch_bounds__(256) k_meas_b(Config cfg) {
               acc1 += nij * sG[lane + 32][jl];
             }
           } else {
+            const int row = warp * R + sub;
 #pragma unroll 8
-            for (int jl = 0; jl < 32; ++jl) acc0 += sN[warp][jl] * sG[lane][jl];
+            for (int jl = 0; jl < 32; ++jl) acc0 += sN[row][jl] * sG[rp][jl];
           }
         }
         if (i < n) {
           const A f = (A)(expV(pb, sp, w.vs[par][i]) - 1.0);
           A* bv = reinterpret_cast<A*>(w.bvec);
-          if (lane < nc) bv[((size_t)sp * nc + lane) * ld + i] = f * acc0;
-          if (lane + 32 < nc) bv[((size_t)sp * nc + lane + 32) * ld + i] = f * acc1;
+          if (rp < nc) bv[((size_t)sp * nc + rp) * ld + i] = f * acc0;
+          if (two && rp + 32 < nc) bv[((size_t)sp * nc + rp + 32) * ld + i] = f * acc1;
         }
       });
 }
@@ -334,6 +343,9 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
   __shared__ A Bs[MK][MR + 1];
   __shared__ GridTime s_ga[MT], s_gi[MK];
   __shared__ int s_row[MK];  // table row of g0(x - r_i, .), -1 for a dead vertex
+  __shared__ int s_ph[MK], s_mb[MK];  // phase-table path: phase p_i and m offset of vertex i
+  __shared__ float s_fw[MK];          // and its interpolation weight
+  const int q = kGrid ? pb.meas_q : 0;
   const int tid = threadIdx.x;
   const int ta = tid & (MT - 1), tr = tid >> 6;  // 4 groups of reference sites
   A acc[MR / 4];
@@ -352,23 +364,60 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
       const int i = i0 + tid;
       const bool live = i < n && vs[i] != 0;
       s_row[tid] = live ? __ldg(pb.site_sub + x * nc + vsite[i]) : -1;
-      if (kGrid && live) s_gi[tid] = grid_time(vtau[i], pb.tau_scale);
-    }
-    __syncthreads();
-    for (int e = tid; e < MT * MK; e += 256) {
-      const int al = e / MK, il = e - al * MK;
-      const int a = a0 + al, d = s_row[il];
-      A v = (A)0;
-      if (a < ntm && d >= 0) {
-        const double* row = row_base + (size_t)d * np1;
-        if (kGrid) {
-          v = (A)g0_interp_grid(g0f_row(pb, sp, d), pb.n_tau, s_ga[al], s_gi[il]);
-        } else {
-          const double ta_ = ((double)a + 0.5) * pb.beta / (double)ntm;
-          v = (A)g0_interp(row, pb.n_tau, pb.beta, pb.tau_scale, ta_ - vtau[i0 + il]);
+      if (kGrid && live) {
+        const GridTime gi = grid_time(vtau[i], pb.tau_scale);
+        s_gi[tid] = gi;
+        if (q > 0) {
+          // grid offset of tau_a - tau_i: l = q a + c, c = q/2 - gi.i - (gi.f > 0), weight 1 - gi.f
+          const int c = q / 2 - gi.i - (gi.f > 0.0f ? 1 : 0);
+          const int p = ((c % q) + q) % q;
+          s_ph[tid] = p;
+          s_mb[tid] = (c - p) / q;
+          s_fw[tid] = gi.f > 0.0f ? 1.0f - gi.f : 0.0f;
         }
       }
-      As[al][il] = v;
+    }
+    __syncthreads();
+    if (q > 0) {
+      // phase table: consecutive threads take consecutive tau points of one
+      // vertex, i.e. consecutive entries of one phase row
+      const size_t mrow = (size_t)ntm + 1;
+      const float* gm = pb.g0m + (size_t)sp * q * nc * mrow;
+      for (int e = tid; e < MT * MK; e += 256) {
+        const int il = e / MT, al = e - il * MT;
+        const int a = a0 + al, d = s_row[il];
+        A v = (A)0;
+        if (a < ntm && d >= 0) {
+          const int p = s_ph[il];
+          int m = a + s_mb[il];
+          float sgn = 1.0f;
+          if (m < 0) {  // tau_a - tau_i < 0: antiperiodic continuation
+            m += ntm;
+            sgn = -1.0f;
+          }
+          const float lo = __ldg(gm + ((size_t)p * nc + d) * mrow + m);
+          const float hi = p + 1 < q ? __ldg(gm + ((size_t)(p + 1) * nc + d) * mrow + m)
+                                     : __ldg(gm + (size_t)d * mrow + m + 1);
+          v = (A)(sgn * (lo + s_fw[il] * (hi - lo)));
+        }
+        As[al][il] = v;
+      }
+    } else {
+      for (int e = tid; e < MT * MK; e += 256) {
+        const int al = e / MK, il = e - al * MK;
+        const int a = a0 + al, d = s_row[il];
+        A v = (A)0;
+        if (a < ntm && d >= 0) {
+          const double* row = row_base + (size_t)d * np1;
+          if (kGrid) {
+            v = (A)g0_interp_grid(g0f_row(pb, sp, d), pb.n_tau, s_ga[al], s_gi[il]);
+          } else {
+            const double ta_ = ((double)a + 0.5) * pb.beta / (double)ntm;
+            v = (A)g0_interp(row, pb.n_tau, pb.beta, pb.tau_scale, ta_ - vtau[i0 + il]);
+          }
+        }
+        As[al][il] = v;
+      }
     }
     for (int e = tid; e < MK * MR; e += 256) {
       const int il = e / MR, rp = e - il * MR;
@@ -533,23 +582,48 @@ void launch_negate(const double* src, double* dst, float* dstf, size_t n, cudaSt
   k_negate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, dstf, n);
 }
 
+// g0m[sp][p][d][m] = g0f[sp][d][q m + p] for q m + p <= n_tau, else 0.
+__global__ void k_meas_table(const float* g0f, float* g0m, int nc, int n_tau, int q, int ntm) {
+  const size_t total = (size_t)2 * q * nc * (ntm + 1);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e % (ntm + 1));
+    size_t r = e / (ntm + 1);
+    const int d = (int)(r % nc);
+    r /= nc;
+    const int p = (int)(r % q), sp = (int)(r / q);
+    const int l = q * m + p;
+    g0m[e] = l <= n_tau ? g0f[((size_t)sp * nc + d) * (n_tau + 1) + l] : 0.0f;
+  }
+}
+
+void launch_meas_table(const ProblemDev& pd, int n_tau_meas, cudaStream_t st) {
+  const size_t total = (size_t)2 * pd.meas_q * pd.nc * (n_tau_meas + 1);
+  const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 4096);
+  k_meas_table<<<blocks, 256, 0, st>>>(pd.g0f, const_cast<float*>(pd.g0m), pd.nc, pd.n_tau, pd.meas_q, n_tau_meas);
+}
+
 int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) {
   const int W = cfg.n_walkers;
   const long long S = 2LL * W;
-  k_meas_gr<<<grid_for(S * blocks_of((long long)max_nc * max_cap, 256)), 256, 0, st>>>(cfg);
-  const int gb = grid_for(S * blocks_of(max_cap, 8));
-  if (cfg.prec == PREC_MIXED) k_meas_b<float, float><<<gb, 256, 0, st>>>(cfg);
-  else k_meas_b<double, double><<<gb, 256, 0, st>>>(cfg);
-  const int gg = grid_for(S * max_nc * blocks_of(cfg.n_tau_meas, MT));
+  k_meas_gr<<<persist_grid((const void*)k_meas_gr, S * blocks_of((long long)max_nc * max_cap, 256), 256), 256, 0,
+              st>>>(cfg);
+  const long long ib = S * blocks_of(max_cap, 8);
+  if (cfg.prec == PREC_MIXED)
+    k_meas_b<float, float><<<persist_grid((const void*)k_meas_b<float, float>, ib, 256), 256, 0, st>>>(cfg);
+  else
+    k_meas_b<double, double><<<persist_grid((const void*)k_meas_b<double, double>, ib, 256), 256, 0, st>>>(cfg);
+  const long long ig = S * max_nc * blocks_of(cfg.n_tau_meas, MT);
+#define DCA_MEAS_GEMM(A, MR) k_meas_gemm<A, MR><<<persist_grid((const void*)k_meas_gemm<A, MR>, ig, 256), 256, 0, st>>>(cfg)
   if (cfg.prec == PREC_MIXED) {
-    k_meas_gemm<float, 16><<<gg, 256, 0, st>>>(cfg);
-    if (max_nc > 16) k_meas_gemm<float, 32><<<gg, 256, 0, st>>>(cfg);
-    if (max_nc > 32) k_meas_gemm<float, 64><<<gg, 256, 0, st>>>(cfg);
+    DCA_MEAS_GEMM(float, 16);
+    if (max_nc > 16) DCA_MEAS_GEMM(float, 32);
+    if (max_nc > 32) DCA_MEAS_GEMM(float, 64);
   } else {
-    k_meas_gemm<double, 16><<<gg, 256, 0, st>>>(cfg);
-    if (max_nc > 16) k_meas_gemm<double, 32><<<gg, 256, 0, st>>>(cfg);
-    if (max_nc > 32) k_meas_gemm<double, 64><<<gg, 256, 0, st>>>(cfg);
+    DCA_MEAS_GEMM(double, 16);
+    if (max_nc > 16) DCA_MEAS_GEMM(double, 32);
+    if (max_nc > 32) DCA_MEAS_GEMM(double, 64);
   }
+#undef DCA_MEAS_GEMM
   k_meas_acc<<<grid_for((long long)W * blocks_of(2LL * max_nc * cfg.n_tau_meas, 256)), 256, 0, st>>>(cfg);
   k_meas_finish<<<(W + 127) / 128, 128, 0, st>>>(cfg);
   (void)max_cap;

@@ -22,6 +22,9 @@
 #include <cstdint>
 #include <cstdio>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "device_util.cuh"
 #include "kernels.h"
 #include "state.h"
@@ -1250,6 +1253,28 @@ __global__ void k_loop_reset(LoopState* ls, int64_t max_iters) {
 // Persistent grids: a few blocks per SM walk the flattened work of all walkers.
 constexpr int PERSIST_BLOCKS = 4 * 152;
 
+int persist_grid(const void* fn, long long items, int block, size_t smem) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;  // resident blocks on the device
+  int total = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(fn);
+    if (it != cache.end()) {
+      total = it->second;
+    } else {
+      int dev = 0, sms = 0, per_sm = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem) != cudaSuccess)
+        per_sm = 0;
+      total = (per_sm > 0 && sms > 0) ? per_sm * sms : PERSIST_BLOCKS;
+      cache.emplace(fn, total);
+    }
+  }
+  return (int)(items < 1 ? 1 : (items < total ? items : total));
+}
+
 // Grid of a persistent kernel: at most PERSIST_BLOCKS, at most the largest
 // possible number of work items.
 static int grid_for(long long items) {
@@ -1267,10 +1292,10 @@ static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_
       k_begin<<<W, 128, 0, st>>>(cfg);
       return 1;
     case GROUP_EXTEND:
-      k_cand_zero<<<grid_for(S * kc), 256, 0, st>>>(cfg);
+      k_cand_zero<<<persist_grid((const void*)k_cand_zero, S * kc, 256), 256, 0, st>>>(cfg);
       if (cfg.prec == PREC_MIXED) {
         int k = launch_ext_mixed(cfg, max_cap, st);
-        k_cand_cc<A><<<grid_for(S * 16), 256, 0, st>>>(cfg);
+        k_cand_cc<A><<<persist_grid((const void*)k_cand_cc<A>, S * 16, 256), 256, 0, st>>>(cfg);
         return 2 + k;
       }
       k_cand_ext<T, A><<<grid_for(S * t64 * t64), 256, ext_smem_bytes<A>(), st>>>(cfg);
@@ -1282,8 +1307,8 @@ static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_
       return 1;
     }
     case GROUP_UPDATE_PRE:
-      k_upd_lrow<T><<<grid_for(S * kc), 256, 0, st>>>(cfg);
-      k_upd_lp_rr<T, A><<<grid_for(2 * S * kc), 256, 0, st>>>(cfg);
+      k_upd_lrow<T><<<persist_grid((const void*)k_upd_lrow<T>, S * kc, 256), 256, 0, st>>>(cfg);
+      k_upd_lp_rr<T, A><<<persist_grid((const void*)k_upd_lp_rr<T, A>, 2 * S * kc, 256), 256, 0, st>>>(cfg);
       if (cfg.prec == PREC_MIXED && cfg.upd_kernel == UPD_TCGEN05) {
         launch_upd_ops(cfg, st);
         return 3;
@@ -1296,7 +1321,7 @@ static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_
         k_upd_apply<T, A><<<grid_for(S * t32 * t32), 256, 0, st>>>(cfg);
       return 1;
     case GROUP_UPDATE_POST:
-      k_upd_border<T, A><<<grid_for(2 * S * kc), 256, 0, st>>>(cfg);
+      k_upd_border<T, A><<<persist_grid((const void*)k_upd_border<T, A>, 2 * S * kc, 256), 256, 0, st>>>(cfg);
       k_window_end<<<W, 256, 0, st>>>(cfg);
       k_compact_N<T><<<grid_for(S * t32 * t32), 256, 0, st>>>(cfg);
       k_compact_end<<<W, 256, 0, st>>>(cfg);

@@ -52,6 +52,11 @@ void launch_refine_adopt(const Config& cfg, int max_cap, cudaStream_t st);
 // part: GROUP_RECOMPUTE_PRE, GROUP_RECOMPUTE or GROUP_RECOMPUTE_POST.
 int launch_recompute(int part, const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st);
 int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
+
+// Grid of a persistent item kernel (for_each_item): as many blocks as the SMs
+// hold at once (occupancy of `fn` at `block` threads and `smem` dynamic bytes,
+// cached per kernel), at most `items`.
+int persist_grid(const void* fn, long long items, int block, size_t smem = 0);
 // Candidate extension of the mixed path: the two streaming passes over N.
 int launch_ext_mixed(const Config& cfg, int max_cap, cudaStream_t st);
 // Tensor-core N update (mixed precision): kernel attributes, tile width for
@@ -67,6 +72,8 @@ void launch_ext_x_tc(const Config& cfg, cudaStream_t st);
 void launch_upd_ops(const Config& cfg, cudaStream_t st);
 void launch_upd_tc(const Config& cfg, cudaStream_t st);
 void launch_negate(const double* src, double* dst, float* dstf, size_t n, cudaStream_t st);
+// Phase table of the measurement grid (ProblemDev::g0m) from the FP32 table g0f.
+void launch_meas_table(const ProblemDev& pd, int n_tau_meas, cudaStream_t st);
 void launch_g0_isolated(int nc, const double* d_eps, const double* d_kr, double mu_eff, double beta, int n_tau,
                         double* d_out, cudaStream_t st);
 

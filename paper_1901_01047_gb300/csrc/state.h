@@ -54,6 +54,13 @@ struct ProblemDev {
   const int32_t* site_add;            // [nc*nc]: site_add[y*nc + d] = x with site_sub[x*nc + y] = d
   const double* g0;                   // [2][nc][n_tau+1], g0 = -G0
   const float* g0f;                   // FP32 copy of g0 (mixed-precision interpolation)
+  // Measurement grid tau_a = (a + 1/2) beta / n_tau_meas on the g0 grid when
+  // n_tau = q n_tau_meas with q even (mixed path; else meas_q = 0): the grid
+  // offset of tau_a - tau_i is q a + c_i, so each vertex reads one phase
+  // p = c_i mod q of the table.  g0m[sp][p][d][m] = g0f[sp][d][q m + p],
+  // m = 0 .. n_tau_meas (0 past the table end).
+  const float* g0m;
+  int32_t meas_q;
 };
 
 struct Proposal {

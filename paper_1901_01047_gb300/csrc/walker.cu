@@ -212,6 +212,21 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     d.site_add = (const int32_t*)da;
     d.g0 = (const double*)dg;
     d.g0f = (const float*)dgf;
+    const int q = (p.n_tau_meas > 0 && d.n_tau % p.n_tau_meas == 0) ? d.n_tau / p.n_tau_meas : 0;
+    if (p.precision == DCA_PREC_MIXED && q >= 2 && q % 2 == 0) {
+      void* dgm = h->dalloc(sizeof(float) * 2 * (size_t)q * pr.nc * (p.n_tau_meas + 1));
+      if (!dgm) {
+        h->err = "device allocation of the measurement phase table";
+        return bail(DCA_ERR_OOM);
+      }
+      d.g0m = (const float*)dgm;
+      d.meas_q = q;
+      dca::launch_meas_table(d, p.n_tau_meas, h->stream);
+      if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        h->err = "measurement phase table";
+        return bail(DCA_ERR_CUDA);
+      }
+    }
     h->max_nc = std::max(h->max_nc, pr.nc);
   }
   h->h_P = hp;
@@ -693,6 +708,10 @@ extern "C" DCA_API int dca_walker_update_G0(dca_walker* h, int32_t problem, cons
   CK(cudaMemcpyAsync(h->g0_stage[problem], G0, sizeof(double) * tsz, cudaMemcpyHostToDevice, h->stream));
   dca::launch_negate(h->g0_stage[problem], const_cast<double*>(pd.g0), const_cast<float*>(pd.g0f), tsz, h->stream);
   h->total_launches += 1;
+  if (pd.meas_q > 0) {
+    dca::launch_meas_table(pd, h->ntm, h->stream);
+    h->total_launches += 1;
+  }
   CK(cudaGetLastError());
   return DCA_OK;
 }
@@ -875,7 +894,7 @@ extern "C" DCA_API int dca_fresh_N(const dca_problem* problem, int32_t n, const 
     return DCA_OK;
   }
   const dca_problem& pr = *problem;
-  ProblemDev d;
+  ProblemDev d{};
   std::vector<int32_t> add;
   std::vector<double> g0;
   dca::prepare_problem(pr, d, add, g0);
