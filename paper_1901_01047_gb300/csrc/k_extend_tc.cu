@@ -9,7 +9,7 @@
 // free during the extension); N tiles are split in shared memory.
 //
 // Work item = one 128-row block of one walker-spin N.  The CTA streams the
-// block's columns 32 at a time through a three-stage ring:
+// block's columns 32 at a time through a ring of four stages (three for CN = 128):
 //   warp 4 (TMA producer)   N box (128 rows x 32 columns) and the V boxes;
 //   warps 0-3 (converters)  split the N box in place into hi and a lo plane,
 //                           zero the columns >= n; at the end of the item they
@@ -30,14 +30,14 @@
 namespace dca {
 
 constexpr int XT_BM = 128;    // rows per item
-constexpr int XT_STAGES = 3;
 
 template <int CN>
 struct XtLayout {
   static constexpr int N_BOX = XT_BM * 128;     // 128 rows x 32 FP32 columns
   static constexpr int V_BOX = CN * 128;        // CN rows x 32 columns
   static constexpr int STAGE = 2 * N_BOX + 2 * V_BOX;  // N (hi), N lo, V hi, V lo
-  static constexpr int OFF_BAR = XT_STAGES * STAGE;
+  static constexpr int STAGES = CN <= 64 ? 4 : 3;      // ring depth: as many stages as fit
+  static constexpr int OFF_BAR = STAGES * STAGE;
   static constexpr int SMEM = OFF_BAR + 256 + 1024;
   static constexpr uint32_t TMEM_COLS = CN < 32 ? 32 : CN;
   static_assert(SMEM + sizeof(ItemPlan) <= 232448, "shared memory (dynamic + the static item plan)");
@@ -68,17 +68,19 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
   const uint32_t sb = (raw + 1023u) & ~1023u;
   uint8_t* gb = xt_raw + (sb - raw);
   const uint32_t bar = sb + L::OFF_BAR;
-  // barriers: full[3], conv[3], empty[3], dg_full, dg_empty, fin
+  // barriers: full[S], conv[S], empty[S], dg_full, dg_empty, fin (S = L::STAGES)
+  constexpr int S = L::STAGES;
   auto full = [&](int st) { return bar + 8 * st; };
-  auto conv = [&](int st) { return bar + 24 + 8 * st; };
-  auto empty = [&](int st) { return bar + 48 + 8 * st; };
-  const uint32_t dg_full = bar + 72, dg_empty = bar + 80, fin = bar + 88;
-  uint32_t* tmem_slot = (uint32_t*)(gb + L::OFF_BAR + 96);
-  volatile int* abort_flag = (volatile int*)(gb + L::OFF_BAR + 100);
+  auto conv = [&](int st) { return bar + 8 * (S + st); };
+  auto empty = [&](int st) { return bar + 8 * (2 * S + st); };
+  const uint32_t dg_full = bar + 8 * (3 * S), dg_empty = dg_full + 8, fin = dg_full + 16;
+  uint32_t* tmem_slot = (uint32_t*)(gb + L::OFF_BAR + 8 * (3 * S + 3));
+  volatile int* abort_flag = (volatile int*)(gb + L::OFF_BAR + 8 * (3 * S + 3) + 4);
+  static_assert(8 * (3 * S + 3) + 8 <= 256, "barrier area");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int st = 0; st < XT_STAGES; ++st) {
+    for (int st = 0; st < S; ++st) {
       tc::mbar_init(full(st), 1);
       tc::mbar_init(conv(st), 4);
       tc::mbar_init(empty(st), 1);
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
       XtIter it;
       it.start(cfg, plan);
       uint32_t g = 0;
-      uint32_t armed[XT_STAGES] = {0u, 0u, 0u};
+      uint32_t armed[S] = {};
       int set = 0, rb = 0;
       bool ok = true;
       while (ok && it.next(cfg, set, rb)) {
@@ -115,8 +117,8 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
         const void* mN = xt_map(cfg, wi, sp, 2 + w.parity);
         const void* mV = xt_map(cfg, wi, sp, 4);
         for (int j0 = 0; j0 < n; j0 += 32, ++g) {
-          const int st = (int)(g % XT_STAGES);
-          const uint32_t u = g / XT_STAGES;
+          const int st = (int)(g % S);
+          const uint32_t u = g / S;
           if (u > 0 && !tc::mbar_wait(empty(st), (u - 1) & 1u, abort_flag)) {
             ok = false;
             break;
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
       }
       if (!ok) {
         cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
-        for (int st = 0; st < XT_STAGES; ++st)
+        for (int st = 0; st < S; ++st)
           if (armed[st] > 0) tc::mbar_wait(full(st), (armed[st] - 1) & 1u, nullptr, 400000000LL);
       }
     }
@@ -153,8 +155,8 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
         tc::fence_after_sync();
         bool first = true;
         for (int j0 = 0; j0 < n; j0 += 32, ++g) {
-          const int st = (int)(g % XT_STAGES);
-          const uint32_t u = g / XT_STAGES;
+          const int st = (int)(g % S);
+          const uint32_t u = g / S;
           if (!tc::mbar_wait(conv(st), u & 1u, abort_flag)) {
             ok = false;
             break;
@@ -194,8 +196,8 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
       WalkerDev& w = cfg.W[set >> 1];
       const int sp = set & 1, n = w.n, nc_ = w.n_cand, ld = w.cap, i0 = rb * XT_BM;
       for (int j0 = 0; j0 < n; j0 += 32, ++g) {
-        const int st = (int)(g % XT_STAGES);
-        const uint32_t u = g / XT_STAGES;
+        const int st = (int)(g % S);
+        const uint32_t u = g / S;
         const bool mine = tc::mbar_wait(full(st), u & 1u, abort_flag);
         if (!__all_sync(0xffffffffu, mine)) {
           stop = true;
@@ -270,17 +272,23 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
 // transposed, split and swizzled from the four 32 x 32 boxes the TMA loads.
 // Accumulator: 128 lanes (candidates) x 128 columns.
 constexpr int XX2_BJ = 128;  // columns per item
-constexpr int XX2_STAGES = 2;
 
+// Stage: U hi | U lo (CN candidate rows each) | N boxes | N^T hi | N^T lo.
+// The MMA has M = 128: with CN = 64 its rows 64 .. 127 read the next planes
+// of the same stage (accumulator lanes that are never stored).
+template <int CN>
 struct Xx2Layout {
+  static constexpr int U_TILE = CN * 128;              // CN candidates x 32 rows
   static constexpr int N_BOX = 32 * 128;               // 32 rows x 32 columns (TMA)
   static constexpr int N_TILE = 4 * N_BOX;             // 32 rows x 128 columns
   static constexpr int T_TILE = 128 * 128;             // N^T: 128 columns x 32 rows, one plane
-  static constexpr int U_TILE = 128 * 128;             // 128 candidates x 32 rows
-  static constexpr int STAGE = N_TILE + 2 * T_TILE + 2 * U_TILE;
-  static constexpr int OFF_BAR = XX2_STAGES * STAGE;
+  static constexpr int OFF_U = 0, OFF_N = 2 * U_TILE, OFF_T = OFF_N + N_TILE;
+  static constexpr int STAGE = OFF_T + 2 * T_TILE;
+  static constexpr int STAGES = CN <= 64 ? 3 : 2;      // ring depth: as many stages as fit
+  static constexpr int OFF_BAR = STAGES * STAGE;
   static constexpr int SMEM = OFF_BAR + 256 + 1024;
   static constexpr uint32_t TMEM_COLS = XX2_BJ;
+  static_assert(2 * U_TILE + N_TILE >= 128 * 128, "the M = 128 rows of the lo plane stay inside the stage");
   static_assert(SMEM + sizeof(ItemPlan) <= 232448, "shared memory (dynamic + the static item plan)");
 };
 
@@ -297,23 +305,26 @@ struct Xx2Iter {
   }
 };
 
+template <int CN>
 __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
-  using L = Xx2Layout;
+  using L = Xx2Layout<CN>;
   extern __shared__ uint8_t xx_raw[];
   const uint32_t raw = tc::smem_u32(xx_raw);
   const uint32_t sb = (raw + 1023u) & ~1023u;
   uint8_t* gb = xx_raw + (sb - raw);
   const uint32_t bar = sb + L::OFF_BAR;
+  constexpr int S = L::STAGES;
   auto full = [&](int st) { return bar + 8 * st; };
-  auto conv = [&](int st) { return bar + 24 + 8 * st; };
-  auto empty = [&](int st) { return bar + 48 + 8 * st; };
-  const uint32_t dx_full = bar + 72, dx_empty = bar + 80, fin = bar + 88;
-  uint32_t* tmem_slot = (uint32_t*)(gb + L::OFF_BAR + 96);
-  volatile int* abort_flag = (volatile int*)(gb + L::OFF_BAR + 100);
+  auto conv = [&](int st) { return bar + 8 * (S + st); };
+  auto empty = [&](int st) { return bar + 8 * (2 * S + st); };
+  const uint32_t dx_full = bar + 8 * (3 * S), dx_empty = dx_full + 8, fin = dx_full + 16;
+  uint32_t* tmem_slot = (uint32_t*)(gb + L::OFF_BAR + 8 * (3 * S + 3));
+  volatile int* abort_flag = (volatile int*)(gb + L::OFF_BAR + 8 * (3 * S + 3) + 4);
+  static_assert(8 * (3 * S + 3) + 8 <= 256, "barrier area");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int st = 0; st < XX2_STAGES; ++st) {
+    for (int st = 0; st < S; ++st) {
       tc::mbar_init(full(st), 1);
       tc::mbar_init(conv(st), 4);
       tc::mbar_init(empty(st), 1);
@@ -341,7 +352,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
       Xx2Iter it;
       it.start(cfg, plan);
       uint32_t g = 0;
-      uint32_t armed[XX2_STAGES] = {0u, 0u};
+      uint32_t armed[S] = {};
       int set = 0, jb = 0;
       bool ok = true;
       while (ok && it.next(cfg, set, jb)) {
@@ -350,8 +361,8 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
         const void* mN = xt_map(cfg, wi, sp, 6 + w.parity);
         const void* mU = xt_map(cfg, wi, sp, 5);
         for (int i0 = 0; i0 < n; i0 += 32, ++g) {
-          const int st = (int)(g % XX2_STAGES);
-          const uint32_t u = g / XX2_STAGES;
+          const int st = (int)(g % S);
+          const uint32_t u = g / S;
           if (u > 0 && !tc::mbar_wait(empty(st), (u - 1) & 1u, abort_flag)) {
             ok = false;
             break;
@@ -359,14 +370,14 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
           const uint32_t s0 = sb + st * L::STAGE;
           tc::mbar_expect_tx(full(st), (uint32_t)(L::N_TILE + 2 * L::U_TILE));
           armed[st] = u + 1;
-          for (int b = 0; b < 4; ++b) tc::tma_load_2d(s0 + b * L::N_BOX, mN, j0 + 32 * b, i0, full(st));
-          tc::tma_load_2d(s0 + L::N_TILE + 2 * L::T_TILE, mU, i0, 0, full(st));
-          tc::tma_load_2d(s0 + L::N_TILE + 2 * L::T_TILE + L::U_TILE, mU, i0, KS_MAX, full(st));
+          for (int b = 0; b < 4; ++b) tc::tma_load_2d(s0 + L::OFF_N + b * L::N_BOX, mN, j0 + 32 * b, i0, full(st));
+          tc::tma_load_2d(s0 + L::OFF_U, mU, i0, 0, full(st));
+          tc::tma_load_2d(s0 + L::OFF_U + L::U_TILE, mU, i0, KS_MAX, full(st));
         }
       }
       if (!ok) {
         cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
-        for (int st = 0; st < XX2_STAGES; ++st)
+        for (int st = 0; st < S; ++st)
           if (armed[st] > 0) tc::mbar_wait(full(st), (armed[st] - 1) & 1u, nullptr, 400000000LL);
       }
     }
@@ -388,15 +399,15 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
         tc::fence_after_sync();
         bool first = true;
         for (int i0 = 0; i0 < n; i0 += 32, ++g) {
-          const int st = (int)(g % XX2_STAGES);
-          const uint32_t u = g / XX2_STAGES;
+          const int st = (int)(g % S);
+          const uint32_t u = g / S;
           if (!tc::mbar_wait(conv(st), u & 1u, abort_flag)) {
             ok = false;
             break;
           }
           tc::fence_after_sync();
           const uint32_t s0 = sb + st * L::STAGE;
-          const uint32_t tH = s0 + L::N_TILE, tL = tH + L::T_TILE, uH = tL + L::T_TILE, uL = uH + L::U_TILE;
+          const uint32_t tH = s0 + L::OFF_T, tL = tH + L::T_TILE, uH = s0 + L::OFF_U, uL = uH + L::U_TILE;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             // K step of 8 rows of N: 32 bytes inside the 128-byte swizzle rows of U and N^T
@@ -430,8 +441,8 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
       WalkerDev& w = cfg.W[set >> 1];
       const int sp = set & 1, n = w.n, nc_ = w.n_cand, ld = w.cap, j0 = jb * XX2_BJ;
       for (int i0 = 0; i0 < n; i0 += 32, ++g) {
-        const int st = (int)(g % XX2_STAGES);
-        const uint32_t u = g / XX2_STAGES;
+        const int st = (int)(g % S);
+        const uint32_t u = g / S;
         const bool mine = tc::mbar_wait(full(st), u & 1u, abort_flag);
         if (!__all_sync(0xffffffffu, mine)) {
           stop = true;
@@ -444,8 +455,8 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
         // Rows >= n are zeroed (K padding); the logical chunk lc of the box row
         // sits at physical chunk lc ^ (r & 7).
         const bool row_ok = i0 + r < n;
-        const uint8_t* nrow = gb + st * L::STAGE + bx * L::N_BOX + r * 128;
-        uint8_t* tH = gb + st * L::STAGE + L::N_TILE;
+        const uint8_t* nrow = gb + st * L::STAGE + L::OFF_N + bx * L::N_BOX + r * 128;
+        uint8_t* tH = gb + st * L::STAGE + L::OFF_T;
         uint8_t* tL = tH + L::T_TILE;
 #pragma unroll
         for (int lc = 0; lc < 8; ++lc) {
@@ -508,7 +519,9 @@ cudaError_t setup_ext_tc() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_ext_g_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, XtLayout<128>::SMEM);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ext_x_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, Xx2Layout::SMEM);
+    e = cudaFuncSetAttribute(k_ext_x_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, Xx2Layout<64>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ext_x_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Xx2Layout<128>::SMEM);
   return e;
 }
 
@@ -519,7 +532,7 @@ void launch_ext_g_tc(const Config& cfg, cudaStream_t st) {
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
   }
-  if (cfg.ks <= 64) k_ext_g_tc<64><<<sms, 192, XtLayout<64>::SMEM, st>>>(cfg);
+  if (ext_tile_c(cfg.ks) <= 64) k_ext_g_tc<64><<<sms, 192, XtLayout<64>::SMEM, st>>>(cfg);
   else k_ext_g_tc<128><<<sms, 192, XtLayout<128>::SMEM, st>>>(cfg);
 }
 
@@ -530,7 +543,8 @@ void launch_ext_x_tc(const Config& cfg, cudaStream_t st) {
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
   }
-  k_ext_x_tc<<<sms, 192, Xx2Layout::SMEM, st>>>(cfg);
+  if (ext_tile_c(cfg.ks) <= 64) k_ext_x_tc<64><<<sms, 192, Xx2Layout<64>::SMEM, st>>>(cfg);
+  else k_ext_x_tc<128><<<sms, 192, Xx2Layout<128>::SMEM, st>>>(cfg);
 }
 
 }  // namespace dca

@@ -430,8 +430,8 @@ bool encode_update_maps(const WalkerDev& w, int ks, TmapDev* out) {
     // in the update-operand buffer (free during the extension)
     if (!encode_2d(m + 4, w.Aop[sp], C, 2 * (uint64_t)KS_MAX, C * 4, (uint32_t)ext_tile_c(ks))) return false;
     // candidate table U ([hi | lo] x KS_MAX rows x C columns, in the other
-    // operand buffer), 128-row boxes (the M extent of the X product)
-    if (!encode_2d(m + 5, w.Bop[sp], C, 2 * (uint64_t)KS_MAX, C * 4, 128u)) return false;
+    // operand buffer), boxes of the candidate tile's rows
+    if (!encode_2d(m + 5, w.Bop[sp], C, 2 * (uint64_t)KS_MAX, C * 4, (uint32_t)ext_tile_c(ks))) return false;
     for (int par = 0; par < 2; ++par)
       if (!encode_2d(m + 6 + par, w.N[par][sp], C, C, C * 4, 32u)) return false;
   }
