@@ -54,9 +54,11 @@ FP64_TFLOPS = 1.25
 TF32_PER_BF16 = 1.1 / 2.25
 
 # DRAM bytes (read + write) per launch of a kernel from an ncu capture of the
-# named workload (profiles/top_kernels_batched256_mixed.md); quoted as
-# `traffic` for that kernel on that workload only.
-NCU_TRAFFIC = {("batched256", "update"): 1.388e9}
+# named workload (profiles/tensor_core_kernels_batched256_mixed.md: k_upd_tc,
+# 847.8 MB read + 524.2 MB written in one window of the pooled schedule, where
+# every window carries all walkers); quoted as `traffic` for that kernel on
+# that workload only.
+NCU_TRAFFIC = {("batched256", "update"): 1.372e9}
 
 
 class ClockSampler:
@@ -154,8 +156,10 @@ def workload_problems(wl, use_gpu_builder):
 # --------------------------------------------------------------------------
 # CPU baseline: the oracle as it stands, on a bounded sample of the workload
 # --------------------------------------------------------------------------
-def _oracle_sample(args):
-    wl_name, walker_id, seed, seconds = args
+def _oracle_worker(stats, stop, ready, wl_name, walker_id, seed):
+    """One oracle walker of the workload in its own process: warmed up once,
+    then sweeping until told to stop, publishing after every sweep its decided
+    proposals, the time (monotonic clock) and the sweep count."""
     sys.path.insert(0, ROOT)
     from oracle import ctaux
     wl = inputs.WORKLOADS[wl_name]
@@ -166,48 +170,110 @@ def _oracle_sample(args):
                            n_tau_meas=wl.n_tau_meas, seed=seed, walker_id=walker_id,
                            init_config_size=wl.init_config_size)
     w.sweep(wl.warmup_sweeps)
-    p0 = w.counters()["proposals"]
-    t0 = time.perf_counter()
     sweeps = 0
-    while time.perf_counter() - t0 < seconds:
+
+    def publish():
+        with stats.get_lock():
+            stats[0] = float(w.counters()["proposals"])
+            stats[1] = time.perf_counter()
+            stats[2] = float(sweeps)
+
+    publish()
+    ready.set()
+    while not stop.is_set():
         w.sweep(1)
         sweeps += 1
-    dt = time.perf_counter() - t0
-    return w.counters()["proposals"] - p0, dt, sweeps
+        publish()
+
+
+class OraclePool:
+    """The oracle on the host cores: one walker of the workload per core
+    (spawned processes), each warmed up once and then sweeping continuously.
+    The rate between two snapshots is the sum over walkers of decided
+    proposals over time, each walker between its own sweep boundaries."""
+
+    def __init__(self, wl_name):
+        import multiprocessing as mp
+        wl = inputs.WORKLOADS[wl_name]
+        self.wl = wl
+        self.cores = max(1, min(wl.walkers, os.cpu_count() or 1))
+        ctx = mp.get_context("spawn")
+        self.stop = ctx.Event()
+        self.stats, self.ready, self.procs = [], [], []
+        for i in range(self.cores):
+            st = ctx.Array("d", 3)
+            ev = ctx.Event()
+            p = ctx.Process(target=_oracle_worker, args=(st, self.stop, ev, wl_name, i, wl.seed), daemon=True)
+            p.start()
+            self.stats.append(st)
+            self.ready.append(ev)
+            self.procs.append(p)
+        for ev in self.ready:
+            if not ev.wait(timeout=1800):
+                raise RuntimeError("oracle warm-up did not finish")
+
+    def snapshot(self):
+        out = []
+        for st in self.stats:
+            with st.get_lock():
+                out.append((st[0], st[1], st[2]))
+        return out
+
+    def advanced(self, s0, limit=600.0):
+        """Wait until every walker has finished a sweep after snapshot s0."""
+        t0 = time.perf_counter()
+        while True:
+            s1 = self.snapshot()
+            if all(b[1] > a[1] for a, b in zip(s0, s1)) or time.perf_counter() - t0 > limit:
+                return s1
+            time.sleep(0.02)
+
+    def measure(self, s0, s1, seconds):
+        rate = sum((b[0] - a[0]) / (b[1] - a[1]) for a, b in zip(s0, s1) if b[1] > a[1])
+        sample = "%d walkers, one per core, %d measured sweeps in %.1f s (after %d warm-up sweeps each)" % (
+            self.cores, int(sum(b[2] - a[2] for a, b in zip(s0, s1))), seconds, self.wl.warmup_sweeps)
+        return {"value": rate, "unit": UNIT, "cores": self.cores, "kind": "oracle", "sample": sample}
+
+    def close(self):
+        self.stop.set()
+        for p in self.procs:
+            p.join(timeout=120)
+            if p.is_alive():
+                p.terminate()
 
 
 def cpu_baseline(wl_name, seconds=12.0):
-    wl = inputs.WORKLOADS[wl_name]
-    cores = max(1, min(wl.walkers, os.cpu_count() or 1))
-    if cores == 1:
-        props, dt, sweeps = _oracle_sample((wl_name, 0, wl.seed, seconds))
-        rate = props / dt
-        sample = "%d measured sweeps of 1 walker after %d warm-up sweeps (%.1f s)" % (sweeps, wl.warmup_sweeps, dt)
-    else:
-        import multiprocessing as mp
-        with mp.get_context("spawn").Pool(cores) as pool:
-            res = pool.map(_oracle_sample, [(wl_name, i, wl.seed, seconds) for i in range(cores)])
-        rate = sum(r[0] / r[1] for r in res)
-        sample = "%d walkers, one per core, %d sweeps in total (%.1f s each)" % (
-            cores, sum(r[2] for r in res), seconds)
-    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    pool = OraclePool(wl_name)
+    try:
+        s0 = pool.snapshot()
+        t0 = time.perf_counter()
+        time.sleep(seconds)
+        s1 = pool.advanced(s0)
+        return pool.measure(s0, s1, time.perf_counter() - t0)
+    finally:
+        pool.close()
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
     wl = workload_of(args)
+    # the walkers are warmed up once; the timed steps together sample about a minute
     per_step = max(0.2, min(10.0, 60.0 / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        cpu_baseline(args.workload, seconds=per_step)
-    vals = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(args.workload, seconds=per_step))
-    dt = time.perf_counter() - t0
-    v = sum(x["value"] for x in vals) / len(vals)
-    cb = dict(vals[-1])
-    cb["value"] = v
+    pool = OraclePool(args.workload)
+    try:
+        for _ in range(args.warmup):
+            time.sleep(per_step)
+        s0 = pool.snapshot()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):  # each step: per_step seconds of every walker's sweeps
+            time.sleep(per_step)
+        s1 = pool.advanced(s0)
+        dt = time.perf_counter() - t0
+        cb = pool.measure(s0, s1, dt)
+    finally:
+        pool.close()
+    v = cb["value"]
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / max(1, args.steps),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
