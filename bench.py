@@ -54,7 +54,7 @@ FP64_TFLOPS = 1.25
 TF32_PER_BF16 = 1.1 / 2.25
 
 # DRAM bytes (read + write) per launch of a kernel from an ncu capture of the
-# named workload (profiles/tensor_core_kernels_batched256_mixed.md: k_upd_tc,
+# named workload (profiles/top_kernels_batched256_mixed.md: k_upd_tc,
 # 847.8 MB read + 524.2 MB written in one window of the pooled schedule, where
 # every window carries all walkers); quoted as `traffic` for that kernel on
 # that workload only.
