@@ -52,6 +52,13 @@ FP64_TFLOPS = 1.25
 # Dense TF32 / BF16 tensor rate ratio from the nominal figures (1.1 / 2.25),
 # applied to the measured BF16 peak.
 TF32_PER_BF16 = 1.1 / 2.25
+# Mixed-path recompute, bound by FP32 issue: 152 SMs x 128 FP32 lanes x 2.07 GHz
+# = 40.3e12 instructions/s.  The residual I - A N (2n^3 flop) takes 11 FP32
+# instructions per double-float multiply-add (2 flop), the correction N R
+# (2n^3 flop) one FMA per 2 flop, so the 4n^3 flop of a recompute run at most
+# at 4 / (2 / 7.32 + 2 / 80.5) TFLOP/s.
+FP32_INSTR_PER_S = 152 * 128 * 2.07e9
+MIXED_RECOMPUTE_TFLOPS = 4.0 / (2.0 / (FP32_INSTR_PER_S * 2 / 11 / 1e12) + 2.0 / (FP32_INSTR_PER_S * 2 / 1e12))
 
 # DRAM bytes (read + write) per launch of a kernel from an ncu capture of the
 # named workload (profiles/top_kernels_batched256_mixed.md: k_upd_tc,
@@ -468,6 +475,11 @@ def roofline(group, g_ms, windows, work, peaks, kind, wl):
     work_b, work_f = work[group]
     tfs = work_f / sec / 1e12
     if work_b is None:
+        if wl.precision == "mixed":
+            return {**base, "bound": "alu", "achieved": tfs, "peak": MIXED_RECOMPUTE_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tfs / MIXED_RECOMPUTE_TFLOPS,
+                    "peak_kind": "derived: FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz), 11 instructions per "
+                                 "double-float multiply-add in the residual, one FMA in the correction"}
         return {**base, "bound": "alu", "achieved": tfs, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
                 "frac": tfs / FP64_TFLOPS, "peak_kind": "nominal FP64 (recipe table)"}
     gbs = work_b / sec / 1e9

@@ -1,0 +1,39 @@
+"""Host-side arithmetic of bench.py (no GPU): the roofline entries and the
+derived peak of the mixed-path recompute."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def test_mixed_recompute_peak_is_the_fp32_issue_bound():
+    import bench
+    instr = 152 * 128 * 2.07e9
+    residual = instr * 2 / 11 / 1e12      # double-float multiply-add: 2 flop in 11 instructions
+    correction = instr * 2 / 1e12         # FP32 FMA: 2 flop per instruction
+    assert bench.MIXED_RECOMPUTE_TFLOPS == pytest.approx(4.0 / (2.0 / residual + 2.0 / correction))
+    assert 13.0 < bench.MIXED_RECOMPUTE_TFLOPS < 14.0
+
+
+def test_roofline_entries():
+    import bench
+    from paper_1901_01047_gb300 import inputs
+    peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+    mixed = inputs.WORKLOADS["batched256"]
+    fp64 = inputs.WORKLOADS["betts16"]
+    work = {"update": (6.8e9, 13.6e9), "recompute": (None, 2.0e12)}
+    r = bench.roofline("update", 2000.0, 10, work, peaks, "measured", mixed)  # 2 s for 6.8 GB
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(3.4) and r["frac"] == pytest.approx(3.4 / 6800.0)
+    assert r["launch_ms"] == pytest.approx(200.0)
+    assert r["tf32_peak_tflops"] == pytest.approx(1900.0 * 1.1 / 2.25)
+    r = bench.roofline("recompute", 1000.0, 10, work, peaks, "measured", mixed)
+    assert r["bound"] == "alu" and r["achieved"] == pytest.approx(2.0)
+    assert r["peak"] == pytest.approx(bench.MIXED_RECOMPUTE_TFLOPS)
+    r = bench.roofline("recompute", 1000.0, 10, work, peaks, "measured", fp64)
+    assert r["peak"] == pytest.approx(bench.FP64_TFLOPS)
+    r = bench.roofline("metropolis", 1000.0, 10, work, peaks, "measured", mixed)
+    assert r["bound"] is None and r["frac"] is None
