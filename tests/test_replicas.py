@@ -72,3 +72,18 @@ def test_config_names_the_replicas():
     from paper_1901_01047_gb300 import inputs
     cfg = bench.config_of(inputs.WORKLOADS["batched256"], 4)
     assert cfg["parallelism"] == "replicas4" and cfg["workload"] == "batched256"
+    assert cfg["schedule"] == "pooled"
+
+
+def test_schedule_override_keeps_the_workload():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Args:
+        workload = "batched256"
+        schedule = "lockstep"
+
+    wl = bench.workload_of(Args)
+    assert wl.schedule == "lockstep" and wl.walkers == 256 and wl.name == "batched256"
+    Args.schedule = None
+    assert bench.workload_of(Args).schedule == "pooled"
