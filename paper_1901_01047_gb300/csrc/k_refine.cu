@@ -230,10 +230,12 @@ static int refine_grid(long long items) {
 }
 
 void launch_refine_gemms(const Config& cfg, int max_cap, cudaStream_t st) {
+  // every block resident at once (the residual holds 3 blocks per SM): a grid
+  // past the resident blocks would run its last blocks' items as a second wave
   const long long t = (max_cap + RT - 1) / RT;
-  const int g = refine_grid(2LL * cfg.n_walkers * t * t);
-  k_refine_resid<<<g, 256, 0, st>>>(cfg);
-  k_refine_correct<<<g, 256, 0, st>>>(cfg);
+  const long long items = 2LL * cfg.n_walkers * t * t;
+  k_refine_resid<<<persist_grid((const void*)k_refine_resid, items, 256), 256, 0, st>>>(cfg);
+  k_refine_correct<<<persist_grid((const void*)k_refine_correct, items, 256), 256, 0, st>>>(cfg);
 }
 
 void launch_refine_adopt(const Config& cfg, int max_cap, cudaStream_t st) {

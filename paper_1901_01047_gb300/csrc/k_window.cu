@@ -1323,7 +1323,7 @@ static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_
     case GROUP_UPDATE_POST:
       k_upd_border<T, A><<<persist_grid((const void*)k_upd_border<T, A>, 2 * S * kc, 256), 256, 0, st>>>(cfg);
       k_window_end<<<W, 256, 0, st>>>(cfg);
-      k_compact_N<T><<<grid_for(S * t32 * t32), 256, 0, st>>>(cfg);
+      k_compact_N<T><<<persist_grid((const void*)k_compact_N<T>, S * t32 * t32, 256), 256, 0, st>>>(cfg);
       k_compact_end<<<W, 256, 0, st>>>(cfg);
       return 4;
     default:
