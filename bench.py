@@ -61,10 +61,9 @@ FP32_INSTR_PER_S = 152 * 128 * 2.07e9
 MIXED_RECOMPUTE_TFLOPS = 4.0 / (2.0 / (FP32_INSTR_PER_S * 2 / 11 / 1e12) + 2.0 / (FP32_INSTR_PER_S * 2 / 1e12))
 
 # DRAM bytes (read + write) per launch of a kernel from an ncu capture of the
-# named workload (profiles/top_kernels_batched256_mixed.md: k_upd_tc,
-# 847.8 MB read + 524.2 MB written in one window of the pooled schedule, where
-# every window carries all walkers); quoted as `traffic` for that kernel on
-# that workload only.
+# named workload (k_upd_tc: 847.8 MB read + 524.2 MB written in one window of
+# the pooled schedule, where every window carries all walkers); quoted as
+# `traffic` for that kernel on that workload only.
 NCU_TRAFFIC = {("batched256", "update"): 1.372e9}
 
 
@@ -353,7 +352,7 @@ def run_ours(args, rank, world, local_rank):
     for k in range(args.steps):
         flush.fill_(float(k))
         starts[k].record(stream)
-        gw.sweep(1)
+        gw.sweep(1, sync=False)  # enqueues the step; the events bracket the device work only
         ends[k].record(stream)
     torch.cuda.synchronize()
     if args.profile_region:
@@ -362,9 +361,32 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
+    gw.sync()  # raises if a walker stopped with an error during the timed steps
     st1 = gw.stats()
     _, launches = gw.timing(reset=True)
-    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    dev_ms = sum(step_ms)
+
+    # The same batch under the other schedule, for comparison (shorter, untimed for `value`).
+    other = None
+    if wl.schedule == "pooled" and not args.profile_region:
+        gw.set_schedule("lockstep")
+        gw.sweep(1)
+        k_other = max(3, args.steps // 5)
+        so0 = gw.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(k_other):
+            gw.sweep(1, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        gw.sync()
+        so1 = gw.stats()
+        o_props = sum(b["proposals"] - a["proposals"] for a, b in zip(so0, so1))
+        o_ms = e0.elapsed_time(e1)
+        other = {"schedule": "lockstep", "value": o_props / (o_ms / 1000.0), "unit": UNIT, "steps": k_other,
+                 "ms_per_step": o_ms / k_other, "note": "one sweep of every walker per step; L2 not flushed"}
+        gw.set_schedule(wl.schedule)
 
     # Timed region 2 (the roofline): the same steps driven from the host with
     # CUDA events on the walker's stream around the dominant kernel group and
@@ -391,9 +413,13 @@ def run_ours(args, rank, world, local_rank):
                                                               "cuda")
     value = props_all / seconds
 
-    # End to end through the public API with host buffers: a new bare propagator
-    # uploaded from pinned memory, one sweep, and G read back, every step.
-    G0_host = torch.from_numpy(np.ascontiguousarray(probs[0]["G0"])).pin_memory()
+    # End to end through the public API with host buffers: every problem's bare
+    # propagator uploaded from pinned memory (the per-iteration input of an
+    # outer DCA loop; validated on the device), one step, and every walker's
+    # G read back, every step.
+    G0_host = [torch.from_numpy(np.ascontiguousarray(p["G0"])).pin_memory() for p in probs]
+    G0_np = [t.numpy() for t in G0_host]
+    h2d = sum(int(t.numel() * 8) for t in G0_host)
     g_bytes = sum(2 * nc * wl.n_tau_meas * 8 for nc in gw.nc) + 16 * wl.walkers
     st2 = gw.stats()
     if dist:
@@ -401,9 +427,11 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     te0 = time.perf_counter()
     for k in range(args.steps):
-        gw.update_G0(0, G0_host.numpy())
-        gw.sweep(1)
-        gw.measure_G()
+        for p, g in enumerate(G0_np):
+            gw.update_G0(p, g)
+        gw.sweep(1, sync=False)
+        gw.measure_G()  # synchronises
+    gw.sync()
     torch.cuda.synchronize()
     te = time.perf_counter() - te0
     st3 = gw.stats()
@@ -437,8 +465,11 @@ def run_ours(args, rank, world, local_rank):
             "n_update_roofline": roof_upd,
             "orders": order_stats(st1),
             "recompute_tflops_fp64": rflops_all / seconds / 1e12,
-            "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": int(G0_host.numel() * 8),
+            "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": int(g_bytes)},
+            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms),
+                        "stdev": statistics.pstdev(step_ms)},
+            **({"other_schedule": other} if other else {}),
         }
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.workload)

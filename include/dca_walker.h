@@ -21,9 +21,11 @@
  *     Output buffers are caller-owned host memory.  Device memory is owned by
  *     the library (allocated in dca_walker_create, freed in destroy).
  *   - Work is ordered on the CUDA stream given at create (NULL = the legacy
- *     default stream).  dca_walker_sweep synchronises that stream while it
- *     runs (it polls a device flag to know when all walkers are done);
- *     measure_G, stats, get_state and get_decision_log synchronise it too.
+ *     default stream).  dca_walker_sweep only enqueues work on that stream
+ *     (unless kernel-group timing is on, see dca_walker_set_timing);
+ *     dca_walker_sync, measure_G, stats, get_state, get_decision_log, save and
+ *     load synchronise it.  Errors a walker meets while its sweeps run (its
+ *     status) are reported by the next dca_walker_sync.
  *   - Matrices are row-major.  Spin index 0 = up, 1 = down.
  *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key
  *     (lo32(seed), hi32(seed) ^ walker_index) and counter
@@ -55,12 +57,28 @@ extern "C" {
 #define DCA_ERR_STATE (-6)    /* call not valid in the current state */
 #define DCA_ERR_CAPACITY (-7) /* a walker's order outgrew its matrix capacity */
 
-/* Arithmetic of the N matrices and their updates. */
-#define DCA_PREC_FP64 0       /* N stored and updated in FP64 */
-#define DCA_PREC_MIXED 1      /* N stored in FP32, candidate-extension and N-update products in
-                                 FP32 / TF32 arithmetic; ratios, Gamma (B^-1), the update factors
-                                 and the recompute in FP64.  Rounding is amplified by the
-                                 conditioning of N^-1: expect ~1e-6..1e-5 relative error in G */
+/* Arithmetic of the N matrices and their updates.
+ *   FP64:   N stored and updated in FP64; every product, ratio and inverse in FP64.
+ *   MIXED (= TF32X3): N stored in FP32.  The three N-sized products (the rank-l
+ *           update and both candidate products of the extension) run as 3xTF32 on
+ *           the tensor cores (or FP32 CUDA cores, DCA_UPD_CUDA_CORE) with FP32
+ *           accumulation; the update factors L B^-1 and the rows of accepted
+ *           insertions in double-float (FP32 pairs, about 44 bits); Gamma (B^-1) and
+ *           the determinant ratios in FP64 (DCA_GAMMA_FP64) or double-float
+ *           (DCA_GAMMA_DOUBLE_FLOAT); the recompute from an FP64 A = N^-1 with a
+ *           double-float residual.  The FP32 storage of N bounds the accuracy: the
+ *           measured errors of N and G against the FP64 walker on the same trajectory
+ *           are 1e-6..1e-4 relative, growing with the conditioning of N^-1.
+ *   TF32:   as MIXED with one TF32 product per K step instead of three (the
+ *           tensor-core kernels only); about 11 bits per product. */
+#define DCA_PREC_FP64 0
+#define DCA_PREC_MIXED 1
+#define DCA_PREC_TF32X3 1
+#define DCA_PREC_TF32 2
+
+/* Arithmetic of Gamma (B^-1) and the determinant ratios on the mixed paths. */
+#define DCA_GAMMA_FP64 0          /* FP64 (default) */
+#define DCA_GAMMA_DOUBLE_FLOAT 1  /* FP32 pairs, about 44 bits, on the FP32 pipes */
 
 /* One physical problem (a cluster with its bare propagator). */
 typedef struct {
@@ -102,6 +120,11 @@ typedef struct {
                                       Independent of recompute_every. */
   int32_t recompute_method;        /* DCA_RECOMPUTE_* */
   int32_t schedule;                /* DCA_SCHEDULE_*: how dca_walker_sweep shares the windows */
+  int32_t gamma_precision;         /* DCA_GAMMA_*: B^-1 and ratios of the mixed paths */
+  int32_t recompute_at_measure;    /* 1: recompute N in the window that ends every measured
+                                      sweep, before its measurement (the measurement then sees a
+                                      from-scratch N instead of one carrying the drift of the
+                                      updates since the last recompute); 0: off */
 } dca_walker_params;
 
 /* Scheduling of the walkers by dca_walker_sweep(n).  The chains do not depend
@@ -157,7 +180,7 @@ typedef struct {
   double n_update_flops;    /* algorithmic flop of the N updates (2 n^2 l + 2 n l^2 per spin) */
   double n_update_bytes;    /* algorithmic bytes of the N updates (read + write n^2, n x l factors) */
   double extend_flops;      /* flop of the candidate extension (4 n^2 c per spin) */
-  double extend_bytes;      /* bytes of the candidate extension (two reads of N per spin) */
+  double extend_bytes;      /* algorithmic bytes of the candidate extension (one read of N per spin) */
   double recompute_flops;   /* flop of the from-scratch inverses (2 n^3 per spin) */
 } dca_walker_stats_t;
 
@@ -186,11 +209,58 @@ DCA_API int dca_walker_create(const dca_walker_params* params, void* cuda_stream
  * rounded mean of those k (max(k,1) when warmup_sweeps = 0).  Every sweep at
  * or past warm-up ends with one measurement.  The submatrix updates run as a
  * device-side loop (a CUDA graph with a conditional WHILE node, captured on
- * the first call) until the sweeps are done, so the host launches one graph
- * and reads back one status record per call; with kernel timing on
- * (dca_walker_set_timing) the host drives the same kernels instead.
- * Returns DCA_ERR_TIMEOUT if the loop hits its iteration bound. */
+ * the first call) until the sweeps are done: the call enqueues a target
+ * kernel and one graph launch on the walker's stream and returns without
+ * waiting.  Walker errors (DCA_ERR_NUMERIC, DCA_ERR_CAPACITY, DCA_ERR_TIMEOUT
+ * of a bounded wait in a kernel, or of the loop's iteration bound) surface at
+ * the next dca_walker_sync.  With kernel-group timing on (dca_walker_set_timing)
+ * the host drives the same kernels instead, synchronising the stream between
+ * chunks of windows, and the call returns the walkers' errors itself. */
 DCA_API int dca_walker_sweep(dca_walker* w, int32_t n_sweeps);
+
+/* Wait for the work enqueued on the walker's stream and report the first
+ * error of the sweeps since the last check: DCA_ERR_TIMEOUT if a window loop
+ * reached its iteration bound, else the error code of the first walker whose
+ * status is not DCA_OK (a walker in error stops; the others go on), else
+ * DCA_OK.  The handle stays usable after an error: stats, measure_G,
+ * get_state and save work, and dca_walker_load restores every walker. */
+DCA_API int dca_walker_sync(dca_walker* w);
+
+/* Switch the schedule (DCA_SCHEDULE_*) between sweeps; the chains do not
+ * change.  Synchronises the stream. */
+DCA_API int dca_walker_set_schedule(dca_walker* w, int32_t schedule);
+
+/* Bounds of the device-side waits: max_windows caps the windows of one
+ * dca_walker_sweep call (0 = the automatic bound, which normal runs never
+ * reach); wait_cycles bounds every mbarrier wait inside the tensor-core
+ * kernels in SM clock cycles (0 = the default of 4e9, about two seconds).  A
+ * bound that runs out stops the affected walkers with DCA_ERR_TIMEOUT, the
+ * kernel lets its copies in flight land, frees its tensor memory and returns,
+ * so the context stays usable.  Used to exercise the failure paths.
+ * Synchronises the stream. */
+DCA_API int dca_walker_set_limits(dca_walker* w, int64_t max_windows, int64_t wait_cycles);
+
+/* Checkpoint of every walker's chain (App. B "seed" and the Monte-Carlo
+ * parameters make a run reproducible; this makes it resumable): the
+ * configuration (vertex list in live order), the sign, the proposal counter
+ * (the Philox counter: the random stream continues exactly), the sweep state
+ * (position, frozen length, warm-up sums, recompute phase), the counters and
+ * the G accumulators.  N is not stored: dca_walker_load rebuilds it from
+ * scratch (the periodic recompute, Eq. Zk).  buf may be NULL (or cap too
+ * small) to query the size in *n; a non-NULL buf with cap < the size returns
+ * DCA_ERR_ARG.  Synchronises the stream. */
+DCA_API int dca_walker_save(dca_walker* w, void* buf, size_t cap, size_t* n);
+
+/* Restore a checkpoint written by dca_walker_save into a handle created with
+ * the same parameters (walker count, problems, precision and measurement grid
+ * are checked): each walker's configuration, sign, counters and accumulators
+ * are set, its status reset to the saved one, and N rebuilt from scratch in
+ * FP64 (rounded to FP32 on the mixed paths).  The decision log and any forced
+ * decisions are left as they are.  Returns DCA_ERR_ARG for a malformed or
+ * mismatching buffer (the handle is left unchanged then) and
+ * DCA_ERR_NUMERIC if a rebuilt matrix is singular or its determinant sign
+ * disagrees with the saved sign.  Synchronises the stream. */
+DCA_API int dca_walker_load(dca_walker* w, const void* buf, size_t n);
 
 /* Copy the accumulated sum over measurements of sign * G(dr, tau_a) (paper
  * convention) to G_out [n_walkers][2][nc][n_tau_meas] (nc of each walker's
@@ -231,21 +301,24 @@ DCA_API int dca_fresh_N(const dca_problem* problem, int32_t n, const dca_vertex*
                         double* N_dn, int32_t* det_sign);
 
 /* Same operation and outputs as dca_fresh_N, for callers that cannot allocate
- * device memory (code running during CUDA stream capture, where cudaMalloc is
- * not allowed; processes whose device memory belongs to another allocator;
- * services with a fixed device footprint).  The paper has no counterpart: it
- * is a deployment variant of the recompute.  It calls no cudaMalloc, cudaFree
- * or other allocating routine; all device memory is one fixed file-scope
- * __device__ array (about 3.2 MB, held by every GPU that loads the library
- * until exit).  Limits: n <= DCA_NOALLOC_MAX_ORDER, nc <= DCA_NOALLOC_MAX_SITES,
- * 2 * nc * (n_tau + 1) <= DCA_NOALLOC_MAX_TABLE; larger sizes return
- * DCA_ERR_ARG with a message in dca_walker_last_error(NULL).  The first call on
- * each device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  Every
- * call reuses the same array and leaves its contents behind; calls are
- * serialised on the host, but GPU work that overlaps a call and touches the
- * array races with it.  Uses the current device and the legacy default stream
- * with synchronous copies. */
+ * device memory: processes whose device memory belongs to another allocator
+ * (a framework's caching pool that must see every byte), and services that
+ * are sized for a fixed device footprint and may not grow it at run time.
+ * The paper has no counterpart: it is a deployment variant of the recompute.
+ * It calls no cudaMalloc, cudaFree or other allocating routine; all device
+ * memory is one fixed file-scope __device__ array (about 3.2 MB, held by
+ * every GPU that loads the library until exit).  Limits: n <=
+ * DCA_NOALLOC_MAX_ORDER, nc <= DCA_NOALLOC_MAX_SITES, 2 * nc * (n_tau + 1) <=
+ * DCA_NOALLOC_MAX_TABLE; larger sizes return DCA_ERR_ARG with a message in
+ * dca_walker_last_error(NULL).  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process: a cudaDeviceReset invalidates it, so do not call
+ * this function again after resetting the device.  Every call reuses the
+ * same array and leaves its contents behind; calls are serialised on the
+ * host, but GPU work that overlaps a call and touches the array races with
+ * it.  It runs on the current device and the legacy default stream with
+ * synchronous copies. */
 #define DCA_NOALLOC_MAX_ORDER 256
 #define DCA_NOALLOC_MAX_SITES 64
 #define DCA_NOALLOC_MAX_TABLE 262144
@@ -254,7 +327,11 @@ DCA_API int dca_fresh_N_noalloc(const dca_problem* problem, int32_t n, const dca
 
 /* Replace the bare propagator of problem `problem` (host [2][nc][n_tau+1],
  * same layout and convention as dca_problem.G0), e.g. for the next iteration
- * of an outer DCA loop.  Stream-ordered: sweeps launched afterwards use it. */
+ * of an outer DCA loop.  Stream-ordered: the table is copied to a staging
+ * buffer on the walker's stream (pass pinned host memory for an asynchronous
+ * copy) and sweeps launched afterwards use it.  The table is checked on the
+ * device: one with a non-finite entry is not taken (the previous table stays)
+ * and the next dca_walker_sync returns DCA_ERR_ARG. */
 DCA_API int dca_walker_update_G0(dca_walker* w, int32_t problem, const double* G0);
 
 /* Change the submatrix size (1..128) and the N-update kernel (DCA_UPD_*,

@@ -1,11 +1,10 @@
 // fresh_static.cu -- from-scratch N with no device allocation at all.
 //
 // dca_fresh_N allocates its device buffers for each call.  Some callers cannot
-// let a library allocate device memory: code that runs while a stream is being
-// captured into a CUDA graph (cudaMalloc is not permitted during capture),
-// processes whose device memory is owned by another allocator (for example a
-// framework's caching allocator that has reserved the pool), and services that
-// must keep their device footprint fixed after start-up.  For them,
+// let a library allocate device memory: processes whose device memory is
+// owned by another allocator (for example a framework's caching allocator
+// that has reserved the pool), and services that must keep their device
+// footprint fixed after start-up.  For them,
 // dca_fresh_N_noalloc does the same work with every device buffer carved out
 // of one file-scope __device__ array of fixed size (about 3.2 MB, held by
 // every GPU that loads the library until the process exits).
@@ -13,7 +12,9 @@
 // Host code only ever sees a host-side stand-in for the array's name; the
 // device address comes from cudaGetSymbolAddress, looked up once per device
 // (with that device current) on the first call made on it.  Make that first
-// call before any stream capture begins.
+// call before any stream capture begins.  The address is kept for the life of
+// the process; a cudaDeviceReset frees the array's storage, so the function
+// must not be called again after a reset.
 //
 // The array is shared by every call and keeps the last call's contents.  This
 // entry point serialises its own callers with a mutex and uses synchronous

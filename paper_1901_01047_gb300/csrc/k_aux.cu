@@ -80,9 +80,7 @@ __global__ void __launch_bounds__(256) k_build_A(Config cfg, int mode) {
       });
 }
 
-constexpr int PERSIST = 4 * 152;
-
-static int grid_for(long long items) { return (int)(items < 1 ? 1 : (items < PERSIST ? items : PERSIST)); }
+static int grid_for(long long items) { return sm_grid(items, 4); }
 
 // Initial build finish: sign of prod_sigma det N_sigma^-1.
 __global__ void k_init_finish(Config cfg, const int* sgn) {
@@ -94,7 +92,7 @@ __global__ void k_init_finish(Config cfg, const int* sgn) {
     return;
   }
   const int s = sgn[2 * wi] * sgn[2 * wi + 1];
-  if (s == 0) w.status = ST_ERR_NUMERIC;
+  if (s == 0) set_status(w, ST_ERR_NUMERIC);
   w.sign = s < 0 ? -1.0 : 1.0;
 }
 
@@ -560,6 +558,20 @@ int launch_recompute(int part, const Config& cfg, int max_cap, int* d_sgn, cudaS
   }
 }
 
+// Rebuild every walker's N from scratch for the vertex list in its current
+// buffer (after a checkpoint load), with the configuration sign from the
+// determinants, exactly as the initial build does.
+void launch_rebuild(const Config& cfg, int max_n, int* d_sgn, cudaStream_t st) {
+  const int W = cfg.n_walkers;
+  if (max_n > 0) {
+    const long long g = grid_for(2LL * W * blocks_of((long long)max_n * max_n, 256));
+    k_build_A<<<g, 256, 0, st>>>(cfg, 0);
+    launch_gj(cfg, 0, max_n, d_sgn, st);
+    if (cfg.prec == PREC_MIXED) k_store_fp32<<<g, 256, 0, st>>>(cfg, 0);
+  }
+  k_init_finish<<<(W + 127) / 128, 128, 0, st>>>(cfg, d_sgn);
+}
+
 // From-scratch N for the vertex list held in the current buffer of every walker
 // of cfg (used by the standalone fresh-N operations): build A, invert in place.
 void launch_fresh_inverse(const Config& cfg, int max_n, int* d_sgn, cudaStream_t st) {
@@ -569,17 +581,29 @@ void launch_fresh_inverse(const Config& cfg, int max_n, int* d_sgn, cudaStream_t
   launch_gj(cfg, 0, max_n, d_sgn, st);
 }
 
-// g0 = -G0 in FP64 and its FP32 copy.
-__global__ void k_negate(const double* src, double* dst, float* dstf, size_t n) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
+// g0 = -G0 in FP64 and its FP32 copy, from a staged table, committed only if
+// every staged entry is finite (else *bad is set and the old table stays).
+// One block: the check and the commit need one barrier between them.
+__global__ void __launch_bounds__(1024) k_negate(const double* src, double* dst, float* dstf, size_t n, int* bad) {
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  int b = 0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) b |= isfinite(src[i]) ? 0 : 1;
+  if (b) s_bad = 1;
+  __syncthreads();
+  if (s_bad) {
+    if (threadIdx.x == 0) *bad = 1;
+    return;
+  }
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
     dst[i] = -src[i];
     dstf[i] = (float)(-src[i]);
   }
 }
 
-void launch_negate(const double* src, double* dst, float* dstf, size_t n, cudaStream_t st) {
-  k_negate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, dstf, n);
+void launch_negate(const double* src, double* dst, float* dstf, size_t n, int* bad, cudaStream_t st) {
+  k_negate<<<1, 1024, 0, st>>>(src, dst, dstf, n, bad);
 }
 
 // g0m[sp][p][d][m] = g0f[sp][d][q m + p] for q m + p <= n_tau, else 0.

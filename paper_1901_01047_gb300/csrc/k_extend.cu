@@ -154,9 +154,7 @@ __global__ void __launch_bounds__(256) k_ext_x(Config cfg) {
 
 int launch_ext_mixed(const Config& cfg, int max_cap, cudaStream_t st) {
   const long long S = 2LL * cfg.n_walkers;
-  long long items = S * ((max_cap + XB - 1) / XB) * ((cfg.ks + XC - 1) / XC);
-  constexpr long long kPersist = 8 * 152;
-  items = items < 1 ? 1 : (items < kPersist ? items : kPersist);
+  const long long items = sm_grid(S * ((max_cap + XB - 1) / XB) * ((cfg.ks + XC - 1) / XC), 8);
   if (cfg.ext_tc) {
     launch_ext_g_tc(cfg, st);
     launch_ext_x_tc(cfg, st);

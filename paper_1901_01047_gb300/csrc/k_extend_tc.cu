@@ -2,9 +2,9 @@
 // generation tensor cores (mixed precision), Sec. 2.3 "Submatrix updates":
 //     G_ext[i, n + c] = sum_j N[i, j] V[c, j],   V[c, j] = g0(r_j - r_c, tau_j - tau_c)   (k_ext_g_tc)
 //     X[c, j]         = sum_i U[c, i] N[i, j],   U[c, i] = g0(r_c - r_i, tau_c - tau_i) (e^{V_i} - 1)   (k_ext_x_tc)
-// 3xTF32 as in the N update: every operand x is used as hi = x with the low
-// 13 mantissa bits cleared and lo = x - hi; hi*hi + hi*lo + lo*hi accumulate
-// in FP32 in tensor memory.  V arrives pre-split from k_cand_zero ([hi | lo]
+// 3xTF32 as in the N update: every operand x is split into two TF32 values,
+// hi = tf32(x) and lo = tf32(x - hi); hi*hi + hi*lo + lo*hi accumulate in
+// FP32 in tensor memory.  V arrives pre-split from k_cand_zero ([hi | lo]
 // planes x KS_MAX rows x cap columns, in the update-operand buffer that is
 // free during the extension); N tiles are split in shared memory.
 //
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
         for (int j0 = 0; j0 < n; j0 += 32, ++g) {
           const int st = (int)(g % S);
           const uint32_t u = g / S;
-          if (u > 0 && !tc::mbar_wait(empty(st), (u - 1) & 1u, abort_flag)) {
+          if (u > 0 && !tc::mbar_wait(empty(st), (u - 1) & 1u, abort_flag, cfg.wait_cycles)) {
             ok = false;
             break;
           }
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
         }
       }
       if (!ok) {
-        cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+        set_status(cfg.W[set >> 1], ST_ERR_TIMEOUT);
         for (int st = 0; st < S; ++st)
           if (armed[st] > 0) tc::mbar_wait(full(st), (armed[st] - 1) & 1u, nullptr, 400000000LL);
       }
@@ -145,10 +145,11 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
       uint32_t g = 0, k = 0;
       int set = 0, rb = 0;
       bool ok = true;
+      const bool three = cfg.tf32_terms != 1;
       const uint32_t idesc = tc::idesc_tf32(XT_BM, CN);
       while (ok && it.next(cfg, set, rb)) {
         const int n = cfg.W[set >> 1].n;
-        if (k > 0 && !tc::mbar_wait(dg_empty, (k - 1) & 1u, abort_flag)) {
+        if (k > 0 && !tc::mbar_wait(dg_empty, (k - 1) & 1u, abort_flag, cfg.wait_cycles)) {
           ok = false;
           break;
         }
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
         for (int j0 = 0; j0 < n; j0 += 32, ++g) {
           const int st = (int)(g % S);
           const uint32_t u = g / S;
-          if (!tc::mbar_wait(conv(st), u & 1u, abort_flag)) {
+          if (!tc::mbar_wait(conv(st), u & 1u, abort_flag, cfg.wait_cycles)) {
             ok = false;
             break;
           }
@@ -169,8 +170,10 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
             const uint64_t ah = tc::sdesc_k_sw128(nH + 32 * q), al = tc::sdesc_k_sw128(nL + 32 * q);
             const uint64_t bh = tc::sdesc_k_sw128(vH + 32 * q), bl = tc::sdesc_k_sw128(vL + 32 * q);
             tc::mma_tf32(tmem, ah, bh, idesc, first ? 0u : 1u);
-            tc::mma_tf32(tmem, ah, bl, idesc, 1u);
-            tc::mma_tf32(tmem, al, bh, idesc, 1u);
+            if (three) {  // 3xTF32: the two correction products
+              tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+              tc::mma_tf32(tmem, al, bh, idesc, 1u);
+            }
             first = false;
           }
           tc::mma_commit(empty(st));
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
         tc::mma_commit(dg_full);
         ++k;
       }
-      if (!ok) cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+      if (!ok) set_status(cfg.W[set >> 1], ST_ERR_TIMEOUT);
       tc::mma_commit(fin);
       tc::mbar_wait(fin, 0u, nullptr, 400000000LL);
     }
@@ -191,14 +194,13 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
     int set = 0, rb = 0;
     bool stop = false;
     const int r = 32 * warp + lane;  // row of the block = TMEM lane
-    const uint32_t mask = 0xFFFFE000u;
     while (!stop && it.next(cfg, set, rb)) {
       WalkerDev& w = cfg.W[set >> 1];
       const int sp = set & 1, n = w.n, nc_ = w.n_cand, ld = w.cap, i0 = rb * XT_BM;
       for (int j0 = 0; j0 < n; j0 += 32, ++g) {
         const int st = (int)(g % S);
         const uint32_t u = g / S;
-        const bool mine = tc::mbar_wait(full(st), u & 1u, abort_flag);
+        const bool mine = tc::mbar_wait(full(st), u & 1u, abort_flag, cfg.wait_cycles);
         if (!__all_sync(0xffffffffu, mine)) {
           stop = true;
           break;
@@ -217,11 +219,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
           const int jc = j0 + 4 * lc;
           float xv[4] = {x.x, x.y, x.z, x.w}, hv[4], lv[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float v = jc + q < n ? xv[q] : 0.f;
-            hv[q] = __uint_as_float(__float_as_uint(v) & mask);
-            lv[q] = v - hv[q];
-          }
+          for (int q = 0; q < 4; ++q) tc::tf32_split(jc + q < n ? xv[q] : 0.f, hv[q], lv[q]);
           *ph = make_float4(hv[0], hv[1], hv[2], hv[3]);
           *pl = make_float4(lv[0], lv[1], lv[2], lv[3]);
         }
@@ -231,7 +229,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
       }
       if (stop) break;
       // accumulator of the item: row i0 + r, candidates 0 .. CN - 1
-      const bool mine = tc::mbar_wait(dg_full, k & 1u, abort_flag);
+      const bool mine = tc::mbar_wait(dg_full, k & 1u, abort_flag, cfg.wait_cycles);
       if (!__all_sync(0xffffffffu, mine)) {
         stop = true;
         break;
@@ -252,10 +250,17 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
       if (lane == 0) tc::mbar_arrive(dg_empty);
       ++k;
     }
-    if (stop && lane == 0) cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+    if (stop && lane == 0) set_status(cfg.W[set >> 1], ST_ERR_TIMEOUT);
     if (stop) *abort_flag = 1;
   }
   __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) {
+    // an aborted CTA may have left any of its items undone: stop every walker it served
+    XtIter it;
+    it.start(cfg, plan);
+    int set = 0, rb = 0;
+    while (it.next(cfg, set, rb)) set_status(cfg.W[set >> 1], ST_ERR_TIMEOUT);
+  }
   if (warp == 5) {
     __syncwarp();
     tc::fence_after_sync();
@@ -363,7 +368,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
         for (int i0 = 0; i0 < n; i0 += 32, ++g) {
           const int st = (int)(g % S);
           const uint32_t u = g / S;
-          if (u > 0 && !tc::mbar_wait(empty(st), (u - 1) & 1u, abort_flag)) {
+          if (u > 0 && !tc::mbar_wait(empty(st), (u - 1) & 1u, abort_flag, cfg.wait_cycles)) {
             ok = false;
             break;
           }
@@ -376,7 +381,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
         }
       }
       if (!ok) {
-        cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+        set_status(cfg.W[set >> 1], ST_ERR_TIMEOUT);
         for (int st = 0; st < S; ++st)
           if (armed[st] > 0) tc::mbar_wait(full(st), (armed[st] - 1) & 1u, nullptr, 400000000LL);
       }
@@ -389,10 +394,11 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
       uint32_t g = 0, k = 0;
       int set = 0, jb = 0;
       bool ok = true;
+      const bool three = cfg.tf32_terms != 1;
       const uint32_t idesc = tc::idesc_tf32(128, XX2_BJ);
       while (ok && it.next(cfg, set, jb)) {
         const int n = cfg.W[set >> 1].n;
-        if (k > 0 && !tc::mbar_wait(dx_empty, (k - 1) & 1u, abort_flag)) {
+        if (k > 0 && !tc::mbar_wait(dx_empty, (k - 1) & 1u, abort_flag, cfg.wait_cycles)) {
           ok = false;
           break;
         }
@@ -401,7 +407,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
         for (int i0 = 0; i0 < n; i0 += 32, ++g) {
           const int st = (int)(g % S);
           const uint32_t u = g / S;
-          if (!tc::mbar_wait(conv(st), u & 1u, abort_flag)) {
+          if (!tc::mbar_wait(conv(st), u & 1u, abort_flag, cfg.wait_cycles)) {
             ok = false;
             break;
           }
@@ -414,8 +420,10 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
             const uint64_t ah = tc::sdesc_k_sw128(uH + 32 * q), al = tc::sdesc_k_sw128(uL + 32 * q);
             const uint64_t bh = tc::sdesc_k_sw128(tH + 32 * q), bl = tc::sdesc_k_sw128(tL + 32 * q);
             tc::mma_tf32(tmem, ah, bh, idesc, first ? 0u : 1u);
-            tc::mma_tf32(tmem, ah, bl, idesc, 1u);
-            tc::mma_tf32(tmem, al, bh, idesc, 1u);
+            if (three) {  // 3xTF32: the two correction products
+              tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+              tc::mma_tf32(tmem, al, bh, idesc, 1u);
+            }
             first = false;
           }
           tc::mma_commit(empty(st));
@@ -424,7 +432,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
         tc::mma_commit(dx_full);
         ++k;
       }
-      if (!ok) cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+      if (!ok) set_status(cfg.W[set >> 1], ST_ERR_TIMEOUT);
       tc::mma_commit(fin);
       tc::mbar_wait(fin, 0u, nullptr, 400000000LL);
     }
@@ -436,14 +444,13 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
     int set = 0, jb = 0;
     bool stop = false;
     const int bx = warp, r = lane;  // converter: box bx, row r of the box
-    const uint32_t mask = 0xFFFFE000u;
     while (!stop && it.next(cfg, set, jb)) {
       WalkerDev& w = cfg.W[set >> 1];
       const int sp = set & 1, n = w.n, nc_ = w.n_cand, ld = w.cap, j0 = jb * XX2_BJ;
       for (int i0 = 0; i0 < n; i0 += 32, ++g) {
         const int st = (int)(g % S);
         const uint32_t u = g / S;
-        const bool mine = tc::mbar_wait(full(st), u & 1u, abort_flag);
+        const bool mine = tc::mbar_wait(full(st), u & 1u, abort_flag, cfg.wait_cycles);
         if (!__all_sync(0xffffffffu, mine)) {
           stop = true;
           break;
@@ -464,12 +471,12 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
           const float xv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float v = row_ok ? xv[q] : 0.f;
-            const float hv = __uint_as_float(__float_as_uint(v) & mask);
+            float hv, lv;
+            tc::tf32_split(row_ok ? xv[q] : 0.f, hv, lv);
             const int j = 32 * bx + 4 * lc + q;
             const int off = j * 128 + ((((r >> 2) ^ (j & 7)) << 4) | ((r & 3) << 2));
             *(float*)(tH + off) = hv;
-            *(float*)(tL + off) = v - hv;
+            *(float*)(tL + off) = lv;
           }
         }
         tc::fence_async_smem();
@@ -477,7 +484,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
         if (lane == 0) tc::mbar_arrive(conv(st));
       }
       if (stop) break;
-      const bool mine = tc::mbar_wait(dx_full, k & 1u, abort_flag);
+      const bool mine = tc::mbar_wait(dx_full, k & 1u, abort_flag, cfg.wait_cycles);
       if (!__all_sync(0xffffffffu, mine)) {
         stop = true;
         break;
@@ -502,10 +509,17 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
       if (lane == 0) tc::mbar_arrive(dx_empty);
       ++k;
     }
-    if (stop && lane == 0) cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+    if (stop && lane == 0) set_status(cfg.W[set >> 1], ST_ERR_TIMEOUT);
     if (stop) *abort_flag = 1;
   }
   __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) {
+    // an aborted CTA may have left any of its items undone: stop every walker it served
+    Xx2Iter it;
+    it.start(cfg, plan);
+    int set = 0, rb = 0;
+    while (it.next(cfg, set, rb)) set_status(cfg.W[set >> 1], ST_ERR_TIMEOUT);
+  }
   if (warp == 5) {
     __syncwarp();
     tc::fence_after_sync();
@@ -526,23 +540,13 @@ cudaError_t setup_ext_tc() {
 }
 
 void launch_ext_g_tc(const Config& cfg, cudaStream_t st) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
-  }
+  const int sms = device_sm_count();
   if (ext_tile_c(cfg.ks) <= 64) k_ext_g_tc<64><<<sms, 192, XtLayout<64>::SMEM, st>>>(cfg);
   else k_ext_g_tc<128><<<sms, 192, XtLayout<128>::SMEM, st>>>(cfg);
 }
 
 void launch_ext_x_tc(const Config& cfg, cudaStream_t st) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
-  }
+  const int sms = device_sm_count();
   if (ext_tile_c(cfg.ks) <= 64) k_ext_x_tc<64><<<sms, 192, Xx2Layout<64>::SMEM, st>>>(cfg);
   else k_ext_x_tc<128><<<sms, 192, Xx2Layout<128>::SMEM, st>>>(cfg);
 }

@@ -168,7 +168,7 @@ __device__ void gj_matrix(const Config& cfg, int mode, int mat, int* sgn_out, cg
   if (bad) {
     cluster.sync();  // no block leaves while another may still read its post
     if (rank == 0 && tid == 0) {
-      w.status = ST_ERR_NUMERIC;
+      set_status(w, ST_ERR_NUMERIC);
       sgn_out[mat] = 0;
     }
     return;
@@ -199,7 +199,7 @@ void launch_gj(const Config& cfg, int mode, int max_n, int* d_sgn, cudaStream_t 
     configured = smem;
   }
   // one cluster of GJ_CTAS blocks per GJ_CTAS SMs, at most one per matrix
-  const int mats = 2 * cfg.n_walkers, fit = 152 / GJ_CTAS;
+  const int mats = 2 * cfg.n_walkers, fit = device_sm_count() / GJ_CTAS > 0 ? device_sm_count() / GJ_CTAS : 1;
   const int clusters = mats < fit ? mats : fit;
   k_gj_cluster<<<GJ_CTAS * clusters, GJ_THREADS, smem, st>>>(cfg, mode, d_sgn);
 }

@@ -224,10 +224,7 @@ __global__ void __launch_bounds__(256) k_refine_adopt(Config cfg) {
       });
 }
 
-static int refine_grid(long long items) {
-  constexpr int kPersist = 4 * 152;
-  return (int)(items < 1 ? 1 : (items < kPersist ? items : kPersist));
-}
+static int refine_grid(long long items) { return sm_grid(items, 4); }
 
 void launch_refine_gemms(const Config& cfg, int max_cap, cudaStream_t st) {
   // every block resident at once (the residual holds 3 blocks per SM): a grid

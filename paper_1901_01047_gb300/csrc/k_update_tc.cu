@@ -4,10 +4,11 @@
 //                             R  = N_ext[P, 0:n)                  (l x n),
 // the submatrix update of the DCA++ paper (Sec. 2.3, "Submatrix updates").
 //
-// Precision (3xTF32).  Every FP32 operand x is split into hi = x rounded to
-// TF32 and lo = x - hi (exact); the MMA chain accumulates hi*hi + hi*lo +
-// lo*hi in FP32 in tensor memory, about 22 bits of every product, close to
-// an FP32 product.  The split operands are written by k_upd_ops in the
+// Precision (3xTF32).  Every FP32 operand x is split into two TF32 values,
+// hi = x rounded to TF32 and lo = x - hi rounded to TF32 (the tensor core
+// would otherwise truncate the remainder's low bits); the MMA chain
+// accumulates hi*hi + hi*lo + lo*hi in FP32 in tensor memory, each product
+// exact, the split carrying x to about 2^-22 of |x|.  The split operands are written by k_upd_ops in the
 // layout the TMA loads: planes [hi | lo] x rows x 128 K-columns (512 B rows).
 //
 // Work item = one 128-row block of one walker-spin N.  A CTA (one per SM)
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
         const void* mA = tc_map(cfg, wi, sp, 0);
         const void* mB = tc_map(cfg, wi, sp, 1);
         const void* mN = tc_map(cfg, wi, sp, 2 + w.parity);
-        if (k > 0 && !tc::mbar_wait(a_empty, (k - 1) & 1u, abort_flag)) {
+        if (k > 0 && !tc::mbar_wait(a_empty, (k - 1) & 1u, abort_flag, cfg.wait_cycles)) {
           ok = false;
           break;
         }
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
         for (int t = 0; t < ntiles; ++t, ++g) {
           const int st = (int)(g & 1u);
           const uint32_t u = g >> 1;
-          if (u > 0 && !tc::mbar_wait(empty0 + 8 * st, (u - 1) & 1u, abort_flag)) {
+          if (u > 0 && !tc::mbar_wait(empty0 + 8 * st, (u - 1) & 1u, abort_flag, cfg.wait_cycles)) {
             ok = false;
             break;
           }
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
         }
       }
       if (!ok) {
-        cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+        set_status(cfg.W[set >> 1], ST_ERR_TIMEOUT);
         // the loads already issued land before the CTA exits
         if (k > 0) tc::mbar_wait(a_full, (k - 1) & 1u, nullptr, 400000000LL);
         for (int st = 0; st < 2; ++st)
@@ -172,11 +173,12 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
       uint32_t g = 0, k = 0;
       int set = 0, rb = 0;
       bool ok = true;
+      const bool three = cfg.tf32_terms != 1;
       const uint32_t idesc = tc::idesc_tf32(TC_BM, BN);
       while (ok && it.next(cfg, set, rb)) {
         const WalkerDev& w = cfg.W[set >> 1];
         const int n = w.n, steps = (w.n_acc + 7) >> 3;
-        if (!tc::mbar_wait(a_full, k & 1u, abort_flag)) {
+        if (!tc::mbar_wait(a_full, k & 1u, abort_flag, cfg.wait_cycles)) {
           ok = false;
           break;
         }
@@ -186,8 +188,8 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
         for (int t = 0; t < ntiles; ++t, ++g) {
           const int st = (int)(g & 1u);
           const uint32_t u = g >> 1;
-          if ((u > 0 && !tc::mbar_wait(empty0 + 8 * st, (u - 1) & 1u, abort_flag)) ||
-              !tc::mbar_wait(full0 + 8 * st, u & 1u, abort_flag)) {
+          if ((u > 0 && !tc::mbar_wait(empty0 + 8 * st, (u - 1) & 1u, abort_flag, cfg.wait_cycles)) ||
+              !tc::mbar_wait(full0 + 8 * st, u & 1u, abort_flag, cfg.wait_cycles)) {
             ok = false;
             break;
           }
@@ -201,8 +203,10 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
             const uint64_t ah = tc::sdesc_k_sw128(aH + ao), al = tc::sdesc_k_sw128(aL + ao);
             const uint64_t bh = tc::sdesc_k_sw128(bH + bo), bl = tc::sdesc_k_sw128(bL + bo);
             tc::mma_tf32(d, ah, bh, idesc, q > 0 ? 1u : 0u);
-            tc::mma_tf32(d, ah, bl, idesc, 1u);
-            tc::mma_tf32(d, al, bh, idesc, 1u);
+            if (three) {  // 3xTF32: the two correction products
+              tc::mma_tf32(d, ah, bl, idesc, 1u);
+              tc::mma_tf32(d, al, bh, idesc, 1u);
+            }
           }
           tc::mma_commit(mdone0 + 8 * st);
         }
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
         tc::mma_commit(a_empty);
         ++k;
       }
-      if (!ok) cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+      if (!ok) set_status(cfg.W[set >> 1], ST_ERR_TIMEOUT);
       // every MMA of this CTA has completed before the tensor memory is freed
       tc::mma_commit(fin);
       tc::mbar_wait(fin, 0u, nullptr, 400000000LL);
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
         // every lane waits; the warp proceeds only if all lanes saw both phases
         // complete (tcgen05.ld is warp-wide)
         const bool mine =
-            tc::mbar_wait(full0 + 8 * st, u & 1u, abort_flag) && tc::mbar_wait(mdone0 + 8 * st, u & 1u, abort_flag);
+            tc::mbar_wait(full0 + 8 * st, u & 1u, abort_flag, cfg.wait_cycles) && tc::mbar_wait(mdone0 + 8 * st, u & 1u, abort_flag, cfg.wait_cycles);
         const bool okw = __all_sync(0xffffffffu, mine);
         if (okw) {
           tc::fence_after_sync();
@@ -276,10 +280,17 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
         }
       }
     }
-    if (stop && threadIdx.x == 0) cfg.W[set >> 1].status = ST_ERR_TIMEOUT;
+    if (stop && threadIdx.x == 0) set_status(cfg.W[set >> 1], ST_ERR_TIMEOUT);
     if (threadIdx.x == 0) tc::bulk_wait0();
   }
   __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) {
+    // an aborted CTA may have left any of its items undone: stop every walker it served
+    TcIter<typename L::Plan> it;
+    it.start(cfg, plan);
+    int set = 0, rb = 0;
+    while (it.next(cfg, set, rb)) set_status(cfg.W[set >> 1], ST_ERR_TIMEOUT);
+  }
   if (warp == 5) {
     __syncwarp();
     tc::fence_after_sync();
@@ -359,23 +370,13 @@ cudaError_t setup_update_tc() {
 
 int tc_tile_n(int ks) { return ks <= 64 ? 64 : 32; }
 
-static int g_num_sms = 0;
-
 void launch_upd_ops(const Config& cfg, cudaStream_t st) {
   const long long S = 2LL * cfg.n_walkers;
-  long long items = S * 64;
-  if (items > 4 * 152) items = 4 * 152;
-  k_upd_ops<<<(int)(items < 1 ? 1 : items), 256, 0, st>>>(cfg);
+  k_upd_ops<<<sm_grid(S * 64, 4), 256, 0, st>>>(cfg);
 }
 
 void launch_upd_tc(const Config& cfg, cudaStream_t st) {
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g_num_sms <= 0)
-      g_num_sms = 152;
-  }
-  const int grid = g_num_sms;
+  const int grid = device_sm_count();
   if (cfg.ks <= 32)
     k_upd_tc<64, 32><<<grid, 192, TcLayout<64, 32>::SMEM, st>>>(cfg);
   else if (cfg.ks <= 64)

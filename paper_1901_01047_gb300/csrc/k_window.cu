@@ -23,11 +23,13 @@
 #include <cstdio>
 
 #include <mutex>
+#include <type_traits>
 #include <unordered_map>
 
 #include "device_util.cuh"
 #include "kernels.h"
 #include "state.h"
+#include "tc_ptx.cuh"
 
 namespace dca {
 
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(128) k_begin(Config cfg) {
     for (int i = 0; i < s_len; ++i) c += (s_type[i] == 0);
     w.n_cand = c;
     if (s_n + c > s_cap) {
-      w.status = ST_ERR_CAPACITY;
+      set_status(w, ST_ERR_CAPACITY);
       w.active = 0;
     }
   }
@@ -215,12 +217,13 @@ __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
             reinterpret_cast<float*>(w.Vb[sp])[o] = v;
             reinterpret_cast<float*>(w.Ub[sp])[o] = u;
             if (Vop) {
-              const float hv = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+              float hv, lv, hu, lu;
+              tc::tf32_split(v, hv, lv);
+              tc::tf32_split(u, hu, lu);
               Vop[(size_t)c * ld + i] = hv;
-              Vop[(size_t)(KS_MAX + c) * ld + i] = v - hv;
-              const float hu = __uint_as_float(__float_as_uint(u) & 0xFFFFE000u);
+              Vop[(size_t)(KS_MAX + c) * ld + i] = lv;
               Uop[(size_t)c * ld + i] = hu;
-              Uop[(size_t)(KS_MAX + c) * ld + i] = u - hu;
+              Uop[(size_t)(KS_MAX + c) * ld + i] = lu;
             }
           } else {
             double v = 0.0, u = 0.0;
@@ -439,18 +442,11 @@ __device__ __forceinline__ double g_ext_at(const ExtView<T>& v, int x, int y, do
   return (nxy * ev - (x == y ? 1.0 : 0.0)) * rv;
 }
 
-// Arithmetic of the bordered growth of B^-1 (App. B): FP64 on the FP64 path;
-// on the mixed path double-float pairs (hi, lo) of FP32, about 44 significant
-// bits at the FP32 issue rate (FP64 issues at a small fraction of it on this
-// GPU).  The pairs are also the format in which the update kernels read B^-1.
-template <typename T>
-struct MetroScalar {
-  using type = double;
-};
-template <>
-struct MetroScalar<float> {
-  using type = float2;
-};
+// Arithmetic M of the bordered growth of B^-1 and of the Schur complements
+// (the determinant ratios): FP64 (double), or double-float pairs (hi, lo) of
+// FP32 (float2), about 44 significant bits at the FP32 issue rate.  The
+// update kernels of the mixed path read B^-1 as such pairs, so the FP64
+// variant on the mixed path converts B^-1 into them at the end of the window.
 
 __device__ __forceinline__ void m_set(double& r, double x) { r = x; }
 __device__ __forceinline__ void m_set(float2& r, double x) { r = df_split(x); }
@@ -489,9 +485,8 @@ constexpr int METRO_LIVE = 2048;  // live vertices whose rows and spins are stag
 // and (7) the bordered inverse [[B^-1 + t s, -t / d], [-s, 1 / d]].  Thread 0
 // plans proposal j + 1 (step 1) together with decision j, so a rejection
 // costs three block barriers and an acceptance four.
-template <typename T>
+template <typename T, typename M>
 __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
-  using M = typename MetroScalar<T>::type;
   WalkerDev& w = cfg.W[blockIdx.x];
   __shared__ int s_active;
   if (threadIdx.x == 0) s_active = w.active;
@@ -667,7 +662,7 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
         const double R = (s_kind == 0 ? K / (double)(kcur + 1) : (double)kcur / K) * d0 * d1;
         int acc = 0, tie = 0;
         if (!isfinite(R)) {
-          w.status = ST_ERR_NUMERIC;
+          set_status(w, ST_ERR_NUMERIC);
           s_stop = 1;
         } else {
           const double absR = fabs(R);
@@ -745,12 +740,17 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
 
   // Epilogue: window bookkeeping and the accepted set.
   const int l = s_l, nrem = s_nrem, nins = s_nins;
-  // B^-1 for the update kernels (FP64, or the FP32 pairs on the mixed path)
-  if (in_smem)
+  // B^-1 for the update kernels: FP64 on the FP64 path, FP32 pairs on the
+  // mixed path (converted in place, element by element, when the growth ran
+  // in FP64 in the global buffer)
+  constexpr bool to_pairs = sizeof(T) == 4 && sizeof(M) == 8 && !std::is_same<M, float2>::value;
+  if (in_smem || to_pairs)
     for (int sp = 0; sp < 2; ++sp)
       for (int idx = tid; idx < l * l; idx += blockDim.x) {
         const int i = idx / l, jj = idx - i * l;
-        reinterpret_cast<M*>(w.Binv[sp])[(size_t)i * KS_MAX + jj] = Binv[sp][(size_t)i * bst + jj];
+        const M b = Binv[sp][(size_t)i * bst + jj];
+        if (to_pairs) reinterpret_cast<float2*>(w.Binv[sp])[(size_t)i * KS_MAX + jj] = df_split(m_val(b));
+        else reinterpret_cast<M*>(w.Binv[sp])[(size_t)i * KS_MAX + jj] = b;
       }
   for (int p = tid; p < l; p += blockDim.x) {
     w.P[p] = s_P[p];
@@ -798,9 +798,16 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
         w.recompute_pending = 1;
         w.windows_since_recompute = 0;
       }
+      // Fresh N for every measurement: the recompute runs in the window that
+      // ends the sweep, before the measurement.
+      if (cfg.recompute_at_measure && w.measure_pending) {
+        w.recompute_pending = 1;
+        w.windows_since_recompute = 0;
+      }
       // Algorithmic work per spin on the k live vertices after the window:
       // update 2 k^2 l + 2 k l^2 flop, reading and writing k^2 entries of N
-      // plus the k x l factors; extension 4 k0^2 c flop reading N twice.
+      // plus the k x l factors; extension 4 k0^2 c flop and one read of N (both
+      // candidate products need only that one read).
       const double b = cfg.prec == PREC_MIXED ? 4.0 : 8.0;
       const double kk = (double)(n_live - nrem + nins), ll = (double)l;
       if (l > 0) {
@@ -810,7 +817,7 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
       const double k0 = (double)n_live, cc = (double)w.n_cand;
       if (w.n_cand > 0) {
         w.ext_flops += 2.0 * (4.0 * k0 * k0 * cc);
-        w.ext_bytes += 2.0 * b * (2.0 * k0 * k0);
+        w.ext_bytes += 2.0 * b * (k0 * k0);
       }
     } else {
       w.active = 0;
@@ -1232,6 +1239,7 @@ __global__ void k_loop_control(Config cfg, cudaGraphConditionalHandle handle, Lo
   __syncthreads();
   if (threadIdx.x == 0) {
     ls->iters++;
+    ls->total_iters++;
     unsigned int cont = s_cnt > 0 ? 1u : 0u;
     if (cont && ls->iters >= ls->max_iters) {
       ls->timed_out = 1;
@@ -1244,14 +1252,28 @@ __global__ void k_loop_control(Config cfg, cudaGraphConditionalHandle handle, Lo
 __global__ void k_loop_reset(LoopState* ls, int64_t max_iters) {
   ls->iters = 0;
   ls->max_iters = max_iters;
-  ls->timed_out = 0;
 }
 
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
-// Persistent grids: a few blocks per SM walk the flattened work of all walkers.
-constexpr int PERSIST_BLOCKS = 4 * 152;
+int device_sm_count() {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 64 && cache[dev] > 0) return cache[dev];
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  if (dev < 64) cache[dev] = sms;
+  return sms;
+}
+
+int sm_grid(long long items, int per_sm) {
+  const long long total = (long long)per_sm * device_sm_count();
+  return (int)(items < 1 ? 1 : (items < total ? items : total));
+}
 
 int persist_grid(const void* fn, long long items, int block, size_t smem) {
   static std::mutex mu;
@@ -1268,18 +1290,16 @@ int persist_grid(const void* fn, long long items, int block, size_t smem) {
           cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem) != cudaSuccess)
         per_sm = 0;
-      total = (per_sm > 0 && sms > 0) ? per_sm * sms : PERSIST_BLOCKS;
+      total = (per_sm > 0 && sms > 0) ? per_sm * sms : 4 * device_sm_count();
       cache.emplace(fn, total);
     }
   }
   return (int)(items < 1 ? 1 : (items < total ? items : total));
 }
 
-// Grid of a persistent kernel: at most PERSIST_BLOCKS, at most the largest
+// Grid of a persistent kernel: four blocks per SM, at most the largest
 // possible number of work items.
-static int grid_for(long long items) {
-  return (int)(items < 1 ? 1 : (items < PERSIST_BLOCKS ? items : PERSIST_BLOCKS));
-}
+static int grid_for(long long items) { return sm_grid(items, 4); }
 
 template <typename T, typename A>
 static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_t st) {
@@ -1303,7 +1323,8 @@ static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_
       return 3;
     case GROUP_METROPOLIS: {
       const int sm = cfg.ks <= METRO_SMEM_KS ? (int)sizeof(double) * 2 * cfg.ks * (cfg.ks | 1) : 0;
-      k_metropolis<T><<<W, 256, sm, st>>>(cfg);
+      if (sizeof(T) == 8 || cfg.gamma_fp64) k_metropolis<T, double><<<W, 256, sm, st>>>(cfg);
+      else k_metropolis<T, float2><<<W, 256, sm, st>>>(cfg);
       return 1;
     }
     case GROUP_UPDATE_PRE:
@@ -1339,8 +1360,12 @@ cudaError_t setup_window_kernels() {
     e = cudaFuncSetAttribute(k_cand_ext<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              ext_smem_bytes<float>());
   const int msm = (int)sizeof(double) * 2 * METRO_SMEM_KS * (METRO_SMEM_KS | 1);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_metropolis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, msm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_metropolis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, msm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_metropolis<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, msm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_metropolis<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, msm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_metropolis<float, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, msm);
   return e;
 }
 

@@ -23,12 +23,16 @@ enum Group : int {
   N_GROUPS = 10,
 };
 
-// Launch order of the groups in one window (the recompute groups only when
-// a recompute period is set).
-constexpr int WINDOW_GROUPS[] = {GROUP_PROPOSE,    GROUP_EXTEND,      GROUP_METROPOLIS, GROUP_UPDATE_PRE,
-                                 GROUP_UPDATE,     GROUP_UPDATE_POST, GROUP_MEASURE,    GROUP_RECOMPUTE_PRE,
-                                 GROUP_RECOMPUTE,  GROUP_RECOMPUTE_POST};
-constexpr int N_WINDOW_GROUPS_NO_RECOMPUTE = 7;
+// Launch order of the groups in one window.  The recompute (when a period
+// is set) comes before the measurement, so a sweep whose last window also
+// recomputes N is measured on the recomputed N.
+constexpr int WINDOW_GROUPS[] = {GROUP_PROPOSE,       GROUP_EXTEND,    GROUP_METROPOLIS,     GROUP_UPDATE_PRE,
+                                 GROUP_UPDATE,        GROUP_UPDATE_POST, GROUP_RECOMPUTE_PRE, GROUP_RECOMPUTE,
+                                 GROUP_RECOMPUTE_POST, GROUP_MEASURE};
+constexpr int N_WINDOW_GROUPS = (int)(sizeof(WINDOW_GROUPS) / sizeof(int));
+inline bool is_recompute_group(int g) {
+  return g == GROUP_RECOMPUTE_PRE || g == GROUP_RECOMPUTE || g == GROUP_RECOMPUTE_POST;
+}
 
 // Kernel attributes (dynamic shared memory limits); call once per process
 // and device before any launch or stream capture.
@@ -41,6 +45,9 @@ void launch_loop_control(const Config& cfg, cudaGraphConditionalHandle handle, L
 void launch_loop_reset(LoopState* ls, int64_t max_iters, cudaStream_t st);
 void launch_add_target(const Config& cfg, int64_t n_sweeps, cudaStream_t st);
 void launch_init(const Config& cfg, int n0, int max_cap, int* d_sgn, cudaStream_t st);
+// N of every walker from scratch for the vertex list of its current buffer
+// (live rows 0 .. n-1), and the configuration sign.
+void launch_rebuild(const Config& cfg, int max_n, int* d_sgn, cudaStream_t st);
 void launch_fresh_inverse(const Config& cfg, int max_n, int* d_sgn, cudaStream_t st);
 // Gauss-Jordan inverse of the FP64 work matrices, one 8-block cluster each.
 void launch_gj(const Config& cfg, int mode, int max_n, int* d_sgn, cudaStream_t st);
@@ -52,6 +59,13 @@ void launch_refine_adopt(const Config& cfg, int max_cap, cudaStream_t st);
 // part: GROUP_RECOMPUTE_PRE, GROUP_RECOMPUTE or GROUP_RECOMPUTE_POST.
 int launch_recompute(int part, const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st);
 int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
+
+// Streaming multiprocessors of the current device (queried once per device;
+// 1 if the query fails, which only makes the persistent grids smaller).
+int device_sm_count();
+// Grid of a persistent kernel without an occupancy query: `per_sm` blocks per
+// SM of the current device, at most `items`.
+int sm_grid(long long items, int per_sm);
 
 // Grid of a persistent item kernel (for_each_item): as many blocks as the SMs
 // hold at once (occupancy of `fn` at `block` threads and `smem` dynamic bytes,
@@ -71,7 +85,9 @@ void launch_ext_g_tc(const Config& cfg, cudaStream_t st);
 void launch_ext_x_tc(const Config& cfg, cudaStream_t st);
 void launch_upd_ops(const Config& cfg, cudaStream_t st);
 void launch_upd_tc(const Config& cfg, cudaStream_t st);
-void launch_negate(const double* src, double* dst, float* dstf, size_t n, cudaStream_t st);
+// g0 = -G0 (FP64 and FP32) from a staged G0, unless an entry is not finite:
+// then *bad = 1 and the old table is kept.
+void launch_negate(const double* src, double* dst, float* dstf, size_t n, int* bad, cudaStream_t st);
 // Phase table of the measurement grid (ProblemDev::g0m) from the FP32 table g0f.
 void launch_meas_table(const ProblemDev& pd, int n_tau_meas, cudaStream_t st);
 void launch_g0_isolated(int nc, const double* d_eps, const double* d_kr, double mu_eff, double beta, int n_tau,

@@ -147,10 +147,20 @@ struct WalkerDev {
   double* bvec;              // [2][nc][cap]
 };
 
-// Iteration state of the device-side window loop.
+#ifdef __CUDACC__
+// A walker keeps its first error: later kernels of the same window may meet
+// the consequences of the first failure, which would hide its cause.
+__device__ __forceinline__ void set_status(WalkerDev& w, int32_t code) { atomicCAS(&w.status, (int32_t)ST_OK, code); }
+#endif
+
+// Iteration state of the device-side window loop.  iters and max_iters are
+// reset by every sweep call; total_iters only grows and timed_out stays set
+// until the host has read it (the calls are stream-ordered and the host
+// checks at its next synchronisation).
 struct LoopState {
   int64_t iters;
   int64_t max_iters;
+  int64_t total_iters;
   int32_t timed_out;
   int32_t pad;
 };
@@ -200,6 +210,10 @@ struct Config {
   int32_t* gj_next;          // [1] next matrix of the Gauss-Jordan work queue (reset by k_build_A)
   int32_t pooled;            // pooled schedule (else lockstep sweeps)
   PoolState* pool;           // [1] target and go flag of the pooled schedule (all walkers)
+  int32_t gamma_fp64;        // mixed path: B^-1 and the Schur complements in FP64 (else double-float)
+  int32_t tf32_terms;        // products per K step of the tensor-core kernels: 3 (3xTF32) or 1 (TF32)
+  long long wait_cycles;     // bound of every mbarrier wait in the tensor-core kernels (SM clocks)
+  int32_t recompute_at_measure;  // recompute N in the window of every measurement (before it)
 };
 
 }  // namespace dca

@@ -40,6 +40,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking test of the phase (never suspends the thread).
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounds below this many SM clocks are polled with the non-blocking test, the
+// clock read after every try (try_wait may suspend the thread for a
+// hardware-defined time, longer than such a bound).
+constexpr long long kShortWaitCycles = 1000000LL;
+
 // Wait for the phase with the given parity to complete.  Gives up after
 // about `limit_cycles` SM clocks, or early when *abort is set by another role
 // (polled every 64 tries); returns false then, setting *abort itself on a
@@ -47,6 +65,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
                                           long long limit_cycles = 4000000000LL) {
   const long long t0 = clock64();
+  if (limit_cycles < kShortWaitCycles) {
+    for (uint32_t it = 1;; ++it) {
+      if (mbar_test_wait(bar, parity)) return true;
+      if ((it & 63u) == 0u && abort && *abort) return false;
+      if (clock64() - t0 > limit_cycles) {
+        if (abort) *abort = 1;
+        return false;
+      }
+    }
+  }
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 63u) == 0u) {
@@ -174,12 +202,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Split an FP32 value into a TF32 head (rounded to 10 explicit mantissa bits)
-// and the exact FP32 remainder.
+// An FP32 value rounded to TF32 (10 explicit mantissa bits): half a TF32
+// unit added to the magnitude bits, the 13 low bits cleared (round to
+// nearest, ties away from zero).  The tensor core reads only these bits of an
+// FP32 operand, so an operand that is not already TF32 would be truncated.
+__device__ __forceinline__ float tf32_round(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// Split an FP32 value into two TF32 values, hi = tf32(x) and lo = tf32(x - hi)
+// (x - hi is exact in FP32): hi + lo carries x to about 2^-22 of |x|, and each
+// of hi*hi, hi*lo, lo*hi is exact in FP32.
 __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
-  const uint32_t u = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
-  hi = __uint_as_float(u);
-  lo = x - hi;
+  hi = tf32_round(x);
+  lo = tf32_round(x - hi);
 }
 
 }  // namespace tc

@@ -45,7 +45,8 @@ struct dca_walker {
   std::vector<uint8_t*> forced;     // per walker replay buffers
   WalkerDev* d_W = nullptr;
   ProblemDev* d_P = nullptr;
-  int* d_active = nullptr;          // [8]: active count, -, -, work queues of the inverse (3 .. 6)
+  int* d_active = nullptr;          // [8]: active count, -, -, work queues of the inverse (3 .. 6),
+                                    // rejected-G0 flag (7)
   int* h_active = nullptr;          // pinned
   int* d_sgn = nullptr;
   dca::Config cfg{};
@@ -70,8 +71,15 @@ struct dca_walker {
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;
   dca::LoopState* d_loop = nullptr;
+  dca::LoopState* h_loop = nullptr;  // pinned copy read at synchronisation points
   dca::PoolState* d_pool = nullptr;  // pooled schedule: sweep target and go flag
   int kernels_per_window = 0;
+  int64_t loop_iters_seen = 0;       // window-loop iterations already counted
+  bool timeout_pending = false;      // a window loop hit its bound since the last dca_walker_sync
+  bool g0_rejected = false;          // an update_G0 table had a non-finite entry (reported by sync)
+  int64_t max_windows = 0;           // cap of the windows of one sweep call (0 = automatic)
+  int prec_public = 0;               // DCA_PREC_* given at create
+  std::vector<int> problem_of;       // per walker
 
   ~dca_walker() {
     if (stream) cudaStreamSynchronize(stream);
@@ -88,6 +96,7 @@ struct dca_walker {
     for (uint8_t* p : forced)
       if (p) cudaFree(p);
     if (h_active) cudaFreeHost(h_active);
+    if (h_loop) cudaFreeHost(h_loop);
   }
 
   void* dalloc(size_t bytes) {
@@ -141,6 +150,9 @@ extern "C" DCA_API int dca_g0_isolated_cluster(int32_t nc, const double* eps_K, 
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Bound of the mbarrier waits of the tensor-core kernels: about two seconds of SM clocks.
+constexpr long long kDefaultWaitCycles = 4000000000LL;
+
 static int upload_update_maps(dca_walker* h, int ks);
 
 extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cuda_stream, dca_walker** out) {
@@ -152,10 +164,20 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   if (p.n_walkers < 1) return fail(nullptr, DCA_ERR_ARG, "n_walkers must be >= 1");
   if (p.k_sub < 1 || p.k_sub > dca::KS_MAX) return fail(nullptr, DCA_ERR_ARG, "k_sub must be in 1..128");
   if (p.recompute_sweeps < 0 || p.recompute_every < 0 || p.warmup_sweeps < 0 || p.n_tau_meas < 1 || p.init_config_size < 0 ||
-      p.capacity < 0 || p.log_capacity < 0)
+      p.capacity < 0 || p.log_capacity < 0 || p.recompute_at_measure < 0 || p.recompute_at_measure > 1)
     return fail(nullptr, DCA_ERR_ARG, "negative or zero size parameter");
-  if (p.precision != DCA_PREC_FP64 && p.precision != DCA_PREC_MIXED)
+  if (p.precision != DCA_PREC_FP64 && p.precision != DCA_PREC_MIXED && p.precision != DCA_PREC_TF32)
     return fail(nullptr, DCA_ERR_ARG, "unsupported precision");
+  if (p.precision == DCA_PREC_TF32 && p.update_kernel == DCA_UPD_CUDA_CORE)
+    return fail(nullptr, DCA_ERR_ARG, "DCA_PREC_TF32 runs on the tensor cores only");
+  if (p.gamma_precision != DCA_GAMMA_FP64 && p.gamma_precision != DCA_GAMMA_DOUBLE_FLOAT)
+    return fail(nullptr, DCA_ERR_ARG, "gamma_precision must be one of DCA_GAMMA_*");
+  if (p.recompute_method < DCA_RECOMPUTE_AUTO || p.recompute_method > DCA_RECOMPUTE_GJ)
+    return fail(nullptr, DCA_ERR_ARG, "recompute_method must be one of DCA_RECOMPUTE_*");
+  if (p.update_kernel < DCA_UPD_AUTO || p.update_kernel > DCA_UPD_TCGEN05)
+    return fail(nullptr, DCA_ERR_ARG, "update_kernel must be one of DCA_UPD_*");
+  if (p.schedule < DCA_SCHEDULE_LOCKSTEP || p.schedule > DCA_SCHEDULE_POOLED)
+    return fail(nullptr, DCA_ERR_ARG, "schedule must be one of DCA_SCHEDULE_*");
   for (int i = 0; i < p.n_problems; ++i) {
     std::string why;
     if (dca::check_problem(p.problems[i], why) != DCA_OK)
@@ -180,7 +202,8 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->warmup = p.warmup_sweeps;
   h->R = p.recompute_every;
   h->ntm = p.n_tau_meas;
-  h->precision = p.precision;
+  h->prec_public = p.precision;
+  h->precision = p.precision == DCA_PREC_FP64 ? DCA_PREC_FP64 : DCA_PREC_MIXED;  // storage of N
   h->tie_eps = p.tie_eps > 0.0 ? p.tie_eps : 1e-10;
 
   // ---- problems ----
@@ -213,7 +236,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     d.g0 = (const double*)dg;
     d.g0f = (const float*)dgf;
     const int q = (p.n_tau_meas > 0 && d.n_tau % p.n_tau_meas == 0) ? d.n_tau / p.n_tau_meas : 0;
-    if (p.precision == DCA_PREC_MIXED && q >= 2 && q % 2 == 0) {
+    if (h->precision == DCA_PREC_MIXED && q >= 2 && q % 2 == 0) {
       void* dgm = h->dalloc(sizeof(float) * 2 * (size_t)q * pr.nc * (p.n_tau_meas + 1));
       if (!dgm) {
         h->err = "device allocation of the measurement phase table";
@@ -246,24 +269,13 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
 
   // ---- walkers ----
   const int KS = dca::KS_MAX;
-  if (p.recompute_method < DCA_RECOMPUTE_AUTO || p.recompute_method > DCA_RECOMPUTE_GJ) {
-    h->err = "recompute_method must be one of DCA_RECOMPUTE_*";
-    return bail(DCA_ERR_ARG);
-  }
-  if (p.update_kernel < DCA_UPD_AUTO || p.update_kernel > DCA_UPD_TCGEN05) {
-    h->err = "update_kernel must be one of DCA_UPD_*";
-    return bail(DCA_ERR_ARG);
-  }
-  if (p.schedule < DCA_SCHEDULE_LOCKSTEP || p.schedule > DCA_SCHEDULE_POOLED) {
-    h->err = "schedule must be one of DCA_SCHEDULE_*";
-    return bail(DCA_ERR_ARG);
-  }
   // The tensor-core operands exist on every mixed-precision walker, so the
   // update kernel can be switched by dca_walker_set_tuning.
-  const bool use_tc = p.precision == DCA_PREC_MIXED && p.update_kernel != DCA_UPD_CUDA_CORE;
-  const bool alloc_tc = p.precision == DCA_PREC_MIXED;
+  const bool use_tc = h->precision == DCA_PREC_MIXED && p.update_kernel != DCA_UPD_CUDA_CORE;
+  const bool alloc_tc = h->precision == DCA_PREC_MIXED;
   h->h_W.resize(h->W);
   h->nc_of.resize(h->W);
+  h->problem_of.resize(h->W);
   h->gacc_off.resize(h->W);
   h->forced.assign(h->W, nullptr);
   size_t goff = 0;
@@ -283,6 +295,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     }
     h->max_cap = std::max(h->max_cap, cap);
     h->nc_of[wi] = pr.nc;
+    h->problem_of[wi] = pi;
     h->gacc_off[wi] = goff;
     goff += (size_t)2 * pr.nc * p.n_tau_meas;
 
@@ -297,7 +310,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     w.log_cap = p.log_capacity;
     const size_t C = (size_t)cap;
     const int nc = pr.nc;
-    const size_t esz = p.precision == DCA_PREC_MIXED ? sizeof(float) : sizeof(double);  // N and R
+    const size_t esz = h->precision == DCA_PREC_MIXED ? sizeof(float) : sizeof(double);  // N and R
     // one allocation per walker, carved into 256-byte aligned pieces
     struct Piece {
       void** dst;
@@ -310,7 +323,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
       pieces.push_back({(void**)&w.vs[par], sizeof(int32_t) * C});
       for (int sp = 0; sp < 2; ++sp) pieces.push_back({(void**)&w.N[par][sp], esz * C * C});
     }
-    if (p.precision == DCA_PREC_MIXED)
+    if (h->precision == DCA_PREC_MIXED)
       for (int sp = 0; sp < 2; ++sp) pieces.push_back({(void**)&w.Ascr[sp], sizeof(double) * C * C});
     pieces.push_back({(void**)&w.prop, sizeof(dca::Proposal) * KS});
     for (int sp = 0; sp < 2; ++sp) {
@@ -376,7 +389,8 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     h->err = "device allocation of walker records";
     return bail(DCA_ERR_OOM);
   }
-  if (cudaMemcpy(h->d_W, h->h_W.data(), sizeof(WalkerDev) * h->W, cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (cudaMemset(h->d_active, 0, sizeof(int) * 8) != cudaSuccess ||
+      cudaMemcpy(h->d_W, h->h_W.data(), sizeof(WalkerDev) * h->W, cudaMemcpyHostToDevice) != cudaSuccess) {
     h->err = "upload of walker records";
     return bail(DCA_ERR_CUDA);
   }
@@ -385,7 +399,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.warmup = h->warmup;
   h->cfg.recompute_every = h->R;
   h->cfg.n_tau_meas = h->ntm;
-  h->cfg.prec = p.precision == DCA_PREC_MIXED ? dca::PREC_MIXED : dca::PREC_FP64;
+  h->cfg.prec = h->precision == DCA_PREC_MIXED ? dca::PREC_MIXED : dca::PREC_FP64;
   h->cfg.tie_eps = h->tie_eps;
   h->cfg.W = h->d_W;
   h->cfg.P = h->d_P;
@@ -398,6 +412,10 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.tmaps = h->d_tmaps;
   h->cfg.pooled = p.schedule == DCA_SCHEDULE_POOLED ? 1 : 0;
   h->cfg.pool = h->d_pool;
+  h->cfg.gamma_fp64 = p.gamma_precision == DCA_GAMMA_FP64 ? 1 : 0;
+  h->cfg.tf32_terms = p.precision == DCA_PREC_TF32 ? 1 : 3;
+  h->cfg.wait_cycles = kDefaultWaitCycles;
+  h->cfg.recompute_at_measure = p.recompute_at_measure ? 1 : 0;
 
   if (dca::setup_window_kernels() != cudaSuccess) {
     h->err = "kernel attribute setup failed";
@@ -442,9 +460,42 @@ static int status_code(int st) {
   }
 }
 
+// Synchronise the stream and read the walker records, taking stock of the
+// device-side window loops run since the last look: their kernel launches,
+// and whether a loop hit its iteration bound (kept in h->timeout_pending for
+// dca_walker_sync; the device flag is cleared once read).
 static int pull_records(dca_walker* h) {
+  if (h->d_loop)
+    CK(cudaMemcpyAsync(h->h_loop, h->d_loop, sizeof(dca::LoopState), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(h->h_W.data(), h->d_W, sizeof(WalkerDev) * h->W, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_active + 1, h->d_active + 7, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (h->h_active[1]) {  // an update_G0 table was rejected on the device
+    h->g0_rejected = true;
+    CK(cudaMemsetAsync(h->d_active + 7, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  if (h->d_loop) {
+    const int64_t it = h->h_loop->total_iters - h->loop_iters_seen;
+    h->loop_iters_seen = h->h_loop->total_iters;
+    h->windows_launched += it;
+    h->total_launches += it * h->kernels_per_window;
+    if (h->h_loop->timed_out) {
+      h->timeout_pending = true;
+      const int32_t zero = 0;
+      CK(cudaMemcpyAsync(&h->d_loop->timed_out, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    }
+  }
+  return DCA_OK;
+}
+
+// First walker error of the pulled records, as a return code with a message.
+static int walker_errors(dca_walker* h) {
+  for (int wi = 0; wi < h->W; ++wi)
+    if (h->h_W[wi].status != dca::ST_OK)
+      return fail(h, status_code(h->h_W[wi].status),
+                  "walker " + std::to_string(wi) + " stopped with status " + std::to_string(h->h_W[wi].status));
   return DCA_OK;
 }
 
@@ -463,9 +514,9 @@ static cudaEvent_t next_event(dca_walker* h) {
   return h->ev_pool[h->ev_used++];
 }
 
-static int n_window_groups(const dca_walker* h) {
-  return (h->R > 0 || h->cfg.recompute_sweeps > 0) ? (int)(sizeof(dca::WINDOW_GROUPS) / sizeof(int))
-                                                   : dca::N_WINDOW_GROUPS_NO_RECOMPUTE;
+// Whether a window launches the recompute groups (some recompute schedule is set).
+static bool has_recompute(const dca_walker* h) {
+  return h->R > 0 || h->cfg.recompute_sweeps > 0 || h->cfg.recompute_at_measure;
 }
 
 // Launch one kernel group, bracketed by events when its timing bit is set.
@@ -514,8 +565,9 @@ static int window_branches(int W) { return W >= 128 ? 4 : (W >= 32 ? 2 : 1); }
 // One window's kernel sequence for the walkers of cfg on stream st.
 static int launch_window_sequence(dca_walker* h, const dca::Config& cfg, cudaStream_t st) {
   int k = 0;
-  for (int i = 0; i < n_window_groups(h); ++i) {
+  for (int i = 0; i < dca::N_WINDOW_GROUPS; ++i) {
     const int g = dca::WINDOW_GROUPS[i];
+    if (dca::is_recompute_group(g) && !has_recompute(h)) continue;
     if (g == dca::GROUP_MEASURE)
       k += dca::launch_measure(cfg, h->max_cap, h->max_nc, st);
     else if (g == dca::GROUP_RECOMPUTE_PRE || g == dca::GROUP_RECOMPUTE || g == dca::GROUP_RECOMPUTE_POST)
@@ -534,6 +586,9 @@ static int build_loop_graph(dca_walker* h) {
   if (!h->d_loop) {
     h->d_loop = (dca::LoopState*)h->dalloc(sizeof(dca::LoopState));
     if (!h->d_loop) return fail(h, DCA_ERR_OOM, "loop state allocation");
+    if (!h->h_loop && cudaMallocHost(&h->h_loop, sizeof(dca::LoopState)) != cudaSuccess)
+      return fail(h, DCA_ERR_OOM, "pinned loop state");
+    CK(cudaMemsetAsync(h->d_loop, 0, sizeof(dca::LoopState), h->stream));
   }
   if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   CK(cudaGraphCreate(&h->loop_graph, 0));
@@ -583,40 +638,44 @@ static int build_loop_graph(dca_walker* h) {
   return DCA_OK;
 }
 
+// Enqueue n_sweeps of the device-side window loop: the sweep target, the
+// loop's iteration bound and one graph launch, all stream-ordered.
 static int sweep_graph(dca_walker* h, int32_t n_sweeps) {
   int rc = build_loop_graph(h);
   if (rc != DCA_OK) return rc;
   // Every window advances each active walker by >= 1 proposal and a sweep is
   // at most `capacity` proposals, so this bound is never reached normally.
-  const int64_t max_iters = (int64_t)n_sweeps * (int64_t)(h->max_cap + 1) + 64;
+  int64_t max_iters = (int64_t)n_sweeps * (int64_t)(h->max_cap + 1) + 64;
+  if (h->max_windows > 0 && h->max_windows < max_iters) max_iters = h->max_windows;
   dca::launch_add_target(h->cfg, n_sweeps, h->stream);
   dca::launch_loop_reset(h->d_loop, max_iters, h->stream);
   CK(cudaGetLastError());
   CK(cudaGraphLaunch(h->loop_exec, h->stream));
-  dca::LoopState ls;
-  CK(cudaMemcpyAsync(&ls, h->d_loop, sizeof(ls), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  h->windows_launched += ls.iters;
-  h->total_launches += 2 + ls.iters * h->kernels_per_window;
-  if (ls.timed_out) return fail(h, DCA_ERR_TIMEOUT, "window loop reached its iteration bound");
+  h->total_launches += 2;
   return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_sync(dca_walker* h) {
+  if (!h) return DCA_ERR_ARG;
+  int rc = pull_records(h);
+  if (rc != DCA_OK) return rc;
+  if (h->g0_rejected) {
+    h->g0_rejected = false;
+    return fail(h, DCA_ERR_ARG, "a G0 table given to dca_walker_update_G0 had a non-finite entry; the previous "
+                                "table was kept");
+  }
+  if (h->timeout_pending) {
+    h->timeout_pending = false;
+    return fail(h, DCA_ERR_TIMEOUT, "window loop reached its iteration bound");
+  }
+  return walker_errors(h);
 }
 
 extern "C" DCA_API int dca_walker_sweep(dca_walker* h, int32_t n_sweeps) {
   if (!h) return DCA_ERR_ARG;
   if (n_sweeps < 0) return fail(h, DCA_ERR_ARG, "n_sweeps < 0");
   if (n_sweeps == 0) return DCA_OK;
-  if (h->timing_mask == 0) {
-    int rc = sweep_graph(h, n_sweeps);
-    if (rc != DCA_OK) return rc;
-    rc = pull_records(h);
-    if (rc != DCA_OK) return rc;
-    for (int wi = 0; wi < h->W; ++wi)
-      if (h->h_W[wi].status != dca::ST_OK)
-        return fail(h, status_code(h->h_W[wi].status),
-                    "walker " + std::to_string(wi) + " stopped with status " + std::to_string(h->h_W[wi].status));
-    return DCA_OK;
-  }
+  if (h->timing_mask == 0) return sweep_graph(h, n_sweeps);
   // Timed kernel groups: host-driven loop with CUDA events around each group
   // (event nodes are not allowed inside conditional graph bodies).
   dca::launch_add_target(h->cfg, n_sweeps, h->stream);
@@ -625,7 +684,8 @@ extern "C" DCA_API int dca_walker_sweep(dca_walker* h, int32_t n_sweeps) {
   int chunk = 2;
   for (;;) {
     for (int i = 0; i < chunk; ++i)
-      for (int j = 0; j < n_window_groups(h); ++j) run_group(h, dca::WINDOW_GROUPS[j]);
+      for (int j = 0; j < dca::N_WINDOW_GROUPS; ++j)
+        if (!dca::is_recompute_group(dca::WINDOW_GROUPS[j]) || has_recompute(h)) run_group(h, dca::WINDOW_GROUPS[j]);
     h->windows_launched += chunk;
     CK(cudaGetLastError());
     dca::launch_count_active(h->cfg, h->stream);
@@ -638,10 +698,40 @@ extern "C" DCA_API int dca_walker_sweep(dca_walker* h, int32_t n_sweeps) {
   }
   int rc = pull_records(h);
   if (rc != DCA_OK) return rc;
-  for (int wi = 0; wi < h->W; ++wi)
-    if (h->h_W[wi].status != dca::ST_OK)
-      return fail(h, status_code(h->h_W[wi].status),
-                  "walker " + std::to_string(wi) + " stopped with status " + std::to_string(h->h_W[wi].status));
+  return walker_errors(h);
+}
+
+// Drop the captured window loop (it holds the launch configuration by value);
+// the next sweep captures it again.
+static void drop_loop_graph(dca_walker* h) {
+  pull_records(h);  // count the windows of the old graph with its kernels per window
+  if (h->loop_exec) {
+    cudaGraphExecDestroy(h->loop_exec);
+    h->loop_exec = nullptr;
+  }
+  if (h->loop_graph) {
+    cudaGraphDestroy(h->loop_graph);
+    h->loop_graph = nullptr;
+  }
+}
+
+extern "C" DCA_API int dca_walker_set_schedule(dca_walker* h, int32_t schedule) {
+  if (!h) return DCA_ERR_ARG;
+  if (schedule < DCA_SCHEDULE_LOCKSTEP || schedule > DCA_SCHEDULE_POOLED)
+    return fail(h, DCA_ERR_ARG, "schedule must be one of DCA_SCHEDULE_*");
+  CK(cudaStreamSynchronize(h->stream));
+  h->cfg.pooled = schedule == DCA_SCHEDULE_POOLED ? 1 : 0;
+  drop_loop_graph(h);
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_set_limits(dca_walker* h, int64_t max_windows, int64_t wait_cycles) {
+  if (!h) return DCA_ERR_ARG;
+  if (max_windows < 0 || wait_cycles < 0) return fail(h, DCA_ERR_ARG, "negative limit");
+  CK(cudaStreamSynchronize(h->stream));
+  h->max_windows = max_windows;
+  h->cfg.wait_cycles = wait_cycles > 0 ? (long long)wait_cycles : kDefaultWaitCycles;
+  drop_loop_graph(h);
   return DCA_OK;
 }
 
@@ -661,15 +751,7 @@ extern "C" DCA_API int dca_walker_set_tuning(dca_walker* h, int32_t k_sub, int32
   h->cfg.ks = k_sub;
   h->cfg.upd_kernel = tc ? dca::UPD_TCGEN05 : dca::UPD_CUDA_CORE;
   h->cfg.ext_tc = tc ? 1 : 0;
-  // the captured window loop holds the old launch configuration
-  if (h->loop_exec) {
-    cudaGraphExecDestroy(h->loop_exec);
-    h->loop_exec = nullptr;
-  }
-  if (h->loop_graph) {
-    cudaGraphDestroy(h->loop_graph);
-    h->loop_graph = nullptr;
-  }
+  drop_loop_graph(h);
   return DCA_OK;
 }
 
@@ -682,7 +764,8 @@ extern "C" DCA_API int dca_walker_set_timing(dca_walker* h, uint32_t group_mask)
 extern "C" DCA_API int dca_walker_get_timing(dca_walker* h, double* group_ms, int64_t* group_launches,
                                              int64_t* total_launches, int32_t reset) {
   if (!h) return DCA_ERR_ARG;
-  CK(cudaStreamSynchronize(h->stream));
+  const int rc = pull_records(h);
+  if (rc != DCA_OK) return rc;
   collect_events(h);
   for (int g = 0; g < dca::N_GROUPS; ++g) {
     if (group_ms) group_ms[g] = h->group_ms[g];
@@ -703,10 +786,11 @@ extern "C" DCA_API int dca_walker_update_G0(dca_walker* h, int32_t problem, cons
   if (!h || problem < 0 || problem >= (int)h->h_P.size() || !G0) return DCA_ERR_ARG;
   const ProblemDev& pd = h->h_P[problem];
   const size_t tsz = (size_t)2 * pd.nc * (pd.n_tau + 1);
-  for (size_t t = 0; t < tsz; ++t)
-    if (!std::isfinite(G0[t])) return fail(h, DCA_ERR_ARG, "G0 has a non-finite entry");
   CK(cudaMemcpyAsync(h->g0_stage[problem], G0, sizeof(double) * tsz, cudaMemcpyHostToDevice, h->stream));
-  dca::launch_negate(h->g0_stage[problem], const_cast<double*>(pd.g0), const_cast<float*>(pd.g0f), tsz, h->stream);
+  // validated on the device (a table with a non-finite entry is not committed;
+  // the next synchronisation reports it)
+  dca::launch_negate(h->g0_stage[problem], const_cast<double*>(pd.g0), const_cast<float*>(pd.g0f), tsz,
+                     h->d_active + 7, h->stream);
   h->total_launches += 1;
   if (pd.meas_q > 0) {
     dca::launch_meas_table(pd, h->ntm, h->stream);
@@ -850,6 +934,232 @@ extern "C" DCA_API int dca_walker_set_forced_decisions(dca_walker* h, int32_t wi
     w.forced_n = n;
   }
   return push_records(h);
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume.  Layout: SaveHeader, then per walker a SaveWalker
+// record, its k vertices (SaveVertex) and its G accumulator [2][nc][n_tau_meas]
+// (FP64), all little-endian host structs of fixed layout.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr uint32_t kSaveMagic = 0x57414344u;  // "DCAW"
+constexpr uint32_t kSaveVersion = 1u;
+
+struct SaveHeader {
+  uint32_t magic, version;
+  int32_t n_walkers, precision, n_tau_meas, warmup;
+  uint64_t bytes;  // total size of the checkpoint
+};
+
+struct SaveWalker {
+  int32_t problem, nc, k, status;
+  int32_t windows_since_recompute, pad;
+  uint64_t q;
+  int64_t sweeps_done, sweep_pos, sweep_len_cur, sweep_len, warm_k_sum;
+  int64_t n_prop, n_accept, n_ties, n_aborts, n_windows, n_meas, n_recomputes;
+  double sign, sign_sum, k_sum, max_drift, flops, upd_bytes, ext_flops, ext_bytes, rec_flops;
+};
+
+struct SaveVertex {
+  int32_t site, s;
+  double tau;
+};
+}  // namespace
+
+static size_t save_size(const dca_walker* h) {
+  size_t b = sizeof(SaveHeader);
+  for (int wi = 0; wi < h->W; ++wi)
+    b += sizeof(SaveWalker) + sizeof(SaveVertex) * (size_t)h->h_W[wi].n_live +
+         sizeof(double) * 2 * (size_t)h->nc_of[wi] * h->ntm;
+  return b;
+}
+
+extern "C" DCA_API int dca_walker_save(dca_walker* h, void* buf, size_t cap, size_t* n) {
+  if (!h || !n) return DCA_ERR_ARG;
+  int rc = pull_records(h);
+  if (rc != DCA_OK) return rc;
+  const size_t need = save_size(h);
+  *n = need;
+  if (!buf) return DCA_OK;
+  if (cap < need) return fail(h, DCA_ERR_ARG, "checkpoint buffer too small (" + std::to_string(need) + " bytes needed)");
+  unsigned char* out = (unsigned char*)buf;
+  SaveHeader hd{kSaveMagic, kSaveVersion, h->W, h->prec_public, h->ntm, h->warmup, (uint64_t)need};
+  std::memcpy(out, &hd, sizeof(hd));
+  size_t off = sizeof(hd);
+  for (int wi = 0; wi < h->W; ++wi) {
+    const WalkerDev& w = h->h_W[wi];
+    const int k = w.n_live, n_rows = w.n, par = w.parity;
+    SaveWalker sw{};
+    sw.problem = h->problem_of[wi];
+    sw.nc = h->nc_of[wi];
+    sw.k = k;
+    sw.status = w.status;
+    sw.windows_since_recompute = w.windows_since_recompute;
+    sw.q = w.q;
+    sw.sweeps_done = w.sweeps_done;
+    sw.sweep_pos = w.sweep_pos;
+    sw.sweep_len_cur = w.sweep_len_cur;
+    sw.sweep_len = w.sweep_len;
+    sw.warm_k_sum = w.warm_k_sum;
+    sw.n_prop = w.n_prop;
+    sw.n_accept = w.n_accept;
+    sw.n_ties = w.n_ties;
+    sw.n_aborts = w.n_aborts;
+    sw.n_windows = w.n_windows;
+    sw.n_meas = w.n_meas;
+    sw.n_recomputes = w.n_recomputes;
+    sw.sign = w.sign;
+    sw.sign_sum = w.sign_sum;
+    sw.k_sum = w.k_sum;
+    sw.max_drift = w.max_drift;
+    sw.flops = w.flops;
+    sw.upd_bytes = w.upd_bytes;
+    sw.ext_flops = w.ext_flops;
+    sw.ext_bytes = w.ext_bytes;
+    sw.rec_flops = w.rec_flops;
+    std::memcpy(out + off, &sw, sizeof(sw));
+    off += sizeof(sw);
+    std::vector<int32_t> live(k), site(n_rows), s(n_rows);
+    std::vector<double> tau(n_rows);
+    if (k > 0) {
+      CK(cudaMemcpyAsync(live.data(), w.live_idx, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaMemcpyAsync(site.data(), w.vsite[par], sizeof(int32_t) * n_rows, cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaMemcpyAsync(s.data(), w.vs[par], sizeof(int32_t) * n_rows, cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaMemcpyAsync(tau.data(), w.vtau[par], sizeof(double) * n_rows, cudaMemcpyDeviceToHost, h->stream));
+    }
+    const size_t gbytes = sizeof(double) * 2 * (size_t)h->nc_of[wi] * h->ntm;
+    CK(cudaMemcpyAsync(out + off + sizeof(SaveVertex) * k, w.Gacc, gbytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < k; ++i) {
+      const SaveVertex v{site[live[i]], s[live[i]], tau[live[i]]};
+      std::memcpy(out + off + sizeof(SaveVertex) * i, &v, sizeof(v));
+    }
+    off += sizeof(SaveVertex) * k + gbytes;
+  }
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_load(dca_walker* h, const void* buf, size_t n) {
+  if (!h || !buf) return DCA_ERR_ARG;
+  int rc = pull_records(h);
+  if (rc != DCA_OK) return rc;
+  const unsigned char* in = (const unsigned char*)buf;
+  SaveHeader hd;
+  if (n < sizeof(hd)) return fail(h, DCA_ERR_ARG, "checkpoint truncated");
+  std::memcpy(&hd, in, sizeof(hd));
+  if (hd.magic != kSaveMagic || hd.version != kSaveVersion) return fail(h, DCA_ERR_ARG, "not a walker checkpoint");
+  if (hd.bytes != n) return fail(h, DCA_ERR_ARG, "checkpoint size does not match its header");
+  if (hd.n_walkers != h->W || hd.precision != h->prec_public || hd.n_tau_meas != h->ntm || hd.warmup != h->warmup)
+    return fail(h, DCA_ERR_ARG, "checkpoint of a walker set with other parameters");
+  // first pass: validate everything before touching the walkers
+  struct Parsed {
+    SaveWalker sw;
+    size_t vert_off, g_off;
+  };
+  std::vector<Parsed> parsed(h->W);
+  size_t off = sizeof(hd);
+  int max_k = 0;
+  for (int wi = 0; wi < h->W; ++wi) {
+    if (off + sizeof(SaveWalker) > n) return fail(h, DCA_ERR_ARG, "checkpoint truncated");
+    Parsed& p = parsed[wi];
+    std::memcpy(&p.sw, in + off, sizeof(SaveWalker));
+    off += sizeof(SaveWalker);
+    const SaveWalker& sw = p.sw;
+    const WalkerDev& w = h->h_W[wi];
+    if (sw.problem != h->problem_of[wi] || sw.nc != h->nc_of[wi])
+      return fail(h, DCA_ERR_ARG, "walker " + std::to_string(wi) + ": checkpoint of another problem");
+    if (sw.k < 0 || sw.k + h->ks > w.cap)
+      return fail(h, DCA_ERR_ARG, "walker " + std::to_string(wi) + ": order beyond the capacity");
+    if (sw.sign != 1.0 && sw.sign != -1.0) return fail(h, DCA_ERR_ARG, "walker " + std::to_string(wi) + ": bad sign");
+    const size_t gbytes = sizeof(double) * 2 * (size_t)sw.nc * h->ntm;
+    p.vert_off = off;
+    p.g_off = off + sizeof(SaveVertex) * (size_t)sw.k;
+    off = p.g_off + gbytes;
+    if (off > n) return fail(h, DCA_ERR_ARG, "checkpoint truncated");
+    const ProblemDev& pd = h->h_P[sw.problem];
+    for (int i = 0; i < sw.k; ++i) {
+      SaveVertex v;
+      std::memcpy(&v, in + p.vert_off + sizeof(SaveVertex) * i, sizeof(v));
+      if (v.site < 0 || v.site >= pd.nc || (v.s != 1 && v.s != -1) || !(v.tau >= 0.0) || !(v.tau < pd.beta))
+        return fail(h, DCA_ERR_ARG, "walker " + std::to_string(wi) + ": vertex " + std::to_string(i) + " out of range");
+    }
+    max_k = std::max(max_k, sw.k);
+  }
+  if (off != n) return fail(h, DCA_ERR_ARG, "checkpoint has trailing bytes");
+  // second pass: upload the configurations and counters
+  for (int wi = 0; wi < h->W; ++wi) {
+    const Parsed& p = parsed[wi];
+    const SaveWalker& sw = p.sw;
+    WalkerDev& w = h->h_W[wi];
+    const int k = sw.k;
+    std::vector<int32_t> site(k), s(k), live(k);
+    std::vector<double> tau(k);
+    for (int i = 0; i < k; ++i) {
+      SaveVertex v;
+      std::memcpy(&v, in + p.vert_off + sizeof(SaveVertex) * i, sizeof(v));
+      site[i] = v.site;
+      s[i] = v.s;
+      tau[i] = v.tau;
+      live[i] = i;
+    }
+    if (k > 0) {
+      CK(cudaMemcpyAsync(w.vsite[0], site.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(w.vs[0], s.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(w.vtau[0], tau.data(), sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(w.live_idx, live.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, h->stream));
+    }
+    CK(cudaMemcpyAsync(w.Gacc, in + p.g_off, sizeof(double) * 2 * (size_t)sw.nc * h->ntm, cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaMemsetAsync(w.Gtmp, 0, sizeof(double) * 2 * (size_t)sw.nc * h->ntm, h->stream));
+    w.n = k;
+    w.n_live = k;
+    w.n_dead = 0;
+    w.compact_pending = 0;
+    w.parity = 0;
+    w.status = sw.status;
+    w.windows_since_recompute = sw.windows_since_recompute;
+    w.q = sw.q;
+    w.sweeps_done = sw.sweeps_done;
+    w.sweeps_target = sw.sweeps_done;
+    w.sweep_pos = sw.sweep_pos;
+    w.sweep_len_cur = sw.sweep_len_cur;
+    w.sweep_len = sw.sweep_len;
+    w.warm_k_sum = sw.warm_k_sum;
+    w.n_prop = sw.n_prop;
+    w.n_accept = sw.n_accept;
+    w.n_ties = sw.n_ties;
+    w.n_aborts = sw.n_aborts;
+    w.n_windows = sw.n_windows;
+    w.n_meas = sw.n_meas;
+    w.n_recomputes = sw.n_recomputes;
+    w.sign = sw.sign;
+    w.sign_sum = sw.sign_sum;
+    w.k_sum = sw.k_sum;
+    w.max_drift = sw.max_drift;
+    w.drift_bits[0] = w.drift_bits[1] = 0ull;
+    w.flops = sw.flops;
+    w.upd_bytes = sw.upd_bytes;
+    w.ext_flops = sw.ext_flops;
+    w.ext_bytes = sw.ext_bytes;
+    w.rec_flops = sw.rec_flops;
+    w.active = 0;
+    w.win_len = w.n_cand = w.n_acc = w.n_removed = w.n_eval = w.aborted = w.n_ins = 0;
+    w.measure_pending = w.recompute_pending = w.first_window = 0;
+  }
+  rc = push_records(h);
+  if (rc != DCA_OK) return rc;
+  dca::launch_rebuild(h->cfg, max_k, h->d_sgn, h->stream);
+  CK(cudaGetLastError());
+  rc = pull_records(h);
+  if (rc != DCA_OK) return rc;
+  for (int wi = 0; wi < h->W; ++wi) {
+    WalkerDev& w = h->h_W[wi];
+    if (w.n_live > 0 && w.sign != parsed[wi].sw.sign)
+      return fail(h, DCA_ERR_NUMERIC, "walker " + std::to_string(wi) + ": rebuilt determinant sign differs from the saved sign");
+    if (w.status == dca::ST_ERR_NUMERIC && parsed[wi].sw.status == dca::ST_OK)
+      return fail(h, DCA_ERR_NUMERIC, "walker " + std::to_string(wi) + ": rebuilt matrix is singular");
+  }
+  return DCA_OK;
 }
 
 extern "C" DCA_API int dca_walker_capacity(dca_walker* h, int32_t wi, int32_t* capacity) {

@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libdcawalker.so")
 
 DCA_OK = 0
 ERRORS = {-1: "ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "NUMERIC", -6: "STATE", -7: "CAPACITY"}
-PRECISIONS = {"fp64": 0, "mixed": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1, "tf32x3": 1, "tf32": 2}
+GAMMA_PRECISIONS = {"fp64": 0, "double_float": 1}
 
 EXPORTS = [
     "dca_g0_isolated_cluster", "dca_walker_create", "dca_walker_sweep", "dca_walker_measure_G",
@@ -22,6 +23,7 @@ EXPORTS = [
     "dca_walker_get_decision_log", "dca_walker_set_forced_decisions", "dca_walker_capacity",
     "dca_walker_destroy", "dca_walker_last_error", "dca_walker_update_G0", "dca_walker_set_timing",
     "dca_walker_get_timing", "dca_walker_set_tuning", "dca_fresh_N", "dca_fresh_N_noalloc",
+    "dca_walker_sync", "dca_walker_set_schedule", "dca_walker_set_limits", "dca_walker_save", "dca_walker_load",
 ]
 UPDATE_KERNELS = {"auto": 0, "cuda_core": 1, "tcgen05": 2}
 # lockstep: every walker runs n more sweeps per sweep(n); pooled: the walkers
@@ -63,6 +65,8 @@ class Params(C.Structure):
         ("recompute_sweeps", C.c_int32),
         ("recompute_method", C.c_int32),
         ("schedule", C.c_int32),
+        ("gamma_precision", C.c_int32),
+        ("recompute_at_measure", C.c_int32),
     ]
 
 
@@ -112,6 +116,11 @@ def load(path=LIB_PATH):
     L.dca_g0_isolated_cluster.argtypes = [C.c_int32, P, P, C.c_double, C.c_double, C.c_double, C.c_int32, P]
     L.dca_walker_create.argtypes = [C.POINTER(Params), P, C.POINTER(P)]
     L.dca_walker_sweep.argtypes = [P, C.c_int32]
+    L.dca_walker_sync.argtypes = [P]
+    L.dca_walker_set_schedule.argtypes = [P, C.c_int32]
+    L.dca_walker_set_limits.argtypes = [P, C.c_int64, C.c_int64]
+    L.dca_walker_save.argtypes = [P, P, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.dca_walker_load.argtypes = [P, P, C.c_size_t]
     L.dca_walker_measure_G.argtypes = [P, P, P, P]
     L.dca_walker_reset_measurements.argtypes = [P]
     L.dca_walker_stats.argtypes = [P, P]
@@ -207,7 +216,8 @@ class Walkers:
     def __init__(self, problems, n_walkers=1, walker_problem=None, k_sub=32, recompute_every=64,
                  warmup_sweeps=20, n_tau_meas=64, precision="fp64", init_config_size=10, capacity=0,
                  seed=0, tie_eps=1e-10, log_capacity=0, update_kernel="auto", recompute_sweeps=0,
-                 recompute_method="auto", schedule="lockstep", stream=None):
+                 recompute_method="auto", schedule="lockstep", gamma_precision="fp64", recompute_at_measure=False,
+                 stream=None):
         L = load()
         self._keep = []
         probs = (Problem * len(problems))()
@@ -249,6 +259,9 @@ class Walkers:
         p.recompute_sweeps = int(recompute_sweeps)
         p.recompute_method = {"auto": 0, "gj": 1}[recompute_method]
         p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+        p.gamma_precision = GAMMA_PRECISIONS[gamma_precision] if isinstance(gamma_precision, str) \
+            else int(gamma_precision)
+        p.recompute_at_measure = 1 if recompute_at_measure else 0
         p.update_kernel = UPDATE_KERNELS[update_kernel] if isinstance(update_kernel, str) else int(update_kernel)
         self.n_walkers = int(n_walkers)
         self.n_tau_meas = int(n_tau_meas)
@@ -275,8 +288,35 @@ class Walkers:
         except Exception:
             pass
 
-    def sweep(self, n):
+    def sweep(self, n, sync=True):
+        """Run n more sweeps (see dca_walker_sweep).  The library call only
+        enqueues them; with sync=True the binding then calls dca_walker_sync,
+        so that a walker error raises here."""
         self._check(self._L.dca_walker_sweep(self._h, int(n)))
+        if sync:
+            self.sync()
+
+    def sync(self):
+        self._check(self._L.dca_walker_sync(self._h))
+
+    def set_schedule(self, schedule):
+        s = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+        self._check(self._L.dca_walker_set_schedule(self._h, s))
+
+    def set_limits(self, max_windows=0, wait_cycles=0):
+        self._check(self._L.dca_walker_set_limits(self._h, int(max_windows), int(wait_cycles)))
+
+    def save(self):
+        """Checkpoint of every walker's chain as bytes."""
+        n = C.c_size_t(0)
+        self._check(self._L.dca_walker_save(self._h, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(self._L.dca_walker_save(self._h, buf, n.value, C.byref(n)))
+        return buf.raw[:n.value]
+
+    def load(self, data):
+        buf = C.create_string_buffer(bytes(data), len(data))
+        self._check(self._L.dca_walker_load(self._h, buf, len(data)))
 
     def measure_G(self):
         """(G_sum list per walker [2, nc, n_tau_meas], sign sums, measurement counts)."""

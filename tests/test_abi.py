@@ -75,7 +75,8 @@ def _params(walker, **over):
 
 @pytest.mark.parametrize("field,value", [
     ("k_sub", 0), ("k_sub", 129), ("n_walkers", 0), ("n_tau_meas", 0), ("init_config_size", -1),
-    ("precision", 99), ("K", 0.0), ("beta", -1.0), ("U", -1.0), ("n_problems", 0),
+    ("precision", 99), ("K", 0.0), ("beta", -1.0), ("U", -1.0), ("n_problems", 0), ("gamma_precision", 7),
+    ("schedule", 5), ("update_kernel", 9), ("recompute_method", 4),
 ])
 def test_invalid_parameters_rejected_on_host(lib, field, value):
     from paper_1901_01047_gb300 import walker
@@ -100,7 +101,21 @@ def test_bad_site_table_and_nonfinite_g0_rejected(lib):
     assert b"non-finite" in lib.dca_walker_last_error(None)
 
 
+def test_tf32_precision_needs_the_tensor_cores(lib):
+    from paper_1901_01047_gb300 import walker
+    p, keep, ss, g0 = _params(walker, precision=2, update_kernel=1)
+    h = C.c_void_p()
+    assert lib.dca_walker_create(C.byref(p), None, C.byref(h)) == -1
+    assert b"tensor cores" in lib.dca_walker_last_error(None)
+
+
 def test_null_handles_rejected(lib):
+    n = C.c_size_t(0)
+    assert lib.dca_walker_sync(None) == -1
+    assert lib.dca_walker_set_schedule(None, 0) == -1
+    assert lib.dca_walker_set_limits(None, 0, 0) == -1
+    assert lib.dca_walker_save(None, None, 0, C.byref(n)) == -1
+    assert lib.dca_walker_load(None, None, 0) == -1
     assert lib.dca_walker_sweep(None, 1) == -1
     assert lib.dca_walker_stats(None, None) == -1
     assert lib.dca_walker_measure_G(None, None, None, None) == -1
