@@ -73,6 +73,8 @@ def lib():
         L.orc_try_remove.argtypes = [P, C.c_int32, C.c_int32]
         L.orc_ratio.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int8,
                                 C.POINTER(C.c_double)]
+        L.orc_enable_freq.argtypes = [P, C.c_int32]
+        L.orc_get_M.argtypes = [P, C.c_void_p]
         _lib = L
     return _lib
 
@@ -198,6 +200,21 @@ class OracleWalker:
 
     def reset_accumulators(self):
         lib().orc_reset_accumulators(self._h)
+
+    def enable_freq(self, n_omega):
+        """Measure M(dr, i w_n) for the first n_omega positive fermionic frequencies as well."""
+        rc = lib().orc_enable_freq(self._h, int(n_omega))
+        if rc != 0:
+            raise ValueError("enable_freq failed with code %d" % rc)
+        self.n_omega = int(n_omega)
+
+    def M(self):
+        """Accumulated sum of sign * M(dr, i w_n), complex [2, nc, n_omega]."""
+        out = np.zeros((2, self.nc, self.n_omega, 2), np.float64)
+        rc = lib().orc_get_M(self._h, _ptr(out))
+        if rc != 0:
+            raise ValueError("frequency measurement is off")
+        return out[..., 0] + 1j * out[..., 1]
 
     def fresh_N(self, spin):
         k = self.order

@@ -148,6 +148,8 @@ typedef struct {
     const uint8_t* hints; int64_t hints_n;
     int64_t n_prop, n_acc, n_ties, n_adopted;
     double k_sum; int64_t k_samples;   /* k_sum: sum over measurements of sign * k */
+    int32_t n_omega;          /* frequency measurement: positive Matsubara frequencies, 0 = off */
+    double* Macc;             /* [2][nc][n_omega][re, im]: sum of sign * M(dr, i w_n) */
 } orc_walker;
 
 /* ------------------------------------------------------------------ */
@@ -280,7 +282,7 @@ void orc_destroy(orc_walker* w)
     free(w->site_sub); free(w->site_add); free(w->g0);
     free(w->vsite); free(w->vtau); free(w->vs);
     free(w->N[0]); free(w->N[1]); free(w->work);
-    free(w->Gacc); free(w->log);
+    free(w->Gacc); free(w->log); free(w->Macc);
     free(w);
 }
 
@@ -530,6 +532,8 @@ static int propose(orc_walker* w, uint64_t q)
 /*   g0(r'+dr - r_i, tau_a - tau_i) M_ij g0(r_j - r', tau_j),          */
 /* M = (e^V - 1) N; accumulated as sign * (-G) (paper convention).     */
 /* ------------------------------------------------------------------ */
+static void measure_freq(orc_walker* w);
+
 static void measure(orc_walker* w)
 {
     int n = w->k, nc = w->nc, nt = w->n_meas_tau, ld = w->cap;
@@ -562,8 +566,65 @@ static void measure(orc_walker* w)
         }
     }
     free(b);
+    if (w->n_omega > 0) measure_freq(w);
     w->sign_sum += w->sign;
     w->n_meas++;
+}
+
+/* Frequency-domain measurement of M (Sec. 2.3: the Green's function is
+ * linearly related to M, whose Fourier coefficients are accumulated; the
+ * delayed-NFFT paragraph evaluates exactly these sums).  With M = (e^V - 1) N
+ * and fermionic w_n = (2n + 1) pi / beta,
+ *   M(dr, i w_n) = 1/(beta Nc) sum_{i,j : r_i - r_j = dr} M_ij e^{i w_n (tau_i - tau_j)},
+ * so that, averaged over the cluster and over time translations,
+ *   G(K, i w_n) = g0(K, i w_n) + g0(K, i w_n)^2 M(K, i w_n),
+ *   M(K, i w_n) = sum_dr e^{-i K.dr} M(dr, i w_n)
+ * (g0 = -G0; in the paper's sign, G = G0 - G0^2 M).  Evaluated here as the
+ * plain non-uniform discrete Fourier sum, one cosine and sine per pair and
+ * frequency. */
+static void measure_freq(orc_walker* w)
+{
+    const int n = w->k, nc = w->nc, nw = w->n_omega, ld = w->cap;
+    const double norm = 1.0 / (w->beta * (double)nc);
+    for (int sp = 0; sp < 2; ++sp) {
+        const double* N = w->N[sp];
+        for (int i = 0; i < n; ++i) {
+            const double fi = ev(w, sp, w->vs[i]) - 1.0;
+            for (int j = 0; j < n; ++j) {
+                const double m = w->sign * fi * N[(size_t)i * ld + j] * norm;
+                const int d = w->site_sub[w->vsite[i] * nc + w->vsite[j]];
+                const double t = w->vtau[i] - w->vtau[j];
+                double* acc = w->Macc + ((size_t)sp * nc + d) * (size_t)nw * 2;
+                for (int k = 0; k < nw; ++k) {
+                    const double ang = (double)(2 * k + 1) * 3.14159265358979323846 * t / w->beta;
+                    acc[2 * k] += m * cos(ang);
+                    acc[2 * k + 1] += m * sin(ang);
+                }
+            }
+        }
+    }
+}
+
+/* Switch the frequency measurement on (n_omega > 0) or off (0); clears it. */
+int orc_enable_freq(orc_walker* w, int32_t n_omega)
+{
+    if (!w || n_omega < 0) return ORC_ERR_ARG;
+    free(w->Macc);
+    w->Macc = NULL;
+    w->n_omega = 0;
+    if (n_omega == 0) return ORC_OK;
+    w->Macc = (double*)calloc((size_t)2 * w->nc * n_omega * 2, sizeof(double));
+    if (!w->Macc) return ORC_ERR_OOM;
+    w->n_omega = n_omega;
+    return ORC_OK;
+}
+
+/* Accumulated sum of sign * M(dr, i w_n): out [2][nc][n_omega][re, im]. */
+int orc_get_M(const orc_walker* w, double* out)
+{
+    if (!w || !out || !w->Macc) return ORC_ERR_ARG;
+    memcpy(out, w->Macc, sizeof(double) * (size_t)2 * w->nc * w->n_omega * 2);
+    return ORC_OK;
 }
 
 /* ------------------------------------------------------------------ */
@@ -651,6 +712,7 @@ void orc_reset_accumulators(orc_walker* w)
     w->n_meas = 0;
     w->k_sum = 0.0;
     w->k_samples = 0;
+    if (w->Macc) memset(w->Macc, 0, sizeof(double) * (size_t)2 * w->nc * w->n_omega * 2);
 }
 
 /* Decision log: one byte per proposal, bit 0 = accepted, bit 1 = near tie. */

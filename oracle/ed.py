@@ -116,6 +116,39 @@ class HubbardED:
                 out[site_sub[x, y]] += G[x, y]
         return out / nc
 
+    def greens_freq(self, beta, n_omega, H=None, spin=0):
+        """G(x, y; i w_n) = int_0^beta d tau e^{i w_n tau} G(x, y; tau) for the first n_omega
+        positive fermionic frequencies w_n = (2n + 1) pi / beta, from the Lehmann sum
+        (1/Z) sum_mn (c_x)_mn (c_y)_mn (e^{-beta E_n} + e^{-beta E_m}) / (i w_n + E_m - E_n),
+        shape [nc, nc, n_omega] (complex)."""
+        E, V, _ = self.thermal(beta, H)
+        Z = np.sum(np.exp(-beta * E))
+        w = (2 * np.arange(n_omega) + 1) * np.pi / beta
+        ct = [V.T @ self.c[spin * self.nc + x] @ V for x in range(self.nc)]
+        bw = np.exp(-beta * E)
+        num = bw[None, :] + bw[:, None]           # [m, n]
+        dE = E[:, None] - E[None, :]              # E_m - E_n
+        out = np.zeros((self.nc, self.nc, n_omega), np.complex128)
+        for k, wk in enumerate(w):
+            D = num / (1j * wk + dE)
+            for x in range(self.nc):
+                A = ct[x] * D
+                for y in range(self.nc):
+                    out[x, y, k] = np.sum(A * ct[y]) / Z
+        return out
+
+    def greens_freq_K(self, beta, n_omega, site_sub, k_dot_r, H=None, spin=0):
+        """G(K, i w_n) = sum_dr e^{-i K.dr} (1/Nc) sum_y G(y + dr, y; i w_n), [nc_K, n_omega]."""
+        G = self.greens_freq(beta, n_omega, H=H, spin=spin)
+        nc = self.nc
+        site_sub = np.asarray(site_sub)
+        Gdr = np.zeros((nc, n_omega), np.complex128)
+        for x in range(nc):
+            for y in range(nc):
+                Gdr[site_sub[x, y]] += G[x, y]
+        Gdr /= nc
+        return np.exp(-1j * np.asarray(k_dot_r)) @ Gdr
+
     def h0_shifted(self):
         """CT-AUX H0 = hopping - (mu - U/2) n (Eq. generalized_hubbard, single band)."""
         return self.hop - (self.mu - 0.5 * self.U) * self.ntot

@@ -40,17 +40,20 @@ __global__ void __launch_bounds__(128) k_begin(Config cfg) {
   WalkerDev& w = cfg.W[blockIdx.x];
   __shared__ int s_active, s_len, s_n, s_cap, s_par;
   __shared__ int s_type[KS_MAX];
-  // Lockstep sweeps: a walker works only while its sweep count equals the
-  // smallest count among the walkers that still have sweeps to do, so every
-  // walker starts sweep m in the same window (each chain is unchanged; only
-  // the interleaving of the walkers is fixed).
+  // Lockstep sweeps: a walker works only while the sweeps it has done in the
+  // current call equal the smallest such count among the walkers that still
+  // have sweeps to do, so every walker starts the m-th sweep of the call in
+  // the same window (each chain is unchanged; only the interleaving of the
+  // walkers is fixed).  Counting from the call's start keeps walkers whose
+  // totals differ (after pooled calls) running together.
   __shared__ unsigned long long s_min;
   if (threadIdx.x == 0) s_min = ~0ull;
   __syncthreads();
   if (!cfg.pooled)
     for (int i = threadIdx.x; i < cfg.n_walkers; i += blockDim.x) {
       const WalkerDev& o = cfg.W[i];
-      if (o.status == ST_OK && o.sweeps_done < o.sweeps_target) atomicMin(&s_min, (unsigned long long)o.sweeps_done);
+      if (o.status == ST_OK && o.sweeps_done < o.sweeps_target)
+        atomicMin(&s_min, (unsigned long long)(o.sweeps_done - o.sweeps_base));
     }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -64,7 +67,7 @@ __global__ void __launch_bounds__(128) k_begin(Config cfg) {
     w.recompute_pending = 0;
     int act = cfg.pooled ? ((w.status == ST_OK && cfg.pool->go) ? 1 : 0)
                          : ((w.status == ST_OK && w.sweeps_done < w.sweeps_target &&
-                             (unsigned long long)w.sweeps_done == s_min) ? 1 : 0);
+                             (unsigned long long)(w.sweeps_done - w.sweeps_base) == s_min) ? 1 : 0);
     if (act) {
       w.first_window = w.sweep_pos == 0 ? 1 : 0;
       if (w.sweep_pos == 0) {
@@ -1214,7 +1217,10 @@ __global__ void k_count_active(Config cfg) {
 
 __global__ void k_add_target(Config cfg, int64_t n_sweeps) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < cfg.n_walkers) cfg.W[i].sweeps_target = cfg.W[i].sweeps_done + n_sweeps;
+  if (i < cfg.n_walkers) {
+    cfg.W[i].sweeps_base = cfg.W[i].sweeps_done;
+    cfg.W[i].sweeps_target = cfg.W[i].sweeps_done + n_sweeps;
+  }
 }
 
 // Loop control of the device-side window loop (body of a conditional WHILE

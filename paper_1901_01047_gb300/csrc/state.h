@@ -88,6 +88,7 @@ struct WalkerDev {
   uint32_t key0, key1;       // Philox key
   uint64_t q;                // next proposal number
   int64_t sweeps_done, sweeps_target, sweep_pos, sweep_len_cur, sweep_len, warm_k_sum;
+  int64_t sweeps_base;       // sweeps_done when the current lockstep call began
   double sign;
 
   // ---- current window ----

@@ -1121,6 +1121,7 @@ extern "C" DCA_API int dca_walker_load(dca_walker* h, const void* buf, size_t n)
     w.q = sw.q;
     w.sweeps_done = sw.sweeps_done;
     w.sweeps_target = sw.sweeps_done;
+    w.sweeps_base = sw.sweeps_done;
     w.sweep_pos = sw.sweep_pos;
     w.sweep_len_cur = sw.sweep_len_cur;
     w.sweep_len = sw.sweep_len;

@@ -95,6 +95,49 @@ def test_2x2_full_run_parity():
     assert st["proposals"] > 3_000_000 and st["max_drift"] < 1e-9
 
 
+def test_betts16_parity_at_order_1000():
+    # 16-site cluster workload (t' = -0.15, U = 6, beta = 20, density 0.9,
+    # k_s = 64, N recomputed every 64 submatrix updates), shortened to a few
+    # sweeps.  It starts from 1000 random vertices, so the first sweeps run at
+    # order ~1000 while the chain relaxes towards its equilibrium order (~760):
+    # FP64 parity at the matrix sizes of the workload.  N^-1 is ill-conditioned
+    # there (kappa ~ 1e7 and more), so two exact-in-FP64 algorithms (the
+    # oracle's rank-1 updates, the GPU's rank-k updates and recomputes) agree
+    # on N only to about kappa * 2^-53: the bound is max(1e-10, 50 kappa 2^-53),
+    # and the GPU's N must be as close to the FP64 inverse of its final
+    # configuration as the oracle's is.  Decisions and vertices are exact.
+    from paper_1901_01047_gb300 import inputs
+    wl = inputs.WORKLOADS["betts16"]
+    c, eps, kr, G0 = problem(16, 1.0, -0.15, 6.0, 20.0, wl.mu, 4096)
+    res = run_pair(16, 1.0, -0.15, 6.0, 20.0, wl.mu, 4096, k_sub=64, sweeps=5, seed=0, warmup=2, init=1000,
+                   ntm=64, R=64)
+    gs, os_, glog, olog, Gg, ssg, nmg, (Go, sso, nmo), st, oc = res[0]
+    assert glog.size == olog.size and np.array_equal(glog & 1, olog & 1)
+    assert st["proposals"] == oc["proposals"] > 3000 and st["status"] == 0
+    assert np.array_equal(gs["site"], os_["site"]) and np.array_equal(gs["s"], os_["s"])
+    assert np.array_equal(gs["tau"], os_["tau"])
+    assert nmg == nmo == 3 and ssg == sso and st["recomputes"] >= 1 and gs["site"].size > 700
+    ow = ctaux.OracleWalker(16, c.site_sub, 6.0, 20.0, 1.0, G0, init_config_size=0)
+    ow.set_config(gs["site"], gs["tau"], gs["s"])
+    kappa = 0.0
+    for sp in range(2):
+        ref = os_["N"][sp]
+        exact, _ = ow.fresh_N(sp)
+        k_sp = np.linalg.cond(ref)
+        kappa = max(kappa, k_sp)
+        tol = max(TOL, 50 * k_sp * 2.0 ** -53)
+        err = np.abs(gs["N"][sp] - ref).max() / np.abs(ref).max()
+        e_gpu = np.abs(gs["N"][sp] - exact).max() / np.abs(exact).max()
+        e_ora = np.abs(ref - exact).max() / np.abs(exact).max()
+        print("order %d spin %d: kappa %.2e, |N_gpu - N_ora| %.2e (bound %.2e), to the exact inverse: GPU %.2e, "
+              "oracle %.2e" % (gs["site"].size, sp, k_sp, err, tol, e_gpu, e_ora))
+        assert err <= tol
+        assert e_gpu <= 10 * e_ora + 1e-13
+    errG = np.abs(Gg - Go).max() / np.abs(Go).max()
+    print("accumulated G: %.2e" % errG)
+    assert errG <= max(TOL, 50 * kappa * 2.0 ** -53)
+
+
 @pytest.mark.parametrize("k_sub", [1, 3, 16, 128])
 def test_window_sizes_reach_the_same_chain(k_sub):
     res = run_pair(4, 1.0, 0.0, 4.0, 5.0, 1.2, 1024, k_sub=k_sub, sweeps=120, seed=3, warmup=5, ntm=8)
