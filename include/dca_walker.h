@@ -125,6 +125,9 @@ typedef struct {
                                       sweep, before its measurement (the measurement then sees a
                                       from-scratch N instead of one carrying the drift of the
                                       updates since the last recompute); 0: off */
+  int32_t n_omega_meas;            /* frequency measurement of M (delayed NFFT, read by
+                                      dca_walker_measure_M): positive fermionic Matsubara
+                                      frequencies, 8..4096; 0 = off */
 } dca_walker_params;
 
 /* Scheduling of the walkers by dca_walker_sweep(n).  The chains do not depend
@@ -269,6 +272,22 @@ DCA_API int dca_walker_load(dca_walker* w, const void* buf, size_t n);
  * the outputs may be NULL.  Synchronises the stream. */
 DCA_API int dca_walker_measure_G(dca_walker* w, double* G_out, double* sign_sum_out, int64_t* n_meas_out);
 
+/* Accumulated frequency-domain measurement (Sec. 2.3: the Fourier
+ * coefficients of M are accumulated; Eq. nfft with the transform delayed to
+ * the read-out).  For every walker, spin, cluster difference dr and
+ * w_n = (2n + 1) pi / beta, n < n_omega_meas:
+ *   sum over measurements of sign * M(dr, i w_n),
+ *   M(dr, i w_n) = 1/(beta Nc) sum_{i,j : r_i - r_j = dr} (e^{V_i} - 1) N_ij e^{i w_n (tau_i - tau_j)},
+ * so that G(K, i w_n) = G0(K, i w_n) - G0(K, i w_n)^2 <M(K, i w_n)> with
+ * M(K) = sum_dr e^{-i K.dr} M(dr) (paper sign convention).  M_out: host
+ * [n_walkers][2][nc][n_omega_meas][re, im] (walkers back to back, nc of each
+ * walker's problem); sign_sum_out [n_walkers] and n_meas_out [n_walkers] as
+ * in dca_walker_measure_G; any output may be NULL.  The spreading onto the
+ * oversampled grid uses a truncated Gaussian window with a relative error of
+ * about 1e-12 (FP64) or 1e-8 (mixed paths).  Returns DCA_ERR_STATE if the
+ * frequency measurement is off.  Synchronises the stream. */
+DCA_API int dca_walker_measure_M(dca_walker* w, double* M_out, double* sign_sum_out, int64_t* n_meas_out);
+
 /* Zero the G accumulators, sign sums and measurement counters. */
 DCA_API int dca_walker_reset_measurements(dca_walker* w);
 
@@ -324,6 +343,60 @@ DCA_API int dca_fresh_N(const dca_problem* problem, int32_t n, const dca_vertex*
 #define DCA_NOALLOC_MAX_TABLE 262144
 DCA_API int dca_fresh_N_noalloc(const dca_problem* problem, int32_t n, const dca_vertex* verts,
                                 double* N_up, double* N_dn, int32_t* det_sign);
+
+/* ---------------------------------------------------------------------------
+ * Outer DCA loop (Sec. 2.1): the steps that turn the walkers' measured M into
+ * the next bare propagator of the cluster, for the single-band Hubbard model
+ * on the square lattice, eps_k = -2t (cos kx + cos ky) - 4t' cos kx cos ky,
+ * paramagnetic.  Frequency arrays are host [nc][n_omega][re, im] over the
+ * cluster momenta K and w_n = (2n + 1) pi / beta, n < n_omega; everything
+ * runs in FP64 on the current device (device memory allocated for the call
+ * and freed).  The lattice must be inversion symmetric (G(-K) = G(K)).
+ * One iteration:
+ *   dca_sigma_update   (after the walkers ran on calG0')   new Sigma
+ *   dca_coarse_grain   Gbar, calG0, calG0', xi from Sigma
+ *   dca_g0_table_from_freq   the table for dca_walker_update_G0
+ * Start with Sigma = 0 (dca_coarse_grain then gives the first bath).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t nc;             /* cluster sites = cluster momenta, 1..64 */
+  const double* kpts;     /* host [nc][2] cluster momenta K */
+  const double* k_dot_r;  /* host [nc][nc] K . r (K index, site index) */
+  double recip[4];        /* reciprocal superlattice vectors b1 = (recip[0], recip[1]),
+                             b2 = (recip[2], recip[3]): a_i . b_j = 2 pi delta_ij */
+  double t, tp, mu, U, beta;
+  int32_t n_fine;         /* patch integration: n_fine x n_fine midpoints per patch, 1..64 */
+} dca_lattice;
+
+/* Eqs. sigma_dca and G_coarsegrained, then Eq. cluster-exclusion:
+ *   Gbar(K, i w_n) = mean over the patch of K (the reciprocal-superlattice cell
+ *                    centred on K) of [i w_n + mu - eps(K + k~) - Sigma(K, i w_n)]^-1,
+ *   calG0 = [Gbar^-1 + Sigma]^-1, and the CT-AUX bare propagator of H0 with the
+ *   +U/2 shift of Eq. generalized_hubbard, calG0'^-1 = calG0^-1 - U/2;
+ *   xi_shifted [nc] = patch mean of eps - mu + U/2 (the high-frequency form
+ *   1/(i w_n - xi) of calG0' to second order).  Outputs may be NULL. */
+DCA_API int dca_coarse_grain(const dca_lattice* lat, int32_t n_omega, const double* sigma, double* Gbar,
+                             double* G0w, double* G0w_shifted, double* xi_shifted);
+
+/* Eq. dyson_sigma and Eq. self-energy-mixing from measurements taken with the
+ * bare propagator calG0' (G0w_shifted): M_dr holds n_sets accumulators as
+ * written by dca_walker_measure_M for walkers of this problem ([n_sets][2][nc]
+ * [n_omega][re, im], sums of sign * M(dr, i w_n)), sign_sum their sign sums;
+ *   <M(K)> = sum over sets and spins of sum_dr e^{-i K.dr} M(dr) / (2 sum sign_sum),
+ *   <G> = calG0' - calG0'^2 <M>,  Sigma_QMC = calG0'^-1 + U/2 - <G>^-1,
+ *   sigma_out = alpha Sigma_QMC + (1 - alpha) sigma_old,  0 < alpha <= 1.
+ * Returns DCA_ERR_NUMERIC if the sign sum is zero. */
+DCA_API int dca_sigma_update(const dca_lattice* lat, int32_t n_omega, const double* G0w_shifted, int32_t n_sets,
+                             const double* M_dr, const double* sign_sum, const double* sigma_old, double alpha,
+                             double* sigma_out);
+
+/* The walker table [2][nc][n_tau + 1] (paper sign convention, both spins, as
+ * dca_problem.G0 and dca_walker_update_G0 take it) from calG0'(K, i w_n):
+ * G0(r, tau_l) = (1/Nc) sum_K cos(K.r) G0(K, tau_l), tau_l = l beta / n_tau,
+ * with the tail 1/(i w_n - xi_K) summed in closed form and the remainder over
+ * n < n_omega (the remainder falls off as 1/w_n^3). */
+DCA_API int dca_g0_table_from_freq(const dca_lattice* lat, int32_t n_omega, const double* G0w_shifted,
+                                   const double* xi_shifted, int32_t n_tau, double* G0_table);
 
 /* Replace the bare propagator of problem `problem` (host [2][nc][n_tau+1],
  * same layout and convention as dca_problem.G0), e.g. for the next iteration

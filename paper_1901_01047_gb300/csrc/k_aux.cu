@@ -263,9 +263,12 @@ __global__ void __launch_bounds__(256) k_meas_b(Config cfg) {
         const int sub = lane / lw, rp = lane - sub * lw;  // row of the warp, reference site
         const int i0 = item * 8 * R + warp * R;           // first row of the warp
         const int i = i0 + sub;
-        A acc0 = (A)0, acc1 = (A)0;
+        // products summed in A within a chunk of 32 columns, chunk sums in FP64
+        // (the rounding of a long FP32 sum would otherwise grow with n)
+        double tot0 = 0.0, tot1 = 0.0;
         const bool two = nc > 32;  // uniform: the second reference-site half exists (R = 1)
         for (int j0 = 0; j0 < n; j0 += 32) {
+          A acc0 = (A)0, acc1 = (A)0;
           __syncthreads();
           {
             const int j = j0 + lane;
@@ -289,12 +292,14 @@ __global__ void __launch_bounds__(256) k_meas_b(Config cfg) {
 #pragma unroll 8
             for (int jl = 0; jl < 32; ++jl) acc0 += sN[row][jl] * sG[rp][jl];
           }
+          tot0 += (double)acc0;
+          tot1 += (double)acc1;
         }
         if (i < n) {
-          const A f = (A)(expV(pb, sp, w.vs[par][i]) - 1.0);
+          const double f = expV(pb, sp, w.vs[par][i]) - 1.0;
           A* bv = reinterpret_cast<A*>(w.bvec);
-          if (rp < nc) bv[((size_t)sp * nc + rp) * ld + i] = f * acc0;
-          if (two && rp + 32 < nc) bv[((size_t)sp * nc + rp + 32) * ld + i] = f * acc1;
+          if (rp < nc) bv[((size_t)sp * nc + rp) * ld + i] = (A)(f * tot0);
+          if (two && rp + 32 < nc) bv[((size_t)sp * nc + rp + 32) * ld + i] = (A)(f * tot1);
         }
       });
 }
@@ -346,9 +351,10 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
   const int q = kGrid ? pb.meas_q : 0;
   const int tid = threadIdx.x;
   const int ta = tid & (MT - 1), tr = tid >> 6;  // 4 groups of reference sites
-  A acc[MR / 4];
+  // products summed in A within a tile of MK vertices, tile sums in FP64
+  double tot[MR / 4];
 #pragma unroll
-  for (int m = 0; m < MR / 4; ++m) acc[m] = (A)0;
+  for (int m = 0; m < MR / 4; ++m) tot[m] = 0.0;
   const int* vsite = w.vsite[par];
   const double* vtau = w.vtau[par];
   const int* vs = w.vs[par];
@@ -423,12 +429,17 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
       Bs[il][rp] = (i < n && rp < nc) ? reinterpret_cast<const A*>(w.bvec)[((size_t)sp * nc + rp) * ld + i] : (A)0;
     }
     __syncthreads();
+    A acc[MR / 4];
+#pragma unroll
+    for (int m = 0; m < MR / 4; ++m) acc[m] = (A)0;
 #pragma unroll 4
     for (int k = 0; k < MK; ++k) {
       const A g = As[ta][k];
 #pragma unroll
       for (int m = 0; m < MR / 4; ++m) acc[m] += g * Bs[k][tr + 4 * m];
     }
+#pragma unroll
+    for (int m = 0; m < MR / 4; ++m) tot[m] += (double)acc[m];
   }
   const int a = a0 + ta;
   if (a < ntm) {
@@ -437,7 +448,7 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
       const int rp = tr + 4 * m;
       if (rp < nc) {
         const int d = __ldg(pb.site_sub + x * nc + rp);
-        atomicAdd(&w.Gtmp[((size_t)sp * nc + d) * ntm + a], (double)acc[m]);
+        atomicAdd(&w.Gtmp[((size_t)sp * nc + d) * ntm + a], tot[m]);
       }
     }
   }
@@ -649,9 +660,9 @@ int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) 
   }
 #undef DCA_MEAS_GEMM
   k_meas_acc<<<grid_for((long long)W * blocks_of(2LL * max_nc * cfg.n_tau_meas, 256)), 256, 0, st>>>(cfg);
+  const int nf = launch_meas_nfft(cfg, max_cap, max_nc, st);
   k_meas_finish<<<(W + 127) / 128, 128, 0, st>>>(cfg);
-  (void)max_cap;
-  return 5 + (max_nc > 16) + (max_nc > 32);
+  return 5 + (max_nc > 16) + (max_nc > 32) + nf;
 }
 
 void launch_g0_isolated(int nc, const double* d_eps, const double* d_kr, double mu_eff, double beta, int n_tau,

@@ -88,6 +88,13 @@ void launch_upd_tc(const Config& cfg, cudaStream_t st);
 // g0 = -G0 (FP64 and FP32) from a staged G0, unless an entry is not finite:
 // then *bad = 1 and the old table is kept.
 void launch_negate(const double* src, double* dst, float* dstf, size_t n, int* bad, cudaStream_t st);
+// Delayed-NFFT frequency measurement: kernel attributes, the spreading of one
+// measurement (launched with the other measurement kernels) and the
+// transform of the accumulated grids at read-out (out at per-walker offsets
+// d_base, [2][nc][n_omega][re, im] each).
+cudaError_t setup_nfft();
+int launch_meas_nfft(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
+void launch_nfft_finish(const Config& cfg, int max_nc, const long long* d_base, double* d_out, cudaStream_t st);
 // Phase table of the measurement grid (ProblemDev::g0m) from the FP32 table g0f.
 void launch_meas_table(const ProblemDev& pd, int n_tau_meas, cudaStream_t st);
 void launch_g0_isolated(int nc, const double* d_eps, const double* d_kr, double mu_eff, double beta, int n_tau,

@@ -146,6 +146,7 @@ struct WalkerDev {
   double* Gtmp;              // [2][nc][n_tau_meas] correction term of one measurement
   double* gR;                // [2][nc][cap]
   double* bvec;              // [2][nc][cap]
+  double* Mgrid;             // [2][nc][nfft_L] delayed-NFFT grid of M (frequency measurement), or null
 };
 
 #ifdef __CUDACC__
@@ -215,6 +216,9 @@ struct Config {
   int32_t tf32_terms;        // products per K step of the tensor-core kernels: 3 (3xTF32) or 1 (TF32)
   long long wait_cycles;     // bound of every mbarrier wait in the tensor-core kernels (SM clocks)
   int32_t recompute_at_measure;  // recompute N in the window of every measurement (before it)
+  int32_t n_omega;           // frequency measurement: positive Matsubara frequencies (0 = off)
+  int32_t nfft_L;            // its grid points over [0, beta)
+  int32_t nfft_msp;          // its window half-width in grid points
 };
 
 }  // namespace dca

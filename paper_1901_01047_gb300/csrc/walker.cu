@@ -79,6 +79,8 @@ struct dca_walker {
   bool g0_rejected = false;          // an update_G0 table had a non-finite entry (reported by sync)
   int64_t max_windows = 0;           // cap of the windows of one sweep call (0 = automatic)
   int prec_public = 0;               // DCA_PREC_* given at create
+  double* d_Mout = nullptr;          // read-out of the frequency measurement, all walkers
+  long long* d_Mbase = nullptr;      // its per-walker offsets
   std::vector<int> problem_of;       // per walker
 
   ~dca_walker() {
@@ -164,12 +166,15 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   if (p.n_walkers < 1) return fail(nullptr, DCA_ERR_ARG, "n_walkers must be >= 1");
   if (p.k_sub < 1 || p.k_sub > dca::KS_MAX) return fail(nullptr, DCA_ERR_ARG, "k_sub must be in 1..128");
   if (p.recompute_sweeps < 0 || p.recompute_every < 0 || p.warmup_sweeps < 0 || p.n_tau_meas < 1 || p.init_config_size < 0 ||
-      p.capacity < 0 || p.log_capacity < 0 || p.recompute_at_measure < 0 || p.recompute_at_measure > 1)
+      p.capacity < 0 || p.log_capacity < 0 || p.recompute_at_measure < 0 || p.recompute_at_measure > 1 ||
+      p.n_omega_meas < 0)
     return fail(nullptr, DCA_ERR_ARG, "negative or zero size parameter");
   if (p.precision != DCA_PREC_FP64 && p.precision != DCA_PREC_MIXED && p.precision != DCA_PREC_TF32)
     return fail(nullptr, DCA_ERR_ARG, "unsupported precision");
   if (p.precision == DCA_PREC_TF32 && p.update_kernel == DCA_UPD_CUDA_CORE)
     return fail(nullptr, DCA_ERR_ARG, "DCA_PREC_TF32 runs on the tensor cores only");
+  if (p.n_omega_meas != 0 && (p.n_omega_meas < 8 || p.n_omega_meas > 4096))
+    return fail(nullptr, DCA_ERR_ARG, "n_omega_meas must be 0 or in 8..4096");
   if (p.gamma_precision != DCA_GAMMA_FP64 && p.gamma_precision != DCA_GAMMA_DOUBLE_FLOAT)
     return fail(nullptr, DCA_ERR_ARG, "gamma_precision must be one of DCA_GAMMA_*");
   if (p.recompute_method < DCA_RECOMPUTE_AUTO || p.recompute_method > DCA_RECOMPUTE_GJ)
@@ -351,6 +356,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     pieces.push_back({(void**)&w.Gtmp, sizeof(double) * 2 * nc * p.n_tau_meas});
     pieces.push_back({(void**)&w.gR, sizeof(double) * 2 * nc * C});
     pieces.push_back({(void**)&w.bvec, sizeof(double) * 2 * nc * C});
+    if (p.n_omega_meas > 0) pieces.push_back({(void**)&w.Mgrid, sizeof(double) * 2 * nc * 4 * (size_t)p.n_omega_meas});
     if (p.log_capacity > 0) pieces.push_back({(void**)&w.log, (size_t)p.log_capacity});
     size_t total = 0;
     for (auto& pc : pieces) total += align_up(pc.bytes, 256);
@@ -416,8 +422,11 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.tf32_terms = p.precision == DCA_PREC_TF32 ? 1 : 3;
   h->cfg.wait_cycles = kDefaultWaitCycles;
   h->cfg.recompute_at_measure = p.recompute_at_measure ? 1 : 0;
+  h->cfg.n_omega = p.n_omega_meas;
+  h->cfg.nfft_L = 4 * p.n_omega_meas;
+  h->cfg.nfft_msp = h->precision == DCA_PREC_FP64 ? 12 : 8;
 
-  if (dca::setup_window_kernels() != cudaSuccess) {
+  if (dca::setup_window_kernels() != cudaSuccess || dca::setup_nfft() != cudaSuccess) {
     h->err = "kernel attribute setup failed";
     return bail(DCA_ERR_CUDA);
   }
@@ -816,6 +825,38 @@ extern "C" DCA_API int dca_walker_measure_G(dca_walker* h, double* G_out, double
   return DCA_OK;
 }
 
+extern "C" DCA_API int dca_walker_measure_M(dca_walker* h, double* M_out, double* sign_sum_out, int64_t* n_meas_out) {
+  if (!h) return DCA_ERR_ARG;
+  if (h->cfg.n_omega <= 0) return fail(h, DCA_ERR_STATE, "the frequency measurement is off (n_omega_meas = 0)");
+  int rc = pull_records(h);
+  if (rc != DCA_OK) return rc;
+  const size_t per = (size_t)2 * h->cfg.n_omega * 2;  // spins x frequencies x (re, im), per site difference
+  std::vector<long long> base(h->W);
+  size_t total = 0;
+  for (int wi = 0; wi < h->W; ++wi) {
+    base[wi] = (long long)total;
+    total += per * h->nc_of[wi];
+  }
+  if (M_out) {
+    if (!h->d_Mout) {
+      h->d_Mout = (double*)h->dalloc(sizeof(double) * total);
+      h->d_Mbase = (long long*)h->dalloc(sizeof(long long) * h->W);
+      if (!h->d_Mout || !h->d_Mbase) return fail(h, DCA_ERR_OOM, "read-out buffers of the frequency measurement");
+      CK(cudaMemcpyAsync(h->d_Mbase, base.data(), sizeof(long long) * h->W, cudaMemcpyHostToDevice, h->stream));
+    }
+    dca::launch_nfft_finish(h->cfg, h->max_nc, h->d_Mbase, h->d_Mout, h->stream);
+    h->total_launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(M_out, h->d_Mout, sizeof(double) * total, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  for (int wi = 0; wi < h->W; ++wi) {
+    if (sign_sum_out) sign_sum_out[wi] = h->h_W[wi].sign_sum;
+    if (n_meas_out) n_meas_out[wi] = h->h_W[wi].n_meas;
+  }
+  return DCA_OK;
+}
+
 extern "C" DCA_API int dca_walker_reset_measurements(dca_walker* h) {
   if (!h) return DCA_ERR_ARG;
   int rc = pull_records(h);
@@ -823,6 +864,7 @@ extern "C" DCA_API int dca_walker_reset_measurements(dca_walker* h) {
   for (int wi = 0; wi < h->W; ++wi) {
     WalkerDev& w = h->h_W[wi];
     CK(cudaMemsetAsync(w.Gacc, 0, sizeof(double) * 2 * h->nc_of[wi] * h->ntm, h->stream));
+    if (w.Mgrid) CK(cudaMemsetAsync(w.Mgrid, 0, sizeof(double) * 2 * h->nc_of[wi] * h->cfg.nfft_L, h->stream));
     w.sign_sum = 0.0;
     w.n_meas = 0;
     w.k_sum = 0.0;
@@ -938,16 +980,17 @@ extern "C" DCA_API int dca_walker_set_forced_decisions(dca_walker* h, int32_t wi
 
 // ---------------------------------------------------------------------------
 // Checkpoint / resume.  Layout: SaveHeader, then per walker a SaveWalker
-// record, its k vertices (SaveVertex) and its G accumulator [2][nc][n_tau_meas]
+// record, its k vertices (SaveVertex), its G accumulator [2][nc][n_tau_meas]
+// and, with the frequency measurement on, its NFFT grid [2][nc][4 n_omega]
 // (FP64), all little-endian host structs of fixed layout.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr uint32_t kSaveMagic = 0x57414344u;  // "DCAW"
-constexpr uint32_t kSaveVersion = 1u;
+constexpr uint32_t kSaveVersion = 2u;
 
 struct SaveHeader {
   uint32_t magic, version;
-  int32_t n_walkers, precision, n_tau_meas, warmup;
+  int32_t n_walkers, precision, n_tau_meas, warmup, n_omega, pad;
   uint64_t bytes;  // total size of the checkpoint
 };
 
@@ -966,11 +1009,15 @@ struct SaveVertex {
 };
 }  // namespace
 
+// Bytes of a walker's accumulators in a checkpoint: G(tau), then the NFFT grid.
+static size_t acc_bytes(const dca_walker* h, int wi) {
+  return sizeof(double) * 2 * (size_t)h->nc_of[wi] * ((size_t)h->ntm + (size_t)h->cfg.nfft_L);
+}
+
 static size_t save_size(const dca_walker* h) {
   size_t b = sizeof(SaveHeader);
   for (int wi = 0; wi < h->W; ++wi)
-    b += sizeof(SaveWalker) + sizeof(SaveVertex) * (size_t)h->h_W[wi].n_live +
-         sizeof(double) * 2 * (size_t)h->nc_of[wi] * h->ntm;
+    b += sizeof(SaveWalker) + sizeof(SaveVertex) * (size_t)h->h_W[wi].n_live + acc_bytes(h, wi);
   return b;
 }
 
@@ -983,7 +1030,7 @@ extern "C" DCA_API int dca_walker_save(dca_walker* h, void* buf, size_t cap, siz
   if (!buf) return DCA_OK;
   if (cap < need) return fail(h, DCA_ERR_ARG, "checkpoint buffer too small (" + std::to_string(need) + " bytes needed)");
   unsigned char* out = (unsigned char*)buf;
-  SaveHeader hd{kSaveMagic, kSaveVersion, h->W, h->prec_public, h->ntm, h->warmup, (uint64_t)need};
+  SaveHeader hd{kSaveMagic, kSaveVersion, h->W, h->prec_public, h->ntm, h->warmup, h->cfg.n_omega, 0, (uint64_t)need};
   std::memcpy(out, &hd, sizeof(hd));
   size_t off = sizeof(hd);
   for (int wi = 0; wi < h->W; ++wi) {
@@ -1029,12 +1076,15 @@ extern "C" DCA_API int dca_walker_save(dca_walker* h, void* buf, size_t cap, siz
     }
     const size_t gbytes = sizeof(double) * 2 * (size_t)h->nc_of[wi] * h->ntm;
     CK(cudaMemcpyAsync(out + off + sizeof(SaveVertex) * k, w.Gacc, gbytes, cudaMemcpyDeviceToHost, h->stream));
+    if (w.Mgrid)
+      CK(cudaMemcpyAsync(out + off + sizeof(SaveVertex) * k + gbytes, w.Mgrid, acc_bytes(h, wi) - gbytes,
+                         cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     for (int i = 0; i < k; ++i) {
       const SaveVertex v{site[live[i]], s[live[i]], tau[live[i]]};
       std::memcpy(out + off + sizeof(SaveVertex) * i, &v, sizeof(v));
     }
-    off += sizeof(SaveVertex) * k + gbytes;
+    off += sizeof(SaveVertex) * k + acc_bytes(h, wi);
   }
   return DCA_OK;
 }
@@ -1049,7 +1099,8 @@ extern "C" DCA_API int dca_walker_load(dca_walker* h, const void* buf, size_t n)
   std::memcpy(&hd, in, sizeof(hd));
   if (hd.magic != kSaveMagic || hd.version != kSaveVersion) return fail(h, DCA_ERR_ARG, "not a walker checkpoint");
   if (hd.bytes != n) return fail(h, DCA_ERR_ARG, "checkpoint size does not match its header");
-  if (hd.n_walkers != h->W || hd.precision != h->prec_public || hd.n_tau_meas != h->ntm || hd.warmup != h->warmup)
+  if (hd.n_walkers != h->W || hd.precision != h->prec_public || hd.n_tau_meas != h->ntm || hd.warmup != h->warmup ||
+      hd.n_omega != h->cfg.n_omega)
     return fail(h, DCA_ERR_ARG, "checkpoint of a walker set with other parameters");
   // first pass: validate everything before touching the walkers
   struct Parsed {
@@ -1071,10 +1122,9 @@ extern "C" DCA_API int dca_walker_load(dca_walker* h, const void* buf, size_t n)
     if (sw.k < 0 || sw.k + h->ks > w.cap)
       return fail(h, DCA_ERR_ARG, "walker " + std::to_string(wi) + ": order beyond the capacity");
     if (sw.sign != 1.0 && sw.sign != -1.0) return fail(h, DCA_ERR_ARG, "walker " + std::to_string(wi) + ": bad sign");
-    const size_t gbytes = sizeof(double) * 2 * (size_t)sw.nc * h->ntm;
     p.vert_off = off;
     p.g_off = off + sizeof(SaveVertex) * (size_t)sw.k;
-    off = p.g_off + gbytes;
+    off = p.g_off + acc_bytes(h, wi);
     if (off > n) return fail(h, DCA_ERR_ARG, "checkpoint truncated");
     const ProblemDev& pd = h->h_P[sw.problem];
     for (int i = 0; i < sw.k; ++i) {
@@ -1108,8 +1158,11 @@ extern "C" DCA_API int dca_walker_load(dca_walker* h, const void* buf, size_t n)
       CK(cudaMemcpyAsync(w.vtau[0], tau.data(), sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
       CK(cudaMemcpyAsync(w.live_idx, live.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, h->stream));
     }
-    CK(cudaMemcpyAsync(w.Gacc, in + p.g_off, sizeof(double) * 2 * (size_t)sw.nc * h->ntm, cudaMemcpyHostToDevice,
-                       h->stream));
+    const size_t gbytes = sizeof(double) * 2 * (size_t)sw.nc * h->ntm;
+    CK(cudaMemcpyAsync(w.Gacc, in + p.g_off, gbytes, cudaMemcpyHostToDevice, h->stream));
+    if (w.Mgrid)
+      CK(cudaMemcpyAsync(w.Mgrid, in + p.g_off + gbytes, acc_bytes(h, wi) - gbytes, cudaMemcpyHostToDevice,
+                         h->stream));
     CK(cudaMemsetAsync(w.Gtmp, 0, sizeof(double) * 2 * (size_t)sw.nc * h->ntm, h->stream));
     w.n = k;
     w.n_live = k;

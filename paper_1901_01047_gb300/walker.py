@@ -24,6 +24,7 @@ EXPORTS = [
     "dca_walker_destroy", "dca_walker_last_error", "dca_walker_update_G0", "dca_walker_set_timing",
     "dca_walker_get_timing", "dca_walker_set_tuning", "dca_fresh_N", "dca_fresh_N_noalloc",
     "dca_walker_sync", "dca_walker_set_schedule", "dca_walker_set_limits", "dca_walker_save", "dca_walker_load",
+    "dca_walker_measure_M", "dca_coarse_grain", "dca_sigma_update", "dca_g0_table_from_freq",
 ]
 UPDATE_KERNELS = {"auto": 0, "cuda_core": 1, "tcgen05": 2}
 # lockstep: every walker runs n more sweeps per sweep(n); pooled: the walkers
@@ -67,6 +68,22 @@ class Params(C.Structure):
         ("schedule", C.c_int32),
         ("gamma_precision", C.c_int32),
         ("recompute_at_measure", C.c_int32),
+        ("n_omega_meas", C.c_int32),
+    ]
+
+
+class Lattice(C.Structure):
+    _fields_ = [
+        ("nc", C.c_int32),
+        ("kpts", C.POINTER(C.c_double)),
+        ("k_dot_r", C.POINTER(C.c_double)),
+        ("recip", C.c_double * 4),
+        ("t", C.c_double),
+        ("tp", C.c_double),
+        ("mu", C.c_double),
+        ("U", C.c_double),
+        ("beta", C.c_double),
+        ("n_fine", C.c_int32),
     ]
 
 
@@ -122,6 +139,7 @@ def load(path=LIB_PATH):
     L.dca_walker_save.argtypes = [P, P, C.c_size_t, C.POINTER(C.c_size_t)]
     L.dca_walker_load.argtypes = [P, P, C.c_size_t]
     L.dca_walker_measure_G.argtypes = [P, P, P, P]
+    L.dca_walker_measure_M.argtypes = [P, P, P, P]
     L.dca_walker_reset_measurements.argtypes = [P]
     L.dca_walker_stats.argtypes = [P, P]
     L.dca_walker_get_state.argtypes = [P, C.c_int32, P, C.POINTER(C.c_int32), P, P]
@@ -134,6 +152,9 @@ def load(path=LIB_PATH):
     L.dca_walker_get_timing.argtypes = [P, P, P, C.POINTER(C.c_int64), C.c_int32]
     L.dca_fresh_N.argtypes = [C.POINTER(Problem), C.c_int32, P, P, P, C.POINTER(C.c_int32)]
     L.dca_fresh_N_noalloc.argtypes = [C.POINTER(Problem), C.c_int32, P, P, P, C.POINTER(C.c_int32)]
+    L.dca_coarse_grain.argtypes = [C.POINTER(Lattice), C.c_int32, P, P, P, P, P]
+    L.dca_sigma_update.argtypes = [C.POINTER(Lattice), C.c_int32, P, C.c_int32, P, P, P, C.c_double, P]
+    L.dca_g0_table_from_freq.argtypes = [C.POINTER(Lattice), C.c_int32, P, P, C.c_int32, P]
     L.dca_walker_destroy.argtypes = [P]
     L.dca_walker_destroy.restype = None
     L.dca_walker_last_error.argtypes = [P]
@@ -217,7 +238,7 @@ class Walkers:
                  warmup_sweeps=20, n_tau_meas=64, precision="fp64", init_config_size=10, capacity=0,
                  seed=0, tie_eps=1e-10, log_capacity=0, update_kernel="auto", recompute_sweeps=0,
                  recompute_method="auto", schedule="lockstep", gamma_precision="fp64", recompute_at_measure=False,
-                 stream=None):
+                 n_omega_meas=0, stream=None):
         L = load()
         self._keep = []
         probs = (Problem * len(problems))()
@@ -262,6 +283,8 @@ class Walkers:
         p.gamma_precision = GAMMA_PRECISIONS[gamma_precision] if isinstance(gamma_precision, str) \
             else int(gamma_precision)
         p.recompute_at_measure = 1 if recompute_at_measure else 0
+        p.n_omega_meas = int(n_omega_meas)
+        self.n_omega_meas = int(n_omega_meas)
         p.update_kernel = UPDATE_KERNELS[update_kernel] if isinstance(update_kernel, str) else int(update_kernel)
         self.n_walkers = int(n_walkers)
         self.n_tau_meas = int(n_tau_meas)
@@ -332,6 +355,21 @@ class Walkers:
             off += m
         return out, ss, nm
 
+    def measure_M(self):
+        """(sum of sign * M(dr, i w_n) per walker as complex [2, nc, n_omega], sign sums, counts)."""
+        total = sum(2 * nc * self.n_omega_meas * 2 for nc in self.nc)
+        m = np.zeros(max(total, 1), np.float64)
+        ss = np.zeros(self.n_walkers, np.float64)
+        nm = np.zeros(self.n_walkers, np.int64)
+        self._check(self._L.dca_walker_measure_M(self._h, _ptr(m), _ptr(ss), _ptr(nm)))
+        out, off = [], 0
+        for nc in self.nc:
+            k = 2 * nc * self.n_omega_meas * 2
+            a = m[off:off + k].reshape(2, nc, self.n_omega_meas, 2)
+            out.append(a[..., 0] + 1j * a[..., 1])
+            off += k
+        return out, ss, nm
+
     def reset_measurements(self):
         self._check(self._L.dca_walker_reset_measurements(self._h))
 
@@ -395,3 +433,75 @@ class Walkers:
     def set_forced_decisions(self, wi, log):
         log = np.ascontiguousarray(log, np.uint8)
         self._check(self._L.dca_walker_set_forced_decisions(self._h, int(wi), _ptr(log), int(log.size)))
+
+
+# ---------------------------------------------------------------------------
+# Outer DCA loop (marshalling of the three C calls)
+# ---------------------------------------------------------------------------
+def _lattice(nc, kpts, k_dot_r, recip, t, tp, mu, U, beta, n_fine, keep):
+    kp = np.ascontiguousarray(kpts, np.float64)
+    kr = np.ascontiguousarray(k_dot_r, np.float64)
+    rc = np.ascontiguousarray(recip, np.float64).reshape(-1)
+    keep += [kp, kr]
+    lat = Lattice()
+    lat.nc = int(nc)
+    lat.kpts = kp.ctypes.data_as(C.POINTER(C.c_double))
+    lat.k_dot_r = kr.ctypes.data_as(C.POINTER(C.c_double))
+    for i in range(4):
+        lat.recip[i] = float(rc[i])
+    lat.t, lat.tp, lat.mu, lat.U, lat.beta = float(t), float(tp), float(mu), float(U), float(beta)
+    lat.n_fine = int(n_fine)
+    return lat
+
+
+def _c2(a):
+    a = np.ascontiguousarray(a, np.complex128)
+    return np.ascontiguousarray(np.stack([a.real, a.imag], axis=-1))
+
+
+def _from2(a):
+    return a[..., 0] + 1j * a[..., 1]
+
+
+class DCALoop:
+    """The outer DCA loop on the GPU for one cluster (dca_coarse_grain,
+    dca_sigma_update, dca_g0_table_from_freq)."""
+
+    def __init__(self, nc, kpts, k_dot_r, recip, t, tp, mu, U, beta, n_fine, n_omega):
+        self._keep = []
+        self.lat = _lattice(nc, kpts, k_dot_r, recip, t, tp, mu, U, beta, n_fine, self._keep)
+        self.nc, self.n_omega = int(nc), int(n_omega)
+        self._L = load()
+
+    def _check(self, rc):
+        if rc != DCA_OK:
+            raise WalkerError(rc, self._L.dca_walker_last_error(None).decode())
+
+    def coarse_grain(self, sigma):
+        """(Gbar, calG0, calG0', xi') from the cluster self-energy [nc, n_omega] (complex)."""
+        sig = _c2(sigma)
+        shp = (self.nc, self.n_omega, 2)
+        gb, g0, g0s = np.zeros(shp), np.zeros(shp), np.zeros(shp)
+        xi = np.zeros(self.nc)
+        self._check(self._L.dca_coarse_grain(C.byref(self.lat), self.n_omega, _ptr(sig), _ptr(gb), _ptr(g0),
+                                             _ptr(g0s), _ptr(xi)))
+        return _from2(gb), _from2(g0), _from2(g0s), xi
+
+    def sigma_update(self, G0w_shifted, M_sets, sign_sums, sigma_old, alpha):
+        """New Sigma from the walkers' accumulators M_sets [n_sets, 2, nc, n_omega] (complex)."""
+        g0s = _c2(G0w_shifted)
+        m = _c2(np.asarray(M_sets))
+        ss = np.ascontiguousarray(sign_sums, np.float64)
+        old = _c2(sigma_old)
+        out = np.zeros((self.nc, self.n_omega, 2))
+        self._check(self._L.dca_sigma_update(C.byref(self.lat), self.n_omega, _ptr(g0s), int(ss.size), _ptr(m),
+                                             _ptr(ss), _ptr(old), float(alpha), _ptr(out)))
+        return _from2(out)
+
+    def g0_table(self, G0w_shifted, xi, n_tau):
+        g0s = _c2(G0w_shifted)
+        x = np.ascontiguousarray(xi, np.float64)
+        out = np.zeros((2, self.nc, n_tau + 1))
+        self._check(self._L.dca_g0_table_from_freq(C.byref(self.lat), self.n_omega, _ptr(g0s), _ptr(x), int(n_tau),
+                                                   _ptr(out)))
+        return out
