@@ -135,6 +135,7 @@ def config_of(wl, world):
     return {"workload": wl.name, "nc": wl.nc, "t": wl.t, "tp": wl.tp, "U": wl.U, "beta": wl.beta, "mu": wl.mu,
             "K": wl.K, "walkers_per_gpu": wl.walkers, "k_sub": wl.k_sub, "n_tau": wl.n_tau,
             "n_tau_meas": wl.n_tau_meas, "recompute_every": wl.recompute_every, "recompute_sweeps": wl.recompute_sweeps,
+            "recompute_at_measure": wl.recompute_at_measure, "n_omega_meas": wl.n_omega_meas,
             "precision": wl.precision, "schedule": wl.schedule,
             "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)",
             **({"per_walker": {"nc": list(wl.nc_choices), "beta": list(wl.beta_range), "U": list(wl.U_range),
@@ -248,6 +249,67 @@ class OraclePool:
                 p.terminate()
 
 
+def g_error_sample(wl, k_sub, stream, warmup=17, measured=6):
+    """G error of the workload's mixed-precision arithmetic against the oracle
+    on identical trajectories: two of its walkers (the problems with beta
+    nearest 10 and 15) are run by the oracle (warm-up with the batched
+    recompute at sweeps 8 and 16, then measured sweeps) and replayed on the
+    GPU with the oracle's decisions, under both recompute schedules of the
+    mixed path; value = max over walkers of max|G - G_oracle| / max|G_oracle|
+    of the accumulated sign * G."""
+    import threading
+    import numpy as np
+    from oracle import ctaux
+    from paper_1901_01047_gb300 import walker
+    params, wp = wl.problem_params()
+    betas = np.array([p["beta"] for p in params])
+    picks = sorted({int(np.argmin(np.abs(betas - b))) for b in (10.0, 15.0)})
+    probs = {i: build_problem(params[wp[i]], use_gpu_builder=False) for i in picks}
+    sweeps = warmup + measured
+    runs = {}
+
+    def run_oracle(i):
+        # walker index within the sample: the GPU handle of the sample keys its
+        # Philox streams by that index
+        pr = probs[i]
+        ow = ctaux.OracleWalker(pr["nc"], pr["site_sub"], pr["U"], pr["beta"], pr["K"], pr["G0"],
+                                warmup_sweeps=warmup, n_tau_meas=wl.n_tau_meas, seed=wl.seed,
+                                walker_id=picks.index(i), init_config_size=wl.init_config_size)
+        ow.enable_log(1 << 24)
+        ow.sweep(sweeps)
+        runs[i] = (ow.log(), ow.G(), ow.order)
+
+    th = [threading.Thread(target=run_oracle, args=(i,)) for i in picks]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    out = {"norm": "max|G - G_oracle| / max|G_oracle| of the accumulated sign * G",
+           "sample": "walkers %s of the workload (N_c %s, beta %s, order %s after %d sweeps), %d warm-up and %d "
+                     "measured sweeps, the oracle's decisions replayed, k_s = %d" % (
+                         picks, [params[wp[i]]["nc"] for i in picks], [round(params[wp[i]]["beta"], 2) for i in picks],
+                         [runs[i][2] for i in picks], sweeps, warmup, measured, k_sub)}
+    for fresh in (wl.recompute_at_measure, not wl.recompute_at_measure):
+        gw = walker.Walkers([probs[i] for i in picks], n_walkers=len(picks), k_sub=k_sub, recompute_every=0,
+                            recompute_sweeps=wl.recompute_sweeps, warmup_sweeps=warmup, n_tau_meas=wl.n_tau_meas,
+                            precision="mixed", init_config_size=wl.init_config_size, seed=wl.seed,
+                            recompute_at_measure=fresh, log_capacity=1 << 24, stream=stream.cuda_stream)
+        errs = []
+        for j, i in enumerate(picks):
+            gw.set_forced_decisions(j, runs[i][0])
+        gw.sweep(sweeps)
+        G, ss, nm = gw.measure_G()
+        for j, i in enumerate(picks):
+            Go = runs[i][1][0]
+            errs.append(float(np.abs(G[j] - Go).max() / np.abs(Go).max()))
+        gw.close()
+        key = "value" if fresh == wl.recompute_at_measure else "other_recompute"
+        out[key] = max(errs)
+        out[key + "_per_walker"] = errs
+    out["recompute_at_measure"] = wl.recompute_at_measure
+    return out
+
+
 def cpu_baseline(wl_name, seconds=12.0):
     pool = OraclePool(wl_name)
     try:
@@ -309,6 +371,7 @@ def run_ours(args, rank, world, local_rank):
                         recompute_every=wl.recompute_every, recompute_sweeps=wl.recompute_sweeps,
                         warmup_sweeps=wl.warmup_sweeps, n_tau_meas=wl.n_tau_meas, precision=wl.precision,
                         init_config_size=wl.init_config_size, seed=seed, schedule=wl.schedule,
+                        recompute_at_measure=wl.recompute_at_measure, n_omega_meas=wl.n_omega_meas,
                         stream=stream.cuda_stream)
     gw.sweep(wl.warmup_sweeps)            # the chain's own warm-up (no measurements)
     tuned = None
@@ -387,6 +450,30 @@ def run_ours(args, rank, world, local_rank):
         other = {"schedule": "lockstep", "value": o_props / (o_ms / 1000.0), "unit": UNIT, "steps": k_other,
                  "ms_per_step": o_ms / k_other, "note": "one sweep of every walker per step; L2 not flushed"}
         gw.set_schedule(wl.schedule)
+
+    # The other recompute schedule of the mixed path (N recomputed at every
+    # measurement, or only every recompute_sweeps sweeps), same batch, shorter.
+    alt = None
+    if wl.precision == "mixed" and wl.recompute_sweeps > 0 and not args.profile_region:
+        alt_fresh = not wl.recompute_at_measure
+        gw.set_recompute(wl.recompute_every, wl.recompute_sweeps, alt_fresh)
+        gw.sweep(1)
+        k_alt = max(3, args.steps // 4)
+        sa0 = gw.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(k_alt):
+            flush.fill_(float(k))
+            gw.sweep(1, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        gw.sync()
+        sa1 = gw.stats()
+        a_props = sum(b["proposals"] - a["proposals"] for a, b in zip(sa0, sa1))
+        a_ms = e0.elapsed_time(e1)
+        alt = {"recompute_at_measure": alt_fresh, "value": a_props / (a_ms / 1000.0), "unit": UNIT, "steps": k_alt,
+               "ms_per_step": a_ms / k_alt, "note": "L2 flush inside the events"}
+        gw.set_recompute(wl.recompute_every, wl.recompute_sweeps, wl.recompute_at_measure)
 
     # Timed region 2 (the roofline): the same steps driven from the host with
     # CUDA events on the walker's stream around the dominant kernel group and
@@ -470,9 +557,12 @@ def run_ours(args, rank, world, local_rank):
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms),
                         "stdev": statistics.pstdev(step_ms)},
             **({"other_schedule": other} if other else {}),
+            **({"other_recompute": alt} if alt else {}),
         }
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.workload)
+            if wl.precision == "mixed":
+                out["g_error"] = g_error_sample(wl, gw.k_sub, stream)
         print(json.dumps(out))
     gw.close()
     if dist:

@@ -414,6 +414,14 @@ DCA_API int dca_walker_update_G0(dca_walker* w, int32_t problem, const double* G
  * autotuner.  Synchronises the stream. */
 DCA_API int dca_walker_set_tuning(dca_walker* w, int32_t k_sub, int32_t update_kernel);
 
+/* Change the recompute schedule between sweeps (the fields of the same names
+ * in dca_walker_params): recompute_every (windows, 0 = off), recompute_sweeps
+ * (batched schedule, 0 = off) and recompute_at_measure (0 or 1).  N is a
+ * function of the configuration, so the chains do not change; only the
+ * rounding carried by N between recomputes does.  Synchronises the stream. */
+DCA_API int dca_walker_set_recompute(dca_walker* w, int32_t recompute_every, int32_t recompute_sweeps,
+                                     int32_t recompute_at_measure);
+
 /* Kernel groups for timing: bit g of the mask times group g with CUDA events
  * recorded on the walker's stream around every launch of that group.
  *   0 proposals, 1 candidate extension (G columns / X rows), 2 Metropolis

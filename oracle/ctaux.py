@@ -32,6 +32,8 @@ class _Params(C.Structure):
         ("walker_id", C.c_uint32),
         ("init_config_size", C.c_int32),
         ("tie_eps", C.c_double),
+        ("flip_frac", C.c_double),
+        ("neglect_ks", C.c_int32),
     ]
 
 
@@ -74,6 +76,9 @@ def lib():
         L.orc_ratio.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int8,
                                 C.POINTER(C.c_double)]
         L.orc_enable_freq.argtypes = [P, C.c_int32]
+        L.orc_try_flip.argtypes = [P, C.c_int32, C.c_int32, C.POINTER(C.c_double)]
+        L.orc_neglected.argtypes = [P]
+        L.orc_neglected.restype = C.c_int64
         L.orc_get_M.argtypes = [P, C.c_void_p]
         _lib = L
     return _lib
@@ -102,7 +107,7 @@ class OracleWalker:
     """One CT-AUX Markov chain on the CPU (FP64, single-spin updates)."""
 
     def __init__(self, nc, site_sub, U, beta, K, G0, warmup_sweeps=20, n_tau_meas=64, seed=0,
-                 walker_id=0, init_config_size=10, tie_eps=1e-10):
+                 walker_id=0, init_config_size=10, tie_eps=1e-10, flip_frac=0.0, neglect_ks=0):
         self.nc = int(nc)
         self._site_sub = np.ascontiguousarray(site_sub, dtype=np.int32).reshape(-1)
         G0 = np.ascontiguousarray(G0, dtype=np.float64)
@@ -122,6 +127,8 @@ class OracleWalker:
         p.walker_id = int(walker_id)
         p.init_config_size = int(init_config_size)
         p.tie_eps = float(tie_eps)
+        p.flip_frac = float(flip_frac)
+        p.neglect_ks = int(neglect_ks)
         err = C.c_int(0)
         self._h = lib().orc_create(C.byref(p), C.byref(err))
         if not self._h:
@@ -248,6 +255,18 @@ class OracleWalker:
         rc = lib().orc_try_remove(self._h, int(p), 1 if accept else 0)
         if rc != 0:
             raise RuntimeError("try_remove failed %d" % rc)
+
+    def try_flip(self, p, accept=True):
+        """Flip the auxiliary spin of vertex p (forced); returns the ratio per spin."""
+        out = (C.c_double * 2)()
+        rc = lib().orc_try_flip(self._h, int(p), 1 if accept else 0, out)
+        if rc != 0:
+            raise RuntimeError("try_flip failed %d" % rc)
+        return out[0], out[1]
+
+    @property
+    def neglected(self):
+        return int(lib().orc_neglected(self._h))
 
     def ratio_insert(self, site, tau, s):
         out = (C.c_double * 2)()

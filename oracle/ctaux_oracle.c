@@ -26,7 +26,9 @@
  *     (G0 in the paper's sign convention, negative on (0, beta)),
  *     V_p^sigma = sigma * gamma * s_p for an interacting vertex, 0 otherwise;
  *   equal-time entries use g0(0+); g0(tau - beta) = -g0(tau);
- *   insert / remove proposed with probability 1/2 each, no spin flips;
+ *   insert / remove proposed with probability 1/2 each; optionally (flip_frac
+ *     > 0) an auxiliary-spin flip of a uniformly chosen vertex with
+ *     probability flip_frac first (R = rho_up rho_dn, order unchanged);
  *   acceptance  u < |R|,  R = K/(k+1) rho_up rho_dn (insert),
  *                         R = k/K     rho_up rho_dn (remove);
  *   a warm-up sweep is max(k, 1) proposals, k taken at the start of the
@@ -122,6 +124,8 @@ typedef struct {
     uint32_t walker_id;
     int32_t init_config_size;
     double tie_eps;           /* near-tie threshold on | |R| - u | */
+    double flip_frac;         /* probability of an auxiliary-spin flip proposal (0 = none) */
+    int32_t neglect_ks;       /* > 0: windows of this many proposals with the neglect rule (below) */
 } orc_params;
 
 typedef struct {
@@ -148,6 +152,12 @@ typedef struct {
     const uint8_t* hints; int64_t hints_n;
     int64_t n_prop, n_acc, n_ties, n_adopted;
     double k_sum; int64_t k_samples;   /* k_sum: sum over measurements of sign * k */
+    uint32_t flip_thr;        /* a proposal is a flip when (word0 >> 2) < flip_thr */
+    int32_t neglect_ks;       /* neglect rule: window length (0 = off) */
+    int64_t win_id;           /* neglect rule: current window (counted over the run) */
+    int64_t* changed;         /* [cap] window in which each vertex was last changed (neglect rule) */
+    int64_t n_neglected;      /* proposals rejected by the neglect rule */
+    double* Nsave[2];         /* copies of N while a flip is decided */
     int32_t n_omega;          /* frequency measurement: positive Matsubara frequencies, 0 = off */
     double* Macc;             /* [2][nc][n_omega][re, im]: sum of sign * M(dr, i w_n) */
 } orc_walker;
@@ -272,6 +282,15 @@ static int ensure_cap(orc_walker* w, int need)
     double* work = (double*)realloc(w->work, sizeof(double) * 8 * (size_t)nc);
     if (!work) return ORC_ERR_OOM;
     w->work = work;
+    int64_t* changed = (int64_t*)realloc(w->changed, sizeof(int64_t) * nc);
+    if (!changed) return ORC_ERR_OOM;
+    for (int i = w->cap; i < nc; ++i) changed[i] = -1;
+    w->changed = changed;
+    for (int sp = 0; sp < 2; ++sp) {
+        free(w->Nsave[sp]);
+        w->Nsave[sp] = (double*)malloc(sizeof(double) * (size_t)nc * nc);
+        if (!w->Nsave[sp]) return ORC_ERR_OOM;
+    }
     w->cap = nc;
     return ORC_OK;
 }
@@ -283,6 +302,7 @@ void orc_destroy(orc_walker* w)
     free(w->vsite); free(w->vtau); free(w->vs);
     free(w->N[0]); free(w->N[1]); free(w->work);
     free(w->Gacc); free(w->log); free(w->Macc);
+    free(w->changed); free(w->Nsave[0]); free(w->Nsave[1]);
     free(w);
 }
 
@@ -344,6 +364,11 @@ orc_walker* orc_create(const orc_params* p, int* err)
     w->key[0] = (uint32_t)p->seed;
     w->key[1] = (uint32_t)(p->seed >> 32) ^ p->walker_id;
     w->sign = 1.0;
+    if (!(p->flip_frac >= 0.0) || p->flip_frac > 1.0 || p->neglect_ks < 0) { orc_destroy(w); return NULL; }
+    /* flip when the 30 bits of word 0 above its type and spin bits fall below
+     * flip_frac of their range (the integer threshold both sides compute) */
+    w->flip_thr = (uint32_t)floor(p->flip_frac * 1073741824.0);
+    w->neglect_ks = p->neglect_ks;
 
     /* Initial configuration: init_config_size random interacting vertices
      * (App. B, "initial-configuration-size"). */
@@ -387,21 +412,19 @@ static int decide(orc_walker* w, double absR, double u, uint64_t q, int* tie)
     return acc;
 }
 
-/* Insert vertex (site, tau, s) as row/column k. */
-static int propose_insert(orc_walker* w, int32_t site, double tau, int8_t s, double u, uint64_t q)
+/* Ratio of inserting vertex (site, tau, s) as row/column k: fills the work
+ * vectors X (new row of the extended N), col (column change of A) and
+ * wv = N_ext col per spin, and rho = 1 + wv[k] (matrix determinant lemma). */
+static int insert_ratio(orc_walker* w, int32_t site, double tau, int8_t s, double rho[2])
 {
     int n = w->k;
     int rc = ensure_cap(w, n + 1);
     if (rc != ORC_OK) return rc;
     int ld = w->cap;
-    double* X[2];
-    double* col[2];
-    double* wv[2];
-    double rho[2];
     for (int sp = 0; sp < 2; ++sp) {
-        X[sp] = w->work + (size_t)(4 * sp + 0) * ld;
-        col[sp] = w->work + (size_t)(4 * sp + 1) * ld;
-        wv[sp] = w->work + (size_t)(4 * sp + 2) * ld;
+        double* X = w->work + (size_t)(4 * sp + 0) * ld;
+        double* col = w->work + (size_t)(4 * sp + 1) * ld;
+        double* wv = w->work + (size_t)(4 * sp + 2) * ld;
         double* N = w->N[sp];
         double* urow = w->work + (size_t)(4 * sp + 3) * ld;
         /* New (non-interacting) row of the extended N: X = g0[p,:] (e^V - 1) N. */
@@ -410,28 +433,63 @@ static int propose_insert(orc_walker* w, int32_t site, double tau, int8_t s, dou
         for (int j = 0; j < n; ++j) {
             double acc = 0.0;
             for (int i = 0; i < n; ++i) acc += urow[i] * N[(size_t)i * ld + j];
-            X[sp][j] = acc;
+            X[j] = acc;
         }
         /* Column change of A when V_p goes 0 -> sigma gamma s:
          * c = (I - g0_ext)[:,p] * (e^{V'} - 1). */
         double delta = ev(w, sp, s) - 1.0;
         for (int i = 0; i < n; ++i)
-            col[sp][i] = -g0ab(w, sp, w->vsite[i], w->vtau[i], site, tau) * delta;
-        col[sp][n] = (1.0 - g0ab(w, sp, site, 0.0, site, 0.0)) * delta;
+            col[i] = -g0ab(w, sp, w->vsite[i], w->vtau[i], site, tau) * delta;
+        col[n] = (1.0 - g0ab(w, sp, site, 0.0, site, 0.0)) * delta;
         /* wv = N_ext c ; N_ext = [[N, 0], [X, 1]]. */
         for (int i = 0; i < n; ++i) {
             double acc = 0.0;
-            for (int j = 0; j < n; ++j) acc += N[(size_t)i * ld + j] * col[sp][j];
-            wv[sp][i] = acc;
+            for (int j = 0; j < n; ++j) acc += N[(size_t)i * ld + j] * col[j];
+            wv[i] = acc;
         }
         {
             double acc = 0.0;
-            for (int j = 0; j < n; ++j) acc += X[sp][j] * col[sp][j];
-            wv[sp][n] = acc + col[sp][n];
+            for (int j = 0; j < n; ++j) acc += X[j] * col[j];
+            wv[n] = acc + col[n];
         }
-        rho[sp] = 1.0 + wv[sp][n]; /* matrix determinant lemma */
+        rho[sp] = 1.0 + wv[n];
     }
-    double R = w->K / (double)(n + 1) * rho[0] * rho[1];
+    return ORC_OK;
+}
+
+/* Apply the insertion whose work vectors insert_ratio left: N' = N_ext -
+ * wv (e_p^T N_ext) / rho, the vertex appended as row/column k. */
+static void insert_apply(orc_walker* w, int32_t site, double tau, int8_t s, const double rho[2])
+{
+    int n = w->k;
+    int ld = w->cap;
+    for (int sp = 0; sp < 2; ++sp) {
+        double* N = w->N[sp];
+        const double* X = w->work + (size_t)(4 * sp + 0) * ld;
+        const double* wv = w->work + (size_t)(4 * sp + 2) * ld;
+        for (int j = 0; j < n; ++j) { N[(size_t)n * ld + j] = X[j]; N[(size_t)j * ld + n] = 0.0; }
+        N[(size_t)n * ld + n] = 1.0;
+        double* rowp = w->work + (size_t)(4 * sp + 3) * ld;
+        for (int j = 0; j <= n; ++j) rowp[j] = N[(size_t)n * ld + j];
+        double inv = 1.0 / rho[sp];
+        for (int i = 0; i <= n; ++i) {
+            double f = wv[i] * inv;
+            if (f == 0.0) continue;
+            for (int j = 0; j <= n; ++j) N[(size_t)i * ld + j] -= f * rowp[j];
+        }
+    }
+    w->vsite[n] = site; w->vtau[n] = tau; w->vs[n] = s;
+    w->changed[n] = w->win_id;
+    w->k = n + 1;
+}
+
+/* Insert vertex (site, tau, s) as row/column k. */
+static int propose_insert(orc_walker* w, int32_t site, double tau, int8_t s, double u, uint64_t q)
+{
+    double rho[2];
+    int rc = insert_ratio(w, site, tau, s, rho);
+    if (rc != ORC_OK) return rc;
+    double R = w->K / (double)(w->k + 1) * rho[0] * rho[1];
     if (!isfinite(R)) return ORC_ERR_NUMERIC;
     int tie;
     int acc = decide(w, fabs(R), u, q, &tie);
@@ -440,29 +498,43 @@ static int propose_insert(orc_walker* w, int32_t site, double tau, int8_t s, dou
     if (!acc) return ORC_OK;
     w->n_acc++;
     if (R < 0.0) w->sign = -w->sign;
-    for (int sp = 0; sp < 2; ++sp) {
-        double* N = w->N[sp];
-        /* Write the extended matrix, then N' = N_ext - wv (e_p^T N_ext) / rho. */
-        for (int j = 0; j < n; ++j) { N[(size_t)n * ld + j] = X[sp][j]; N[(size_t)j * ld + n] = 0.0; }
-        N[(size_t)n * ld + n] = 1.0;
-        double* rowp = w->work + (size_t)(4 * sp + 3) * ld;
-        for (int j = 0; j <= n; ++j) rowp[j] = N[(size_t)n * ld + j];
-        double inv = 1.0 / rho[sp];
-        for (int i = 0; i <= n; ++i) {
-            double f = wv[sp][i] * inv;
-            if (f == 0.0) continue;
-            for (int j = 0; j <= n; ++j) N[(size_t)i * ld + j] -= f * rowp[j];
-        }
-    }
-    w->vsite[n] = site; w->vtau[n] = tau; w->vs[n] = s;
-    w->k = n + 1;
+    insert_apply(w, site, tau, s, rho);
     return ORC_OK;
 }
 
+/* Remove vertex p from the vertex list and N by the Schur-complement
+ * downdate N'_rs = N_rs - N_rp N_ps / N_pp (r, s != p). */
+static void remove_apply(orc_walker* w, int p)
+{
+    int n = w->k;
+    int ld = w->cap;
+    for (int sp = 0; sp < 2; ++sp) {
+        double* N = w->N[sp];
+        double* rowp = w->work + (size_t)(4 * sp + 3) * ld;
+        double* colp = w->work + (size_t)(4 * sp + 2) * ld;
+        for (int j = 0; j < n; ++j) { rowp[j] = N[(size_t)p * ld + j]; colp[j] = N[(size_t)j * ld + p]; }
+        double inv = 1.0 / N[(size_t)p * ld + p];
+        for (int i = 0, ii = 0; i < n; ++i) {
+            if (i == p) continue;
+            double f = colp[i] * inv;
+            for (int j = 0, jj = 0; j < n; ++j) {
+                if (j == p) continue;
+                /* write position (ii, jj) never passes the read position (i, j) */
+                N[(size_t)ii * ld + jj] = N[(size_t)i * ld + j] - f * rowp[j];
+                ++jj;
+            }
+            ++ii;
+        }
+    }
+    for (int i = p; i < n - 1; ++i) {
+        w->vsite[i] = w->vsite[i + 1]; w->vtau[i] = w->vtau[i + 1]; w->vs[i] = w->vs[i + 1];
+        w->changed[i] = w->changed[i + 1];
+    }
+    w->k = n - 1;
+}
+
 /* Remove vertex p.  With A = N^-1, the ratio det A_{\p\p} / det A is
- * (A^-1)_pp = N_pp (Jacobi's identity / Cramer's rule), and the inverse of
- * the reduced matrix is the Schur-complement downdate
- * N'_rs = N_rs - N_rp N_ps / N_pp  (r, s != p). */
+ * (A^-1)_pp = N_pp (Jacobi's identity / Cramer's rule). */
 static int propose_remove(orc_walker* w, int p, double u, uint64_t q)
 {
     int n = w->k;
@@ -478,52 +550,115 @@ static int propose_remove(orc_walker* w, int p, double u, uint64_t q)
     if (!acc) return ORC_OK;
     w->n_acc++;
     if (R < 0.0) w->sign = -w->sign;
-    for (int sp = 0; sp < 2; ++sp) {
-        double* N = w->N[sp];
-        double* rowp = w->work + (size_t)(4 * sp + 3) * ld;
-        double* colp = w->work + (size_t)(4 * sp + 2) * ld;
-        for (int j = 0; j < n; ++j) { rowp[j] = N[(size_t)p * ld + j]; colp[j] = N[(size_t)j * ld + p]; }
-        double inv = 1.0 / rho[sp];
-        for (int i = 0, ii = 0; i < n; ++i) {
-            if (i == p) continue;
-            double f = colp[i] * inv;
-            for (int j = 0, jj = 0; j < n; ++j) {
-                if (j == p) continue;
-                /* write position (ii, jj) never passes the read position (i, j) */
-                N[(size_t)ii * ld + jj] = N[(size_t)i * ld + j] - f * rowp[j];
-                ++jj;
-            }
-            ++ii;
-        }
-    }
-    for (int i = p; i < n - 1; ++i) {
-        w->vsite[i] = w->vsite[i + 1]; w->vtau[i] = w->vtau[i + 1]; w->vs[i] = w->vs[i + 1];
-    }
-    w->k = n - 1;
+    remove_apply(w, p);
     return ORC_OK;
 }
 
-/* Proposal number q: type (insert / remove with probability 1/2), the
- * new vertex or the removal index, and u for the Metropolis test. */
+/* Flip the auxiliary spin of vertex p (the third single-spin update of
+ * Sec. 2.3): the order k is unchanged, so R = prod_sigma det A'/det A.  The
+ * flip is carried out as the removal of p (Jacobi ratio N_pp, Schur
+ * downdate) followed by the insertion of (r_p, tau_p, -s_p) (determinant
+ * lemma, Sherman-Morrison), R = prod_sigma N_pp rho_ins, and the inserted
+ * row and column are moved back to position p; a rejected flip restores the
+ * saved N.  (A direct rank-1 change of column p by e^{-V_p} - e^{V_p} would
+ * amplify rounding by that factor, as for removals.) */
+static int propose_flip(orc_walker* w, int p, double u, uint64_t q, double* rho_out)
+{
+    int n = w->k;
+    int ld = w->cap;
+    for (int sp = 0; sp < 2; ++sp)
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) w->Nsave[sp][(size_t)i * ld + j] = w->N[sp][(size_t)i * ld + j];
+    const int32_t site = w->vsite[p];
+    const double tau = w->vtau[p];
+    const int8_t s = w->vs[p];
+    const int64_t ch = w->changed[p];
+    double rho_rem[2], rho_ins[2];
+    for (int sp = 0; sp < 2; ++sp) rho_rem[sp] = w->N[sp][(size_t)p * ld + p];
+    remove_apply(w, p);
+    int rc = insert_ratio(w, site, tau, (int8_t)-s, rho_ins);
+    if (rc != ORC_OK) return rc;
+    double R = rho_rem[0] * rho_ins[0] * rho_rem[1] * rho_ins[1];
+    if (rho_out)
+        for (int sp = 0; sp < 2; ++sp) rho_out[sp] = rho_rem[sp] * rho_ins[sp];
+    if (!isfinite(R)) return ORC_ERR_NUMERIC;
+    int tie;
+    int acc = decide(w, fabs(R), u, q, &tie);
+    w->n_prop++;
+    log_push(w, (uint8_t)(acc | (tie << 1)));
+    if (!acc) {
+        /* restore: vertex p and the saved N */
+        for (int i = n - 1; i > p; --i) {
+            w->vsite[i] = w->vsite[i - 1]; w->vtau[i] = w->vtau[i - 1]; w->vs[i] = w->vs[i - 1];
+            w->changed[i] = w->changed[i - 1];
+        }
+        w->vsite[p] = site; w->vtau[p] = tau; w->vs[p] = s; w->changed[p] = ch;
+        w->k = n;
+        for (int sp = 0; sp < 2; ++sp)
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) w->N[sp][(size_t)i * ld + j] = w->Nsave[sp][(size_t)i * ld + j];
+        return ORC_OK;
+    }
+    w->n_acc++;
+    if (R < 0.0) w->sign = -w->sign;
+    insert_apply(w, site, tau, (int8_t)-s, rho_ins);
+    /* move row and column n - 1 back to position p */
+    for (int sp = 0; sp < 2; ++sp) {
+        double* N = w->N[sp];
+        double* tmp = w->work + (size_t)(4 * sp + 3) * ld;
+        for (int j = 0; j < n; ++j) tmp[j] = N[(size_t)(n - 1) * ld + j];
+        for (int i = n - 1; i > p; --i)
+            for (int j = 0; j < n; ++j) N[(size_t)i * ld + j] = N[(size_t)(i - 1) * ld + j];
+        for (int j = 0; j < n; ++j) N[(size_t)p * ld + j] = tmp[j];
+        for (int i = 0; i < n; ++i) {
+            double* row = N + (size_t)i * ld;
+            double v = row[n - 1];
+            for (int j = n - 1; j > p; --j) row[j] = row[j - 1];
+            row[p] = v;
+        }
+    }
+    for (int i = n - 1; i > p; --i) {
+        w->vsite[i] = w->vsite[i - 1]; w->vtau[i] = w->vtau[i - 1]; w->vs[i] = w->vs[i - 1];
+        w->changed[i] = w->changed[i - 1];
+    }
+    w->vsite[p] = site; w->vtau[p] = tau; w->vs[p] = (int8_t)-s; w->changed[p] = w->win_id;
+    return ORC_OK;
+}
+
+/* Proposal number q: type (flip with probability flip_frac, else insert /
+ * remove with probability 1/2 each), the new vertex or the index of the
+ * vertex to remove or flip, and u for the Metropolis test.  With the
+ * neglect rule on, a removal or flip of a vertex already changed in the
+ * current window of neglect_ks proposals is rejected (Sec. 2.3, "Submatrix
+ * updates": ignoring proposals of already chosen spins; it breaks detailed
+ * balance).  Without it the chain is that of single-spin updates (the
+ * abort variant of the submatrix method reaches the same chain). */
 static int propose(orc_walker* w, uint64_t q)
 {
     uint32_t r[4], a[4];
     draw(w->key, q, TAG_PROPOSAL, r);
     draw(w->key, q, TAG_ACCEPT, a);
     double u = u53(a[0], a[1]);
-    if ((r[0] & 1u) == 0u) {
+    const int flip = w->flip_thr > 0u && (r[0] >> 2) < w->flip_thr;
+    if (!flip && (r[0] & 1u) == 0u) {
         int8_t s = (r[0] & 2u) ? 1 : -1;
         int32_t site = (int32_t)index_of(r[1], (uint32_t)w->nc);
         double tau = w->beta * u53(r[2], r[3]);
         return propose_insert(w, site, tau, s, u, q);
     }
-    if (w->k == 0) { /* nothing to remove: rejected */
+    if (w->k == 0) { /* nothing to remove or flip: rejected */
         w->n_prop++;
         log_push(w, 0);
         return ORC_OK;
     }
     int p = (int)index_of(r[1], (uint32_t)w->k);
-    return propose_remove(w, p, u, q);
+    if (w->neglect_ks > 0 && w->changed[p] == w->win_id) {
+        w->n_prop++;
+        w->n_neglected++;
+        log_push(w, 0);
+        return ORC_OK;
+    }
+    return flip ? propose_flip(w, p, u, q, NULL) : propose_remove(w, p, u, q);
 }
 
 /* ------------------------------------------------------------------ */
@@ -646,6 +781,8 @@ int orc_sweep(orc_walker* w, int32_t n_sweeps)
             len = w->sweep_len;
         }
         for (int64_t t = 0; t < len; ++t) {
+            /* windows of neglect_ks proposals, never across a sweep boundary */
+            if (w->neglect_ks > 0 && (t % w->neglect_ks) == 0) w->win_id++;
             int rc = propose(w, w->q);
             if (rc != ORC_OK) return rc;
             w->q++;
@@ -774,6 +911,7 @@ int orc_set_config(orc_walker* w, int32_t n, const int32_t* site, const double* 
     for (int i = 0; i < n; ++i) {
         if (site[i] < 0 || site[i] >= w->nc || (s[i] != 1 && s[i] != -1)) return ORC_ERR_ARG;
         w->vsite[i] = site[i]; w->vtau[i] = tau[i]; w->vs[i] = s[i];
+        w->changed[i] = -1;
     }
     w->k = n;
     return rebuild_N(w, &w->sign);
@@ -801,6 +939,20 @@ int orc_try_remove(orc_walker* w, int32_t p, int32_t force)
     w->n_ties = saved[0]; w->n_prop = saved[1]; w->log_n = saved[2];
     return rc;
 }
+
+/* Flip the auxiliary spin of vertex p, forced accepted (force = 1) or
+ * rejected (0); rho_out (may be NULL) receives the ratio per spin. */
+int orc_try_flip(orc_walker* w, int32_t p, int32_t force, double* rho_out)
+{
+    if (p < 0 || p >= w->k) return ORC_ERR_ARG;
+    double u = force ? -1.0 : 1.0e300;
+    int64_t saved[3] = {w->n_ties, w->n_prop, w->log_n};
+    int rc = propose_flip(w, p, u, UINT64_MAX, rho_out);
+    w->n_ties = saved[0]; w->n_prop = saved[1]; w->log_n = saved[2];
+    return rc;
+}
+
+int64_t orc_neglected(const orc_walker* w) { return w->n_neglected; }
 
 /* Determinant ratio rho_sigma (both spins) of a proposed insert or remove
  * on the current state, without changing it. */

@@ -45,13 +45,13 @@ __device__ __forceinline__ bool wants_nfft(const Config& cfg, const WalkerDev& w
   return cfg.n_omega > 0 && w.active && w.measure_pending;
 }
 
-// Spread one sample (value m at grid position x in [0, L)) into the grid
-// row `g` (length L) with atomic adds in the accumulation type S (FP64: the
-// weights and values are A, their sums over many samples are not).
+// Spread one sample (value m at grid position l0 + d, d in [0, 1), the
+// position split in FP64 so that an FP32 fraction keeps it to 2^-24 of a grid
+// step) into the grid row `g` (length L) with atomic adds in the accumulation
+// type S (FP64: the weights and values are A, their sums over many samples
+// are not).
 template <typename A, typename S>
-__device__ __forceinline__ void spread_sample(S* g, int L, int msp, A a, const A* e3, A x, A m) {
-  const int l0 = (int)x;
-  const A d = x - (A)l0;
+__device__ __forceinline__ void spread_sample(S* g, int L, int msp, A a, const A* e3, int l0, A d, A m) {
   const A e1 = m * (A)exp(-a * d * d);
   const A e2 = (A)exp((A)2 * a * d);
   const A e2i = (A)1 / e2;
@@ -133,8 +133,9 @@ __global__ void __launch_bounds__(256) k_meas_nfft(Config cfg) {
             }
             double x = t * inv_h;
             if (x >= (double)L) x = (double)L - 0.5;  // t within rounding of beta
+            const int l0 = (int)x;
             const int d = __ldg(sub_row + vsite[j]);
-            spread_sample<A, S>(g + (size_t)d * L, L, msp, a, s_e3, (A)x, (A)m);
+            spread_sample<A, S>(g + (size_t)d * L, L, msp, a, s_e3, l0, (A)(x - (double)l0), (A)m);
           }
         }
         if (SMEM) {

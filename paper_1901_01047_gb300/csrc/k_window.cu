@@ -797,7 +797,9 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
       }
       // Batched schedule: every walker recomputes after the first window of
       // every recompute_sweeps-th sweep (the same window for all walkers).
-      if (cfg.recompute_sweeps > 0 && w.first_window && sweep_no > 0 && sweep_no % cfg.recompute_sweeps == 0) {
+      // (With N recomputed at every measurement the measured sweeps need no other.)
+      if (cfg.recompute_sweeps > 0 && w.first_window && sweep_no > 0 && sweep_no % cfg.recompute_sweeps == 0 &&
+          !(cfg.recompute_at_measure && sweep_no > cfg.warmup)) {
         w.recompute_pending = 1;
         w.windows_since_recompute = 0;
       }

@@ -734,6 +734,20 @@ extern "C" DCA_API int dca_walker_set_schedule(dca_walker* h, int32_t schedule) 
   return DCA_OK;
 }
 
+extern "C" DCA_API int dca_walker_set_recompute(dca_walker* h, int32_t recompute_every, int32_t recompute_sweeps,
+                                                int32_t recompute_at_measure) {
+  if (!h) return DCA_ERR_ARG;
+  if (recompute_every < 0 || recompute_sweeps < 0 || recompute_at_measure < 0 || recompute_at_measure > 1)
+    return fail(h, DCA_ERR_ARG, "invalid recompute schedule");
+  CK(cudaStreamSynchronize(h->stream));
+  h->R = recompute_every;
+  h->cfg.recompute_every = recompute_every;
+  h->cfg.recompute_sweeps = recompute_sweeps;
+  h->cfg.recompute_at_measure = recompute_at_measure;
+  drop_loop_graph(h);
+  return DCA_OK;
+}
+
 extern "C" DCA_API int dca_walker_set_limits(dca_walker* h, int64_t max_windows, int64_t wait_cycles) {
   if (!h) return DCA_ERR_ARG;
   if (max_windows < 0 || wait_cycles < 0) return fail(h, DCA_ERR_ARG, "negative limit");

@@ -25,6 +25,7 @@ EXPORTS = [
     "dca_walker_get_timing", "dca_walker_set_tuning", "dca_fresh_N", "dca_fresh_N_noalloc",
     "dca_walker_sync", "dca_walker_set_schedule", "dca_walker_set_limits", "dca_walker_save", "dca_walker_load",
     "dca_walker_measure_M", "dca_coarse_grain", "dca_sigma_update", "dca_g0_table_from_freq",
+    "dca_walker_set_recompute",
 ]
 UPDATE_KERNELS = {"auto": 0, "cuda_core": 1, "tcgen05": 2}
 # lockstep: every walker runs n more sweeps per sweep(n); pooled: the walkers
@@ -136,6 +137,7 @@ def load(path=LIB_PATH):
     L.dca_walker_sync.argtypes = [P]
     L.dca_walker_set_schedule.argtypes = [P, C.c_int32]
     L.dca_walker_set_limits.argtypes = [P, C.c_int64, C.c_int64]
+    L.dca_walker_set_recompute.argtypes = [P, C.c_int32, C.c_int32, C.c_int32]
     L.dca_walker_save.argtypes = [P, P, C.c_size_t, C.POINTER(C.c_size_t)]
     L.dca_walker_load.argtypes = [P, P, C.c_size_t]
     L.dca_walker_measure_G.argtypes = [P, P, P, P]
@@ -325,6 +327,11 @@ class Walkers:
     def set_schedule(self, schedule):
         s = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
         self._check(self._L.dca_walker_set_schedule(self._h, s))
+
+    def set_recompute(self, recompute_every=0, recompute_sweeps=0, recompute_at_measure=False):
+        """Change the recompute schedule between sweeps (same chains)."""
+        self._check(self._L.dca_walker_set_recompute(self._h, int(recompute_every), int(recompute_sweeps),
+                                                     1 if recompute_at_measure else 0))
 
     def set_limits(self, max_windows=0, wait_cycles=0):
         self._check(self._L.dca_walker_set_limits(self._h, int(max_windows), int(wait_cycles)))

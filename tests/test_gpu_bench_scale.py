@@ -25,12 +25,17 @@ from tests.helpers import problem
 
 pytestmark = pytest.mark.gpu
 
-# Mixed-path bounds for walkers of order up to ~1100 (conditioning of N^-1 up
-# to ~1e7), recomputing every 8 (4) sweeps: a few times the largest errors
-# measured on these chains.  With N recomputed before every measurement the
-# accumulated G is limited by the FP32 measurement arithmetic only.
-TOL_N = 2e-3
-TOL_G = 2e-3
+# Mixed-path bounds, about three times the largest errors measured on these
+# chains (the error budget of the mixed path: FP32 storage of N and the drift
+# of the 3xTF32 updates between recomputes).  Batch of orders up to ~1180,
+# recompute every 8 sweeps: N 1.4e-4, G 3.4e-5.  36-site walkers (order
+# ~700, recompute every 4 sweeps, a sign problem): N 1.8e-4, G 5.9e-4.  With
+# N recomputed before every measurement, G is limited by the FP32
+# measurement arithmetic: measured 5e-8 .. 3.1e-7 on both; the bound is the
+# target of the mixed path, 1e-6.
+TOL_N = 5e-4
+TOL_G_BATCH = 1e-4
+TOL_G_36 = 2e-3
 TOL_G_FRESH = 1e-6
 
 
@@ -186,7 +191,7 @@ def test_batched_pooled_four_branch_replay_at_bench_scale():
     assert big["max_order"] >= 1000, big
     assert all(r["recomputes"] >= 3 and r["measurements"] >= 2 for r in res), res
     for r in res:
-        assert r["errN"] < TOL_N and r["errG"] < TOL_G, r
+        assert r["errN"] < TOL_N and r["errG"] < TOL_G_BATCH, r
     # Half filling on bipartite clusters (t' = 0): no sign problem, so every
     # walker, free-running ones included, keeps sign +1 in every measurement.
     assert signs == [True] * W, [wi for wi, ok in enumerate(signs) if not ok]
@@ -213,7 +218,7 @@ def test_betts36_walkers_replay_the_oracle():
     print("36-site replay:", res)
     for r in res:
         assert r["order"] >= 400, r
-        assert r["errN"] < TOL_N and r["errG"] < TOL_G, r
+        assert r["errN"] < TOL_N and r["errG"] < TOL_G_36, r
     res, _ = _replay_batch(probs, runs, recompute_at_measure=True, **kw)
     print("36-site replay, N recomputed at every measurement:", res)
     for r in res:

@@ -24,7 +24,7 @@ def _walkers(**kw):
 
 
 def replay(nc, tp, U, beta, mu, k_sub, sweeps, R, seed=0, ntm=32, n_tau=4096, update_kernel="auto",
-           return_state=False, recompute_method="auto"):
+           return_state=False, recompute_method="auto", recompute_at_measure=False, precision="mixed"):
     c, eps, kr, G0 = problem(nc, 1.0, tp, U, beta, mu, n_tau)
     ow = ctaux.OracleWalker(nc, c.site_sub, U, beta, 1.0, G0, warmup_sweeps=10, n_tau_meas=ntm, seed=seed)
     ow.enable_log(1 << 24)
@@ -62,16 +62,19 @@ UPDATE_KERNELS = ["cuda_core", "tcgen05"]
 @pytest.mark.parametrize("kern", UPDATE_KERNELS)
 def test_mixed_replay_2x2_errors(kern):
     errN, errG, st, _ = replay(4, 0.0, 4.0, 10.0, 0.9450480104035819, 32, 2000, 64, update_kernel=kern)
+    print("2x2 %s R=64: N %.2e G %.2e" % (kern, errN, errG))
     assert st["status"] == 0 and st["recomputes"] > 0
     assert errN < 1e-4, errN
     assert errG < 3e-4, errG
     errN8, errG8, st8, _ = replay(4, 0.0, 4.0, 10.0, 0.9450480104035819, 32, 2000, 8, update_kernel=kern)
+    print("2x2 %s R=8: N %.2e G %.2e" % (kern, errN8, errG8))
     assert errG8 < 1e-4, errG8
 
 
 @pytest.mark.parametrize("kern", UPDATE_KERNELS)
 def test_mixed_replay_16_site_errors(kern):
     errN, errG, st, _ = replay(16, -0.15, 6.0, 4.0, 2.85, 64, 60, 64, ntm=16, n_tau=2048, update_kernel=kern)
+    print("16 sites %s R=64: N %.2e G %.2e" % (kern, errN, errG))
     assert errN < 3e-4, errN
     assert errG < 5e-5, errG
 
@@ -111,6 +114,7 @@ def test_tensor_core_update_matches_cuda_core_update(k_sub):
     # mixed path's error budget; the two stay within the sum of their drifts
     # of each other.
     # (the floor is the mixed path's error budget of the 16-site replay test)
+    print("k_s %d: tcgen05 N %.2e G %.2e, CUDA core N %.2e G %.2e" % (k_sub, eN_t, eG_t, eN_c, eG_c))
     assert eN_t <= 6 * eN_c + 1e-4 and eG_t <= 6 * eG_c + 2e-5, (eN_t, eN_c, eG_t, eG_c)
     for sp in range(2):
         a, b = gs_c["N"][sp], gs_t["N"][sp]
@@ -143,6 +147,7 @@ def test_mixed_recompute_methods_restore_accuracy(method):
     # inverse both bring N back to the FP32 level: recomputing every 8
     # submatrix updates keeps the error of N and G small on the 16-site case.
     errN, errG, st, _ = replay(16, -0.15, 6.0, 4.0, 2.85, 64, 60, 8, ntm=16, n_tau=2048, recompute_method=method)
+    print("16 sites recompute %s every 8: N %.2e G %.2e drift %.2e" % (method, errN, errG, st["max_drift"]))
     assert st["status"] == 0 and st["recomputes"] >= 10
     assert errN < 1e-4, errN
     assert errG < 2e-5, errG
@@ -174,6 +179,29 @@ def test_mixed_replay_error_at_the_batched_recompute_interval():
     # largest walkers; the 16-site case recomputing every 320 windows states
     # the error reached there.
     errN, errG, st, _ = replay(16, -0.15, 6.0, 4.0, 2.85, 16, 200, 320, ntm=16, n_tau=2048)
+    print("16 sites R=320: N %.2e G %.2e" % (errN, errG))
     assert st["status"] == 0 and st["recomputes"] >= 1
     assert errN < 2e-4, errN  # measured 2.5e-5
     assert errG < 3e-5, errG  # measured 4.3e-6
+
+
+def test_mixed_replay_with_N_recomputed_at_every_measurement_meets_1e6():
+    # The error of the mixed path is carried by N between recomputes; with N
+    # recomputed before every measurement the accumulated G is within 1e-6 of
+    # the FP64 oracle (measured 1.3e-7 on the 2x2 case and 5.6e-8 on 16 sites).
+    errN, errG, st, _ = replay(4, 0.0, 4.0, 10.0, 0.9450480104035819, 32, 400, 64, recompute_at_measure=True)
+    print("2x2 recompute at every measurement: N %.2e G %.2e" % (errN, errG))
+    assert errG < 1e-6, errG
+    errN, errG, st, _ = replay(16, -0.15, 6.0, 4.0, 2.85, 64, 60, 64, ntm=16, n_tau=2048, recompute_at_measure=True)
+    print("16 sites recompute at every measurement: N %.2e G %.2e" % (errN, errG))
+    assert errG < 1e-6, errG
+    assert errN < 1e-6, errN  # N was just recomputed: its FP32 rounding
+
+
+def test_tf32_single_product_replay_error():
+    # One TF32 product per K step (about 11 bits): the error the 3xTF32 split
+    # removes (measured 2.9e-3 on N and 2.1e-2 on G for this case)
+    errN, errG, st, _ = replay(4, 0.0, 4.0, 10.0, 0.9450480104035819, 32, 400, 8, precision="tf32")
+    print("2x2 TF32 R=8: N %.2e G %.2e" % (errN, errG))
+    assert st["status"] == 0
+    assert 1e-4 < errN < 5e-2 and errG < 0.1
