@@ -30,7 +30,11 @@
  *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key
  *     (lo32(seed), hi32(seed) ^ walker_index) and counter
  *     (lo32(j), hi32(j), tag, 0); tag 0 = proposal words, 1 = acceptance
- *     uniform, 2 = initial configuration.
+ *     uniform, 2 = initial configuration.  Proposal q from its words w0..w3:
+ *     a flip when (w0 >> 2) < floor(flip_fraction * 2^30), else an insertion
+ *     (w0 bit 0 clear: spin from bit 1, site floor(w1 nc / 2^32), time
+ *     beta u53(w2, w3)) or a removal; removal and flip pick the vertex
+ *     floor(w1 k / 2^32) of the current order k.
  */
 #ifndef DCA_WALKER_H
 #define DCA_WALKER_H
@@ -128,7 +132,21 @@ typedef struct {
   int32_t n_omega_meas;            /* frequency measurement of M (delayed NFFT, read by
                                       dca_walker_measure_M): positive fermionic Matsubara
                                       frequencies, 8..4096; 0 = off */
+  double flip_fraction;            /* probability that a proposal is an auxiliary-spin flip of
+                                      a uniformly chosen vertex (Sec. 2.3, the third single-spin
+                                      update; R = rho_up rho_dn), in [0, 1]; else insert / remove
+                                      with probability 1/2 each.  0 = no flips */
+  int32_t duplicate_rule;          /* DCA_DUP_*: a removal or flip that picks a spin already
+                                      changed in the current submatrix update */
 } dca_walker_params;
+
+/* Spins changed twice in one submatrix update (Sec. 2.3, "Submatrix updates"):
+ *   ABORT:   end the update before that proposal and evaluate it first in the
+ *            next one (exact: the chain of single-spin updates);
+ *   NEGLECT: reject the proposal (no performance loss; breaks detailed
+ *            balance, as the paper notes). */
+#define DCA_DUP_ABORT 0
+#define DCA_DUP_NEGLECT 1
 
 /* Scheduling of the walkers by dca_walker_sweep(n).  The chains do not depend
  * on it: each walker's windows, recomputes and measurements follow from its
@@ -185,6 +203,7 @@ typedef struct {
   double extend_flops;      /* flop of the candidate extension (4 n^2 c per spin) */
   double extend_bytes;      /* algorithmic bytes of the candidate extension (one read of N per spin) */
   double recompute_flops;   /* flop of the from-scratch inverses (2 n^3 per spin) */
+  int64_t neglected;        /* proposals rejected by DCA_DUP_NEGLECT */
 } dca_walker_stats_t;
 
 typedef struct dca_walker dca_walker;

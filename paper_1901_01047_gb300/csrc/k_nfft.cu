@@ -38,7 +38,7 @@
 
 namespace dca {
 
-constexpr int NFFT_RB = 64;        // rows of N per item
+constexpr int NFFT_RB = 128;       // rows of N per item
 constexpr int NFFT_MSP_MAX = 12;
 
 __device__ __forceinline__ bool wants_nfft(const Config& cfg, const WalkerDev& w) {
@@ -48,8 +48,7 @@ __device__ __forceinline__ bool wants_nfft(const Config& cfg, const WalkerDev& w
 // Spread one sample (value m at grid position l0 + d, d in [0, 1), the
 // position split in FP64 so that an FP32 fraction keeps it to 2^-24 of a grid
 // step) into the grid row `g` (length L) with atomic adds in the accumulation
-// type S (FP64: the weights and values are A, their sums over many samples
-// are not).
+// type S.
 template <typename A, typename S>
 __device__ __forceinline__ void spread_sample(S* g, int L, int msp, A a, const A* e3, int l0, A d, A m) {
   const A e1 = m * (A)exp(-a * d * d);
@@ -107,7 +106,8 @@ __global__ void __launch_bounds__(256) k_meas_nfft(Config cfg) {
         const int* vsite = w.vsite[par];
         const double* vtau = w.vtau[par];
         double* gglob = w.Mgrid + (size_t)sp * nc * L;
-        using S = double;  // accumulation in FP64 on both paths (shared-memory atomics when staged)
+        // accumulation: the staged grid in A (one item's sums), the walker's grid in FP64
+        using S = typename std::conditional<SMEM, A, double>::type;
         S* g = SMEM ? reinterpret_cast<S*>(nfft_raw) : reinterpret_cast<S*>(gglob);
         __syncthreads();  // the previous item of this block is done with the staged grid
         if (SMEM)
@@ -185,7 +185,10 @@ __global__ void __launch_bounds__(256) k_nfft_finish(Config cfg, const long long
 // accumulated in global memory directly.
 constexpr size_t NFFT_SMEM_MAX = 160 * 1024;
 
-size_t nfft_smem_bytes(const Config& cfg, int max_nc) { return (size_t)max_nc * (size_t)cfg.nfft_L * sizeof(double); }
+size_t nfft_smem_bytes(const Config& cfg, int max_nc) {
+  const size_t acc = cfg.prec == PREC_MIXED ? sizeof(float) : sizeof(double);
+  return (size_t)max_nc * (size_t)cfg.nfft_L * acc;
+}
 
 cudaError_t setup_nfft() {
   cudaError_t e = cudaFuncSetAttribute(k_meas_nfft<double, double, true>,

@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(128) k_begin(Config cfg) {
     const Philox4 r = draw(w, qj, TAG_PROPOSAL);
     const Philox4 a = draw(w, qj, TAG_ACCEPT);
     pr.u = uniform53(a.v[0], a.v[1]);
-    pr.type = (int)(r.v[0] & 1u);
+    const bool flip = cfg.flip_thr > 0u && (r.v[0] >> 2) < cfg.flip_thr;
+    pr.type = flip ? 2 : (int)(r.v[0] & 1u);
     pr.s = (r.v[0] & 2u) ? 1 : -1;
     pr.site = (int)scaled_index(r.v[1], (uint32_t)pb.nc);
     pr.tau = pb.beta * uniform53(r.v[2], r.v[3]);
@@ -157,9 +158,10 @@ constexpr int ET = 64;   // tile of the extension kernel
 constexpr int EC = 32;   // candidates per pass
 
 // Persistent grid; one item = 256 vertices i of one walker-spin, all
-// candidates c: clears the reduction targets Gc / Xr and tabulates the
-// candidate factors V and U once per window (the tile kernel then reads them
-// instead of interpolating).  The mixed path interpolates on the split grid
+// candidates c: clears the reduction targets (the FP64 path's Gc / Xr, and
+// the candidate-block rows of Gc) and tabulates the candidate factors V and U
+// once per window (the tile kernels then read them instead of interpolating;
+// the tensor-core path takes U only in its split form).  The mixed path interpolates on the split grid
 // time (FP32 arithmetic), the FP64 path in FP64.
 __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
   __shared__ GridTime s_gc[KS_MAX];
@@ -208,8 +210,10 @@ __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
         const float em1f = (float)em1;
         for (int c = 0; c < nc_; ++c) {
           const size_t o = (size_t)c * ld + i;
-          w.Gc[sp][o] = 0.0;
-          w.Xr[sp][o] = 0.0;
+          if (!mixed) {  // targets of the FP64 path's atomics (the mixed-path kernels store rows < n whole)
+            w.Gc[sp][o] = 0.0;
+            w.Xr[sp][o] = 0.0;
+          }
           const int rc = s_rc[c];
           if (mixed) {
             float v = 0.0f, u = 0.0f;
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
               u = g0_interp_grid(g0f_row(pb, sp, __ldg(pb.site_sub + rc * pb.nc + ri)), pb.n_tau, s_gc[c], gi) * em1f;
             }
             reinterpret_cast<float*>(w.Vb[sp])[o] = v;
-            reinterpret_cast<float*>(w.Ub[sp])[o] = u;
+            if (!Vop) reinterpret_cast<float*>(w.Ub[sp])[o] = u;  // read only by the CUDA-core X pass
             if (Vop) {
               float hv, lv, hu, lu;
               tc::tf32_split(v, hv, lv);
@@ -517,9 +521,10 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
   __shared__ int s_P[KS_MAX];
   __shared__ int s_Pup[KS_MAX];       // spin of a live P_p > 0
   __shared__ int s_removed[KS_MAX];   // live ranks removed in this window, ascending
+  __shared__ int s_flipped[KS_MAX];   // live ranks whose auxiliary spin was flipped in this window
   __shared__ double s_ev[2][2], s_rv[2][2];  // e^{V} and 1 / (e^{V} - 1): [spin][s > 0]
   __shared__ double s_anew[2], s_Btt[2];
-  __shared__ int s_target, s_tup, s_kind, s_stop, s_accept, s_l, s_nrem, s_nins, s_kcur, s_eval, s_rank;
+  __shared__ int s_target, s_tup, s_kind, s_stop, s_accept, s_l, s_nrem, s_nins, s_kcur, s_eval, s_rank, s_nflip;
   __shared__ double s_sign;
 
   const bool live_smem = n_live <= METRO_LIVE;
@@ -538,6 +543,7 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
     s_l = 0;
     s_nrem = 0;
     s_nins = 0;
+    s_nflip = 0;
     s_stop = 0;
     s_sign = w.sign;
     s_eval = 0;
@@ -546,10 +552,16 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
   const uint64_t q0 = w.q;
   const int64_t forced_n = w.forced_n, log_cap = w.log_cap;
   const double K = pb.K;
-  int64_t c_prop = 0, c_acc = 0, c_ties = 0;
+  int64_t c_prop = 0, c_acc = 0, c_ties = 0, c_negl = 0;
   __syncthreads();
 
   // Step 1 (thread 0): target of proposal j, its spin and the new a_t.
+  // Kinds: 0 insert, 1 remove, 3 flip, 2 rejected without a ratio (removal or
+  // flip from the empty configuration, or a proposal the neglect rule drops).
+  // A removal or flip that picks a spin already changed in this window (an
+  // insertion or a flip of this window) ends the window (the abort variant;
+  // the proposal is re-evaluated first in the next window) or, under the
+  // neglect rule, is rejected.
   auto plan = [&](int j) {
     const Proposal& pr = s_prop[j];
     const int kcur = n_live - s_nrem + s_nins;
@@ -561,16 +573,21 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
       kind = 2;
     } else {
       const int idx = (int)scaled_index(pr.word, (uint32_t)kcur);
-      if (idx >= n_live - s_nrem) {
-        s_stop = 1;  // picks a spin inserted in this window: end the window here
-      } else {
+      bool dup = idx >= n_live - s_nrem;  // a spin inserted in this window
+      if (!dup) {
         // idx-th live vertex not yet removed in this window
         rank = idx;
         for (int r = 0; r < s_nrem; ++r) {
           if (s_removed[r] <= rank) ++rank;
           else break;
         }
-        kind = 1;
+        for (int r = 0; r < s_nflip; ++r) dup |= s_flipped[r] == rank;
+      }
+      if (dup) {
+        if (cfg.neglect) kind = 2;
+        else s_stop = 1;  // end the window here
+      } else {
+        kind = pr.type == 2 ? 3 : 1;
         if (live_smem) {
           const int v = s_live[rank];
           target = v >> 1;
@@ -579,7 +596,10 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
           target = w.live_idx[rank];
           up = ev[0].vs[target] > 0 ? 1 : 0;
         }
-        for (int sp = 0; sp < 2; ++sp) s_anew[sp] = s_ev[sp][up ? 0 : 1] - 1.0;  // e^{V(-s)} - 1
+        for (int sp = 0; sp < 2; ++sp) {
+          const double e = s_ev[sp][up ? 0 : 1];  // e^{V(-s)}: removal e^{-V} - 1, flip e^{-2V} - 1
+          s_anew[sp] = kind == 3 ? e * e - 1.0 : e - 1.0;
+        }
       }
     }
     s_kind = kind;
@@ -595,12 +615,14 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
     if (s_stop) break;
     const int l = s_l;
     if (s_kind == 2) {
-      // a removal from the empty configuration: ratio zero, rejected
+      // a removal or flip from the empty configuration (ratio zero), or a
+      // proposal dropped by the neglect rule: rejected
       __syncthreads();  // every thread has read s_kind and s_l
       if (tid == 0) {
         const uint64_t q = q0 + (uint64_t)j;
         if ((int64_t)q < log_cap) w.log[q] = 0;
         ++c_prop;
+        c_negl += s_kcur > 0;
         s_eval = j + 1;
         if (j + 1 < len) plan(j + 1);
       }
@@ -662,7 +684,7 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
         const Proposal& pr = s_prop[j];
         const uint64_t q = q0 + (uint64_t)j;
         const int kcur = s_kcur;
-        const double R = (s_kind == 0 ? K / (double)(kcur + 1) : (double)kcur / K) * d0 * d1;
+        const double R = (s_kind == 0 ? K / (double)(kcur + 1) : (s_kind == 1 ? (double)kcur / K : 1.0)) * d0 * d1;
         int acc = 0, tie = 0;
         if (!isfinite(R)) {
           set_status(w, ST_ERR_NUMERIC);
@@ -693,6 +715,8 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
               }
               s_removed[r] = s_rank;
               s_nrem++;
+            } else if (s_kind == 3) {
+              s_flipped[s_nflip++] = s_rank;
             } else {
               s_nins++;
             }
@@ -742,7 +766,7 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
   __syncthreads();
 
   // Epilogue: window bookkeeping and the accepted set.
-  const int l = s_l, nrem = s_nrem, nins = s_nins;
+  const int l = s_l, nrem = s_nrem, nins = s_nins, nflip = s_nflip;
   // B^-1 for the update kernels: FP64 on the FP64 path, FP32 pairs on the
   // mixed path (converted in place, element by element, when the growth ran
   // in FP64 in the global buffer)
@@ -761,7 +785,10 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
     w.aP[1][p] = s_aP[1][p];
   }
   for (int r = tid; r < nrem; r += blockDim.x) w.removed[r] = s_removed[r];
+  for (int r = tid; r < nflip; r += blockDim.x) w.flipped[r] = s_flipped[r];
   if (tid == 0) {
+    w.n_flipped = nflip;
+    w.n_neglected += c_negl;
     w.n_prop += c_prop;
     w.n_ties += c_ties;
     w.n_accept += c_acc;
@@ -1079,6 +1106,10 @@ __global__ void __launch_bounds__(256) k_window_end(Config cfg) {
   const int par = w.parity, n = w.n, nrem = w.n_removed, ni = w.n_ins, nl = w.n_live;
   if (w.n_acc > 0) {
     for (int r = threadIdx.x; r < nrem; r += blockDim.x) w.vs[par][w.live_idx[w.removed[r]]] = 0;
+    for (int r = threadIdx.x; r < w.n_flipped; r += blockDim.x) {
+      const int x = w.live_idx[w.flipped[r]];
+      w.vs[par][x] = -w.vs[par][x];
+    }
     // new live list: surviving ranks in order, then the appended rows
     for (int i = threadIdx.x; i < nl; i += blockDim.x) {
       int below = 0, gone = 0;

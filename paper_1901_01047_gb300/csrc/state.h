@@ -66,10 +66,10 @@ struct ProblemDev {
 struct Proposal {
   double tau;      // insert: new vertex time
   double u;        // Metropolis uniform
-  int32_t type;    // 0 insert, 1 remove
+  int32_t type;    // 0 insert, 1 remove, 2 auxiliary-spin flip
   int32_t s;       // insert: +1 / -1
   int32_t site;    // insert: site
-  uint32_t word;   // remove: index word, index = floor(word * k / 2^32)
+  uint32_t word;   // remove / flip: index word, index = floor(word * k / 2^32)
   int32_t slot;    // insert: candidate slot c, extended row n + c
   int32_t pad;
 };
@@ -135,6 +135,10 @@ struct WalkerDev {
   double* aP[2];             // [spin][KS_MAX]
   int32_t* P;                // [KS_MAX] extended index of accepted flips, in order
   int32_t* removed;          // [KS_MAX] live ranks removed this window, ascending
+  int32_t* flipped;          // [KS_MAX] live ranks whose auxiliary spin was flipped this window
+  int32_t n_flipped;         // accepted flips this window
+  int32_t pad_flip;
+  int64_t n_neglected;       // proposals rejected by the neglect rule
   int32_t* acc_slot;         // [KS_MAX] candidate slot of the m-th accepted insertion
   int32_t* acc_p;            // [KS_MAX] its position in P
   double* Lrow[2];           // [spin][cap][KS_MAX] rows of L at extended row index
@@ -216,6 +220,8 @@ struct Config {
   int32_t tf32_terms;        // products per K step of the tensor-core kernels: 3 (3xTF32) or 1 (TF32)
   long long wait_cycles;     // bound of every mbarrier wait in the tensor-core kernels (SM clocks)
   int32_t recompute_at_measure;  // recompute N in the window of every measurement (before it)
+  uint32_t flip_thr;         // a proposal is an auxiliary-spin flip when (word0 >> 2) < flip_thr (0 = none)
+  int32_t neglect;           // duplicate spin in a window: 0 abort the window, 1 reject the proposal
   int32_t n_omega;           // frequency measurement: positive Matsubara frequencies (0 = off)
   int32_t nfft_L;            // its grid points over [0, beta)
   int32_t nfft_msp;          // its window half-width in grid points

@@ -173,6 +173,10 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     return fail(nullptr, DCA_ERR_ARG, "unsupported precision");
   if (p.precision == DCA_PREC_TF32 && p.update_kernel == DCA_UPD_CUDA_CORE)
     return fail(nullptr, DCA_ERR_ARG, "DCA_PREC_TF32 runs on the tensor cores only");
+  if (!(p.flip_fraction >= 0.0) || p.flip_fraction > 1.0)
+    return fail(nullptr, DCA_ERR_ARG, "flip_fraction must be in [0, 1]");
+  if (p.duplicate_rule != DCA_DUP_ABORT && p.duplicate_rule != DCA_DUP_NEGLECT)
+    return fail(nullptr, DCA_ERR_ARG, "duplicate_rule must be one of DCA_DUP_*");
   if (p.n_omega_meas != 0 && (p.n_omega_meas < 8 || p.n_omega_meas > 4096))
     return fail(nullptr, DCA_ERR_ARG, "n_omega_meas must be 0 or in 8..4096");
   if (p.gamma_precision != DCA_GAMMA_FP64 && p.gamma_precision != DCA_GAMMA_DOUBLE_FLOAT)
@@ -348,6 +352,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     }
     pieces.push_back({(void**)&w.P, sizeof(int32_t) * KS});
     pieces.push_back({(void**)&w.removed, sizeof(int32_t) * KS});
+    pieces.push_back({(void**)&w.flipped, sizeof(int32_t) * KS});
     pieces.push_back({(void**)&w.acc_slot, sizeof(int32_t) * KS});
     pieces.push_back({(void**)&w.acc_p, sizeof(int32_t) * KS});
     pieces.push_back({(void**)&w.live_idx, sizeof(int32_t) * C});
@@ -422,6 +427,8 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.tf32_terms = p.precision == DCA_PREC_TF32 ? 1 : 3;
   h->cfg.wait_cycles = kDefaultWaitCycles;
   h->cfg.recompute_at_measure = p.recompute_at_measure ? 1 : 0;
+  h->cfg.flip_thr = (uint32_t)std::floor(p.flip_fraction * 1073741824.0);
+  h->cfg.neglect = p.duplicate_rule == DCA_DUP_NEGLECT ? 1 : 0;
   h->cfg.n_omega = p.n_omega_meas;
   h->cfg.nfft_L = 4 * p.n_omega_meas;
   h->cfg.nfft_msp = h->precision == DCA_PREC_FP64 ? 12 : 8;
@@ -912,6 +919,7 @@ extern "C" DCA_API int dca_walker_stats(dca_walker* h, dca_walker_stats_t* out) 
     s.extend_flops = w.ext_flops;
     s.extend_bytes = w.ext_bytes;
     s.recompute_flops = w.rec_flops;
+    s.neglected = w.n_neglected;
   }
   return DCA_OK;
 }
@@ -1000,7 +1008,7 @@ extern "C" DCA_API int dca_walker_set_forced_decisions(dca_walker* h, int32_t wi
 // ---------------------------------------------------------------------------
 namespace {
 constexpr uint32_t kSaveMagic = 0x57414344u;  // "DCAW"
-constexpr uint32_t kSaveVersion = 2u;
+constexpr uint32_t kSaveVersion = 3u;
 
 struct SaveHeader {
   uint32_t magic, version;
@@ -1013,7 +1021,7 @@ struct SaveWalker {
   int32_t windows_since_recompute, pad;
   uint64_t q;
   int64_t sweeps_done, sweep_pos, sweep_len_cur, sweep_len, warm_k_sum;
-  int64_t n_prop, n_accept, n_ties, n_aborts, n_windows, n_meas, n_recomputes;
+  int64_t n_prop, n_accept, n_ties, n_aborts, n_windows, n_meas, n_recomputes, n_neglected;
   double sign, sign_sum, k_sum, max_drift, flops, upd_bytes, ext_flops, ext_bytes, rec_flops;
 };
 
@@ -1069,6 +1077,7 @@ extern "C" DCA_API int dca_walker_save(dca_walker* h, void* buf, size_t cap, siz
     sw.n_windows = w.n_windows;
     sw.n_meas = w.n_meas;
     sw.n_recomputes = w.n_recomputes;
+    sw.n_neglected = w.n_neglected;
     sw.sign = w.sign;
     sw.sign_sum = w.sign_sum;
     sw.k_sum = w.k_sum;
@@ -1200,6 +1209,7 @@ extern "C" DCA_API int dca_walker_load(dca_walker* h, const void* buf, size_t n)
     w.n_windows = sw.n_windows;
     w.n_meas = sw.n_meas;
     w.n_recomputes = sw.n_recomputes;
+    w.n_neglected = sw.n_neglected;
     w.sign = sw.sign;
     w.sign_sum = sw.sign_sum;
     w.k_sum = sw.k_sum;

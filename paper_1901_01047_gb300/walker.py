@@ -70,6 +70,8 @@ class Params(C.Structure):
         ("gamma_precision", C.c_int32),
         ("recompute_at_measure", C.c_int32),
         ("n_omega_meas", C.c_int32),
+        ("flip_fraction", C.c_double),
+        ("duplicate_rule", C.c_int32),
     ]
 
 
@@ -113,6 +115,7 @@ class Stats(C.Structure):
         ("extend_flops", C.c_double),
         ("extend_bytes", C.c_double),
         ("recompute_flops", C.c_double),
+        ("neglected", C.c_int64),
     ]
 
     def as_dict(self):
@@ -240,7 +243,7 @@ class Walkers:
                  warmup_sweeps=20, n_tau_meas=64, precision="fp64", init_config_size=10, capacity=0,
                  seed=0, tie_eps=1e-10, log_capacity=0, update_kernel="auto", recompute_sweeps=0,
                  recompute_method="auto", schedule="lockstep", gamma_precision="fp64", recompute_at_measure=False,
-                 n_omega_meas=0, stream=None):
+                 n_omega_meas=0, flip_fraction=0.0, duplicate_rule="abort", stream=None):
         L = load()
         self._keep = []
         probs = (Problem * len(problems))()
@@ -286,6 +289,9 @@ class Walkers:
             else int(gamma_precision)
         p.recompute_at_measure = 1 if recompute_at_measure else 0
         p.n_omega_meas = int(n_omega_meas)
+        p.flip_fraction = float(flip_fraction)
+        p.duplicate_rule = {"abort": 0, "neglect": 1}[duplicate_rule] if isinstance(duplicate_rule, str) \
+            else int(duplicate_rule)
         self.n_omega_meas = int(n_omega_meas)
         p.update_kernel = UPDATE_KERNELS[update_kernel] if isinstance(update_kernel, str) else int(update_kernel)
         self.n_walkers = int(n_walkers)

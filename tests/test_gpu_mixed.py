@@ -31,8 +31,9 @@ def replay(nc, tp, U, beta, mu, k_sub, sweeps, R, seed=0, ntm=32, n_tau=4096, up
     ow.sweep(sweeps)
     log = ow.log()
     gw = _walkers(problems=[dict(nc=nc, site_sub=c.site_sub, U=U, beta=beta, K=1.0, G0=G0)], k_sub=k_sub,
-                  recompute_every=R, warmup_sweeps=10, n_tau_meas=ntm, seed=seed, precision="mixed",
-                  log_capacity=1 << 24, update_kernel=update_kernel, recompute_method=recompute_method)
+                  recompute_every=R, warmup_sweeps=10, n_tau_meas=ntm, seed=seed, precision=precision,
+                  log_capacity=1 << 24, update_kernel=update_kernel, recompute_method=recompute_method,
+                  recompute_at_measure=recompute_at_measure)
     gw.set_forced_decisions(0, log)
     gw.sweep(sweeps)
     gs, os_ = gw.state(0), ow.state()
