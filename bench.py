@@ -136,6 +136,7 @@ def config_of(wl, world):
             "K": wl.K, "walkers_per_gpu": wl.walkers, "k_sub": wl.k_sub, "n_tau": wl.n_tau,
             "n_tau_meas": wl.n_tau_meas, "recompute_every": wl.recompute_every, "recompute_sweeps": wl.recompute_sweeps,
             "recompute_at_measure": wl.recompute_at_measure, "n_omega_meas": wl.n_omega_meas,
+            **({"freq_method": wl.freq_method} if wl.n_omega_meas else {}),
             "precision": wl.precision, "schedule": wl.schedule,
             "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)",
             **({"per_walker": {"nc": list(wl.nc_choices), "beta": list(wl.beta_range), "U": list(wl.U_range),
@@ -372,7 +373,7 @@ def run_ours(args, rank, world, local_rank):
                         warmup_sweeps=wl.warmup_sweeps, n_tau_meas=wl.n_tau_meas, precision=wl.precision,
                         init_config_size=wl.init_config_size, seed=seed, schedule=wl.schedule,
                         recompute_at_measure=wl.recompute_at_measure, n_omega_meas=wl.n_omega_meas,
-                        stream=stream.cuda_stream)
+                        freq_method=wl.freq_method, stream=stream.cuda_stream)
     gw.sweep(wl.warmup_sweeps)            # the chain's own warm-up (no measurements)
     tuned = None
     if wl.autotune and not args.no_autotune:  # untimed; the trial sweeps are ordinary sweeps of the chains

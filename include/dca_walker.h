@@ -138,7 +138,18 @@ typedef struct {
                                       with probability 1/2 each.  0 = no flips */
   int32_t duplicate_rule;          /* DCA_DUP_*: a removal or flip that picks a spin already
                                       changed in the current submatrix update */
+  int32_t freq_method;             /* DCA_FREQ_*: how the frequency measurement is evaluated */
 } dca_walker_params;
+
+/* The frequency measurement of M (dca_walker_measure_M):
+ *   NFFT: the delayed NFFT of Sec. 2.3 (Eq. nfft): every measurement spreads its
+ *         n^2 samples onto an oversampled grid with a Gaussian window; one
+ *         transform at read-out;
+ *   DFT:  the same sums evaluated directly, as a contraction of N with the
+ *         phase factors e^{-i w_n tau_j} (n^2 n_omega multiply-adds per spin;
+ *         no window error). */
+#define DCA_FREQ_NFFT 0
+#define DCA_FREQ_DFT 1
 
 /* Spins changed twice in one submatrix update (Sec. 2.3, "Submatrix updates"):
  *   ABORT:   end the update before that proposal and evaluate it first in the
@@ -301,10 +312,11 @@ DCA_API int dca_walker_measure_G(dca_walker* w, double* G_out, double* sign_sum_
  * M(K) = sum_dr e^{-i K.dr} M(dr) (paper sign convention).  M_out: host
  * [n_walkers][2][nc][n_omega_meas][re, im] (walkers back to back, nc of each
  * walker's problem); sign_sum_out [n_walkers] and n_meas_out [n_walkers] as
- * in dca_walker_measure_G; any output may be NULL.  The spreading onto the
- * oversampled grid uses a truncated Gaussian window with a relative error of
- * about 1e-12 (FP64) or 1e-8 (mixed paths).  Returns DCA_ERR_STATE if the
- * frequency measurement is off.  Synchronises the stream. */
+ * in dca_walker_measure_G; any output may be NULL.  With DCA_FREQ_NFFT the
+ * spreading onto the oversampled grid uses a truncated Gaussian window with a
+ * relative error of about 1e-12 (FP64) or 1e-8 (mixed paths); DCA_FREQ_DFT
+ * evaluates the sums directly.  Returns DCA_ERR_STATE if the frequency
+ * measurement is off.  Synchronises the stream. */
 DCA_API int dca_walker_measure_M(dca_walker* w, double* M_out, double* sign_sum_out, int64_t* n_meas_out);
 
 /* Zero the G accumulators, sign sums and measurement counters. */

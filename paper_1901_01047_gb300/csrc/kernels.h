@@ -95,6 +95,10 @@ void launch_negate(const double* src, double* dst, float* dstf, size_t n, int* b
 cudaError_t setup_nfft();
 int launch_meas_nfft(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
 void launch_nfft_finish(const Config& cfg, int max_nc, const long long* d_base, double* d_out, cudaStream_t st);
+// The dense-DFT variant: per measurement the site sort and the contraction;
+// at read-out a copy of the accumulators (same output layout).
+int launch_meas_ndft(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
+void launch_ndft_copy(const Config& cfg, int max_nc, const long long* d_base, double* d_out, cudaStream_t st);
 // Phase table of the measurement grid (ProblemDev::g0m) from the FP32 table g0f.
 void launch_meas_table(const ProblemDev& pd, int n_tau_meas, cudaStream_t st);
 void launch_g0_isolated(int nc, const double* d_eps, const double* d_kr, double mu_eff, double beta, int n_tau,

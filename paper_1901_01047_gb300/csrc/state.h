@@ -151,6 +151,10 @@ struct WalkerDev {
   double* gR;                // [2][nc][cap]
   double* bvec;              // [2][nc][cap]
   double* Mgrid;             // [2][nc][nfft_L] delayed-NFFT grid of M (frequency measurement), or null
+  double* Mfreq;             // [2][nc][n_omega][re, im] dense-DFT accumulator of M, or null
+  unsigned long long* vx;    // [cap] frequency measurement: per vertex (floor(tau/beta 2^56) << 8) | (site + 1), 0 if dead
+  int32_t* perm;             // [cap] live columns sorted by site (dense DFT)
+  int32_t* goff;             // [nc + 1] their site-group offsets
 };
 
 #ifdef __CUDACC__
@@ -225,6 +229,7 @@ struct Config {
   int32_t n_omega;           // frequency measurement: positive Matsubara frequencies (0 = off)
   int32_t nfft_L;            // its grid points over [0, beta)
   int32_t nfft_msp;          // its window half-width in grid points
+  int32_t freq_dft;          // frequency measurement as the dense contraction (else delayed NFFT)
 };
 
 }  // namespace dca

@@ -177,6 +177,8 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     return fail(nullptr, DCA_ERR_ARG, "flip_fraction must be in [0, 1]");
   if (p.duplicate_rule != DCA_DUP_ABORT && p.duplicate_rule != DCA_DUP_NEGLECT)
     return fail(nullptr, DCA_ERR_ARG, "duplicate_rule must be one of DCA_DUP_*");
+  if (p.freq_method != DCA_FREQ_NFFT && p.freq_method != DCA_FREQ_DFT)
+    return fail(nullptr, DCA_ERR_ARG, "freq_method must be one of DCA_FREQ_*");
   if (p.n_omega_meas != 0 && (p.n_omega_meas < 8 || p.n_omega_meas > 4096))
     return fail(nullptr, DCA_ERR_ARG, "n_omega_meas must be 0 or in 8..4096");
   if (p.gamma_precision != DCA_GAMMA_FP64 && p.gamma_precision != DCA_GAMMA_DOUBLE_FLOAT)
@@ -361,7 +363,14 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     pieces.push_back({(void**)&w.Gtmp, sizeof(double) * 2 * nc * p.n_tau_meas});
     pieces.push_back({(void**)&w.gR, sizeof(double) * 2 * nc * C});
     pieces.push_back({(void**)&w.bvec, sizeof(double) * 2 * nc * C});
-    if (p.n_omega_meas > 0) pieces.push_back({(void**)&w.Mgrid, sizeof(double) * 2 * nc * 4 * (size_t)p.n_omega_meas});
+    if (p.n_omega_meas > 0) pieces.push_back({(void**)&w.vx, sizeof(unsigned long long) * C});
+    if (p.n_omega_meas > 0 && p.freq_method == DCA_FREQ_NFFT)
+      pieces.push_back({(void**)&w.Mgrid, sizeof(double) * 2 * nc * 4 * (size_t)p.n_omega_meas});
+    if (p.n_omega_meas > 0 && p.freq_method == DCA_FREQ_DFT) {
+      pieces.push_back({(void**)&w.Mfreq, sizeof(double) * 2 * nc * 2 * (size_t)p.n_omega_meas});
+      pieces.push_back({(void**)&w.perm, sizeof(int32_t) * C});
+      pieces.push_back({(void**)&w.goff, sizeof(int32_t) * (nc + 1)});
+    }
     if (p.log_capacity > 0) pieces.push_back({(void**)&w.log, (size_t)p.log_capacity});
     size_t total = 0;
     for (auto& pc : pieces) total += align_up(pc.bytes, 256);
@@ -432,6 +441,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.n_omega = p.n_omega_meas;
   h->cfg.nfft_L = 4 * p.n_omega_meas;
   h->cfg.nfft_msp = h->precision == DCA_PREC_FP64 ? 12 : 8;
+  h->cfg.freq_dft = p.freq_method == DCA_FREQ_DFT ? 1 : 0;
 
   if (dca::setup_window_kernels() != cudaSuccess || dca::setup_nfft() != cudaSuccess) {
     h->err = "kernel attribute setup failed";
@@ -865,7 +875,8 @@ extern "C" DCA_API int dca_walker_measure_M(dca_walker* h, double* M_out, double
       if (!h->d_Mout || !h->d_Mbase) return fail(h, DCA_ERR_OOM, "read-out buffers of the frequency measurement");
       CK(cudaMemcpyAsync(h->d_Mbase, base.data(), sizeof(long long) * h->W, cudaMemcpyHostToDevice, h->stream));
     }
-    dca::launch_nfft_finish(h->cfg, h->max_nc, h->d_Mbase, h->d_Mout, h->stream);
+    if (h->cfg.freq_dft) dca::launch_ndft_copy(h->cfg, h->max_nc, h->d_Mbase, h->d_Mout, h->stream);
+    else dca::launch_nfft_finish(h->cfg, h->max_nc, h->d_Mbase, h->d_Mout, h->stream);
     h->total_launches += 1;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(M_out, h->d_Mout, sizeof(double) * total, cudaMemcpyDeviceToHost, h->stream));
@@ -886,6 +897,7 @@ extern "C" DCA_API int dca_walker_reset_measurements(dca_walker* h) {
     WalkerDev& w = h->h_W[wi];
     CK(cudaMemsetAsync(w.Gacc, 0, sizeof(double) * 2 * h->nc_of[wi] * h->ntm, h->stream));
     if (w.Mgrid) CK(cudaMemsetAsync(w.Mgrid, 0, sizeof(double) * 2 * h->nc_of[wi] * h->cfg.nfft_L, h->stream));
+    if (w.Mfreq) CK(cudaMemsetAsync(w.Mfreq, 0, sizeof(double) * 4 * h->nc_of[wi] * h->cfg.n_omega, h->stream));
     w.sign_sum = 0.0;
     w.n_meas = 0;
     w.k_sum = 0.0;
@@ -1012,7 +1024,7 @@ constexpr uint32_t kSaveVersion = 3u;
 
 struct SaveHeader {
   uint32_t magic, version;
-  int32_t n_walkers, precision, n_tau_meas, warmup, n_omega, pad;
+  int32_t n_walkers, precision, n_tau_meas, warmup, n_omega, freq_dft;
   uint64_t bytes;  // total size of the checkpoint
 };
 
@@ -1031,9 +1043,15 @@ struct SaveVertex {
 };
 }  // namespace
 
-// Bytes of a walker's accumulators in a checkpoint: G(tau), then the NFFT grid.
+// Bytes of a walker's accumulators in a checkpoint: G(tau), then the
+// frequency measurement's (the NFFT grid or the dense sums).
+static size_t freq_acc_doubles(const dca_walker* h, int wi) {
+  if (h->cfg.n_omega <= 0) return 0;
+  return (size_t)h->nc_of[wi] * (h->cfg.freq_dft ? 4 * (size_t)h->cfg.n_omega : 2 * (size_t)h->cfg.nfft_L);
+}
+
 static size_t acc_bytes(const dca_walker* h, int wi) {
-  return sizeof(double) * 2 * (size_t)h->nc_of[wi] * ((size_t)h->ntm + (size_t)h->cfg.nfft_L);
+  return sizeof(double) * (2 * (size_t)h->nc_of[wi] * (size_t)h->ntm + freq_acc_doubles(h, wi));
 }
 
 static size_t save_size(const dca_walker* h) {
@@ -1052,7 +1070,8 @@ extern "C" DCA_API int dca_walker_save(dca_walker* h, void* buf, size_t cap, siz
   if (!buf) return DCA_OK;
   if (cap < need) return fail(h, DCA_ERR_ARG, "checkpoint buffer too small (" + std::to_string(need) + " bytes needed)");
   unsigned char* out = (unsigned char*)buf;
-  SaveHeader hd{kSaveMagic, kSaveVersion, h->W, h->prec_public, h->ntm, h->warmup, h->cfg.n_omega, 0, (uint64_t)need};
+  SaveHeader hd{kSaveMagic, kSaveVersion, h->W, h->prec_public, h->ntm, h->warmup, h->cfg.n_omega, h->cfg.freq_dft,
+                (uint64_t)need};
   std::memcpy(out, &hd, sizeof(hd));
   size_t off = sizeof(hd);
   for (int wi = 0; wi < h->W; ++wi) {
@@ -1099,9 +1118,9 @@ extern "C" DCA_API int dca_walker_save(dca_walker* h, void* buf, size_t cap, siz
     }
     const size_t gbytes = sizeof(double) * 2 * (size_t)h->nc_of[wi] * h->ntm;
     CK(cudaMemcpyAsync(out + off + sizeof(SaveVertex) * k, w.Gacc, gbytes, cudaMemcpyDeviceToHost, h->stream));
-    if (w.Mgrid)
-      CK(cudaMemcpyAsync(out + off + sizeof(SaveVertex) * k + gbytes, w.Mgrid, acc_bytes(h, wi) - gbytes,
-                         cudaMemcpyDeviceToHost, h->stream));
+    if (w.Mgrid || w.Mfreq)
+      CK(cudaMemcpyAsync(out + off + sizeof(SaveVertex) * k + gbytes, w.Mgrid ? w.Mgrid : w.Mfreq,
+                         acc_bytes(h, wi) - gbytes, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     for (int i = 0; i < k; ++i) {
       const SaveVertex v{site[live[i]], s[live[i]], tau[live[i]]};
@@ -1123,7 +1142,7 @@ extern "C" DCA_API int dca_walker_load(dca_walker* h, const void* buf, size_t n)
   if (hd.magic != kSaveMagic || hd.version != kSaveVersion) return fail(h, DCA_ERR_ARG, "not a walker checkpoint");
   if (hd.bytes != n) return fail(h, DCA_ERR_ARG, "checkpoint size does not match its header");
   if (hd.n_walkers != h->W || hd.precision != h->prec_public || hd.n_tau_meas != h->ntm || hd.warmup != h->warmup ||
-      hd.n_omega != h->cfg.n_omega)
+      hd.n_omega != h->cfg.n_omega || hd.freq_dft != h->cfg.freq_dft)
     return fail(h, DCA_ERR_ARG, "checkpoint of a walker set with other parameters");
   // first pass: validate everything before touching the walkers
   struct Parsed {
@@ -1183,9 +1202,9 @@ extern "C" DCA_API int dca_walker_load(dca_walker* h, const void* buf, size_t n)
     }
     const size_t gbytes = sizeof(double) * 2 * (size_t)sw.nc * h->ntm;
     CK(cudaMemcpyAsync(w.Gacc, in + p.g_off, gbytes, cudaMemcpyHostToDevice, h->stream));
-    if (w.Mgrid)
-      CK(cudaMemcpyAsync(w.Mgrid, in + p.g_off + gbytes, acc_bytes(h, wi) - gbytes, cudaMemcpyHostToDevice,
-                         h->stream));
+    if (w.Mgrid || w.Mfreq)
+      CK(cudaMemcpyAsync(w.Mgrid ? w.Mgrid : w.Mfreq, in + p.g_off + gbytes, acc_bytes(h, wi) - gbytes,
+                         cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemsetAsync(w.Gtmp, 0, sizeof(double) * 2 * (size_t)sw.nc * h->ntm, h->stream));
     w.n = k;
     w.n_live = k;

@@ -1,7 +1,8 @@
 """Seeded synthetic inputs shared by the GPU path, its tests and the oracle.
 
 This module holds no CT-AUX arithmetic: only the geometry of square-lattice
-DCA clusters (sites, the r_i - r_j table, cluster momenta), the dispersion of
+DCA clusters (sites, the r_i - r_j table, cluster momenta and their
+differences), the dispersion of
 the single-band Hubbard model on the square lattice (t, t' as in the model
 parameters of App. B), and the named workload parameter sets.
 
@@ -24,6 +25,7 @@ class Cluster:
     sites: np.ndarray        # [nc, 2] integer coordinates, reduced into the cell
     site_sub: np.ndarray     # [nc, nc] int32: index of (r_i - r_j) reduced into the cell
     kpts: np.ndarray         # [nc, 2] cluster momenta
+    k_sub: np.ndarray        # [nc, nc] int32: index of (K_a - K_b) reduced modulo the reciprocal lattice
 
     @property
     def nc(self) -> int:
@@ -69,7 +71,10 @@ def make_cluster(vecs) -> Cluster:
     if len(ks) != nc:
         raise ValueError("found %d cluster momenta, expected %d" % (len(ks), nc))
     kpts = 2.0 * np.pi * np.array(ks, dtype=np.float64) / nc
-    return Cluster(vecs=tuple(map(tuple, A.tolist())), sites=sites, site_sub=site_sub, kpts=kpts)
+    kindex = {p: i for i, p in enumerate(ks)}
+    k_sub = np.array([[kindex[((ka[0] - kb[0]) % nc, (ka[1] - kb[1]) % nc)] for kb in ks] for ka in ks],
+                     dtype=np.int32)
+    return Cluster(vecs=tuple(map(tuple, A.tolist())), sites=sites, site_sub=site_sub, kpts=kpts, k_sub=k_sub)
 
 
 def square_dispersion(kpts: np.ndarray, t: float, tp: float) -> np.ndarray:
@@ -118,7 +123,8 @@ class Workload:
     recompute_every: int = 64
     recompute_sweeps: int = 0
     recompute_at_measure: bool = False  # mixed path: N recomputed before every measurement
-    n_omega_meas: int = 0  # frequency measurement of M (delayed NFFT): positive Matsubara frequencies
+    n_omega_meas: int = 0  # frequency measurement of M: positive Matsubara frequencies
+    freq_method: str = "nfft"  # "nfft" (delayed NFFT) or "dft" (the same sums as a dense contraction)
     autotune: bool = False  # bench: choose k_s and the update kernel by the autotuner
     schedule: str = "lockstep"  # "pooled": the walkers share the sweep budget (all active every window)
     precision: str = "fp64"
@@ -169,12 +175,18 @@ WORKLOADS = {
                            n_tau=2048, k_sub=64, walkers=256, warmup_sweeps=40, n_tau_meas=128,
                            recompute_every=0, recompute_sweeps=8, precision="mixed", nc_choices=(8, 16),
                            autotune=True, schedule="pooled", beta_range=(5.0, 25.0), U_range=(4.0, 7.0)),
-    # the same batch with the frequency measurement of M (delayed NFFT, 128 frequencies) on
+    # the same batch with the frequency measurement of M on (128 frequencies): the
+    # delayed NFFT, and the same sums as a dense contraction
     "batched256_freq": Workload(name="batched256_freq", nc=16, t=1.0, tp=0.0, U=5.5, beta=15.0, mu=2.75, K=1.0,
                                 n_tau=2048, k_sub=64, walkers=256, warmup_sweeps=40, n_tau_meas=128,
                                 recompute_every=0, recompute_sweeps=8, precision="mixed", n_omega_meas=128,
                                 nc_choices=(8, 16), autotune=True, schedule="pooled", beta_range=(5.0, 25.0),
                                 U_range=(4.0, 7.0)),
+    "batched256_dft": Workload(name="batched256_dft", nc=16, t=1.0, tp=0.0, U=5.5, beta=15.0, mu=2.75, K=1.0,
+                               n_tau=2048, k_sub=64, walkers=256, warmup_sweeps=40, n_tau_meas=128,
+                               recompute_every=0, recompute_sweeps=8, precision="mixed", n_omega_meas=128,
+                               freq_method="dft", nc_choices=(8, 16), autotune=True, schedule="pooled",
+                               beta_range=(5.0, 25.0), U_range=(4.0, 7.0)),
     # 36-site square cluster, U = 7, beta = 30, density 0.95, 32 walkers, G on 2048 tau points
     "betts36": Workload(name="betts36", nc=36, t=1.0, tp=0.0, U=7.0, beta=30.0, mu=3.4878678207599574, K=1.0,
                         n_tau=4096, k_sub=64, walkers=32, warmup_sweeps=40, n_tau_meas=2048,

@@ -72,6 +72,7 @@ class Params(C.Structure):
         ("n_omega_meas", C.c_int32),
         ("flip_fraction", C.c_double),
         ("duplicate_rule", C.c_int32),
+        ("freq_method", C.c_int32),
     ]
 
 
@@ -243,7 +244,7 @@ class Walkers:
                  warmup_sweeps=20, n_tau_meas=64, precision="fp64", init_config_size=10, capacity=0,
                  seed=0, tie_eps=1e-10, log_capacity=0, update_kernel="auto", recompute_sweeps=0,
                  recompute_method="auto", schedule="lockstep", gamma_precision="fp64", recompute_at_measure=False,
-                 n_omega_meas=0, flip_fraction=0.0, duplicate_rule="abort", stream=None):
+                 n_omega_meas=0, flip_fraction=0.0, duplicate_rule="abort", freq_method="nfft", stream=None):
         L = load()
         self._keep = []
         probs = (Problem * len(problems))()
@@ -290,6 +291,7 @@ class Walkers:
         p.recompute_at_measure = 1 if recompute_at_measure else 0
         p.n_omega_meas = int(n_omega_meas)
         p.flip_fraction = float(flip_fraction)
+        p.freq_method = {"nfft": 0, "dft": 1}[freq_method] if isinstance(freq_method, str) else int(freq_method)
         p.duplicate_rule = {"abort": 0, "neglect": 1}[duplicate_rule] if isinstance(duplicate_rule, str) \
             else int(duplicate_rule)
         self.n_omega_meas = int(n_omega_meas)
