@@ -80,6 +80,9 @@ def lib():
         L.orc_neglected.argtypes = [P]
         L.orc_neglected.restype = C.c_int64
         L.orc_get_M.argtypes = [P, C.c_void_p]
+        L.orc_enable_g4.argtypes = [P, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
+        L.orc_get_g4.argtypes = [P, C.c_void_p, C.c_void_p]
+        L.orc_m2.argtypes = [P, C.c_int32, C.c_void_p]
         _lib = L
     return _lib
 
@@ -221,6 +224,37 @@ class OracleWalker:
         rc = lib().orc_get_M(self._h, _ptr(out))
         if rc != 0:
             raise ValueError("frequency measurement is off")
+        return out[..., 0] + 1j * out[..., 1]
+
+    def enable_g4(self, n_w4, m4, kdotr, k_dn):
+        """Measure the particle-particle up-down two-particle function on the
+        points s = (K, n), n = -n_w4 .. n_w4 - 1, with the bosonic transfer
+        index m4 and k_dn[K] = index of Q - K (kdotr [nc, nc] = K . r)."""
+        self._kdotr = np.ascontiguousarray(kdotr, np.float64)
+        self._k_dn = np.ascontiguousarray(k_dn, np.int32)
+        rc = lib().orc_enable_g4(self._h, int(n_w4), int(m4), _ptr(self._kdotr), _ptr(self._k_dn))
+        if rc != 0:
+            raise ValueError("enable_g4 failed with code %d" % rc)
+        self.n_w4 = int(n_w4)
+
+    def g4(self):
+        """Accumulators (A [S, S], D [2, S]) complex, S = nc * 2 n_w4: A = sum sign
+        M_up(s1, s2) M_dn(q - s1, q - s2), D[sigma] = sum sign M_sigma(s, s)."""
+        S = self.nc * 2 * self.n_w4
+        A = np.zeros((S, S, 2), np.float64)
+        D = np.zeros((2, S, 2), np.float64)
+        rc = lib().orc_get_g4(self._h, _ptr(A), _ptr(D))
+        if rc != 0:
+            raise ValueError("two-particle measurement is off or failed (%d)" % rc)
+        return A[..., 0] + 1j * A[..., 1], D[..., 0] + 1j * D[..., 1]
+
+    def m2(self, spin):
+        """M_sigma(s1, s2) of the current configuration (no sign), complex [S, S]."""
+        S = self.nc * 2 * self.n_w4
+        out = np.zeros((S, S, 2), np.float64)
+        rc = lib().orc_m2(self._h, int(spin), _ptr(out))
+        if rc != 0:
+            raise ValueError("m2 failed (%d)" % rc)
         return out[..., 0] + 1j * out[..., 1]
 
     def fresh_N(self, spin):

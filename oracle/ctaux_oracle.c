@@ -160,6 +160,12 @@ typedef struct {
     double* Nsave[2];         /* copies of N while a flip is decided */
     int32_t n_omega;          /* frequency measurement: positive Matsubara frequencies, 0 = off */
     double* Macc;             /* [2][nc][n_omega][re, im]: sum of sign * M(dr, i w_n) */
+    int32_t n_w4;             /* two-particle measurement: fermionic frequencies per sign, 0 = off */
+    int32_t m4;               /* its bosonic transfer index, nu = 2 pi m4 / beta */
+    double* kdotr;            /* [nc][nc] K_a . r_s */
+    int32_t* k_dn;            /* [nc] index of Q - K for each K */
+    double* G4acc;            /* [S][S][re, im]: sum of sign * M_up(s1, s2) M_dn(s1, s2) */
+    double* G4d;              /* [2][S][re, im]: sum of sign * M_sigma(s, s) */
 } orc_walker;
 
 /* ------------------------------------------------------------------ */
@@ -302,6 +308,7 @@ void orc_destroy(orc_walker* w)
     free(w->vsite); free(w->vtau); free(w->vs);
     free(w->N[0]); free(w->N[1]); free(w->work);
     free(w->Gacc); free(w->log); free(w->Macc);
+    free(w->kdotr); free(w->k_dn); free(w->G4acc); free(w->G4d);
     free(w->changed); free(w->Nsave[0]); free(w->Nsave[1]);
     free(w);
 }
@@ -668,6 +675,7 @@ static int propose(orc_walker* w, uint64_t q)
 /* M = (e^V - 1) N; accumulated as sign * (-G) (paper convention).     */
 /* ------------------------------------------------------------------ */
 static void measure_freq(orc_walker* w);
+static void measure_g4(orc_walker* w);
 
 static void measure(orc_walker* w)
 {
@@ -702,6 +710,7 @@ static void measure(orc_walker* w)
     }
     free(b);
     if (w->n_omega > 0) measure_freq(w);
+    if (w->n_w4 > 0) measure_g4(w);
     w->sign_sum += w->sign;
     w->n_meas++;
 }
@@ -752,6 +761,166 @@ int orc_enable_freq(orc_walker* w, int32_t n_omega)
     if (!w->Macc) return ORC_ERR_OOM;
     w->n_omega = n_omega;
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Two-particle measurement, particle-particle up-down channel         */
+/* ------------------------------------------------------------------ */
+/* Within one configuration the problem is quadratic in each spin, so the
+ * two-particle Green's function of the particle-particle up-down channel
+ * (Sec. 2.5, Eq. bse_cluster; App. B four-point type
+ * PARTICLE_PARTICLE_UP_DOWN) factorises into two-point functions of the two
+ * spins, which carry no exchange term:
+ *   G2(K, K', q) = < G_up(K, K') G_dn(q - K, q - K') >,
+ * with the combined index K = (K, i w_n), q = (Q, i nu_m), nu_m = 2 pi m / beta,
+ * and per configuration (the two-point form of the relation G = G0 - G0 M G0
+ * of Sec. 2.3, in the paper's sign)
+ *   G_sigma(k1, k2) = G0_sigma(k1) delta_{k1 k2} - G0_sigma(k1) M_sigma(k1, k2) G0_sigma(k2),
+ *   M_sigma(k1, k2) = 1/(beta Nc) sum_{ij} e^{i (w1 tau_i - K1.r_i)} [(e^V - 1) N]_ij e^{-i (w2 tau_j - K2.r_j)},
+ * whose diagonal M_sigma(k, k) is the single-particle M(K, i w_n) of
+ * measure_freq.  The measured points are s = (K, n) for K over the cluster
+ * momenta and n = -n_w4 .. n_w4 - 1 (index s = K * 2 n_w4 + n + n_w4); the
+ * spin-down factor is taken at q - s = (Q - K, i w_{m - n - 1}).  What is
+ * accumulated is the part that depends on the configuration,
+ *   G4acc(s1, s2) = sum sign M_up(s1, s2) M_dn(q - s1, q - s2),
+ *   G4d(sigma, s) = sum sign M_sigma(s, s)   (sigma = dn at q - s),
+ * from which G2 follows for any G0 by expanding the product (oracle/g4.py):
+ *   G2 sum_sign = G0u(s1) G0d(s1) [ delta (sum_sign - G4d_up(s1) G0u(s1) - G4d_dn(s1) G0d(s1))
+ *                                  + G4acc(s1, s2) G0u(s2) G0d(s2) ]. */
+
+/* Momentum and frequency of measured point s for spin sp. */
+static void g4_point(const orc_walker* w, int sp, int s, int* K, double* wn)
+{
+    const int nf = 2 * w->n_w4;
+    const int k = s / nf, n = s % nf - w->n_w4;
+    if (sp == 0) {
+        *K = k;
+        *wn = (double)(2 * n + 1) * 3.14159265358979323846 / w->beta;
+    } else {
+        *K = w->k_dn[k];
+        *wn = (double)(2 * (w->m4 - n - 1) + 1) * 3.14159265358979323846 / w->beta;
+    }
+}
+
+/* M_sigma(s1, s2) of the current configuration, out [S][S][re, im] (no sign):
+ * T(i, s2) = sum_j c_ij e^{-i phase_j(s2)}, then M(s1, s2) = norm sum_i
+ * e^{i phase_i(s1)} T(i, s2), with c = (e^V - 1) N and phase_i(s) = w_s tau_i - K_s.r_i. */
+static int g4_m2(const orc_walker* w, int sp, double* out)
+{
+    const int n = w->k, nc = w->nc, ld = w->cap;
+    const int S = nc * 2 * w->n_w4;
+    const double norm = 1.0 / (w->beta * (double)nc);
+    double* ph = (double*)malloc(sizeof(double) * 2 * (size_t)S * (n > 0 ? n : 1));
+    double* T = (double*)malloc(sizeof(double) * 2 * (size_t)S * (n > 0 ? n : 1));
+    if (!ph || !T) { free(ph); free(T); return ORC_ERR_OOM; }
+    for (int s = 0; s < S; ++s) {
+        int K; double wn;
+        g4_point(w, sp, s, &K, &wn);
+        for (int i = 0; i < n; ++i) {
+            const double a = wn * w->vtau[i] - w->kdotr[(size_t)K * nc + w->vsite[i]];
+            ph[((size_t)s * n + i) * 2] = cos(a);
+            ph[((size_t)s * n + i) * 2 + 1] = sin(a);
+        }
+    }
+    const double* N = w->N[sp];
+    for (int i = 0; i < n; ++i) {
+        const double fi = ev(w, sp, w->vs[i]) - 1.0;
+        for (int s = 0; s < S; ++s) {
+            double re = 0.0, im = 0.0;
+            for (int j = 0; j < n; ++j) {
+                const double c = fi * N[(size_t)i * ld + j];
+                re += c * ph[((size_t)s * n + j) * 2];       /* c e^{-i a_j}: (cos a, -sin a) */
+                im -= c * ph[((size_t)s * n + j) * 2 + 1];
+            }
+            T[((size_t)i * S + s) * 2] = re;
+            T[((size_t)i * S + s) * 2 + 1] = im;
+        }
+    }
+    for (int s1 = 0; s1 < S; ++s1)
+        for (int s2 = 0; s2 < S; ++s2) {
+            double re = 0.0, im = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const double c = ph[((size_t)s1 * n + i) * 2], sn = ph[((size_t)s1 * n + i) * 2 + 1];
+                const double tr = T[((size_t)i * S + s2) * 2], ti = T[((size_t)i * S + s2) * 2 + 1];
+                re += c * tr - sn * ti;
+                im += c * ti + sn * tr;
+            }
+            out[((size_t)s1 * S + s2) * 2] = norm * re;
+            out[((size_t)s1 * S + s2) * 2 + 1] = norm * im;
+        }
+    free(ph);
+    free(T);
+    return ORC_OK;
+}
+
+static void measure_g4(orc_walker* w)
+{
+    const int S = w->nc * 2 * w->n_w4;
+    double* Mu = (double*)malloc(sizeof(double) * 2 * (size_t)S * S);
+    double* Md = (double*)malloc(sizeof(double) * 2 * (size_t)S * S);
+    if (!Mu || !Md || g4_m2(w, 0, Mu) != ORC_OK || g4_m2(w, 1, Md) != ORC_OK) {
+        free(Mu); free(Md);
+        w->n_w4 = -w->n_w4;  /* out of memory: the measurement stops (reported by orc_get_g4) */
+        return;
+    }
+    for (size_t e = 0; e < (size_t)S * S; ++e) {
+        const double ar = Mu[2 * e], ai = Mu[2 * e + 1], br = Md[2 * e], bi = Md[2 * e + 1];
+        w->G4acc[2 * e] += w->sign * (ar * br - ai * bi);
+        w->G4acc[2 * e + 1] += w->sign * (ar * bi + ai * br);
+    }
+    for (int s = 0; s < S; ++s) {
+        const size_t e = (size_t)s * S + s;
+        w->G4d[2 * s] += w->sign * Mu[2 * e];
+        w->G4d[2 * s + 1] += w->sign * Mu[2 * e + 1];
+        w->G4d[2 * ((size_t)S + s)] += w->sign * Md[2 * e];
+        w->G4d[2 * ((size_t)S + s) + 1] += w->sign * Md[2 * e + 1];
+    }
+    free(Mu);
+    free(Md);
+}
+
+/* Switch the two-particle measurement on (n_w4 > 0) or off (0); clears it.
+ * kdotr [nc][nc] = K_a . r_s, k_dn [nc] = index of Q - K_a, m4 the bosonic
+ * transfer index. */
+int orc_enable_g4(orc_walker* w, int32_t n_w4, int32_t m4, const double* kdotr, const int32_t* k_dn)
+{
+    if (!w || n_w4 < 0 || (n_w4 > 0 && (!kdotr || !k_dn))) return ORC_ERR_ARG;
+    free(w->kdotr); free(w->k_dn); free(w->G4acc); free(w->G4d);
+    w->kdotr = NULL; w->k_dn = NULL; w->G4acc = NULL; w->G4d = NULL;
+    w->n_w4 = 0;
+    if (n_w4 == 0) return ORC_OK;
+    const int nc = w->nc;
+    for (int k = 0; k < nc; ++k)
+        if (k_dn[k] < 0 || k_dn[k] >= nc) return ORC_ERR_ARG;
+    const size_t S = (size_t)nc * 2 * n_w4;
+    w->kdotr = (double*)malloc(sizeof(double) * (size_t)nc * nc);
+    w->k_dn = (int32_t*)malloc(sizeof(int32_t) * (size_t)nc);
+    w->G4acc = (double*)calloc(S * S * 2, sizeof(double));
+    w->G4d = (double*)calloc(2 * S * 2, sizeof(double));
+    if (!w->kdotr || !w->k_dn || !w->G4acc || !w->G4d) return ORC_ERR_OOM;
+    for (size_t e = 0; e < (size_t)nc * nc; ++e) w->kdotr[e] = kdotr[e];
+    for (int k = 0; k < nc; ++k) w->k_dn[k] = k_dn[k];
+    w->n_w4 = n_w4;
+    w->m4 = m4;
+    return ORC_OK;
+}
+
+/* Accumulators of the two-particle measurement: A [S][S][re, im], D [2][S][re, im]. */
+int orc_get_g4(const orc_walker* w, double* A, double* D)
+{
+    if (!w || !A || !D || !w->G4acc) return ORC_ERR_ARG;
+    if (w->n_w4 < 0) return ORC_ERR_OOM;
+    const size_t S = (size_t)w->nc * 2 * w->n_w4;
+    for (size_t e = 0; e < S * S * 2; ++e) A[e] = w->G4acc[e];
+    for (size_t e = 0; e < 2 * S * 2; ++e) D[e] = w->G4d[e];
+    return ORC_OK;
+}
+
+/* M_sigma(s1, s2) of the current configuration: out [S][S][re, im]. */
+int orc_m2(const orc_walker* w, int32_t sp, double* out)
+{
+    if (!w || !out || w->n_w4 <= 0 || sp < 0 || sp > 1) return ORC_ERR_ARG;
+    return g4_m2(w, sp, out);
 }
 
 /* Accumulated sum of sign * M(dr, i w_n): out [2][nc][n_omega][re, im]. */
@@ -850,6 +1019,11 @@ void orc_reset_accumulators(orc_walker* w)
     w->k_sum = 0.0;
     w->k_samples = 0;
     if (w->Macc) memset(w->Macc, 0, sizeof(double) * (size_t)2 * w->nc * w->n_omega * 2);
+    if (w->G4acc) {
+        const size_t S = (size_t)w->nc * 2 * w->n_w4;
+        memset(w->G4acc, 0, sizeof(double) * S * S * 2);
+        memset(w->G4d, 0, sizeof(double) * 2 * S * 2);
+    }
 }
 
 /* Decision log: one byte per proposal, bit 0 = accepted, bit 1 = near tie. */
