@@ -137,6 +137,7 @@ def config_of(wl, world):
             "n_tau_meas": wl.n_tau_meas, "recompute_every": wl.recompute_every, "recompute_sweeps": wl.recompute_sweeps,
             "recompute_at_measure": wl.recompute_at_measure, "n_omega_meas": wl.n_omega_meas,
             **({"freq_method": wl.freq_method} if wl.n_omega_meas else {}),
+            **({"n_w4": wl.n_w4, "w4_transfer": wl.w4_transfer, "q4_transfer": wl.q4_transfer} if wl.n_w4 else {}),
             "precision": wl.precision, "schedule": wl.schedule,
             "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)",
             **({"per_walker": {"nc": list(wl.nc_choices), "beta": list(wl.beta_range), "U": list(wl.U_range),
@@ -153,7 +154,8 @@ def build_problem(pp, use_gpu_builder):
     else:
         from oracle import g0 as og0
         G0 = og0.g0_table(eps, kr, pp["mu"], pp["U"], pp["beta"], pp["n_tau"])
-    return dict(nc=pp["nc"], site_sub=c.site_sub, U=pp["U"], beta=pp["beta"], K=pp["K"], G0=G0)
+    return dict(nc=pp["nc"], site_sub=c.site_sub, U=pp["U"], beta=pp["beta"], K=pp["K"], G0=G0, k_dot_r=kr,
+                k_sub=c.k_sub)
 
 
 def workload_problems(wl, use_gpu_builder):
@@ -373,7 +375,8 @@ def run_ours(args, rank, world, local_rank):
                         warmup_sweeps=wl.warmup_sweeps, n_tau_meas=wl.n_tau_meas, precision=wl.precision,
                         init_config_size=wl.init_config_size, seed=seed, schedule=wl.schedule,
                         recompute_at_measure=wl.recompute_at_measure, n_omega_meas=wl.n_omega_meas,
-                        freq_method=wl.freq_method, stream=stream.cuda_stream)
+                        freq_method=wl.freq_method, n_w4=wl.n_w4, w4_transfer=wl.w4_transfer,
+                        q4_transfer=wl.q4_transfer, stream=stream.cuda_stream)
     gw.sweep(wl.warmup_sweeps)            # the chain's own warm-up (no measurements)
     tuned = None
     if wl.autotune and not args.no_autotune:  # untimed; the trial sweeps are ordinary sweeps of the chains

@@ -97,6 +97,10 @@ typedef struct {
                               (negative on (0, beta)); l = 0 holds G0(r, 0+),
                               l = n_tau holds G0(r, beta-).  Linear interpolation in
                               between, antiperiodic continuation to (-beta, 0). */
+  const double* k_dot_r;   /* host [nc][nc] K_a . r_s (cluster momentum a, site s); read
+                              only by the two-particle measurement (n_w4 > 0), else NULL */
+  const int32_t* k_sub;    /* host [nc][nc] index of K_a - K_b modulo the reciprocal lattice;
+                              same use */
 } dca_problem;
 
 typedef struct {
@@ -139,6 +143,13 @@ typedef struct {
   int32_t duplicate_rule;          /* DCA_DUP_*: a removal or flip that picks a spin already
                                       changed in the current submatrix update */
   int32_t freq_method;             /* DCA_FREQ_*: how the frequency measurement is evaluated */
+  int32_t n_w4;                    /* two-particle measurement (dca_walker_measure_G4), particle-
+                                      particle up-down channel: fermionic frequencies per sign
+                                      (App. B "four-point-fermionic-frequencies"), 1..32; 0 = off */
+  int32_t w4_transfer;             /* its bosonic transfer index m, nu_m = 2 pi m / beta
+                                      (App. B four-point "frequency-transfer"), |m| <= 64 */
+  int32_t q4_transfer;             /* its momentum transfer Q as a cluster-momentum index
+                                      (App. B four-point "momentum-transfer"), 0..nc-1 of every problem */
 } dca_walker_params;
 
 /* The frequency measurement of M (dca_walker_measure_M):
@@ -318,6 +329,38 @@ DCA_API int dca_walker_measure_G(dca_walker* w, double* G_out, double* sign_sum_
  * evaluates the sums directly.  Returns DCA_ERR_STATE if the frequency
  * measurement is off.  Synchronises the stream. */
 DCA_API int dca_walker_measure_M(dca_walker* w, double* M_out, double* sign_sum_out, int64_t* n_meas_out);
+
+/* Two-particle measurement of the particle-particle up-down channel
+ * (Sec. 2.5, Eq. bse_cluster; App. B four-point type PARTICLE_PARTICLE_UP_DOWN).
+ * Per configuration the spins are independent, so
+ *   G2(K, K', q) = < G_up(K, K') G_dn(q - K, q - K') >,
+ *   G_sigma(k1, k2) = G0(k1) delta_{k1 k2} - G0(k1) M_sigma(k1, k2) G0(k2),
+ *   M_sigma(k1, k2) = 1/(beta Nc) sum_ij e^{i (w1 tau_i - K1.r_i)} [(e^V - 1) N]_ij e^{-i (w2 tau_j - K2.r_j)},
+ * with the combined index k = (K, i w_n) and q = (Q, i nu_m) (q4_transfer,
+ * w4_transfer).  The measured points are s = K * 2 n_w4 + n + n_w4 for the
+ * cluster momenta K and n = -n_w4 .. n_w4 - 1; the spin-down factor is taken
+ * at q - s = (Q - K, i w_{m - n - 1}).  After every measured sweep each walker
+ * adds, with S = nc * 2 n_w4,
+ *   A(s1, s2) = sign M_up(s1, s2) M_dn(q - s1, q - s2)   [S][S]
+ *   D(up, s) = sign M_up(s, s),  D(dn, s) = sign M_dn(q - s, q - s)   [2][S]
+ * (M_sigma as dense products on the GPU, FP64 on the FP64 path, FP32 products
+ * with FP64 accumulators on the mixed path); G2 for a given G0 follows from
+ * them by dca_g4_assemble.  Outputs (host, may be NULL):
+ * A_out [W][S_w][S_w][re, im], D_out [W][2][S_w][re, im] concatenated over
+ * walkers (S_w of the walker's problem), sign_sum_out [W], n_meas_out [W].
+ * Returns DCA_ERR_STATE if the measurement is off.  Synchronises the stream. */
+DCA_API int dca_walker_measure_G4(dca_walker* w, double* A_out, double* D_out, double* sign_sum_out,
+                                  int64_t* n_meas_out);
+
+/* G2(s1, s2) [S][S][re, im] from one set of accumulators (A [S][S][re, im],
+ * D [2][S][re, im], their sign sum) and the bare propagator at the measured
+ * points, G0_up [S][re, im] at s and G0_dn [S][re, im] at q - s (paper sign):
+ *   G2 sign_sum = G0u(s1) G0d(s1) [ delta_{s1 s2} (sign_sum - D_up(s1) G0u(s1) - D_dn(s1) G0d(s1))
+ *                                   + A(s1, s2) G0u(s2) G0d(s2) ].
+ * Host arrays; evaluated on the current device.  Returns DCA_ERR_NUMERIC if
+ * sign_sum is zero. */
+DCA_API int dca_g4_assemble(int32_t S, const double* A, const double* D, double sign_sum, const double* G0_up,
+                            const double* G0_dn, double* G2_out);
 
 /* Zero the G accumulators, sign sums and measurement counters. */
 DCA_API int dca_walker_reset_measurements(dca_walker* w);

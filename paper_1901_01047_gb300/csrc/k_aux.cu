@@ -660,7 +660,7 @@ int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) 
   }
 #undef DCA_MEAS_GEMM
   k_meas_acc<<<grid_for((long long)W * blocks_of(2LL * max_nc * cfg.n_tau_meas, 256)), 256, 0, st>>>(cfg);
-  const int nf = launch_meas_nfft(cfg, max_cap, max_nc, st);
+  const int nf = launch_meas_nfft(cfg, max_cap, max_nc, st) + launch_meas_g4(cfg, max_cap, max_nc, st);
   k_meas_finish<<<(W + 127) / 128, 128, 0, st>>>(cfg);
   return 5 + (max_nc > 16) + (max_nc > 32) + nf;
 }

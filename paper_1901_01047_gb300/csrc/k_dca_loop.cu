@@ -282,3 +282,26 @@ extern "C" DCA_API int dca_g0_table_from_freq(const dca_lattice* lat, int32_t n_
   if (e != cudaSuccess) return loop_fail(DCA_ERR_CUDA, std::string("dca_g0_table_from_freq: ") + cudaGetErrorString(e));
   return DCA_OK;
 }
+
+extern "C" DCA_API int dca_g4_assemble(int32_t S, const double* A, const double* D, double sign_sum,
+                                       const double* G0_up, const double* G0_dn, double* G2_out) {
+  if (S < 1 || S > 4096 || !A || !D || !G0_up || !G0_dn || !G2_out)
+    return loop_fail(DCA_ERR_ARG, "dca_g4_assemble: invalid argument");
+  if (!(sign_sum != 0.0) || !std::isfinite(sign_sum)) return loop_fail(DCA_ERR_NUMERIC, "dca_g4_assemble: sign sum is zero");
+  const size_t sq = (size_t)S * S * 2;
+  Scratch s;
+  double *d_a = s.get(sq), *d_d = s.get(4 * (size_t)S), *d_u = s.get(2 * (size_t)S), *d_n = s.get(2 * (size_t)S),
+         *d_o = s.get(sq);
+  if (!d_a || !d_d || !d_u || !d_n || !d_o) return loop_fail(DCA_ERR_OOM, "dca_g4_assemble: device memory");
+  cudaError_t e = cudaMemcpy(d_a, A, sizeof(double) * sq, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_d, D, sizeof(double) * 4 * S, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_u, G0_up, sizeof(double) * 2 * S, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_n, G0_dn, sizeof(double) * 2 * S, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    dca::launch_g4_assemble(S, d_a, d_d, sign_sum, d_u, d_n, d_o, 0);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(G2_out, d_o, sizeof(double) * sq, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return loop_fail(DCA_ERR_CUDA, std::string("dca_g4_assemble: ") + cudaGetErrorString(e));
+  return DCA_OK;
+}

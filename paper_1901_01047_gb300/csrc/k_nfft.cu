@@ -49,16 +49,18 @@ constexpr int NFFT_RB = 64;        // rows of N per item
 constexpr int NFFT_MSP_MAX = 12;
 constexpr unsigned long long X56_MASK = (1ull << 56) - 1ull;
 
+// A measured walker needs the time words for the frequency measurement of M
+// and for the two-particle measurement.
 __device__ __forceinline__ bool wants_freq(const Config& cfg, const WalkerDev& w) {
-  return cfg.n_omega > 0 && w.active && w.measure_pending;
+  return (cfg.n_omega > 0 || cfg.n_w4 > 0) && w.active && w.measure_pending;
 }
 
 __device__ __forceinline__ bool wants_nfft(const Config& cfg, const WalkerDev& w) {
-  return !cfg.freq_dft && wants_freq(cfg, w);
+  return cfg.n_omega > 0 && !cfg.freq_dft && wants_freq(cfg, w);
 }
 
 __device__ __forceinline__ bool wants_dft(const Config& cfg, const WalkerDev& w) {
-  return cfg.freq_dft && wants_freq(cfg, w);
+  return cfg.n_omega > 0 && cfg.freq_dft && wants_freq(cfg, w);
 }
 
 // Time word of a vertex: (floor(tau / beta 2^56) << 8) | (site + 1), 0 for a
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(256) k_freq_prep(Config cfg) {
   const double inv_beta = 1.0 / pb.beta;
   for (int j = threadIdx.x; j < n; j += blockDim.x)
     w.vx[j] = time_word(w.vtau[par][j], inv_beta, w.vsite[par][j], w.vs[par][j]);
-  if (!cfg.freq_dft) return;
+  if (!cfg.freq_dft || cfg.n_omega <= 0) return;
   __shared__ int s_cnt[65], s_pos[65];
   for (int r = threadIdx.x; r <= nc; r += blockDim.x) s_cnt[r] = 0;
   __syncthreads();
@@ -289,8 +291,9 @@ cudaError_t setup_nfft() {
 }
 
 int launch_meas_nfft(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) {
-  if (cfg.n_omega <= 0) return 0;
+  if (cfg.n_omega <= 0 && cfg.n_w4 <= 0) return 0;
   k_freq_prep<<<cfg.n_walkers, 256, 0, st>>>(cfg);
+  if (cfg.n_omega <= 0) return 1;
   if (cfg.freq_dft) return 1 + launch_meas_ndft(cfg, max_cap, max_nc, st);
   const long long items = 2LL * cfg.n_walkers * blocks_of(max_cap, NFFT_RB);
   const size_t smem = nfft_smem_bytes(cfg, max_nc);

@@ -98,6 +98,10 @@ void launch_nfft_finish(const Config& cfg, int max_nc, const long long* d_base, 
 // The dense-DFT variant: per measurement the site sort and the contraction;
 // at read-out a copy of the accumulators (same output layout).
 int launch_meas_ndft(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
+// Two-particle measurement (k_g4.cu): returns the number of kernels launched.
+int launch_meas_g4(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
+void launch_g4_assemble(int S, const double* A, const double* D, double sign_sum, const double* Gu, const double* Gd,
+                        double* out, cudaStream_t st);
 void launch_ndft_copy(const Config& cfg, int max_nc, const long long* d_base, double* d_out, cudaStream_t st);
 // Phase table of the measurement grid (ProblemDev::g0m) from the FP32 table g0f.
 void launch_meas_table(const ProblemDev& pd, int n_tau_meas, cudaStream_t st);

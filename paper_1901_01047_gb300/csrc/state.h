@@ -61,6 +61,10 @@ struct ProblemDev {
   // m = 0 .. n_tau_meas (0 past the table end).
   const float* g0m;
   int32_t meas_q;
+  // Two-particle measurement: K_a . r_s / 2 pi modulo 1 as 56-bit fractions
+  // [nc][nc], and the index of Q - K for every K [nc] (null when off).
+  const unsigned long long* kr56;
+  const int32_t* k_dn;
 };
 
 struct Proposal {
@@ -153,6 +157,10 @@ struct WalkerDev {
   double* Mgrid;             // [2][nc][nfft_L] delayed-NFFT grid of M (frequency measurement), or null
   double* Mfreq;             // [2][nc][n_omega][re, im] dense-DFT accumulator of M, or null
   unsigned long long* vx;    // [cap] frequency measurement: per vertex (floor(tau/beta 2^56) << 8) | (site + 1), 0 if dead
+  void* g4E;                 // [2][cap][S] complex pairs of T: e^{i (w_s tau_j - K_s.r_j)} (two-particle measurement)
+  void* g4T;                 // [2][cap][S] complex pairs of T: f_i sum_j N_ij conj(E(j, s))
+  double* g4A;               // [S][S][re, im] sum of sign M_up(s1, s2) M_dn(q - s1, q - s2)
+  double* g4D;               // [2][S][re, im] sum of sign M_sigma(s, s)
   int32_t* perm;             // [cap] live columns sorted by site (dense DFT)
   int32_t* goff;             // [nc + 1] their site-group offsets
 };
@@ -230,6 +238,8 @@ struct Config {
   int32_t nfft_L;            // its grid points over [0, beta)
   int32_t nfft_msp;          // its window half-width in grid points
   int32_t freq_dft;          // frequency measurement as the dense contraction (else delayed NFFT)
+  int32_t n_w4;              // two-particle measurement: fermionic frequencies per sign (0 = off)
+  int32_t m4;                // its bosonic transfer index
 };
 
 }  // namespace dca

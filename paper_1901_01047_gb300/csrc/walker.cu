@@ -12,6 +12,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/dca_walker.h"
@@ -38,6 +39,7 @@ struct dca_walker {
   int W = 0, ks = 0, warmup = 0, R = 0, ntm = 0, precision = 0;
   double tie_eps = 1e-10;
   int max_cap = 0, max_nc = 0;
+  int q4 = 0;                       // momentum transfer of the two-particle measurement
   std::vector<int> nc_of;           // per walker
   std::vector<size_t> gacc_off;     // per walker offset into the host G layout
   std::vector<WalkerDev> h_W;       // host copies of the walker records
@@ -189,11 +191,24 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     return fail(nullptr, DCA_ERR_ARG, "update_kernel must be one of DCA_UPD_*");
   if (p.schedule < DCA_SCHEDULE_LOCKSTEP || p.schedule > DCA_SCHEDULE_POOLED)
     return fail(nullptr, DCA_ERR_ARG, "schedule must be one of DCA_SCHEDULE_*");
+  if (p.n_w4 < 0 || p.n_w4 > 32) return fail(nullptr, DCA_ERR_ARG, "n_w4 must be in 0..32");
+  if (p.n_w4 > 0 && (p.w4_transfer < -64 || p.w4_transfer > 64))
+    return fail(nullptr, DCA_ERR_ARG, "w4_transfer must be in -64..64");
   for (int i = 0; i < p.n_problems; ++i) {
     std::string why;
     if (dca::check_problem(p.problems[i], why) != DCA_OK)
       return fail(nullptr, DCA_ERR_ARG, "problem " + std::to_string(i) + ": " + why);
     if (p.problems[i].nc > 64) return fail(nullptr, DCA_ERR_ARG, "problem " + std::to_string(i) + ": nc > 64");
+    if (p.n_w4 > 0) {
+      const dca_problem& pr = p.problems[i];
+      if (!pr.k_dot_r || !pr.k_sub)
+        return fail(nullptr, DCA_ERR_ARG, "problem " + std::to_string(i) + ": the two-particle measurement needs k_dot_r and k_sub");
+      if (p.q4_transfer < 0 || p.q4_transfer >= pr.nc)
+        return fail(nullptr, DCA_ERR_ARG, "q4_transfer out of range for problem " + std::to_string(i));
+      for (int e = 0; e < pr.nc * pr.nc; ++e)
+        if (pr.k_sub[e] < 0 || pr.k_sub[e] >= pr.nc || !std::isfinite(pr.k_dot_r[e]))
+          return fail(nullptr, DCA_ERR_ARG, "problem " + std::to_string(i) + ": k_sub / k_dot_r out of range");
+    }
   }
   if (p.walker_problem)
     for (int w = 0; w < p.n_walkers; ++w)
@@ -260,6 +275,31 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
         h->err = "measurement phase table";
         return bail(DCA_ERR_CUDA);
       }
+    }
+    if (p.n_w4 > 0) {
+      // K.r / 2 pi modulo 1 as 56-bit fractions, and the index of Q - K
+      std::vector<unsigned long long> kr(pr.nc * pr.nc);
+      std::vector<int32_t> kdn(pr.nc);
+      for (int e = 0; e < pr.nc * pr.nc; ++e) {
+        const double x = pr.k_dot_r[e] / (2.0 * M_PI);
+        const double f = x - std::floor(x);
+        const double v = std::ldexp(f, 56);
+        kr[e] = v >= std::ldexp(1.0, 56) ? 0ull : (unsigned long long)v;
+      }
+      for (int k = 0; k < pr.nc; ++k) kdn[k] = pr.k_sub[p.q4_transfer * pr.nc + k];
+      void* dkr = h->dalloc(sizeof(unsigned long long) * kr.size());
+      void* dkd = h->dalloc(sizeof(int32_t) * kdn.size());
+      if (!dkr || !dkd) {
+        h->err = "device allocation of the two-particle tables";
+        return bail(DCA_ERR_OOM);
+      }
+      if (cudaMemcpy(dkr, kr.data(), sizeof(unsigned long long) * kr.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(dkd, kdn.data(), sizeof(int32_t) * kdn.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        h->err = "upload of the two-particle tables failed";
+        return bail(DCA_ERR_CUDA);
+      }
+      d.kr56 = (const unsigned long long*)dkr;
+      d.k_dn = (const int32_t*)dkd;
     }
     h->max_nc = std::max(h->max_nc, pr.nc);
   }
@@ -363,7 +403,14 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     pieces.push_back({(void**)&w.Gtmp, sizeof(double) * 2 * nc * p.n_tau_meas});
     pieces.push_back({(void**)&w.gR, sizeof(double) * 2 * nc * C});
     pieces.push_back({(void**)&w.bvec, sizeof(double) * 2 * nc * C});
-    if (p.n_omega_meas > 0) pieces.push_back({(void**)&w.vx, sizeof(unsigned long long) * C});
+    if (p.n_omega_meas > 0 || p.n_w4 > 0) pieces.push_back({(void**)&w.vx, sizeof(unsigned long long) * C});
+    if (p.n_w4 > 0) {
+      const size_t S4 = (size_t)nc * 2 * p.n_w4;
+      pieces.push_back({(void**)&w.g4E, 2 * esz * 2 * C * S4});
+      pieces.push_back({(void**)&w.g4T, 2 * esz * 2 * C * S4});
+      pieces.push_back({(void**)&w.g4A, sizeof(double) * 2 * S4 * S4});
+      pieces.push_back({(void**)&w.g4D, sizeof(double) * 4 * S4});
+    }
     if (p.n_omega_meas > 0 && p.freq_method == DCA_FREQ_NFFT)
       pieces.push_back({(void**)&w.Mgrid, sizeof(double) * 2 * nc * 4 * (size_t)p.n_omega_meas});
     if (p.n_omega_meas > 0 && p.freq_method == DCA_FREQ_DFT) {
@@ -442,6 +489,9 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.nfft_L = 4 * p.n_omega_meas;
   h->cfg.nfft_msp = h->precision == DCA_PREC_FP64 ? 12 : 8;
   h->cfg.freq_dft = p.freq_method == DCA_FREQ_DFT ? 1 : 0;
+  h->cfg.n_w4 = p.n_w4;
+  h->cfg.m4 = p.n_w4 > 0 ? p.w4_transfer : 0;
+  h->q4 = p.n_w4 > 0 ? p.q4_transfer : 0;
 
   if (dca::setup_window_kernels() != cudaSuccess || dca::setup_nfft() != cudaSuccess) {
     h->err = "kernel attribute setup failed";
@@ -889,6 +939,27 @@ extern "C" DCA_API int dca_walker_measure_M(dca_walker* h, double* M_out, double
   return DCA_OK;
 }
 
+extern "C" DCA_API int dca_walker_measure_G4(dca_walker* h, double* A_out, double* D_out, double* sign_sum_out,
+                                             int64_t* n_meas_out) {
+  if (!h) return DCA_ERR_ARG;
+  if (h->cfg.n_w4 <= 0) return fail(h, DCA_ERR_STATE, "the two-particle measurement is off (n_w4 = 0)");
+  int rc = pull_records(h);
+  if (rc != DCA_OK) return rc;
+  size_t offA = 0, offD = 0;
+  for (int wi = 0; wi < h->W; ++wi) {
+    const WalkerDev& w = h->h_W[wi];
+    const size_t S4 = (size_t)h->nc_of[wi] * 2 * h->cfg.n_w4;
+    if (A_out) CK(cudaMemcpyAsync(A_out + offA, w.g4A, sizeof(double) * 2 * S4 * S4, cudaMemcpyDeviceToHost, h->stream));
+    if (D_out) CK(cudaMemcpyAsync(D_out + offD, w.g4D, sizeof(double) * 4 * S4, cudaMemcpyDeviceToHost, h->stream));
+    offA += 2 * S4 * S4;
+    offD += 4 * S4;
+    if (sign_sum_out) sign_sum_out[wi] = w.sign_sum;
+    if (n_meas_out) n_meas_out[wi] = w.n_meas;
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return DCA_OK;
+}
+
 extern "C" DCA_API int dca_walker_reset_measurements(dca_walker* h) {
   if (!h) return DCA_ERR_ARG;
   int rc = pull_records(h);
@@ -898,6 +969,11 @@ extern "C" DCA_API int dca_walker_reset_measurements(dca_walker* h) {
     CK(cudaMemsetAsync(w.Gacc, 0, sizeof(double) * 2 * h->nc_of[wi] * h->ntm, h->stream));
     if (w.Mgrid) CK(cudaMemsetAsync(w.Mgrid, 0, sizeof(double) * 2 * h->nc_of[wi] * h->cfg.nfft_L, h->stream));
     if (w.Mfreq) CK(cudaMemsetAsync(w.Mfreq, 0, sizeof(double) * 4 * h->nc_of[wi] * h->cfg.n_omega, h->stream));
+    if (w.g4A) {
+      const size_t S4 = (size_t)h->nc_of[wi] * 2 * h->cfg.n_w4;
+      CK(cudaMemsetAsync(w.g4A, 0, sizeof(double) * 2 * S4 * S4, h->stream));
+      CK(cudaMemsetAsync(w.g4D, 0, sizeof(double) * 4 * S4, h->stream));
+    }
     w.sign_sum = 0.0;
     w.n_meas = 0;
     w.k_sum = 0.0;
@@ -1016,15 +1092,17 @@ extern "C" DCA_API int dca_walker_set_forced_decisions(dca_walker* h, int32_t wi
 // Checkpoint / resume.  Layout: SaveHeader, then per walker a SaveWalker
 // record, its k vertices (SaveVertex), its G accumulator [2][nc][n_tau_meas]
 // and, with the frequency measurement on, its NFFT grid [2][nc][4 n_omega]
-// (FP64), all little-endian host structs of fixed layout.
+// or dense sums [2][nc][n_omega][2], with the two-particle measurement on, its
+// accumulators [S][S][2] and [2][S][2] (FP64), all little-endian host structs of
+// fixed layout.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr uint32_t kSaveMagic = 0x57414344u;  // "DCAW"
-constexpr uint32_t kSaveVersion = 3u;
+constexpr uint32_t kSaveVersion = 4u;
 
 struct SaveHeader {
   uint32_t magic, version;
-  int32_t n_walkers, precision, n_tau_meas, warmup, n_omega, freq_dft;
+  int32_t n_walkers, precision, n_tau_meas, warmup, n_omega, freq_dft, n_w4, w4_transfer, q4_transfer, pad;
   uint64_t bytes;  // total size of the checkpoint
 };
 
@@ -1050,8 +1128,28 @@ static size_t freq_acc_doubles(const dca_walker* h, int wi) {
   return (size_t)h->nc_of[wi] * (h->cfg.freq_dft ? 4 * (size_t)h->cfg.n_omega : 2 * (size_t)h->cfg.nfft_L);
 }
 
+static size_t g4_acc_doubles(const dca_walker* h, int wi) {
+  if (h->cfg.n_w4 <= 0) return 0;
+  const size_t S4 = (size_t)h->nc_of[wi] * 2 * h->cfg.n_w4;
+  return 2 * S4 * S4 + 4 * S4;
+}
+
 static size_t acc_bytes(const dca_walker* h, int wi) {
-  return sizeof(double) * (2 * (size_t)h->nc_of[wi] * (size_t)h->ntm + freq_acc_doubles(h, wi));
+  return sizeof(double) * (2 * (size_t)h->nc_of[wi] * (size_t)h->ntm + freq_acc_doubles(h, wi) + g4_acc_doubles(h, wi));
+}
+
+// The device accumulators of a walker in checkpoint order (pointer, bytes).
+static std::vector<std::pair<double*, size_t>> acc_segments(const dca_walker* h, int wi) {
+  const WalkerDev& w = h->h_W[wi];
+  std::vector<std::pair<double*, size_t>> seg;
+  seg.push_back({w.Gacc, sizeof(double) * 2 * (size_t)h->nc_of[wi] * h->ntm});
+  if (w.Mgrid || w.Mfreq) seg.push_back({w.Mgrid ? w.Mgrid : w.Mfreq, sizeof(double) * freq_acc_doubles(h, wi)});
+  if (w.g4A) {
+    const size_t S4 = (size_t)h->nc_of[wi] * 2 * h->cfg.n_w4;
+    seg.push_back({w.g4A, sizeof(double) * 2 * S4 * S4});
+    seg.push_back({w.g4D, sizeof(double) * 4 * S4});
+  }
+  return seg;
 }
 
 static size_t save_size(const dca_walker* h) {
@@ -1070,8 +1168,8 @@ extern "C" DCA_API int dca_walker_save(dca_walker* h, void* buf, size_t cap, siz
   if (!buf) return DCA_OK;
   if (cap < need) return fail(h, DCA_ERR_ARG, "checkpoint buffer too small (" + std::to_string(need) + " bytes needed)");
   unsigned char* out = (unsigned char*)buf;
-  SaveHeader hd{kSaveMagic, kSaveVersion, h->W, h->prec_public, h->ntm, h->warmup, h->cfg.n_omega, h->cfg.freq_dft,
-                (uint64_t)need};
+  SaveHeader hd{kSaveMagic,       kSaveVersion, h->W,      h->prec_public, h->ntm, h->warmup, h->cfg.n_omega,
+                h->cfg.freq_dft, h->cfg.n_w4,  h->cfg.m4, h->q4,          0,      (uint64_t)need};
   std::memcpy(out, &hd, sizeof(hd));
   size_t off = sizeof(hd);
   for (int wi = 0; wi < h->W; ++wi) {
@@ -1116,11 +1214,11 @@ extern "C" DCA_API int dca_walker_save(dca_walker* h, void* buf, size_t cap, siz
       CK(cudaMemcpyAsync(s.data(), w.vs[par], sizeof(int32_t) * n_rows, cudaMemcpyDeviceToHost, h->stream));
       CK(cudaMemcpyAsync(tau.data(), w.vtau[par], sizeof(double) * n_rows, cudaMemcpyDeviceToHost, h->stream));
     }
-    const size_t gbytes = sizeof(double) * 2 * (size_t)h->nc_of[wi] * h->ntm;
-    CK(cudaMemcpyAsync(out + off + sizeof(SaveVertex) * k, w.Gacc, gbytes, cudaMemcpyDeviceToHost, h->stream));
-    if (w.Mgrid || w.Mfreq)
-      CK(cudaMemcpyAsync(out + off + sizeof(SaveVertex) * k + gbytes, w.Mgrid ? w.Mgrid : w.Mfreq,
-                         acc_bytes(h, wi) - gbytes, cudaMemcpyDeviceToHost, h->stream));
+    size_t aoff = off + sizeof(SaveVertex) * k;
+    for (const auto& sg : acc_segments(h, wi)) {
+      CK(cudaMemcpyAsync(out + aoff, sg.first, sg.second, cudaMemcpyDeviceToHost, h->stream));
+      aoff += sg.second;
+    }
     CK(cudaStreamSynchronize(h->stream));
     for (int i = 0; i < k; ++i) {
       const SaveVertex v{site[live[i]], s[live[i]], tau[live[i]]};
@@ -1142,7 +1240,8 @@ extern "C" DCA_API int dca_walker_load(dca_walker* h, const void* buf, size_t n)
   if (hd.magic != kSaveMagic || hd.version != kSaveVersion) return fail(h, DCA_ERR_ARG, "not a walker checkpoint");
   if (hd.bytes != n) return fail(h, DCA_ERR_ARG, "checkpoint size does not match its header");
   if (hd.n_walkers != h->W || hd.precision != h->prec_public || hd.n_tau_meas != h->ntm || hd.warmup != h->warmup ||
-      hd.n_omega != h->cfg.n_omega || hd.freq_dft != h->cfg.freq_dft)
+      hd.n_omega != h->cfg.n_omega || hd.freq_dft != h->cfg.freq_dft || hd.n_w4 != h->cfg.n_w4 ||
+      hd.w4_transfer != h->cfg.m4 || hd.q4_transfer != h->q4)
     return fail(h, DCA_ERR_ARG, "checkpoint of a walker set with other parameters");
   // first pass: validate everything before touching the walkers
   struct Parsed {
@@ -1200,11 +1299,11 @@ extern "C" DCA_API int dca_walker_load(dca_walker* h, const void* buf, size_t n)
       CK(cudaMemcpyAsync(w.vtau[0], tau.data(), sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
       CK(cudaMemcpyAsync(w.live_idx, live.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, h->stream));
     }
-    const size_t gbytes = sizeof(double) * 2 * (size_t)sw.nc * h->ntm;
-    CK(cudaMemcpyAsync(w.Gacc, in + p.g_off, gbytes, cudaMemcpyHostToDevice, h->stream));
-    if (w.Mgrid || w.Mfreq)
-      CK(cudaMemcpyAsync(w.Mgrid ? w.Mgrid : w.Mfreq, in + p.g_off + gbytes, acc_bytes(h, wi) - gbytes,
-                         cudaMemcpyHostToDevice, h->stream));
+    size_t aoff = p.g_off;
+    for (const auto& sg : acc_segments(h, wi)) {
+      CK(cudaMemcpyAsync(sg.first, in + aoff, sg.second, cudaMemcpyHostToDevice, h->stream));
+      aoff += sg.second;
+    }
     CK(cudaMemsetAsync(w.Gtmp, 0, sizeof(double) * 2 * (size_t)sw.nc * h->ntm, h->stream));
     w.n = k;
     w.n_live = k;

@@ -125,6 +125,9 @@ class Workload:
     recompute_at_measure: bool = False  # mixed path: N recomputed before every measurement
     n_omega_meas: int = 0  # frequency measurement of M: positive Matsubara frequencies
     freq_method: str = "nfft"  # "nfft" (delayed NFFT) or "dft" (the same sums as a dense contraction)
+    n_w4: int = 0  # two-particle measurement (pp up-down): fermionic frequencies per sign
+    w4_transfer: int = 0  # its bosonic frequency transfer index
+    q4_transfer: int = 0  # its momentum transfer (cluster momentum index)
     autotune: bool = False  # bench: choose k_s and the update kernel by the autotuner
     schedule: str = "lockstep"  # "pooled": the walkers share the sweep budget (all active every window)
     precision: str = "fp64"
@@ -187,6 +190,13 @@ WORKLOADS = {
                                recompute_every=0, recompute_sweeps=8, precision="mixed", n_omega_meas=128,
                                freq_method="dft", nc_choices=(8, 16), autotune=True, schedule="pooled",
                                beta_range=(5.0, 25.0), U_range=(4.0, 7.0)),
+    # the same batch with the two-particle measurement on: 8 fermionic frequencies
+    # per sign (S = 128 or 256 points per spin), zero transfer
+    "batched256_g4": Workload(name="batched256_g4", nc=16, t=1.0, tp=0.0, U=5.5, beta=15.0, mu=2.75, K=1.0,
+                              n_tau=2048, k_sub=64, walkers=256, warmup_sweeps=40, n_tau_meas=128,
+                              recompute_every=0, recompute_sweeps=8, precision="mixed", n_w4=8,
+                              nc_choices=(8, 16), autotune=True, schedule="pooled", beta_range=(5.0, 25.0),
+                              U_range=(4.0, 7.0)),
     # 36-site square cluster, U = 7, beta = 30, density 0.95, 32 walkers, G on 2048 tau points
     "betts36": Workload(name="betts36", nc=36, t=1.0, tp=0.0, U=7.0, beta=30.0, mu=3.4878678207599574, K=1.0,
                         n_tau=4096, k_sub=64, walkers=32, warmup_sweeps=40, n_tau_meas=2048,

@@ -25,7 +25,7 @@ EXPORTS = [
     "dca_walker_get_timing", "dca_walker_set_tuning", "dca_fresh_N", "dca_fresh_N_noalloc",
     "dca_walker_sync", "dca_walker_set_schedule", "dca_walker_set_limits", "dca_walker_save", "dca_walker_load",
     "dca_walker_measure_M", "dca_coarse_grain", "dca_sigma_update", "dca_g0_table_from_freq",
-    "dca_walker_set_recompute",
+    "dca_walker_set_recompute", "dca_walker_measure_G4", "dca_g4_assemble",
 ]
 UPDATE_KERNELS = {"auto": 0, "cuda_core": 1, "tcgen05": 2}
 # lockstep: every walker runs n more sweeps per sweep(n); pooled: the walkers
@@ -44,6 +44,8 @@ class Problem(C.Structure):
         ("K", C.c_double),
         ("n_tau", C.c_int32),
         ("G0", C.POINTER(C.c_double)),
+        ("k_dot_r", C.POINTER(C.c_double)),
+        ("k_sub", C.POINTER(C.c_int32)),
     ]
 
 
@@ -73,6 +75,9 @@ class Params(C.Structure):
         ("flip_fraction", C.c_double),
         ("duplicate_rule", C.c_int32),
         ("freq_method", C.c_int32),
+        ("n_w4", C.c_int32),
+        ("w4_transfer", C.c_int32),
+        ("q4_transfer", C.c_int32),
     ]
 
 
@@ -146,6 +151,8 @@ def load(path=LIB_PATH):
     L.dca_walker_load.argtypes = [P, P, C.c_size_t]
     L.dca_walker_measure_G.argtypes = [P, P, P, P]
     L.dca_walker_measure_M.argtypes = [P, P, P, P]
+    L.dca_walker_measure_G4.argtypes = [P, P, P, P, P]
+    L.dca_g4_assemble.argtypes = [C.c_int32, P, P, C.c_double, P, P, P]
     L.dca_walker_reset_measurements.argtypes = [P]
     L.dca_walker_stats.argtypes = [P, P]
     L.dca_walker_get_state.argtypes = [P, C.c_int32, P, C.POINTER(C.c_int32), P, P]
@@ -208,6 +215,22 @@ def _problem_struct(pr, keep):
     return p
 
 
+def g4_assemble(A, D, sign_sum, G0_up, G0_dn):
+    """G2 [S, S] (complex) from one set of two-particle accumulators and the bare
+    propagator at the measured points (dca_g4_assemble, on the GPU)."""
+    L = load()
+    S = A.shape[0]
+    a = np.ascontiguousarray(np.stack([A.real, A.imag], -1), np.float64)
+    d = np.ascontiguousarray(np.stack([D.real, D.imag], -1), np.float64)
+    gu = np.ascontiguousarray(np.stack([np.real(G0_up), np.imag(G0_up)], -1), np.float64)
+    gd = np.ascontiguousarray(np.stack([np.real(G0_dn), np.imag(G0_dn)], -1), np.float64)
+    out = np.zeros((S, S, 2), np.float64)
+    rc = L.dca_g4_assemble(int(S), _ptr(a), _ptr(d), float(sign_sum), _ptr(gu), _ptr(gd), _ptr(out))
+    if rc != DCA_OK:
+        raise WalkerError(rc, L.dca_walker_last_error(None).decode())
+    return out[..., 0] + 1j * out[..., 1]
+
+
 def _vertices(site, tau, s):
     n = len(site)
     verts = (Vertex * max(n, 1))()
@@ -244,7 +267,8 @@ class Walkers:
                  warmup_sweeps=20, n_tau_meas=64, precision="fp64", init_config_size=10, capacity=0,
                  seed=0, tie_eps=1e-10, log_capacity=0, update_kernel="auto", recompute_sweeps=0,
                  recompute_method="auto", schedule="lockstep", gamma_precision="fp64", recompute_at_measure=False,
-                 n_omega_meas=0, flip_fraction=0.0, duplicate_rule="abort", freq_method="nfft", stream=None):
+                 n_omega_meas=0, flip_fraction=0.0, duplicate_rule="abort", freq_method="nfft", n_w4=0,
+                 w4_transfer=0, q4_transfer=0, stream=None):
         L = load()
         self._keep = []
         probs = (Problem * len(problems))()
@@ -260,6 +284,12 @@ class Walkers:
             probs[i].K = float(pr.get("K", 1.0))
             probs[i].n_tau = int(g0.shape[-1] - 1)
             probs[i].G0 = g0.ctypes.data_as(C.POINTER(C.c_double))
+            if pr.get("k_dot_r") is not None:
+                kr = np.ascontiguousarray(pr["k_dot_r"], np.float64).reshape(-1)
+                ks = np.ascontiguousarray(pr["k_sub"], np.int32).reshape(-1)
+                self._keep += [kr, ks]
+                probs[i].k_dot_r = kr.ctypes.data_as(C.POINTER(C.c_double))
+                probs[i].k_sub = ks.ctypes.data_as(C.POINTER(C.c_int32))
         p = Params()
         p.n_problems = len(problems)
         p.problems = probs
@@ -295,6 +325,10 @@ class Walkers:
         p.duplicate_rule = {"abort": 0, "neglect": 1}[duplicate_rule] if isinstance(duplicate_rule, str) \
             else int(duplicate_rule)
         self.n_omega_meas = int(n_omega_meas)
+        p.n_w4 = int(n_w4)
+        p.w4_transfer = int(w4_transfer)
+        p.q4_transfer = int(q4_transfer)
+        self.n_w4 = int(n_w4)
         p.update_kernel = UPDATE_KERNELS[update_kernel] if isinstance(update_kernel, str) else int(update_kernel)
         self.n_walkers = int(n_walkers)
         self.n_tau_meas = int(n_tau_meas)
@@ -383,6 +417,24 @@ class Walkers:
             a = m[off:off + k].reshape(2, nc, self.n_omega_meas, 2)
             out.append(a[..., 0] + 1j * a[..., 1])
             off += k
+        return out, ss, nm
+
+    def measure_G4(self):
+        """Two-particle accumulators per walker: (A complex [S, S], D complex [2, S]) with
+        S = nc * 2 n_w4, the sign sums and the measurement counts."""
+        sizes = [nc * 2 * self.n_w4 for nc in self.nc]
+        A = np.zeros(max(sum(2 * S * S for S in sizes), 1), np.float64)
+        D = np.zeros(max(sum(4 * S for S in sizes), 1), np.float64)
+        ss = np.zeros(self.n_walkers, np.float64)
+        nm = np.zeros(self.n_walkers, np.int64)
+        self._check(self._L.dca_walker_measure_G4(self._h, _ptr(A), _ptr(D), _ptr(ss), _ptr(nm)))
+        out, oa, od = [], 0, 0
+        for S in sizes:
+            a = A[oa:oa + 2 * S * S].reshape(S, S, 2)
+            d = D[od:od + 4 * S].reshape(2, S, 2)
+            out.append((a[..., 0] + 1j * a[..., 1], d[..., 0] + 1j * d[..., 1]))
+            oa += 2 * S * S
+            od += 4 * S
         return out, ss, nm
 
     def reset_measurements(self):

@@ -76,7 +76,7 @@ def _params(walker, **over):
 @pytest.mark.parametrize("field,value", [
     ("k_sub", 0), ("k_sub", 129), ("n_walkers", 0), ("n_tau_meas", 0), ("init_config_size", -1),
     ("precision", 99), ("K", 0.0), ("beta", -1.0), ("U", -1.0), ("n_problems", 0), ("gamma_precision", 7),
-    ("schedule", 5), ("update_kernel", 9), ("recompute_method", 4),
+    ("schedule", 5), ("update_kernel", 9), ("recompute_method", 4), ("n_w4", 33), ("n_w4", -1),
 ])
 def test_invalid_parameters_rejected_on_host(lib, field, value):
     from paper_1901_01047_gb300 import walker
@@ -101,6 +101,42 @@ def test_bad_site_table_and_nonfinite_g0_rejected(lib):
     assert b"non-finite" in lib.dca_walker_last_error(None)
 
 
+def test_two_particle_measurement_needs_the_momentum_tables(lib):
+    from paper_1901_01047_gb300 import inputs, walker
+    p, keep, ss, g0 = _params(walker, n_w4=2)
+    h = C.c_void_p()
+    assert lib.dca_walker_create(C.byref(p), None, C.byref(h)) == -1
+    assert b"k_dot_r" in lib.dca_walker_last_error(None)
+    c = inputs.cluster(4)
+    kr = np.ascontiguousarray(inputs.k_dot_r(c), np.float64)
+    ks = np.ascontiguousarray(c.k_sub, np.int32)
+    keep += [kr, ks]
+    p.problems[0].k_dot_r = kr.ctypes.data_as(C.POINTER(C.c_double))
+    p.problems[0].k_sub = ks.ctypes.data_as(C.POINTER(C.c_int32))
+    p.q4_transfer = 4  # not a momentum index of a 4-site cluster
+    assert lib.dca_walker_create(C.byref(p), None, C.byref(h)) == -1
+    assert b"q4_transfer" in lib.dca_walker_last_error(None)
+    p.q4_transfer = 0
+    p.w4_transfer = 65
+    assert lib.dca_walker_create(C.byref(p), None, C.byref(h)) == -1
+    ks[1, 2] = 9
+    p.w4_transfer = 0
+    assert lib.dca_walker_create(C.byref(p), None, C.byref(h)) == -1
+    assert b"out of range" in lib.dca_walker_last_error(None)
+    assert not h.value
+
+
+def test_g4_assemble_checks_its_arguments(lib):
+    a = np.zeros((4, 4, 2))
+    d = np.zeros((2, 4, 2))
+    g = np.zeros((4, 2))
+    o = np.zeros((4, 4, 2))
+    ptr = lambda x: x.ctypes.data_as(C.c_void_p)
+    assert lib.dca_g4_assemble(0, ptr(a), ptr(d), 1.0, ptr(g), ptr(g), ptr(o)) == -1
+    assert lib.dca_g4_assemble(4, None, ptr(d), 1.0, ptr(g), ptr(g), ptr(o)) == -1
+    assert lib.dca_g4_assemble(4, ptr(a), ptr(d), 0.0, ptr(g), ptr(g), ptr(o)) == -5
+
+
 def test_tf32_precision_needs_the_tensor_cores(lib):
     from paper_1901_01047_gb300 import walker
     p, keep, ss, g0 = _params(walker, precision=2, update_kernel=1)
@@ -119,6 +155,7 @@ def test_null_handles_rejected(lib):
     assert lib.dca_walker_sweep(None, 1) == -1
     assert lib.dca_walker_stats(None, None) == -1
     assert lib.dca_walker_measure_G(None, None, None, None) == -1
+    assert lib.dca_walker_measure_G4(None, None, None, None, None) == -1
     assert lib.dca_g0_isolated_cluster(0, None, None, 0.0, 0.0, 1.0, 4, None) == -1
 
 
