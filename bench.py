@@ -60,11 +60,14 @@ TF32_PER_BF16 = 1.1 / 2.25
 FP32_INSTR_PER_S = 152 * 128 * 2.07e9
 MIXED_RECOMPUTE_TFLOPS = 4.0 / (2.0 / (FP32_INSTR_PER_S * 2 / 11 / 1e12) + 2.0 / (FP32_INSTR_PER_S * 2 / 1e12))
 
-# DRAM bytes (read + write) per launch of a kernel from an ncu capture of the
-# named workload (k_upd_tc: 847.8 MB read + 524.2 MB written in one window of
-# the pooled schedule, where every window carries all walkers); quoted as
-# `traffic` for that kernel on that workload only.
-NCU_TRAFFIC = {("batched256", "update"): 1.372e9}
+# DRAM bytes (read + write) per window of a kernel group from ncu captures of
+# the named workload (one window of the pooled schedule carries all walkers;
+# mean of two captured launches per kernel), quoted as `traffic` for that group
+# on that workload only:
+#   update  k_upd_tc 863.8 MB read + 533.0 MB written;
+#   extend  k_cand_zero 54.9 + 84.6, k_ext_g_tc 714.9 + 45.4, k_ext_x_tc
+#           703.5 + 44.9, k_cand_cc 125.6 + 2.3 (MB read + written).
+NCU_TRAFFIC = {("batched256", "update"): 1.397e9, ("batched256", "extend"): 1.776e9}
 
 
 class ClockSampler:
@@ -508,9 +511,10 @@ def run_ours(args, rank, world, local_rank):
     # propagator uploaded from pinned memory (the per-iteration input of an
     # outer DCA loop; validated on the device), one step, and every walker's
     # G read back, every step.
-    G0_host = [torch.from_numpy(np.ascontiguousarray(p["G0"])).pin_memory() for p in probs]
-    G0_np = [t.numpy() for t in G0_host]
-    h2d = sum(int(t.numel() * 8) for t in G0_host)
+    G0_host = torch.from_numpy(np.concatenate([np.ascontiguousarray(p["G0"], np.float64).reshape(-1)
+                                               for p in probs])).pin_memory()
+    G0_np = G0_host.numpy()
+    h2d = int(G0_host.numel() * 8)
     g_bytes = sum(2 * nc * wl.n_tau_meas * 8 for nc in gw.nc) + 16 * wl.walkers
     st2 = gw.stats()
     if dist:
@@ -518,8 +522,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     te0 = time.perf_counter()
     for k in range(args.steps):
-        for p, g in enumerate(G0_np):
-            gw.update_G0(p, g)
+        gw.update_G0_all(G0_np)  # one copy of every problem's table, checked and committed on the device
         gw.sweep(1, sync=False)
         gw.measure_G()  # synchronises
     gw.sync()
@@ -535,6 +538,7 @@ def run_ours(args, rank, world, local_rank):
         windows = max(1, gtimes["propose"][1])  # one proposal kernel per window
         roof = roofline(dominant, gtimes[dominant][0], windows, work, peaks, kind, wl)
         roof_upd = roofline("update", gtimes["update"][0], windows, work, peaks, kind, wl)
+        roof["traffic"] = NCU_TRAFFIC.get((wl.name, dominant))
         roof_upd["traffic"] = NCU_TRAFFIC.get((wl.name, "update"))
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

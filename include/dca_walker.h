@@ -478,8 +478,23 @@ DCA_API int dca_g0_table_from_freq(const dca_lattice* lat, int32_t n_omega, cons
  * buffer on the walker's stream (pass pinned host memory for an asynchronous
  * copy) and sweeps launched afterwards use it.  The table is checked on the
  * device: one with a non-finite entry is not taken (the previous table stays)
- * and the next dca_walker_sync returns DCA_ERR_ARG. */
+ * and the next dca_walker_sync returns DCA_ERR_ARG.  A table that differs
+ * from the current one changes N^-1 = e^V - g0 (e^V - 1) of every walker on
+ * that problem, so their N is rebuilt from scratch (Gauss-Jordan, FP64) for
+ * their current configurations, and their signs are taken from the new
+ * determinants; an unchanged table leaves the walkers as they are. */
 DCA_API int dca_walker_update_G0(dca_walker* w, int32_t problem, const double* G0);
+
+/* Replace the bare propagators of all problems at once: G0_all is the host
+ * concatenation of every problem's table in problem order (problem p:
+ * [2][nc_p][n_tau_p + 1], as for dca_walker_update_G0).  One copy to the
+ * staging buffers (pinned host memory makes it asynchronous) and three
+ * kernels for all problems, stream-ordered like dca_walker_update_G0 (with
+ * pinned memory the host array must stay unchanged until the stream has
+ * passed the copy, e.g. until the next dca_walker_sync); a
+ * problem whose table has a non-finite entry keeps its previous table (the
+ * others are taken) and the next dca_walker_sync returns DCA_ERR_ARG. */
+DCA_API int dca_walker_update_G0_all(dca_walker* w, const double* G0_all);
 
 /* Change the submatrix size (1..128) and the N-update kernel (DCA_UPD_*,
  * mixed precision only) between sweeps.  The submatrix method reaches the

@@ -36,13 +36,18 @@ __global__ void k_init_vertices(Config cfg, int n0) {
 // is N[dst][sp] itself for FP64 storage and Ascr[sp] for FP32 storage.
 // mode 0: dst = current parity (initial build); mode 1: dst = other parity
 // (periodic recompute, only walkers with recompute_pending).
+// mode 0: every walker (initial build, rebuild after a checkpoint load);
+// mode 1: walkers with a periodic recompute in this window (into the other
+// buffer); mode 2: walkers whose bare propagator changed (in place).
 __device__ __forceinline__ bool wants_build(const WalkerDev& w, int mode) {
-  return mode == 0 ? true : (w.active && w.recompute_pending && w.status == ST_OK);
+  if (mode == 0) return true;
+  if (mode == 2) return w.rebuild_pending && w.status == ST_OK;
+  return w.active && w.recompute_pending && w.status == ST_OK;
 }
 
 __device__ __forceinline__ double* work_matrix(const Config& cfg, const WalkerDev& w, int mode, int sp) {
   if (cfg.prec == PREC_MIXED) return w.Ascr[sp];
-  return (double*)w.N[mode == 0 ? w.parity : w.parity ^ 1][sp];
+  return (double*)w.N[mode == 1 ? w.parity ^ 1 : w.parity][sp];
 }
 
 // Persistent grid; one item = 256 entries of one walker-spin's A.
@@ -109,7 +114,7 @@ __global__ void __launch_bounds__(256) k_store_fp32(Config cfg, int mode) {
         const WalkerDev& w = cfg.W[s >> 1];
         const int sp = s & 1, n = w.n, ld = w.cap;
         const double* A = w.Ascr[sp];
-        float* N = (float*)w.N[mode == 0 ? w.parity : w.parity ^ 1][sp];
+        float* N = (float*)w.N[mode == 1 ? w.parity ^ 1 : w.parity][sp];
         const long long idx = (long long)item * 256 + threadIdx.x;
         if (idx < (long long)n * n) {
           const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
@@ -593,9 +598,11 @@ void launch_fresh_inverse(const Config& cfg, int max_n, int* d_sgn, cudaStream_t
 }
 
 // g0 = -G0 in FP64 and its FP32 copy, from a staged table, committed only if
-// every staged entry is finite (else *bad is set and the old table stays).
+// every staged entry is finite (else *bad is set and the old table stays);
+// *changed is set if the committed table differs from the old one.
 // One block: the check and the commit need one barrier between them.
-__global__ void __launch_bounds__(1024) k_negate(const double* src, double* dst, float* dstf, size_t n, int* bad) {
+__global__ void __launch_bounds__(1024) k_negate(const double* src, double* dst, float* dstf, size_t n, int* bad,
+                                                 int* changed) {
   __shared__ int s_bad;
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
@@ -607,28 +614,66 @@ __global__ void __launch_bounds__(1024) k_negate(const double* src, double* dst,
     if (threadIdx.x == 0) *bad = 1;
     return;
   }
+  int c = 0;
   for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+    c |= dst[i] != -src[i] ? 1 : 0;
     dst[i] = -src[i];
     dstf[i] = (float)(-src[i]);
   }
+  if (__syncthreads_or(c) && threadIdx.x == 0) *changed = 1;
 }
 
-void launch_negate(const double* src, double* dst, float* dstf, size_t n, int* bad, cudaStream_t st) {
-  k_negate<<<1, 1024, 0, st>>>(src, dst, dstf, n, bad);
+void launch_negate(const double* src, double* dst, float* dstf, size_t n, int* bad, int* changed, cudaStream_t st) {
+  k_negate<<<1, 1024, 0, st>>>(src, dst, dstf, n, bad, changed);
+}
+
+// Walkers of a problem whose table changed: N rebuilt from scratch in place
+// (the inverse of e^V - g0 (e^V - 1) for the new g0), with the configuration
+// sign from the determinants.
+__global__ void k_mark_rebuild(Config cfg, const int* changed) {
+  const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (wi >= cfg.n_walkers) return;
+  WalkerDev& w = cfg.W[wi];
+  w.rebuild_pending = (changed[w.problem] && w.n > 0 && w.status == ST_OK) ? 1 : 0;
+}
+
+__global__ void k_rebuild_finish(Config cfg, const int* sgn) {
+  const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (wi >= cfg.n_walkers) return;
+  WalkerDev& w = cfg.W[wi];
+  if (!w.rebuild_pending) return;
+  w.rebuild_pending = 0;
+  const int s = sgn[2 * wi] * sgn[2 * wi + 1];
+  if (s == 0) set_status(w, ST_ERR_NUMERIC);
+  w.sign = s < 0 ? -1.0 : 1.0;
+}
+
+int launch_rebuild_changed(const Config& cfg, int max_cap, const int* changed, int* d_sgn, cudaStream_t st) {
+  const int W = cfg.n_walkers;
+  k_mark_rebuild<<<(W + 127) / 128, 128, 0, st>>>(cfg, changed);
+  const long long g = grid_for(2LL * W * blocks_of((long long)max_cap * max_cap, 256));
+  k_build_A<<<g, 256, 0, st>>>(cfg, 2);
+  launch_gj(cfg, 2, max_cap, d_sgn, st);
+  if (cfg.prec == PREC_MIXED) k_store_fp32<<<g, 256, 0, st>>>(cfg, 2);
+  k_rebuild_finish<<<(W + 127) / 128, 128, 0, st>>>(cfg, d_sgn);
+  return cfg.prec == PREC_MIXED ? 5 : 4;
 }
 
 // g0m[sp][p][d][m] = g0f[sp][d][q m + p] for q m + p <= n_tau, else 0.
+__device__ __forceinline__ float meas_table_entry(const float* g0f, int nc, int n_tau, int q, int ntm, size_t e) {
+  const int m = (int)(e % (ntm + 1));
+  size_t r = e / (ntm + 1);
+  const int d = (int)(r % nc);
+  r /= nc;
+  const int p = (int)(r % q), sp = (int)(r / q);
+  const int l = q * m + p;
+  return l <= n_tau ? g0f[((size_t)sp * nc + d) * (n_tau + 1) + l] : 0.0f;
+}
+
 __global__ void k_meas_table(const float* g0f, float* g0m, int nc, int n_tau, int q, int ntm) {
   const size_t total = (size_t)2 * q * nc * (ntm + 1);
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int m = (int)(e % (ntm + 1));
-    size_t r = e / (ntm + 1);
-    const int d = (int)(r % nc);
-    r /= nc;
-    const int p = (int)(r % q), sp = (int)(r / q);
-    const int l = q * m + p;
-    g0m[e] = l <= n_tau ? g0f[((size_t)sp * nc + d) * (n_tau + 1) + l] : 0.0f;
-  }
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+    g0m[e] = meas_table_entry(g0f, nc, n_tau, q, ntm, e);
 }
 
 void launch_meas_table(const ProblemDev& pd, int n_tau_meas, cudaStream_t st) {
@@ -636,6 +681,61 @@ void launch_meas_table(const ProblemDev& pd, int n_tau_meas, cudaStream_t st) {
   const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 4096);
   k_meas_table<<<blocks, 256, 0, st>>>(pd.g0f, const_cast<float*>(pd.g0m), pd.nc, pd.n_tau, pd.meas_q, n_tau_meas);
 }
+
+// All problems at once: the staged tables lie back to back (problem p at
+// off[p], 2 nc (n_tau + 1) entries).  Check: bad[p] = 1 (and *bad_any = 1) if a
+// staged entry of problem p is not finite; commit: g0 = -G0 and its FP32
+// copy for every problem with bad[p] == 0; then the measurement phase tables.
+__global__ void k_g0_check_all(const ProblemDev* P, int np, const double* stage, const long long* off, int* bad,
+                               int* bad_any) {
+  const int p = blockIdx.y;
+  if (p >= np) return;
+  const long long n = 2LL * P[p].nc * (P[p].n_tau + 1);
+  const double* src = stage + off[p];
+  int b = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b |= isfinite(src[i]) ? 0 : 1;
+  if (__syncthreads_or(b) && threadIdx.x == 0) {
+    bad[p] = 1;
+    *bad_any = 1;
+  }
+}
+
+__global__ void k_g0_commit_all(const ProblemDev* P, int np, const double* stage, const long long* off,
+                                const int* bad, int* changed) {
+  const int p = blockIdx.y;
+  if (p >= np || bad[p]) return;
+  const long long n = 2LL * P[p].nc * (P[p].n_tau + 1);
+  const double* src = stage + off[p];
+  double* dst = const_cast<double*>(P[p].g0);
+  float* dstf = const_cast<float*>(P[p].g0f);
+  int c = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    c |= dst[i] != -src[i] ? 1 : 0;
+    dst[i] = -src[i];
+    dstf[i] = (float)(-src[i]);
+  }
+  if (__syncthreads_or(c) && threadIdx.x == 0) changed[p] = 1;
+}
+
+__global__ void k_meas_table_all(const ProblemDev* P, int np, int ntm, const int* bad) {
+  const int p = blockIdx.y;
+  if (p >= np || bad[p] || P[p].meas_q <= 0) return;
+  const int q = P[p].meas_q, nc = P[p].nc;
+  float* g0m = const_cast<float*>(P[p].g0m);
+  const size_t total = (size_t)2 * q * nc * (ntm + 1);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+    g0m[e] = meas_table_entry(P[p].g0f, nc, P[p].n_tau, q, ntm, e);
+}
+
+void launch_g0_update_all(const ProblemDev* d_P, int np, int ntm, const double* stage, const long long* off, int* bad,
+                          int* bad_any, int* changed, cudaStream_t st) {
+  const dim3 grid(16, np);
+  k_g0_check_all<<<grid, 256, 0, st>>>(d_P, np, stage, off, bad, bad_any);
+  k_g0_commit_all<<<grid, 256, 0, st>>>(d_P, np, stage, off, bad, changed);
+  k_meas_table_all<<<grid, 256, 0, st>>>(d_P, np, ntm, bad);
+}
+
 
 int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) {
   const int W = cfg.n_walkers;

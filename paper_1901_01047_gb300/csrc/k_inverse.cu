@@ -43,10 +43,13 @@ __device__ void gj_matrix(const Config& cfg, int mode, int mat, int* sgn_out, cg
 
 __device__ __forceinline__ bool gj_wants(const Config& cfg, int mode, int mat) {
   const WalkerDev& w = cfg.W[mat >> 1];
-  return mode == 0 ? true : (w.active && w.recompute_pending && w.status == ST_OK);
+  if (mode == 0) return true;
+  if (mode == 2) return w.rebuild_pending && w.status == ST_OK;
+  return w.active && w.recompute_pending && w.status == ST_OK;
 }
 
-// mode 0: initial build / standalone; mode 1: periodic recompute.
+// mode 0: initial build / standalone; mode 1: periodic recompute (into the
+// other buffer); mode 2: rebuild after a change of the bare propagator.
 // Persistent grid of clusters fed by a work queue: the rank-0 block of a
 // cluster takes the next matrix (walker * 2 + spin) from cfg.gj_next (reset to
 // 0 by k_build_A before every launch), so clusters that drew small matrices
@@ -82,7 +85,7 @@ __device__ void gj_matrix(const Config& cfg, int mode, int mat, int* sgn_out, cg
   const int wi = mat >> 1, sp = mat & 1;
   WalkerDev& w = cfg.W[wi];
   const int n = w.n, ld = w.cap;
-  double* A = (cfg.prec == PREC_MIXED) ? w.Ascr[sp] : (double*)w.N[mode == 0 ? w.parity : w.parity ^ 1][sp];
+  double* A = (cfg.prec == PREC_MIXED) ? w.Ascr[sp] : (double*)w.N[mode == 1 ? w.parity ^ 1 : w.parity][sp];
   extern __shared__ int s_piv[];
   __shared__ GjPost s_post;
   __shared__ GjPost s_warp[GJ_THREADS / 32];

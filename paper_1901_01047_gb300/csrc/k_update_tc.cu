@@ -8,7 +8,7 @@
 // hi = x rounded to TF32 and lo = x - hi rounded to TF32 (the tensor core
 // would otherwise truncate the remainder's low bits); the MMA chain
 // accumulates hi*hi + hi*lo + lo*hi in FP32 in tensor memory, each product
-// exact, the split carrying x to about 2^-22 of |x|.  The split operands are written by k_upd_ops in the
+// exact, the split carrying x to about 2^-22 of |x|.  The split operands are written by k_upd_factors in the
 // layout the TMA loads: planes [hi | lo] x rows x 128 K-columns (512 B rows).
 //
 // Work item = one 128-row block of one walker-spin N.  A CTA (one per SM)
@@ -298,59 +298,155 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
   }
 }
 
-// Split operands of the tensor-core update, written in the TMA layout
-// [plane hi | lo][cap rows][TC_KS columns] (FP32):
-//   A rows i < n:  L'[i, p]          (p < l; zero for l <= p < lpad)
-//   B rows j < n:  R[p, j] = N[P_p, j] (transposed through shared memory)
-// lpad = l rounded up to 32 (the K extent of the loaded chunks).
-// Persistent grid over walker-spin pairs; per pair the items are the A
-// blocks (256 entries each) followed by the B blocks (32 rows of B each).
-__global__ void __launch_bounds__(256) k_upd_ops(Config cfg) {
-  __shared__ float s_t[TC_KS][33];
+// The update factors of the tensor-core path in one pass (replaces the three
+// kernels of the other paths, L -> L' -> split operands):
+//   L[x, p]  = (G_ext[x, P_p] - delta_{x P_p}) a_p   for the rows x of the block,
+//   L'[x, :] = L[x, :] B^-1                           (double-float, stored in Lp),
+//   A rows x < n of the operand: TF32 split of L'[x, p], zero for l <= p < lpad;
+// and per 32-column block of R = N_ext[P, :] (stored in Rr for the border
+// update) its transposed TF32 split into the B operand.
+// L is formed in double-float on the FP32 pipes for the rows x < n (N and
+// the candidate columns G_ext[x < n, c] are FP32 products, so exact in FP32;
+// the per-column factors e^{V} / (e^{V} - 1) a_p are formed once per item in
+// FP64 and split), in FP64 for the rows of accepted insertions (X is FP64).
+// Items per walker-spin: ceil(rows / 32) row blocks (rows = n + n_ins), then
+// ceil(n / 32) column blocks.
+__global__ void __launch_bounds__(256) k_upd_factors(Config cfg) {
+  constexpr int RB = 32;
+  __shared__ __align__(16) unsigned char s_raw[RB * KS_MAX * sizeof(float2)];
+  __shared__ float2 s_c1[KS_MAX];
+  float2(*s_L)[KS_MAX] = reinterpret_cast<float2(*)[KS_MAX]>(s_raw);  // [RB][KS_MAX]
+  float(*s_t)[33] = reinterpret_cast<float(*)[33]>(s_raw);             // [KS_MAX][33]
+  static_assert(KS_MAX * 33 * sizeof(float) <= sizeof(s_raw), "transpose tile");
   for_each_item(
       2 * cfg.n_walkers,
       [&](int s) -> long long {
         const WalkerDev& w = cfg.W[s >> 1];
         if (!(w.active && w.n_acc > 0)) return 0;
-        const int lpad = (w.n_acc + 31) & ~31;
-        return blocks_of((long long)w.n * lpad, 256) + (w.n + 31) / 32;
+        return blocks_of(w.n + w.n_ins, RB) + blocks_of(w.n, RB);
       },
       [&](int s, int item) {
         const WalkerDev& w = cfg.W[s >> 1];
-        const int sp = s & 1, n = w.n, l = w.n_acc, cap = w.cap;
-        const int lpad = (l + 31) & ~31;
-        const int a_blocks = (int)blocks_of((long long)n * lpad, 256);
-        if (item < a_blocks) {
-          const long long idx = (long long)item * 256 + threadIdx.x;
-          if (idx < (long long)n * lpad) {
-            const int i = (int)(idx / lpad), p = (int)(idx - (long long)i * lpad);
-            // L' is stored as FP32 pairs on the mixed path (hi carries the FP32 value)
-            const float x = p < l ? reinterpret_cast<const float2*>(w.Lp[sp])[(size_t)i * KS_MAX + p].x : 0.0f;
-            float hi, lo;
-            tc::tf32_split(x, hi, lo);
-            w.Aop[sp][(size_t)i * TC_KS + p] = hi;
-            w.Aop[sp][((size_t)cap + i) * TC_KS + p] = lo;
+        const int sp = s & 1, n = w.n, l = w.n_acc, cap = w.cap, ld = w.cap;
+        const int rows = n + w.n_ins, lpad = (l + 31) & ~31;
+        const int ra = (int)blocks_of(rows, RB);
+        const ProblemDev& pb = cfg.P[w.problem];
+        const float* N = (const float*)w.N[w.parity][sp];
+        const int* vs = w.vs[w.parity];
+        __syncthreads();  // the previous item is done with the shared tiles
+        if (item < ra) {
+          const int t0 = item * RB;
+          for (int p = threadIdx.x; p < l; p += blockDim.x) {
+            const int P = w.P[p];
+            const double a = w.aP[sp][p];
+            if (P < n) {
+              const int sy = vs[P];
+              s_c1[p] = df_split(expV(pb, sp, sy) * pb.rexpVm1[sp][sy > 0 ? 1 : 0] * a);
+            } else {
+              s_c1[p] = df_split(a);
+            }
+          }
+          __syncthreads();
+          for (int e = threadIdx.x; e < RB * l; e += blockDim.x) {
+            const int r = e / l, p = e - r * l;
+            const int t = t0 + r;
+            float2 v = make_float2(0.f, 0.f);
+            if (t < rows) {
+              const int x = t < n ? t : n + w.acc_slot[t - n];
+              const int P = w.P[p];
+              const double a = w.aP[sp][p];
+              if (a != 0.0 && !(x < n && vs[x] == 0)) {
+                if (x < n) {
+                  // FP32-exact entry times the column factor, in double-float.  An
+                  // existing column y = P: G_ext[x, y] = (N_xy e^{V_y} - delta) / (e^{V_y} - 1),
+                  // so (G_ext - delta) a = (N_xy - delta) e^{V_y} a / (e^{V_y} - 1) = (N_xy - delta) c1;
+                  // a candidate column: (G_ext[x, c] - 0) a with c1 = a (x < n is never the candidate)
+                  const float g = P < n ? N[(size_t)x * ld + P] : (float)w.Gc[sp][(size_t)(P - n) * ld + x];
+                  float hi = 0.f, lo = 0.f;
+                  df_fma(hi, lo, g, 0.f, s_c1[p].x, s_c1[p].y);
+                  if (x == P) df_fma(hi, lo, -1.f, 0.f, s_c1[p].x, s_c1[p].y);
+                  v = df_norm(hi, lo);
+                } else {
+                  double val;
+                  if (P < n) {
+                    const int sy = vs[P];
+                    val = (w.Xr[sp][(size_t)(x - n) * ld + P] * expV(pb, sp, sy)) * pb.rexpVm1[sp][sy > 0 ? 1 : 0] * a;
+                  } else {
+                    val = (w.Gc[sp][(size_t)(P - n) * ld + x] - (x == P ? 1.0 : 0.0)) * a;
+                  }
+                  v = df_split(val);
+                }
+              }
+            }
+            s_L[r][p] = v;
+          }
+          __syncthreads();
+          // L' = L B^-1: four consecutive outputs of a row per thread (four
+          // independent double-float chains sharing the loads of L)
+          const int lq = lpad / 4;
+          const float2* Bi = reinterpret_cast<const float2*>(w.Binv[sp]);
+          for (int e = threadIdx.x; e < RB * lq; e += blockDim.x) {
+            const int r = e / lq, q = (e - r * lq) * 4;
+            const int t = t0 + r;
+            if (t >= rows) continue;
+            const int x = t < n ? t : n + w.acc_slot[t - n];
+            float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+            if (q < l) {
+              for (int p = 0; p < l; ++p) {
+                const float2 a = s_L[r][p];
+                const float2* brow = Bi + (size_t)p * KS_MAX + q;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  const float2 b = brow[u];  // columns >= l of B^-1 are never read back
+                  df_fma(hi[u], lo[u], a.x, a.y, b.x, b.y);
+                }
+              }
+            }
+            float2* lp = reinterpret_cast<float2*>(w.Lp[sp]) + (size_t)x * KS_MAX + q;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float2 o = df_norm(hi[u], lo[u]);
+              if (q + u < l) lp[u] = o;
+              if (x < n) {
+                float th, tl;
+                tc::tf32_split(q + u < l ? o.x : 0.0f, th, tl);
+                w.Aop[sp][(size_t)x * TC_KS + q + u] = th;
+                w.Aop[sp][((size_t)cap + x) * TC_KS + q + u] = tl;
+              }
+            }
           }
         } else {
-          const int j0 = (item - a_blocks) * 32;
-          const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-          const float* Rr = (const float*)w.Rr[sp];
-          for (int p = warp; p < lpad; p += 8)
-            s_t[p][lane] = (p < l && j0 + lane < n) ? Rr[(size_t)p * cap + j0 + lane] : 0.0f;
+          // R rows (Rr, for the border update) and the transposed split B operand
+          const int j0 = (item - ra) * RB;
+          const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, j = j0 + lane;
+          float* Rr = (float*)w.Rr[sp];
+          for (int p = warp; p < lpad; p += 8) {
+            float v = 0.0f;
+            if (p < l && j < n) {
+              const int P = w.P[p];
+              v = P < n ? N[(size_t)P * ld + j] : (float)w.Xr[sp][(size_t)(P - n) * ld + j];
+              Rr[(size_t)p * cap + j] = v;
+            }
+            s_t[p][lane] = v;
+          }
           __syncthreads();
-          for (int jj = warp; jj < 32; jj += 8) {
-            const int j = j0 + jj;
-            if (j < n)
+          for (int jj = warp; jj < RB; jj += 8) {
+            const int jr = j0 + jj;
+            if (jr < n)
               for (int p = lane; p < lpad; p += 32) {
                 float hi, lo;
                 tc::tf32_split(s_t[p][jj], hi, lo);
-                w.Bop[sp][(size_t)j * TC_KS + p] = hi;
-                w.Bop[sp][((size_t)cap + j) * TC_KS + p] = lo;
+                w.Bop[sp][(size_t)jr * TC_KS + p] = hi;
+                w.Bop[sp][((size_t)cap + jr) * TC_KS + p] = lo;
               }
           }
-          __syncthreads();
         }
       });
+}
+
+void launch_upd_factors(const Config& cfg, int max_cap, cudaStream_t st) {
+  const long long items = 2LL * cfg.n_walkers * (blocks_of(max_cap, 32) + blocks_of(max_cap, 32));
+  k_upd_factors<<<persist_grid((const void*)k_upd_factors, items, 256), 256, 0, st>>>(cfg);
 }
 
 // ---------------------------------------------------------------------------
@@ -370,10 +466,6 @@ cudaError_t setup_update_tc() {
 
 int tc_tile_n(int ks) { return ks <= 64 ? 64 : 32; }
 
-void launch_upd_ops(const Config& cfg, cudaStream_t st) {
-  const long long S = 2LL * cfg.n_walkers;
-  k_upd_ops<<<sm_grid(S * 64, 4), 256, 0, st>>>(cfg);
-}
 
 void launch_upd_tc(const Config& cfg, cudaStream_t st) {
   const int grid = device_sm_count();

@@ -1367,12 +1367,12 @@ static int launch_group_t(int group, const Config& cfg, int max_cap, cudaStream_
       return 1;
     }
     case GROUP_UPDATE_PRE:
+      if (cfg.prec == PREC_MIXED && cfg.upd_kernel == UPD_TCGEN05) {
+        launch_upd_factors(cfg, max_cap, st);
+        return 1;
+      }
       k_upd_lrow<T><<<persist_grid((const void*)k_upd_lrow<T>, S * kc, 256), 256, 0, st>>>(cfg);
       k_upd_lp_rr<T, A><<<persist_grid((const void*)k_upd_lp_rr<T, A>, 2 * S * kc, 256), 256, 0, st>>>(cfg);
-      if (cfg.prec == PREC_MIXED && cfg.upd_kernel == UPD_TCGEN05) {
-        launch_upd_ops(cfg, st);
-        return 3;
-      }
       return 2;
     case GROUP_UPDATE:
       if (cfg.prec == PREC_MIXED && cfg.upd_kernel == UPD_TCGEN05)

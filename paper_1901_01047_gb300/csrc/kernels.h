@@ -83,11 +83,12 @@ bool encode_update_maps(const WalkerDev& w, int ks, TmapDev* out);
 cudaError_t setup_ext_tc();
 void launch_ext_g_tc(const Config& cfg, cudaStream_t st);
 void launch_ext_x_tc(const Config& cfg, cudaStream_t st);
-void launch_upd_ops(const Config& cfg, cudaStream_t st);
+// L, L' and both split operands of the tensor-core update in one kernel.
+void launch_upd_factors(const Config& cfg, int max_cap, cudaStream_t st);
 void launch_upd_tc(const Config& cfg, cudaStream_t st);
 // g0 = -G0 (FP64 and FP32) from a staged G0, unless an entry is not finite:
 // then *bad = 1 and the old table is kept.
-void launch_negate(const double* src, double* dst, float* dstf, size_t n, int* bad, cudaStream_t st);
+void launch_negate(const double* src, double* dst, float* dstf, size_t n, int* bad, int* changed, cudaStream_t st);
 // Delayed-NFFT frequency measurement: kernel attributes, the spreading of one
 // measurement (launched with the other measurement kernels) and the
 // transform of the accumulated grids at read-out (out at per-walker offsets
@@ -105,6 +106,13 @@ void launch_g4_assemble(int S, const double* A, const double* D, double sign_sum
 void launch_ndft_copy(const Config& cfg, int max_nc, const long long* d_base, double* d_out, cudaStream_t st);
 // Phase table of the measurement grid (ProblemDev::g0m) from the FP32 table g0f.
 void launch_meas_table(const ProblemDev& pd, int n_tau_meas, cudaStream_t st);
+// Every problem's staged table checked, committed (where finite) and its
+// measurement phase table rebuilt: three kernels.
+void launch_g0_update_all(const ProblemDev* d_P, int np, int ntm, const double* stage, const long long* off, int* bad,
+                          int* bad_any, int* changed, cudaStream_t st);
+// N rebuilt from scratch (in place) for the walkers whose problem has
+// changed[problem] != 0; returns the number of kernels launched.
+int launch_rebuild_changed(const Config& cfg, int max_cap, const int* changed, int* d_sgn, cudaStream_t st);
 void launch_g0_isolated(int nc, const double* d_eps, const double* d_kr, double mu_eff, double beta, int n_tau,
                         double* d_out, cudaStream_t st);
 

@@ -106,6 +106,7 @@ struct WalkerDev {
   int32_t n_ins;             // accepted insertions (appended rows)
   int32_t measure_pending;
   int32_t recompute_pending;
+  int32_t rebuild_pending;   // the bare propagator changed: N is rebuilt from scratch (Gauss-Jordan) before the next window
   int32_t first_window;      // this window starts a sweep
 
   // ---- counters ----

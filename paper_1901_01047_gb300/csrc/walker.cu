@@ -57,7 +57,11 @@ struct dca_walker {
   int64_t windows_launched = 0;
   // problem tables (device) for dca_walker_update_G0
   std::vector<ProblemDev> h_P;
-  std::vector<double*> g0_stage;    // per problem staging buffer [2][nc][n_tau+1]
+  std::vector<double*> g0_stage;    // per problem staging buffer [2][nc][n_tau+1] (slices of one allocation)
+  size_t g0_stage_doubles = 0;      // all problems' tables back to back
+  long long* d_stage_off = nullptr; // [n_problems] offsets of the slices
+  int* d_g0_bad = nullptr;          // [n_problems] per-problem rejection flags of dca_walker_update_G0_all
+  int* d_g0_changed = nullptr;      // [n_problems] the last update changed the problem's table
   // timing of kernel groups with CUDA events on the walker's stream
   uint32_t timing_mask = 0;
   std::vector<cudaEvent_t> ev_pool;
@@ -304,13 +308,25 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     h->max_nc = std::max(h->max_nc, pr.nc);
   }
   h->h_P = hp;
-  for (int i = 0; i < p.n_problems; ++i) {
-    double* st = (double*)h->dalloc(sizeof(double) * 2 * hp[i].nc * (hp[i].n_tau + 1));
-    if (!st) {
+  {
+    std::vector<long long> soff(p.n_problems);
+    for (int i = 0; i < p.n_problems; ++i) {
+      soff[i] = (long long)h->g0_stage_doubles;
+      h->g0_stage_doubles += (size_t)2 * hp[i].nc * (hp[i].n_tau + 1);
+    }
+    double* st = (double*)h->dalloc(sizeof(double) * h->g0_stage_doubles);
+    h->d_stage_off = (long long*)h->dalloc(sizeof(long long) * p.n_problems);
+    h->d_g0_bad = (int*)h->dalloc(sizeof(int) * p.n_problems);
+    h->d_g0_changed = (int*)h->dalloc(sizeof(int) * p.n_problems);
+    if (!st || !h->d_stage_off || !h->d_g0_bad || !h->d_g0_changed) {
       h->err = "device allocation of G0 staging buffer";
       return bail(DCA_ERR_OOM);
     }
-    h->g0_stage.push_back(st);
+    if (cudaMemcpy(h->d_stage_off, soff.data(), sizeof(long long) * p.n_problems, cudaMemcpyHostToDevice) != cudaSuccess) {
+      h->err = "upload of the staging offsets failed";
+      return bail(DCA_ERR_CUDA);
+    }
+    for (int i = 0; i < p.n_problems; ++i) h->g0_stage.push_back(st + soff[i]);
   }
   h->d_P = (ProblemDev*)h->dalloc(sizeof(ProblemDev) * p.n_problems);
   if (!h->d_P || cudaMemcpy(h->d_P, hp.data(), sizeof(ProblemDev) * p.n_problems, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -877,15 +893,33 @@ extern "C" DCA_API int dca_walker_update_G0(dca_walker* h, int32_t problem, cons
   const ProblemDev& pd = h->h_P[problem];
   const size_t tsz = (size_t)2 * pd.nc * (pd.n_tau + 1);
   CK(cudaMemcpyAsync(h->g0_stage[problem], G0, sizeof(double) * tsz, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(h->d_g0_changed, 0, sizeof(int) * h->h_P.size(), h->stream));
   // validated on the device (a table with a non-finite entry is not committed;
   // the next synchronisation reports it)
   dca::launch_negate(h->g0_stage[problem], const_cast<double*>(pd.g0), const_cast<float*>(pd.g0f), tsz,
-                     h->d_active + 7, h->stream);
+                     h->d_active + 7, h->d_g0_changed + problem, h->stream);
   h->total_launches += 1;
   if (pd.meas_q > 0) {
     dca::launch_meas_table(pd, h->ntm, h->stream);
     h->total_launches += 1;
   }
+  // N of the walkers on this problem is rebuilt for the new table (only if it changed)
+  h->total_launches += dca::launch_rebuild_changed(h->cfg, h->max_cap, h->d_g0_changed, h->d_sgn, h->stream);
+  CK(cudaGetLastError());
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_update_G0_all(dca_walker* h, const double* G0_all) {
+  if (!h || !G0_all) return DCA_ERR_ARG;
+  const int np = (int)h->h_P.size();
+  CK(cudaMemcpyAsync(h->g0_stage[0], G0_all, sizeof(double) * h->g0_stage_doubles, cudaMemcpyHostToDevice,
+                     h->stream));
+  CK(cudaMemsetAsync(h->d_g0_bad, 0, sizeof(int) * np, h->stream));
+  CK(cudaMemsetAsync(h->d_g0_changed, 0, sizeof(int) * np, h->stream));
+  dca::launch_g0_update_all(h->d_P, np, h->ntm, h->g0_stage[0], h->d_stage_off, h->d_g0_bad, h->d_active + 7,
+                            h->d_g0_changed, h->stream);
+  h->total_launches += 3;
+  h->total_launches += dca::launch_rebuild_changed(h->cfg, h->max_cap, h->d_g0_changed, h->d_sgn, h->stream);
   CK(cudaGetLastError());
   return DCA_OK;
 }

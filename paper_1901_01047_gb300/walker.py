@@ -25,7 +25,7 @@ EXPORTS = [
     "dca_walker_get_timing", "dca_walker_set_tuning", "dca_fresh_N", "dca_fresh_N_noalloc",
     "dca_walker_sync", "dca_walker_set_schedule", "dca_walker_set_limits", "dca_walker_save", "dca_walker_load",
     "dca_walker_measure_M", "dca_coarse_grain", "dca_sigma_update", "dca_g0_table_from_freq",
-    "dca_walker_set_recompute", "dca_walker_measure_G4", "dca_g4_assemble",
+    "dca_walker_set_recompute", "dca_walker_measure_G4", "dca_g4_assemble", "dca_walker_update_G0_all",
 ]
 UPDATE_KERNELS = {"auto": 0, "cuda_core": 1, "tcgen05": 2}
 # lockstep: every walker runs n more sweeps per sweep(n); pooled: the walkers
@@ -160,6 +160,7 @@ def load(path=LIB_PATH):
     L.dca_walker_set_forced_decisions.argtypes = [P, C.c_int32, P, C.c_int64]
     L.dca_walker_capacity.argtypes = [P, C.c_int32, C.POINTER(C.c_int32)]
     L.dca_walker_update_G0.argtypes = [P, C.c_int32, P]
+    L.dca_walker_update_G0_all.argtypes = [P, P]
     L.dca_walker_set_timing.argtypes = [P, C.c_uint32]
     L.dca_walker_set_tuning.argtypes = [P, C.c_int32, C.c_int32]
     L.dca_walker_get_timing.argtypes = [P, P, P, C.POINTER(C.c_int64), C.c_int32]
@@ -475,6 +476,16 @@ class Walkers:
         """Upload a new bare propagator (host array, paper convention) for a problem."""
         G0 = np.ascontiguousarray(G0, np.float64)
         self._check(self._L.dca_walker_update_G0(self._h, int(problem), _ptr(G0)))
+
+    def update_G0_all(self, G0_all):
+        """Upload every problem's bare propagator at once: a 1-D float64 array holding the
+        tables back to back in problem order (pinned memory makes the copy asynchronous;
+        keep it unchanged until the stream has passed the copy), or a list of per-problem
+        tables."""
+        if isinstance(G0_all, (list, tuple)):
+            G0_all = np.concatenate([np.ascontiguousarray(g, np.float64).reshape(-1) for g in G0_all])
+        G0_all = np.ascontiguousarray(G0_all, np.float64)
+        self._check(self._L.dca_walker_update_G0_all(self._h, _ptr(G0_all)))
 
     def set_tuning(self, k_sub, update_kernel="auto"):
         """Change the submatrix size and the N-update kernel between sweeps (same Markov chain)."""

@@ -103,3 +103,37 @@ def test_one_dca_iteration_around_the_walkers():
     gw.sweep(20)
     assert all(s["status"] == 0 for s in gw.stats())
     gw.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_update_G0_rebuilds_N_for_the_new_table(precision):
+    # a new bare propagator changes N^-1 = e^V - g0 (e^V - 1): the walkers of
+    # that problem get N rebuilt from scratch, with the configuration sign
+    # from the new determinants; an unchanged table leaves N alone
+    import torch
+    from paper_1901_01047_gb300 import walker
+    from tests.helpers import problem
+    nc, U, beta = 4, 4.0, 4.0
+    c, eps, kr, G0a = problem(nc, 1.0, 0.0, U, beta, 1.0, 1024)
+    _, _, _, G0b = problem(nc, 1.0, 0.0, U, beta, 1.4, 1024)
+    prob = dict(nc=nc, site_sub=c.site_sub, U=U, beta=beta, K=1.0, G0=G0a)
+    gw = walker.Walkers([prob], n_walkers=2, k_sub=16, recompute_every=8, warmup_sweeps=2, n_tau_meas=8, seed=3,
+                        precision=precision, stream=torch.cuda.current_stream().cuda_stream)
+    gw.sweep(25)
+    before = gw.state(0)
+    gw.update_G0(0, G0a)  # the same table: nothing to rebuild
+    same = gw.state(0)
+    assert np.array_equal(same["N"][0], before["N"][0])
+    gw.update_G0(0, G0b)
+    after = gw.state(0)
+    assert np.array_equal(after["site"], before["site"]) and np.array_equal(after["tau"], before["tau"])
+    ow = ctaux.OracleWalker(nc, c.site_sub, U, beta, 1.0, G0b, warmup_sweeps=0, n_tau_meas=8, seed=3)
+    ow.set_config(after["site"], after["tau"], after["s"])
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    for sp in range(2):
+        fresh, _ = ow.fresh_N(sp)
+        assert np.abs(after["N"][sp] - fresh).max() < tol * np.abs(fresh).max()
+    assert gw.stats()[0]["sign"] == ow.sign
+    gw.sweep(10)
+    assert all(s["status"] == 0 for s in gw.stats())
+    gw.close()

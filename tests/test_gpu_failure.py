@@ -157,3 +157,38 @@ def test_non_finite_table_given_to_update_G0_is_rejected_on_the_device():
     ow.sweep(20)
     assert np.array_equal(ow.log() & 1, log & 1)
     gw.close()
+
+
+def test_update_G0_all_takes_the_finite_tables_and_rejects_the_others():
+    # two problems; one call replaces both tables: problem 0 gets a new finite
+    # table (another chemical potential), problem 1 a table with a NaN, which
+    # is rejected while problem 0's is taken
+    nc, U, beta = 4, 4.0, 4.0
+    c, eps, kr, G0a = problem(nc, 1.0, 0.0, U, beta, 1.0, 1024)
+    _, _, _, G0b = problem(nc, 1.0, 0.0, U, 3.0, 0.8, 1024)
+    _, _, _, G0a_new = problem(nc, 1.0, 0.0, U, beta, 1.3, 1024)
+    probs = [dict(nc=nc, site_sub=c.site_sub, U=U, beta=beta, K=1.0, G0=G0a),
+             dict(nc=nc, site_sub=c.site_sub, U=U, beta=3.0, K=1.0, G0=G0b)]
+    gw = _walkers(problems=probs, n_walkers=2, k_sub=16, recompute_every=8, warmup_sweeps=2, n_tau_meas=8, seed=5,
+                  log_capacity=1 << 20)
+    bad = G0b.copy()
+    bad[0, 1, 7] = np.inf
+    gw.update_G0_all([G0a_new, bad])
+    with pytest.raises(_err()) as e:
+        gw.sync()
+    assert e.value.code == -1
+    gw.sweep(20)
+    for wi, (b, g0) in enumerate(((beta, G0a_new), (3.0, G0b))):
+        log = gw.decision_log(wi)
+        ow = ctaux.OracleWalker(nc, c.site_sub, U, b, 1.0, g0, warmup_sweeps=2, n_tau_meas=8, seed=5, walker_id=wi)
+        ow.enable_log(1 << 20)
+        ow.set_hints(log)
+        ow.sweep(20)
+        assert np.array_equal(ow.log() & 1, log & 1), wi
+        Go, sso, _ = ow.G()
+        Gg, ssg, _ = gw.measure_G()
+        assert np.abs(Gg[wi] - Go).max() < 1e-10 * np.abs(Go).max()
+    # a finite pair of tables: no error
+    gw.update_G0_all(np.concatenate([G0a.reshape(-1), G0b.reshape(-1)]))
+    gw.sync()
+    gw.close()
