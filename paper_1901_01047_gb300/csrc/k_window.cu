@@ -483,6 +483,14 @@ __device__ __forceinline__ float2 m_shfl_xor(float2 a, int o) {
   return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
 }
 
+// Lanes per row for the l-term row sums of the Metropolis kernel (256
+// threads, both spins): the largest power of two G <= 32 with 2 l G <= 256.
+__device__ __forceinline__ int row_lanes(int l) {
+  int G = 1;
+  while (G < 32 && 4 * l * G <= 256) G <<= 1;
+  return G;
+}
+
 constexpr int METRO_LIVE = 2048;  // live vertices whose rows and spins are staged in shared memory
 
 // One block per walker, both spins.  Per proposal: (1) its target and a_t,
@@ -652,16 +660,22 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
       }
     }
     __syncthreads();
-    // 3. t = B^-1 b_col
-    if (tid < 2 * KS_MAX) {
-      const int sp = tid / KS_MAX, i = tid - sp * KS_MAX;
-      if (i < l) {
+    // 3. t = B^-1 b_col.  Each of the 2 l rows (both spins) is summed by a
+    // group of G lanes (the largest power of two with 2 l G <= 256, at most a
+    // warp), so the dependent chain of a row is l / G terms long.
+    const int G = row_lanes(l);
+    {
+      const int r = tid / G, g = tid - r * G;
+      const bool ok = r < 2 * l;
+      const int sp = ok ? r / l : 0, i = ok ? r - sp * l : 0;
+      M acc;
+      m_zero(acc);
+      if (ok) {
         const M* B = Binv[sp] + (size_t)i * bst;
-        M acc;
-        m_zero(acc);
-        for (int p = 0; p < l; ++p) m_fma(acc, B[p], s_bcol[sp][p]);
-        s_t[sp][i] = m_fin(acc);
+        for (int p = g; p < l; p += G) m_fma(acc, B[p], s_bcol[sp][p]);
       }
+      for (int o = G >> 1; o > 0; o >>= 1) m_acc(acc, m_shfl_xor(acc, o));
+      if (ok && g == 0) s_t[sp][i] = m_fin(acc);
     }
     __syncthreads();
     // 4. Schur complements d = B_tt - b_row . t, and 5. the decision (warp 0);
@@ -729,15 +743,17 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
     }
     __syncthreads();
     if (!s_accept) continue;
-    // 6. s = b_row B^-1 / d
-    if (tid < 2 * KS_MAX) {
-      const int sp = tid / KS_MAX, jj = tid - sp * KS_MAX;
-      if (jj < l) {
-        M acc;
-        m_zero(acc);
-        for (int i = 0; i < l; ++i) m_fma(acc, s_brow[sp][i], Binv[sp][(size_t)i * bst + jj]);
-        s_s[sp][jj] = m_mul(m_fin(acc), s_rd[sp]);
-      }
+    // 6. s = b_row B^-1 / d (column sums, G lanes per column as in step 3)
+    {
+      const int r = tid / G, g = tid - r * G;
+      const bool ok = r < 2 * l;
+      const int sp = ok ? r / l : 0, jj = ok ? r - sp * l : 0;
+      M acc;
+      m_zero(acc);
+      if (ok)
+        for (int i = g; i < l; i += G) m_fma(acc, s_brow[sp][i], Binv[sp][(size_t)i * bst + jj]);
+      for (int o = G >> 1; o > 0; o >>= 1) m_acc(acc, m_shfl_xor(acc, o));
+      if (ok && g == 0) s_s[sp][jj] = m_mul(m_fin(acc), s_rd[sp]);
     }
     __syncthreads();
     // 7. bordered inverse: [[B^-1 + t s, -t / d], [-s, 1 / d]] (s already / d)
