@@ -310,14 +310,25 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
 // the per-column factors e^{V} / (e^{V} - 1) a_p are formed once per item in
 // FP64 and split), in FP64 for the rows of accepted insertions (X is FP64).
 // Items per walker-spin: ceil(rows / 32) row blocks (rows = n + n_ins), then
-// ceil(n / 32) column blocks.
+// ceil(n / 32) column blocks.  Dynamic shared memory: the L rows of a row
+// block [32][ld], ld = 64 with k_s <= 64 (then also B^-1, [64][64]) or 128;
+// a column block reuses it as the transposition tile [128][33].
+constexpr int FACT_RB = 32, FACT_BS = 64;
+
+__host__ __device__ constexpr size_t fact_smem(bool bs) {
+  return bs ? sizeof(float2) * (FACT_RB * FACT_BS + FACT_BS * FACT_BS) : sizeof(float2) * FACT_RB * KS_MAX;
+}
+
 __global__ void __launch_bounds__(256) k_upd_factors(Config cfg) {
-  constexpr int RB = 32;
-  __shared__ __align__(16) unsigned char s_raw[RB * KS_MAX * sizeof(float2)];
+  constexpr int RB = FACT_RB;
+  static_assert(KS_MAX * 33 * sizeof(float) <= fact_smem(false) && fact_smem(false) <= fact_smem(true), "tiles");
   __shared__ float2 s_c1[KS_MAX];
-  float2(*s_L)[KS_MAX] = reinterpret_cast<float2(*)[KS_MAX]>(s_raw);  // [RB][KS_MAX]
-  float(*s_t)[33] = reinterpret_cast<float(*)[33]>(s_raw);             // [KS_MAX][33]
-  static_assert(KS_MAX * 33 * sizeof(float) <= sizeof(s_raw), "transpose tile");
+  extern __shared__ __align__(16) float2 s_dyn[];
+  const bool bs = cfg.ks <= FACT_BS;
+  const int lds = bs ? FACT_BS : KS_MAX;  // row stride of the L rows
+  float2* s_Lb = s_dyn;                   // [RB][lds]
+  float2* s_binv = s_dyn + RB * FACT_BS;  // [FACT_BS][FACT_BS] (bs only)
+  float(*s_t)[33] = reinterpret_cast<float(*)[33]>(s_dyn);  // [KS_MAX][33]
   for_each_item(
       2 * cfg.n_walkers,
       [&](int s) -> long long {
@@ -346,6 +357,12 @@ __global__ void __launch_bounds__(256) k_upd_factors(Config cfg) {
               s_c1[p] = df_split(a);
             }
           }
+          const float2* Bi = reinterpret_cast<const float2*>(w.Binv[sp]);
+          if (bs)
+            for (int e = threadIdx.x; e < l * lpad; e += blockDim.x) {
+              const int p = e / lpad, q = e - p * lpad;
+              s_binv[p * FACT_BS + q] = q < l ? Bi[(size_t)p * KS_MAX + q] : make_float2(0.f, 0.f);
+            }
           __syncthreads();
           for (int e = threadIdx.x; e < RB * l; e += blockDim.x) {
             const int r = e / l, p = e - r * l;
@@ -378,13 +395,12 @@ __global__ void __launch_bounds__(256) k_upd_factors(Config cfg) {
                 }
               }
             }
-            s_L[r][p] = v;
+            s_Lb[r * lds + p] = v;
           }
           __syncthreads();
           // L' = L B^-1: four consecutive outputs of a row per thread (four
           // independent double-float chains sharing the loads of L)
           const int lq = lpad / 4;
-          const float2* Bi = reinterpret_cast<const float2*>(w.Binv[sp]);
           for (int e = threadIdx.x; e < RB * lq; e += blockDim.x) {
             const int r = e / lq, q = (e - r * lq) * 4;
             const int t = t0 + r;
@@ -393,8 +409,8 @@ __global__ void __launch_bounds__(256) k_upd_factors(Config cfg) {
             float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
             if (q < l) {
               for (int p = 0; p < l; ++p) {
-                const float2 a = s_L[r][p];
-                const float2* brow = Bi + (size_t)p * KS_MAX + q;
+                const float2 a = s_Lb[r * lds + p];
+                const float2* brow = bs ? s_binv + p * FACT_BS + q : Bi + (size_t)p * KS_MAX + q;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                   const float2 b = brow[u];  // columns >= l of B^-1 are never read back
@@ -446,7 +462,8 @@ __global__ void __launch_bounds__(256) k_upd_factors(Config cfg) {
 
 void launch_upd_factors(const Config& cfg, int max_cap, cudaStream_t st) {
   const long long items = 2LL * cfg.n_walkers * (blocks_of(max_cap, 32) + blocks_of(max_cap, 32));
-  k_upd_factors<<<persist_grid((const void*)k_upd_factors, items, 256), 256, 0, st>>>(cfg);
+  const size_t smem = fact_smem(cfg.ks <= FACT_BS);
+  k_upd_factors<<<persist_grid((const void*)k_upd_factors, items, 256, smem), 256, smem, st>>>(cfg);
 }
 
 // ---------------------------------------------------------------------------
@@ -458,7 +475,8 @@ static cudaError_t tc_setup_one() {
 }
 
 cudaError_t setup_update_tc() {
-  cudaError_t e = tc_setup_one<64, 32>();
+  cudaError_t e = cudaFuncSetAttribute(k_upd_factors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fact_smem(true));
+  if (e == cudaSuccess) e = tc_setup_one<64, 32>();
   if (e == cudaSuccess) e = tc_setup_one<64, 64>();
   if (e == cudaSuccess) e = tc_setup_one<32, 128>();
   return e;
