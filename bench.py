@@ -547,8 +547,11 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic",
             "config": {**config_of(wl, world), "k_sub": gw.k_sub,
                        **({"autotune": {"k_sub": tuned["k_sub"], "update_kernel": tuned["update_kernel"],
+                                        "update_tile": tuned["update_tile"],
                                         "updates_per_s": {"%d/%s" % (r["k_sub"], r["update_kernel"]):
-                                                          round(r["updates_per_s"]) for r in tuned["table"]}}}
+                                                          round(r["updates_per_s"]) for r in tuned["table"]},
+                                        "tile_updates_per_s": {str(r["update_tile"]): round(r["updates_per_s"])
+                                                               for r in tuned["tiles"]}}}
                           if tuned else {})},
             "final_order": st1[0]["order"],
             "n_update_tflops": flops_all / seconds / 1e12,

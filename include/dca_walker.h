@@ -503,6 +503,14 @@ DCA_API int dca_walker_update_G0_all(dca_walker* w, const double* G0_all);
  * autotuner.  Synchronises the stream. */
 DCA_API int dca_walker_set_tuning(dca_walker* w, int32_t k_sub, int32_t update_kernel);
 
+/* Column tile of the tensor-core N update (DCA_UPD_TCGEN05): 32 or 64
+ * columns of N per tile, 0 for the default (64).  With k_sub > 64 the tile is
+ * 32 whatever is asked (the operands of the larger K extent leave room for no
+ * more).  A performance parameter like k_sub (the results differ only by the
+ * order of FP32 additions); used by the autotuner.  DCA_ERR_ARG for another
+ * value.  Synchronises the stream. */
+DCA_API int dca_walker_set_update_tile(dca_walker* w, int32_t tile_n);
+
 /* Change the recompute schedule between sweeps (the fields of the same names
  * in dca_walker_params): recompute_every (windows, 0 = off), recompute_sweeps
  * (batched schedule, 0 = off) and recompute_at_measure (0 or 1).  N is a

@@ -1,4 +1,4 @@
-"""Autotuner of the submatrix size k_s and the N-update kernel.
+"""Autotuner of the submatrix size k_s, the N-update kernel and its tile.
 
 The submatrix method reaches exactly the Markov chain of single-spin updates
 for every k_s (DCA++ paper, Sec. 2.3, "Submatrix updates"), and the two
@@ -7,12 +7,15 @@ performance parameters.  The tuner times every candidate on the caller's own
 walkers, after their warm-up (the orders then have their working size),
 with CUDA events on the walker's stream around whole sweeps, and leaves the
 walkers on the fastest candidate.  The chains simply continue: each trial
-sweep is an ordinary sweep of the run.
+sweep is an ordinary sweep of the run.  After k_s and the kernel, the column
+tile of the tensor-core N update (32 or 64 columns of N per tile, for k_s <=
+64) is timed the same way.
 """
 import itertools
 
 KS_CANDIDATES = (16, 32, 64, 128)
 KERNEL_CANDIDATES = ("tcgen05", "cuda_core")
+TILE_CANDIDATES = (64, 32)
 
 
 def _time_sweeps(gw, sweeps, stream, tries=3):
@@ -54,4 +57,15 @@ def tune(gw, precision, ks_candidates=KS_CANDIDATES, kernels=KERNEL_CANDIDATES, 
         table.append({"k_sub": ks, "update_kernel": kern, "updates_per_s": rate, "ms": ms})
     best = max(table, key=lambda r: r["updates_per_s"])
     gw.set_tuning(best["k_sub"], best["update_kernel"])
-    return {"k_sub": best["k_sub"], "update_kernel": best["update_kernel"], "table": table}
+    tile, tiles = 64, []
+    if best["update_kernel"] == "tcgen05" and best["k_sub"] <= 64:
+        for bn in TILE_CANDIDATES:
+            gw.set_update_tile(bn)
+            if settle:
+                gw.sweep(settle)
+            rate, ms = _time_sweeps(gw, sweeps, stream)
+            tiles.append({"update_tile": bn, "updates_per_s": rate, "ms": ms})
+        tile = max(tiles, key=lambda r: r["updates_per_s"])["update_tile"]
+        gw.set_update_tile(tile)
+    return {"k_sub": best["k_sub"], "update_kernel": best["update_kernel"], "update_tile": tile, "table": table,
+            "tiles": tiles}

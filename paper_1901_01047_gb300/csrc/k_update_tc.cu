@@ -477,22 +477,31 @@ static cudaError_t tc_setup_one() {
 cudaError_t setup_update_tc() {
   cudaError_t e = cudaFuncSetAttribute(k_upd_factors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fact_smem(true));
   if (e == cudaSuccess) e = tc_setup_one<64, 32>();
+  if (e == cudaSuccess) e = tc_setup_one<32, 32>();
+  if (e == cudaSuccess) e = tc_setup_one<32, 64>();
   if (e == cudaSuccess) e = tc_setup_one<64, 64>();
   if (e == cudaSuccess) e = tc_setup_one<32, 128>();
   return e;
 }
 
-int tc_tile_n(int ks) { return ks <= 64 ? 64 : 32; }
+int tc_tile_n(int ks, int bn) {
+  if (ks > 64) return 32;           // the K extent of 128 leaves room for BN = 32 only
+  return bn == 32 ? 32 : 64;        // default 64
+}
 
 
 void launch_upd_tc(const Config& cfg, cudaStream_t st) {
   const int grid = device_sm_count();
-  if (cfg.ks <= 32)
-    k_upd_tc<64, 32><<<grid, 192, TcLayout<64, 32>::SMEM, st>>>(cfg);
-  else if (cfg.ks <= 64)
-    k_upd_tc<64, 64><<<grid, 192, TcLayout<64, 64>::SMEM, st>>>(cfg);
-  else
+  const bool wide = tc_tile_n(cfg.ks, cfg.upd_bn) == 64;
+  if (cfg.ks <= 32) {
+    if (wide) k_upd_tc<64, 32><<<grid, 192, TcLayout<64, 32>::SMEM, st>>>(cfg);
+    else k_upd_tc<32, 32><<<grid, 192, TcLayout<32, 32>::SMEM, st>>>(cfg);
+  } else if (cfg.ks <= 64) {
+    if (wide) k_upd_tc<64, 64><<<grid, 192, TcLayout<64, 64>::SMEM, st>>>(cfg);
+    else k_upd_tc<32, 64><<<grid, 192, TcLayout<32, 64>::SMEM, st>>>(cfg);
+  } else {
     k_upd_tc<32, 128><<<grid, 192, TcLayout<32, 128>::SMEM, st>>>(cfg);
+  }
 }
 
 // Tensor maps of walker wi, spin sp: A operand, B operand, N of parity 0 and
@@ -528,9 +537,9 @@ static bool encode_2d(TmapDev* out, void* base, uint64_t cols, uint64_t rows, ui
 
 int ext_tile_c(int ks) { return ks <= 64 ? 64 : 128; }
 
-bool encode_update_maps(const WalkerDev& w, int ks, TmapDev* out) {
+bool encode_update_maps(const WalkerDev& w, int ks, int upd_bn, TmapDev* out) {
   const uint64_t C = (uint64_t)w.cap;
-  const uint32_t bn = (uint32_t)tc_tile_n(ks);
+  const uint32_t bn = (uint32_t)tc_tile_n(ks, upd_bn);
   for (int sp = 0; sp < 2; ++sp) {
     TmapDev* m = out + TMAPS_PER_SPIN * sp;
     if (!encode_2d(m + 0, w.Aop[sp], TC_KS, 2 * C, TC_KS * 4, TC_BM)) return false;

@@ -77,9 +77,10 @@ int launch_ext_mixed(const Config& cfg, int max_cap, cudaStream_t st);
 // a submatrix size, tensor maps of one walker ([spin][A, B, N0, N1]), the
 // operand split and the update itself.
 cudaError_t setup_update_tc();
-int tc_tile_n(int ks);
+// Column tile of the tcgen05 N update for k_s and the requested tile (0 = default 64).
+int tc_tile_n(int ks, int bn);
 int ext_tile_c(int ks);  // candidate tile (N extent) of the tensor-core extension
-bool encode_update_maps(const WalkerDev& w, int ks, TmapDev* out);
+bool encode_update_maps(const WalkerDev& w, int ks, int upd_bn, TmapDev* out);
 cudaError_t setup_ext_tc();
 void launch_ext_g_tc(const Config& cfg, cudaStream_t st);
 void launch_ext_x_tc(const Config& cfg, cudaStream_t st);

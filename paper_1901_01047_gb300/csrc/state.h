@@ -224,6 +224,7 @@ struct Config {
   const ProblemDev* P;       // [n_problems]
   int32_t* active_count;     // [1]
   int32_t upd_kernel;        // UPD_CUDA_CORE or UPD_TCGEN05 (mixed precision)
+  int32_t upd_bn;            // column tile of the tcgen05 N update: 32 or 64 (64 only for k_s <= 64)
   const TmapDev* tmaps;      // [n_walkers][2 spins][TMAPS_PER_SPIN]
   int32_t ext_tc;            // mixed path: candidate products G_ext and X on tcgen05
   int32_t* gj_next;          // [1] next matrix of the Gauss-Jordan work queue (reset by k_build_A)

@@ -161,7 +161,7 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // Bound of the mbarrier waits of the tensor-core kernels: about two seconds of SM clocks.
 constexpr long long kDefaultWaitCycles = 4000000000LL;
 
-static int upload_update_maps(dca_walker* h, int ks);
+static int upload_update_maps(dca_walker* h, int ks, int bn);
 
 extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cuda_stream, dca_walker** out) {
   if (!out) return fail(nullptr, DCA_ERR_ARG, "out is NULL");
@@ -454,7 +454,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   }
   if (alloc_tc) {
     h->d_tmaps = (dca::TmapDev*)h->dalloc(sizeof(dca::TmapDev) * (size_t)h->W * 2 * dca::TMAPS_PER_SPIN);
-    if (!h->d_tmaps || upload_update_maps(h, p.k_sub) != DCA_OK) {
+    if (!h->d_tmaps || upload_update_maps(h, p.k_sub, h->cfg.upd_bn) != DCA_OK) {
       h->err = "TMA tensor maps of the tensor-core update";
       return bail(DCA_ERR_CUDA);
     }
@@ -532,10 +532,10 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
 
 // Encode and upload the TMA tensor maps of every walker (the B-operand box
 // depends on the submatrix size).
-static int upload_update_maps(dca_walker* h, int ks) {
+static int upload_update_maps(dca_walker* h, int ks, int bn) {
   std::vector<dca::TmapDev> maps((size_t)h->W * 2 * dca::TMAPS_PER_SPIN);
   for (int wi = 0; wi < h->W; ++wi)
-    if (!dca::encode_update_maps(h->h_W[wi], ks, maps.data() + (size_t)wi * 2 * dca::TMAPS_PER_SPIN))
+    if (!dca::encode_update_maps(h->h_W[wi], ks, bn, maps.data() + (size_t)wi * 2 * dca::TMAPS_PER_SPIN))
       return DCA_ERR_CUDA;
   if (cudaMemcpy(h->d_tmaps, maps.data(), sizeof(dca::TmapDev) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return DCA_ERR_CUDA;
@@ -849,14 +849,32 @@ extern "C" DCA_API int dca_walker_set_tuning(dca_walker* h, int32_t k_sub, int32
   CK(cudaStreamSynchronize(h->stream));
   const bool mixed = h->cfg.prec == dca::PREC_MIXED;
   const bool tc = mixed && update_kernel != DCA_UPD_CUDA_CORE;
-  if (mixed && (dca::tc_tile_n(k_sub) != dca::tc_tile_n(h->ks) || dca::ext_tile_c(k_sub) != dca::ext_tile_c(h->ks))) {
-    const int rc = upload_update_maps(h, k_sub);
+  if (mixed && (dca::tc_tile_n(k_sub, h->cfg.upd_bn) != dca::tc_tile_n(h->ks, h->cfg.upd_bn) ||
+                dca::ext_tile_c(k_sub) != dca::ext_tile_c(h->ks))) {
+    const int rc = upload_update_maps(h, k_sub, h->cfg.upd_bn);
     if (rc != DCA_OK) return fail(h, rc, "TMA tensor maps of the tensor-core update");
   }
   h->ks = k_sub;
   h->cfg.ks = k_sub;
   h->cfg.upd_kernel = tc ? dca::UPD_TCGEN05 : dca::UPD_CUDA_CORE;
   h->cfg.ext_tc = tc ? 1 : 0;
+  drop_loop_graph(h);
+  return DCA_OK;
+}
+
+extern "C" DCA_API int dca_walker_set_update_tile(dca_walker* h, int32_t tile_n) {
+  if (!h) return DCA_ERR_ARG;
+  if (tile_n != 0 && tile_n != 32 && tile_n != 64) return fail(h, DCA_ERR_ARG, "tile_n must be 0, 32 or 64");
+  if (h->cfg.prec != dca::PREC_MIXED) {
+    h->cfg.upd_bn = tile_n;
+    return DCA_OK;
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  if (dca::tc_tile_n(h->ks, tile_n) != dca::tc_tile_n(h->ks, h->cfg.upd_bn)) {
+    const int rc = upload_update_maps(h, h->ks, tile_n);
+    if (rc != DCA_OK) return fail(h, rc, "TMA tensor maps of the tensor-core update");
+  }
+  h->cfg.upd_bn = tile_n;
   drop_loop_graph(h);
   return DCA_OK;
 }

@@ -26,6 +26,7 @@ EXPORTS = [
     "dca_walker_sync", "dca_walker_set_schedule", "dca_walker_set_limits", "dca_walker_save", "dca_walker_load",
     "dca_walker_measure_M", "dca_coarse_grain", "dca_sigma_update", "dca_g0_table_from_freq",
     "dca_walker_set_recompute", "dca_walker_measure_G4", "dca_g4_assemble", "dca_walker_update_G0_all",
+    "dca_walker_set_update_tile",
 ]
 UPDATE_KERNELS = {"auto": 0, "cuda_core": 1, "tcgen05": 2}
 # lockstep: every walker runs n more sweeps per sweep(n); pooled: the walkers
@@ -161,6 +162,7 @@ def load(path=LIB_PATH):
     L.dca_walker_capacity.argtypes = [P, C.c_int32, C.POINTER(C.c_int32)]
     L.dca_walker_update_G0.argtypes = [P, C.c_int32, P]
     L.dca_walker_update_G0_all.argtypes = [P, P]
+    L.dca_walker_set_update_tile.argtypes = [P, C.c_int32]
     L.dca_walker_set_timing.argtypes = [P, C.c_uint32]
     L.dca_walker_set_tuning.argtypes = [P, C.c_int32, C.c_int32]
     L.dca_walker_get_timing.argtypes = [P, P, P, C.POINTER(C.c_int64), C.c_int32]
@@ -486,6 +488,11 @@ class Walkers:
             G0_all = np.concatenate([np.ascontiguousarray(g, np.float64).reshape(-1) for g in G0_all])
         G0_all = np.ascontiguousarray(G0_all, np.float64)
         self._check(self._L.dca_walker_update_G0_all(self._h, _ptr(G0_all)))
+
+    def set_update_tile(self, tile_n):
+        """Column tile of the tensor-core N update: 32, 64 or 0 (default 64; 32 when k_s > 64)."""
+        self._check(self._L.dca_walker_set_update_tile(self._h, int(tile_n)))
+        self.update_tile = int(tile_n)
 
     def set_tuning(self, k_sub, update_kernel="auto"):
         """Change the submatrix size and the N-update kernel between sweeps (same Markov chain)."""

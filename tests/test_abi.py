@@ -156,6 +156,7 @@ def test_null_handles_rejected(lib):
     assert lib.dca_walker_stats(None, None) == -1
     assert lib.dca_walker_measure_G(None, None, None, None) == -1
     assert lib.dca_walker_measure_G4(None, None, None, None, None) == -1
+    assert lib.dca_walker_set_update_tile(None, 32) == -1
     assert lib.dca_g0_isolated_cluster(0, None, None, 0.0, 0.0, 1.0, 4, None) == -1
 
 

@@ -24,7 +24,7 @@ def _walkers(**kw):
 
 
 def replay(nc, tp, U, beta, mu, k_sub, sweeps, R, seed=0, ntm=32, n_tau=4096, update_kernel="auto",
-           return_state=False, recompute_method="auto", recompute_at_measure=False, precision="mixed"):
+           return_state=False, recompute_method="auto", recompute_at_measure=False, precision="mixed", update_tile=0):
     c, eps, kr, G0 = problem(nc, 1.0, tp, U, beta, mu, n_tau)
     ow = ctaux.OracleWalker(nc, c.site_sub, U, beta, 1.0, G0, warmup_sweeps=10, n_tau_meas=ntm, seed=seed)
     ow.enable_log(1 << 24)
@@ -34,6 +34,8 @@ def replay(nc, tp, U, beta, mu, k_sub, sweeps, R, seed=0, ntm=32, n_tau=4096, up
                   recompute_every=R, warmup_sweeps=10, n_tau_meas=ntm, seed=seed, precision=precision,
                   log_capacity=1 << 24, update_kernel=update_kernel, recompute_method=recompute_method,
                   recompute_at_measure=recompute_at_measure)
+    if update_tile:
+        gw.set_update_tile(update_tile)
     gw.set_forced_decisions(0, log)
     gw.sweep(sweeps)
     gs, os_ = gw.state(0), ow.state()
@@ -98,15 +100,16 @@ def test_mixed_free_run_follows_the_oracle_for_a_long_stretch():
     assert first > 2000, first
 
 
-@pytest.mark.parametrize("k_sub", [16, 64, 128])
-def test_tensor_core_update_matches_cuda_core_update(k_sub):
+@pytest.mark.parametrize("k_sub,tile", [(16, 64), (16, 32), (64, 64), (64, 32), (128, 0)])
+def test_tensor_core_update_matches_cuda_core_update(k_sub, tile):
     # Same forced trajectory, no recompute: the 3xTF32 tcgen05 update and the
     # FP32 CUDA-core update differ only by rounding.  k_sub covers the three
-    # K extents of the tensor-core kernel (32, 64, 128) and n spans several
-    # 128-row blocks with a ragged tail.
+    # K extents of the tensor-core kernel (32, 64, 128), tile both column
+    # tiles of N, and n spans several 128-row blocks with a ragged tail.
     args = (16, -0.15, 6.0, 6.0, 2.85, k_sub, 30, 0)
     eN_c, eG_c, st_c, gs_c = replay(*args, ntm=16, n_tau=2048, update_kernel="cuda_core", return_state=True)
-    eN_t, eG_t, st_t, gs_t = replay(*args, ntm=16, n_tau=2048, update_kernel="tcgen05", return_state=True)
+    eN_t, eG_t, st_t, gs_t = replay(*args, ntm=16, n_tau=2048, update_kernel="tcgen05", return_state=True,
+                                    update_tile=tile)
     assert st_t["status"] == 0 and st_c["status"] == 0
     assert gs_t["N"][0].shape[0] > 128
     # Both drift from the FP64 oracle (no recompute).  3xTF32 keeps about 22
@@ -168,6 +171,7 @@ def test_autotuner_selects_a_candidate_and_leaves_walkers_on_it():
     res = autotune.tune(gw, "mixed", sweeps=1, settle=1)
     assert len(res["table"]) == 8
     assert res["k_sub"] in autotune.KS_CANDIDATES and res["update_kernel"] in autotune.KERNEL_CANDIDATES
+    assert res["update_tile"] in autotune.TILE_CANDIDATES
     assert all(r["updates_per_s"] > 0 for r in res["table"])
     assert gw.k_sub == res["k_sub"]
     gw.sweep(2)
