@@ -5,8 +5,11 @@
  * Sec. 2.3) on one GPU: submatrix (delayed) updates of the per-spin N
  * matrices (Sec. 2.3, "Submatrix updates"), sign tracking, periodic
  * recomputation of N, and accumulation of the measured Green's function G(tau)
- * (Sec. 2.3, the equation for <G> in terms of M).  Every step of a sweep runs
- * in CUDA kernels built for sm_103a; there is no CPU fallback.
+ * (Sec. 2.3, the equation for <G> in terms of M), of M(i w_n) by the delayed
+ * NFFT or a dense transform (Sec. 2.3, Eq. nfft) and of the two-particle
+ * Green's function (Sec. 2.5); and the steps of the outer DCA loop (Sec. 2.1)
+ * that turn the measured M into the next bare propagator.  Every step runs in
+ * CUDA kernels built for sm_103a; there is no CPU fallback.
  *
  * Problem statement (Sec. 2.3, Eq. generalized_hubbard and the decoupling
  * equations): a single-band Hubbard cluster of Nc sites with on-site U,
@@ -72,7 +75,10 @@ extern "C" {
  *           (DCA_GAMMA_DOUBLE_FLOAT); the recompute from an FP64 A = N^-1 with a
  *           double-float residual.  The FP32 storage of N bounds the accuracy: the
  *           measured errors of N and G against the FP64 walker on the same trajectory
- *           are 1e-6..1e-4 relative, growing with the conditioning of N^-1.
+ *           are 1e-6..1e-4 relative, growing with the conditioning of N^-1 and with
+ *           the updates since the last recompute; with N recomputed before every
+ *           measurement (recompute_at_measure) the accumulated G is within about
+ *           3e-7.
  *   TF32:   as MIXED with one TF32 product per K step instead of three (the
  *           tensor-core kernels only); about 11 bits per product. */
 #define DCA_PREC_FP64 0
