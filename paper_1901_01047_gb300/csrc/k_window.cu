@@ -449,6 +449,15 @@ __device__ __forceinline__ double g_ext_at(const ExtView<T>& v, int x, int y, do
   return (nxy * ev - (x == y ? 1.0 : 0.0)) * rv;
 }
 
+// Address of the stored entry g_ext_at reads for (x, y).
+template <typename T>
+__device__ __forceinline__ const void* g_ext_ptr(const ExtView<T>& v, int x, int y) {
+  if (y >= v.n) return v.Gc + (size_t)(y - v.n) * v.ld + x;
+  return (x < v.n) ? (const void*)(v.N + (size_t)x * v.ld + y) : (const void*)(v.X + (size_t)(x - v.n) * v.ld + y);
+}
+
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 // Arithmetic M of the bordered growth of B^-1 and of the Schur complements
 // (the determinant ratios): FP64 (double), or double-float pairs (hi, lo) of
 // FP32 (float2), about 44 significant bits at the FP32 issue rate.  The
@@ -531,6 +540,7 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
   __shared__ int s_removed[KS_MAX];   // live ranks removed in this window, ascending
   __shared__ int s_flipped[KS_MAX];   // live ranks whose auxiliary spin was flipped in this window
   __shared__ double s_ev[2][2], s_rv[2][2];  // e^{V} and 1 / (e^{V} - 1): [spin][s > 0]
+  __shared__ double s_anew_tab[3][2][2];      // a_t of an insertion / removal / flip: [kind][spin][s > 0]
   __shared__ double s_anew[2], s_Btt[2];
   __shared__ int s_target, s_tup, s_kind, s_stop, s_accept, s_l, s_nrem, s_nins, s_kcur, s_eval, s_rank, s_nflip;
   __shared__ double s_sign;
@@ -545,6 +555,10 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
   if (tid < 4) {
     const int sp = tid >> 1, up = tid & 1;
     s_ev[sp][up] = pb.expV[sp][up];
+    const double e = pb.expV[sp][up ? 0 : 1];  // e^{V(-s)}: removal e^{-V} - 1, flip e^{-2V} - 1
+    s_anew_tab[0][sp][up] = pb.expV[sp][up] - 1.0;
+    s_anew_tab[1][sp][up] = e - 1.0;
+    s_anew_tab[2][sp][up] = e * e - 1.0;
     s_rv[sp][up] = pb.rexpVm1[sp][up];
   }
   if (tid == 0) {
@@ -576,19 +590,23 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
     int kind = 0, target = -1, rank = -1, up = 0;
     if (pr.type == 0) {
       target = n + pr.slot;
-      for (int sp = 0; sp < 2; ++sp) s_anew[sp] = s_ev[sp][pr.s > 0 ? 1 : 0] - 1.0;
+      for (int sp = 0; sp < 2; ++sp) s_anew[sp] = s_anew_tab[0][sp][pr.s > 0 ? 1 : 0];
     } else if (kcur == 0) {
       kind = 2;
     } else {
       const int idx = (int)scaled_index(pr.word, (uint32_t)kcur);
       bool dup = idx >= n_live - s_nrem;  // a spin inserted in this window
       if (!dup) {
-        // idx-th live vertex not yet removed in this window
-        rank = idx;
-        for (int r = 0; r < s_nrem; ++r) {
-          if (s_removed[r] <= rank) ++rank;
-          else break;
+        // idx-th live vertex not yet removed in this window: rank = idx + r*,
+        // r* the first r with s_removed[r] - r > idx (s_removed ascending and
+        // distinct, so s_removed[r] - r is non-decreasing): binary search
+        int lo = 0, hi = s_nrem;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (s_removed[mid] - mid <= idx) lo = mid + 1;
+          else hi = mid;
         }
+        rank = idx + lo;
         for (int r = 0; r < s_nflip; ++r) dup |= s_flipped[r] == rank;
       }
       if (dup) {
@@ -604,10 +622,7 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
           target = w.live_idx[rank];
           up = ev[0].vs[target] > 0 ? 1 : 0;
         }
-        for (int sp = 0; sp < 2; ++sp) {
-          const double e = s_ev[sp][up ? 0 : 1];  // e^{V(-s)}: removal e^{-V} - 1, flip e^{-2V} - 1
-          s_anew[sp] = kind == 3 ? e * e - 1.0 : e - 1.0;
-        }
+        for (int sp = 0; sp < 2; ++sp) s_anew[sp] = s_anew_tab[kind == 3 ? 2 : 1][sp][up];
       }
     }
     s_kind = kind;
@@ -693,12 +708,31 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
         m_acc(a0, m_shfl_xor(a0, o));
         m_acc(a1, m_shfl_xor(a1, o));
       }
+      // the Schur complements of lane 0; then the three quotients the decision
+      // needs (the ratio's prefactor, 1/d0 and 1/d1) in one pass of the warp
+      const double d0 = __shfl_sync(0xffffffffu, s_Btt[0] - m_val(a0), 0);
+      const double d1 = __shfl_sync(0xffffffffu, s_Btt[1] - m_val(a1), 0);
+      const int kcur = s_kcur;
+      double num = 1.0, den = 1.0;
       if (tid == 0) {
-        const double d0 = s_Btt[0] - m_val(a0), d1 = s_Btt[1] - m_val(a1);
+        if (s_kind == 0) {
+          num = K;
+          den = (double)(kcur + 1);
+        } else if (s_kind == 1) {
+          num = (double)kcur;
+          den = K;
+        }
+      } else if (tid == 1) {
+        den = d0;
+      } else if (tid == 2) {
+        den = d1;
+      }
+      const double quo = num / den;
+      const double rd0 = __shfl_sync(0xffffffffu, quo, 1), rd1 = __shfl_sync(0xffffffffu, quo, 2);
+      if (tid == 0) {
         const Proposal& pr = s_prop[j];
         const uint64_t q = q0 + (uint64_t)j;
-        const int kcur = s_kcur;
-        const double R = (s_kind == 0 ? K / (double)(kcur + 1) : (s_kind == 1 ? (double)kcur / K : 1.0)) * d0 * d1;
+        const double R = quo * d0 * d1;
         int acc = 0, tie = 0;
         if (!isfinite(R)) {
           set_status(w, ST_ERR_NUMERIC);
@@ -715,8 +749,8 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
           c_acc += acc;
           s_eval = j + 1;
           if (acc) {
-            m_set(s_rd[0], 1.0 / d0);
-            m_set(s_rd[1], 1.0 / d1);
+            m_set(s_rd[0], rd0);
+            m_set(s_rd[1], rd1);
             s_P[l] = t;
             s_Pup[l] = tup;
             s_aP[0][l] = s_anew[0];
@@ -742,6 +776,24 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
       }
     }
     __syncthreads();
+    // The next proposal is planned: start the loads of its border entries
+    // (steps 6 and 7 of an accepted proposal run meanwhile).
+    if (j + 1 < len && !s_stop && s_kind != 2) {
+      const int l1 = s_l, t1 = s_target;
+      for (int idx = tid; idx < 4 * l1 + 2; idx += blockDim.x) {
+        int sp, x = t1, y = t1;
+        if (idx < 4 * l1) {
+          sp = idx / (2 * l1);
+          const int rem = idx - sp * 2 * l1;
+          const int P = s_P[rem >> 1];
+          if (rem & 1) x = P;
+          else y = P;
+        } else {
+          sp = idx - 4 * l1;
+        }
+        prefetch_l1(g_ext_ptr(ev[sp], x, y));
+      }
+    }
     if (!s_accept) continue;
     // 6. s = b_row B^-1 / d (column sums, G lanes per column as in step 3)
     {
