@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_ext_x(Config cfg) {
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
               const int j = j0 + 4 * tj + m;
-              if (j < n) w.Xr[sp][(size_t)c * ld + j] = (double)acc[q][m];
+              if (j < n) reinterpret_cast<float*>(w.Xr[sp])[(size_t)c * ld + j] = acc[q][m];
             }
         }
       });

@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
       // accumulator lane = candidate 32 warp + lane, columns j0 .. j0 + 127
       if (32 * warp < nc_) {
         const int c = 32 * warp + lane;
-        double* xrow = w.Xr[sp] + (size_t)c * ld;
+        float* xrow = reinterpret_cast<float*>(w.Xr[sp]) + (size_t)c * ld;
 #pragma unroll 1
         for (int cb = 0; cb < XX2_BJ; cb += 32) {
           float v[32];
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
           if (c < nc_)
 #pragma unroll
             for (int q = 0; q < 32; ++q)
-              if (j0 + cb + q < n) xrow[j0 + cb + q] = (double)v[q];
+              if (j0 + cb + q < n) xrow[j0 + cb + q] = v[q];
         }
       }
       tc::fence_before_sync();

@@ -387,7 +387,8 @@ __global__ void __launch_bounds__(256) k_upd_factors(Config cfg) {
                   double val;
                   if (P < n) {
                     const int sy = vs[P];
-                    val = (w.Xr[sp][(size_t)(x - n) * ld + P] * expV(pb, sp, sy)) * pb.rexpVm1[sp][sy > 0 ? 1 : 0] * a;
+                    val = ((double)reinterpret_cast<const float*>(w.Xr[sp])[(size_t)(x - n) * ld + P] * expV(pb, sp, sy)) *
+                          pb.rexpVm1[sp][sy > 0 ? 1 : 0] * a;
                   } else {
                     val = (w.Gc[sp][(size_t)(P - n) * ld + x] - (x == P ? 1.0 : 0.0)) * a;
                   }
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(256) k_upd_factors(Config cfg) {
             float v = 0.0f;
             if (p < l && j < n) {
               const int P = w.P[p];
-              v = P < n ? N[(size_t)P * ld + j] : (float)w.Xr[sp][(size_t)(P - n) * ld + j];
+              v = P < n ? N[(size_t)P * ld + j] : reinterpret_cast<const float*>(w.Xr[sp])[(size_t)(P - n) * ld + j];
               Rr[(size_t)p * cap + j] = v;
             }
             s_t[p][lane] = v;

@@ -326,7 +326,7 @@ __device__ __forceinline__ void cand_ext_tile(const Config& cfg, int wi, int sp,
         for (int a = 0; a < 2; ++a) {
           const int r = 2 * tp + a;
           if (i0 + r < n) atomicAdd(&w.Gc[sp][(size_t)cg * ld + i0 + r], (double)g[a][b]);
-          if (j0 + r < n) atomicAdd(&w.Xr[sp][(size_t)cg * ld + j0 + r], (double)x[a][b]);
+          if (j0 + r < n) atomicAdd(reinterpret_cast<T*>(w.Xr[sp]) + (size_t)cg * ld + j0 + r, (T)x[a][b]);
         }
       }
     }
@@ -366,14 +366,14 @@ __global__ void __launch_bounds__(256) k_cand_cc(Config cfg) {
         const int cpb = (tile / tiles) * 32, cb = (tile - (tile / tiles) * tiles) * 32;
         const int jlo = seg * CC_SEG, jhi = min(n, jlo + CC_SEG);
         const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-        const double* X = w.Xr[sp];
+        const A* X = reinterpret_cast<const A*>(w.Xr[sp]);  // A is the storage type of N and X
         const A* V = reinterpret_cast<const A*>(w.Vb[sp]);
         A acc[4] = {(A)0, (A)0, (A)0, (A)0};
         for (int j0 = jlo; j0 < jhi; j0 += 32) {
           __syncthreads();
           const int j = j0 + tx;
           for (int r = ty; r < 32; r += 8) {
-            Xs[r][tx] = (A)((cpb + r < nc_ && j < jhi) ? X[(size_t)(cpb + r) * ld + j] : 0.0);
+            Xs[r][tx] = (cpb + r < nc_ && j < jhi) ? X[(size_t)(cpb + r) * ld + j] : (A)0;
             Vs[r][tx] = (cb + r < nc_ && j < jhi) ? V[(size_t)(cb + r) * ld + j] : (A)0;
           }
           __syncthreads();
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(256) k_cand_cc(Config cfg) {
 template <typename T>
 struct ExtView {
   const T* N;        // current N (ld)
-  const double* X;   // candidate rows [c][ld]
+  const T* X;        // candidate rows [c][ld] (stored like N)
   const double* Gc;  // candidate columns [c][ld]
   const int* vs;
   int n, ld;
@@ -420,7 +420,7 @@ template <typename T>
 __device__ __forceinline__ ExtView<T> make_view(const WalkerDev& w, int sp) {
   ExtView<T> v;
   v.N = (const T*)w.N[w.parity][sp];
-  v.X = w.Xr[sp];
+  v.X = reinterpret_cast<const T*>(w.Xr[sp]);
   v.Gc = w.Gc[sp];
   v.vs = w.vs[w.parity];
   v.n = w.n;
@@ -433,7 +433,7 @@ __device__ __forceinline__ ExtView<T> make_view(const WalkerDev& w, int sp) {
 template <typename T>
 __device__ __forceinline__ double g_ext(const ExtView<T>& v, const ProblemDev& pb, int sp, int x, int y) {
   if (y >= v.n) return v.Gc[(size_t)(y - v.n) * v.ld + x];
-  const double nxy = (x < v.n) ? ldN(v.N, (size_t)x * v.ld + y) : v.X[(size_t)(x - v.n) * v.ld + y];
+  const double nxy = ldN(x < v.n ? v.N : v.X, (size_t)(x < v.n ? x : x - v.n) * v.ld + y);
   const int sy = v.vs[y];
   const double ev = expV(pb, sp, sy);
   // (N e^V - 1) / (e^V - 1) with the reciprocal tabulated per spin (no FP64 division)
@@ -445,7 +445,7 @@ __device__ __forceinline__ double g_ext(const ExtView<T>& v, const ProblemDev& p
 template <typename T>
 __device__ __forceinline__ double g_ext_at(const ExtView<T>& v, int x, int y, double ev, double rv) {
   if (y >= v.n) return v.Gc[(size_t)(y - v.n) * v.ld + x];
-  const double nxy = (x < v.n) ? ldN(v.N, (size_t)x * v.ld + y) : v.X[(size_t)(x - v.n) * v.ld + y];
+  const double nxy = ldN(x < v.n ? v.N : v.X, (size_t)(x < v.n ? x : x - v.n) * v.ld + y);
   return (nxy * ev - (x == y ? 1.0 : 0.0)) * rv;
 }
 
@@ -1042,7 +1042,7 @@ __global__ void __launch_bounds__(256) k_upd_lp_rr(Config cfg) {
             const int p = idx / n, j = idx - p * n;
             const int P = w.P[p];
             ((A*)w.Rr[sp])[(size_t)p * w.cap + j] =
-                P < n ? ldA<A>(v.N, (size_t)P * v.ld + j) : (A)v.X[(size_t)(P - n) * v.ld + j];
+                P < n ? ldA<A>(v.N, (size_t)P * v.ld + j) : ldA<A>(v.X, (size_t)(P - n) * v.ld + j);
           }
         }
       });
@@ -1139,8 +1139,7 @@ __global__ void __launch_bounds__(256) k_upd_border(Config cfg) {
       // cancellation (double-float on the mixed path)
       if (sizeof(A) == 4) {
         const float2* L = reinterpret_cast<const float2*>(w.Lp[sp]) + (size_t)(n + c) * KS_MAX;
-        const float2 x0 = df_split(w.Xr[sp][(size_t)c * ld + j]);
-        float hi = x0.x, lo = x0.y;
+        float hi = reinterpret_cast<const float*>(w.Xr[sp])[(size_t)c * ld + j], lo = 0.f;
         for (int p = 0; p < l; ++p) {
           const float2 a = L[p];
           df_fma(hi, lo, a.x, a.y, (float)Rr[(size_t)p * ld + j], 0.f);

@@ -131,7 +131,8 @@ struct WalkerDev {
   int32_t* surv_tmp;         // [cap] scratch for rebuilding live_idx
   Proposal* prop;            // [KS_MAX]
   double* Gc[2];             // [spin][KS_MAX][cap]: G_ext[:, n + c] stored per candidate c
-  double* Xr[2];             // [spin][KS_MAX][cap]: X[c, :] = g0[c,:] (e^V - 1) N
+  double* Xr[2];             // [spin][KS_MAX][cap]: X[c, :] = g0[c,:] (e^V - 1) N, stored in the type of N
+                             // (FP32 on the mixed path, where X is an FP32 product: read it through xrows())
   // V, U, gR and bvec hold the arithmetic type of the products: FP64 on the
   // FP64 path, FP32 (first half of the buffer, same indexing) on the mixed path.
   double* Vb[2];             // [spin][KS_MAX][cap]: V[c, j] = g0(r_j - r_c, tau_j - tau_c) (0 if j dead)
