@@ -311,23 +311,25 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
 // FP64 and split), in FP64 for the rows of accepted insertions (X is FP64).
 // Items per walker-spin: ceil(rows / 32) row blocks (rows = n + n_ins), then
 // ceil(n / 32) column blocks.  Dynamic shared memory: the L rows of a row
-// block [32][ld], ld = 64 with k_s <= 64 (then also B^-1, [64][64]) or 128;
-// a column block reuses it as the transposition tile [128][33].
-constexpr int FACT_RB = 32, FACT_BS = 64;
+// block [32][ld], ld = 65 with k_s <= 64 (then also B^-1, [64][64]) or 129
+// (odd strides: the rows a warp reads at one p fall in different banks); a
+// column block reuses it as the transposition tile [128][33].
+constexpr int FACT_RB = 32, FACT_BS = 64, FACT_PB = 8;
 
 __host__ __device__ constexpr size_t fact_smem(bool bs) {
-  return bs ? sizeof(float2) * (FACT_RB * FACT_BS + FACT_BS * FACT_BS) : sizeof(float2) * FACT_RB * KS_MAX;
+  return bs ? sizeof(float2) * (FACT_RB * (FACT_BS + 1) + FACT_BS * FACT_BS) : sizeof(float2) * FACT_RB * (KS_MAX + 1);
 }
 
 __global__ void __launch_bounds__(256) k_upd_factors(Config cfg) {
   constexpr int RB = FACT_RB;
   static_assert(KS_MAX * 33 * sizeof(float) <= fact_smem(false) && fact_smem(false) <= fact_smem(true), "tiles");
   __shared__ float2 s_c1[KS_MAX];
+  __shared__ int s_pp[KS_MAX], s_ok[KS_MAX], s_xr[FACT_RB];
   extern __shared__ __align__(16) float2 s_dyn[];
   const bool bs = cfg.ks <= FACT_BS;
-  const int lds = bs ? FACT_BS : KS_MAX;  // row stride of the L rows
-  float2* s_Lb = s_dyn;                   // [RB][lds]
-  float2* s_binv = s_dyn + RB * FACT_BS;  // [FACT_BS][FACT_BS] (bs only)
+  const int lds = bs ? FACT_BS + 1 : KS_MAX + 1;  // row stride of the L rows
+  float2* s_Lb = s_dyn;                           // [RB][lds]
+  float2* s_binv = s_dyn + RB * (FACT_BS + 1);    // [FACT_BS][FACT_BS] (bs only)
   float(*s_t)[33] = reinterpret_cast<float(*)[33]>(s_dyn);  // [KS_MAX][33]
   for_each_item(
       2 * cfg.n_walkers,
@@ -347,9 +349,20 @@ __global__ void __launch_bounds__(256) k_upd_factors(Config cfg) {
         __syncthreads();  // the previous item is done with the shared tiles
         if (item < ra) {
           const int t0 = item * RB;
+          for (int r = threadIdx.x; r < RB; r += blockDim.x) {
+            const int t = t0 + r;
+            int x = -1;
+            if (t < rows) {
+              x = t < n ? t : n + w.acc_slot[t - n];
+              if (x < n && vs[x] == 0) x = -1;  // dead row: its L row is zero
+            }
+            s_xr[r] = x;
+          }
           for (int p = threadIdx.x; p < l; p += blockDim.x) {
             const int P = w.P[p];
             const double a = w.aP[sp][p];
+            s_pp[p] = P;
+            s_ok[p] = a != 0.0;
             if (P < n) {
               const int sy = vs[P];
               s_c1[p] = df_split(expV(pb, sp, sy) * pb.rexpVm1[sp][sy > 0 ? 1 : 0] * a);
@@ -364,26 +377,40 @@ __global__ void __launch_bounds__(256) k_upd_factors(Config cfg) {
               s_binv[p * FACT_BS + q] = q < l ? Bi[(size_t)p * KS_MAX + q] : make_float2(0.f, 0.f);
             }
           __syncthreads();
-          for (int e = threadIdx.x; e < RB * l; e += blockDim.x) {
-            const int r = e / l, p = e - r * l;
-            const int t = t0 + r;
-            float2 v = make_float2(0.f, 0.f);
-            if (t < rows) {
-              const int x = t < n ? t : n + w.acc_slot[t - n];
-              const int P = w.P[p];
-              const double a = w.aP[sp][p];
-              if (a != 0.0 && !(x < n && vs[x] == 0)) {
+          // L in batches of FACT_PB entries per thread: the loads of a batch are all
+          // issued before the arithmetic (they are scattered columns of N)
+          for (int e0 = 0; e0 < RB * l; e0 += FACT_PB * 256) {
+            float gv[FACT_PB];
+#pragma unroll
+            for (int k = 0; k < FACT_PB; ++k) {
+              const int e = e0 + k * 256 + threadIdx.x;
+              gv[k] = 0.f;
+              if (e < RB * l) {
+                const int r = e / l, p = e - r * l;
+                const int x = s_xr[r], P = s_pp[p];
+                if (x >= 0 && x < n && s_ok[p])
+                  gv[k] = P < n ? N[(size_t)x * ld + P] : (float)w.Gc[sp][(size_t)(P - n) * ld + x];
+              }
+            }
+#pragma unroll
+            for (int k = 0; k < FACT_PB; ++k) {
+              const int e = e0 + k * 256 + threadIdx.x;
+              if (e >= RB * l) break;
+              const int r = e / l, p = e - r * l;
+              const int x = s_xr[r], P = s_pp[p];
+              float2 v = make_float2(0.f, 0.f);
+              if (x >= 0 && s_ok[p]) {
                 if (x < n) {
                   // FP32-exact entry times the column factor, in double-float.  An
                   // existing column y = P: G_ext[x, y] = (N_xy e^{V_y} - delta) / (e^{V_y} - 1),
                   // so (G_ext - delta) a = (N_xy - delta) e^{V_y} a / (e^{V_y} - 1) = (N_xy - delta) c1;
                   // a candidate column: (G_ext[x, c] - 0) a with c1 = a (x < n is never the candidate)
-                  const float g = P < n ? N[(size_t)x * ld + P] : (float)w.Gc[sp][(size_t)(P - n) * ld + x];
                   float hi = 0.f, lo = 0.f;
-                  df_fma(hi, lo, g, 0.f, s_c1[p].x, s_c1[p].y);
+                  df_fma(hi, lo, gv[k], 0.f, s_c1[p].x, s_c1[p].y);
                   if (x == P) df_fma(hi, lo, -1.f, 0.f, s_c1[p].x, s_c1[p].y);
                   v = df_norm(hi, lo);
                 } else {
+                  const double a = w.aP[sp][p];
                   double val;
                   if (P < n) {
                     const int sy = vs[P];
@@ -395,8 +422,8 @@ __global__ void __launch_bounds__(256) k_upd_factors(Config cfg) {
                   v = df_split(val);
                 }
               }
+              s_Lb[r * lds + p] = v;
             }
-            s_Lb[r * lds + p] = v;
           }
           __syncthreads();
           // L' = L B^-1: four consecutive outputs of a row per thread (four
@@ -437,14 +464,23 @@ __global__ void __launch_bounds__(256) k_upd_factors(Config cfg) {
           const int j0 = (item - ra) * RB;
           const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, j = j0 + lane;
           float* Rr = (float*)w.Rr[sp];
-          for (int p = warp; p < lpad; p += 8) {
-            float v = 0.0f;
+          float rv[KS_MAX / 8];  // this lane's entries of rows p = warp + 8 k, loads issued together
+#pragma unroll
+          for (int k = 0; k < KS_MAX / 8; ++k) {
+            const int p = warp + 8 * k;
+            rv[k] = 0.0f;
             if (p < l && j < n) {
               const int P = w.P[p];
-              v = P < n ? N[(size_t)P * ld + j] : reinterpret_cast<const float*>(w.Xr[sp])[(size_t)(P - n) * ld + j];
-              Rr[(size_t)p * cap + j] = v;
+              rv[k] = P < n ? N[(size_t)P * ld + j] : reinterpret_cast<const float*>(w.Xr[sp])[(size_t)(P - n) * ld + j];
             }
-            s_t[p][lane] = v;
+          }
+#pragma unroll
+          for (int k = 0; k < KS_MAX / 8; ++k) {
+            const int p = warp + 8 * k;
+            if (p < lpad) {
+              if (p < l && j < n) Rr[(size_t)p * cap + j] = rv[k];
+              s_t[p][lane] = rv[k];
+            }
           }
           __syncthreads();
           for (int jj = warp; jj < RB; jj += 8) {

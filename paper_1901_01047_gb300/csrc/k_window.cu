@@ -208,6 +208,8 @@ __global__ void __launch_bounds__(256) k_cand_zero(Config cfg) {
         const double em1 = si != 0 ? expV(pb, sp, si) - 1.0 : 0.0;
         const GridTime gi = grid_time(ti, pb.tau_scale);
         const float em1f = (float)em1;
+        // unrolled: the table loads of several candidates are in flight together
+#pragma unroll 4
         for (int c = 0; c < nc_; ++c) {
           const size_t o = (size_t)c * ld + i;
           if (!mixed) {  // targets of the FP64 path's atomics (the mixed-path kernels store rows < n whole)

@@ -16,7 +16,7 @@ enum Group : int {
   GROUP_UPDATE = 3,          // the rank-l update of N
   GROUP_MEASURE = 4,         // k_meas_*
   GROUP_RECOMPUTE = 5,       // k_gj_cluster
-  GROUP_UPDATE_PRE = 6,      // k_upd_lrow, k_upd_lp_rr
+  GROUP_UPDATE_PRE = 6,      // k_upd_factors (tcgen05 path) or k_upd_lrow, k_upd_lp_rr
   GROUP_UPDATE_POST = 7,     // k_upd_border, k_window_end, k_compact_N, k_compact_end
   GROUP_RECOMPUTE_PRE = 8,   // k_build_A
   GROUP_RECOMPUTE_POST = 9,  // (k_store_fp32), k_recompute_drift, k_recompute_adopt

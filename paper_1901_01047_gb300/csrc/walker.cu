@@ -6,6 +6,7 @@
 // device-side walker records, so the host reads back only a small status word
 // between chunks of windows.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdio>
@@ -612,7 +613,15 @@ static bool has_recompute(const dca_walker* h) {
 }
 
 // Launch one kernel group, bracketed by events when its timing bit is set.
+// NVTX names of the kernel groups (ranges around each group of the host-driven
+// loop, and around the graph launch of the device-side loop), for profilers
+// that filter by range.
+static const char* const kGroupNames[dca::N_GROUPS] = {
+    "dca:propose", "dca:extend",      "dca:metropolis",    "dca:update",       "dca:measure",
+    "dca:recompute", "dca:update_pre", "dca:update_post", "dca:recompute_pre", "dca:recompute_post"};
+
 static void run_group(dca_walker* h, int group) {
+  nvtxRangePushA(kGroupNames[group]);
   const bool timed = (h->timing_mask >> group) & 1u;
   cudaEvent_t e0 = nullptr;
   size_t i0 = 0;
@@ -638,6 +647,7 @@ static void run_group(dca_walker* h, int group) {
       h->ev_pending.push_back({group, (int)i0});
     }
   }
+  nvtxRangePop();
 }
 
 // After a stream synchronisation: fold the recorded intervals into the totals.
@@ -739,10 +749,13 @@ static int sweep_graph(dca_walker* h, int32_t n_sweeps) {
   // at most `capacity` proposals, so this bound is never reached normally.
   int64_t max_iters = (int64_t)n_sweeps * (int64_t)(h->max_cap + 1) + 64;
   if (h->max_windows > 0 && h->max_windows < max_iters) max_iters = h->max_windows;
+  nvtxRangePushA("dca:sweep_graph");
   dca::launch_add_target(h->cfg, n_sweeps, h->stream);
   dca::launch_loop_reset(h->d_loop, max_iters, h->stream);
+  const cudaError_t le = cudaGraphLaunch(h->loop_exec, h->stream);
+  nvtxRangePop();
   CK(cudaGetLastError());
-  CK(cudaGraphLaunch(h->loop_exec, h->stream));
+  CK(le);
   h->total_launches += 2;
   return DCA_OK;
 }
