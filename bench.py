@@ -64,10 +64,10 @@ MIXED_RECOMPUTE_TFLOPS = 4.0 / (2.0 / (FP32_INSTR_PER_S * 2 / 11 / 1e12) + 2.0 /
 # the named workload (one window of the pooled schedule carries all walkers;
 # mean of two captured launches per kernel), quoted as `traffic` for that group
 # on that workload only:
-#   update  k_upd_tc 863.8 MB read + 533.0 MB written;
-#   extend  k_cand_zero 54.9 + 84.6, k_ext_g_tc 714.9 + 45.4, k_ext_x_tc
-#           703.5 + 44.9, k_cand_cc 125.6 + 2.3 (MB read + written).
-NCU_TRAFFIC = {("batched256", "update"): 1.397e9, ("batched256", "extend"): 1.776e9}
+#   update  k_upd_tc 863.1 MB read + 532.7 MB written;
+#   extend  k_cand_zero 55.3 + 85.8, k_ext_g_tc 714.0 + 44.9, k_ext_x_tc
+#           704.2 + 23.3, k_cand_cc 99.2 + 1.6 (MB read + written).
+NCU_TRAFFIC = {("batched256", "update"): 1.396e9, ("batched256", "extend"): 1.728e9}
 
 
 class ClockSampler:
