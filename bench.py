@@ -131,6 +131,8 @@ def workload_of(args):
     wl = inputs.WORKLOADS[args.workload]
     if getattr(args, "schedule", None):
         wl = dataclasses.replace(wl, schedule=args.schedule)
+    if getattr(args, "duplicate_rule", None):
+        wl = dataclasses.replace(wl, duplicate_rule=args.duplicate_rule)
     return wl
 
 
@@ -141,7 +143,7 @@ def config_of(wl, world):
             "recompute_at_measure": wl.recompute_at_measure, "n_omega_meas": wl.n_omega_meas,
             **({"freq_method": wl.freq_method} if wl.n_omega_meas else {}),
             **({"n_w4": wl.n_w4, "w4_transfer": wl.w4_transfer, "q4_transfer": wl.q4_transfer} if wl.n_w4 else {}),
-            "precision": wl.precision, "schedule": wl.schedule,
+            "precision": wl.precision, "schedule": wl.schedule, "duplicate_rule": wl.duplicate_rule,
             "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)",
             **({"per_walker": {"nc": list(wl.nc_choices), "beta": list(wl.beta_range), "U": list(wl.U_range),
                                "mu": "U/2"}} if wl.nc_choices else {})}
@@ -299,7 +301,8 @@ def g_error_sample(wl, k_sub, stream, warmup=17, measured=6):
         gw = walker.Walkers([probs[i] for i in picks], n_walkers=len(picks), k_sub=k_sub, recompute_every=0,
                             recompute_sweeps=wl.recompute_sweeps, warmup_sweeps=warmup, n_tau_meas=wl.n_tau_meas,
                             precision="mixed", init_config_size=wl.init_config_size, seed=wl.seed,
-                            recompute_at_measure=fresh, log_capacity=1 << 24, stream=stream.cuda_stream)
+                            recompute_at_measure=fresh, log_capacity=1 << 24, duplicate_rule=wl.duplicate_rule,
+                            stream=stream.cuda_stream)
         errs = []
         for j, i in enumerate(picks):
             gw.set_forced_decisions(j, runs[i][0])
@@ -379,7 +382,7 @@ def run_ours(args, rank, world, local_rank):
                         init_config_size=wl.init_config_size, seed=seed, schedule=wl.schedule,
                         recompute_at_measure=wl.recompute_at_measure, n_omega_meas=wl.n_omega_meas,
                         freq_method=wl.freq_method, n_w4=wl.n_w4, w4_transfer=wl.w4_transfer,
-                        q4_transfer=wl.q4_transfer, stream=stream.cuda_stream)
+                        q4_transfer=wl.q4_transfer, duplicate_rule=wl.duplicate_rule, stream=stream.cuda_stream)
     gw.sweep(wl.warmup_sweeps)            # the chain's own warm-up (no measurements)
     tuned = None
     if wl.autotune and not args.no_autotune:  # untimed; the trial sweeps are ordinary sweeps of the chains
@@ -639,6 +642,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the workload's stored k_s and update kernel")
     ap.add_argument("--schedule", choices=["lockstep", "pooled"], default=None,
                     help="walker schedule (default: the workload's)")
+    ap.add_argument("--duplicate-rule", choices=["abort", "update"], default=None,
+                    help="a spin changed twice in one window (default: the workload's)")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off) "
                          "and launch the window kernels from the host in that region")

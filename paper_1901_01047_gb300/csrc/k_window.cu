@@ -541,6 +541,10 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
   __shared__ int s_Pup[KS_MAX];       // spin of a live P_p > 0
   __shared__ int s_removed[KS_MAX];   // live ranks removed in this window, ascending
   __shared__ int s_flipped[KS_MAX];   // live ranks whose auxiliary spin was flipped in this window
+  __shared__ int s_flip_p[KS_MAX];    // their positions in P
+  __shared__ int s_ins_p[KS_MAX];     // positions in P of the vertices inserted in this window, in order
+  __shared__ int s_gone[KS_MAX];      // P entry of a vertex inserted and removed again in this window
+  __shared__ int s_dupq, s_dupi, s_upq;  // duplicate update: P position, list index; P position being applied
   __shared__ double s_ev[2][2], s_rv[2][2];  // e^{V} and 1 / (e^{V} - 1): [spin][s > 0]
   __shared__ double s_anew_tab[3][2][2];      // a_t of an insertion / removal / flip: [kind][spin][s > 0]
   __shared__ double s_anew[2], s_Btt[2];
@@ -584,20 +588,24 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
   // flip from the empty configuration, or a proposal the neglect rule drops).
   // A removal or flip that picks a spin already changed in this window (an
   // insertion or a flip of this window) ends the window (the abort variant;
-  // the proposal is re-evaluated first in the next window) or, under the
-  // neglect rule, is rejected.
+  // the proposal is re-evaluated first in the next window), is rejected (the
+  // neglect rule), or is evaluated in place (kinds 4 to 7, the update rule:
+  // a rank-1 change of one column of B).
   auto plan = [&](int j) {
     const Proposal& pr = s_prop[j];
     const int kcur = n_live - s_nrem + s_nins;
     int kind = 0, target = -1, rank = -1, up = 0;
     if (pr.type == 0) {
       target = n + pr.slot;
-      for (int sp = 0; sp < 2; ++sp) s_anew[sp] = s_anew_tab[0][sp][pr.s > 0 ? 1 : 0];
+      up = pr.s > 0 ? 1 : 0;  // the candidate's spin (its factors e^V are not needed: G_ext is tabulated)
+      for (int sp = 0; sp < 2; ++sp) s_anew[sp] = s_anew_tab[0][sp][up];
     } else if (kcur == 0) {
       kind = 2;
     } else {
       const int idx = (int)scaled_index(pr.word, (uint32_t)kcur);
-      bool dup = idx >= n_live - s_nrem;  // a spin inserted in this window
+      const int nold = n_live - s_nrem;
+      bool dup = idx >= nold;  // a spin inserted in this window
+      int dupq = dup ? s_ins_p[idx - nold] : -1, dupi = idx - nold;
       if (!dup) {
         // idx-th live vertex not yet removed in this window: rank = idx + r*,
         // r* the first r with s_removed[r] - r > idx (s_removed ascending and
@@ -609,11 +617,31 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
           else hi = mid;
         }
         rank = idx + lo;
-        for (int r = 0; r < s_nflip; ++r) dup |= s_flipped[r] == rank;
+        for (int r = 0; r < s_nflip; ++r)
+          if (s_flipped[r] == rank) {
+            dup = true;
+            dupq = s_flip_p[r];
+            dupi = r;
+          }
       }
       if (dup) {
-        if (cfg.neglect) kind = 2;
-        else s_stop = 1;  // end the window here
+        if (cfg.dup_rule == 1) {
+          kind = 2;  // neglect rule: rejected
+        } else if (cfg.dup_rule == 2) {
+          // the spin at P position dupq changes again: kinds 4 / 5 remove / flip a
+          // vertex inserted in this window, 6 / 7 remove / flip one flipped in it;
+          // a' is the total change against the start of the window
+          const bool ins = idx >= nold;
+          kind = (ins ? 4 : 6) + (pr.type == 2 ? 1 : 0);
+          target = s_P[dupq];
+          up = s_Pup[dupq];
+          for (int sp = 0; sp < 2; ++sp)
+            s_anew[sp] = kind == 4 || kind == 7 ? 0.0 : (kind == 5 ? s_anew_tab[0][sp][up ^ 1] : s_anew_tab[1][sp][up]);
+          s_dupq = dupq;
+          s_dupi = dupi;
+        } else {
+          s_stop = 1;  // abort rule: end the window here
+        }
       } else {
         kind = pr.type == 2 ? 3 : 1;
         if (live_smem) {
@@ -652,6 +680,97 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
         if (j + 1 < len) plan(j + 1);
       }
       __syncthreads();
+      continue;
+    }
+    if (s_kind >= 4) {
+      // A spin changed earlier in this window changes again: column q of B
+      // changes by u = (e_q - G_Pq)(a' - a) = c (B e_q - e_q), c = (a' - a) / a, so
+      // det B'/det B = 1 + c (1 - (B^-1)_qq) and, by Sherman-Morrison,
+      // B'^-1 = B^-1 - (c / rho) (e_q - B^-1 e_q) e_q^T B^-1.  Exact: the chain
+      // of single-spin updates without ending the window.
+      __syncthreads();  // every thread has read s_kind
+      if (tid == 0) {
+        const int qp = s_dupq, kind = s_kind;
+        const Proposal& pr = s_prop[j];
+        const uint64_t q = q0 + (uint64_t)j;
+        double rho[2], coef[2];
+        for (int sp = 0; sp < 2; ++sp) {
+          // a = 0 only where every factor is (U = 0, e^V = 1): then a' = a, no change
+          const double a = s_aP[sp][qp], c = s_anew[sp] == a ? 0.0 : (s_anew[sp] - a) / a;
+          rho[sp] = 1.0 + c * (1.0 - m_val(Binv[sp][(size_t)qp * bst + qp]));
+          coef[sp] = c / rho[sp];
+        }
+        const double R = (kind == 4 || kind == 6 ? (double)s_kcur / K : 1.0) * rho[0] * rho[1];
+        int acc = 0, tie = 0;
+        if (!isfinite(R)) {
+          set_status(w, ST_ERR_NUMERIC);
+          s_stop = 1;
+        } else {
+          const double absR = fabs(R);
+          acc = pr.u < absR;
+          tie = fabs(absR - pr.u) < cfg.tie_eps;
+          if ((int64_t)q < forced_n) acc = w.forced[q] & 1;
+          if (acc && R < 0.0) s_sign = -s_sign;
+          if ((int64_t)q < log_cap) w.log[q] = (uint8_t)(acc | (tie << 1));
+          ++c_prop;
+          c_ties += tie;
+          c_acc += acc;
+          s_eval = j + 1;
+          if (acc) {
+            s_upq = qp;
+            m_set(s_rd[0], coef[0]);
+            m_set(s_rd[1], coef[1]);
+            s_aP[0][qp] = s_anew[0];
+            s_aP[1][qp] = s_anew[1];
+            const int di = s_dupi;
+            if (kind == 4) {  // the inserted vertex goes: later insertions move up one place
+              for (int r = di; r + 1 < s_nins; ++r) s_ins_p[r] = s_ins_p[r + 1];
+              s_nins--;
+              s_gone[qp] = 1;
+            } else if (kind == 5) {  // the inserted vertex keeps its place with the other spin
+              s_Pup[qp] ^= 1;
+            } else {  // kinds 6, 7: no longer a flipped vertex
+              for (int r = di; r + 1 < s_nflip; ++r) {
+                s_flipped[r] = s_flipped[r + 1];
+                s_flip_p[r] = s_flip_p[r + 1];
+              }
+              s_nflip--;
+              if (kind == 6) {  // removed: its rank joins the removed ranks (ascending)
+                int r = s_nrem;
+                while (r > 0 && s_removed[r - 1] > s_rank) {
+                  s_removed[r] = s_removed[r - 1];
+                  --r;
+                }
+                s_removed[r] = s_rank;
+                s_nrem++;
+              }
+            }
+          }
+          if (j + 1 < len) plan(j + 1);
+        }
+        s_accept = acc;
+      }
+      __syncthreads();
+      if (!s_accept) continue;
+      {
+        const int qp = s_upq;
+        for (int idx = tid; idx < 2 * l; idx += blockDim.x) {
+          const int sp = idx >= l ? 1 : 0, i = idx - sp * l;
+          const M* B = Binv[sp];
+          m_set(s_t[sp][i], -m_val(s_rd[sp]) * ((i == qp ? 1.0 : 0.0) - m_val(B[(size_t)i * bst + qp])));
+          s_s[sp][i] = B[(size_t)qp * bst + i];
+        }
+        __syncthreads();
+        for (int idx = tid; idx < 2 * l * l; idx += blockDim.x) {
+          const int sp = idx >= l * l ? 1 : 0, r = idx - sp * l * l;
+          const int i = r / l, jj = r - i * l;
+          M* B = Binv[sp] + (size_t)i * bst + jj;
+          M b = *B;
+          m_fma(b, s_t[sp][i], s_s[sp][jj]);
+          *B = m_fin(b);
+        }
+        // no barrier: as after step 7
+      }
       continue;
     }
     const int t = s_target, tup = s_tup;
@@ -755,6 +874,7 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
             m_set(s_rd[1], rd1);
             s_P[l] = t;
             s_Pup[l] = tup;
+            s_gone[l] = 0;
             s_aP[0][l] = s_anew[0];
             s_aP[1][l] = s_anew[1];
             if (s_kind == 1) {
@@ -766,9 +886,10 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
               s_removed[r] = s_rank;
               s_nrem++;
             } else if (s_kind == 3) {
+              s_flip_p[s_nflip] = l;
               s_flipped[s_nflip++] = s_rank;
             } else {
-              s_nins++;
+              s_ins_p[s_nins++] = l;
             }
             s_l = l + 1;
           }
@@ -780,7 +901,7 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
     __syncthreads();
     // The next proposal is planned: start the loads of its border entries
     // (steps 6 and 7 of an accepted proposal run meanwhile).
-    if (j + 1 < len && !s_stop && s_kind != 2) {
+    if (j + 1 < len && !s_stop && s_kind != 2 && s_kind < 4) {
       const int l1 = s_l, t1 = s_target;
       for (int idx = tid; idx < 4 * l1 + 2; idx += blockDim.x) {
         int sp, x = t1, y = t1;
@@ -864,9 +985,10 @@ __global__ void __launch_bounds__(256) k_metropolis(Config cfg) {
     w.n_accept += c_acc;
     int m = 0;
     for (int p = 0; p < l; ++p)
-      if (s_P[p] >= n) {
+      if (s_P[p] >= n && !s_gone[p]) {  // an inserted candidate (not removed again)
         w.acc_slot[m] = s_P[p] - n;
         w.acc_p[m] = p;
+        w.vs[w.parity][s_P[p]] = s_Pup[p] ? 1 : -1;  // its spin (a flip in the window may have changed it)
         ++m;
       }
     const int eval = s_eval;

@@ -236,7 +236,8 @@ struct Config {
   long long wait_cycles;     // bound of every mbarrier wait in the tensor-core kernels (SM clocks)
   int32_t recompute_at_measure;  // recompute N in the window of every measurement (before it)
   uint32_t flip_thr;         // a proposal is an auxiliary-spin flip when (word0 >> 2) < flip_thr (0 = none)
-  int32_t neglect;           // duplicate spin in a window: 0 abort the window, 1 reject the proposal
+  int32_t dup_rule;          // spin changed twice in a window: 0 end the window, 1 reject the proposal,
+                             // 2 apply the change within the window
   int32_t n_omega;           // frequency measurement: positive Matsubara frequencies (0 = off)
   int32_t nfft_L;            // its grid points over [0, beta)
   int32_t nfft_msp;          // its window half-width in grid points

@@ -182,7 +182,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     return fail(nullptr, DCA_ERR_ARG, "DCA_PREC_TF32 runs on the tensor cores only");
   if (!(p.flip_fraction >= 0.0) || p.flip_fraction > 1.0)
     return fail(nullptr, DCA_ERR_ARG, "flip_fraction must be in [0, 1]");
-  if (p.duplicate_rule != DCA_DUP_ABORT && p.duplicate_rule != DCA_DUP_NEGLECT)
+  if (p.duplicate_rule != DCA_DUP_ABORT && p.duplicate_rule != DCA_DUP_NEGLECT && p.duplicate_rule != DCA_DUP_UPDATE)
     return fail(nullptr, DCA_ERR_ARG, "duplicate_rule must be one of DCA_DUP_*");
   if (p.freq_method != DCA_FREQ_NFFT && p.freq_method != DCA_FREQ_DFT)
     return fail(nullptr, DCA_ERR_ARG, "freq_method must be one of DCA_FREQ_*");
@@ -501,7 +501,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.wait_cycles = kDefaultWaitCycles;
   h->cfg.recompute_at_measure = p.recompute_at_measure ? 1 : 0;
   h->cfg.flip_thr = (uint32_t)std::floor(p.flip_fraction * 1073741824.0);
-  h->cfg.neglect = p.duplicate_rule == DCA_DUP_NEGLECT ? 1 : 0;
+  h->cfg.dup_rule = p.duplicate_rule;
   h->cfg.n_omega = p.n_omega_meas;
   h->cfg.nfft_L = 4 * p.n_omega_meas;
   h->cfg.nfft_msp = h->precision == DCA_PREC_FP64 ? 12 : 8;

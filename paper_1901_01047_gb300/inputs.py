@@ -130,6 +130,9 @@ class Workload:
     q4_transfer: int = 0  # its momentum transfer (cluster momentum index)
     autotune: bool = False  # bench: choose k_s and the update kernel by the autotuner
     schedule: str = "lockstep"  # "pooled": the walkers share the sweep budget (all active every window)
+    # a spin changed twice in one window: "update" applies it in place, "abort"
+    # ends the window there (both give the chain of single-spin updates)
+    duplicate_rule: str = "update"
     precision: str = "fp64"
     # batched workloads: per-walker problems drawn from these ranges (seeded)
     nc_choices: Tuple[int, ...] = ()

@@ -325,7 +325,7 @@ class Walkers:
         p.n_omega_meas = int(n_omega_meas)
         p.flip_fraction = float(flip_fraction)
         p.freq_method = {"nfft": 0, "dft": 1}[freq_method] if isinstance(freq_method, str) else int(freq_method)
-        p.duplicate_rule = {"abort": 0, "neglect": 1}[duplicate_rule] if isinstance(duplicate_rule, str) \
+        p.duplicate_rule = {"abort": 0, "neglect": 1, "update": 2}[duplicate_rule] if isinstance(duplicate_rule, str) \
             else int(duplicate_rule)
         self.n_omega_meas = int(n_omega_meas)
         p.n_w4 = int(n_w4)

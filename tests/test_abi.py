@@ -77,6 +77,7 @@ def _params(walker, **over):
     ("k_sub", 0), ("k_sub", 129), ("n_walkers", 0), ("n_tau_meas", 0), ("init_config_size", -1),
     ("precision", 99), ("K", 0.0), ("beta", -1.0), ("U", -1.0), ("n_problems", 0), ("gamma_precision", 7),
     ("schedule", 5), ("update_kernel", 9), ("recompute_method", 4), ("n_w4", 33), ("n_w4", -1),
+    ("duplicate_rule", 3), ("duplicate_rule", -1),
 ])
 def test_invalid_parameters_rejected_on_host(lib, field, value):
     from paper_1901_01047_gb300 import walker
