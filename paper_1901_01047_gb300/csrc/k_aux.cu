@@ -765,6 +765,22 @@ int launch_measure(const Config& cfg, int max_cap, int max_nc, cudaStream_t st) 
   return 5 + (max_nc > 16) + (max_nc > 32) + nf;
 }
 
+// Read-out of the tau-grid measurement: every walker's accumulator Gacc
+// [2][nc][n_tau_meas] to out + base[walker].  grid = (chunks, walkers).
+__global__ void k_gather_G(Config cfg, const long long* base, double* out) {
+  const int wi = blockIdx.y;
+  const WalkerDev& w = cfg.W[wi];
+  const long long total = 2LL * cfg.P[w.problem].nc * cfg.n_tau_meas;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x)
+    out[base[wi] + e] = w.Gacc[e];
+}
+
+void launch_gather_G(const Config& cfg, int max_nc, const long long* d_base, double* d_out, cudaStream_t st) {
+  const long long per = 2LL * max_nc * cfg.n_tau_meas;
+  const int bx = (int)((per + 255) / 256 < 64 ? (per + 255) / 256 : 64);
+  k_gather_G<<<dim3(bx, cfg.n_walkers), 256, 0, st>>>(cfg, d_base, d_out);
+}
+
 void launch_g0_isolated(int nc, const double* d_eps, const double* d_kr, double mu_eff, double beta, int n_tau,
                         double* d_out, cudaStream_t st) {
   const int m = nc * (n_tau + 1);

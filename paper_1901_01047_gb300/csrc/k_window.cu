@@ -341,68 +341,107 @@ constexpr int ext_smem_bytes() {
 }
 
 // G_ext[n+c', n+c] = X[c',:] . V[c,:] + g0(r_c' - r_c, tau_c' - tau_c)
-// (V[c, j] = g0(r_j - r_c, tau_j - tau_c), zero on dead j).  Item = 32 x 32
-// tile of candidate pairs and one segment of CC_SEG columns of one
-// walker-spin; the X and V rows are staged through shared memory 32 columns
-// at a time, the segment sums are added into the targets (zeroed by
-// k_cand_zero) with FP64 atomics and segment 0 adds the g0 term.  The products
-// run in the arithmetic type A.  Block 256 = 32 c x 8 c'.
-constexpr int CC_SEG = 256;
+// (V[c, j] = g0(r_j - r_c, tau_j - tau_c), zero on dead j).  Item = TS x TS
+// tile of candidate pairs (TS = 32 for up to 32 candidates, else 64) and one
+// segment of CC_SEG columns of one walker-spin; the X and V rows pass through
+// shared memory CC_KC columns at a time, the next chunk's loads in flight in
+// registers while the current one is multiplied.  Thread (tx, ty) of 16 x 16
+// owns c' = ty + 16 a, c = tx + 16 b (a, b < TS / 16).  The segment sums are
+// added into the targets (zeroed by k_cand_zero) with FP64 atomics and
+// segment 0 adds the g0 term.  The products run in the storage type A of N
+// and X.
+constexpr int CC_SEG = 128;
+constexpr int CC_KC = 32;
+
+__device__ __forceinline__ int cc_tile(int nc_) { return nc_ <= 32 ? 32 : 64; }
+
+template <typename A, int TS>
+__device__ __forceinline__ void cand_cc_item(const Config& cfg, const WalkerDev& w, int sp, int tile, int seg,
+                                             A (*Xs)[65], A (*Vs)[65]) {
+  constexpr int MT = TS / 16, PR = TS * CC_KC / 256;  // outputs per thread per axis, loads per thread per operand
+  const int n = w.n, nc_ = w.n_cand, ld = w.cap, par = w.parity;
+  const int tiles = (nc_ + TS - 1) / TS;
+  const int cpb = (tile / tiles) * TS, cb = (tile - (tile / tiles) * tiles) * TS;
+  const int jlo = seg * CC_SEG, jhi = min(n, jlo + CC_SEG);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const A* X = reinterpret_cast<const A*>(w.Xr[sp]);
+  const A* V = reinterpret_cast<const A*>(w.Vb[sp]);
+  A xr[PR], vr[PR];
+  auto fetch = [&](int j0) {
+#pragma unroll
+    for (int q = 0; q < PR; ++q) {
+      const int e = tid + 256 * q, col = e & (CC_KC - 1), r = e / CC_KC, j = j0 + col;
+      xr[q] = (cpb + r < nc_ && j < jhi) ? X[(size_t)(cpb + r) * ld + j] : (A)0;
+      vr[q] = (cb + r < nc_ && j < jhi) ? V[(size_t)(cb + r) * ld + j] : (A)0;
+    }
+  };
+  A acc[MT][MT];
+#pragma unroll
+  for (int a = 0; a < MT; ++a)
+#pragma unroll
+    for (int b = 0; b < MT; ++b) acc[a][b] = (A)0;
+  if (jlo < jhi) fetch(jlo);
+  for (int j0 = jlo; j0 < jhi; j0 += CC_KC) {
+    __syncthreads();  // the previous chunk (or item) is done with the shared rows
+#pragma unroll
+    for (int q = 0; q < PR; ++q) {
+      const int e = tid + 256 * q, col = e & (CC_KC - 1), r = e / CC_KC;
+      Xs[col][r] = xr[q];
+      Vs[col][r] = vr[q];
+    }
+    __syncthreads();
+    if (j0 + CC_KC < jhi) fetch(j0 + CC_KC);
+#pragma unroll 8
+    for (int k = 0; k < CC_KC; ++k) {
+      A xa[MT], vb[MT];
+#pragma unroll
+      for (int a = 0; a < MT; ++a) xa[a] = Xs[k][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < MT; ++b) vb[b] = Vs[k][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < MT; ++a)
+#pragma unroll
+        for (int b = 0; b < MT; ++b) acc[a][b] += xa[a] * vb[b];
+    }
+  }
+  const ProblemDev& pb = cfg.P[w.problem];
+#pragma unroll
+  for (int b = 0; b < MT; ++b) {
+    const int c = cb + tx + 16 * b;
+    if (c >= nc_) continue;
+    const int rc = w.vsite[par][n + c];
+    const double tc = w.vtau[par][n + c];
+#pragma unroll
+    for (int a = 0; a < MT; ++a) {
+      const int cp = cpb + ty + 16 * a;
+      if (cp < nc_) {
+        double v = (double)acc[a][b];
+        if (seg == 0)
+          v += (cp == c) ? g0_diag(pb, sp, rc) : g0_pair(pb, sp, w.vsite[par][n + cp], w.vtau[par][n + cp], rc, tc);
+        atomicAdd(&w.Gc[sp][(size_t)c * ld + n + cp], v);
+      }
+    }
+  }
+}
 
 template <typename A>
-__global__ void __launch_bounds__(256) k_cand_cc(Config cfg) {
-  __shared__ A Xs[32][33];
-  __shared__ A Vs[32][33];
+__global__ void __launch_bounds__(256, sizeof(A) == 4 ? 3 : 2) k_cand_cc(Config cfg) {
+  __shared__ A Xs[CC_KC][65];  // [column][c'], padded: conflict-free transposed stores
+  __shared__ A Vs[CC_KC][65];  // [column][c]
   for_each_item(
       2 * cfg.n_walkers,
       [&](int s) -> long long {
         const WalkerDev& w = cfg.W[s >> 1];
-        const long long t = (w.n_cand + 31) / 32;
+        const int ts = cc_tile(w.n_cand);
+        const long long t = (w.n_cand + ts - 1) / ts;
         return (w.active && w.n_cand > 0) ? t * t * ((w.n + CC_SEG - 1) / CC_SEG + (w.n == 0)) : 0;
       },
       [&](int s, int item) {
         const WalkerDev& w = cfg.W[s >> 1];
-        const int sp = s & 1, n = w.n, nc_ = w.n_cand, ld = w.cap, par = w.parity;
-        const int tiles = (nc_ + 31) / 32, segs = (n + CC_SEG - 1) / CC_SEG + (n == 0);
+        const int segs = (w.n + CC_SEG - 1) / CC_SEG + (w.n == 0);
         const int seg = item % segs, tile = item / segs;
-        const int cpb = (tile / tiles) * 32, cb = (tile - (tile / tiles) * tiles) * 32;
-        const int jlo = seg * CC_SEG, jhi = min(n, jlo + CC_SEG);
-        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-        const A* X = reinterpret_cast<const A*>(w.Xr[sp]);  // A is the storage type of N and X
-        const A* V = reinterpret_cast<const A*>(w.Vb[sp]);
-        A acc[4] = {(A)0, (A)0, (A)0, (A)0};
-        for (int j0 = jlo; j0 < jhi; j0 += 32) {
-          __syncthreads();
-          const int j = j0 + tx;
-          for (int r = ty; r < 32; r += 8) {
-            Xs[r][tx] = (cpb + r < nc_ && j < jhi) ? X[(size_t)(cpb + r) * ld + j] : (A)0;
-            Vs[r][tx] = (cb + r < nc_ && j < jhi) ? V[(size_t)(cb + r) * ld + j] : (A)0;
-          }
-          __syncthreads();
-#pragma unroll 8
-          for (int jj = 0; jj < 32; ++jj) {
-            const A v = Vs[tx][jj];
-#pragma unroll
-            for (int m = 0; m < 4; ++m) acc[m] += Xs[ty + 8 * m][jj] * v;
-          }
-        }
-        const int c = cb + tx;
-        if (c < nc_) {
-          const ProblemDev& pb = cfg.P[w.problem];
-          const int rc = w.vsite[par][n + c];
-          const double tc = w.vtau[par][n + c];
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            const int cp = cpb + ty + 8 * m;
-            if (cp < nc_) {
-              double v = (double)acc[m];
-              if (seg == 0)
-                v += (cp == c) ? g0_diag(pb, sp, rc)
-                               : g0_pair(pb, sp, w.vsite[par][n + cp], w.vtau[par][n + cp], rc, tc);
-              atomicAdd(&w.Gc[sp][(size_t)c * ld + n + cp], v);
-            }
-          }
-        }
+        if (cc_tile(w.n_cand) == 32) cand_cc_item<A, 32>(cfg, w, s & 1, tile, seg, Xs, Vs);
+        else cand_cc_item<A, 64>(cfg, w, s & 1, tile, seg, Xs, Vs);
       });
 }
 

@@ -105,6 +105,8 @@ int launch_meas_g4(const Config& cfg, int max_cap, int max_nc, cudaStream_t st);
 void launch_g4_assemble(int S, const double* A, const double* D, double sign_sum, const double* Gu, const double* Gd,
                         double* out, cudaStream_t st);
 void launch_ndft_copy(const Config& cfg, int max_nc, const long long* d_base, double* d_out, cudaStream_t st);
+// Every walker's tau-grid accumulator to d_out + d_base[walker] (one read-out copy).
+void launch_gather_G(const Config& cfg, int max_nc, const long long* d_base, double* d_out, cudaStream_t st);
 // Phase table of the measurement grid (ProblemDev::g0m) from the FP32 table g0f.
 void launch_meas_table(const ProblemDev& pd, int n_tau_meas, cudaStream_t st);
 // Every problem's staged table checked, committed (where finite) and its

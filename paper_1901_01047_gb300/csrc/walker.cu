@@ -88,6 +88,9 @@ struct dca_walker {
   int prec_public = 0;               // DCA_PREC_* given at create
   double* d_Mout = nullptr;          // read-out of the frequency measurement, all walkers
   long long* d_Mbase = nullptr;      // its per-walker offsets
+  double* d_Gout = nullptr;          // read-out of the tau-grid measurement, all walkers back to back
+  long long* d_Gbase = nullptr;      // its per-walker offsets (gacc_off)
+  double* h_Gout = nullptr;          // pinned host copy of d_Gout (one device-to-host copy per read-out)
   std::vector<int> problem_of;       // per walker
 
   ~dca_walker() {
@@ -106,6 +109,7 @@ struct dca_walker {
       if (p) cudaFree(p);
     if (h_active) cudaFreeHost(h_active);
     if (h_loop) cudaFreeHost(h_loop);
+    if (h_Gout) cudaFreeHost(h_Gout);
   }
 
   void* dalloc(size_t bytes) {
@@ -957,17 +961,37 @@ extern "C" DCA_API int dca_walker_update_G0_all(dca_walker* h, const double* G0_
 
 extern "C" DCA_API int dca_walker_measure_G(dca_walker* h, double* G_out, double* sign_sum_out, int64_t* n_meas_out) {
   if (!h) return DCA_ERR_ARG;
-  int rc = pull_records(h);
+  if (G_out) {
+    // every walker's accumulator gathered on the device into one buffer, one
+    // copy to pinned host memory (instead of one small copy per walker)
+    const size_t total = (size_t)h->gacc_off[h->W - 1] + (size_t)2 * h->nc_of[h->W - 1] * h->ntm;
+    if (!h->d_Gout) {
+      h->d_Gout = (double*)h->dalloc(sizeof(double) * total);
+      h->d_Gbase = (long long*)h->dalloc(sizeof(long long) * h->W);
+      if (!h->d_Gout || !h->d_Gbase) return fail(h, DCA_ERR_OOM, "read-out buffers of the tau-grid measurement");
+      if (cudaMallocHost(&h->h_Gout, sizeof(double) * total) != cudaSuccess) {
+        h->h_Gout = nullptr;
+        cudaGetLastError();
+        return fail(h, DCA_ERR_OOM, "pinned read-out buffer of the tau-grid measurement");
+      }
+      std::vector<long long> base(h->gacc_off.begin(), h->gacc_off.end());
+      CK(cudaMemcpyAsync(h->d_Gbase, base.data(), sizeof(long long) * h->W, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaStreamSynchronize(h->stream));  // base is a host temporary
+    }
+    dca::launch_gather_G(h->cfg, h->max_nc, h->d_Gbase, h->d_Gout, h->stream);
+    h->total_launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_Gout, h->d_Gout, sizeof(double) * total, cudaMemcpyDeviceToHost, h->stream));
+  }
+  int rc = pull_records(h);  // synchronises the stream (after the copy above)
   if (rc != DCA_OK) return rc;
+  if (G_out) std::memcpy(G_out, h->h_Gout, sizeof(double) * ((size_t)h->gacc_off[h->W - 1] +
+                                                            (size_t)2 * h->nc_of[h->W - 1] * h->ntm));
   for (int wi = 0; wi < h->W; ++wi) {
     const WalkerDev& w = h->h_W[wi];
-    if (G_out)
-      CK(cudaMemcpyAsync(G_out + h->gacc_off[wi], w.Gacc, sizeof(double) * 2 * h->nc_of[wi] * h->ntm,
-                         cudaMemcpyDeviceToHost, h->stream));
     if (sign_sum_out) sign_sum_out[wi] = w.sign_sum;
     if (n_meas_out) n_meas_out[wi] = w.n_meas;
   }
-  CK(cudaStreamSynchronize(h->stream));
   return DCA_OK;
 }
 

@@ -2,8 +2,9 @@
 
 The throughput figures are taken on a batch of many walkers of uneven order
 under the pooled schedule, mixed precision on the tensor cores, the batched
-recompute every 8 sweeps and autotuned k_s, with the captured window split
-into four concurrent branches (128 walkers or more).  Here that configuration
+recompute every 8 sweeps, autotuned k_s and a spin changed twice in a
+window applied in place, with the captured window split into four
+concurrent branches (128 walkers or more).  Here that configuration
 runs with a few of its walkers replaying the oracle's decisions (one walker
 in each branch, the largest at order >= 1000), k_s switched from 64 to 128
 part-way, and every replayed walker is compared with its own oracle chain:
@@ -110,7 +111,7 @@ def _replay_batch(probs, runs, warmup, ntm, init, target_walker, target_sweeps, 
                         recompute_sweeps=recompute_sweeps, warmup_sweeps=warmup, n_tau_meas=ntm, precision="mixed",
                         update_kernel="tcgen05", init_config_size=init, seed=seed, schedule=schedule,
                         log_capacity=1 << 26, recompute_at_measure=recompute_at_measure,
-                        stream=torch.cuda.current_stream().cuda_stream)
+                        duplicate_rule="update", stream=torch.cuda.current_stream().cuda_stream)
     for wi in replay:
         gw.set_forced_decisions(wi, runs[wi].log)
     max_order = {wi: 0 for wi in replay}
