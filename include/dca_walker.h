@@ -196,14 +196,22 @@ typedef struct {
 #define DCA_SCHEDULE_LOCKSTEP 0
 #define DCA_SCHEDULE_POOLED 1
 
-/* Recompute of N (the inverse of e^V - g0 (e^V - 1), Eq. Zk, formed from
- * scratch in FP64 for the current configuration):
- *   AUTO: DCA_PREC_FP64 inverts it by Gauss-Jordan with partial pivoting;
- *         DCA_PREC_MIXED applies one Newton step N <- N + N (I - A N) with the
- *         residual in FP64 (squares the relative error of the FP32 N).
- *   GJ:   Gauss-Jordan on both paths. */
+/* Recompute of N (the inverse of A = e^V - g0 (e^V - 1), Eq. Zk, formed
+ * from scratch in FP64 for the current configuration):
+ *   AUTO:      DCA_PREC_FP64 inverts it by Gauss-Jordan with partial
+ *              pivoting; the mixed paths apply one Newton step
+ *              N <- N + N (I - A N) whose residual I - A N is formed on the
+ *              tensor cores from exponent-aligned 9-bit digit planes of A (5)
+ *              and N (4), the leading plane products summed exactly (Ozaki
+ *              et al., Numer. Algorithms 59, 2012): about 2^-40 of the row /
+ *              column maxima, so the step brings the FP32 N back to its
+ *              rounding level.  Needs 18 cap^2 bytes per spin and walker.
+ *   GJ:        Gauss-Jordan on both paths.
+ *   NEWTON_DF: the mixed paths' Newton step with the residual in double-float
+ *              arithmetic on the CUDA cores (about 2^-44 of sum |A| |N|). */
 #define DCA_RECOMPUTE_AUTO 0
 #define DCA_RECOMPUTE_GJ 1
+#define DCA_RECOMPUTE_NEWTON_DF 2
 
 /* N-update kernels of the mixed-precision path (ignored by DCA_PREC_FP64). */
 #define DCA_UPD_AUTO 0       /* DCA_UPD_TCGEN05 */

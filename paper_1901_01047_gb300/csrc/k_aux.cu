@@ -549,6 +549,11 @@ int launch_recompute(int part, const Config& cfg, int max_cap, int* d_sgn, cudaS
       return 1;
     case GROUP_RECOMPUTE:
       if (cfg.prec == PREC_MIXED && !cfg.recompute_gj) {
+        if (cfg.recompute_oz) {
+          launch_refine_oz(cfg, max_cap, st);
+          launch_refine_correct(cfg, max_cap, st);
+          return 5;
+        }
         launch_refine_gemms(cfg, max_cap, st);
         return 2;
       }

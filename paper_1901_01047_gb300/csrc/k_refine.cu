@@ -232,6 +232,12 @@ void launch_refine_gemms(const Config& cfg, int max_cap, cudaStream_t st) {
   const long long t = (max_cap + RT - 1) / RT;
   const long long items = 2LL * cfg.n_walkers * t * t;
   k_refine_resid<<<persist_grid((const void*)k_refine_resid, items, 256), 256, 0, st>>>(cfg);
+  launch_refine_correct(cfg, max_cap, st);
+}
+
+void launch_refine_correct(const Config& cfg, int max_cap, cudaStream_t st) {
+  const long long t = (max_cap + RT - 1) / RT;
+  const long long items = 2LL * cfg.n_walkers * t * t;
   k_refine_correct<<<persist_grid((const void*)k_refine_correct, items, 256), 256, 0, st>>>(cfg);
 }
 

@@ -572,6 +572,21 @@ static bool encode_2d(TmapDev* out, void* base, uint64_t cols, uint64_t rows, ui
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// FP16 digit planes of the sliced recompute residual: `rows` rows of `cols`
+// FP16 values (row pitch cols * 2 bytes), boxes of 64 values (128 bytes) x
+// box_rows.
+static bool encode_2d_f16(TmapDev* out, void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {cols * 2};
+  const cuuint32_t box[2] = {64u, box_rows};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return fn(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int ext_tile_c(int ks) { return ks <= 64 ? 64 : 128; }
 
 bool encode_update_maps(const WalkerDev& w, int ks, int upd_bn, TmapDev* out) {
@@ -591,6 +606,10 @@ bool encode_update_maps(const WalkerDev& w, int ks, int upd_bn, TmapDev* out) {
     if (!encode_2d(m + 5, w.Bop[sp], C, 2 * (uint64_t)KS_MAX, C * 4, (uint32_t)ext_tile_c(ks))) return false;
     for (int par = 0; par < 2; ++par)
       if (!encode_2d(m + 6 + par, w.N[par][sp], C, C, C * 4, 32u)) return false;
+    // digit planes of the sliced recompute residual: N (4 planes, 128-row
+    // boxes, the MMA's M side) and A (5 planes, 64-row boxes)
+    if (w.OzN[sp] && !encode_2d_f16(m + 8, w.OzN[sp], C, 4 * C, 128u)) return false;
+    if (w.OzA[sp] && !encode_2d_f16(m + 9, w.OzA[sp], C, 5 * C, 64u)) return false;
   }
   return true;
 }

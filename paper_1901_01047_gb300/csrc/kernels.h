@@ -55,6 +55,12 @@ void launch_gj(const Config& cfg, int mode, int max_n, int* d_sgn, cudaStream_t 
 // the two products (R = I - A N0 in FP64, N1 = N0 + N0 R in FP32), then the
 // drift measurement and the copy of N1 into the other buffer.
 void launch_refine_gemms(const Config& cfg, int max_cap, cudaStream_t st);
+// N1 = N0 + N0 R (FP32), R from either residual.
+void launch_refine_correct(const Config& cfg, int max_cap, cudaStream_t st);
+// The residual R = I - A N0 by exponent-aligned digit slicing on the tensor
+// cores (four kernels).
+void launch_refine_oz(const Config& cfg, int max_cap, cudaStream_t st);
+cudaError_t setup_refine_tc();
 void launch_refine_adopt(const Config& cfg, int max_cap, cudaStream_t st);
 // part: GROUP_RECOMPUTE_PRE, GROUP_RECOMPUTE or GROUP_RECOMPUTE_POST.
 int launch_recompute(int part, const Config& cfg, int max_cap, int* d_sgn, cudaStream_t st);

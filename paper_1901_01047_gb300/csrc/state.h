@@ -127,6 +127,9 @@ struct WalkerDev {
   int32_t* vs[2];            // +1 / -1 interacting, 0 dead (non-interacting)
   void* N[2][2];             // [parity][spin] cap x cap, row-major, ld = cap; FP64 or FP32
   double* Ascr[2];           // [spin] cap x cap FP64 work matrix of the recompute (mixed only)
+  void* OzA[2];              // [spin][5][cap][cap] FP16 digit planes of the rows of A (sliced residual)
+  void* OzN[2];              // [spin][4][cap][cap] FP16 digit planes of the columns of N, transposed
+  int32_t* OzE[2];           // [spin][2][cap] their exponents: rows of A, columns of N
   int32_t* live_idx;         // [cap] rows of the live vertices, ascending
   int32_t* surv_tmp;         // [cap] scratch for rebuilding live_idx
   Proposal* prop;            // [KS_MAX]
@@ -197,8 +200,9 @@ struct PoolState {
 
 // TMA tensor maps per walker and spin: update operands A and B, N of parity 0
 // and 1 (128-row boxes), the candidate tables V and U of the tensor-core
-// extension, N of parity 0 and 1 in 32-row boxes (MN-major operand).
-constexpr int TMAPS_PER_SPIN = 8;
+// extension, N of parity 0 and 1 in 32-row boxes (MN-major operand), the
+// digit planes of the sliced recompute residual (N: 128-row boxes, A: 64).
+constexpr int TMAPS_PER_SPIN = 10;
 
 // Opaque copy of a TMA tensor map (CUtensorMap: 128 bytes, 64-byte aligned).
 struct alignas(64) TmapDev {
@@ -218,6 +222,7 @@ struct Config {
   int32_t recompute_every;
   int32_t recompute_sweeps;  // batched schedule: recompute every walker every this many sweeps
   int32_t recompute_gj;      // mixed path: Gauss-Jordan inverse instead of the Newton step
+  int32_t recompute_oz;      // mixed path: Newton residual by digit slicing on the tensor cores
   int32_t n_tau_meas;
   int32_t prec;              // PREC_FP64 or PREC_MIXED
   double tie_eps;

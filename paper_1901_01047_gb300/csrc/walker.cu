@@ -120,6 +120,11 @@ struct dca_walker {
   }
 };
 
+// The sliced residual lists its tiles (128 x 64 per walker-spin) in the
+// 12-bit sub-item field of a persistent CTA's work list; larger capacities
+// (n above ~5700) keep the double-float residual.
+static bool oz_fits(int cap) { return (long long)((cap + 127) / 128) * ((cap + 63) / 64) < 4096; }
+
 static int fail(dca_walker* w, int code, const std::string& msg) {
   if (w) w->err = msg;
   else g_create_error = msg;
@@ -194,7 +199,7 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     return fail(nullptr, DCA_ERR_ARG, "n_omega_meas must be 0 or in 8..4096");
   if (p.gamma_precision != DCA_GAMMA_FP64 && p.gamma_precision != DCA_GAMMA_DOUBLE_FLOAT)
     return fail(nullptr, DCA_ERR_ARG, "gamma_precision must be one of DCA_GAMMA_*");
-  if (p.recompute_method < DCA_RECOMPUTE_AUTO || p.recompute_method > DCA_RECOMPUTE_GJ)
+  if (p.recompute_method < DCA_RECOMPUTE_AUTO || p.recompute_method > DCA_RECOMPUTE_NEWTON_DF)
     return fail(nullptr, DCA_ERR_ARG, "recompute_method must be one of DCA_RECOMPUTE_*");
   if (p.update_kernel < DCA_UPD_AUTO || p.update_kernel > DCA_UPD_TCGEN05)
     return fail(nullptr, DCA_ERR_ARG, "update_kernel must be one of DCA_UPD_*");
@@ -397,6 +402,12 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
     }
     if (h->precision == DCA_PREC_MIXED)
       for (int sp = 0; sp < 2; ++sp) pieces.push_back({(void**)&w.Ascr[sp], sizeof(double) * C * C});
+    if (h->precision == DCA_PREC_MIXED && p.recompute_method == DCA_RECOMPUTE_AUTO && oz_fits(cap))
+      for (int sp = 0; sp < 2; ++sp) {  // digit planes of the sliced residual (FP16) and their exponents
+        pieces.push_back({(void**)&w.OzA[sp], 2 * 5 * C * C});
+        pieces.push_back({(void**)&w.OzN[sp], 2 * 4 * C * C});
+        pieces.push_back({(void**)&w.OzE[sp], sizeof(int32_t) * 2 * C});
+      }
     pieces.push_back({(void**)&w.prop, sizeof(dca::Proposal) * KS});
     for (int sp = 0; sp < 2; ++sp) {
       pieces.push_back({(void**)&w.Gc[sp], sizeof(double) * KS * C});
@@ -463,7 +474,8 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
       h->err = "TMA tensor maps of the tensor-core update";
       return bail(DCA_ERR_CUDA);
     }
-    if (dca::setup_update_tc() != cudaSuccess || dca::setup_ext_tc() != cudaSuccess) {
+    if (dca::setup_update_tc() != cudaSuccess || dca::setup_ext_tc() != cudaSuccess ||
+        dca::setup_refine_tc() != cudaSuccess) {
       h->err = "tensor-core update kernel attribute setup failed";
       return bail(DCA_ERR_CUDA);
     }
@@ -495,6 +507,8 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   h->cfg.gj_next = h->d_active + 3;
   h->cfg.recompute_sweeps = p.recompute_sweeps;
   h->cfg.recompute_gj = p.recompute_method == DCA_RECOMPUTE_GJ ? 1 : 0;
+  h->cfg.recompute_oz =
+      h->precision == DCA_PREC_MIXED && p.recompute_method == DCA_RECOMPUTE_AUTO && oz_fits(h->max_cap) ? 1 : 0;
   h->cfg.upd_kernel = use_tc ? dca::UPD_TCGEN05 : dca::UPD_CUDA_CORE;
   h->cfg.ext_tc = use_tc ? 1 : 0;  // the tcgen05 path covers the G_ext product of the extension too
   h->cfg.tmaps = h->d_tmaps;

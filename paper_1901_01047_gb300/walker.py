@@ -317,7 +317,7 @@ class Walkers:
         p.tie_eps = float(tie_eps)
         p.log_capacity = int(log_capacity)
         p.recompute_sweeps = int(recompute_sweeps)
-        p.recompute_method = {"auto": 0, "gj": 1}[recompute_method]
+        p.recompute_method = {"auto": 0, "gj": 1, "newton_df": 2}[recompute_method]
         p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
         p.gamma_precision = GAMMA_PRECISIONS[gamma_precision] if isinstance(gamma_precision, str) \
             else int(gamma_precision)

@@ -145,10 +145,11 @@ def test_mixed_batched_sweep_synchronised_recompute():
     gw.close()
 
 
-@pytest.mark.parametrize("method", ["auto", "gj"])
+@pytest.mark.parametrize("method", ["auto", "newton_df", "gj"])
 def test_mixed_recompute_methods_restore_accuracy(method):
-    # The Newton step (FP64 residual, FP32 correction) and the Gauss-Jordan
-    # inverse both bring N back to the FP32 level: recomputing every 8
+    # The Newton step (residual from digit planes on the tensor cores, or in
+    # double-float on the CUDA cores; FP32 correction) and the Gauss-Jordan
+    # inverse all bring N back to the FP32 level: recomputing every 8
     # submatrix updates keeps the error of N and G small on the 16-site case.
     errN, errG, st, _ = replay(16, -0.15, 6.0, 4.0, 2.85, 64, 60, 8, ntm=16, n_tau=2048, recompute_method=method)
     print("16 sites recompute %s every 8: N %.2e G %.2e drift %.2e" % (method, errN, errG, st["max_drift"]))
@@ -210,3 +211,20 @@ def test_tf32_single_product_replay_error():
     print("2x2 TF32 R=8: N %.2e G %.2e" % (errN, errG))
     assert st["status"] == 0
     assert 1e-4 < errN < 5e-2 and errG < 0.1
+
+
+@pytest.mark.parametrize("method", ["auto", "newton_df", "gj"])
+def test_recompute_methods_bring_N_to_its_fp32_rounding(method):
+    # N recomputed in the window that ends the last sweep: the state is the
+    # recompute's result, within the FP32 rounding of N times its conditioning
+    # for every method (the sliced residual's products are exact up to 2^-40
+    # of the row and column maxima).  16 sites at order ~150 (two 128-column
+    # and three 64-row tiles of the residual, a ragged K chunk) and the 2x2
+    # cluster at beta = 10.
+    for args, kw in [((16, -0.15, 6.0, 4.0, 2.85, 64, 60, 64), dict(ntm=16, n_tau=2048)),
+                     ((4, 0.0, 4.0, 10.0, 0.9450480104035819, 32, 200, 64), {})]:
+        errN, errG, st, gs = replay(*args, recompute_at_measure=True, recompute_method=method, return_state=True, **kw)
+        print("recompute %s, order %d: N %.2e G %.2e" % (method, gs["site"].size, errN, errG))
+        assert st["status"] == 0 and st["recomputes"] >= 10
+        assert errN < 1e-6, errN
+        assert errG < 1e-6, errG
