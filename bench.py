@@ -59,6 +59,16 @@ TF32_PER_BF16 = 1.1 / 2.25
 # at 4 / (2 / 7.32 + 2 / 80.5) TFLOP/s.
 FP32_INSTR_PER_S = 152 * 128 * 2.07e9
 MIXED_RECOMPUTE_TFLOPS = 4.0 / (2.0 / (FP32_INSTR_PER_S * 2 / 11 / 1e12) + 2.0 / (FP32_INSTR_PER_S * 2 / 1e12))
+# With the residual from digit planes on the tensor cores (the default), its
+# 2n^3 flop take 17 FP16 plane products of 2n^3 flop each at the measured
+# dense 16-bit tensor rate (the sustained BF16 figure: FP16 runs at the same
+# rate), the correction 2n^3 flop at the FP32 issue rate.
+OZ_PRODUCTS = 17
+
+
+def sliced_recompute_tflops(peaks):
+    p16 = peaks["bf16_tflops_sustained"]
+    return 4.0 / (2.0 * OZ_PRODUCTS / p16 + 2.0 / (FP32_INSTR_PER_S * 2 / 1e12))
 
 # DRAM bytes (read + write) per window of a kernel group from ncu captures of
 # the named workload (one window of the pooled schedule carries all walkers;
@@ -144,6 +154,7 @@ def config_of(wl, world):
             **({"freq_method": wl.freq_method} if wl.n_omega_meas else {}),
             **({"n_w4": wl.n_w4, "w4_transfer": wl.w4_transfer, "q4_transfer": wl.q4_transfer} if wl.n_w4 else {}),
             "precision": wl.precision, "schedule": wl.schedule, "duplicate_rule": wl.duplicate_rule,
+            "recompute_method": wl.recompute_method,
             "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)",
             **({"per_walker": {"nc": list(wl.nc_choices), "beta": list(wl.beta_range), "U": list(wl.U_range),
                                "mu": "U/2"}} if wl.nc_choices else {})}
@@ -382,7 +393,8 @@ def run_ours(args, rank, world, local_rank):
                         init_config_size=wl.init_config_size, seed=seed, schedule=wl.schedule,
                         recompute_at_measure=wl.recompute_at_measure, n_omega_meas=wl.n_omega_meas,
                         freq_method=wl.freq_method, n_w4=wl.n_w4, w4_transfer=wl.w4_transfer,
-                        q4_transfer=wl.q4_transfer, duplicate_rule=wl.duplicate_rule, stream=stream.cuda_stream)
+                        q4_transfer=wl.q4_transfer, duplicate_rule=wl.duplicate_rule,
+                        recompute_method=wl.recompute_method, stream=stream.cuda_stream)
     gw.sweep(wl.warmup_sweeps)            # the chain's own warm-up (no measurements)
     tuned = None
     if wl.autotune and not args.no_autotune:  # untimed; the trial sweeps are ordinary sweeps of the chains
@@ -488,7 +500,7 @@ def run_ours(args, rank, world, local_rank):
     # Timed region 2 (the roofline): the same steps driven from the host with
     # CUDA events on the walker's stream around the dominant kernel group and
     # around the N-update kernel.
-    gw.set_timing(sorted({dominant, "update"}))
+    gw.set_timing(sorted({dominant, "update", "recompute"}))
     st_k0 = gw.stats()
     for k in range(args.steps):
         flush.fill_(float(k))
@@ -543,6 +555,7 @@ def run_ours(args, rank, world, local_rank):
         roof_upd = roofline("update", gtimes["update"][0], windows, work, peaks, kind, wl)
         roof["traffic"] = NCU_TRAFFIC.get((wl.name, dominant))
         roof_upd["traffic"] = NCU_TRAFFIC.get((wl.name, "update"))
+        roof_rec = roofline("recompute", gtimes["recompute"][0], windows, work, peaks, kind, wl)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * seconds / args.steps, "higher_is_better": True,
@@ -564,6 +577,7 @@ def run_ours(args, rank, world, local_rank):
             "kernel_ms": {g: round(v[0], 4) for g, v in times.items()},
             "roofline": roof,
             "n_update_roofline": roof_upd,
+            "recompute_roofline": roof_rec,
             "orders": order_stats(st1),
             "recompute_tflops_fp64": rflops_all / seconds / 1e12,
             "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -610,6 +624,12 @@ def roofline(group, g_ms, windows, work, peaks, kind, wl):
     work_b, work_f = work[group]
     tfs = work_f / sec / 1e12
     if work_b is None:
+        if wl.precision == "mixed" and wl.recompute_method == "auto":
+            pk = sliced_recompute_tflops(peaks)
+            return {**base, "bound": "tensor", "achieved": tfs, "peak": pk, "unit": "TFLOP/s", "frac": tfs / pk,
+                    "peak_kind": "derived (%s): the residual's 2n^3 flop as %d FP16 plane products at the sustained "
+                                 "16-bit tensor rate, the correction's 2n^3 at the FP32 issue rate (152 SMs x 128 "
+                                 "lanes x 2.07 GHz)" % (kind, OZ_PRODUCTS)}
         if wl.precision == "mixed":
             return {**base, "bound": "alu", "achieved": tfs, "peak": MIXED_RECOMPUTE_TFLOPS, "unit": "TFLOP/s",
                     "frac": tfs / MIXED_RECOMPUTE_TFLOPS,

@@ -74,38 +74,47 @@ __device__ __forceinline__ int oz_exponent(float m) {
   return e + 1;
 }
 
-// Items per walker-spin: blocks of 8 rows of A (a warp per row), then blocks
-// of 256 columns of N0 (a thread per column).
+// Items per walker-spin: blocks of 8 rows of A (a warp per row), then
+// strips of 32 columns of N0 (8 row groups of 32 threads, one thread per
+// column and group, the group maxima combined in shared memory).
 __global__ void __launch_bounds__(256) k_oz_exp(Config cfg) {
+  __shared__ float s_m[8][32];
   for_each_item(
       2 * cfg.n_walkers,
       [&](int s) -> long long {
         const WalkerDev& w = cfg.W[s >> 1];
-        return oz_wants(w) ? blocks_of(w.n, 8) + blocks_of(w.n, 256) : 0;
+        return oz_wants(w) ? blocks_of(w.n, 8) + blocks_of(w.n, 32) : 0;
       },
       [&](int s, int item) {
         const WalkerDev& w = cfg.W[s >> 1];
         const int sp = s & 1, n = w.n, ld = w.cap;
         const int rb = (int)blocks_of(n, 8);
-        int* ea = w.OzE[sp];
-        int* eb = w.OzE[sp] + ld;
+        const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
         if (item < rb) {
-          const int i = item * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+          const int i = item * 8 + grp;
           if (i >= n) return;
           const float2* A = reinterpret_cast<const float2*>(w.Ascr[sp]) + (size_t)i * ld;
           float m = 0.0f;
           for (int k = lane; k < n; k += 32) m = fmaxf(m, fabsf(A[k].x));
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-          if (lane == 0) ea[i] = oz_exponent(m);
+          if (lane == 0) w.OzE[sp][i] = oz_exponent(m);
         } else {
-          const int j = (item - rb) * 256 + threadIdx.x;
-          if (j >= n) return;
+          // block-uniform branch: the strip's barrier is reached by every thread
+          const int j = (item - rb) * 32 + lane;
           const float* N0 = (const float*)w.N[w.parity][sp];
           float m = 0.0f;
+          if (j < n)
 #pragma unroll 4
-          for (int k = 0; k < n; ++k) m = fmaxf(m, fabsf(N0[(size_t)k * ld + j]));
-          eb[j] = oz_exponent(m);
+            for (int k = grp; k < n; k += 8) m = fmaxf(m, fabsf(N0[(size_t)k * ld + j]));
+          __syncthreads();  // the previous strip's reads of s_m are done
+          s_m[grp][lane] = m;
+          __syncthreads();
+          if (grp == 0 && j < n) {
+#pragma unroll
+            for (int g = 1; g < 8; ++g) m = fmaxf(m, s_m[g][lane]);
+            w.OzE[sp][ld + j] = oz_exponent(m);
+          }
         }
       });
 }
@@ -510,7 +519,7 @@ cudaError_t setup_refine_tc() {
 
 void launch_refine_oz(const Config& cfg, int max_cap, cudaStream_t st) {
   const long long S = 2LL * cfg.n_walkers;
-  k_oz_exp<<<persist_grid((const void*)k_oz_exp, S * (blocks_of(max_cap, 8) + blocks_of(max_cap, 256)), 256), 256,
+  k_oz_exp<<<persist_grid((const void*)k_oz_exp, S * (blocks_of(max_cap, 8) + blocks_of(max_cap, 32)), 256), 256,
              0, st>>>(cfg);
   k_oz_slice_a<<<persist_grid((const void*)k_oz_slice_a, S * blocks_of((long long)max_cap * max_cap, 256), 256), 256,
                  0, st>>>(cfg);

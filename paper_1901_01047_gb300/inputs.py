@@ -133,6 +133,9 @@ class Workload:
     # a spin changed twice in one window: "update" applies it in place, "abort"
     # ends the window there (both give the chain of single-spin updates)
     duplicate_rule: str = "update"
+    # recompute of N: "auto" (mixed: Newton step, residual from digit planes on
+    # the tensor cores), "newton_df" (residual in double-float), "gj"
+    recompute_method: str = "auto"
     precision: str = "fp64"
     # batched workloads: per-walker problems drawn from these ranges (seeded)
     nc_choices: Tuple[int, ...] = ()
