@@ -26,7 +26,6 @@ namespace dca {
 
 constexpr int RT = 64;   // output tile
 constexpr int RK = 16;   // K step of the FP64 product
-constexpr int RK32 = 32; // K step of the FP32 product
 
 __device__ __forceinline__ bool refine_wants(const WalkerDev& w) {
   return w.active && w.recompute_pending && w.status == ST_OK;
@@ -120,55 +119,97 @@ __global__ void __launch_bounds__(256) k_refine_resid(Config cfg) {
       });
 }
 
-// N1 = N0 + N0 R, FP32, into Ascr[sp] viewed as FP32 (ld = cap).
+// N1 = N0 + N0 R, FP32, into Ascr[sp] viewed as FP32 (ld = cap).  Item =
+// 128 x 128 output tile; thread (tx, ty) of 16 x 16 owns rows ty 4 + a +
+// 64 p and columns tx 4 + b + 64 q (a, b < 4; p, q < 2): 64 accumulators and
+// four 16-byte shared-memory reads per 64 FMAs.  The next K step's tiles are
+// loaded into registers while the current one is multiplied.
+constexpr int CT = 128;  // output tile
+constexpr int CK = 16;   // K step
+
 __global__ void __launch_bounds__(256) k_refine_correct(Config cfg) {
-  __shared__ float As[RK32][RT + 1];  // [k][i] of N0
-  __shared__ float Bs[RK32][RT];      // [k][j] of R
+  __shared__ __align__(16) float As[CK][CT + 4];  // [k][i] of N0
+  __shared__ __align__(16) float Bs[CK][CT + 4];  // [k][j] of R
   for_each_item(
-      2 * cfg.n_walkers, [&](int s) -> long long { return refine_tiles(cfg.W[s >> 1]); },
+      2 * cfg.n_walkers,
+      [&](int s) -> long long {
+        const WalkerDev& w = cfg.W[s >> 1];
+        const long long t = (w.n + CT - 1) / CT;
+        return refine_wants(w) ? t * t : 0;
+      },
       [&](int s, int item) {
         const WalkerDev& w = cfg.W[s >> 1];
         const int sp = s & 1, n = w.n, ld = w.cap;
-        const int tiles = (n + RT - 1) / RT;
-        const int i0 = (item / tiles) * RT, j0 = (item - (item / tiles) * tiles) * RT;
+        const int tiles = (n + CT - 1) / CT;
+        const int i0 = (item / tiles) * CT, j0 = (item - (item / tiles) * tiles) * CT;
         const float* N0 = (const float*)w.N[w.parity][sp];
         const float* R = (const float*)w.N[w.parity ^ 1][sp];
         float* N1 = (float*)w.Ascr[sp];
-        const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-        float acc[4][4];
+        const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+        float ra[8], rb[8];  // the next K step: A rows (k fastest), R rows (j fastest)
+        auto fetch = [&](int k0) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+          for (int q = 0; q < 8; ++q) {
+            const int e = tid + 256 * q;
+            const int ia = e >> 4, ka = e & 15;   // A: 128 rows x 16 k
+            ra[q] = (i0 + ia < n && k0 + ka < n) ? N0[(size_t)(i0 + ia) * ld + k0 + ka] : 0.0f;
+            const int kb = e >> 7, jb = e & 127;  // R: 16 k x 128 columns
+            rb[q] = (k0 + kb < n && j0 + jb < n) ? R[(size_t)(k0 + kb) * ld + j0 + jb] : 0.0f;
+          }
+        };
+        float acc[8][8];
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
-        for (int k0 = 0; k0 < n; k0 += RK32) {
-          __syncthreads();
-          for (int e = threadIdx.x; e < RT * RK32; e += 256) {
-            const int i = e / RK32, k = e - i * RK32;
-            As[k][i] = (i0 + i < n && k0 + k < n) ? N0[(size_t)(i0 + i) * ld + k0 + k] : 0.0f;
-            const int kk = e / RT, j = e - kk * RT;
-            Bs[kk][j] = (k0 + kk < n && j0 + j < n) ? R[(size_t)(k0 + kk) * ld + j0 + j] : 0.0f;
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+        fetch(0);
+        for (int k0 = 0; k0 < n; k0 += CK) {
+          __syncthreads();  // the previous K step (or item) is done with the tiles
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int e = tid + 256 * q;
+            As[e & 15][e >> 4] = ra[q];
+            Bs[e >> 7][e & 127] = rb[q];
           }
           __syncthreads();
-#pragma unroll 4
-          for (int k = 0; k < RK32; ++k) {
-            float av[4], bv[4];
+          if (k0 + CK < n) fetch(k0 + CK);
 #pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = As[k][ty + 16 * a];
+          for (int k = 0; k < CK; ++k) {
+            float av[8], bv[8];
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[k][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[k][64 + tx * 4]);
+            av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w;
+            av[4] = a1.x; av[5] = a1.y; av[6] = a1.z; av[7] = a1.w;
+            bv[0] = b0.x; bv[1] = b0.y; bv[2] = b0.z; bv[3] = b0.w;
+            bv[4] = b1.x; bv[5] = b1.y; bv[6] = b1.z; bv[7] = b1.w;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) bv[b] = Bs[k][tx + 16 * b];
+            for (int a = 0; a < 8; ++a)
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-              for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+              for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
           }
         }
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int i = i0 + ty + 16 * a;
+        for (int a = 0; a < 8; ++a) {
+          const int i = i0 + ty * 4 + (a & 3) + 64 * (a >> 2);
+          if (i >= n) continue;
 #pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int j = j0 + tx + 16 * b;
-            if (i < n && j < n) N1[(size_t)i * ld + j] = N0[(size_t)i * ld + j] + acc[a][b];
+          for (int q = 0; q < 2; ++q) {
+            const int j = j0 + tx * 4 + 64 * q;  // 16-byte aligned: ld and j0 are multiples of 4
+            const size_t o = (size_t)i * ld + j;
+            if (j + 3 < n) {
+              float4 v = *reinterpret_cast<const float4*>(N0 + o);
+              v.x += acc[a][4 * q];
+              v.y += acc[a][4 * q + 1];
+              v.z += acc[a][4 * q + 2];
+              v.w += acc[a][4 * q + 3];
+              *reinterpret_cast<float4*>(N1 + o) = v;
+            } else {
+#pragma unroll
+              for (int b = 0; b < 4; ++b)
+                if (j + b < n) N1[o + b] = N0[o + b] + acc[a][4 * q + b];
+            }
           }
         }
       });
@@ -236,7 +277,7 @@ void launch_refine_gemms(const Config& cfg, int max_cap, cudaStream_t st) {
 }
 
 void launch_refine_correct(const Config& cfg, int max_cap, cudaStream_t st) {
-  const long long t = (max_cap + RT - 1) / RT;
+  const long long t = (max_cap + CT - 1) / CT;
   const long long items = 2LL * cfg.n_walkers * t * t;
   k_refine_correct<<<persist_grid((const void*)k_refine_correct, items, 256), 256, 0, st>>>(cfg);
 }
