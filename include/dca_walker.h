@@ -112,7 +112,7 @@ typedef struct {
 typedef struct {
   int32_t n_problems;              /* >= 1 */
   const dca_problem* problems;     /* host [n_problems] */
-  int32_t n_walkers;               /* >= 1 */
+  int32_t n_walkers;               /* 1 .. 16383 */
   const int32_t* walker_problem;   /* host [n_walkers] problem index per walker, or NULL
                                       for walker w -> problem w % n_problems */
   int32_t k_sub;                   /* proposals per submatrix update, 1..128

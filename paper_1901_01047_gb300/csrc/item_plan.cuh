@@ -14,7 +14,9 @@
 
 namespace dca {
 
-constexpr int PLAN_SUB_BITS = 12;  // sub-item field of a list entry (row blocks of a set < 4096)
+// sub-item field of a list entry (items of a set < 65536); the set index takes
+// the 15 bits above it, so a list serves fewer than 32768 sets (walker-spins)
+constexpr int PLAN_SUB_BITS = 16;
 
 // ITEMS listed items per CTA; CHUNK sets counted and scanned per pass.
 template <int ITEMS, int CHUNK>

@@ -121,9 +121,9 @@ struct dca_walker {
 };
 
 // The sliced residual lists its tiles (128 x 64 per walker-spin) in the
-// 12-bit sub-item field of a persistent CTA's work list; larger capacities
-// (n above ~5700) keep the double-float residual.
-static bool oz_fits(int cap) { return (long long)((cap + 127) / 128) * ((cap + 63) / 64) < 4096; }
+// 16-bit sub-item field of a persistent CTA's work list; larger capacities
+// (n above ~23000) keep the double-float residual.
+static bool oz_fits(int cap) { return (long long)((cap + 127) / 128) * ((cap + 63) / 64) < 65536; }
 
 static int fail(dca_walker* w, int code, const std::string& msg) {
   if (w) w->err = msg;
@@ -180,6 +180,8 @@ extern "C" DCA_API int dca_walker_create(const dca_walker_params* prm, void* cud
   const dca_walker_params& p = *prm;
   if (p.n_problems < 1 || !p.problems) return fail(nullptr, DCA_ERR_ARG, "need at least one problem");
   if (p.n_walkers < 1) return fail(nullptr, DCA_ERR_ARG, "n_walkers must be >= 1");
+  if (p.n_walkers > 16383)  // the work lists of the persistent kernels index walker-spins in 15 bits
+    return fail(nullptr, DCA_ERR_ARG, "n_walkers must be <= 16383");
   if (p.k_sub < 1 || p.k_sub > dca::KS_MAX) return fail(nullptr, DCA_ERR_ARG, "k_sub must be in 1..128");
   if (p.recompute_sweeps < 0 || p.recompute_every < 0 || p.warmup_sweeps < 0 || p.n_tau_meas < 1 || p.init_config_size < 0 ||
       p.capacity < 0 || p.log_capacity < 0 || p.recompute_at_measure < 0 || p.recompute_at_measure > 1 ||

@@ -74,7 +74,7 @@ def _params(walker, **over):
 
 
 @pytest.mark.parametrize("field,value", [
-    ("k_sub", 0), ("k_sub", 129), ("n_walkers", 0), ("n_tau_meas", 0), ("init_config_size", -1),
+    ("k_sub", 0), ("k_sub", 129), ("n_walkers", 0), ("n_walkers", 16384), ("n_tau_meas", 0), ("init_config_size", -1),
     ("precision", 99), ("K", 0.0), ("beta", -1.0), ("U", -1.0), ("n_problems", 0), ("gamma_precision", 7),
     ("schedule", 5), ("update_kernel", 9), ("recompute_method", 4), ("n_w4", 33), ("n_w4", -1),
     ("duplicate_rule", 3), ("duplicate_rule", -1),
