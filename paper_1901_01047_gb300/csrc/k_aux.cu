@@ -348,7 +348,7 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
   const int x = item / tblocks, a0 = (item - x * tblocks) * MT;
   constexpr bool kGrid = sizeof(A) == 4;
   __shared__ A As[MT][MK + 1];
-  __shared__ A Bs[MK][MR + 1];
+  __shared__ __align__(16) A Bs[MK][MR];  // rows of MR values: a thread's MR / 4 sites are contiguous
   __shared__ GridTime s_ga[MT], s_gi[MK];
   __shared__ int s_row[MK];  // table row of g0(x - r_i, .), -1 for a dead vertex
   __shared__ int s_ph[MK], s_mb[MK];  // phase-table path: phase p_i and m offset of vertex i
@@ -356,10 +356,16 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
   const int q = kGrid ? pb.meas_q : 0;
   const int tid = threadIdx.x;
   const int ta = tid & (MT - 1), tr = tid >> 6;  // 4 groups of reference sites
-  // products summed in A within a tile of MK vertices, tile sums in FP64
+  // products summed in A within a tile of MK vertices; the tile sums in FP64
+  // (FP64 path) or in double-float (FP32 path: an error-free FP32 two-sum per
+  // tile instead of a conversion and an add on GB300's scarce FP64 units)
   double tot[MR / 4];
+  float th[MR / 4], tl[MR / 4];
 #pragma unroll
-  for (int m = 0; m < MR / 4; ++m) tot[m] = 0.0;
+  for (int m = 0; m < MR / 4; ++m) {
+    tot[m] = 0.0;
+    th[m] = tl[m] = 0.0f;
+  }
   const int* vsite = w.vsite[par];
   const double* vtau = w.vtau[par];
   const int* vs = w.vs[par];
@@ -440,20 +446,44 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
 #pragma unroll 4
     for (int k = 0; k < MK; ++k) {
       const A g = As[ta][k];
+      // sites MR/4 tr .. MR/4 tr + MR/4 - 1: the same row segment for the whole
+      // warp (a broadcast), read as 16-byte vectors on the FP32 path
+      if constexpr (sizeof(A) == 4) {
 #pragma unroll
-      for (int m = 0; m < MR / 4; ++m) acc[m] += g * Bs[k][tr + 4 * m];
+        for (int m4 = 0; m4 < MR / 16; ++m4) {
+          const float4 b = *reinterpret_cast<const float4*>(&Bs[k][tr * (MR / 4) + 4 * m4]);
+          acc[4 * m4] += g * b.x;
+          acc[4 * m4 + 1] += g * b.y;
+          acc[4 * m4 + 2] += g * b.z;
+          acc[4 * m4 + 3] += g * b.w;
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < MR / 4; ++m) acc[m] += g * Bs[k][tr * (MR / 4) + m];
+      }
     }
+    if constexpr (sizeof(A) == 4) {
 #pragma unroll
-    for (int m = 0; m < MR / 4; ++m) tot[m] += (double)acc[m];
+      for (int m = 0; m < MR / 4; ++m) {
+        const float s1 = __fadd_rn(th[m], (float)acc[m]);
+        const float bb = __fsub_rn(s1, th[m]);
+        tl[m] += __fadd_rn(__fsub_rn(th[m], __fsub_rn(s1, bb)), __fsub_rn((float)acc[m], bb));
+        th[m] = s1;
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < MR / 4; ++m) tot[m] += (double)acc[m];
+    }
   }
   const int a = a0 + ta;
   if (a < ntm) {
 #pragma unroll
     for (int m = 0; m < MR / 4; ++m) {
-      const int rp = tr + 4 * m;
+      const int rp = tr * (MR / 4) + m;
       if (rp < nc) {
         const int d = __ldg(pb.site_sub + x * nc + rp);
-        atomicAdd(&w.Gtmp[((size_t)sp * nc + d) * ntm + a], tot[m]);
+        const double v = sizeof(A) == 4 ? (double)th[m] + (double)tl[m] : tot[m];
+        atomicAdd(&w.Gtmp[((size_t)sp * nc + d) * ntm + a], v);
       }
     }
   }

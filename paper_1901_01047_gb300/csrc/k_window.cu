@@ -1301,13 +1301,23 @@ __global__ void __launch_bounds__(256) k_upd_border(Config cfg) {
       // FP64-grade on both paths: the new row X + L'R is formed with
       // cancellation (double-float on the mixed path)
       if (sizeof(A) == 4) {
+        // two independent double-float chains (even and odd p), joined by an
+        // error-free sum: the latency of one dependent chain of l terms halves
         const float2* L = reinterpret_cast<const float2*>(w.Lp[sp]) + (size_t)(n + c) * KS_MAX;
-        float hi = reinterpret_cast<const float*>(w.Xr[sp])[(size_t)c * ld + j], lo = 0.f;
-        for (int p = 0; p < l; ++p) {
+        float hi = reinterpret_cast<const float*>(w.Xr[sp])[(size_t)c * ld + j], lo = 0.f, hi2 = 0.f, lo2 = 0.f;
+        int p = 0;
+        for (; p + 1 < l; p += 2) {
+          const float2 a = L[p], b = L[p + 1];
+          df_fma(hi, lo, a.x, a.y, (float)Rr[(size_t)p * ld + j], 0.f);
+          df_fma(hi2, lo2, b.x, b.y, (float)Rr[(size_t)(p + 1) * ld + j], 0.f);
+        }
+        if (p < l) {
           const float2 a = L[p];
           df_fma(hi, lo, a.x, a.y, (float)Rr[(size_t)p * ld + j], 0.f);
         }
-        stN(N, (size_t)(n + m) * ld + j, (double)__fadd_rn(hi, lo));
+        const float s1 = __fadd_rn(hi, hi2), bb = __fsub_rn(s1, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s1, bb)), __fsub_rn(hi2, bb));
+        stN(N, (size_t)(n + m) * ld + j, (double)__fadd_rn(s1, __fadd_rn(__fadd_rn(lo, lo2), err)));
       } else {
         const double* L = w.Lp[sp] + (size_t)(n + c) * KS_MAX;
         double acc = w.Xr[sp][(size_t)c * ld + j];
