@@ -525,7 +525,9 @@ def run_ours(args, rank, world, local_rank):
     # End to end through the public API with host buffers: every problem's bare
     # propagator uploaded from pinned memory (the per-iteration input of an
     # outer DCA loop; validated on the device), one step, and every walker's
-    # G read back, every step.
+    # G read back, every step.  The upload of step k + 1's tables is issued
+    # while step k's sweep runs (the library copies on its own stream and
+    # commits the tables after that sweep), as a pipelined caller would.
     G0_host = torch.from_numpy(np.concatenate([np.ascontiguousarray(p["G0"], np.float64).reshape(-1)
                                                for p in probs])).pin_memory()
     G0_np = G0_host.numpy()
@@ -536,9 +538,13 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     torch.cuda.synchronize()
     te0 = time.perf_counter()
+    gw.update_G0_all(G0_np)  # the first step's tables
     for k in range(args.steps):
-        gw.update_G0_all(G0_np)  # one copy of every problem's table, checked and committed on the device
         gw.sweep(1, sync=False)
+        if k + 1 < args.steps:
+            # the next step's tables: one copy of every problem's table (overlapping
+            # this step's sweep), checked and committed on the device after it
+            gw.update_G0_all(G0_np)
         gw.measure_G()  # synchronises
     gw.sync()
     torch.cuda.synchronize()

@@ -509,9 +509,12 @@ DCA_API int dca_walker_update_G0(dca_walker* w, int32_t problem, const double* G
  * concatenation of every problem's table in problem order (problem p:
  * [2][nc_p][n_tau_p + 1], as for dca_walker_update_G0).  One copy to the
  * staging buffers (pinned host memory makes it asynchronous) and three
- * kernels for all problems, stream-ordered like dca_walker_update_G0 (with
- * pinned memory the host array must stay unchanged until the stream has
- * passed the copy, e.g. until the next dca_walker_sync); a
+ * kernels for all problems, stream-ordered like dca_walker_update_G0: the
+ * copy itself runs on a stream of the handle, so it overlaps the sweeps
+ * enqueued before the call, and the kernels that take the tables wait for it
+ * on the walker's stream (with pinned memory the host array must stay
+ * unchanged until the stream has passed the copy, e.g. until the next
+ * dca_walker_sync); a
  * problem whose table has a non-finite entry keeps its previous table (the
  * others are taken) and the next dca_walker_sync returns DCA_ERR_ARG. */
 DCA_API int dca_walker_update_G0_all(dca_walker* w, const double* G0_all);

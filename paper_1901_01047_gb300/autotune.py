@@ -13,7 +13,7 @@ tile of the tensor-core N update (32 or 64 columns of N per tile, for k_s <=
 """
 import itertools
 
-KS_CANDIDATES = (16, 32, 64, 128)
+KS_CANDIDATES = (16, 32, 48, 64, 96, 128)
 KERNEL_CANDIDATES = ("tcgen05", "cuda_core")
 TILE_CANDIDATES = (64, 32)
 

@@ -75,6 +75,11 @@ struct dca_walker {
   cudaStream_t cap_stream = nullptr;
   cudaStream_t cap_br[4] = {nullptr, nullptr, nullptr, nullptr};  // branches of the captured window
   cudaEvent_t ev_fork = nullptr, ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
+  // dca_walker_update_G0_all: the host-to-device copy runs on its own stream,
+  // so that it overlaps the sweeps already enqueued; the walker's stream waits
+  // for it (staged) and the next copy waits for the commit (stage free)
+  cudaStream_t g0_stream = nullptr;
+  cudaEvent_t ev_g0_staged = nullptr, ev_g0_free = nullptr;
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;
   dca::LoopState* d_loop = nullptr;
@@ -98,6 +103,10 @@ struct dca_walker {
     if (loop_exec) cudaGraphExecDestroy(loop_exec);
     if (loop_graph) cudaGraphDestroy(loop_graph);
     if (ev_fork) cudaEventDestroy(ev_fork);
+    if (g0_stream) cudaStreamSynchronize(g0_stream);
+    if (ev_g0_staged) cudaEventDestroy(ev_g0_staged);
+    if (ev_g0_free) cudaEventDestroy(ev_g0_free);
+    if (g0_stream) cudaStreamDestroy(g0_stream);
     for (int b = 0; b < 4; ++b) {
       if (ev_join[b]) cudaEventDestroy(ev_join[b]);
       if (cap_br[b]) cudaStreamDestroy(cap_br[b]);
@@ -954,6 +963,8 @@ extern "C" DCA_API int dca_walker_update_G0(dca_walker* h, int32_t problem, cons
     dca::launch_meas_table(pd, h->ntm, h->stream);
     h->total_launches += 1;
   }
+  // the staging buffer has been read: a later dca_walker_update_G0_all copy may overwrite it
+  if (h->ev_g0_free) CK(cudaEventRecord(h->ev_g0_free, h->stream));
   // N of the walkers on this problem is rebuilt for the new table (only if it changed)
   h->total_launches += dca::launch_rebuild_changed(h->cfg, h->max_cap, h->d_g0_changed, h->d_sgn, h->stream);
   CK(cudaGetLastError());
@@ -963,12 +974,24 @@ extern "C" DCA_API int dca_walker_update_G0(dca_walker* h, int32_t problem, cons
 extern "C" DCA_API int dca_walker_update_G0_all(dca_walker* h, const double* G0_all) {
   if (!h || !G0_all) return DCA_ERR_ARG;
   const int np = (int)h->h_P.size();
+  if (!h->g0_stream) {
+    CK(cudaStreamCreateWithFlags(&h->g0_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_g0_staged, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_g0_free, cudaEventDisableTiming));
+    CK(cudaEventRecord(h->ev_g0_free, h->stream));  // the staging buffers are free after the work enqueued so far
+  }
+  // the copy overlaps the work already on the walker's stream; the previous
+  // commit has read the staging buffers before it starts
+  CK(cudaStreamWaitEvent(h->g0_stream, h->ev_g0_free, 0));
   CK(cudaMemcpyAsync(h->g0_stage[0], G0_all, sizeof(double) * h->g0_stage_doubles, cudaMemcpyHostToDevice,
-                     h->stream));
+                     h->g0_stream));
+  CK(cudaEventRecord(h->ev_g0_staged, h->g0_stream));
+  CK(cudaStreamWaitEvent(h->stream, h->ev_g0_staged, 0));
   CK(cudaMemsetAsync(h->d_g0_bad, 0, sizeof(int) * np, h->stream));
   CK(cudaMemsetAsync(h->d_g0_changed, 0, sizeof(int) * np, h->stream));
   dca::launch_g0_update_all(h->d_P, np, h->ntm, h->g0_stage[0], h->d_stage_off, h->d_g0_bad, h->d_active + 7,
                             h->d_g0_changed, h->stream);
+  CK(cudaEventRecord(h->ev_g0_free, h->stream));
   h->total_launches += 3;
   h->total_launches += dca::launch_rebuild_changed(h->cfg, h->max_cap, h->d_g0_changed, h->d_sgn, h->stream);
   CK(cudaGetLastError());

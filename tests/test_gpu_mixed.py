@@ -100,12 +100,14 @@ def test_mixed_free_run_follows_the_oracle_for_a_long_stretch():
     assert first > 2000, first
 
 
-@pytest.mark.parametrize("k_sub,tile", [(16, 64), (16, 32), (64, 64), (64, 32), (128, 0)])
+@pytest.mark.parametrize("k_sub,tile", [(16, 64), (16, 32), (48, 64), (64, 64), (64, 32), (96, 0), (128, 0)])
 def test_tensor_core_update_matches_cuda_core_update(k_sub, tile):
     # Same forced trajectory, no recompute: the 3xTF32 tcgen05 update and the
     # FP32 CUDA-core update differ only by rounding.  k_sub covers the three
-    # K extents of the tensor-core kernel (32, 64, 128), tile both column
-    # tiles of N, and n spans several 128-row blocks with a ragged tail.
+    # K extents of the tensor-core kernel (32, 64, 128), each also with a
+    # window that fills it only in part (48, 96: the autotuner's other
+    # sizes), tile both column tiles of N, and n spans several 128-row blocks
+    # with a ragged tail.
     args = (16, -0.15, 6.0, 6.0, 2.85, k_sub, 30, 0)
     eN_c, eG_c, st_c, gs_c = replay(*args, ntm=16, n_tau=2048, update_kernel="cuda_core", return_state=True)
     eN_t, eG_t, st_t, gs_t = replay(*args, ntm=16, n_tau=2048, update_kernel="tcgen05", return_state=True,
