@@ -572,7 +572,7 @@ def run_ours(args, rank, world, local_rank):
                                         "update_tile": tuned["update_tile"],
                                         "updates_per_s": {"%d/%s" % (r["k_sub"], r["update_kernel"]):
                                                           round(r["updates_per_s"]) for r in tuned["table"]},
-                                        "tile_updates_per_s": {str(r["update_tile"]): round(r["updates_per_s"])
+                                        "tile_update_group_updates_per_s": {str(r["update_tile"]): round(r["updates_per_s"])
                                                                for r in tuned["tiles"]}}}
                           if tuned else {})},
             "final_order": st1[0]["order"],

@@ -9,7 +9,7 @@ with CUDA events on the walker's stream around whole sweeps, and leaves the
 walkers on the fastest candidate.  The chains simply continue: each trial
 sweep is an ordinary sweep of the run.  After k_s and the kernel, the column
 tile of the tensor-core N update (32 or 64 columns of N per tile, for k_s <=
-64) is timed the same way.
+64) is chosen by the device time of the N-update kernel group alone.
 """
 import itertools
 
@@ -39,6 +39,22 @@ def _time_sweeps(gw, sweeps, stream, tries=3):
     return (sum(x["proposals"] for x in s) - p0) / (ms / 1000.0), ms
 
 
+def _time_group(gw, group, sweeps):
+    """Proposals per second of one kernel group's own device time (CUDA
+    events around the group on the walker's stream) over `sweeps` sweeps: the
+    column tile changes only the N update, whose share of a whole sweep is
+    below the sweep-to-sweep spread of the measurements and recomputes."""
+    gw.set_timing([group])
+    gw.timing(reset=True)
+    p0 = sum(x["proposals"] for x in gw.stats())
+    gw.sweep(sweeps)
+    t, _ = gw.timing(reset=True)
+    props = sum(x["proposals"] for x in gw.stats()) - p0
+    gw.set_timing([])
+    ms = t[group][0]
+    return props / (ms / 1000.0) if ms > 0 else 0.0, ms
+
+
 def tune(gw, precision, ks_candidates=KS_CANDIDATES, kernels=KERNEL_CANDIDATES, sweeps=2, settle=1):
     """Time each (k_s, kernel) candidate on the walkers `gw` and select the
     fastest.  Returns {"k_sub": .., "update_kernel": .., "table": [...]}.
@@ -63,7 +79,7 @@ def tune(gw, precision, ks_candidates=KS_CANDIDATES, kernels=KERNEL_CANDIDATES, 
             gw.set_update_tile(bn)
             if settle:
                 gw.sweep(settle)
-            rate, ms = _time_sweeps(gw, sweeps, stream)
+            rate, ms = _time_group(gw, "update", 2 * sweeps)
             tiles.append({"update_tile": bn, "updates_per_s": rate, "ms": ms})
         tile = max(tiles, key=lambda r: r["updates_per_s"])["update_tile"]
         gw.set_update_tile(tile)

@@ -339,20 +339,26 @@ __global__ void __launch_bounds__(256) k_meas_gemm(Config cfg) {
       [&](int s, int item) { meas_gemm_item<A, MR>(cfg, s >> 1, s & 1, item); });
 }
 
+// Item = (reference site x, MT tau points): the tiles of MK vertices pass
+// through shared memory.  On the FP32 path in two stages: while the tile t
+// is multiplied, the table values of tile t + 1 are filled in and the vertex
+// records of tile t + 2 prepared, one barrier per tile; the FP64 path keeps
+// one stage (its tiles would not fit twice in static shared memory).
 template <typename A, int MR>
 __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp, int item) {
+  constexpr bool kGrid = sizeof(A) == 4;
+  constexpr int NS = kGrid ? 2 : 1;  // stages
   const WalkerDev& w = cfg.W[wi];
   const ProblemDev& pb = cfg.P[w.problem];
   const int nc = pb.nc, ntm = cfg.n_tau_meas, n = w.n, par = w.parity, ld = w.cap;
   const int tblocks = (ntm + MT - 1) / MT;
   const int x = item / tblocks, a0 = (item - x * tblocks) * MT;
-  constexpr bool kGrid = sizeof(A) == 4;
-  __shared__ A As[MT][MK + 1];
-  __shared__ __align__(16) A Bs[MK][MR];  // rows of MR values: a thread's MR / 4 sites are contiguous
-  __shared__ GridTime s_ga[MT], s_gi[MK];
-  __shared__ int s_row[MK];  // table row of g0(x - r_i, .), -1 for a dead vertex
-  __shared__ int s_ph[MK], s_mb[MK];  // phase-table path: phase p_i and m offset of vertex i
-  __shared__ float s_fw[MK];          // and its interpolation weight
+  __shared__ A As[NS][MT][MK + 1];
+  __shared__ __align__(16) A Bs[NS][MK][MR];  // rows of MR values: a thread's MR / 4 sites are contiguous
+  __shared__ GridTime s_ga[MT], s_gi[NS][MK];
+  __shared__ int s_row[NS][MK];               // table row of g0(x - r_i, .), -1 for a dead vertex
+  __shared__ int s_ph[NS][MK], s_mb[NS][MK];  // phase-table path: phase p_i and m offset of vertex i
+  __shared__ float s_fw[NS][MK];              // and its interpolation weight
   const int q = kGrid ? pb.meas_q : 0;
   const int tid = threadIdx.x;
   const int ta = tid & (MT - 1), tr = tid >> 6;  // 4 groups of reference sites
@@ -371,28 +377,29 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
   const int* vs = w.vs[par];
   const int np1 = pb.n_tau + 1;
   const double* row_base = pb.g0 + (size_t)sp * nc * np1;
-  __syncthreads();  // the previous item of this block is done with the shared tiles
-  if (kGrid && tid < MT) s_ga[tid] = grid_time(((double)(a0 + tid) + 0.5) * pb.beta / (double)ntm, pb.tau_scale);
-  for (int i0 = 0; i0 < n; i0 += MK) {
-    __syncthreads();
+
+  // vertex records of the tile at i0 into stage b (threads tid < MK)
+  auto prep = [&](int i0, int b) {
     if (tid < MK) {
       const int i = i0 + tid;
       const bool live = i < n && vs[i] != 0;
-      s_row[tid] = live ? __ldg(pb.site_sub + x * nc + vsite[i]) : -1;
+      s_row[b][tid] = live ? __ldg(pb.site_sub + x * nc + vsite[i]) : -1;
       if (kGrid && live) {
         const GridTime gi = grid_time(vtau[i], pb.tau_scale);
-        s_gi[tid] = gi;
+        s_gi[b][tid] = gi;
         if (q > 0) {
           // grid offset of tau_a - tau_i: l = q a + c, c = q/2 - gi.i - (gi.f > 0), weight 1 - gi.f
           const int c = q / 2 - gi.i - (gi.f > 0.0f ? 1 : 0);
           const int p = ((c % q) + q) % q;
-          s_ph[tid] = p;
-          s_mb[tid] = (c - p) / q;
-          s_fw[tid] = gi.f > 0.0f ? 1.0f - gi.f : 0.0f;
+          s_ph[b][tid] = p;
+          s_mb[b][tid] = (c - p) / q;
+          s_fw[b][tid] = gi.f > 0.0f ? 1.0f - gi.f : 0.0f;
         }
       }
     }
-    __syncthreads();
+  };
+  // table values g0(x - r_i, tau_a - tau_i) and the rows b_i of the tile at i0 into stage b
+  auto fill = [&](int i0, int b) {
     if (q > 0) {
       // phase table: consecutive threads take consecutive tau points of one
       // vertex, i.e. consecutive entries of one phase row
@@ -400,11 +407,11 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
       const float* gm = pb.g0m + (size_t)sp * q * nc * mrow;
       for (int e = tid; e < MT * MK; e += 256) {
         const int il = e / MT, al = e - il * MT;
-        const int a = a0 + al, d = s_row[il];
+        const int a = a0 + al, d = s_row[b][il];
         A v = (A)0;
         if (a < ntm && d >= 0) {
-          const int p = s_ph[il];
-          int m = a + s_mb[il];
+          const int p = s_ph[b][il];
+          int m = a + s_mb[b][il];
           float sgn = 1.0f;
           if (m < 0) {  // tau_a - tau_i < 0: antiperiodic continuation
             m += ntm;
@@ -413,53 +420,55 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
           const float lo = __ldg(gm + ((size_t)p * nc + d) * mrow + m);
           const float hi = p + 1 < q ? __ldg(gm + ((size_t)(p + 1) * nc + d) * mrow + m)
                                      : __ldg(gm + (size_t)d * mrow + m + 1);
-          v = (A)(sgn * (lo + s_fw[il] * (hi - lo)));
+          v = (A)(sgn * (lo + s_fw[b][il] * (hi - lo)));
         }
-        As[al][il] = v;
+        As[b][al][il] = v;
       }
     } else {
       for (int e = tid; e < MT * MK; e += 256) {
         const int al = e / MK, il = e - al * MK;
-        const int a = a0 + al, d = s_row[il];
+        const int a = a0 + al, d = s_row[b][il];
         A v = (A)0;
         if (a < ntm && d >= 0) {
           const double* row = row_base + (size_t)d * np1;
           if (kGrid) {
-            v = (A)g0_interp_grid(g0f_row(pb, sp, d), pb.n_tau, s_ga[al], s_gi[il]);
+            v = (A)g0_interp_grid(g0f_row(pb, sp, d), pb.n_tau, s_ga[al], s_gi[b][il]);
           } else {
             const double ta_ = ((double)a + 0.5) * pb.beta / (double)ntm;
             v = (A)g0_interp(row, pb.n_tau, pb.beta, pb.tau_scale, ta_ - vtau[i0 + il]);
           }
         }
-        As[al][il] = v;
+        As[b][al][il] = v;
       }
     }
     for (int e = tid; e < MK * MR; e += 256) {
       const int il = e / MR, rp = e - il * MR;
       const int i = i0 + il;
-      Bs[il][rp] = (i < n && rp < nc) ? reinterpret_cast<const A*>(w.bvec)[((size_t)sp * nc + rp) * ld + i] : (A)0;
+      Bs[b][il][rp] = (i < n && rp < nc) ? reinterpret_cast<const A*>(w.bvec)[((size_t)sp * nc + rp) * ld + i] : (A)0;
     }
-    __syncthreads();
+  };
+  // products of stage b, added to the tile sums
+  auto compute = [&](int b) {
     A acc[MR / 4];
 #pragma unroll
     for (int m = 0; m < MR / 4; ++m) acc[m] = (A)0;
 #pragma unroll 4
     for (int k = 0; k < MK; ++k) {
-      const A g = As[ta][k];
+      const A g = As[b][ta][k];
       // sites MR/4 tr .. MR/4 tr + MR/4 - 1: the same row segment for the whole
       // warp (a broadcast), read as 16-byte vectors on the FP32 path
       if constexpr (sizeof(A) == 4) {
 #pragma unroll
         for (int m4 = 0; m4 < MR / 16; ++m4) {
-          const float4 b = *reinterpret_cast<const float4*>(&Bs[k][tr * (MR / 4) + 4 * m4]);
-          acc[4 * m4] += g * b.x;
-          acc[4 * m4 + 1] += g * b.y;
-          acc[4 * m4 + 2] += g * b.z;
-          acc[4 * m4 + 3] += g * b.w;
+          const float4 bv = *reinterpret_cast<const float4*>(&Bs[b][k][tr * (MR / 4) + 4 * m4]);
+          acc[4 * m4] += g * bv.x;
+          acc[4 * m4 + 1] += g * bv.y;
+          acc[4 * m4 + 2] += g * bv.z;
+          acc[4 * m4 + 3] += g * bv.w;
         }
       } else {
 #pragma unroll
-        for (int m = 0; m < MR / 4; ++m) acc[m] += g * Bs[k][tr * (MR / 4) + m];
+        for (int m = 0; m < MR / 4; ++m) acc[m] += g * Bs[b][k][tr * (MR / 4) + m];
       }
     }
     if constexpr (sizeof(A) == 4) {
@@ -473,6 +482,34 @@ __device__ __forceinline__ void meas_gemm_item(const Config& cfg, int wi, int sp
     } else {
 #pragma unroll
       for (int m = 0; m < MR / 4; ++m) tot[m] += (double)acc[m];
+    }
+  };
+
+  __syncthreads();  // the previous item of this block is done with the shared tiles
+  if (kGrid && tid < MT) s_ga[tid] = grid_time(((double)(a0 + tid) + 0.5) * pb.beta / (double)ntm, pb.tau_scale);
+  if constexpr (NS == 2) {
+    if (n > 0) {
+      prep(0, 0);
+      if (MK < n) prep(MK, 1);
+      __syncthreads();
+      fill(0, 0);
+      __syncthreads();
+      for (int i0 = 0, t = 0; i0 < n; i0 += MK, ++t) {
+        const int b = t & 1;
+        if (i0 + MK < n) fill(i0 + MK, b ^ 1);     // reads the records of stage b ^ 1
+        compute(b);
+        if (i0 + 2 * MK < n) prep(i0 + 2 * MK, b);  // stage b's records were read one tile ago
+        __syncthreads();
+      }
+    }
+  } else {
+    for (int i0 = 0; i0 < n; i0 += MK) {
+      __syncthreads();
+      prep(i0, 0);
+      __syncthreads();
+      fill(i0, 0);
+      __syncthreads();
+      compute(0);
     }
   }
   const int a = a0 + ta;
