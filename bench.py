@@ -67,17 +67,17 @@ OZ_PRODUCTS = 17
 
 
 def sliced_recompute_tflops(peaks):
-    p16 = peaks["bf16_tflops_sustained"]
+    p16 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
     return 4.0 / (2.0 * OZ_PRODUCTS / p16 + 2.0 / (FP32_INSTR_PER_S * 2 / 1e12))
 
 # DRAM bytes (read + write) per window of a kernel group from ncu captures of
 # the named workload (one window of the pooled schedule carries all walkers;
 # mean of two captured launches per kernel), quoted as `traffic` for that group
 # on that workload only:
-#   update  k_upd_tc 863.1 MB read + 532.7 MB written;
-#   extend  k_cand_zero 55.3 + 85.8, k_ext_g_tc 714.0 + 44.9, k_ext_x_tc
-#           704.2 + 23.3, k_cand_cc 99.2 + 1.6 (MB read + written).
-NCU_TRAFFIC = {("batched256", "update"): 1.396e9, ("batched256", "extend"): 1.728e9}
+#   update  k_upd_tc 838.5 MB read + 511.0 MB written;
+#   extend  k_cand_zero 56.0 + 86.9, k_ext_g_tc 697.8 + 45.5, k_ext_x_tc
+#           686.8 + 23.3, k_cand_cc 101.2 + 1.5 (MB read + written).
+NCU_TRAFFIC = {("batched256", "update"): 1.350e9, ("batched256", "extend"): 1.699e9}
 
 
 class ClockSampler:

@@ -173,11 +173,12 @@ typedef struct {
  *            next one (exact: the chain of single-spin updates);
  *   NEGLECT: reject the proposal (no performance loss; breaks detailed
  *            balance, as the paper notes);
- *   UPDATE:  apply the second change within the update (the paper's other
- *            exact option, in place of Bennett's algorithm): it changes one column
- *            of the window's matrix B, so the ratio is 1 + c (1 - (B^-1)_qq) and
- *            B^-1 follows by a rank-1 (Sherman-Morrison) correction; the chain of
- *            single-spin updates without ending the window. */
+ *   UPDATE:  apply the second change within the update (the paper's first
+ *            option, which it carries out with Bennett's factor updating; here
+ *            the change of one column of the window's matrix B gives the ratio
+ *            1 + c (1 - (B^-1)_qq), and B^-1 follows by a rank-1 Sherman-Morrison
+ *            correction): the chain of single-spin updates without ending the
+ *            window. */
 #define DCA_DUP_ABORT 0
 #define DCA_DUP_NEGLECT 1
 #define DCA_DUP_UPDATE 2

@@ -1,5 +1,6 @@
 """Host-side arithmetic of bench.py (no GPU): the roofline entries and the
 derived peak of the mixed-path recompute."""
+import dataclasses
 import os
 import sys
 
@@ -30,9 +31,18 @@ def test_roofline_entries():
     assert r["achieved"] == pytest.approx(3.4) and r["frac"] == pytest.approx(3.4 / 6800.0)
     assert r["launch_ms"] == pytest.approx(200.0)
     assert r["tf32_peak_tflops"] == pytest.approx(1900.0 * 1.1 / 2.25)
+    # mixed path, residual from digit planes: 17 FP16 products at the 16-bit
+    # tensor rate plus the FP32 correction, 4n^3 flop in all
     r = bench.roofline("recompute", 1000.0, 10, work, peaks, "measured", mixed)
-    assert r["bound"] == "alu" and r["achieved"] == pytest.approx(2.0)
-    assert r["peak"] == pytest.approx(bench.MIXED_RECOMPUTE_TFLOPS)
+    assert r["bound"] == "tensor" and r["achieved"] == pytest.approx(2.0)
+    fp32 = 152 * 128 * 2.07e9 * 2 / 1e12
+    assert r["peak"] == pytest.approx(4.0 / (2.0 * 17 / 1900.0 + 2.0 / fp32))
+    peaks_s = dict(peaks, bf16_tflops_sustained=1700.0)
+    r = bench.roofline("recompute", 1000.0, 10, work, peaks_s, "measured", mixed)
+    assert r["peak"] == pytest.approx(4.0 / (2.0 * 17 / 1700.0 + 2.0 / fp32))
+    # the double-float residual: FP32 issue bound
+    r = bench.roofline("recompute", 1000.0, 10, work, peaks, "measured", dataclasses.replace(mixed, recompute_method="newton_df"))
+    assert r["bound"] == "alu" and r["peak"] == pytest.approx(bench.MIXED_RECOMPUTE_TFLOPS)
     r = bench.roofline("recompute", 1000.0, 10, work, peaks, "measured", fp64)
     assert r["peak"] == pytest.approx(bench.FP64_TFLOPS)
     r = bench.roofline("metropolis", 1000.0, 10, work, peaks, "measured", mixed)
