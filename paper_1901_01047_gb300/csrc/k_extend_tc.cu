@@ -115,6 +115,8 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
         const WalkerDev& w = cfg.W[set >> 1];
         const int wi = set >> 1, sp = set & 1, n = w.n, i0 = rb * XT_BM;
         const void* mN = xt_map(cfg, wi, sp, 2 + w.parity);
+        const void* mN32 = xt_map(cfg, wi, sp, 6 + w.parity);  // 32-row boxes: the last, partial row block
+        const int nsub = n - i0 >= XT_BM ? 4 : (n - i0 + 31) / 32;  // 32-row boxes that start below n
         const void* mV = xt_map(cfg, wi, sp, 4);
         for (int j0 = 0; j0 < n; j0 += 32, ++g) {
           const int st = (int)(g % S);
@@ -124,9 +126,13 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
             break;
           }
           const uint32_t s0 = sb + st * L::STAGE;
-          tc::mbar_expect_tx(full(st), (uint32_t)(L::N_BOX + 2 * L::V_BOX));
+          tc::mbar_expect_tx(full(st), (uint32_t)(nsub * (L::N_BOX / 4) + 2 * L::V_BOX));
           armed[st] = u + 1;
-          tc::tma_load_2d(s0, mN, j0, i0, full(st));
+          if (nsub == 4) {
+            tc::tma_load_2d(s0, mN, j0, i0, full(st));
+          } else {
+            for (int q = 0; q < nsub; ++q) tc::tma_load_2d(s0 + q * (L::N_BOX / 4), mN32, j0, i0 + 32 * q, full(st));
+          }
           tc::tma_load_2d(s0 + 2 * L::N_BOX, mV, j0, 0, full(st));
           tc::tma_load_2d(s0 + 2 * L::N_BOX + L::V_BOX, mV, j0, KS_MAX, full(st));
         }
@@ -209,7 +215,9 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
         // Logical 16-byte chunk lc of row r sits at physical chunk lc ^ (r & 7)
         // (128-byte swizzle): walking logical chunks spreads the lanes of a warp
         // over all banks (walking physical chunks put all 32 lanes on 4 banks).
+        // Rows >= n are zeroed: in the last row block their 32-row boxes are not loaded.
         uint8_t* nrow = gb + st * L::STAGE + r * 128;
+        const bool row_ok = i0 + r < n;
 #pragma unroll
         for (int lc = 0; lc < 8; ++lc) {
           const int pc = lc ^ (r & 7);
@@ -219,7 +227,7 @@ __global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
           const int jc = j0 + 4 * lc;
           float xv[4] = {x.x, x.y, x.z, x.w}, hv[4], lv[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) tc::tf32_split(jc + q < n ? xv[q] : 0.f, hv[q], lv[q]);
+          for (int q = 0; q < 4; ++q) tc::tf32_split(row_ok && jc + q < n ? xv[q] : 0.f, hv[q], lv[q]);
           *ph = make_float4(hv[0], hv[1], hv[2], hv[3]);
           *pl = make_float4(lv[0], lv[1], lv[2], lv[3]);
         }
@@ -373,9 +381,11 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
             break;
           }
           const uint32_t s0 = sb + st * L::STAGE;
-          tc::mbar_expect_tx(full(st), (uint32_t)(L::N_TILE + 2 * L::U_TILE));
+          // the 32-column boxes that start below n (the others are not loaded)
+          const int ncb = (n - j0 + 31) / 32 < 4 ? (n - j0 + 31) / 32 : 4;
+          tc::mbar_expect_tx(full(st), (uint32_t)(ncb * L::N_BOX + 2 * L::U_TILE));
           armed[st] = u + 1;
-          for (int b = 0; b < 4; ++b) tc::tma_load_2d(s0 + L::OFF_N + b * L::N_BOX, mN, j0 + 32 * b, i0, full(st));
+          for (int b = 0; b < ncb; ++b) tc::tma_load_2d(s0 + L::OFF_N + b * L::N_BOX, mN, j0 + 32 * b, i0, full(st));
           tc::tma_load_2d(s0 + L::OFF_U, mU, i0, 0, full(st));
           tc::tma_load_2d(s0 + L::OFF_U + L::U_TILE, mU, i0, KS_MAX, full(st));
         }
@@ -459,9 +469,10 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
         // split, and write N^T[j][i] into the K-major planes (row j, 128-byte
         // swizzle: 16-byte chunk (r >> 2) ^ (j & 7), word r & 3).  The 32 lanes
         // of a warp write the 32 words of one 128-byte row: no bank conflicts.
-        // Rows >= n are zeroed (K padding); the logical chunk lc of the box row
-        // sits at physical chunk lc ^ (r & 7).
-        const bool row_ok = i0 + r < n;
+        // Rows >= n (K padding) and the boxes of columns >= n (not loaded) are
+        // zeroed; the logical chunk lc of the box row sits at physical chunk
+        // lc ^ (r & 7).
+        const bool row_ok = i0 + r < n && j0 + 32 * bx < n;  // and the box was loaded
         const uint8_t* nrow = gb + st * L::STAGE + L::OFF_N + bx * L::N_BOX + r * 128;
         uint8_t* tH = gb + st * L::STAGE + L::OFF_T;
         uint8_t* tL = tH + L::T_TILE;

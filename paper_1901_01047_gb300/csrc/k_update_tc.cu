@@ -19,7 +19,9 @@
 //                          accumulators (M = 128, N = BN);
 //   warps 0-3 (epilogue)   TMEM -> registers, add into the N tile held in
 //                          shared memory (128-byte swizzle), TMA store.
-// Rows or columns >= n are stored back unchanged.
+// Only the 32-column boxes, and in the last row block the 32-row boxes, that
+// start below n are loaded and stored; inside them, rows or columns >= n are
+// stored back unchanged.
 #include <cuda.h>
 
 #include <cstdint>
@@ -72,6 +74,17 @@ struct TcIter {
     return pw.next(2 * cfg.n_walkers, [&](int s) { return tc_items(cfg, s); }, set, rb);
   }
 };
+
+// 32-row boxes of the row block at i0 that start below n (4: the whole block),
+// and 32-column boxes of the tile at j0 (BN columns) that start below n.
+__device__ __forceinline__ int tc_row_boxes(int n, int i0) {
+  const int r = n - i0;
+  return r >= TC_BM ? 4 : (r + 31) / 32;
+}
+__device__ __forceinline__ int tc_col_boxes(int n, int j0, int bn) {
+  const int c = (n - j0 + 31) / 32;
+  return c < bn / 32 ? c : bn / 32;
+}
 
 __device__ __forceinline__ const void* tc_map(const Config& cfg, int wi, int sp, int kind) {
   return (const void*)(cfg.tmaps + ((size_t)wi * 2 + sp) * TMAPS_PER_SPIN + kind);
@@ -130,6 +143,8 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
         const void* mA = tc_map(cfg, wi, sp, 0);
         const void* mB = tc_map(cfg, wi, sp, 1);
         const void* mN = tc_map(cfg, wi, sp, 2 + w.parity);
+        const void* mN32 = tc_map(cfg, wi, sp, 6 + w.parity);  // 32-row boxes: the last, partial row block
+        const int nsub = tc_row_boxes(n, i0);
         if (k > 0 && !tc::mbar_wait(a_empty, (k - 1) & 1u, abort_flag, cfg.wait_cycles)) {
           ok = false;
           break;
@@ -149,12 +164,23 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
           }
           const int j0 = t * BN;
           const uint32_t sB = sb + L::OFF_B + st * L::B_STAGE, sN = sb + L::OFF_N + st * L::N_STAGE;
-          tc::mbar_expect_tx(full0 + 8 * st, (uint32_t)(kch * 2 * L::B_CHUNK + L::N_STAGE));
+          // the N tile: 32-column boxes that start below n, and in the last row
+          // block only the 32-row boxes that start below n (the rest of the
+          // tile is neither read nor stored)
+          const int ncb = tc_col_boxes(n, j0, BN);
+          tc::mbar_expect_tx(full0 + 8 * st, (uint32_t)(kch * 2 * L::B_CHUNK + ncb * nsub * (L::N_BOX / 4)));
           armed[st] = u + 1;
           for (int c = 0; c < kch; ++c)
             for (int h = 0; h < 2; ++h)
               tc::tma_load_2d(sB + h * L::B_PLANE + c * L::B_CHUNK, mB, 32 * c, h * cap + j0, full0 + 8 * st);
-          for (int b = 0; b < BN / 32; ++b) tc::tma_load_2d(sN + b * L::N_BOX, mN, j0 + 32 * b, i0, full0 + 8 * st);
+          for (int b = 0; b < ncb; ++b) {
+            if (nsub == 4) {
+              tc::tma_load_2d(sN + b * L::N_BOX, mN, j0 + 32 * b, i0, full0 + 8 * st);
+            } else {
+              for (int q = 0; q < nsub; ++q)
+                tc::tma_load_2d(sN + b * L::N_BOX + q * (L::N_BOX / 4), mN32, j0 + 32 * b, i0 + 32 * q, full0 + 8 * st);
+            }
+          }
         }
       }
       if (!ok) {
@@ -231,6 +257,8 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
       const WalkerDev& w = cfg.W[set >> 1];
       const int wi = set >> 1, sp = set & 1, n = w.n, i0 = rb * TC_BM;
       const void* mN = tc_map(cfg, wi, sp, 2 + w.parity);
+      const void* mN32 = tc_map(cfg, wi, sp, 6 + w.parity);
+      const int nsub = tc_row_boxes(n, i0);
       const bool row_ok = i0 + r < n;
       const int ntiles = (n + BN - 1) / BN;
       for (int t = 0; t < ntiles; ++t, ++g) {
@@ -272,8 +300,16 @@ __global__ void __launch_bounds__(192, 1) k_upd_tc(Config cfg) {
         stop = tc::named_bar_or(1, 128, !okw || *abort_flag != 0);
         if (stop) break;
         if (threadIdx.x == 0) {
-          for (int b = 0; b < BN / 32; ++b)
-            tc::tma_store_2d(mN, j0 + 32 * b, i0, sb + L::OFF_N + st * L::N_STAGE + b * L::N_BOX);
+          const int ncb = tc_col_boxes(n, j0, BN);
+          for (int b = 0; b < ncb; ++b) {
+            const uint32_t box = sb + L::OFF_N + st * L::N_STAGE + b * L::N_BOX;
+            if (nsub == 4) {
+              tc::tma_store_2d(mN, j0 + 32 * b, i0, box);
+            } else {
+              for (int q = 0; q < nsub; ++q)
+                tc::tma_store_2d(mN32, j0 + 32 * b, i0 + 32 * q, box + q * (L::N_BOX / 4));
+            }
+          }
           tc::bulk_commit();
           tc::bulk_wait_read0();
           tc::mbar_arrive(empty0 + 8 * st);
