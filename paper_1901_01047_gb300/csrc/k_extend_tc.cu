@@ -31,16 +31,19 @@ namespace dca {
 
 constexpr int XT_BM = 128;    // rows per item
 
-template <int CN>
+// CTAS CTAs per SM: one with a ring of as many stages as fit, or (CN = 64)
+// two with two stages each, so that one CTA's epilogue overlaps the other's
+// loads and products.
+template <int CN, int CTAS = 1>
 struct XtLayout {
   static constexpr int N_BOX = XT_BM * 128;     // 128 rows x 32 FP32 columns
   static constexpr int V_BOX = CN * 128;        // CN rows x 32 columns
   static constexpr int STAGE = 2 * N_BOX + 2 * V_BOX;  // N (hi), N lo, V hi, V lo
-  static constexpr int STAGES = CN <= 64 ? 4 : 3;      // ring depth: as many stages as fit
+  static constexpr int STAGES = CTAS == 2 ? 2 : (CN <= 64 ? 4 : 3);  // ring depth
   static constexpr int OFF_BAR = STAGES * STAGE;
   static constexpr int SMEM = OFF_BAR + 256 + 1024;
   static constexpr uint32_t TMEM_COLS = CN < 32 ? 32 : CN;
-  static_assert(SMEM + sizeof(ItemPlan) <= 232448, "shared memory (dynamic + the static item plan)");
+  static_assert(CTAS * (SMEM + sizeof(ItemPlan) + 1024) <= 233472, "shared memory of the CTAs of one SM");
 };
 
 __device__ __forceinline__ long long xt_items(const Config& cfg, int s) {
@@ -60,9 +63,9 @@ __device__ __forceinline__ const void* xt_map(const Config& cfg, int wi, int sp,
   return (const void*)(cfg.tmaps + ((size_t)wi * 2 + sp) * TMAPS_PER_SPIN + kind);
 }
 
-template <int CN>
-__global__ void __launch_bounds__(192, 1) k_ext_g_tc(Config cfg) {
-  using L = XtLayout<CN>;
+template <int CN, int CTAS>
+__global__ void __launch_bounds__(192, CTAS) k_ext_g_tc(Config cfg) {
+  using L = XtLayout<CN, CTAS>;
   extern __shared__ uint8_t xt_raw[];
   const uint32_t raw = tc::smem_u32(xt_raw);
   const uint32_t sb = (raw + 1023u) & ~1023u;
@@ -539,10 +542,10 @@ __global__ void __launch_bounds__(192, 1) k_ext_x_tc(Config cfg) {
 }
 
 cudaError_t setup_ext_tc() {
-  cudaError_t e = cudaFuncSetAttribute(k_ext_g_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       XtLayout<64>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(k_ext_g_tc<64, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       XtLayout<64, 2>::SMEM);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ext_g_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, XtLayout<128>::SMEM);
+    e = cudaFuncSetAttribute(k_ext_g_tc<128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, XtLayout<128>::SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_ext_x_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, Xx2Layout<64>::SMEM);
   if (e == cudaSuccess)
@@ -552,8 +555,8 @@ cudaError_t setup_ext_tc() {
 
 void launch_ext_g_tc(const Config& cfg, cudaStream_t st) {
   const int sms = device_sm_count();
-  if (ext_tile_c(cfg.ks) <= 64) k_ext_g_tc<64><<<sms, 192, XtLayout<64>::SMEM, st>>>(cfg);
-  else k_ext_g_tc<128><<<sms, 192, XtLayout<128>::SMEM, st>>>(cfg);
+  if (ext_tile_c(cfg.ks) <= 64) k_ext_g_tc<64, 2><<<2 * sms, 192, XtLayout<64, 2>::SMEM, st>>>(cfg);
+  else k_ext_g_tc<128, 1><<<sms, 192, XtLayout<128>::SMEM, st>>>(cfg);
 }
 
 void launch_ext_x_tc(const Config& cfg, cudaStream_t st) {
