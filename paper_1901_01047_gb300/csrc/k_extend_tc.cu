@@ -9,7 +9,8 @@
 // free during the extension); N tiles are split in shared memory.
 //
 // Work item = one 128-row block of one walker-spin N.  The CTA streams the
-// block's columns 32 at a time through a ring of four stages (three for CN = 128):
+// block's columns 32 at a time through a ring of stages (CN = 64: two CTAs
+// per SM with two stages each; CN = 128: one CTA with three):
 //   warp 4 (TMA producer)   N box (128 rows x 32 columns) and the V boxes;
 //   warps 0-3 (converters)  split the N box in place into hi and a lo plane,
 //                           zero the columns >= n; at the end of the item they
