@@ -75,9 +75,9 @@ def sliced_recompute_tflops(peaks):
 # mean of two captured launches per kernel), quoted as `traffic` for that group
 # on that workload only:
 #   update  k_upd_tc 789.1 MB read + 457.0 MB written;
-#   extend  k_cand_zero 56.0 + 86.7, k_ext_g_tc 654.4 + 45.0, k_ext_x_tc
+#   extend  k_cand_zero 56.0 + 86.7, k_ext_g_tc 664.6 + 44.2, k_ext_x_tc
 #           654.2 + 23.2, k_cand_cc 101.1 + 1.5 (MB read + written).
-NCU_TRAFFIC = {("batched256", "update"): 1.246e9, ("batched256", "extend"): 1.622e9}
+NCU_TRAFFIC = {("batched256", "update"): 1.246e9, ("batched256", "extend"): 1.632e9}
 
 
 class ClockSampler:
