@@ -143,6 +143,8 @@ def workload_of(args):
         wl = dataclasses.replace(wl, schedule=args.schedule)
     if getattr(args, "duplicate_rule", None):
         wl = dataclasses.replace(wl, duplicate_rule=args.duplicate_rule)
+    if getattr(args, "walkers", None):
+        wl = dataclasses.replace(wl, walkers=args.walkers)
     return wl
 
 
@@ -670,6 +672,9 @@ def main():
                     help="walker schedule (default: the workload's)")
     ap.add_argument("--duplicate-rule", choices=["abort", "update"], default=None,
                     help="a spin changed twice in one window (default: the workload's)")
+    ap.add_argument("--walkers", type=int, default=None,
+                    help="run only the first K walkers of the workload (small profiling captures; "
+                         "the line is then not the workload's)")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off) "
                          "and launch the window kernels from the host in that region")

@@ -47,3 +47,14 @@ def test_roofline_entries():
     assert r["peak"] == pytest.approx(bench.FP64_TFLOPS)
     r = bench.roofline("metropolis", 1000.0, 10, work, peaks, "measured", mixed)
     assert r["bound"] is None and r["frac"] is None
+
+
+def test_workload_overrides():
+    import argparse
+    import bench
+    args = argparse.Namespace(workload="batched256", schedule="lockstep", duplicate_rule="abort", walkers=32)
+    wl = bench.workload_of(args)
+    assert wl.walkers == 32 and wl.schedule == "lockstep" and wl.duplicate_rule == "abort"
+    params, wp = wl.problem_params()
+    full, _ = bench.workload_of(argparse.Namespace(workload="batched256")).problem_params()
+    assert len(params) == 32 and params == full[:32]  # the first walkers' problems of the full batch
